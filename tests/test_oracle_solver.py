@@ -1,0 +1,278 @@
+"""Pins of the oracle's smoothers, multigrid and Krylov solvers (CPU only).
+
+FDM / Schwarz: on rectilinear (tensor-product) box meshes the separable extended operator of
+eq 5 is exactly the Galerkin restriction R_e A R_e^T, so the fast-diagonalisation solve of eqs
+8-9 must equal the dense inverse of that window of the brute-force assembled matrix.
+Chebyshev (Algorithm 2): I - M A equals the scaled Chebyshev polynomial of SA, built here by the
+three-term recurrence and cosh(m arccosh sigma).  Arnoldi: exact once the Krylov space is
+exhausted.  Multigrid: the transfers are adjoint and reproduce coarse polynomials; the V-cycle
+(Algorithm 1) is linear with an exact coarse solve and contracts the error.  Solvers: the
+converged solution equals a dense direct solve; the discrete solution converges spectrally.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as o
+import workloads as wl
+from tests.dense_reference import assembled_stiffness, free_nodes
+
+
+def rectilinear_lattice(xs, ys, zs):
+    V = np.empty((len(zs), len(ys), len(xs), 3))
+    V[..., 0] = np.asarray(xs)[None, None, :]
+    V[..., 1] = np.asarray(ys)[None, :, None]
+    V[..., 2] = np.asarray(zs)[:, None, None]
+    return V
+
+
+def window_nodes(lv, e):
+    """Global ids of the free nodes of element e's extended window, in window order, and their
+    positions (a, b, c) in the pbar^3 window."""
+    p = lv.p
+    pb = p + 3
+    nx, ny, nz = lv.nel
+    NX, NY, NZ = lv.lattice
+    ex, ey, ez = e % nx, (e // nx) % ny, e // (nx * ny)
+    free = np.zeros(lv.n_global, dtype=bool)
+    free[lv.gid[lv.mask > 0]] = True
+    ids, pos = [], []
+    for c in range(pb):
+        for b in range(pb):
+            for a in range(pb):
+                I, J, K = ex * p - 1 + a, ey * p - 1 + b, ez * p - 1 + c
+                if 0 <= I < NX and 0 <= J < NY and 0 <= K < NZ:
+                    g = I + NX * (J + NY * K)
+                    if free[g]:
+                        ids.append(g)
+                        pos.append((c, b, a))
+    return np.array(ids), pos
+
+
+@pytest.fixture(scope="module")
+def rect_case():
+    V = rectilinear_lattice([0, 0.3, 0.55, 1.0], [0, 0.45, 1.0], [0, 0.6, 1.0])
+    nel = (3, 2, 2)
+    p = 3
+    lv = o.make_level(V, nel, p, amp=0.0)
+    x, w = o.gll(p)
+    A = assembled_stiffness(lv, x, w)
+    lv.extra["fdm"] = o.fdm_setup(lv, V, amp=0.0)
+    return V, lv, A
+
+
+def test_fdm_similarity_transforms():
+    rng = np.random.default_rng(0)
+    for p in (3, 5, 7):
+        for hl, hr, dl, dr in [(True, True, True, True), (False, True, True, True),
+                               (True, False, True, True), (False, True, False, True)]:
+            lens = rng.uniform(0.5, 2.0, size=(4, 3))
+            Ab, Bd, active = o.fdm_1d(p, lens, hl, hr, dl, dr)
+            S, L = o.fdm_factors(p, lens, hl, hr, dl, dr)
+            Sa = S[:, active, :len(active)]
+            for m in range(4):
+                StAS = Sa[m].T @ Ab[m] @ Sa[m]
+                StBS = Sa[m].T @ np.diag(Bd[m]) @ Sa[m]
+                assert np.allclose(StAS, np.diag(L[m, :len(active)]), atol=1e-12 * np.abs(StAS).max())
+                assert np.allclose(StBS, np.eye(len(active)), atol=1e-13)
+            assert Ab.shape[1] == (p + 3) - (not hl) - (not hr) - ((not hl) and dl) - ((not hr) and dr)
+
+
+def test_fdm_equals_dense_window_inverse(rect_case):
+    V, lv, A = rect_case
+    S, Lm = lv.extra["fdm"]
+    rng = np.random.default_rng(1)
+    pb = lv.p + 3
+    for e in range(lv.E):
+        ids, pos = window_nodes(lv, e)
+        Aw = A[np.ix_(ids, ids)]
+        rw = rng.standard_normal(len(ids))
+        rbar = np.zeros((1, pb, pb, pb))
+        for v, (c, b, a) in zip(rw, pos):
+            rbar[0, c, b, a] = v
+        z = o.fdm_apply(S[e:e + 1], Lm[e:e + 1], rbar)[0]
+        zw = np.array([z[c, b, a] for (c, b, a) in pos])
+        assert np.allclose(zw, np.linalg.solve(Aw, rw), rtol=1e-11, atol=1e-11 * np.abs(zw).max())
+        inactive = np.ones((pb, pb, pb), dtype=bool)
+        for (c, b, a) in pos:
+            inactive[c, b, a] = False
+        assert np.all(z[inactive] == 0.0)
+
+
+def dense_schwarz(lv, A, kind):
+    """Dense RAS (own nodes weighted 1/mult) or ASM (whole window, then divided by the
+    number of windows covering the node) with exact window inverses."""
+    n = lv.n_global
+    Msum = np.zeros((n, n))
+    cover = np.zeros(n)
+    mult_g = np.zeros(n)
+    mult_g[lv.gid.ravel()] = lv.mult.ravel()
+    for e in range(lv.E):
+        ids, pos = window_nodes(lv, e)
+        inv = np.linalg.inv(A[np.ix_(ids, ids)])
+        own = set(lv.gid[e].ravel().tolist())
+        for r_, g in enumerate(ids):
+            if kind == "ras":
+                if g in own:
+                    Msum[g, ids] += inv[r_] / mult_g[g]
+            else:
+                Msum[g, ids] += inv[r_]
+                cover[g] += 1
+    if kind == "asm":
+        nz = cover > 0
+        Msum[nz] /= cover[nz][:, None]
+    return Msum
+
+
+@pytest.mark.parametrize("kind", ["ras", "asm"])
+def test_schwarz_equals_dense(rect_case, kind):
+    V, lv, A = rect_case
+    M = dense_schwarz(lv, A, kind)
+    rng = np.random.default_rng(2)
+    rg = rng.standard_normal(lv.n_global)
+    r = lv.mask * o.from_global(lv, rg)
+    s = o.ras(lv, r) if kind == "ras" else o.asm(lv, r)
+    cols = free_nodes(lv)
+    ref = M[np.ix_(cols, cols)] @ o.to_global(lv, r)[cols]
+    assert np.allclose(o.to_global(lv, s)[cols], ref, rtol=1e-11, atol=1e-11 * np.abs(ref).max())
+
+
+def chebyshev_matrix_polynomial(SA, lmin, lmax, m):
+    theta, delta = 0.5 * (lmax + lmin), 0.5 * (lmax - lmin)
+    X = (theta * np.eye(len(SA)) - SA) / delta
+    T0, T1 = np.eye(len(SA)), X
+    for _ in range(m - 1):
+        T0, T1 = T1, 2 * X @ T1 - T0
+    sigma = theta / delta
+    return T1 / math.cosh(m * math.acosh(sigma))
+
+
+def operator_matrix(lv, fn, cols):
+    M = np.zeros((len(cols), len(cols)))
+    for n, g in enumerate(cols):
+        ug = np.zeros(lv.n_global)
+        ug[g] = 1.0
+        M[:, n] = o.to_global(lv, fn(lv.mask * o.from_global(lv, ug)))[cols]
+    return M
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+@pytest.mark.parametrize("smoother", ["jacobi", "ras"])
+def test_chebyshev_error_operator(rect_case, order, smoother):
+    V, lv, A = rect_case
+    lv.extra["diag"] = o.jacobi_diag(lv)
+    cols = free_nodes(lv)
+    Af = A[np.ix_(cols, cols)]
+    S = (lambda r: o.jacobi(lv, r)) if smoother == "jacobi" else (lambda r: o.ras(lv, r))
+    Sm = operator_matrix(lv, S, cols)
+    SA = Sm @ Af
+    lmax_true = np.max(np.abs(np.linalg.eigvals(SA)))
+    lmin, lmax = 0.1 * lmax_true, 1.1 * lmax_true
+    Mm = operator_matrix(lv, lambda r: o.chebyshev(r, lambda u: o.ax(lv, u), S, lmin, lmax, order), cols)
+    lhs = np.eye(len(cols)) - Mm @ Af
+    rhs_ = chebyshev_matrix_polynomial(SA, lmin, lmax, order + 1)
+    assert np.allclose(lhs, rhs_, atol=1e-9)
+    if smoother == "jacobi":
+        # SA is similar to an SPD matrix: on [lmin, lmax] the amplification is bounded by
+        # 1/T_{k+1}(sigma); below lmin it stays below 1
+        ev = np.linalg.eigvals(SA).real
+        theta, delta = 0.5 * (lmax + lmin), 0.5 * (lmax - lmin)
+        bound = 1.0 / math.cosh((order + 1) * math.acosh(theta / delta))
+        amp = np.abs(np.linalg.eigvals(lhs))
+        inside = (ev >= lmin) & (ev <= lmax)
+        amp_in = np.abs(np.polynomial.chebyshev.chebval((theta - ev[inside]) / delta, [0] * (order + 1) + [1])) * bound
+        assert np.all(amp_in <= bound * (1 + 1e-9))
+        assert amp.max() <= 1.0 + 1e-9
+
+
+@pytest.mark.parametrize("smoother", ["jacobi", "ras"])
+def test_arnoldi_estimate(rect_case, smoother):
+    V, lv, A = rect_case
+    lv.extra["diag"] = o.jacobi_diag(lv)
+    cols = free_nodes(lv)
+    S = (lambda r: o.jacobi(lv, r)) if smoother == "jacobi" else (lambda r: o.ras(lv, r))
+    SA = operator_matrix(lv, S, cols) @ A[np.ix_(cols, cols)]
+    lam_true = np.max(np.abs(np.linalg.eigvals(SA)))
+    v0 = lv.mask * o.from_global(lv, wl.arnoldi_start_global(1000, lv.n_global))
+    dotf = lambda a, b: o.dot(lv, a, b)
+    Aop = lambda u: o.ax(lv, u)
+    lam_full, _ = o.arnoldi_lambda(Aop, S, v0, dotf, steps=len(cols) + 5)
+    assert abs(lam_full - lam_true) < 1e-9 * lam_true
+    lam10, H = o.arnoldi_lambda(Aop, S, v0, dotf, steps=10)
+    assert H.shape == (11, 10)
+    assert 0.8 * lam_true < lam10 <= lam_true * (1 + 1e-10)
+
+
+@pytest.fixture(scope="module")
+def mg_case():
+    nel = (2, 2, 2)
+    V = wl.vertex_lattice(nel, 0.1, seed=4)
+    return V, nel
+
+
+def test_transfers_adjoint_and_exact(mg_case):
+    V, nel = mg_case
+    for pf, pc in [(5, 3), (3, 1), (7, 3)]:
+        lf = o.make_level(V, nel, pf)
+        lc = o.make_level(V, nel, pc)
+        rng = np.random.default_rng(pf)
+        rf = lf.mask * o.from_global(lf, rng.standard_normal(lf.n_global))
+        ec = lc.mask * o.from_global(lc, rng.standard_normal(lc.n_global))
+        lhs = o.dot(lc, o.restrict(lf, lc, rf), ec)
+        rhs_ = o.dot(lf, rf, o.prolong(lf, lc, ec))
+        assert abs(lhs - rhs_) < 1e-12 * max(1.0, abs(lhs))
+    # prolongation reproduces a global polynomial of the coarse degree on an affine mesh
+    Va = wl.vertex_lattice(nel)
+    lf = o.make_level(Va, nel, 5, bc=("N",) * 6, amp=0.0)
+    lc = o.make_level(Va, nel, 3, bc=("N",) * 6, amp=0.0)
+    poly = lambda X: X[0] ** 3 - 2 * X[1] ** 2 * X[2] + X[0] * X[1] * X[2] + 1
+    assert np.allclose(o.prolong(lf, lc, poly(lc.X)), poly(lf.X), atol=1e-12)
+
+
+@pytest.mark.parametrize("smoother", ["ras", "jacobi"])
+def test_vcycle_linear_and_contracting(mg_case, smoother):
+    V, nel = mg_case
+    pmg = o.pmg_setup(V, nel, (3, 1), smoother=smoother, order=2, coarse_tol=1e-14, coarse_maxit=2000)
+    lv = pmg.levels[0]
+    rng = np.random.default_rng(3)
+    a = lv.mask * o.from_global(lv, rng.standard_normal(lv.n_global))
+    b = lv.mask * o.from_global(lv, rng.standard_normal(lv.n_global))
+    va, vb, vab = o.vcycle(pmg, a), o.vcycle(pmg, b), o.vcycle(pmg, a + 2 * b)
+    assert np.allclose(vab, va + 2 * vb, atol=1e-9 * np.abs(vab).max())
+    cols = free_nodes(lv)
+    x, w = o.gll(3)
+    Af = assembled_stiffness(lv, x, w)[np.ix_(cols, cols)]
+    Mm = operator_matrix(lv, lambda r: o.vcycle(pmg, r), cols)
+    rho = np.max(np.abs(np.linalg.eigvals(np.eye(len(cols)) - Mm @ Af)))
+    assert rho < 0.5
+
+
+@pytest.mark.parametrize("method", ["fpcg", "fgmres"])
+@pytest.mark.parametrize("pre", ["jacobi", "ras", "asm"])
+def test_solution_matches_direct_solve(mg_case, method, pre):
+    V, nel = mg_case
+    lv, b = o.problem(V, nel, 5)
+    pmg = None if pre == "jacobi" else o.pmg_setup(V, nel, (5, 3, 1), smoother=pre, order=2)
+    xsol, it, rel = o.solve(lv, b, pmg, method=method, tol=1e-10)
+    assert rel <= 1e-10 and it < 400
+    cols = free_nodes(lv)
+    xg, wg = o.gll(5)
+    Af = assembled_stiffness(lv, xg, wg)[np.ix_(cols, cols)]
+    xd = np.linalg.solve(Af, o.to_global(lv, b)[cols])
+    assert np.allclose(o.to_global(lv, xsol)[cols], xd, rtol=0, atol=1e-8 * np.abs(xd).max())
+    true_res = b - o.ax(lv, xsol)
+    assert math.sqrt(o.dot(lv, true_res, true_res)) <= 1e-9 * math.sqrt(o.dot(lv, b, b))
+
+
+def test_spectral_convergence():
+    nel = (2, 2, 2)
+    V = wl.vertex_lattice(nel, 0.05, seed=0)
+    errs = []
+    for p in (2, 4, 6, 8):
+        lv, b = o.problem(V, nel, p)
+        x, it, rel = o.solve(lv, b, None, tol=1e-13, maxit=5000)
+        errs.append(np.max(np.abs(x - wl.u_exact(*lv.X))))
+    for a, b_ in zip(errs, errs[1:]):
+        assert b_ < a / 8.0
+    assert errs[-1] < 5e-5
