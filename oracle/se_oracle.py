@@ -337,6 +337,8 @@ def fdm_1d(p, lengths, has_left, has_right, dir_left, dir_right):
     A1 = np.zeros((M, n1, n1))
     B1 = np.zeros((M, n1))
     for s in range(3):
+        if (s == 0 and not has_left) or (s == 2 and not has_right):
+            continue                      # no neighbour: no segment beyond this side
         o = s * p
         l = lengths[:, s]
         A1[:, o:o + N, o:o + N] += (2.0 / l)[:, None, None] * Ke[None]

@@ -50,12 +50,12 @@ def window_nodes(lv, e):
     return np.array(ids), pos
 
 
-@pytest.fixture(scope="module")
-def rect_case():
+@pytest.fixture(scope="module", params=[("D",) * 6, ("N", "D", "D", "N", "D", "D")])
+def rect_case(request):
     V = rectilinear_lattice([0, 0.3, 0.55, 1.0], [0, 0.45, 1.0], [0, 0.6, 1.0])
     nel = (3, 2, 2)
     p = 3
-    lv = o.make_level(V, nel, p, amp=0.0)
+    lv = o.make_level(V, nel, p, bc=request.param, amp=0.0)
     x, w = o.gll(p)
     A = assembled_stiffness(lv, x, w)
     lv.extra["fdm"] = o.fdm_setup(lv, V, amp=0.0)
