@@ -1,0 +1,210 @@
+/*
+ * se.h -- C ABI of the GB300 spectral-element Poisson library (libse.so).
+ *
+ * The library implements the pressure-Poisson hot path of Phillips, Kerkemeier and Fischer,
+ * "Tuning Spectral Element Preconditioners for Parallel Scalability on GPUs" (arXiv 2110.07663):
+ * the matrix-free spectral element operator (Sec. 2.1), the p-multigrid V-cycle (Algorithm 1)
+ * with Chebyshev acceleration (Algorithm 2) of restrictive/additive Schwarz smoothers built on
+ * fast-diagonalisation local solves (Sec. 2.3.2, eqs 4-9) or of Jacobi smoothing, and flexible
+ * Krylov outer solvers (Sec. 2.2).  One GPU, hand-written CUDA kernels for sm_103a.
+ *
+ * Conventions for every call:
+ *  - Return value: SE_OK (0) or an se_status error code; se_last_error() gives a message
+ *    (thread-local, valid until the next failing call on that thread).
+ *  - Handles (se_mesh_t, se_pmg_t, se_server_t) are opaque, owned by the library, freed only by
+ *    the matching *_destroy call.
+ *  - Vectors are CALLER-OWNED device pointers (cudaMalloc or torch tensors) of FP64 values in
+ *    L-vector layout unless stated: length L = E*N^3 with N = p+1, element-major, index
+ *    i + N*(j + N*(k + N*e)) with i the fastest reference direction r; element
+ *    e = ex + nx*(ey + ny*ez).  "Continuous" means all local copies of a global node hold the
+ *    same value.  The library never frees caller memory and keeps no pointer to it after
+ *    returning (except se_serve_submit, which copies the right-hand side).
+ *  - Streams: `stream` is a cudaStream_t passed as void*; NULL means the handle's own stream,
+ *    a blocking stream (ordered with the legacy default stream).  Calls enqueue work and return
+ *    without synchronising unless they return host results (se_dot, se_solve statistics,
+ *    se_pmg_coarse_solve iteration count, se_serve_*).
+ */
+#ifndef SE_H
+#define SE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+enum se_status {
+  SE_OK = 0,
+  SE_EINVAL = 1,    /* invalid argument (null pointer, unsupported order, bad descriptor) */
+  SE_ENOMEM = 2,    /* device or host allocation failed */
+  SE_ENOTCONV = 3,  /* solver reached maxit without meeting the tolerance; stats are filled */
+  SE_ECUDA = 4,     /* a CUDA runtime call failed; se_last_error() names it */
+  SE_ETIMEOUT = 5,  /* a bounded device-side wait ran out (no hang: the kernel returned) */
+  SE_EBUSY = 6,     /* served request still pending */
+  SE_EREFUSED = 7   /* served request can never fit the HBM budget */
+};
+
+enum { SE_BC_DIRICHLET = 0, SE_BC_NEUMANN = 1 };
+enum { SE_FP64 = 0, SE_FP32 = 1 };
+enum { SE_SMOOTH_JACOBI = 0, SE_SMOOTH_RAS = 1, SE_SMOOTH_ASM = 2 };
+enum { SE_FPCG = 0, SE_FGMRES = 1 };
+/* se_ax flags */
+enum { SE_AX_ASSEMBLE = 1, SE_AX_MASK = 2, SE_AX_FP32 = 4 };
+
+#define SE_MAX_LEVELS 8
+#define SE_MAX_ORDER 10
+
+typedef struct se_mesh_s* se_mesh_t;
+typedef struct se_pmg_s* se_pmg_t;
+
+const char* se_last_error(void);
+int se_version(void);
+
+/* ---------------------------------------------------------------- mesh (Sec. 2.1) */
+/* Box-topology hexahedral mesh: nel[0]*nel[1]*nel[2] elements of a structured lattice of
+ * (nel[0]+1)(nel[1]+1)(nel[2]+1) vertices.  Each element is mapped trilinearly from its 8
+ * vertices to its GLL points, then every node x receives the smooth map
+ * x_c <- x_c + deform_amp*sin(2 pi x)sin(2 pi y)sin(2 pi z) (same scalar for c = x, y, z).  The
+ * isoparametric geometry of Sec. 2.1 is built from those node positions. */
+typedef struct se_mesh_desc {
+  int nel[3];              /* elements per direction, each >= 1 */
+  int p;                   /* polynomial order, 1..SE_MAX_ORDER */
+  const double* vertex_xyz;/* HOST, optional: vertex positions, xyz interleaved, vertex id
+                              v = a + (nx+1)(b + (ny+1)c); NULL: unit box lattice whose interior
+                              vertices move by perturb_frac*h*(2U-1) per direction, U the
+                              SplitMix64 uniform number 3v+d of stream `seed` */
+  double deform_amp;       /* amplitude of the smooth map (0.05 in the synthetic workloads) */
+  double perturb_frac;     /* used only when vertex_xyz == NULL */
+  uint64_t seed;
+  int bc[6];               /* faces x-, x+, y-, y+, z-, z+: SE_BC_DIRICHLET or SE_BC_NEUMANN */
+  int flags;               /* reserved, 0 */
+} se_mesh_desc;
+
+typedef struct se_mesh_info {
+  int64_t E, N, L, n_global;  /* elements, points per direction, local points, global nodes */
+  int64_t n_dof;              /* E*p^3, the paper's n (Sec. 1, Table 2) */
+  int p;
+  int nel[3];
+} se_mesh_info;
+
+/* Builds geometry, the QQ^T index map, masks and the Jacobi diagonal on the device. */
+int se_mesh_create(const se_mesh_desc* desc, se_mesh_t* out);
+int se_mesh_destroy(se_mesh_t m);
+int se_mesh_get_info(se_mesh_t m, se_mesh_info* info);
+/* Node coordinates: xyz_dev is a device array of 3*L doubles (x block, y block, z block). */
+int se_mesh_nodes(se_mesh_t m, double* xyz_dev, void* stream);
+/* Vertex lattice actually used (host array of 3*(nx+1)(ny+1)(nz+1) doubles, interleaved). */
+int se_mesh_vertices(se_mesh_t m, double* xyz_host);
+/* b = M QQ^T (B_L f) (Sec. 2.1, eq 3): f_dev holds f at the nodes (L-vector). */
+int se_mesh_rhs(se_mesh_t m, const double* f_dev, double* b_dev, void* stream);
+
+/* ---------------------------------------------------------------- operator (Sec. 2.1) */
+/* y = [M] [QQ^T] A_L [M] u.  flags: SE_AX_ASSEMBLE applies QQ^T (direct stiffness
+ * summation), SE_AX_MASK zeroes Dirichlet nodes of input and output, SE_AX_FP32 computes in
+ * FP32 (inputs and outputs stay FP64).  A_L is applied by tensor-product sum factorisation
+ * (Sec. 1: ~7E(p+1)^3 reads, 12E(p+1)^4 operations).  u and y must not overlap. */
+int se_ax(se_mesh_t m, const double* u, double* y, int flags, void* stream);
+/* In place u <- [M] QQ^T u (Sec. 2.1, gather-scatter); mask != 0 also zeroes Dirichlet nodes. */
+int se_gs(se_mesh_t m, double* u, int mask, void* stream);
+/* Unique-node inner product sum_l a_l b_l / mult_l of two continuous L-vectors (FP64,
+ * deterministic order).  Synchronises the stream; result written to *out_host. */
+int se_dot(se_mesh_t m, const double* a, const double* b, double* out_host, void* stream);
+/* Assembled, masked diagonal of A (Jacobi surrogate, Sec. 2.3.3) as an L-vector; Dirichlet
+ * nodes get 1. */
+int se_jacobi_diag(se_mesh_t m, double* d_dev, void* stream);
+
+/* ---------------------------------------------------------------- p-multigrid (Sec. 2.3) */
+typedef struct se_pmg_desc {
+  int nlev;                      /* levels, 2..SE_MAX_LEVELS */
+  int schedule[SE_MAX_LEVELS];   /* orders, schedule[0] == mesh p, strictly decreasing */
+  int smoother;                  /* SE_SMOOTH_RAS, SE_SMOOTH_ASM or SE_SMOOTH_JACOBI */
+  int cheb_order[SE_MAX_LEVELS]; /* Chebyshev order (loop count of Algorithm 2) per level */
+  double eig_lo, eig_hi;         /* bounds (eig_lo, eig_hi)*lambda-tilde; paper: (0.1, 1.1) */
+  int arnoldi_steps;             /* Arnoldi rounds for lambda-tilde; paper: 10 */
+  uint64_t seed;                 /* start-vector stream: level l uses 1000 + l + 7919*seed */
+  double coarse_tol;             /* coarsest-level Jacobi-PCG relative tolerance (1e-4) */
+  int coarse_maxit;              /* and iteration cap (500) */
+  int precision;                 /* SE_FP64, or SE_FP32 for the whole V-cycle except the
+                                    coarse solve (Arnoldi and coarse solve stay FP64) */
+} se_pmg_desc;
+
+/* Builds the levels (each rediscretised on the same mapped mesh), Jacobi diagonals, FDM
+ * factors S and Lambda (eqs 6-7), the assembled coarsest operator, and the Chebyshev bounds
+ * from Arnoldi on S A at every level but the coarsest.  Synchronises. */
+int se_pmg_setup(se_mesh_t m, const se_pmg_desc* desc, se_pmg_t* out);
+int se_pmg_destroy(se_pmg_t pmg);
+/* z = M r: one V-cycle (Algorithm 1) with x = 0 on entry.  r, z: fine-level L-vectors. */
+int se_pmg_apply(se_pmg_t pmg, const double* r, double* z, void* stream);
+/* lambda-tilde of level lvl (largest |Ritz value| of Arnoldi on S A, Sec. 2.3.3). */
+int se_pmg_lambda(se_pmg_t pmg, int lvl, double* lam);
+int se_pmg_level_info(se_pmg_t pmg, int lvl, se_mesh_info* info);
+/* Level-lvl building blocks, all on level-lvl L-vectors (FP64 in/out; computed in the pmg's
+ * precision except where noted): */
+/* y = M QQ^T A_L u (FP64 always). */
+int se_pmg_level_ax(se_pmg_t pmg, int lvl, const double* u, double* y, void* stream);
+/* s = S r: the surrogate smoother (RAS: eq 4 with own-node weights; ASM: eq 4; Jacobi). */
+int se_pmg_smooth(se_pmg_t pmg, int lvl, const double* r, double* s, void* stream);
+/* rbar = R_e r for all elements: E*(p+3)^3 values, element-major, window index
+ * a + (p+3)*(b + (p+3)*c), window point (a,b,c) = lattice node (ex*p-1+a, ey*p-1+b, ez*p-1+c);
+ * 0 outside the domain. */
+int se_pmg_gather_ext(se_pmg_t pmg, int lvl, const double* r, double* rbar, void* stream);
+/* zbar = Abar_e^-1 rbar per element by fast diagonalisation (eqs 8-9), E*(p+3)^3 values. */
+int se_pmg_fdm(se_pmg_t pmg, int lvl, const double* rbar, double* zbar, void* stream);
+/* x = Chebyshev correction of Algorithm 2 for residual res (order and bounds of the level). */
+int se_pmg_cheby(se_pmg_t pmg, int lvl, const double* res, double* x, void* stream);
+/* rc = P^T rf (level lvl -> lvl+1) and ef = P ec (level lvl+1 -> lvl). */
+int se_pmg_restrict(se_pmg_t pmg, int lvl, const double* rf, double* rc, void* stream);
+int se_pmg_prolong(se_pmg_t pmg, int lvl, const double* ec, double* ef, void* stream);
+/* Coarsest level: x = A_c^-1 r by Jacobi-PCG to coarse_tol (FP64, one persistent cooperative
+ * launch).  *iters receives the iteration count (synchronises). */
+int se_pmg_coarse_solve(se_pmg_t pmg, const double* r, double* x, int* iters, void* stream);
+
+/* ---------------------------------------------------------------- solve (Sec. 2.2) */
+typedef struct se_solve_opts {
+  int method;        /* SE_FPCG (flexible CG) or SE_FGMRES (right-preconditioned, flexible) */
+  int restart;       /* FGMRES restart length m (paper: 20) */
+  double tol;        /* stop when ||r_k||_2 / ||r_0||_2 <= tol (unique-node 2-norm) */
+  int maxit;
+  int graph_capture; /* 1: replay each preconditioner application as a captured CUDA graph */
+  void* stream;      /* NULL: the mesh's stream */
+} se_solve_opts;
+
+typedef struct se_solve_stats {
+  int iterations;
+  int status;
+  double rel_residual;   /* final ||r||/||r_0|| as tracked by the method */
+  double ms_total;       /* wall time of the solve (events on the stream) */
+  double ms_precond;     /* time inside preconditioner applications */
+  double ms_operator;    /* time inside outer operator applications */
+} se_solve_stats;
+
+/* x (in: initial guess, out: solution) of A x = b; pmg == NULL selects Jacobi preconditioning.
+ * Returns SE_ENOTCONV (stats filled) if maxit is reached.  Synchronises. */
+int se_solve(se_mesh_t m, se_pmg_t pmg, const double* b, double* x, const se_solve_opts* opts,
+             se_solve_stats* stats);
+
+/* ---------------------------------------------------------------- profiling */
+/* Kernel classes timed with CUDA events on their launch stream while profiling is enabled. */
+enum {
+  SE_K_AX = 0, SE_K_GS = 1, SE_K_FDM = 2, SE_K_CHEBY_UPD = 3, SE_K_RESTRICT = 4,
+  SE_K_PROLONG = 5, SE_K_COARSE = 6, SE_K_KRYLOV = 7, SE_K_JACOBI = 8, SE_K_COUNT = 9
+};
+int se_prof_enable(int on);
+int se_prof_reset(void);
+/* Totals since the last reset: summed event time (ms), launches, and the work units the
+ * launches processed (points for AX/GS/KRYLOV, elements for FDM, ...; see each kernel). */
+int se_prof_query(int kind, double* ms_total, int64_t* launches, double* units, double* bytes,
+                  double* flops);
+
+/* ---------------------------------------------------------------- self-test of bounded waits */
+/* Runs the library's grid barrier with one more expected arrival than blocks launched, so no
+ * block can ever pass it; each block gives up after timeout_ms and the call returns
+ * SE_ETIMEOUT.  Checks the wait-limit path without hanging the GPU. */
+int se_selftest_wait_timeout(double timeout_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SE_H */

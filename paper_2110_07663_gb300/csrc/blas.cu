@@ -1,0 +1,393 @@
+// Vector kernels of the Krylov solvers and smoothers: fused updates and deterministic
+// unique-node inner products.
+//
+// GB300 executes FP64 at ~1/62 of its FP32 rate, so a streaming FP64 kernel has a budget of
+// about one FP64 FMA per 11 bytes moved.  Inner products therefore apply the 1/multiplicity
+// weight (1, 1/2, 1/4 or 1/8, exact powers of two) to one operand by lowering its binary
+// exponent with integer instructions, leaving one FP64 FMA per point and product.
+#include "se_internal.h"
+
+namespace se {
+
+// log2 of the multiplicity stored in the low bits of a point flag (1, 2, 4, 8 -> 0..3)
+__device__ __forceinline__ int mult_log2(uint8_t f) { return __ffs(f & 0x0F) - 1; }
+
+// a * 2^-k for k in 0..3 by exponent arithmetic (integer ops only).  Values whose exponent
+// would underflow (|a| < 2^-1019, including zero and subnormals) give 0; NaN/Inf pass through.
+__device__ __forceinline__ double scale_pow2(double a, int k) {
+  const long long b = __double_as_longlong(a);
+  const long long e = (b >> 52) & 0x7FF;
+  const long long r = b - ((long long)k << 52);
+  return __longlong_as_double(e == 0x7FF ? b : (e > k ? r : 0LL));
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-reduce K values (deterministic shuffle tree); result valid in thread 0.
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K], double (*sh)[RED_THREADS / 32]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double s = warp_sum(v[k]);
+    if (lane == 0) sh[k][warp] = s;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double s = lane < RED_THREADS / 32 ? sh[k][lane] : 0.0;
+      v[k] = warp_sum(s);
+    }
+  }
+  __syncthreads();
+}
+
+// Generic fused elementwise + reduction kernel.  Op provides:
+//   static constexpr int K (number of reduced values, >= 1),
+//   __device__ void point(int64_t i, double (&acc)[K])
+//   __device__ void finalize(const double* sums)   (K sums, called once by the last block)
+template <class Op>
+__global__ void __launch_bounds__(RED_THREADS) fused_kernel(Op op, int64_t n,
+                                                            double* __restrict__ partial,
+                                                            unsigned* __restrict__ counter) {
+  constexpr int K = Op::K;
+  double acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k] = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * RED_THREADS;
+  for (int64_t i = (int64_t)blockIdx.x * RED_THREADS + threadIdx.x; i < n; i += stride)
+    op.point(i, acc);
+  {
+    __shared__ double sh[K][RED_THREADS / 32];
+    __shared__ bool last;
+    double (&v)[K] = acc;
+    block_sum<K>(v, sh);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) partial[(int64_t)blockIdx.x * K + k] = v[k];
+      __threadfence();
+      const unsigned t = atomicAdd(counter, 1u);
+      last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double w[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) w[k] = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += RED_THREADS)
+#pragma unroll
+      for (int k = 0; k < K; ++k) w[k] += __ldcg(partial + (int64_t)b * K + k);
+    block_sum<K>(w, sh);
+    if (threadIdx.x == 0) {
+      op.finalize(w);
+      *counter = 0u;
+    }
+  }
+}
+
+template <class Op>
+static int run_fused(const Op& op, int64_t n, Scratch& sc, cudaStream_t s, int kind, double bytes,
+                     double flops) {
+  ProfScope prof(kind, s, (double)n, bytes, flops);
+  const unsigned blocks = grid_for(n, RED_THREADS, RED_MAX_BLOCKS);
+  fused_kernel<Op><<<blocks, RED_THREADS, 0, s>>>(op, n, sc.partial, sc.counter);
+  SE_LAUNCH_CHECK();
+  return SE_OK;
+}
+
+// ------------------------------------------------------------------ ops
+struct DotOp {  // dst = (a, b)
+  static constexpr int K = 1;
+  const double* a;
+  const double* b;
+  const uint8_t* pf;
+  double* dst;
+  __device__ void point(int64_t i, double (&acc)[1]) const {
+    acc[0] = fma(scale_pow2(a[i], mult_log2(pf[i])), b[i], acc[0]);
+  }
+  __device__ void finalize(const double* s) const { *dst = s[0]; }
+};
+
+int dot_weighted(const Level& lv, const double* a, const double* b, double* dst_dev, Scratch& sc,
+                 cudaStream_t s) {
+  return run_fused(DotOp{a, b, lv.pflag, dst_dev}, lv.L, sc, s, SE_K_KRYLOV, lv.L * 17.0, lv.L * 2.0);
+}
+
+// ------------------------------------------------------------------ simple elementwise kernels
+template <class Tin, class Tout>
+__global__ void convert_kernel(const Tin* __restrict__ in, Tout* __restrict__ out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (Tout)in[i];
+}
+template <class Tin, class Tout>
+int convert(const Tin* in, Tout* out, int64_t n, cudaStream_t s) {
+  convert_kernel<Tin, Tout><<<grid_for(n, 256), 256, 0, s>>>(in, out, n);
+  SE_LAUNCH_CHECK();
+  return SE_OK;
+}
+template int convert<double, float>(const double*, float*, int64_t, cudaStream_t);
+template int convert<float, double>(const float*, double*, int64_t, cudaStream_t);
+template int convert<double, double>(const double*, double*, int64_t, cudaStream_t);
+template int convert<float, float>(const float*, float*, int64_t, cudaStream_t);
+
+template <class T>
+int fill_zero(T* x, int64_t n, cudaStream_t s) {
+  SE_CUDA(cudaMemsetAsync(x, 0, n * sizeof(T), s));
+  return SE_OK;
+}
+template int fill_zero<double>(double*, int64_t, cudaStream_t);
+template int fill_zero<float>(float*, int64_t, cudaStream_t);
+
+// out may alias x or y (element-wise read before write)
+template <class T>
+__global__ void axpby_kernel(T a, const T* x, T b, const T* y, T* out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a * x[i] + b * y[i];
+}
+template <class T>
+int axpby(T a, const T* x, T b, const T* y, T* out, int64_t n, cudaStream_t s) {
+  ProfScope prof(SE_K_KRYLOV, s, (double)n, 3.0 * n * sizeof(T), 3.0 * n);
+  axpby_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(a, x, b, y, out, n);
+  SE_LAUNCH_CHECK();
+  return SE_OK;
+}
+template int axpby<double>(double, const double*, double, const double*, double*, int64_t, cudaStream_t);
+template int axpby<float>(float, const float*, float, const float*, float*, int64_t, cudaStream_t);
+
+template <class T>
+__global__ void scale_mul_kernel(const T* __restrict__ a, const T* __restrict__ b,
+                                 T* __restrict__ out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a[i] * b[i];
+}
+template <class T>
+int scale_mul(const T* a, const T* b, T* out, int64_t n, cudaStream_t s) {
+  ProfScope prof(SE_K_JACOBI, s, (double)n, 3.0 * n * sizeof(T), (double)n);
+  scale_mul_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(a, b, out, n);
+  SE_LAUNCH_CHECK();
+  return SE_OK;
+}
+template int scale_mul<double>(const double*, const double*, double*, int64_t, cudaStream_t);
+template int scale_mul<float>(const float*, const float*, float*, int64_t, cudaStream_t);
+
+// Chebyshev recurrence step of Algorithm 2 (one pass):
+//   s = dinv .* sv (Jacobi surrogate) or s = sv (Schwarz output, already S A d)
+//   x = x + d (x = d when `first`), r = r - s, d = c1 d + c2 r
+template <class T>
+__global__ void cheb_update_kernel(T* __restrict__ x, T* __restrict__ d, T* __restrict__ r,
+                                   const T* __restrict__ sv, const T* __restrict__ dinv, int64_t n,
+                                   T c1, T c2, bool first) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const T dv = d[i];
+  const T sval = dinv ? dinv[i] * sv[i] : sv[i];
+  x[i] = first ? dv : x[i] + dv;
+  const T rv = r[i] - sval;
+  r[i] = rv;
+  d[i] = c1 * dv + c2 * rv;
+}
+template <class T>
+int cheb_update(T* x, T* d, T* r, const T* sv, const T* dinv, int64_t n, T c1, T c2, bool first,
+                cudaStream_t s) {
+  ProfScope prof(SE_K_CHEBY_UPD, s, (double)n, (first ? 6.0 : 7.0) * n * sizeof(T), 6.0 * n);
+  cheb_update_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(x, d, r, sv, dinv, n, c1, c2, first);
+  SE_LAUNCH_CHECK();
+  return SE_OK;
+}
+template int cheb_update<double>(double*, double*, double*, const double*, const double*, int64_t,
+                                 double, double, bool, cudaStream_t);
+template int cheb_update<float>(float*, float*, float*, const float*, const float*, int64_t, float,
+                                float, bool, cudaStream_t);
+
+// ------------------------------------------------------------------ FPCG kernels (FP64)
+struct AlphaOp {  // pw = (p, w); alpha = rz / pw
+  static constexpr int K = 1;
+  const double* p;
+  const double* w;
+  const uint8_t* pf;
+  double* scal;
+  __device__ void point(int64_t i, double (&acc)[1]) const {
+    acc[0] = fma(scale_pow2(p[i], mult_log2(pf[i])), w[i], acc[0]);
+  }
+  __device__ void finalize(const double* s) const {
+    scal[SC_PW] = s[0];
+    scal[SC_ALPHA] = scal[SC_RZ] / s[0];
+  }
+};
+
+struct UpdateXROp {  // x += alpha p; r2 = r - alpha w; rr = (r2, r2)
+  static constexpr int K = 1;
+  double* x;
+  const double* p;
+  const double* r;
+  const double* w;
+  double* r2;
+  const uint8_t* pf;
+  double* scal;
+  __device__ void point(int64_t i, double (&acc)[1]) const {
+    const double alpha = scal[SC_ALPHA];
+    x[i] = fma(alpha, p[i], x[i]);
+    const double rv = fma(-alpha, w[i], r[i]);
+    r2[i] = rv;
+    acc[0] = fma(scale_pow2(rv, mult_log2(pf[i])), rv, acc[0]);
+  }
+  __device__ void finalize(const double* s) const { scal[SC_RR] = s[0]; }
+};
+
+struct BetaOp {  // zr = (z, r2); zro = (z, r); beta = (zr - zro)/rz; rz = zr
+  static constexpr int K = 2;
+  const double* z;
+  const double* r2;
+  const double* r;
+  const uint8_t* pf;
+  double* scal;
+  __device__ void point(int64_t i, double (&acc)[2]) const {
+    const double zw = scale_pow2(z[i], mult_log2(pf[i]));
+    acc[0] = fma(zw, r2[i], acc[0]);
+    acc[1] = fma(zw, r[i], acc[1]);
+  }
+  __device__ void finalize(const double* s) const {
+    scal[SC_BETA] = (s[0] - s[1]) / scal[SC_RZ];
+    scal[SC_RZ] = s[0];
+  }
+};
+
+struct RZInitOp {  // rz = (r, z); rr = (r, r); r0 = rr
+  static constexpr int K = 2;
+  const double* r;
+  const double* z;
+  const uint8_t* pf;
+  double* scal;
+  __device__ void point(int64_t i, double (&acc)[2]) const {
+    const double rv = r[i];
+    const double rw = scale_pow2(rv, mult_log2(pf[i]));
+    acc[0] = fma(rw, z[i], acc[0]);
+    acc[1] = fma(rw, rv, acc[1]);
+  }
+  __device__ void finalize(const double* s) const {
+    scal[SC_RZ] = s[0];
+    scal[SC_RR] = s[1];
+    scal[SC_R0] = s[1];
+  }
+};
+
+__global__ void pupdate_kernel(double* __restrict__ p, const double* __restrict__ z,
+                               const double* __restrict__ scal, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = fma(scal[SC_BETA], p[i], z[i]);
+}
+
+int fpcg_init(const Level& lv, const double* r, const double* z, Scratch& sc, cudaStream_t s) {
+  return run_fused(RZInitOp{r, z, lv.pflag, sc.scal}, lv.L, sc, s, SE_K_KRYLOV, lv.L * 17.0,
+                   lv.L * 4.0);
+}
+int fpcg_alpha(const Level& lv, const double* p, const double* w, Scratch& sc, cudaStream_t s) {
+  return run_fused(AlphaOp{p, w, lv.pflag, sc.scal}, lv.L, sc, s, SE_K_KRYLOV, lv.L * 17.0,
+                   lv.L * 2.0);
+}
+int fpcg_update(const Level& lv, double* x, const double* p, const double* r, const double* w,
+                double* r2, Scratch& sc, cudaStream_t s) {
+  return run_fused(UpdateXROp{x, p, r, w, r2, lv.pflag, sc.scal}, lv.L, sc, s, SE_K_KRYLOV,
+                   lv.L * 49.0, lv.L * 6.0);
+}
+int fpcg_beta(const Level& lv, const double* z, const double* r2, const double* r, Scratch& sc,
+              cudaStream_t s) {
+  return run_fused(BetaOp{z, r2, r, lv.pflag, sc.scal}, lv.L, sc, s, SE_K_KRYLOV, lv.L * 25.0,
+                   lv.L * 4.0);
+}
+int fpcg_pupdate(const Level& lv, double* p, const double* z, Scratch& sc, cudaStream_t s) {
+  ProfScope prof(SE_K_KRYLOV, s, (double)lv.L, lv.L * 24.0, lv.L * 2.0);
+  pupdate_kernel<<<grid_for(lv.L, 256), 256, 0, s>>>(p, z, sc.scal, lv.L);
+  SE_LAUNCH_CHECK();
+  return SE_OK;
+}
+
+// ------------------------------------------------------------------ Gram-Schmidt kernels (FP64)
+struct DotToSlotOp {  // scal[slot] = (a, b)
+  static constexpr int K = 1;
+  const double* a;
+  const double* b;
+  const uint8_t* pf;
+  double* scal;
+  int slot;
+  __device__ void point(int64_t i, double (&acc)[1]) const {
+    acc[0] = fma(scale_pow2(a[i], mult_log2(pf[i])), b[i], acc[0]);
+  }
+  __device__ void finalize(const double* s) const { scal[slot] = s[0]; }
+};
+
+struct AxpyDotOp {  // w -= scal[hslot] v; scal[nslot] = (w, vnext) (vnext may be w itself)
+  static constexpr int K = 1;
+  double* w;
+  const double* v;
+  const double* vnext;
+  const uint8_t* pf;
+  double* scal;
+  int hslot, nslot;
+  __device__ void point(int64_t i, double (&acc)[1]) const {
+    const double wv = fma(-scal[hslot], v[i], w[i]);
+    w[i] = wv;
+    acc[0] = fma(scale_pow2(wv, mult_log2(pf[i])), vnext ? vnext[i] : wv, acc[0]);
+  }
+  __device__ void finalize(const double* s) const { scal[nslot] = s[0]; }
+};
+
+__global__ void scale_by_inv_sqrt_kernel(double* __restrict__ out, const double* __restrict__ in,
+                                         const double* __restrict__ scal, int slot, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = in[i] * (1.0 / sqrt(scal[slot]));
+}
+
+// out = in / sqrt(scal[slot])  (one division per thread)
+int scale_inv_sqrt(double* out, const double* in, double* scal, int slot, int64_t n, cudaStream_t s) {
+  ProfScope prof(SE_K_KRYLOV, s, (double)n, 16.0 * n, (double)n);
+  scale_by_inv_sqrt_kernel<<<grid_for(n, 256), 256, 0, s>>>(out, in, scal, slot, n);
+  SE_LAUNCH_CHECK();
+  return SE_OK;
+}
+int dot_to_slot(const Level& lv, const double* a, const double* b, Scratch& sc, int slot,
+                cudaStream_t s) {
+  return run_fused(DotToSlotOp{a, b, lv.pflag, sc.scal, slot}, lv.L, sc, s, SE_K_KRYLOV,
+                   lv.L * 17.0, lv.L * 2.0);
+}
+int axpy_dot(const Level& lv, double* w, const double* v, const double* vnext, Scratch& sc,
+             int hslot, int nslot, cudaStream_t s) {
+  return run_fused(AxpyDotOp{w, v, vnext, lv.pflag, sc.scal, hslot, nslot}, lv.L, sc, s,
+                   SE_K_KRYLOV, lv.L * (vnext ? 33.0 : 25.0), lv.L * 4.0);
+}
+
+// x += sum_j y_j z_j for host coefficients y (up to 8 vectors per pass)
+__global__ void lincomb_kernel(double* __restrict__ x, const double* const* __restrict__ zs,
+                               const double* __restrict__ y, int m, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = x[i];
+  for (int j = 0; j < m; ++j) acc = fma(y[j], zs[j][i], acc);
+  x[i] = acc;
+}
+int lincomb(double* x, const double* const* zs_dev, const double* y_dev, int m, int64_t n,
+            cudaStream_t s) {
+  ProfScope prof(SE_K_KRYLOV, s, (double)n, (m + 2.0) * 8.0 * n, 2.0 * m * n);
+  lincomb_kernel<<<grid_for(n, 256), 256, 0, s>>>(x, zs_dev, y_dev, m, n);
+  SE_LAUNCH_CHECK();
+  return SE_OK;
+}
+
+}  // namespace se
+
+using namespace se;
+
+extern "C" int se_dot(se_mesh_t m, const double* a, const double* b, double* out_host, void* stream) {
+  SE_CHECK(m && a && b && out_host, SE_EINVAL, "se_dot: null argument");
+  cudaStream_t s = as_stream(stream, m->stream);
+  SE_TRY(dot_weighted(m->fine, a, b, m->scratch.scal + SC_TMP, m->scratch, s));
+  SE_CUDA(cudaMemcpyAsync(out_host, m->scratch.scal + SC_TMP, sizeof(double), cudaMemcpyDeviceToHost, s));
+  SE_CUDA(cudaStreamSynchronize(s));
+  return SE_OK;
+}

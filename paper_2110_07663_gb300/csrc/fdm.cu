@@ -1,0 +1,463 @@
+// Overlapping Schwarz smoother with fast-diagonalisation local solves (Sec. 2.3.2, eqs 4-9).
+//
+// Set-up: for every element and direction, the extended 1D stiffness/mass pair over
+// [left neighbour, element, right neighbour] (box lengths from the mapped corners), restricted to
+// the pbar = p+3 window points, is diagonalised on the GPU (one thread per problem, cyclic
+// Jacobi rotations on B^-1/2 A B^-1/2): S^T A S = Lambda, S^T B S = I (eqs 6-7).
+// Apply: each block gathers its element's pbar^3 window of the assembled residual (own nodes
+// plus one layer from up to 26 neighbours, zero outside the domain), applies
+// (S_z x S_y x S_x) D^-1 (S_z^T x S_y^T x S_x^T) (eqs 8-9) with the three tensor directions as
+// line contractions in shared memory, and writes either the own nodes weighted by
+// 1/multiplicity (restrictive additive Schwarz; QQ^T follows) or the whole window (additive
+// Schwarz, combined by a gather over the covering windows).
+#include <cmath>
+
+#include "se_internal.h"
+
+namespace se {
+
+constexpr int PB_MAX = SE_MAX_ORDER + 3;
+
+// ------------------------------------------------------------------ set-up
+__device__ void jacobi_eigen(int n, double* A, double* V) {
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) V[a * n + b] = a == b ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, dg = 0.0;
+    for (int a = 0; a < n; ++a) {
+      dg += A[a * n + a] * A[a * n + a];
+      for (int b = a + 1; b < n; ++b) off += A[a * n + b] * A[a * n + b];
+    }
+    if (off <= 1e-34 * dg) break;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = A[p * n + q];
+        if (fabs(apq) < 1e-300) continue;
+        const double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < n; ++k) {
+          const double akp = A[k * n + p], akq = A[k * n + q];
+          A[k * n + p] = c * akp - s * akq;
+          A[k * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double apk = A[p * n + k], aqk = A[q * n + k];
+          A[p * n + k] = c * apk - s * aqk;
+          A[q * n + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double vkp = V[k * n + p], vkq = V[k * n + q];
+          V[k * n + p] = c * vkp - s * vkq;
+          V[k * n + q] = s * vkp + c * vkq;
+        }
+      }
+  }
+}
+
+// One thread per (element, direction).  Window point q (0..p+2) is point p-1+q of the
+// 3-element 1D assembly (left: 0..p, own: p..2p, right: 2p..3p).
+__global__ void fdm_setup_kernel(int P, int64_t E, const int* __restrict__ nbr,
+                                 const double* __restrict__ len, const double* __restrict__ Ke,
+                                 const double* __restrict__ wq, int bcbits,
+                                 double* __restrict__ S, double* __restrict__ lam) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * E) return;
+  const int64_t e = t / 3;
+  const int d = (int)(t - 3 * e);
+  const int N = P + 1, PB = P + 3;
+  const int stride = d == 0 ? 1 : (d == 1 ? 3 : 9);
+  const int nl = nbr[27 * e + 13 - stride], nr = nbr[27 * e + 13 + stride];
+  const bool hl = nl >= 0, hr = nr >= 0;
+  const bool dl = (bcbits >> (2 * d)) & 1, dr = (bcbits >> (2 * d + 1)) & 1;
+  const double lseg[3] = {hl ? len[3 * nl + d] : 0.0, len[3 * e + d], hr ? len[3 * nr + d] : 0.0};
+  const bool seg_on[3] = {hl, true, hr};
+  int act[PB_MAX];
+  int n = 0;
+  for (int q = 0; q < PB; ++q) {
+    if (q == 0 && !hl) continue;
+    if (q == PB - 1 && !hr) continue;
+    if (q == 1 && !hl && dl) continue;
+    if (q == PB - 2 && !hr && dr) continue;
+    act[n++] = q;
+  }
+  double A[PB_MAX * PB_MAX], V[PB_MAX * PB_MAX], bi[PB_MAX];
+  for (int a = 0; a < n; ++a) {
+    const int wa = P - 1 + act[a];
+    double bsum = 0.0;
+    for (int sg = 0; sg < 3; ++sg) {
+      const int o = sg * P;
+      if (seg_on[sg] && wa >= o && wa <= o + P) bsum += 0.5 * lseg[sg] * wq[wa - o];
+    }
+    bi[a] = 1.0 / sqrt(bsum);
+  }
+  for (int a = 0; a < n; ++a) {
+    const int wa = P - 1 + act[a];
+    for (int b = 0; b < n; ++b) {
+      const int wb = P - 1 + act[b];
+      double v = 0.0;
+      for (int sg = 0; sg < 3; ++sg) {
+        const int o = sg * P;
+        if (seg_on[sg] && wa >= o && wa <= o + P && wb >= o && wb <= o + P)
+          v += (2.0 / lseg[sg]) * Ke[(wa - o) * N + (wb - o)];
+      }
+      A[a * n + b] = bi[a] * v * bi[b];
+    }
+  }
+  jacobi_eigen(n, A, V);
+  double* Se = S + (3 * e + d) * PB * PB;
+  double* le = lam + (3 * e + d) * PB;
+  for (int q = 0; q < PB * PB; ++q) Se[q] = 0.0;
+  for (int m = 0; m < PB; ++m) le[m] = m < n ? A[m * n + m] : 1.0;
+  for (int a = 0; a < n; ++a)
+    for (int m = 0; m < n; ++m) Se[act[a] * PB + m] = bi[a] * V[a * n + m];
+}
+
+// 1/(lam_x[a] + lam_y[b] + lam_z[c]) per element window point (the paper's D^-1 storage).
+__global__ void fdm_dinv_kernel(int PB, int64_t E, const double* __restrict__ lam,
+                                double* __restrict__ dinv) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int PB3 = PB * PB * PB;
+  if (t >= E * PB3) return;
+  const int64_t e = t / PB3;
+  const int q = (int)(t - e * PB3);
+  const int a = q % PB, b = (q / PB) % PB, c = q / (PB * PB);
+  const double* l = lam + 3 * e * PB;
+  dinv[t] = 1.0 / (l[a] + l[PB + b] + l[2 * PB + c]);
+}
+
+template <class T>
+__global__ void cast_kernel(int64_t n, const double* __restrict__ a, T* __restrict__ b) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (T)a[i];
+}
+
+int fdm_setup(const se_mesh_s* m, Level& lv, Allocs& allocs, bool want32, cudaStream_t s) {
+  const int P = lv.p, N = P + 1, PB = P + 3;
+  const int64_t E = lv.E;
+  // 1D GLL stiffness D^T W D (reference element)
+  double Ke[(SE_MAX_ORDER + 1) * (SE_MAX_ORDER + 1)];
+  for (int a = 0; a < N; ++a)
+    for (int b = 0; b < N; ++b) {
+      double v = 0.0;
+      for (int q = 0; q < N; ++q) v += lv.basis.D[q * N + a] * lv.basis.w[q] * lv.basis.D[q * N + b];
+      Ke[a * N + b] = v;
+    }
+  double *dKe = nullptr, *dw = nullptr, *dlen = nullptr;
+  SE_TRY(dmalloc(allocs, &dKe, N * N));
+  SE_TRY(dmalloc(allocs, &dw, N));
+  SE_TRY(dmalloc(allocs, &dlen, 3 * E));
+  SE_CUDA(cudaMemcpy(dKe, Ke, N * N * sizeof(double), cudaMemcpyHostToDevice));
+  SE_CUDA(cudaMemcpy(dw, lv.basis.w, N * sizeof(double), cudaMemcpyHostToDevice));
+  SE_CUDA(cudaMemcpy(dlen, m->box_len.data(), 3 * E * sizeof(double), cudaMemcpyHostToDevice));
+  SE_TRY(dmalloc(allocs, &lv.S64, 3 * E * PB * PB));
+  SE_TRY(dmalloc(allocs, &lv.lam64, 3 * E * PB));
+  int bits = 0;
+  for (int f = 0; f < 6; ++f)
+    if (lv.bc[f] == SE_BC_DIRICHLET) bits |= 1 << f;
+  fdm_setup_kernel<<<grid_for(3 * E, 64), 64, 0, s>>>(P, E, lv.nbr, dlen, dKe, dw, bits, lv.S64,
+                                                      lv.lam64);
+  SE_LAUNCH_CHECK();
+  const int64_t n3 = E * PB * PB * PB;
+  SE_TRY(dmalloc(allocs, &lv.fdm_dinv64, n3));
+  fdm_dinv_kernel<<<grid_for(n3, 256), 256, 0, s>>>(PB, E, lv.lam64, lv.fdm_dinv64);
+  SE_LAUNCH_CHECK();
+  if (want32) {
+    SE_TRY(dmalloc(allocs, &lv.S32, 3 * E * PB * PB));
+    SE_TRY(dmalloc(allocs, &lv.lam32, 3 * E * PB));
+    cast_kernel<float><<<grid_for(3 * E * PB * PB, 256), 256, 0, s>>>(3 * E * PB * PB, lv.S64, lv.S32);
+    cast_kernel<float><<<grid_for(3 * E * PB, 256), 256, 0, s>>>(3 * E * PB, lv.lam64, lv.lam32);
+    SE_LAUNCH_CHECK();
+  }
+  return SE_OK;
+}
+
+// ------------------------------------------------------------------ apply
+enum { FDM_RAS = 0, FDM_FULL = 1, FDM_EXT_IN = 2, FDM_GATHER = 3 };
+
+// Window point (a, b, c) of element e: neighbour slot and local index in that element.
+template <int P>
+__device__ __forceinline__ int64_t window_source(const int* __restrict__ nb, int64_t e, int a,
+                                                 int b, int c) {
+  constexpr int N = P + 1, PB = P + 3;
+  const int da = a == 0 ? -1 : (a == PB - 1 ? 1 : 0);
+  const int db = b == 0 ? -1 : (b == PB - 1 ? 1 : 0);
+  const int dc = c == 0 ? -1 : (c == PB - 1 ? 1 : 0);
+  int64_t src = e;
+  if (da | db | dc) {
+    src = nb[(da + 1) + 3 * (db + 1) + 9 * (dc + 1)];
+    if (src < 0) return -1;
+  }
+  const int ia = da < 0 ? P - 1 : (da > 0 ? 1 : a - 1);
+  const int ib = db < 0 ? P - 1 : (db > 0 ? 1 : b - 1);
+  const int ic = dc < 0 ? P - 1 : (dc > 0 ? 1 : c - 1);
+  return src * (N * N * N) + ia + N * (ib + N * ic);
+}
+
+// One element per block; threads cover the PB*PB lines of each contraction.
+template <int P, typename T, int MODE>
+__global__ void __launch_bounds__(256) fdm_kernel(int64_t E, const int* __restrict__ nbr,
+                                                  const T* __restrict__ in,
+                                                  const T* __restrict__ Sg,
+                                                  const T* __restrict__ lamg,
+                                                  const double* __restrict__ dinvg,
+                                                  const uint8_t* __restrict__ pflag,
+                                                  T* __restrict__ out) {
+  constexpr int N = P + 1, PB = P + 3, PB2 = PB * PB, PB3 = PB * PB * PB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* b0 = reinterpret_cast<T*>(smem_raw);
+  T* b1 = b0 + PB3;
+  T* sS = b1 + PB3;        // [3][PB][PB]
+  T* sl = sS + 3 * PB2;    // [3][PB]
+  __shared__ int snb[27];
+  const int64_t e = blockIdx.x;
+  const int tid = threadIdx.x;
+  if constexpr (MODE != FDM_GATHER) {
+    for (int q = tid; q < 3 * PB2; q += blockDim.x) sS[q] = Sg[e * 3 * PB2 + q];
+    for (int q = tid; q < 3 * PB; q += blockDim.x) sl[q] = lamg[e * 3 * PB + q];
+  }
+  if (tid < 27) snb[tid] = nbr[27 * e + tid];
+  __syncthreads();
+  // ---- gather the extended window
+  if constexpr (MODE == FDM_EXT_IN) {
+    for (int q = tid; q < PB3; q += blockDim.x) b0[q] = in[e * PB3 + q];
+  } else {
+    if (tid < PB2) {
+      const int a = tid % PB, b = tid / PB;
+      for (int c = 0; c < PB; ++c) {
+        const int64_t src = window_source<P>(snb, e, a, b, c);
+        b0[a + PB * (b + PB * c)] = src >= 0 ? in[src] : T(0);
+      }
+    }
+  }
+  if constexpr (MODE == FDM_GATHER) {
+    __syncthreads();
+    for (int q = tid; q < PB3; q += blockDim.x) out[e * PB3 + q] = b0[q];
+    return;
+  } else {
+    __syncthreads();
+    const T* Sx = sS;
+    const T* Sy = sS + PB2;
+    const T* Sz = sS + 2 * PB2;
+    T v[PB];
+    // ---- forward: S_x^T along a (thread = line (b, c))
+    if (tid < PB2) {
+      const int b = tid % PB, c = tid / PB;
+#pragma unroll
+      for (int a = 0; a < PB; ++a) v[a] = b0[a + PB * (b + PB * c)];
+#pragma unroll
+      for (int al = 0; al < PB; ++al) {
+        T acc = T(0);
+#pragma unroll
+        for (int a = 0; a < PB; ++a) acc += Sx[a * PB + al] * v[a];
+        b1[al + PB * (b + PB * c)] = acc;
+      }
+    }
+    __syncthreads();
+    // ---- forward: S_y^T along b (thread = line (alpha, c))
+    if (tid < PB2) {
+      const int al = tid % PB, c = tid / PB;
+#pragma unroll
+      for (int b = 0; b < PB; ++b) v[b] = b1[al + PB * (b + PB * c)];
+#pragma unroll
+      for (int be = 0; be < PB; ++be) {
+        T acc = T(0);
+#pragma unroll
+        for (int b = 0; b < PB; ++b) acc += Sy[b * PB + be] * v[b];
+        b0[al + PB * (be + PB * c)] = acc;
+      }
+    }
+    __syncthreads();
+    // ---- forward: S_z^T along c, then D^-1 (thread = line (alpha, beta))
+    if (tid < PB2) {
+      const int al = tid % PB, be = tid / PB;
+#pragma unroll
+      for (int c = 0; c < PB; ++c) v[c] = b0[al + PB * (be + PB * c)];
+      const T lxy = sl[al] + sl[PB + be];
+#pragma unroll
+      for (int ga = 0; ga < PB; ++ga) {
+        T acc = T(0);
+#pragma unroll
+        for (int c = 0; c < PB; ++c) acc += Sz[c * PB + ga] * v[c];
+        const int q = al + PB * (be + PB * ga);
+        T dv;
+        if constexpr (sizeof(T) == 8) dv = dinvg[e * PB3 + q];
+        else dv = T(1) / (lxy + sl[2 * PB + ga]);
+        b1[q] = acc * dv;
+      }
+    }
+    __syncthreads();
+    // ---- backward: S_z along gamma (own outputs c' = 1..N for RAS, all PB otherwise)
+    constexpr int C0 = MODE == FDM_RAS ? 1 : 0;
+    constexpr int NC = MODE == FDM_RAS ? N : PB;
+    if (tid < PB2) {
+      const int al = tid % PB, be = tid / PB;
+#pragma unroll
+      for (int ga = 0; ga < PB; ++ga) v[ga] = b1[al + PB * (be + PB * ga)];
+#pragma unroll
+      for (int cc = 0; cc < NC; ++cc) {
+        const int c = C0 + cc;
+        T acc = T(0);
+#pragma unroll
+        for (int ga = 0; ga < PB; ++ga) acc += Sz[c * PB + ga] * v[ga];
+        b0[al + PB * (be + PB * c)] = acc;
+      }
+    }
+    __syncthreads();
+    // ---- backward: S_y along beta (thread = line (alpha, c'))
+    if (tid < PB * NC) {
+      const int al = tid % PB, c = C0 + tid / PB;
+#pragma unroll
+      for (int be = 0; be < PB; ++be) v[be] = b0[al + PB * (be + PB * c)];
+#pragma unroll
+      for (int bb = 0; bb < NC; ++bb) {
+        const int b = C0 + bb;
+        T acc = T(0);
+#pragma unroll
+        for (int be = 0; be < PB; ++be) acc += Sy[b * PB + be] * v[be];
+        b1[al + PB * (b + PB * c)] = acc;
+      }
+    }
+    __syncthreads();
+    // ---- backward: S_x along alpha (thread = line (b', c')), write out
+    if (tid < NC * NC) {
+      const int b = C0 + tid % NC, c = C0 + tid / NC;
+#pragma unroll
+      for (int al = 0; al < PB; ++al) v[al] = b1[al + PB * (b + PB * c)];
+#pragma unroll
+      for (int aa = 0; aa < NC; ++aa) {
+        const int a = C0 + aa;
+        T acc = T(0);
+#pragma unroll
+        for (int al = 0; al < PB; ++al) acc += Sx[a * PB + al] * v[al];
+        if constexpr (MODE == FDM_RAS) {
+          const int64_t li = e * (N * N * N) + (a - 1) + N * ((b - 1) + N * (c - 1));
+          const int mlog = __ffs(pflag[li] & 0x0F) - 1;   // 1/multiplicity: exact power of 2
+          const T wt = mlog == 0 ? T(1) : (mlog == 1 ? T(0.5) : (mlog == 2 ? T(0.25) : T(0.125)));
+          out[li] = acc * wt;
+        } else {
+          out[e * PB3 + a + PB * (b + PB * c)] = acc;
+        }
+      }
+    }
+  }
+}
+
+template <int P, typename T, int MODE>
+static int launch_fdm(const Level& lv, const T* in, const T* S, const T* lam, T* out,
+                      cudaStream_t s) {
+  constexpr int PB = P + 3;
+  const int threads = ((PB * PB + 31) / 32) * 32;
+  const size_t smem = (2 * PB * PB * PB + 3 * PB * PB + 3 * PB) * sizeof(T);
+  static bool attr = false;
+  if (!attr) {
+    SE_CUDA(cudaFuncSetAttribute(fdm_kernel<P, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 100 * 1024));
+    attr = true;
+  }
+  fdm_kernel<P, T, MODE><<<(unsigned)lv.E, threads, smem, s>>>(lv.E, lv.nbr, in, S, lam,
+                                                                lv.fdm_dinv64, lv.pflag, out);
+  SE_LAUNCH_CHECK();
+  return SE_OK;
+}
+
+template <typename T, int MODE>
+static int dispatch_fdm(const Level& lv, const T* in, T* out, cudaStream_t s) {
+  const T* S;
+  const T* lam;
+  if constexpr (sizeof(T) == 8) {
+    S = lv.S64;
+    lam = lv.lam64;
+  } else {
+    S = lv.S32;
+    lam = lv.lam32;
+  }
+  SE_CHECK(MODE == FDM_GATHER || S != nullptr, SE_EINVAL, "FDM factors missing for this level/precision");
+  const double PB = lv.p + 3.0, N = lv.N;
+  const double fl = 2.0 * (3.0 * PB * PB * PB * PB + PB * PB * PB * N + PB * PB * N * N + PB * N * N * N) + PB * PB * PB;
+  const double by = (PB * PB * PB + N * N * N + 3 * PB * PB + 3 * PB + (sizeof(T) == 8 ? PB * PB * PB : 0)) * sizeof(T);
+  ProfScope prof(SE_K_FDM, s, (double)lv.E, by * lv.E, fl * lv.E);
+  switch (lv.p) {
+#define SE_FDM_CASE(PP) \
+  case PP: return launch_fdm<PP, T, MODE>(lv, in, S, lam, out, s);
+    SE_FDM_CASE(1) SE_FDM_CASE(2) SE_FDM_CASE(3) SE_FDM_CASE(4) SE_FDM_CASE(5)
+    SE_FDM_CASE(6) SE_FDM_CASE(7) SE_FDM_CASE(8) SE_FDM_CASE(9) SE_FDM_CASE(10)
+#undef SE_FDM_CASE
+    default: set_error("fdm: unsupported p=%d", lv.p); return SE_EINVAL;
+  }
+}
+
+// Additive Schwarz combine (eq 4 with post-multiplied W): for every local point, sum the
+// full-window solutions of all elements whose window covers the node, divide by their count.
+template <typename T>
+__global__ void asm_combine_kernel(int P, int nx, int ny, int nz, int64_t L,
+                                   const T* __restrict__ zbar, const uint8_t* __restrict__ pflag,
+                                   T* __restrict__ out) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= L) return;
+  if (!(pflag[idx] & PF_FREE)) {
+    out[idx] = T(0);
+    return;
+  }
+  const int N = P + 1, N3 = N * N * N, PB = P + 3;
+  const int64_t e = idx / N3;
+  const int pt = (int)(idx - e * N3);
+  const int i = pt % N, j = (pt / N) % N, k = pt / (N * N);
+  const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
+  const int I = ex * P + i, J = ey * P + j, K = ez * P + k;
+  T acc = T(0);
+  int cnt = 0;
+  for (int cz = ez - 1; cz <= ez + 1; ++cz) {
+    if (cz < 0 || cz >= nz) continue;
+    const int c = K - (cz * P - 1);
+    if (c < 0 || c >= PB) continue;
+    for (int cy = ey - 1; cy <= ey + 1; ++cy) {
+      if (cy < 0 || cy >= ny) continue;
+      const int b = J - (cy * P - 1);
+      if (b < 0 || b >= PB) continue;
+      for (int cx = ex - 1; cx <= ex + 1; ++cx) {
+        if (cx < 0 || cx >= nx) continue;
+        const int a = I - (cx * P - 1);
+        if (a < 0 || a >= PB) continue;
+        const int64_t ee = cx + (int64_t)nx * (cy + (int64_t)ny * cz);
+        acc += zbar[ee * PB * PB * PB + a + PB * (b + PB * c)];
+        ++cnt;
+      }
+    }
+  }
+  out[idx] = acc / T(cnt);
+}
+
+template <class T>
+int schwarz_apply(const Level& lv, int kind, const T* r, T* out, cudaStream_t s) {
+  if (kind == SE_SMOOTH_RAS) {
+    SE_TRY((dispatch_fdm<T, FDM_RAS>(lv, r, out, s)));
+    return gs_apply<T>(lv, out, true, s);
+  }
+  T* ext;
+  if constexpr (sizeof(T) == 8) ext = lv.ext64;
+  else ext = lv.ext32;
+  SE_CHECK(ext != nullptr, SE_EINVAL, "ASM window buffer missing");
+  SE_TRY((dispatch_fdm<T, FDM_FULL>(lv, r, ext, s)));
+  ProfScope prof(SE_K_GS, s, (double)lv.L, lv.L * (2.0 * sizeof(T) + 1.0), (double)lv.L);
+  asm_combine_kernel<T><<<grid_for(lv.L, 256), 256, 0, s>>>(lv.p, lv.nel[0], lv.nel[1], lv.nel[2],
+                                                            lv.L, ext, lv.pflag, out);
+  SE_LAUNCH_CHECK();
+  return SE_OK;
+}
+
+template <class T>
+int gather_ext(const Level& lv, const T* r, T* rbar, cudaStream_t s) {
+  return dispatch_fdm<T, FDM_GATHER>(lv, r, rbar, s);
+}
+template <class T>
+int fdm_apply_ext(const Level& lv, const T* rbar, T* zbar, cudaStream_t s) {
+  return dispatch_fdm<T, FDM_EXT_IN>(lv, rbar, zbar, s);
+}
+
+template int schwarz_apply<double>(const Level&, int, const double*, double*, cudaStream_t);
+template int schwarz_apply<float>(const Level&, int, const float*, float*, cudaStream_t);
+template int gather_ext<double>(const Level&, const double*, double*, cudaStream_t);
+template int fdm_apply_ext<double>(const Level&, const double*, double*, cudaStream_t);
+
+}  // namespace se

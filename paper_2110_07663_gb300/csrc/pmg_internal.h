@@ -1,0 +1,52 @@
+// Internal declarations of the p-multigrid handle.
+#pragma once
+
+#include "se_internal.h"
+
+namespace se {
+
+template <class T>
+struct LevelVecs {
+  T *b = nullptr, *x = nullptr, *r = nullptr, *cr = nullptr, *cd = nullptr, *w = nullptr, *sv = nullptr;
+};
+
+int pmg_apply(se_pmg_s* P, const double* r, double* z, cudaStream_t s);
+
+}  // namespace se
+
+struct se_pmg_s {
+  se_mesh_s* mesh = nullptr;
+  se_pmg_desc desc;
+  int nlev = 0;
+  cudaStream_t stream = nullptr;
+  // level 0 is a shallow copy of the mesh level (shares its geometry and index maps); the
+  // smoother data of every level belongs to this handle
+  se::Level owned[SE_MAX_LEVELS];
+  se::Level* lv[SE_MAX_LEVELS] = {};
+  double lam[SE_MAX_LEVELS] = {};
+  double lmin[SE_MAX_LEVELS] = {};
+  double lmax[SE_MAX_LEVELS] = {};
+  double* J64[SE_MAX_LEVELS] = {};
+  float* J32[SE_MAX_LEVELS] = {};
+  se::LevelVecs<double> v64[SE_MAX_LEVELS];
+  se::LevelVecs<float> v32[SE_MAX_LEVELS];
+  se::CoarseWork cw{};
+  se::Allocs allocs;
+  se::Scratch scratch;
+  cudaGraphExec_t graph = nullptr;
+  const double* graph_r = nullptr;
+  double* graph_z = nullptr;
+  cudaStream_t graph_stream = nullptr;
+
+  template <class T>
+  se::LevelVecs<T>& vecs(int l) {
+    if constexpr (sizeof(T) == 8) return v64[l];
+    else return v32[l];
+  }
+  void release_graph() {
+    if (graph) cudaGraphExecDestroy(graph);
+    graph = nullptr;
+    graph_r = nullptr;
+    graph_z = nullptr;
+  }
+};

@@ -1,0 +1,267 @@
+// Internal declarations of libse.so: handles, level data, launch helpers, profiling.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "se.h"
+
+namespace se {
+
+// ------------------------------------------------------------------ errors
+void set_error(const char* fmt, ...);
+
+#define SE_CUDA(call)                                                                         \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) {                                                                  \
+      ::se::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,      \
+                      __LINE__);                                                              \
+      return SE_ECUDA;                                                                        \
+    }                                                                                         \
+  } while (0)
+
+#define SE_CHECK(cond, code, ...)                                                             \
+  do {                                                                                        \
+    if (!(cond)) {                                                                            \
+      ::se::set_error(__VA_ARGS__);                                                           \
+      return code;                                                                            \
+    }                                                                                         \
+  } while (0)
+
+#define SE_TRY(call)                                                                          \
+  do {                                                                                        \
+    int s_ = (call);                                                                          \
+    if (s_ != SE_OK) return s_;                                                               \
+  } while (0)
+
+// Kernel launch check (launch-configuration errors are reported at once).
+#define SE_LAUNCH_CHECK() SE_CUDA(cudaGetLastError())
+
+// ------------------------------------------------------------------ device allocations
+struct Allocs {
+  std::vector<void*> ptrs;
+  size_t bytes = 0;
+  void release();
+};
+
+int dmalloc_bytes(Allocs& a, void** p, size_t bytes);
+template <class T>
+inline int dmalloc(Allocs& a, T** p, size_t count) {
+  return dmalloc_bytes(a, reinterpret_cast<void**>(p), count * sizeof(T) + (count == 0));
+}
+
+// ------------------------------------------------------------------ 1D GLL data (host)
+struct Basis1D {
+  int p = 0;
+  double xi[SE_MAX_ORDER + 1];
+  double w[SE_MAX_ORDER + 1];
+  double D[(SE_MAX_ORDER + 1) * (SE_MAX_ORDER + 1)];  // D[i*N + j] = h_j'(xi_i)
+};
+void gll_basis(int p, Basis1D* b);
+// J[i*Nc + j] = h^c_j(xi^f_i): coarse basis at fine points.
+void interp_matrix(int pf, int pc, double* J);
+
+// SplitMix64 (Steele, Lea, Flood 2014): value number c of stream `seed`.
+__host__ __device__ inline uint64_t splitmix64_hd(uint64_t seed, uint64_t c) {
+  uint64_t z = seed + (c + 1) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+uint64_t splitmix64(uint64_t seed, uint64_t c);
+double uniform01(uint64_t seed, uint64_t c);
+
+// ------------------------------------------------------------------ per-point flags
+// bits 0..3: multiplicity (number of local copies: 1, 2, 4, 8); bit 7: node is free (not on a
+// Dirichlet face).
+constexpr uint8_t PF_FREE = 0x80;
+
+// ------------------------------------------------------------------ one discretisation level
+struct Level {
+  int p = 0, N = 0;
+  int nel[3] = {0, 0, 0};
+  int bc[6] = {0, 0, 0, 0, 0, 0};
+  int64_t E = 0, L = 0, n_global = 0;
+  int NX = 0, NY = 0, NZ = 0;
+  Basis1D basis;
+  double* X = nullptr;       // node coordinates [3][L]
+  double* G64 = nullptr;     // geometric factors [6][L]: rr rs rt ss st tt
+  float* G32 = nullptr;
+  double* B = nullptr;       // diagonal mass w_i w_j w_k det J [L]
+  double* dinv64 = nullptr;  // 1 / assembled diagonal, 0 on Dirichlet nodes [L]
+  float* dinv32 = nullptr;
+  uint8_t* pflag = nullptr;  // multiplicity and free bit [L]
+  double* D64 = nullptr;     // derivative matrix on the device [N*N]
+  float* D32 = nullptr;
+  // QQ^T index map, groups sorted by global id within each class: pairs, quads, octets of
+  // local ids sharing a global node (first id stored as ~id when the node is on a Dirichlet
+  // face), then the single-copy Dirichlet nodes (n_masked of them).
+  int64_t n_pairs = 0, n_quads = 0, n_octs = 0, n_masked = 0;
+  int* gs_ids = nullptr;
+  const int* nbr = nullptr;  // element neighbours [E][27] (owned by the mesh)
+  // fast diagonalisation factors (all levels but the coarsest)
+  double* S64 = nullptr;     // [E][3][pb][pb], S[row = window point][col = mode]
+  double* lam64 = nullptr;   // [E][3][pb]
+  float* S32 = nullptr;
+  float* lam32 = nullptr;
+  double* fdm_dinv64 = nullptr;  // 1/(lam_x + lam_y + lam_z) per window point [E][pb^3]
+  double* ext64 = nullptr;   // full-window work buffer [E][pb^3] (additive Schwarz)
+  float* ext32 = nullptr;
+  // assembled operator of the coarsest level: 27-point rows over global nodes
+  double* Ac = nullptr;      // [27][n_global]
+  double* cdinv = nullptr;   // [n_global]
+  int* g2l = nullptr;        // first local copy of each global node [n_global]
+  int* l2g = nullptr;        // global node of each local node [L]
+};
+
+// ------------------------------------------------------------------ reduction scratch
+// Deterministic two-stage reductions: per-block partial sums, then the last block to finish
+// sums them in block order.  Every handle owns one Scratch; calls on one handle are serialised.
+constexpr int RED_THREADS = 256;
+constexpr int RED_MAX_BLOCKS = 1216;   // 152 SMs x 8
+constexpr int SCAL_SLOTS = 256;
+struct Scratch {
+  double* partial = nullptr;   // [RED_MAX_BLOCKS * 4]
+  unsigned* counter = nullptr; // [1], returned to 0 by the last block
+  double* scal = nullptr;      // device scalars [SCAL_SLOTS]
+  double* hscal = nullptr;     // pinned host mirror [SCAL_SLOTS]
+};
+int scratch_alloc(Allocs& a, Scratch* s);
+
+// Device scalar slots used by the solvers.
+enum {
+  SC_RZ = 0, SC_PW = 1, SC_ALPHA = 2, SC_BETA = 3, SC_RR = 4, SC_R0 = 5, SC_ZR = 6,
+  SC_ZRO = 7, SC_TMP = 8, SC_NORM = 9,
+  SC_H = 16      // SC_H + i: Gram-Schmidt coefficient i of the current column (i <= 200)
+
+};
+
+}  // namespace se
+
+struct se_mesh_s {
+  se_mesh_desc desc;
+  std::vector<double> verts;     // host vertex lattice (interleaved xyz)
+  std::vector<double> box_len;   // host box lengths [E][3]
+  se::Level fine;
+  int* nbr = nullptr;
+  cudaStream_t stream = nullptr;
+  se::Allocs allocs;
+  se::Scratch scratch;
+  double* tmp64 = nullptr;       // [L] work vector
+  float* tmpa32 = nullptr;       // [L]
+  float* tmpb32 = nullptr;       // [L]
+  // outer-solver work vectors, allocated on the first se_solve
+  double *sr = nullptr, *sr2 = nullptr, *sz = nullptr, *sp = nullptr, *sw = nullptr;
+  int gm_m = 0;                  // FGMRES restart length the V/Z blocks were sized for
+  double* gmV = nullptr;         // [(m+1) L]
+  double* gmZ = nullptr;         // [m L]
+  double** gm_zs = nullptr;      // device array of the m Z pointers
+  double* gm_y = nullptr;        // device [m]
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace se {
+
+// ------------------------------------------------------------------ builders (mesh.cu)
+int build_level(se_mesh_s* m, int p, Level* lv, Allocs& allocs, cudaStream_t s);
+int build_jacobi(Level& lv, Allocs& allocs, Scratch& sc, cudaStream_t s);
+int make_fp32_geometry(Level& lv, Allocs& allocs, cudaStream_t s);
+int local_to_global(const Level& lv, int* l2g, cudaStream_t s);
+
+// ------------------------------------------------------------------ kernels' host launchers
+// Operator: y_L = A_L u (local), optionally followed by QQ^T + mask.
+template <class T>
+int ax_local(const Level& lv, const T* u, T* y, bool mask_in, cudaStream_t s);
+template <class T>
+int gs_apply(const Level& lv, T* u, bool mask, cudaStream_t s);
+template <class T>
+inline int ax_apply(const Level& lv, const T* u, T* y, cudaStream_t s) {
+  SE_TRY(ax_local<T>(lv, u, y, false, s));
+  return gs_apply<T>(lv, y, true, s);
+}
+// Elementwise and reduction kernels (blas.cu)
+int dot_weighted(const Level& lv, const double* a, const double* b, double* dst_dev,
+                 Scratch& sc, cudaStream_t s);
+template <class Tin, class Tout>
+int convert(const Tin* in, Tout* out, int64_t n, cudaStream_t s);
+template <class T>
+int fill_zero(T* x, int64_t n, cudaStream_t s);
+template <class T>
+int axpby(T a, const T* x, T b, const T* y, T* out, int64_t n, cudaStream_t s);  // out=a x+b y
+template <class T>
+int cheb_update(T* x, T* d, T* r, const T* sv, const T* dinv, int64_t n, T c1, T c2,
+                bool first, cudaStream_t s);
+template <class T>
+int scale_mul(const T* a, const T* b, T* out, int64_t n, cudaStream_t s);  // out = a*b
+// FP64 Krylov kernels with device scalars (slots of Scratch::scal)
+int fpcg_init(const Level& lv, const double* r, const double* z, Scratch& sc, cudaStream_t s);
+int fpcg_alpha(const Level& lv, const double* p, const double* w, Scratch& sc, cudaStream_t s);
+int fpcg_update(const Level& lv, double* x, const double* p, const double* r, const double* w,
+                double* r2, Scratch& sc, cudaStream_t s);
+int fpcg_beta(const Level& lv, const double* z, const double* r2, const double* r, Scratch& sc,
+              cudaStream_t s);
+int fpcg_pupdate(const Level& lv, double* p, const double* z, Scratch& sc, cudaStream_t s);
+int dot_to_slot(const Level& lv, const double* a, const double* b, Scratch& sc, int slot,
+                cudaStream_t s);
+int axpy_dot(const Level& lv, double* w, const double* v, const double* vnext, Scratch& sc,
+             int hslot, int nslot, cudaStream_t s);
+int scale_inv_sqrt(double* out, const double* in, double* scal, int slot, int64_t n, cudaStream_t s);
+int lincomb(double* x, const double* const* zs_dev, const double* y_dev, int m, int64_t n,
+            cudaStream_t s);
+// Smoothers (fdm.cu)
+template <class T>
+int schwarz_apply(const Level& lv, int kind, const T* r, T* out, cudaStream_t s);
+template <class T>
+int gather_ext(const Level& lv, const T* r, T* rbar, cudaStream_t s);
+template <class T>
+int fdm_apply_ext(const Level& lv, const T* rbar, T* zbar, cudaStream_t s);
+int fdm_setup(const se_mesh_s* m, Level& lv, Allocs& allocs, bool want32, cudaStream_t s);
+int asm_weights(Level& lv, Allocs& allocs, cudaStream_t s);
+// Transfers (transfer.cu): level f (fine) <-> level c (coarse)
+template <class T>
+int restrict_apply(const Level& f, const Level& c, const T* J, const T* rf, T* rc,
+                   cudaStream_t s);
+template <class T>
+int prolong_apply(const Level& f, const Level& c, const T* J, const T* ec, T* ef, bool accumulate,
+                  cudaStream_t s);
+// Coarse solve (coarse.cu)
+int coarse_setup(Level& lv, Allocs& allocs, cudaStream_t s);
+struct CoarseWork {
+  double *x, *r, *z, *p, *q, *partial;
+  unsigned* bar;  // [2]: arrival count, generation
+  int* status;    // [2]: error flag, iterations
+  int nblocks;
+};
+int coarse_alloc(const Level& lv, Allocs& allocs, CoarseWork* w);
+template <class T>
+int coarse_solve(const Level& lv, CoarseWork& w, const T* r_l, T* x_l, double tol, int maxit,
+                 cudaStream_t s);
+
+// ------------------------------------------------------------------ profiling (common.cu)
+struct ProfScope {
+  int kind;
+  cudaStream_t s;
+  double units, bytes, flops;
+  bool on;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ProfScope(int kind, cudaStream_t s, double units, double bytes, double flops);
+  ~ProfScope();
+};
+
+inline unsigned grid_for(int64_t n, int threads, int64_t max_blocks = 1 << 30) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > max_blocks) b = max_blocks;
+  return (unsigned)b;
+}
+
+inline cudaStream_t as_stream(void* s, cudaStream_t dflt) {
+  return s ? reinterpret_cast<cudaStream_t>(s) : dflt;
+}
+
+}  // namespace se

@@ -1,0 +1,295 @@
+"""Thin ctypes binding of libse.so (include/se.h), argument marshalling only.
+
+Every function keeps its C name.  Device vectors are passed as torch CUDA tensors (float64,
+contiguous) or raw device pointers (int); streams as torch.cuda.Stream, raw handles or None.
+A non-zero status raises SeError carrying the code and se_last_error().  The library must have
+been built (``__graft_entry__.build()``); importing this module without it fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libse.so")
+
+SE_OK, SE_EINVAL, SE_ENOMEM, SE_ENOTCONV, SE_ECUDA, SE_ETIMEOUT, SE_EBUSY, SE_EREFUSED = range(8)
+SE_BC_DIRICHLET, SE_BC_NEUMANN = 0, 1
+SE_FP64, SE_FP32 = 0, 1
+SE_SMOOTH_JACOBI, SE_SMOOTH_RAS, SE_SMOOTH_ASM = 0, 1, 2
+SE_FPCG, SE_FGMRES = 0, 1
+SE_AX_ASSEMBLE, SE_AX_MASK, SE_AX_FP32 = 1, 2, 4
+SE_MAX_LEVELS, SE_MAX_ORDER = 8, 10
+(SE_K_AX, SE_K_GS, SE_K_FDM, SE_K_CHEBY_UPD, SE_K_RESTRICT, SE_K_PROLONG, SE_K_COARSE,
+ SE_K_KRYLOV, SE_K_JACOBI, SE_K_COUNT) = range(10)
+KERNEL_NAMES = ["ax", "gs", "fdm", "cheby_update", "restrict", "prolong", "coarse_pcg", "krylov",
+                "jacobi"]
+
+STATUS_NAMES = {0: "SE_OK", 1: "SE_EINVAL", 2: "SE_ENOMEM", 3: "SE_ENOTCONV", 4: "SE_ECUDA",
+                5: "SE_ETIMEOUT", 6: "SE_EBUSY", 7: "SE_EREFUSED"}
+
+
+class SeError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class se_mesh_desc(C.Structure):
+    _fields_ = [("nel", C.c_int * 3), ("p", C.c_int), ("vertex_xyz", C.POINTER(C.c_double)),
+                ("deform_amp", C.c_double), ("perturb_frac", C.c_double), ("seed", C.c_uint64),
+                ("bc", C.c_int * 6), ("flags", C.c_int)]
+
+
+class se_mesh_info(C.Structure):
+    _fields_ = [("E", C.c_int64), ("N", C.c_int64), ("L", C.c_int64), ("n_global", C.c_int64),
+                ("n_dof", C.c_int64), ("p", C.c_int), ("nel", C.c_int * 3)]
+
+
+class se_pmg_desc(C.Structure):
+    _fields_ = [("nlev", C.c_int), ("schedule", C.c_int * SE_MAX_LEVELS), ("smoother", C.c_int),
+                ("cheb_order", C.c_int * SE_MAX_LEVELS), ("eig_lo", C.c_double),
+                ("eig_hi", C.c_double), ("arnoldi_steps", C.c_int), ("seed", C.c_uint64),
+                ("coarse_tol", C.c_double), ("coarse_maxit", C.c_int), ("precision", C.c_int)]
+
+
+class se_solve_opts(C.Structure):
+    _fields_ = [("method", C.c_int), ("restart", C.c_int), ("tol", C.c_double),
+                ("maxit", C.c_int), ("graph_capture", C.c_int), ("stream", C.c_void_p)]
+
+
+class se_solve_stats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("status", C.c_int), ("rel_residual", C.c_double),
+                ("ms_total", C.c_double), ("ms_precond", C.c_double), ("ms_operator", C.c_double)]
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libse.so is not built ({LIB_PATH}); run __graft_entry__.build() first")
+lib = C.CDLL(LIB_PATH)
+
+_vp, _dp, _ip = C.c_void_p, C.POINTER(C.c_double), C.c_int
+_SIGS = {
+    "se_last_error": ([], C.c_char_p),
+    "se_version": ([], C.c_int),
+    "se_mesh_create": ([C.POINTER(se_mesh_desc), C.POINTER(_vp)], C.c_int),
+    "se_mesh_destroy": ([_vp], C.c_int),
+    "se_mesh_get_info": ([_vp, C.POINTER(se_mesh_info)], C.c_int),
+    "se_mesh_nodes": ([_vp, _vp, _vp], C.c_int),
+    "se_mesh_vertices": ([_vp, _dp], C.c_int),
+    "se_mesh_rhs": ([_vp, _vp, _vp, _vp], C.c_int),
+    "se_ax": ([_vp, _vp, _vp, _ip, _vp], C.c_int),
+    "se_gs": ([_vp, _vp, _ip, _vp], C.c_int),
+    "se_dot": ([_vp, _vp, _vp, _dp, _vp], C.c_int),
+    "se_jacobi_diag": ([_vp, _vp, _vp], C.c_int),
+    "se_pmg_setup": ([_vp, C.POINTER(se_pmg_desc), C.POINTER(_vp)], C.c_int),
+    "se_pmg_destroy": ([_vp], C.c_int),
+    "se_pmg_apply": ([_vp, _vp, _vp, _vp], C.c_int),
+    "se_pmg_lambda": ([_vp, _ip, _dp], C.c_int),
+    "se_pmg_level_info": ([_vp, _ip, C.POINTER(se_mesh_info)], C.c_int),
+    "se_pmg_level_ax": ([_vp, _ip, _vp, _vp, _vp], C.c_int),
+    "se_pmg_smooth": ([_vp, _ip, _vp, _vp, _vp], C.c_int),
+    "se_pmg_gather_ext": ([_vp, _ip, _vp, _vp, _vp], C.c_int),
+    "se_pmg_fdm": ([_vp, _ip, _vp, _vp, _vp], C.c_int),
+    "se_pmg_cheby": ([_vp, _ip, _vp, _vp, _vp], C.c_int),
+    "se_pmg_restrict": ([_vp, _ip, _vp, _vp, _vp], C.c_int),
+    "se_pmg_prolong": ([_vp, _ip, _vp, _vp, _vp], C.c_int),
+    "se_pmg_coarse_solve": ([_vp, _vp, _vp, C.POINTER(C.c_int), _vp], C.c_int),
+    "se_solve": ([_vp, _vp, _vp, _vp, C.POINTER(se_solve_opts), C.POINTER(se_solve_stats)], C.c_int),
+    "se_prof_enable": ([_ip], C.c_int),
+    "se_prof_reset": ([], C.c_int),
+    "se_prof_query": ([_ip, _dp, C.POINTER(C.c_int64), _dp, _dp, _dp], C.c_int),
+    "se_selftest_wait_timeout": ([C.c_double], C.c_int),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+EXPORTED = tuple(_SIGS)
+
+
+def se_last_error() -> str:
+    return lib.se_last_error().decode()
+
+
+def _check(code: int, allow=()):
+    if code != SE_OK and code not in allow:
+        raise SeError(code, se_last_error())
+    return code
+
+
+def _ptr(x):
+    """Device pointer of a contiguous CUDA tensor (or a raw int pointer)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if not x.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not x.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return x.data_ptr()
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+# ----------------------------------------------------------------------------- mesh / operator
+def se_mesh_create(nel, p, *, vertex_xyz=None, deform_amp=0.05, perturb_frac=0.0, seed=0,
+                   bc=(SE_BC_DIRICHLET,) * 6):
+    """Create a mesh; vertex_xyz is an optional host float64 array of shape (V, 3)."""
+    d = se_mesh_desc()
+    d.nel[:] = list(nel)
+    d.p = p
+    keep = None
+    if vertex_xyz is not None:
+        import numpy as np
+        keep = np.ascontiguousarray(vertex_xyz, dtype=np.float64).reshape(-1)
+        d.vertex_xyz = keep.ctypes.data_as(C.POINTER(C.c_double))
+    d.deform_amp = deform_amp
+    d.perturb_frac = perturb_frac
+    d.seed = seed
+    d.bc[:] = list(bc)
+    h = _vp()
+    _check(lib.se_mesh_create(C.byref(d), C.byref(h)))
+    return h.value
+
+
+def se_mesh_destroy(m):
+    _check(lib.se_mesh_destroy(m))
+
+
+def se_mesh_get_info(m) -> se_mesh_info:
+    info = se_mesh_info()
+    _check(lib.se_mesh_get_info(m, C.byref(info)))
+    return info
+
+
+def se_mesh_nodes(m, xyz, stream=None):
+    _check(lib.se_mesh_nodes(m, _ptr(xyz), _stream(stream)))
+
+
+def se_mesh_vertices(m, out_np):
+    _check(lib.se_mesh_vertices(m, out_np.ctypes.data_as(C.POINTER(C.c_double))))
+
+
+def se_mesh_rhs(m, f, b, stream=None):
+    _check(lib.se_mesh_rhs(m, _ptr(f), _ptr(b), _stream(stream)))
+
+
+def se_ax(m, u, y, flags=SE_AX_ASSEMBLE | SE_AX_MASK, stream=None):
+    _check(lib.se_ax(m, _ptr(u), _ptr(y), flags, _stream(stream)))
+
+
+def se_gs(m, u, mask=1, stream=None):
+    _check(lib.se_gs(m, _ptr(u), mask, _stream(stream)))
+
+
+def se_dot(m, a, b, stream=None) -> float:
+    out = C.c_double()
+    _check(lib.se_dot(m, _ptr(a), _ptr(b), C.byref(out), _stream(stream)))
+    return out.value
+
+
+def se_jacobi_diag(m, d, stream=None):
+    _check(lib.se_jacobi_diag(m, _ptr(d), _stream(stream)))
+
+
+# ----------------------------------------------------------------------------- p-multigrid
+def pmg_desc(schedule, smoother=SE_SMOOTH_RAS, cheb_order=2, eig_lo=0.1, eig_hi=1.1,
+             arnoldi_steps=10, seed=0, coarse_tol=1e-4, coarse_maxit=500, precision=SE_FP64):
+    d = se_pmg_desc()
+    d.nlev = len(schedule)
+    d.schedule[:len(schedule)] = list(schedule)
+    d.smoother = smoother
+    orders = cheb_order if isinstance(cheb_order, (list, tuple)) else [cheb_order] * len(schedule)
+    d.cheb_order[:len(orders)] = list(orders)
+    d.eig_lo, d.eig_hi = eig_lo, eig_hi
+    d.arnoldi_steps = arnoldi_steps
+    d.seed = seed
+    d.coarse_tol, d.coarse_maxit = coarse_tol, coarse_maxit
+    d.precision = precision
+    return d
+
+
+def se_pmg_setup(m, desc: se_pmg_desc):
+    h = _vp()
+    _check(lib.se_pmg_setup(m, C.byref(desc), C.byref(h)))
+    return h.value
+
+
+def se_pmg_destroy(P):
+    _check(lib.se_pmg_destroy(P))
+
+
+def se_pmg_apply(P, r, z, stream=None):
+    _check(lib.se_pmg_apply(P, _ptr(r), _ptr(z), _stream(stream)))
+
+
+def se_pmg_lambda(P, lvl) -> float:
+    out = C.c_double()
+    _check(lib.se_pmg_lambda(P, lvl, C.byref(out)))
+    return out.value
+
+
+def se_pmg_level_info(P, lvl) -> se_mesh_info:
+    info = se_mesh_info()
+    _check(lib.se_pmg_level_info(P, lvl, C.byref(info)))
+    return info
+
+
+def _lvl_call(fn):
+    def call(P, lvl, a, b, stream=None):
+        _check(fn(P, lvl, _ptr(a), _ptr(b), _stream(stream)))
+    return call
+
+
+se_pmg_level_ax = _lvl_call(lib.se_pmg_level_ax)
+se_pmg_smooth = _lvl_call(lib.se_pmg_smooth)
+se_pmg_gather_ext = _lvl_call(lib.se_pmg_gather_ext)
+se_pmg_fdm = _lvl_call(lib.se_pmg_fdm)
+se_pmg_cheby = _lvl_call(lib.se_pmg_cheby)
+se_pmg_restrict = _lvl_call(lib.se_pmg_restrict)
+se_pmg_prolong = _lvl_call(lib.se_pmg_prolong)
+
+
+def se_pmg_coarse_solve(P, r, x, stream=None) -> int:
+    it = C.c_int()
+    _check(lib.se_pmg_coarse_solve(P, _ptr(r), _ptr(x), C.byref(it), _stream(stream)))
+    return it.value
+
+
+# ----------------------------------------------------------------------------- solve
+def se_solve(m, P, b, x, method=SE_FPCG, tol=1e-8, maxit=1000, restart=20, graph_capture=0,
+             stream=None, allow_notconv=False) -> se_solve_stats:
+    o = se_solve_opts()
+    o.method, o.restart, o.tol, o.maxit, o.graph_capture = method, restart, tol, maxit, graph_capture
+    o.stream = _stream(stream)
+    st = se_solve_stats()
+    _check(lib.se_solve(m, P, _ptr(b), _ptr(x), C.byref(o), C.byref(st)),
+           allow=(SE_ENOTCONV,) if allow_notconv else ())
+    return st
+
+
+# ----------------------------------------------------------------------------- profiling
+def se_prof_enable(on=True):
+    _check(lib.se_prof_enable(1 if on else 0))
+
+
+def se_prof_reset():
+    _check(lib.se_prof_reset())
+
+
+def se_prof_query(kind):
+    ms, n, units, by, fl = C.c_double(), C.c_int64(), C.c_double(), C.c_double(), C.c_double()
+    _check(lib.se_prof_query(kind, C.byref(ms), C.byref(n), C.byref(units), C.byref(by), C.byref(fl)))
+    return dict(ms=ms.value, launches=n.value, units=units.value, bytes=by.value, flops=fl.value)
+
+
+def se_selftest_wait_timeout(timeout_ms=100.0) -> int:
+    return lib.se_selftest_wait_timeout(timeout_ms)

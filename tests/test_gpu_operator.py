@@ -1,0 +1,143 @@
+"""GPU parity of the operator path (Sec. 2.1) against the oracle, through the C ABI.
+
+Tolerances: FP64 operator relative error <= 1e-12 (max-norm relative to the largest entry);
+FP32 operator <= 2e-5 (single precision with O(N) accumulation depth).
+"""
+import numpy as np
+import pytest
+
+import oracle as o
+import workloads as wl
+from tests.gpu_common import Case, rel_err
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [((1, 1, 1), 1), ((2, 3, 1), 2), ((3, 2, 2), 3), ((2, 2, 3), 4), ((3, 3, 2), 5),
+          ((2, 2, 2), 6), ((3, 1, 2), 7), ((2, 2, 2), 8), ((1, 2, 2), 9), ((2, 1, 1), 10)]
+
+
+@pytest.mark.parametrize("nel,p", SHAPES)
+def test_geometry_and_vertices(nel, p):
+    c = Case(nel, p, seed=p)
+    try:
+        xyz = c.empty(3 * c.info.L)
+        c.se.se_mesh_nodes(c.m, xyz)
+        X = xyz.cpu().numpy().reshape(c.lv.X.shape)
+        assert rel_err(X, c.lv.X) < 1e-14
+        assert c.info.E == np.prod(nel) and c.info.n_dof == np.prod(nel) * p ** 3
+        assert c.info.n_global == c.lv.n_global
+    finally:
+        c.close()
+
+
+def test_library_vertex_generator_matches_inputs():
+    torch, se = Case((1, 1, 1), 1).torch, Case((1, 1, 1), 1).se
+    nel = (5, 4, 3)
+    m = se.se_mesh_create(nel, 3, perturb_frac=0.05, seed=11)
+    try:
+        out = np.empty((nel[2] + 1) * (nel[1] + 1) * (nel[0] + 1) * 3)
+        se.se_mesh_vertices(m, out)
+        ref = wl.vertex_lattice(nel, 0.05, seed=11).reshape(-1)
+        assert np.array_equal(out, ref)
+    finally:
+        se.se_mesh_destroy(m)
+
+
+@pytest.mark.parametrize("nel,p", SHAPES)
+@pytest.mark.parametrize("bc", [("D",) * 6, ("N", "D", "N", "N", "D", "N")])
+def test_ax_fp64(nel, p, bc):
+    c = Case(nel, p, seed=10 + p, bc=bc)
+    try:
+        u = c.random_continuous(1, masked=False)
+        y = c.empty()
+        ug = c.to_gpu(u)
+        se = c.se
+        # assembled + masked
+        se.se_ax(c.m, ug, y, se.SE_AX_ASSEMBLE | se.SE_AX_MASK)
+        assert rel_err(c.to_np(y), o.ax(c.lv, u)) <= 1e-12
+        # local only
+        se.se_ax(c.m, ug, y, 0)
+        assert rel_err(c.to_np(y), o.ax_local(c.lv, u)) <= 1e-12
+        # assembled without mask
+        se.se_ax(c.m, ug, y, se.SE_AX_ASSEMBLE)
+        assert rel_err(c.to_np(y), o.ax(c.lv, u, mask=False)) <= 1e-12
+        # FP32 compute path
+        se.se_ax(c.m, ug, y, se.SE_AX_ASSEMBLE | se.SE_AX_MASK | se.SE_AX_FP32)
+        assert rel_err(c.to_np(y), o.ax(c.lv, u)) <= 2e-5
+    finally:
+        c.close()
+
+
+def test_neumann_nullspace_and_symmetry_on_gpu():
+    c = Case((3, 2, 2), 5, bc=("N",) * 6)
+    try:
+        se = c.se
+        one = c.torch.ones(c.info.L, dtype=c.torch.float64, device=c.dev)
+        y = c.empty()
+        se.se_ax(c.m, one, y, se.SE_AX_ASSEMBLE)
+        assert float(y.abs().max()) < 1e-12
+        u, v = c.to_gpu(c.random_continuous(2, masked=False)), c.to_gpu(c.random_continuous(3, masked=False))
+        au, av = c.empty(), c.empty()
+        se.se_ax(c.m, u, au, se.SE_AX_ASSEMBLE)
+        se.se_ax(c.m, v, av, se.SE_AX_ASSEMBLE)
+        a, b = se.se_dot(c.m, v, au), se.se_dot(c.m, u, av)
+        assert abs(a - b) <= 1e-12 * max(abs(a), 1.0)
+    finally:
+        c.close()
+
+
+@pytest.mark.parametrize("nel,p", SHAPES[::2])
+def test_gs_dot_rhs_and_jacobi(nel, p):
+    c = Case(nel, p, seed=20 + p)
+    try:
+        se = c.se
+        u = wl.random_lvector(c.lv.gid.shape, 5)          # discontinuous L-vector
+        g = c.to_gpu(u)
+        se.se_gs(c.m, g, 1)
+        assert rel_err(c.to_np(g), c.lv.mask * o.qqt(c.lv, u)) <= 1e-14
+        g = c.to_gpu(u)
+        se.se_gs(c.m, g, 0)
+        assert rel_err(c.to_np(g), o.qqt(c.lv, u)) <= 1e-14
+        a, b = c.random_continuous(6), c.random_continuous(7)
+        d = se.se_dot(c.m, c.to_gpu(a), c.to_gpu(b))
+        assert abs(d - o.dot(c.lv, a, b)) <= 1e-13 * max(1.0, abs(d))
+        f = wl.f_rhs(*c.lv.X)
+        bb = c.empty()
+        se.se_mesh_rhs(c.m, c.to_gpu(f), bb)
+        assert rel_err(c.to_np(bb), o.rhs(c.lv, f)) <= 1e-13
+        dg = c.empty()
+        se.se_jacobi_diag(c.m, dg)
+        err = rel_err(c.to_np(dg), o.jacobi_diag(c.lv))
+        assert err <= 1e-12, err
+    finally:
+        c.close()
+
+
+def test_bounded_wait_returns_timeout_status():
+    c = Case((1, 1, 1), 1)
+    try:
+        rc = c.se.se_selftest_wait_timeout(50.0)
+        assert rc == c.se.SE_ETIMEOUT
+        # the context is still usable afterwards
+        y = c.empty()
+        c.se.se_ax(c.m, c.to_gpu(np.ones(c.info.L)), y, 0)
+        c.torch.cuda.synchronize()
+    finally:
+        c.close()
+
+
+def test_invalid_arguments_are_rejected():
+    _, se = Case((1, 1, 1), 1).torch, Case((1, 1, 1), 1).se
+    with pytest.raises(se.SeError) as e:
+        se.se_mesh_create((2, 2, 2), 11)
+    assert e.value.code == se.SE_EINVAL
+    with pytest.raises(se.SeError):
+        se.se_mesh_create((0, 2, 2), 3)
+    c = Case((2, 2, 2), 3)
+    try:
+        with pytest.raises(se.SeError):
+            se.se_pmg_setup(c.m, se.pmg_desc((5, 3, 1)))          # schedule[0] != p
+        with pytest.raises(se.SeError):
+            se.se_pmg_setup(c.m, se.pmg_desc((3, 2)))             # coarsest must be p = 1
+    finally:
+        c.close()

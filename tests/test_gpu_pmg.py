@@ -1,0 +1,130 @@
+"""GPU parity of the p-multigrid building blocks (Sec. 2.3, Algorithms 1-2, eqs 4-9).
+
+Tolerances (relative, max-norm): gather and transfers 1e-13; smoothers, FDM, Chebyshev 1e-10
+(the local eigen-decompositions are computed by different algorithms: cyclic Jacobi rotations
+on the GPU, LAPACK eigh in the oracle; the FDM result is invariant to them up to rounding
+times the local condition number); lambda-tilde 1e-9; V-cycle 1e-8 when both coarse solves
+take the same number of iterations.  FP32 preconditioner against the FP64 oracle: 1e-4.
+"""
+import numpy as np
+import pytest
+
+import oracle as o
+import workloads as wl
+from tests.gpu_common import Case, rel_err
+
+pytestmark = pytest.mark.gpu
+
+SMOOTHERS = {"ras": 1, "asm": 2, "jacobi": 0}
+
+
+def build(nel, p, schedule, smoother, order=2, precision=0, seed=3, bc=("D",) * 6):
+    c = Case(nel, p, seed=seed, bc=bc)
+    se = c.se
+    P = se.se_pmg_setup(c.m, se.pmg_desc(schedule, SMOOTHERS[smoother], order, precision=precision))
+    pmg = o.pmg_setup(c.V, nel, schedule, smoother=smoother, order=order, bc=bc, amp=c.amp)
+    return c, P, pmg
+
+
+CASES = [((3, 2, 2), 5, (5, 3, 1)), ((2, 3, 2), 7, (7, 3, 1)), ((2, 2, 2), 9, (9, 5, 1)),
+         ((4, 3, 2), 3, (3, 1))]
+
+
+@pytest.mark.parametrize("nel,p,schedule", CASES)
+@pytest.mark.parametrize("smoother", ["ras", "jacobi", "asm"])
+def test_pmg_building_blocks(nel, p, schedule, smoother):
+    c, P, pmg = build(nel, p, schedule, smoother)
+    se, torch = c.se, c.torch
+    try:
+        for l in range(len(schedule) - 1):
+            lv = pmg.levels[l]
+            info = se.se_pmg_level_info(P, l)
+            assert info.L == lv.gid.size
+            lam = se.se_pmg_lambda(P, l)
+            assert abs(lam - pmg.lam[l]) <= 1e-9 * pmg.lam[l], (lam, pmg.lam[l])
+            r = c.random_continuous(40 + l, lv)
+            rg = c.to_gpu(r)
+            out = c.empty(info.L)
+            se.se_pmg_level_ax(P, l, rg, out)
+            assert rel_err(c.to_np(out, lv.gid.shape), o.ax(lv, r)) <= 1e-12
+            se.se_pmg_smooth(P, l, rg, out)
+            ref = o.smoother_op(pmg, l)(r)
+            assert rel_err(c.to_np(out, lv.gid.shape), ref) <= 1e-10
+            se.se_pmg_cheby(P, l, rg, out)
+            lmin, lmax = pmg.bounds[l]
+            refc = o.chebyshev(r, lambda u: o.ax(lv, u), o.smoother_op(pmg, l), lmin, lmax, 2)
+            assert rel_err(c.to_np(out, lv.gid.shape), refc) <= 1e-9
+            # transfers to/from the next level
+            lc = pmg.levels[l + 1]
+            rc = c.empty(lc.gid.size)
+            se.se_pmg_restrict(P, l, rg, rc)
+            assert rel_err(c.to_np(rc, lc.gid.shape), o.restrict(lv, lc, r)) <= 1e-13
+            ec = c.random_continuous(50 + l, lc)
+            se.se_pmg_prolong(P, l, c.to_gpu(ec), out)
+            assert rel_err(c.to_np(out, lv.gid.shape), o.prolong(lv, lc, ec)) <= 1e-13
+            if smoother != "jacobi":
+                pb = lv.p + 3
+                rbar = c.empty(lv.E * pb ** 3)
+                se.se_pmg_gather_ext(P, l, rg, rbar)
+                ref_bar = o.extended_gather(lv, r)
+                assert rel_err(c.to_np(rbar, ref_bar.shape), ref_bar) <= 1e-15
+                xb = wl.random_lvector(ref_bar.shape, 60 + l)
+                zb = c.empty(lv.E * pb ** 3)
+                se.se_pmg_fdm(P, l, c.to_gpu(xb), zb)
+                S, Lm = lv.extra["fdm"]
+                assert rel_err(c.to_np(zb, ref_bar.shape), o.fdm_apply(S, Lm, xb)) <= 1e-10
+        # coarse solve and the whole V-cycle
+        lcs = pmg.levels[-1]
+        rc = c.random_continuous(70, lcs)
+        xc = c.empty(lcs.gid.size)
+        it = se.se_pmg_coarse_solve(P, c.to_gpu(rc), xc)
+        pmg.coarse_iters.clear()
+        xref = o.coarse_solve(pmg, rc)
+        it_ref = pmg.coarse_iters[-1]
+        assert abs(it - it_ref) <= 1
+        if it == it_ref:
+            assert rel_err(c.to_np(xc, lcs.gid.shape), xref) <= 1e-8
+        lv0 = pmg.levels[0]
+        r0 = c.random_continuous(80, lv0)
+        z = c.empty()
+        se.se_pmg_apply(P, c.to_gpu(r0), z)
+        pmg.coarse_iters.clear()
+        zref = o.vcycle(pmg, r0)
+        assert rel_err(c.to_np(z), zref) <= 1e-6
+        torch.cuda.synchronize()
+    finally:
+        se.se_pmg_destroy(P)
+        c.close()
+
+
+@pytest.mark.parametrize("smoother", ["ras", "jacobi"])
+def test_fp32_vcycle_against_fp64_oracle(smoother):
+    c, P, pmg = build((3, 2, 2), 7, (7, 3, 1), smoother, precision=1)
+    try:
+        r0 = c.random_continuous(90)
+        z = c.empty()
+        c.se.se_pmg_apply(P, c.to_gpu(r0), z)
+        zref = o.vcycle(pmg, r0)
+        assert rel_err(c.to_np(z), zref) <= 1e-4
+        assert abs(c.se.se_pmg_lambda(P, 0) - pmg.lam[0]) <= 1e-9 * pmg.lam[0]
+    finally:
+        c.se.se_pmg_destroy(P)
+        c.close()
+
+
+def test_two_preconditioners_on_one_mesh():
+    c = Case((2, 2, 2), 5)
+    se = c.se
+    try:
+        P1 = se.se_pmg_setup(c.m, se.pmg_desc((5, 3, 1), se.SE_SMOOTH_RAS, 2))
+        P2 = se.se_pmg_setup(c.m, se.pmg_desc((5, 1), se.SE_SMOOTH_JACOBI, 3))
+        r = c.to_gpu(c.random_continuous(1))
+        z1, z2, z3 = c.empty(), c.empty(), c.empty()
+        se.se_pmg_apply(P1, r, z1)
+        se.se_pmg_apply(P2, r, z2)
+        se.se_pmg_destroy(P2)
+        se.se_pmg_apply(P1, r, z3)
+        assert c.torch.equal(z1, z3)
+        se.se_pmg_destroy(P1)
+    finally:
+        c.close()

@@ -1,0 +1,133 @@
+"""GPU parity of whole solves (Sec. 2.2 outer Krylov with the Sec. 2.3 preconditioners).
+
+Bar: the GPU solution meets the requested relative residual 1e-8 (checked with the ORACLE's
+operator on the GPU solution), and its iteration count is within +-1 of the oracle's on the
+same seeded problem.  Mixed precision (FP32 preconditioner): residual 1e-8 reached; the error
+against the FP64 oracle solution and the iteration counts are reported.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as o
+import workloads as wl
+from tests.gpu_common import Case, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_problem(c):
+    xyz = c.empty(3 * c.info.L)
+    c.se.se_mesh_nodes(c.m, xyz)
+    X = xyz.cpu().numpy().reshape(3, -1)
+    f = wl.f_rhs(X[0], X[1], X[2])
+    b = c.empty()
+    c.se.se_mesh_rhs(c.m, c.to_gpu(f), b)
+    return b
+
+
+def true_rel_residual(c, x_np, b_np):
+    r = b_np - o.ax(c.lv, x_np)
+    return math.sqrt(o.dot(c.lv, r, r) / o.dot(c.lv, b_np, b_np))
+
+
+SMALL = dict(nel=(4, 4, 4), p=7, pert=0.0)
+
+
+@pytest.mark.parametrize("pre,method", [("jacobi", "fpcg"), ("ras", "fpcg"), ("ras", "fgmres"),
+                                        ("chebjac", "fpcg"), ("asm", "fpcg")])
+def test_small_box_solve_parity(pre, method):
+    c = Case(SMALL["nel"], SMALL["p"], pert=SMALL["pert"])
+    se = c.se
+    P = None
+    try:
+        b = gpu_problem(c)
+        lvo, bo = o.problem(c.V, c.nel, c.p, amp=c.amp)
+        assert rel_err(c.to_np(b), bo) <= 1e-13
+        if pre == "jacobi":
+            pmg = None
+        else:
+            sm = {"ras": "ras", "asm": "asm", "chebjac": "jacobi"}[pre]
+            P = se.se_pmg_setup(c.m, se.pmg_desc((7, 3, 1), {"ras": 1, "asm": 2, "jacobi": 0}[sm], 2))
+            pmg = o.pmg_setup(c.V, c.nel, (7, 3, 1), smoother=sm, order=2, amp=c.amp)
+        x = c.empty().zero_()
+        meth = se.SE_FPCG if method == "fpcg" else se.SE_FGMRES
+        st = se.se_solve(c.m, P, b, x, method=meth, tol=1e-8, maxit=2000, restart=20)
+        xo, it_o, rel_o = o.solve(lvo, bo, pmg, method=method, tol=1e-8, maxit=2000)
+        assert st.rel_residual <= 1e-8
+        assert abs(st.iterations - it_o) <= 1, (st.iterations, it_o)
+        assert true_rel_residual(c, c.to_np(x), bo) <= 1.5e-8
+        assert rel_err(c.to_np(x), xo) <= 1e-5
+        print(f"{pre}/{method}: gpu {st.iterations} it, oracle {it_o} it, {st.ms_total:.1f} ms")
+    finally:
+        if P:
+            se.se_pmg_destroy(P)
+        c.close()
+
+
+@pytest.mark.parametrize("p,schedule", [(7, (7, 3, 1)), (9, (9, 5, 1)), (9, (9, 7, 5, 1))])
+def test_mixed_precision_solve(p, schedule):
+    c = Case((4, 4, 4), p, pert=0.0)
+    se = c.se
+    P64 = P32 = None
+    try:
+        b = gpu_problem(c)
+        P64 = se.se_pmg_setup(c.m, se.pmg_desc(schedule, se.SE_SMOOTH_RAS, 2, precision=se.SE_FP64))
+        P32 = se.se_pmg_setup(c.m, se.pmg_desc(schedule, se.SE_SMOOTH_RAS, 2, precision=se.SE_FP32))
+        x64, x32 = c.empty().zero_(), c.empty().zero_()
+        s64 = se.se_solve(c.m, P64, b, x64, tol=1e-8)
+        s32 = se.se_solve(c.m, P32, b, x32, tol=1e-8)
+        lvo, bo = o.problem(c.V, c.nel, p, amp=c.amp)
+        pmg = o.pmg_setup(c.V, c.nel, schedule, smoother="ras", order=2, amp=c.amp)
+        xo, it_o, _ = o.solve(lvo, bo, pmg, tol=1e-8)
+        assert abs(s64.iterations - it_o) <= 1
+        assert true_rel_residual(c, c.to_np(x32), bo) <= 1.5e-8
+        err32 = rel_err(c.to_np(x32), xo)
+        assert err32 <= 1e-5
+        assert s32.iterations <= s64.iterations + 3
+        u_star = wl.u_exact(*lvo.X)
+        print(f"p={p} {schedule}: fp64 {s64.iterations} it, fp32-precond {s32.iterations} it, "
+              f"oracle {it_o} it, |x32-x_oracle|/|x| {err32:.2e}, "
+              f"|x32-u*| {np.max(np.abs(c.to_np(x32) - u_star)):.2e}")
+    finally:
+        for P in (P64, P32):
+            if P:
+                se.se_pmg_destroy(P)
+        c.close()
+
+
+def test_solve_reuses_mesh_and_is_deterministic():
+    c = Case((3, 3, 3), 5, pert=0.05, seed=4)
+    se = c.se
+    P = se.se_pmg_setup(c.m, se.pmg_desc((5, 3, 1), se.SE_SMOOTH_RAS, 1))
+    try:
+        b = gpu_problem(c)
+        x1, x2 = c.empty().zero_(), c.empty().zero_()
+        s1 = se.se_solve(c.m, P, b, x1, tol=1e-10)
+        s2 = se.se_solve(c.m, P, b, x2, tol=1e-10)
+        assert s1.iterations == s2.iterations
+        assert c.torch.equal(x1, x2)
+        # a warm start: the tolerance is relative to the warm start's own residual
+        x3 = x1.clone()
+        s3 = se.se_solve(c.m, P, b, x3, tol=1e-4)
+        assert s3.iterations < s1.iterations
+        assert float((x3 - x1).abs().max()) <= 1e-8 * float(x1.abs().max())
+    finally:
+        se.se_pmg_destroy(P)
+        c.close()
+
+
+def test_not_converged_status():
+    c = Case((3, 3, 3), 5)
+    se = c.se
+    try:
+        b = gpu_problem(c)
+        x = c.empty().zero_()
+        with pytest.raises(se.SeError) as e:
+            se.se_solve(c.m, None, b, x, tol=1e-12, maxit=3)
+        assert e.value.code == se.SE_ENOTCONV
+        st = se.se_solve(c.m, None, b, x.zero_(), tol=1e-12, maxit=3, allow_notconv=True)
+        assert st.iterations == 3 and st.status == se.SE_ENOTCONV
+    finally:
+        c.close()
