@@ -1,0 +1,341 @@
+"""Benchmark: Poisson solves of the 32^3-element, p=7 deformed box (FP64 method).
+
+One step = one whole solve (x0 = 0) of the pressure-Poisson problem with flexible PCG to a
+relative residual of 1e-8, preconditioned by the p-multigrid V-cycle 7->5->3->1 with
+2nd-order Chebyshev-accelerated RAS smoothing and a p=1 Jacobi-PCG coarse solve, all in FP64.
+value = gridpoints solved per second, n = E p^3 per solve (the paper's work-rate measure),
+summed over ranks.  Inputs (mesh, geometry, FDM factors, right-hand side) are resident in HBM
+before the timed region; every step works on ~12 GB of state, far larger than L2.
+
+--impl reference runs the FP64 CPU oracle (test infrastructure) on a bounded sample of the same
+workload instead.  N > 1: independent replicas, one problem per rank (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "box32_p7": dict(nel=(32, 32, 32), p=7, perturb=0.05, seed=0, schedule=(7, 5, 3, 1)),
+    "box24_p7": dict(nel=(24, 24, 24), p=7, perturb=0.05, seed=0, schedule=(7, 5, 3, 1)),
+    "box16_p7": dict(nel=(16, 16, 16), p=7, perturb=0.05, seed=0, schedule=(7, 5, 3, 1)),
+    "box4_p7": dict(nel=(4, 4, 4), p=7, perturb=0.0, seed=0, schedule=(7, 3, 1)),
+}
+SAMPLE = dict(nel=(10, 10, 10), p=7, perturb=0.05, seed=0, schedule=(7, 5, 3, 1))
+METRIC = "Poisson solve time & Ax/smoother GDOF/s (%HBM roof); served solves/s, p99"
+FP64_FMA_PER_CLK_PER_SM = 2      # GB300: 1.25 TFLOP/s FP64 nominal at 152 SMs x 2.07 GHz
+N_SMS = 152
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
+        int(os.environ.get("LOCAL_RANK", 0))
+
+
+def max_over_ranks(value, world):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(value, world):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2110_07663_gb300 import se
+    import workloads as wl
+
+    wk = WORKLOADS[args.workload]
+    nel, p = wk["nel"], wk["p"]
+    m = se.se_mesh_create(nel, p, perturb_frac=wk["perturb"], seed=wk["seed"] + rank,
+                          deform_amp=wl.DEFORM_AMP)
+    info = se.se_mesh_get_info(m)
+    L = info.L
+    xyz = torch.empty(3 * L, dtype=torch.float64, device=dev)
+    se.se_mesh_nodes(m, xyz)
+    X = xyz.view(3, L)
+    f = 3.0 * math.pi ** 2 * torch.sin(math.pi * X[0]) * torch.sin(math.pi * X[1]) * torch.sin(math.pi * X[2])
+    b = torch.empty(L, dtype=torch.float64, device=dev)
+    se.se_mesh_rhs(m, f.contiguous(), b)
+    del xyz, X, f
+    smoother = {"ras": se.SE_SMOOTH_RAS, "jacobi": se.SE_SMOOTH_JACOBI, "asm": se.SE_SMOOTH_ASM}[args.smoother]
+    prec = se.SE_FP32 if args.precond_fp32 else se.SE_FP64
+    t_setup0 = time.perf_counter()
+    P = se.se_pmg_setup(m, se.pmg_desc(wk["schedule"], smoother, args.cheb_order, precision=prec))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_setup0
+    x = torch.zeros(L, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        x.zero_()
+        return se.se_solve(m, P, b, x, tol=1e-8, maxit=500, stream=stream)
+
+    for _ in range(args.warmup):
+        st = step()
+    iters = st.iterations
+    # ---- timed region (device-resident inputs); per-kernel CUDA events on the launch stream
+    se.se_prof_reset()
+    se.se_prof_enable(True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            st = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    se.se_prof_enable(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_max = max_over_ranks(ms, world)
+    prof = {se.KERNEL_NAMES[k]: se.se_prof_query(k) for k in range(se.SE_K_COUNT)}
+    launches = sum(v["launches"] for v in prof.values())
+    # ---- end to end through the public API with host buffers (copies inside the timed region)
+    b_host = b.cpu().pin_memory()
+    x_host = torch.empty(L, dtype=torch.float64).pin_memory()
+    b_dev = torch.empty_like(b)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(1, min(args.steps, 3))
+    f0.record(stream)
+    for _ in range(e2e_steps):
+        b_dev.copy_(b_host, non_blocking=True)
+        x.zero_()
+        se.se_solve(m, P, b_dev, x, tol=1e-8, maxit=500, stream=stream)
+        x_host.copy_(x, non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(f0.elapsed_time(f1) / e2e_steps, world)
+    n_dof = info.n_dof
+    total_dof = sum_over_ranks(float(n_dof), world)
+    value = total_dof / (ms_max * 1e-3) / 1e9
+    e2e_value = total_dof / (e2e_ms * 1e-3) / 1e9
+    # ---- roofline of the dominant kernel
+    pk, pk_kind = peaks()
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    avg_ms = d["ms"] / max(d["launches"], 1)
+    sm_max = pk.get("sm_max_mhz", 2070.0)
+    fp64_peak = N_SMS * FP64_FMA_PER_CLK_PER_SM * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
+    if args.precond_fp32 and dom in ("fdm", "ax", "gs", "cheby_update", "restrict", "prolong"):
+        bound, peak, unit = "hbm", pk["hbm_gbs"], "GB/s"
+        achieved = d["bytes"] / max(d["launches"], 1) / (avg_ms * 1e-3) / 1e9
+    else:
+        bound, peak, unit = "alu", fp64_peak, "TFLOP/s"
+        # algorithmic flops per launch (the library records them per launch: for the RAS local
+        # solve 6 pbar^4 + pbar^3 + 2(pbar^3 N + pbar^2 N^2 + pbar N^3) per element)
+        achieved = d["flops"] / max(d["launches"], 1) / (avg_ms * 1e-3) / 1e12
+    kernels = {k: {"ms_per_step": round(v["ms"] / args.steps, 3), "launches_per_step": v["launches"] / args.steps,
+                   "share": round(v["ms"] / max(sum(w["ms"] for w in prof.values()), 1e-9), 4)}
+               for k, v in prof.items() if v["launches"]}
+    out = {
+        "metric": METRIC, "value": round(value, 4), "unit": "GDOF/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: deformed box {nel[0]}x{nel[1]}x{nel[2]} hex, p={p}, "
+                               f"n={n_dof} (E p^3), pMG {'-'.join(map(str, wk['schedule']))} "
+                               f"Cheby-{args.smoother.upper()}({args.cheb_order}), "
+                               f"FPCG tol 1e-8, {'FP32' if args.precond_fp32 else 'FP64'} preconditioner",
+                   "iterations": iters, "setup_s": round(setup_s, 2),
+                   "l2": "inputs larger than L2 (about 12 GB of resident state per solve)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": round(e2e_value, 4), "unit": "GDOF/s", "h2d_bytes_per_step": int(8 * L),
+                "d2h_bytes_per_step": int(8 * L)},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": bound, "kernel": dom, "achieved": round(achieved, 4),
+                     "peak": round(peak, 4), "unit": unit, "frac": round(achieved / peak, 4),
+                     "traffic": None, "peak_source": pk_kind if bound == "hbm" else
+                     "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x sm_max_mhz"},
+        "kernels": kernels,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline_subprocess(args.cpu_timeout)
+    se.se_pmg_destroy(P)
+    se.se_mesh_destroy(m)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# --------------------------------------------------------------------------------- CPU oracle
+def oracle_sample(timeout_s):
+    """Oracle solve of the bounded sample (same method and tolerance, 6^3 elements)."""
+    import numpy as np
+    import oracle as o
+    import workloads as wl
+    V = wl.vertex_lattice(SAMPLE["nel"], SAMPLE["perturb"], SAMPLE["seed"])
+    lv, b = o.problem(V, SAMPLE["nel"], SAMPLE["p"], amp=wl.DEFORM_AMP)
+    pmg = o.pmg_setup(V, SAMPLE["nel"], SAMPLE["schedule"], smoother="ras", order=2, amp=wl.DEFORM_AMP)
+    t0 = time.perf_counter()
+    x, it, rel = o.solve(lv, b, pmg, tol=1e-8)
+    t = time.perf_counter() - t0
+    n = int(np.prod(SAMPLE["nel"])) * SAMPLE["p"] ** 3
+    return n / t / 1e9, t, it
+
+
+def cpu_baseline_subprocess(timeout_s):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "v, t, it = bench.oracle_sample(0); print(json.dumps([v, t, it]))" % ROOT)
+    try:
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                           timeout=timeout_s, env=env)
+        v, t, it = json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception as e:  # noqa: BLE001
+        return {"value": None, "unit": "GDOF/s", "cores": 1, "kind": "oracle",
+                "sample": f"failed: {type(e).__name__}"}
+    return {"value": round(v, 6), "unit": "GDOF/s", "cores": 1, "kind": "oracle",
+            "sample": f"one full solve of a 10x10x10-element p=7 piece of the same workload "
+                      f"(same map, schedule, smoother, tolerance): {it} iterations in {t:.1f} s, "
+                      f"single thread"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    env_threads = 1
+    vals = []
+    t_total = 0.0
+    for _ in range(args.steps):
+        v, t, it = oracle_sample(0)
+        vals.append(v)
+        t_total += t
+    value = statistics.median(vals)
+    ms = t_total / args.steps * 1e3
+    out = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "GDOF/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload} (oracle on a bounded 10x10x10-element p=7 sample)",
+                   "parallelism": "cpu"},
+        "cpu_baseline": {"value": round(value, 6), "unit": "GDOF/s", "cores": env_threads,
+                         "kind": "oracle",
+                         "sample": "each step one full oracle solve of a 10x10x10-element p=7 piece "
+                                   "of the workload"},
+        "e2e": {"value": round(value, 6), "unit": "GDOF/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="box32_p7", choices=sorted(WORKLOADS))
+    ap.add_argument("--smoother", default="ras", choices=["ras", "jacobi", "asm"])
+    ap.add_argument("--cheb-order", type=int, default=2)
+    ap.add_argument("--precond-fp32", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-timeout", type=float, default=240.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gb300":
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()
