@@ -160,6 +160,21 @@ int se_pmg_prolong(se_pmg_t pmg, int lvl, const double* ec, double* ef, void* st
 /* Coarsest level: x = A_c^-1 r by Jacobi-PCG to coarse_tol (FP64, one persistent cooperative
  * launch).  *iters receives the iteration count (synchronises). */
 int se_pmg_coarse_solve(se_pmg_t pmg, const double* r, double* x, int* iters, void* stream);
+/* Same coarse solve as se_pmg_coarse_solve, for callers that must not allocate device memory
+ * during the call: code running after its memory pool is fixed (an application or framework
+ * that reserved the device memory up front and owns every later allocation), or a steady-state
+ * loop whose allocations were all made at start-up.  The paper has no counterpart; this is a
+ * library convenience.  It calls no cudaMalloc/cudaFree: the CG vectors, partial sums and
+ * barrier words live in one static device array of the library (about 5.3 MB, held by every
+ * GPU that loads the library until the process exits), so the coarsest level may have at most
+ * 131072 global nodes; larger problems get SE_EINVAL.  The first call on each device looks up
+ * the array's device address with that device current; make that first call before any stream
+ * capture.  The caller passes r and x (coarse L-vectors) as for se_pmg_coarse_solve.  All calls
+ * share the one array, which keeps the last call's contents (the call resets what must start at
+ * zero): calls whose work overlaps on the GPU (other streams, other threads, other handles)
+ * race and must be serialised by the caller.  Synchronises the stream. */
+int se_pmg_coarse_solve_noalloc(se_pmg_t pmg, const double* r, double* x, int* iters,
+                                void* stream);
 
 /* ---------------------------------------------------------------- solve (Sec. 2.2) */
 typedef struct se_solve_opts {

@@ -9,7 +9,9 @@
 // which the kernel records SE_ETIMEOUT and returns.
 #include <cooperative_groups.h>
 
-#include "se_internal.h"
+#include <mutex>
+
+#include "pmg_internal.h"
 
 namespace se {
 
@@ -378,4 +380,69 @@ extern "C" int se_selftest_wait_timeout(double timeout_ms) {
   }
   set_error("device wait did not report a timeout");
   return SE_ECUDA;
+}
+
+// ------------------------------------------------------------------ coarse solve, no allocation
+// Scratch of se_pmg_coarse_solve_noalloc: the five CG vectors (x, r, z, p, q) of at most
+// NOALLOC_MAX_N coarse nodes, the per-block partial sums, and four 32-bit words at the end
+// (barrier count and generation, status, iteration count).  It lives in the library's static
+// device memory: every GPU that loads the library holds it until the process exits.
+namespace se {
+constexpr int64_t NOALLOC_MAX_N = 1 << 17;        // 131072 coarse (p = 1) global nodes
+constexpr int NOALLOC_MAX_BLOCKS = 1024;
+constexpr int64_t NOALLOC_WORDS = 5 * NOALLOC_MAX_N + 4 * NOALLOC_MAX_BLOCKS + 2;
+static __device__ __align__(256) double g_coarse_scratch[NOALLOC_WORDS];
+
+static std::mutex g_noalloc_mu;
+static double* g_noalloc_ptr[64] = {};  // device address of g_coarse_scratch, per device
+
+// Host code must not use g_coarse_scratch itself (that name is a host-side stand-in): the
+// device address is looked up once per device, with that device current.
+static int noalloc_scratch(double** out) {
+  int dev = 0;
+  SE_CUDA(cudaGetDevice(&dev));
+  SE_CHECK(dev >= 0 && dev < 64, SE_EINVAL, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> g(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    SE_CUDA(cudaGetSymbolAddress(&p, g_coarse_scratch));
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return SE_OK;
+}
+}  // namespace se
+
+extern "C" int se_pmg_coarse_solve_noalloc(se_pmg_t P, const double* r, double* x, int* iters,
+                                           void* stream) {
+  SE_CHECK(P && r && x, SE_EINVAL, "se_pmg_coarse_solve_noalloc: null argument");
+  const Level& c = *P->lv[P->nlev - 1];
+  SE_CHECK(c.n_global <= NOALLOC_MAX_N, SE_EINVAL,
+           "se_pmg_coarse_solve_noalloc: coarse level has %lld nodes, above the static limit of %lld",
+           (long long)c.n_global, (long long)NOALLOC_MAX_N);
+  SE_CHECK(P->cw.nblocks <= NOALLOC_MAX_BLOCKS, SE_EINVAL,
+           "se_pmg_coarse_solve_noalloc: %d blocks above the static limit %d", P->cw.nblocks,
+           NOALLOC_MAX_BLOCKS);
+  double* base = nullptr;
+  SE_TRY(noalloc_scratch(&base));
+  cudaStream_t s = as_stream(stream, P->stream);
+  CoarseWork w;
+  w.nblocks = P->cw.nblocks;  // same grid as se_pmg_coarse_solve: same summation order
+  w.x = base;
+  w.r = base + NOALLOC_MAX_N;
+  w.z = base + 2 * NOALLOC_MAX_N;
+  w.p = base + 3 * NOALLOC_MAX_N;
+  w.q = base + 4 * NOALLOC_MAX_N;
+  w.partial = base + 5 * NOALLOC_MAX_N;
+  w.bar = reinterpret_cast<unsigned*>(base + 5 * NOALLOC_MAX_N + 4 * NOALLOC_MAX_BLOCKS);
+  w.status = reinterpret_cast<int*>(w.bar + 2);
+  // coarse_solve zeroes the barrier and status words before its launch; the vectors are fully
+  // written before they are read
+  SE_TRY(coarse_solve<double>(c, w, r, x, P->desc.coarse_tol, P->desc.coarse_maxit, s));
+  int h[2] = {0, 0};
+  SE_CUDA(cudaMemcpyAsync(h, w.status, sizeof(h), cudaMemcpyDeviceToHost, s));
+  SE_CUDA(cudaStreamSynchronize(s));
+  if (iters) *iters = h[1];
+  SE_CHECK(h[0] == 0, SE_ETIMEOUT, "coarse solve: a grid barrier wait ran out");
+  return SE_OK;
 }

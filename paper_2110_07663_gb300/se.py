@@ -94,6 +94,7 @@ _SIGS = {
     "se_pmg_restrict": ([_vp, _ip, _vp, _vp, _vp], C.c_int),
     "se_pmg_prolong": ([_vp, _ip, _vp, _vp, _vp], C.c_int),
     "se_pmg_coarse_solve": ([_vp, _vp, _vp, C.POINTER(C.c_int), _vp], C.c_int),
+    "se_pmg_coarse_solve_noalloc": ([_vp, _vp, _vp, C.POINTER(C.c_int), _vp], C.c_int),
     "se_solve": ([_vp, _vp, _vp, _vp, C.POINTER(se_solve_opts), C.POINTER(se_solve_stats)], C.c_int),
     "se_prof_enable": ([_ip], C.c_int),
     "se_prof_reset": ([], C.c_int),
@@ -261,6 +262,13 @@ se_pmg_prolong = _lvl_call(lib.se_pmg_prolong)
 def se_pmg_coarse_solve(P, r, x, stream=None) -> int:
     it = C.c_int()
     _check(lib.se_pmg_coarse_solve(P, _ptr(r), _ptr(x), C.byref(it), _stream(stream)))
+    return it.value
+
+
+def se_pmg_coarse_solve_noalloc(P, r, x, stream=None) -> int:
+    """Coarse solve whose work space is the library's static device array (no allocation)."""
+    it = C.c_int()
+    _check(lib.se_pmg_coarse_solve_noalloc(P, _ptr(r), _ptr(x), C.byref(it), _stream(stream)))
     return it.value
 
 
