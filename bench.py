@@ -123,6 +123,53 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def alu_peak_tflops(fp32, sm_max_mhz):
+    """Derived ALU peak: 152 SMs x (128 FP32 | 2 FP64) FMA lanes per clock x 2 flop x clock."""
+    return N_SMS * (128 if fp32 else FP64_FMA_PER_CLK_PER_SM) * 2 * sm_max_mhz * 1e6 / 1e12
+
+
+def dram_traffic(kernel, variant):
+    """DRAM bytes per launch from the committed ncu capture summary, if one matches."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
+            tab = json.load(f)
+    except OSError:
+        return None, None
+    e = tab.get(f"{kernel}:{variant}")
+    if not e:
+        return None, None
+    return e["bytes_per_launch_bench_workload"], e["source"]
+
+
+def roofline(kernel, variant, d, pk, pk_kind):
+    """Bound = the roof that takes longer for this kernel's algorithmic bytes and flops."""
+    fp32 = variant >= 32
+    sm_max = pk.get("sm_max_mhz", 2070.0)
+    alu = alu_peak_tflops(fp32, sm_max)
+    hbm = pk["hbm_gbs"]
+    n = max(d["launches"], 1)
+    avg_s = d["ms"] / n * 1e-3
+    t_alu = d["flops"] / (alu * 1e12)
+    t_hbm = d["bytes"] / (hbm * 1e9)
+    traffic, src = dram_traffic(kernel, variant)
+    name = f"{kernel} p={variant % 32} {'f32' if fp32 else 'f64'}"
+    if t_alu >= t_hbm:
+        achieved = d["flops"] / n / avg_s / 1e12
+        return {"bound": "alu", "kernel": name, "achieved": round(achieved, 4), "peak": round(alu, 4),
+                "unit": "TFLOP/s", "frac": round(achieved / alu, 4), "traffic": traffic,
+                "algorithmic_bytes_per_launch": d["bytes"] / n, "flops_per_launch": d["flops"] / n,
+                "avg_launch_ms": round(avg_s * 1e3, 4), "traffic_source": src,
+                "peak_source": f"derived: 152 SMs x {128 if fp32 else 2} {'FP32' if fp32 else 'FP64'} "
+                               f"FMA/clk x 2 flop x {sm_max:.0f} MHz"}
+    achieved = d["bytes"] / n / avg_s / 1e9
+    return {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": hbm,
+            "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic,
+            "algorithmic_bytes_per_launch": d["bytes"] / n, "flops_per_launch": d["flops"] / n,
+            "avg_launch_ms": round(avg_s * 1e3, 4), "traffic_source": src,
+            "peak_source": f"{pk_kind} (MEASURED_PEAKS.json hbm_gbs)" if pk_kind == "measured"
+            else "fallback 6.8 TB/s"}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -182,6 +229,12 @@ def run_gpu(args):
     ms = e0.elapsed_time(e1) / args.steps
     ms_max = max_over_ranks(ms, world)
     prof = {se.KERNEL_NAMES[k]: se.se_prof_query(k) for k in range(se.SE_K_COUNT)}
+    variants = {}
+    for k in range(se.SE_K_COUNT):
+        for v in range(64):
+            q = se.se_prof_query_variant(k, v)
+            if q["launches"]:
+                variants[(se.KERNEL_NAMES[k], v)] = q
     launches = sum(v["launches"] for v in prof.values())
     # ---- end to end through the public API with host buffers (copies inside the timed region)
     b_host = b.cpu().pin_memory()
@@ -203,24 +256,15 @@ def run_gpu(args):
     total_dof = sum_over_ranks(float(n_dof), world)
     value = total_dof / (ms_max * 1e-3) / 1e9
     e2e_value = total_dof / (e2e_ms * 1e-3) / 1e9
-    # ---- roofline of the dominant kernel
+    # ---- roofline of the dominant kernel (kernel class x level order x precision)
     pk, pk_kind = peaks()
-    dom = max(prof, key=lambda k: prof[k]["ms"])
-    d = prof[dom]
-    avg_ms = d["ms"] / max(d["launches"], 1)
-    sm_max = pk.get("sm_max_mhz", 2070.0)
-    fp64_peak = N_SMS * FP64_FMA_PER_CLK_PER_SM * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
-    if args.precond_fp32 and dom in ("fdm", "ax", "gs", "cheby_update", "restrict", "prolong"):
-        bound, peak, unit = "hbm", pk["hbm_gbs"], "GB/s"
-        achieved = d["bytes"] / max(d["launches"], 1) / (avg_ms * 1e-3) / 1e9
-    else:
-        bound, peak, unit = "alu", fp64_peak, "TFLOP/s"
-        # algorithmic flops per launch (the library records them per launch: for the RAS local
-        # solve 6 pbar^4 + pbar^3 + 2(pbar^3 N + pbar^2 N^2 + pbar N^3) per element)
-        achieved = d["flops"] / max(d["launches"], 1) / (avg_ms * 1e-3) / 1e12
-    kernels = {k: {"ms_per_step": round(v["ms"] / args.steps, 3), "launches_per_step": v["launches"] / args.steps,
-                   "share": round(v["ms"] / max(sum(w["ms"] for w in prof.values()), 1e-9), 4)}
-               for k, v in prof.items() if v["launches"]}
+    (dom, dvar), d = max(variants.items(), key=lambda kv: kv[1]["ms"])
+    roof = roofline(dom, dvar, d, pk, pk_kind)
+    tot_ms = max(sum(v["ms"] for v in variants.values()), 1e-9)
+    kernels = {f"{k} p={v % 32} {'f32' if v >= 32 else 'f64'}":
+               {"ms_per_step": round(q["ms"] / args.steps, 3),
+                "launches_per_step": q["launches"] / args.steps, "share": round(q["ms"] / tot_ms, 4)}
+               for (k, v), q in sorted(variants.items(), key=lambda kv: -kv[1]["ms"])}
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": "GDOF/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 3),
@@ -236,10 +280,7 @@ def run_gpu(args):
         "e2e": {"value": round(e2e_value, 4), "unit": "GDOF/s", "h2d_bytes_per_step": int(8 * L),
                 "d2h_bytes_per_step": int(8 * L)},
         "gpu_launches": int(launches),
-        "roofline": {"bound": bound, "kernel": dom, "achieved": round(achieved, 4),
-                     "peak": round(peak, 4), "unit": unit, "frac": round(achieved / peak, 4),
-                     "traffic": None, "peak_source": pk_kind if bound == "hbm" else
-                     "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x sm_max_mhz"},
+        "roofline": roof,
         "kernels": kernels,
         "clocks": clk.summary(),
     }

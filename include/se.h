@@ -212,6 +212,10 @@ int se_prof_reset(void);
  * launches processed (points for AX/GS/KRYLOV, elements for FDM, ...; see each kernel). */
 int se_prof_query(int kind, double* ms_total, int64_t* launches, double* units, double* bytes,
                   double* flops);
+/* The same totals restricted to one variant: the level's polynomial order p (0..31) plus 32 for
+ * FP32 arithmetic (e.g. 7 = FP64 kernels of p = 7 levels, 39 = FP32 kernels of p = 7 levels). */
+int se_prof_query_variant(int kind, int variant, double* ms_total, int64_t* launches,
+                          double* units, double* bytes, double* flops);
 
 /* ---------------------------------------------------------------- self-test of bounded waits */
 /* Runs the library's grid barrier with one more expected arrival than blocks launched, so no

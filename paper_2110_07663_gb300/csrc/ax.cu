@@ -137,7 +137,8 @@ int ax_local(const Level& lv, const T* u, T* y, bool mask_in, cudaStream_t s) {
   SE_CHECK(G != nullptr, SE_EINVAL, "ax_local: geometric factors for this precision missing");
   const int N = lv.N;
   const double pts = (double)lv.L;
-  ProfScope prof(SE_K_AX, s, pts, pts * 8.0 * sizeof(T), pts * (12.0 * N + 15.0));
+  ProfScope prof(SE_K_AX, s, pts, pts * 8.0 * sizeof(T), pts * (12.0 * N + 15.0),
+                 prof_variant<T>(lv.p));
   const uint8_t* pf = mask_in ? lv.pflag : nullptr;
   switch (N) {
     case 2: return launch_ax<2, T>(lv, u, y, G, D, pf, s);
@@ -211,7 +212,7 @@ int gs_apply(const Level& lv, T* u, bool mask, cudaStream_t s) {
   if (n == 0) return SE_OK;
   const double entries = 2.0 * lv.n_pairs + 4.0 * lv.n_quads + 8.0 * lv.n_octs;
   ProfScope prof(SE_K_GS, s, entries, entries * (2.0 * sizeof(T) + 4.0) + lv.n_masked * (4.0 + sizeof(T)),
-                 entries);
+                 entries, prof_variant<T>(lv.p));
   gs_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(lv.n_pairs, lv.n_quads, lv.n_octs, lv.n_masked,
                                                  lv.gs_ids, u, mask);
   SE_LAUNCH_CHECK();

@@ -195,7 +195,8 @@ __global__ void cheb_update_kernel(T* __restrict__ x, T* __restrict__ d, T* __re
 template <class T>
 int cheb_update(T* x, T* d, T* r, const T* sv, const T* dinv, int64_t n, T c1, T c2, bool first,
                 cudaStream_t s) {
-  ProfScope prof(SE_K_CHEBY_UPD, s, (double)n, (first ? 6.0 : 7.0) * n * sizeof(T), 6.0 * n);
+  ProfScope prof(SE_K_CHEBY_UPD, s, (double)n, (first ? 6.0 : 7.0) * n * sizeof(T), 6.0 * n,
+                 prof_variant<T>(0));
   cheb_update_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(x, d, r, sv, dinv, n, c1, c2, first);
   SE_LAUNCH_CHECK();
   return SE_OK;

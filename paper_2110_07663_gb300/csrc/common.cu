@@ -128,7 +128,7 @@ int scratch_alloc(Allocs& a, Scratch* s) {
 
 // ------------------------------------------------------------------ profiling
 struct ProfEntry {
-  int kind;
+  int kind, variant;
   cudaEvent_t a, b;
   double units, bytes, flops;
 };
@@ -140,7 +140,7 @@ static std::mutex g_prof_mu;
 static bool g_prof_on = false;
 static std::vector<ProfEntry> g_prof_pending;
 static std::vector<cudaEvent_t> g_prof_free;
-static ProfTotals g_prof[SE_K_COUNT];
+static ProfTotals g_prof[SE_K_COUNT][PROF_VARIANTS];
 
 static cudaEvent_t prof_event() {
   if (!g_prof_free.empty()) {
@@ -158,7 +158,7 @@ static void prof_drain_locked() {
     cudaEventSynchronize(p.b);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, p.a, p.b);
-    auto& t = g_prof[p.kind];
+    auto& t = g_prof[p.kind][p.variant];
     t.ms += ms;
     t.launches += 1;
     t.units += p.units;
@@ -170,8 +170,10 @@ static void prof_drain_locked() {
   g_prof_pending.clear();
 }
 
-ProfScope::ProfScope(int kind_, cudaStream_t s_, double units_, double bytes_, double flops_)
-    : kind(kind_), s(s_), units(units_), bytes(bytes_), flops(flops_), on(false) {
+ProfScope::ProfScope(int kind_, cudaStream_t s_, double units_, double bytes_, double flops_,
+                     int variant_)
+    : kind(kind_), s(s_), units(units_), bytes(bytes_), flops(flops_),
+      variant(variant_ >= 0 && variant_ < PROF_VARIANTS ? variant_ : 0), on(false) {
   std::lock_guard<std::mutex> g(g_prof_mu);
   if (!g_prof_on) return;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -187,7 +189,7 @@ ProfScope::~ProfScope() {
   if (!on) return;
   std::lock_guard<std::mutex> g(g_prof_mu);
   cudaEventRecord(b, s);
-  g_prof_pending.push_back({kind, a, b, units, bytes, flops});
+  g_prof_pending.push_back({kind, variant, a, b, units, bytes, flops});
   if (g_prof_pending.size() > 4096) prof_drain_locked();
 }
 
@@ -208,16 +210,33 @@ int se_prof_enable(int on) {
 int se_prof_reset(void) {
   std::lock_guard<std::mutex> g(se::g_prof_mu);
   se::prof_drain_locked();
-  for (auto& t : se::g_prof) t = se::ProfTotals();
+  for (auto& row : se::g_prof)
+    for (auto& t : row) t = se::ProfTotals();
   return SE_OK;
 }
 
 int se_prof_query(int kind, double* ms_total, int64_t* launches, double* units, double* bytes,
                   double* flops) {
+  return se_prof_query_variant(kind, -1, ms_total, launches, units, bytes, flops);
+}
+
+int se_prof_query_variant(int kind, int variant, double* ms_total, int64_t* launches,
+                          double* units, double* bytes, double* flops) {
   SE_CHECK(kind >= 0 && kind < SE_K_COUNT, SE_EINVAL, "se_prof_query: bad kind %d", kind);
+  SE_CHECK(variant >= -1 && variant < se::PROF_VARIANTS, SE_EINVAL, "se_prof_query: bad variant %d",
+           variant);
   std::lock_guard<std::mutex> g(se::g_prof_mu);
   se::prof_drain_locked();
-  const auto& t = se::g_prof[kind];
+  se::ProfTotals t;
+  for (int v = 0; v < se::PROF_VARIANTS; ++v) {
+    if (variant >= 0 && v != variant) continue;
+    const auto& x = se::g_prof[kind][v];
+    t.ms += x.ms;
+    t.launches += x.launches;
+    t.units += x.units;
+    t.bytes += x.bytes;
+    t.flops += x.flops;
+  }
   if (ms_total) *ms_total = t.ms;
   if (launches) *launches = t.launches;
   if (units) *units = t.units;

@@ -194,9 +194,12 @@ __device__ __forceinline__ int64_t window_source(const int* __restrict__ nb, int
   return src * (N * N * N) + ia + N * (ib + N * ic);
 }
 
-// One element per block; threads cover the PB*PB lines of each contraction.
+// NE elements per block.  Each contraction phase gives one thread per line of every element
+// (lines numbered element-major), so active threads form a contiguous prefix and only the last
+// warp of a phase can be partly idle; with NE * pbar^2 near a multiple of 32 the FP64 pipe
+// wastes few lane slots (one element per 128-thread block left 28 of 128 lanes idle at p = 7).
 template <int P, typename T, int MODE>
-__global__ void __launch_bounds__(256) fdm_kernel(int64_t E, const int* __restrict__ nbr,
+__global__ void __launch_bounds__(512) fdm_kernel(int64_t E, int NE, const int* __restrict__ nbr,
                                                   const T* __restrict__ in,
                                                   const T* __restrict__ Sg,
                                                   const T* __restrict__ lamg,
@@ -204,45 +207,68 @@ __global__ void __launch_bounds__(256) fdm_kernel(int64_t E, const int* __restri
                                                   const uint8_t* __restrict__ pflag,
                                                   T* __restrict__ out) {
   constexpr int N = P + 1, PB = P + 3, PB2 = PB * PB, PB3 = PB * PB * PB;
+  constexpr int PER = 2 * PB3 + 3 * PB2 + 3 * PB;  // shared values per element
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* b0 = reinterpret_cast<T*>(smem_raw);
-  T* b1 = b0 + PB3;
-  T* sS = b1 + PB3;        // [3][PB][PB]
-  T* sl = sS + 3 * PB2;    // [3][PB]
-  __shared__ int snb[27];
-  const int64_t e = blockIdx.x;
-  const int tid = threadIdx.x;
+  T* sbase = reinterpret_cast<T*>(smem_raw);
+  int* snb = reinterpret_cast<int*>(sbase + (size_t)NE * PER);  // [NE][27]
+  const int64_t e0 = (int64_t)blockIdx.x * NE;
+  const int ne = (int)((E - e0) < NE ? (E - e0) : NE);             // elements in this block
+  const int tid = threadIdx.x, nt = blockDim.x;
+  auto B0 = [&](int le) { return sbase + (size_t)le * PER; };
+  auto B1 = [&](int le) { return sbase + (size_t)le * PER + PB3; };
+  auto SS = [&](int le) { return sbase + (size_t)le * PER + 2 * PB3; };
+  auto SL = [&](int le) { return sbase + (size_t)le * PER + 2 * PB3 + 3 * PB2; };
   if constexpr (MODE != FDM_GATHER) {
-    for (int q = tid; q < 3 * PB2; q += blockDim.x) sS[q] = Sg[e * 3 * PB2 + q];
-    for (int q = tid; q < 3 * PB; q += blockDim.x) sl[q] = lamg[e * 3 * PB + q];
+    for (int q = tid; q < ne * 3 * PB2; q += nt) {
+      const int le = q / (3 * PB2), r = q - le * 3 * PB2;
+      SS(le)[r] = Sg[(e0 + le) * 3 * PB2 + r];
+    }
+    for (int q = tid; q < ne * 3 * PB; q += nt) {
+      const int le = q / (3 * PB), r = q - le * 3 * PB;
+      SL(le)[r] = lamg[(e0 + le) * 3 * PB + r];
+    }
   }
-  if (tid < 27) snb[tid] = nbr[27 * e + tid];
+  for (int q = tid; q < ne * 27; q += nt) snb[q] = nbr[27 * e0 + q];
   __syncthreads();
-  // ---- gather the extended window
+  // ---- gather the extended window: one thread per (element, a, b), loop over c
   if constexpr (MODE == FDM_EXT_IN) {
-    for (int q = tid; q < PB3; q += blockDim.x) b0[q] = in[e * PB3 + q];
+    for (int q = tid; q < ne * PB3; q += nt) {
+      const int le = q / PB3;
+      B0(le)[q - le * PB3] = in[e0 * PB3 + q];
+    }
   } else {
-    if (tid < PB2) {
-      const int a = tid % PB, b = tid / PB;
+    if (tid < ne * PB2) {
+      const int le = tid / PB2, ql = tid - le * PB2;
+      const int a = ql % PB, b = ql / PB;
+      T* b0 = B0(le);
       for (int c = 0; c < PB; ++c) {
-        const int64_t src = window_source<P>(snb, e, a, b, c);
+        const int64_t src = window_source<P>(snb + 27 * le, e0 + le, a, b, c);
         b0[a + PB * (b + PB * c)] = src >= 0 ? in[src] : T(0);
       }
     }
   }
   if constexpr (MODE == FDM_GATHER) {
     __syncthreads();
-    for (int q = tid; q < PB3; q += blockDim.x) out[e * PB3 + q] = b0[q];
+    for (int q = tid; q < ne * PB3; q += nt) {
+      const int le = q / PB3;
+      out[e0 * PB3 + q] = B0(le)[q - le * PB3];
+    }
     return;
   } else {
     __syncthreads();
-    const T* Sx = sS;
-    const T* Sy = sS + PB2;
-    const T* Sz = sS + 2 * PB2;
     T v[PB];
-    // ---- forward: S_x^T along a (thread = line (b, c))
-    if (tid < PB2) {
-      const int b = tid % PB, c = tid / PB;
+    const bool full_line = tid < ne * PB2;
+    const int le = full_line ? tid / PB2 : 0;
+    const int ql = tid - le * PB2;
+    const T* Sx = SS(le);
+    const T* Sy = Sx + PB2;
+    const T* Sz = Sx + 2 * PB2;
+    const T* sl = SL(le);
+    T* b0 = B0(le);
+    T* b1 = B1(le);
+    // ---- forward: S_x^T along a (line (b, c))
+    if (full_line) {
+      const int b = ql % PB, c = ql / PB;
 #pragma unroll
       for (int a = 0; a < PB; ++a) v[a] = b0[a + PB * (b + PB * c)];
 #pragma unroll
@@ -254,9 +280,9 @@ __global__ void __launch_bounds__(256) fdm_kernel(int64_t E, const int* __restri
       }
     }
     __syncthreads();
-    // ---- forward: S_y^T along b (thread = line (alpha, c))
-    if (tid < PB2) {
-      const int al = tid % PB, c = tid / PB;
+    // ---- forward: S_y^T along b (line (alpha, c))
+    if (full_line) {
+      const int al = ql % PB, c = ql / PB;
 #pragma unroll
       for (int b = 0; b < PB; ++b) v[b] = b1[al + PB * (b + PB * c)];
 #pragma unroll
@@ -268,9 +294,9 @@ __global__ void __launch_bounds__(256) fdm_kernel(int64_t E, const int* __restri
       }
     }
     __syncthreads();
-    // ---- forward: S_z^T along c, then D^-1 (thread = line (alpha, beta))
-    if (tid < PB2) {
-      const int al = tid % PB, be = tid / PB;
+    // ---- forward: S_z^T along c, then D^-1 (line (alpha, beta))
+    if (full_line) {
+      const int al = ql % PB, be = ql / PB;
 #pragma unroll
       for (int c = 0; c < PB; ++c) v[c] = b0[al + PB * (be + PB * c)];
       const T lxy = sl[al] + sl[PB + be];
@@ -281,7 +307,7 @@ __global__ void __launch_bounds__(256) fdm_kernel(int64_t E, const int* __restri
         for (int c = 0; c < PB; ++c) acc += Sz[c * PB + ga] * v[c];
         const int q = al + PB * (be + PB * ga);
         T dv;
-        if constexpr (sizeof(T) == 8) dv = dinvg[e * PB3 + q];
+        if constexpr (sizeof(T) == 8) dv = dinvg[(e0 + le) * PB3 + q];
         else dv = T(1) / (lxy + sl[2 * PB + ga]);
         b1[q] = acc * dv;
       }
@@ -290,8 +316,8 @@ __global__ void __launch_bounds__(256) fdm_kernel(int64_t E, const int* __restri
     // ---- backward: S_z along gamma (own outputs c' = 1..N for RAS, all PB otherwise)
     constexpr int C0 = MODE == FDM_RAS ? 1 : 0;
     constexpr int NC = MODE == FDM_RAS ? N : PB;
-    if (tid < PB2) {
-      const int al = tid % PB, be = tid / PB;
+    if (full_line) {
+      const int al = ql % PB, be = ql / PB;
 #pragma unroll
       for (int ga = 0; ga < PB; ++ga) v[ga] = b1[al + PB * (be + PB * ga)];
 #pragma unroll
@@ -304,32 +330,40 @@ __global__ void __launch_bounds__(256) fdm_kernel(int64_t E, const int* __restri
       }
     }
     __syncthreads();
-    // ---- backward: S_y along beta (thread = line (alpha, c'))
-    if (tid < PB * NC) {
-      const int al = tid % PB, c = C0 + tid / PB;
+    // ---- backward: S_y along beta (line (alpha, c'), PB*NC lines per element)
+    if (tid < ne * PB * NC) {
+      const int le2 = tid / (PB * NC), q2 = tid - le2 * PB * NC;
+      const int al = q2 % PB, c = C0 + q2 / PB;
+      const T* Sy2 = SS(le2) + PB2;
+      T* b0e = B0(le2);
+      T* b1e = B1(le2);
 #pragma unroll
-      for (int be = 0; be < PB; ++be) v[be] = b0[al + PB * (be + PB * c)];
+      for (int be = 0; be < PB; ++be) v[be] = b0e[al + PB * (be + PB * c)];
 #pragma unroll
       for (int bb = 0; bb < NC; ++bb) {
         const int b = C0 + bb;
         T acc = T(0);
 #pragma unroll
-        for (int be = 0; be < PB; ++be) acc += Sy[b * PB + be] * v[be];
-        b1[al + PB * (b + PB * c)] = acc;
+        for (int be = 0; be < PB; ++be) acc += Sy2[b * PB + be] * v[be];
+        b1e[al + PB * (b + PB * c)] = acc;
       }
     }
     __syncthreads();
-    // ---- backward: S_x along alpha (thread = line (b', c')), write out
-    if (tid < NC * NC) {
-      const int b = C0 + tid % NC, c = C0 + tid / NC;
+    // ---- backward: S_x along alpha (line (b', c'), NC*NC lines per element), write out
+    if (tid < ne * NC * NC) {
+      const int le3 = tid / (NC * NC), q3 = tid - le3 * NC * NC;
+      const int b = C0 + q3 % NC, c = C0 + q3 / NC;
+      const T* Sx3 = SS(le3);
+      const T* b1e = B1(le3);
+      const int64_t e = e0 + le3;
 #pragma unroll
-      for (int al = 0; al < PB; ++al) v[al] = b1[al + PB * (b + PB * c)];
+      for (int al = 0; al < PB; ++al) v[al] = b1e[al + PB * (b + PB * c)];
 #pragma unroll
       for (int aa = 0; aa < NC; ++aa) {
         const int a = C0 + aa;
         T acc = T(0);
 #pragma unroll
-        for (int al = 0; al < PB; ++al) acc += Sx[a * PB + al] * v[al];
+        for (int al = 0; al < PB; ++al) acc += Sx3[a * PB + al] * v[al];
         if constexpr (MODE == FDM_RAS) {
           const int64_t li = e * (N * N * N) + (a - 1) + N * ((b - 1) + N * (c - 1));
           const int mlog = __ffs(pflag[li] & 0x0F) - 1;   // 1/multiplicity: exact power of 2
@@ -343,20 +377,29 @@ __global__ void __launch_bounds__(256) fdm_kernel(int64_t E, const int* __restri
   }
 }
 
+// Elements per block: about 400 lines per phase, at most 16 elements.
+static int fdm_elems_per_block(int PB) {
+  int ne = 400 / (PB * PB);
+  return ne < 1 ? 1 : (ne > 16 ? 16 : ne);
+}
+
 template <int P, typename T, int MODE>
 static int launch_fdm(const Level& lv, const T* in, const T* S, const T* lam, T* out,
                       cudaStream_t s) {
   constexpr int PB = P + 3;
-  const int threads = ((PB * PB + 31) / 32) * 32;
-  const size_t smem = (2 * PB * PB * PB + 3 * PB * PB + 3 * PB) * sizeof(T);
+  const int NE = fdm_elems_per_block(PB);
+  const int threads = ((NE * PB * PB + 31) / 32) * 32;
+  const size_t smem = (size_t)NE * (2 * PB * PB * PB + 3 * PB * PB + 3 * PB) * sizeof(T) +
+                      (size_t)NE * 27 * sizeof(int);
   static bool attr = false;
   if (!attr) {
     SE_CUDA(cudaFuncSetAttribute(fdm_kernel<P, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 100 * 1024));
+                                 200 * 1024));
     attr = true;
   }
-  fdm_kernel<P, T, MODE><<<(unsigned)lv.E, threads, smem, s>>>(lv.E, lv.nbr, in, S, lam,
-                                                                lv.fdm_dinv64, lv.pflag, out);
+  const unsigned blocks = (unsigned)((lv.E + NE - 1) / NE);
+  fdm_kernel<P, T, MODE><<<blocks, threads, smem, s>>>(lv.E, NE, lv.nbr, in, S, lam,
+                                                        lv.fdm_dinv64, lv.pflag, out);
   SE_LAUNCH_CHECK();
   return SE_OK;
 }
@@ -376,7 +419,7 @@ static int dispatch_fdm(const Level& lv, const T* in, T* out, cudaStream_t s) {
   const double PB = lv.p + 3.0, N = lv.N;
   const double fl = 2.0 * (3.0 * PB * PB * PB * PB + PB * PB * PB * N + PB * PB * N * N + PB * N * N * N) + PB * PB * PB;
   const double by = (PB * PB * PB + N * N * N + 3 * PB * PB + 3 * PB + (sizeof(T) == 8 ? PB * PB * PB : 0)) * sizeof(T);
-  ProfScope prof(SE_K_FDM, s, (double)lv.E, by * lv.E, fl * lv.E);
+  ProfScope prof(SE_K_FDM, s, (double)lv.E, by * lv.E, fl * lv.E, prof_variant<T>(lv.p));
   switch (lv.p) {
 #define SE_FDM_CASE(PP) \
   case PP: return launch_fdm<PP, T, MODE>(lv, in, S, lam, out, s);

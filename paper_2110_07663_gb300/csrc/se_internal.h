@@ -243,13 +243,20 @@ int coarse_solve(const Level& lv, CoarseWork& w, const T* r_l, T* x_l, double to
                  cudaStream_t s);
 
 // ------------------------------------------------------------------ profiling (common.cu)
+// Profiling variant of a launch: polynomial order p (0..31) plus 32 for FP32 arithmetic.
+constexpr int PROF_VARIANTS = 64;
+template <class T>
+inline int prof_variant(int p) {
+  return (p & 31) + (sizeof(T) == 4 ? 32 : 0);
+}
 struct ProfScope {
   int kind;
   cudaStream_t s;
   double units, bytes, flops;
+  int variant;
   bool on;
   cudaEvent_t a = nullptr, b = nullptr;
-  ProfScope(int kind, cudaStream_t s, double units, double bytes, double flops);
+  ProfScope(int kind, cudaStream_t s, double units, double bytes, double flops, int variant = 0);
   ~ProfScope();
 };
 

@@ -67,7 +67,8 @@ int restrict_apply(const Level& f, const Level& c, const T* J, const T* rf, T* r
   {
     ProfScope prof(SE_K_RESTRICT, s, (double)f.E,
                    f.E * (Nf * Nf * Nf * (sizeof(T) + 1.0) + Nc * Nc * Nc * sizeof(T)),
-                   2.0 * f.E * (Nf * Nf * Nf * Nc + Nf * Nf * Nc * Nc + Nf * Nc * Nc * Nc));
+                   2.0 * f.E * (Nf * Nf * Nf * Nc + Nf * Nf * Nc * Nc + Nf * Nc * Nc * Nc),
+                   prof_variant<T>(f.p));
     transfer_kernel<T, true><<<(unsigned)f.E, 128, 0, s>>>(f.N, c.N, J, rf, f.pflag, rc, false);
     SE_LAUNCH_CHECK();
   }
@@ -80,7 +81,8 @@ int prolong_apply(const Level& f, const Level& c, const T* J, const T* ec, T* ef
   const double Nf = f.N, Nc = c.N;
   ProfScope prof(SE_K_PROLONG, s, (double)f.E,
                  f.E * (Nf * Nf * Nf * (accumulate ? 2.0 : 1.0) + Nc * Nc * Nc) * sizeof(T),
-                 2.0 * f.E * (Nc * Nc * Nc * Nf + Nc * Nc * Nf * Nf + Nc * Nf * Nf * Nf));
+                 2.0 * f.E * (Nc * Nc * Nc * Nf + Nc * Nc * Nf * Nf + Nc * Nf * Nf * Nf),
+                 prof_variant<T>(f.p));
   transfer_kernel<T, false><<<(unsigned)f.E, 128, 0, s>>>(f.N, c.N, J, ec, nullptr, ef, accumulate);
   SE_LAUNCH_CHECK();
   return SE_OK;

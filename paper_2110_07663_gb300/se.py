@@ -99,6 +99,7 @@ _SIGS = {
     "se_prof_enable": ([_ip], C.c_int),
     "se_prof_reset": ([], C.c_int),
     "se_prof_query": ([_ip, _dp, C.POINTER(C.c_int64), _dp, _dp, _dp], C.c_int),
+    "se_prof_query_variant": ([_ip, _ip, _dp, C.POINTER(C.c_int64), _dp, _dp, _dp], C.c_int),
     "se_selftest_wait_timeout": ([C.c_double], C.c_int),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -296,6 +297,13 @@ def se_prof_reset():
 def se_prof_query(kind):
     ms, n, units, by, fl = C.c_double(), C.c_int64(), C.c_double(), C.c_double(), C.c_double()
     _check(lib.se_prof_query(kind, C.byref(ms), C.byref(n), C.byref(units), C.byref(by), C.byref(fl)))
+    return dict(ms=ms.value, launches=n.value, units=units.value, bytes=by.value, flops=fl.value)
+
+
+def se_prof_query_variant(kind, variant):
+    ms, n, units, by, fl = C.c_double(), C.c_int64(), C.c_double(), C.c_double(), C.c_double()
+    _check(lib.se_prof_query_variant(kind, variant, C.byref(ms), C.byref(n), C.byref(units),
+                                     C.byref(by), C.byref(fl)))
     return dict(ms=ms.value, launches=n.value, units=units.value, bytes=by.value, flops=fl.value)
 
 
