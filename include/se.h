@@ -182,7 +182,10 @@ typedef struct se_solve_opts {
   int restart;       /* FGMRES restart length m (paper: 20) */
   double tol;        /* stop when ||r_k||_2 / ||r_0||_2 <= tol (unique-node 2-norm) */
   int maxit;
-  int graph_capture; /* 1: replay each preconditioner application as a captured CUDA graph */
+  int graph_capture; /* 1 (SE_FPCG only): the whole solve runs as one CUDA graph launch whose
+                        iteration loop is a device-side WHILE node (no host round trip per
+                        iteration); the graph is cached per mesh for the same pmg, b, x, tol,
+                        maxit and rebuilt when one of them changes */
   void* stream;      /* NULL: the mesh's stream */
 } se_solve_opts;
 
@@ -199,6 +202,29 @@ typedef struct se_solve_stats {
  * Returns SE_ENOTCONV (stats filled) if maxit is reached.  Synchronises. */
 int se_solve(se_mesh_t m, se_pmg_t pmg, const double* b, double* x, const se_solve_opts* opts,
              se_solve_stats* stats);
+
+/* ---------------------------------------------------------------- batched solves */
+/* Many independent problems solved together (flexible PCG, device-driven): every problem's
+ * whole solve loop becomes one branch of a single CUDA graph, so one graph launch runs all of
+ * them concurrently on the GPU; problems that converge early simply leave their loop.  Each
+ * problem needs its own mesh handle (its work vectors live there); pmg may be NULL (Jacobi).
+ * b and x are caller-owned device vectors of that mesh; x holds the initial guess at launch. */
+typedef struct se_problem {
+  se_mesh_t mesh;
+  se_pmg_t pmg;
+  const double* b;
+  double* x;
+} se_problem;
+typedef struct se_batch_s* se_batch_t;
+/* Builds and instantiates the batch graph (the inputs are captured by pointer). */
+int se_batch_create(int n, const se_problem* probs, const se_solve_opts* opts, se_batch_t* out);
+/* One graph launch on `stream` (NULL: legacy default stream); returns without waiting. */
+int se_batch_run(se_batch_t batch, void* stream);
+/* Waits for the stream and fills n statistics; returns SE_ENOTCONV if any problem missed tol. */
+int se_batch_stats(se_batch_t batch, void* stream, se_solve_stats* out);
+int se_batch_destroy(se_batch_t batch);
+/* create + run + stats + destroy; ms_total of every entry is the wall time of the whole batch. */
+int se_batch_solve(int n, const se_problem* probs, const se_solve_opts* opts, se_solve_stats* out);
 
 /* ---------------------------------------------------------------- profiling */
 /* Kernel classes timed with CUDA events on their launch stream while profiling is enabled. */

@@ -392,3 +392,34 @@ extern "C" int se_dot(se_mesh_t m, const double* a, const double* b, double* out
   SE_CUDA(cudaStreamSynchronize(s));
   return SE_OK;
 }
+
+namespace se {
+// x += alpha p; r_old = r; r = r - alpha w; rr = (r, r): the in-place variant used by the
+// device-driven (graph) solver, whose captured pointers cannot be swapped between iterations.
+struct UpdateXR2Op {
+  static constexpr int K = 1;
+  double* x;
+  const double* p;
+  double* r;
+  const double* w;
+  double* r_old;
+  const uint8_t* pf;
+  double* scal;
+  __device__ void point(int64_t i, double (&acc)[1]) const {
+    const double alpha = scal[SC_ALPHA];
+    x[i] = fma(alpha, p[i], x[i]);
+    const double ro = r[i];
+    r_old[i] = ro;
+    const double rv = fma(-alpha, w[i], ro);
+    r[i] = rv;
+    acc[0] = fma(scale_pow2(rv, mult_log2(pf[i])), rv, acc[0]);
+  }
+  __device__ void finalize(const double* s) const { scal[SC_RR] = s[0]; }
+};
+
+int fpcg_update_inplace(const Level& lv, double* x, const double* p, double* r, const double* w,
+                        double* r_old, Scratch& sc, cudaStream_t s) {
+  return run_fused(UpdateXR2Op{x, p, r, w, r_old, lv.pflag, sc.scal}, lv.L, sc, s, SE_K_KRYLOV,
+                   lv.L * 57.0, lv.L * 6.0);
+}
+}  // namespace se

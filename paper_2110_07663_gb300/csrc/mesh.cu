@@ -465,6 +465,9 @@ int se_mesh_create(const se_mesh_desc* desc, se_mesh_t* out) {
 int se_mesh_destroy(se_mesh_t m) {
   if (!m) return SE_OK;
   cudaStreamSynchronize(m->stream);
+  if (m->gexec) cudaGraphExecDestroy(m->gexec);
+  if (m->ev0) cudaEventDestroy(m->ev0);
+  if (m->ev1) cudaEventDestroy(m->ev1);
   m->allocs.release();
   if (m->scratch.hscal) cudaFreeHost(m->scratch.hscal);
   cudaStreamDestroy(m->stream);

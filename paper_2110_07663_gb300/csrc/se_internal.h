@@ -163,6 +163,12 @@ struct se_mesh_s {
   double** gm_zs = nullptr;      // device array of the m Z pointers
   double* gm_y = nullptr;        // device [m]
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // device-driven (graph) solve of this mesh: statistics on the device and the cached graph
+  void* gstats = nullptr;        // se::DevStats
+  cudaGraphExec_t gexec = nullptr;
+  const void* gkey[4] = {nullptr, nullptr, nullptr, nullptr};  // pmg, b, x, opts hash
+  double gtol = 0.0;
+  int gmaxit = 0;
 };
 
 namespace se {
@@ -206,6 +212,8 @@ int fpcg_update(const Level& lv, double* x, const double* p, const double* r, co
 int fpcg_beta(const Level& lv, const double* z, const double* r2, const double* r, Scratch& sc,
               cudaStream_t s);
 int fpcg_pupdate(const Level& lv, double* p, const double* z, Scratch& sc, cudaStream_t s);
+int fpcg_update_inplace(const Level& lv, double* x, const double* p, double* r, const double* w,
+                        double* r_old, Scratch& sc, cudaStream_t s);
 int dot_to_slot(const Level& lv, const double* a, const double* b, Scratch& sc, int slot,
                 cudaStream_t s);
 int axpy_dot(const Level& lv, double* w, const double* v, const double* vnext, Scratch& sc,

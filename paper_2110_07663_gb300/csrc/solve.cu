@@ -4,6 +4,8 @@
 #include <cmath>
 #include <vector>
 
+#include <cuda_runtime.h>
+
 #include "pmg_internal.h"
 
 namespace se {
@@ -161,6 +163,9 @@ static int fgmres(se_mesh_s* m, se_pmg_s* P, const double* b, double* x, const s
   return SE_ENOTCONV;
 }
 
+int graph_solve(se_mesh_s* m, se_pmg_s* P, const double* b, double* x, const se_solve_opts& o,
+                cudaStream_t s, se_solve_stats* st);
+
 }  // namespace se
 
 using namespace se;
@@ -177,7 +182,9 @@ extern "C" int se_solve(se_mesh_t m, se_pmg_t P, const double* b, double* x,
   SE_TRY(ensure_solve_work(m, o.restart, o.method == SE_FGMRES));
   se_solve_stats st{};
   SE_CUDA(cudaEventRecord(m->ev0, s));
-  int rc = o.method == SE_FPCG ? fpcg(m, P, b, x, o, s, &st) : fgmres(m, P, b, x, o, s, &st);
+  int rc;
+  if (o.graph_capture && o.method == SE_FPCG) rc = graph_solve(m, P, b, x, o, s, &st);
+  else rc = o.method == SE_FPCG ? fpcg(m, P, b, x, o, s, &st) : fgmres(m, P, b, x, o, s, &st);
   cudaEventRecord(m->ev1, s);
   cudaEventSynchronize(m->ev1);
   float ms = 0.f;
@@ -187,3 +194,276 @@ extern "C" int se_solve(se_mesh_t m, se_pmg_t P, const double* b, double* x,
   if (stats) *stats = st;
   return rc;
 }
+
+// =============================================================================================
+// Device-driven flexible PCG as one CUDA graph: the iteration is a WHILE node whose condition a
+// one-thread kernel sets from the device-resident residual norm; after convergence an IF node
+// skips the preconditioner.  No host round trip per iteration: one graph launch per solve.
+// Several solves become parallel branches of one graph (se_batch_*).
+// =============================================================================================
+namespace se {
+
+struct DevStats {
+  int iterations;
+  int status;
+  double rel;
+};
+
+__global__ void fpcg_graph_init_kernel(const double* __restrict__ scal, DevStats* st, int maxit,
+                                       cudaGraphConditionalHandle hw) {
+  const double r0 = scal[SC_R0];
+  st->iterations = 0;
+  st->status = 0;
+  st->rel = r0 > 0.0 ? 1.0 : 0.0;
+  cudaGraphSetConditional(hw, (r0 > 0.0 && maxit > 0) ? 1u : 0u);
+}
+
+__global__ void fpcg_graph_check_kernel(const double* __restrict__ scal, DevStats* st, double tol,
+                                        int maxit, cudaGraphConditionalHandle hw,
+                                        cudaGraphConditionalHandle hif) {
+  const int it = st->iterations + 1;
+  st->iterations = it;
+  const double rel = sqrt(scal[SC_RR] / scal[SC_R0]);
+  st->rel = rel;
+  const bool go = rel > tol && it < maxit;  // a NaN residual stops the loop too
+  cudaGraphSetConditional(hw, go ? 1u : 0u);
+  cudaGraphSetConditional(hif, go ? 1u : 0u);
+}
+
+// Adds a conditional node at the capture frontier of `cs` and moves the frontier after it.
+static int add_conditional(cudaStream_t cs, cudaGraphConditionalHandle h,
+                           cudaGraphConditionalNodeType type, cudaGraph_t* body) {
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  SE_CUDA(cudaStreamGetCaptureInfo(cs, &st, nullptr, &g, &deps, nullptr, &ndeps));
+  SE_CHECK(st == cudaStreamCaptureStatusActive, SE_ECUDA, "graph build: stream is not capturing");
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = type;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  SE_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp));
+  *body = cp.conditional.phGraph_out[0];
+  SE_CUDA(cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return SE_OK;
+}
+
+// Appends one whole FPCG solve (x0 = the content of x at launch) to graph G, independent of the
+// rest of G.  All buffers must already exist: nothing is allocated while capturing.
+static int append_fpcg_solve(cudaGraph_t G, cudaStream_t cs, se_mesh_s* m, se_pmg_s* P,
+                             const double* b, double* x, double tol, int maxit) {
+  const Level& lv = m->fine;
+  Scratch& sc = m->scratch;
+  double *r = m->sr, *r_old = m->sr2, *z = m->sz, *p = m->sp, *w = m->sw;
+  DevStats* st = static_cast<DevStats*>(m->gstats);
+  cudaGraphConditionalHandle hw, hif;
+  SE_CUDA(cudaGraphConditionalHandleCreate(&hw, G, 0, 0));
+  // ---- initialisation
+  SE_CUDA(cudaStreamBeginCaptureToGraph(cs, G, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  int rc = SE_OK;
+  cudaGraph_t wbody = nullptr, ifbody = nullptr;
+  do {
+    if ((rc = ax_apply<double>(lv, x, w, cs)) != SE_OK) break;
+    if ((rc = axpby<double>(1.0, b, -1.0, w, r, lv.L, cs)) != SE_OK) break;
+    if ((rc = precondition(m, P, r, z, cs)) != SE_OK) break;
+    if ((rc = fpcg_init(lv, r, z, sc, cs)) != SE_OK) break;
+    if (cudaMemcpyAsync(p, z, lv.L * sizeof(double), cudaMemcpyDeviceToDevice, cs) != cudaSuccess) {
+      set_error("graph build: copy capture failed");
+      rc = SE_ECUDA;
+      break;
+    }
+    fpcg_graph_init_kernel<<<1, 1, 0, cs>>>(sc.scal, st, maxit, hw);
+    rc = add_conditional(cs, hw, cudaGraphCondTypeWhile, &wbody);
+  } while (0);
+  cudaGraph_t out = nullptr;
+  cudaError_t ec = cudaStreamEndCapture(cs, &out);
+  if (rc != SE_OK) return rc;
+  SE_CHECK(ec == cudaSuccess, SE_ECUDA, "graph build (init): %s", cudaGetErrorString(ec));
+  // ---- WHILE body: w = A p, alpha, x/r update, convergence test
+  SE_CUDA(cudaGraphConditionalHandleCreate(&hif, G, 0, 0));
+  SE_CUDA(cudaStreamBeginCaptureToGraph(cs, wbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  do {
+    if ((rc = ax_apply<double>(lv, p, w, cs)) != SE_OK) break;
+    if ((rc = fpcg_alpha(lv, p, w, sc, cs)) != SE_OK) break;
+    if ((rc = fpcg_update_inplace(lv, x, p, r, w, r_old, sc, cs)) != SE_OK) break;
+    fpcg_graph_check_kernel<<<1, 1, 0, cs>>>(sc.scal, st, tol, maxit, hw, hif);
+    rc = add_conditional(cs, hif, cudaGraphCondTypeIf, &ifbody);
+  } while (0);
+  ec = cudaStreamEndCapture(cs, &out);
+  if (rc != SE_OK) return rc;
+  SE_CHECK(ec == cudaSuccess, SE_ECUDA, "graph build (loop): %s", cudaGetErrorString(ec));
+  // ---- IF body: z = M r, beta, p = z + beta p
+  SE_CUDA(cudaStreamBeginCaptureToGraph(cs, ifbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  do {
+    if ((rc = precondition(m, P, r, z, cs)) != SE_OK) break;
+    if ((rc = fpcg_beta(lv, z, r, r_old, sc, cs)) != SE_OK) break;
+    rc = fpcg_pupdate(lv, p, z, sc, cs);
+  } while (0);
+  ec = cudaStreamEndCapture(cs, &out);
+  if (rc != SE_OK) return rc;
+  SE_CHECK(ec == cudaSuccess, SE_ECUDA, "graph build (preconditioner): %s", cudaGetErrorString(ec));
+  return SE_OK;
+}
+
+static int prepare_graph_solve(se_mesh_s* m) {
+  SE_TRY(ensure_solve_work(m, 0, false));
+  if (!m->gstats) SE_TRY(dmalloc_bytes(m->allocs, &m->gstats, sizeof(DevStats)));
+  return SE_OK;
+}
+
+static int read_graph_stats(se_mesh_s* m, cudaStream_t s, se_solve_stats* out, double tol, int maxit) {
+  DevStats h{};
+  SE_CUDA(cudaMemcpyAsync(&h, m->gstats, sizeof(h), cudaMemcpyDeviceToHost, s));
+  SE_CUDA(cudaStreamSynchronize(s));
+  out->iterations = h.iterations;
+  out->rel_residual = h.rel;
+  if (std::isnan(h.rel)) {
+    set_error("se_solve: residual became NaN");
+    return SE_ENOTCONV;
+  }
+  if (h.rel > tol) {
+    set_error("se_solve: no convergence in %d iterations (rel. residual %.3e)", maxit, h.rel);
+    return SE_ENOTCONV;
+  }
+  return SE_OK;
+}
+
+// se_solve with graph_capture: build (or reuse) this mesh's solve graph and launch it once.
+int graph_solve(se_mesh_s* m, se_pmg_s* P, const double* b, double* x, const se_solve_opts& o,
+                cudaStream_t s, se_solve_stats* st) {
+  SE_TRY(prepare_graph_solve(m));
+  const bool same = m->gexec && m->gkey[0] == P && m->gkey[1] == b && m->gkey[2] == x &&
+                    m->gtol == o.tol && m->gmaxit == o.maxit;
+  if (!same) {
+    if (m->gexec) cudaGraphExecDestroy(m->gexec);
+    m->gexec = nullptr;
+    cudaGraph_t G;
+    SE_CUDA(cudaGraphCreate(&G, 0));
+    cudaStream_t cs;
+    SE_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    int rc = append_fpcg_solve(G, cs, m, P, b, x, o.tol, o.maxit);
+    cudaStreamDestroy(cs);
+    if (rc == SE_OK) {
+      cudaError_t e = cudaGraphInstantiate(&m->gexec, G, 0);
+      if (e != cudaSuccess) {
+        set_error("cudaGraphInstantiate: %s", cudaGetErrorString(e));
+        rc = SE_ECUDA;
+        m->gexec = nullptr;
+      }
+    }
+    cudaGraphDestroy(G);
+    if (rc != SE_OK) return rc;
+    m->gkey[0] = P;
+    m->gkey[1] = b;
+    m->gkey[2] = x;
+    m->gtol = o.tol;
+    m->gmaxit = o.maxit;
+  }
+  SE_CUDA(cudaGraphLaunch(m->gexec, s));
+  return read_graph_stats(m, s, st, o.tol, o.maxit);
+}
+
+}  // namespace se
+
+struct se_batch_s {
+  std::vector<se_problem> probs;
+  se_solve_opts opts;
+  cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+int se_batch_create(int n, const se_problem* probs, const se_solve_opts* opts, se_batch_t* out) {
+  SE_CHECK(n >= 1 && probs && opts && out, SE_EINVAL, "se_batch_create: bad argument");
+  SE_CHECK(opts->method == SE_FPCG, SE_EINVAL, "se_batch_create: batched solves use SE_FPCG");
+  SE_CHECK(opts->tol > 0 && opts->maxit >= 1, SE_EINVAL, "se_batch_create: bad tolerance or maxit");
+  for (int i = 0; i < n; ++i) {
+    SE_CHECK(probs[i].mesh && probs[i].b && probs[i].x, SE_EINVAL, "se_batch_create: problem %d incomplete", i);
+    SE_CHECK(!probs[i].pmg || probs[i].pmg->mesh == probs[i].mesh, SE_EINVAL,
+             "se_batch_create: problem %d: preconditioner of another mesh", i);
+    for (int j = 0; j < i; ++j)
+      SE_CHECK(probs[j].mesh != probs[i].mesh, SE_EINVAL,
+               "se_batch_create: problems %d and %d share a mesh (its work space)", j, i);
+    SE_TRY(prepare_graph_solve(probs[i].mesh));
+  }
+  auto* B = new se_batch_s();
+  B->probs.assign(probs, probs + n);
+  B->opts = *opts;
+  cudaGraph_t G;
+  if (cudaGraphCreate(&G, 0) != cudaSuccess) {
+    delete B;
+    set_error("cudaGraphCreate failed");
+    return SE_ECUDA;
+  }
+  cudaStream_t cs;
+  cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  int rc = SE_OK;
+  for (int i = 0; i < n && rc == SE_OK; ++i)
+    rc = append_fpcg_solve(G, cs, probs[i].mesh, probs[i].pmg, probs[i].b, probs[i].x, opts->tol,
+                           opts->maxit);
+  cudaStreamDestroy(cs);
+  if (rc == SE_OK && cudaGraphInstantiate(&B->exec, G, 0) != cudaSuccess) {
+    set_error("se_batch_create: cudaGraphInstantiate: %s", cudaGetErrorString(cudaGetLastError()));
+    rc = SE_ECUDA;
+  }
+  cudaGraphDestroy(G);
+  if (rc != SE_OK) {
+    delete B;
+    return rc;
+  }
+  *out = B;
+  return SE_OK;
+}
+
+int se_batch_run(se_batch_t B, void* stream) {
+  SE_CHECK(B, SE_EINVAL, "se_batch_run: null batch");
+  SE_CUDA(cudaGraphLaunch(B->exec, reinterpret_cast<cudaStream_t>(stream)));
+  return SE_OK;
+}
+
+int se_batch_stats(se_batch_t B, void* stream, se_solve_stats* out) {
+  SE_CHECK(B && out, SE_EINVAL, "se_batch_stats: null argument");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int worst = SE_OK;
+  for (size_t i = 0; i < B->probs.size(); ++i) {
+    se_solve_stats st{};
+    int rc = read_graph_stats(B->probs[i].mesh, s, &st, B->opts.tol, B->opts.maxit);
+    st.status = rc;
+    out[i] = st;
+    if (rc != SE_OK) worst = rc;
+  }
+  return worst;
+}
+
+int se_batch_destroy(se_batch_t B) {
+  if (!B) return SE_OK;
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  delete B;
+  return SE_OK;
+}
+
+int se_batch_solve(int n, const se_problem* probs, const se_solve_opts* opts, se_solve_stats* out) {
+  se_batch_t B = nullptr;
+  SE_TRY(se_batch_create(n, probs, opts, &B));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(opts->stream);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+  int rc = se_batch_run(B, opts->stream);
+  cudaEventRecord(e1, s);
+  if (rc == SE_OK) rc = se_batch_stats(B, opts->stream, out);
+  float ms = 0.f;
+  cudaEventSynchronize(e1);
+  cudaEventElapsedTime(&ms, e0, e1);
+  for (int i = 0; i < n; ++i) out[i].ms_total = ms;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  se_batch_destroy(B);
+  return rc;
+}
+
+}  // extern "C"

@@ -58,6 +58,10 @@ class se_solve_opts(C.Structure):
                 ("maxit", C.c_int), ("graph_capture", C.c_int), ("stream", C.c_void_p)]
 
 
+class se_problem(C.Structure):
+    _fields_ = [("mesh", C.c_void_p), ("pmg", C.c_void_p), ("b", C.c_void_p), ("x", C.c_void_p)]
+
+
 class se_solve_stats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("status", C.c_int), ("rel_residual", C.c_double),
                 ("ms_total", C.c_double), ("ms_precond", C.c_double), ("ms_operator", C.c_double)]
@@ -96,6 +100,11 @@ _SIGS = {
     "se_pmg_coarse_solve": ([_vp, _vp, _vp, C.POINTER(C.c_int), _vp], C.c_int),
     "se_pmg_coarse_solve_noalloc": ([_vp, _vp, _vp, C.POINTER(C.c_int), _vp], C.c_int),
     "se_solve": ([_vp, _vp, _vp, _vp, C.POINTER(se_solve_opts), C.POINTER(se_solve_stats)], C.c_int),
+    "se_batch_create": ([_ip, C.POINTER(se_problem), C.POINTER(se_solve_opts), C.POINTER(_vp)], C.c_int),
+    "se_batch_run": ([_vp, _vp], C.c_int),
+    "se_batch_stats": ([_vp, _vp, C.POINTER(se_solve_stats)], C.c_int),
+    "se_batch_destroy": ([_vp], C.c_int),
+    "se_batch_solve": ([_ip, C.POINTER(se_problem), C.POINTER(se_solve_opts), C.POINTER(se_solve_stats)], C.c_int),
     "se_prof_enable": ([_ip], C.c_int),
     "se_prof_reset": ([], C.c_int),
     "se_prof_query": ([_ip, _dp, C.POINTER(C.c_int64), _dp, _dp, _dp], C.c_int),
@@ -283,6 +292,51 @@ def se_solve(m, P, b, x, method=SE_FPCG, tol=1e-8, maxit=1000, restart=20, graph
     _check(lib.se_solve(m, P, _ptr(b), _ptr(x), C.byref(o), C.byref(st)),
            allow=(SE_ENOTCONV,) if allow_notconv else ())
     return st
+
+
+# ----------------------------------------------------------------------------- batched solves
+def _problems(problems):
+    arr = (se_problem * len(problems))()
+    for i, (m, P, b, x) in enumerate(problems):
+        arr[i].mesh, arr[i].pmg, arr[i].b, arr[i].x = m, P, _ptr(b), _ptr(x)
+    return arr
+
+
+def _opts(tol, maxit, stream, method=SE_FPCG, restart=20, graph_capture=1):
+    o = se_solve_opts()
+    o.method, o.restart, o.tol, o.maxit, o.graph_capture = method, restart, tol, maxit, graph_capture
+    o.stream = _stream(stream)
+    return o
+
+
+def se_batch_create(problems, tol=1e-8, maxit=1000, stream=None):
+    """problems: list of (mesh, pmg or None, b, x).  Returns the batch handle."""
+    arr = _problems(problems)
+    h = _vp()
+    _check(lib.se_batch_create(len(problems), arr, C.byref(_opts(tol, maxit, stream)), C.byref(h)))
+    return h.value
+
+
+def se_batch_run(B, stream=None):
+    _check(lib.se_batch_run(B, _stream(stream)))
+
+
+def se_batch_stats(B, n, stream=None, allow_notconv=False):
+    out = (se_solve_stats * n)()
+    _check(lib.se_batch_stats(B, _stream(stream), out), allow=(SE_ENOTCONV,) if allow_notconv else ())
+    return list(out)
+
+
+def se_batch_destroy(B):
+    _check(lib.se_batch_destroy(B))
+
+
+def se_batch_solve(problems, tol=1e-8, maxit=1000, stream=None, allow_notconv=False):
+    arr = _problems(problems)
+    out = (se_solve_stats * len(problems))()
+    _check(lib.se_batch_solve(len(problems), arr, C.byref(_opts(tol, maxit, stream)), out),
+           allow=(SE_ENOTCONV,) if allow_notconv else ())
+    return list(out)
 
 
 # ----------------------------------------------------------------------------- profiling

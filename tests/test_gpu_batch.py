@@ -1,0 +1,125 @@
+"""Device-driven solves (one CUDA graph per solve) and batched solves (one graph for many).
+
+The graph solve runs the same kernels as the host-driven loop with the same arithmetic per
+point, so iterations and solutions must agree exactly; every problem of a batch must give the
+same iterations and solution as when solved alone (deterministic reductions, no shared work
+space), and the batch must meet the tolerance for each problem.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as o
+import workloads as wl
+from tests.gpu_common import Case, gpu, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+def problem(se, torch, nel, p, seed, schedule, precision, smoother=1):
+    m = se.se_mesh_create(nel, p, perturb_frac=0.05, seed=seed, deform_amp=wl.DEFORM_AMP)
+    info = se.se_mesh_get_info(m)
+    xyz = torch.empty(3 * info.L, dtype=torch.float64, device="cuda")
+    se.se_mesh_nodes(m, xyz)
+    X = xyz.view(3, -1).cpu().numpy()
+    k, a = wl.request_modes(seed)
+    f = torch.from_numpy(wl.f_rhs_modes(X[0], X[1], X[2], k, a)).cuda()
+    b = torch.empty(info.L, dtype=torch.float64, device="cuda")
+    se.se_mesh_rhs(m, f, b)
+    P = se.se_pmg_setup(m, se.pmg_desc(schedule, smoother, 2, precision=precision))
+    return m, P, b, info
+
+
+@pytest.mark.parametrize("pre", ["ras", "jacobi_pcg"])
+def test_graph_solve_equals_host_loop(pre):
+    torch, se = gpu()
+    m, P, b, info = problem(se, torch, (4, 3, 3), 7, 3, (7, 3, 1), se.SE_FP64)
+    try:
+        Pu = P if pre == "ras" else None
+        x1 = torch.zeros_like(b)
+        x2 = torch.zeros_like(b)
+        s1 = se.se_solve(m, Pu, b, x1, tol=1e-9)
+        s2 = se.se_solve(m, Pu, b, x2, tol=1e-9, graph_capture=1)
+        assert s1.iterations == s2.iterations
+        assert abs(s1.rel_residual - s2.rel_residual) <= 1e-12
+        assert rel_err(x2.cpu().numpy(), x1.cpu().numpy()) <= 1e-14
+        # replay the cached graph: same result again
+        x2.zero_()
+        s3 = se.se_solve(m, Pu, b, x2, tol=1e-9, graph_capture=1)
+        assert s3.iterations == s1.iterations
+        assert rel_err(x2.cpu().numpy(), x1.cpu().numpy()) <= 1e-14
+    finally:
+        se.se_pmg_destroy(P)
+        se.se_mesh_destroy(m)
+
+
+def test_batch_equals_alone_and_converges():
+    torch, se = gpu()
+    specs = [((4, 4, 4), 3, (3, 1), se.SE_FP32), ((5, 4, 3), 5, (5, 3, 1), se.SE_FP32),
+             ((3, 3, 4), 7, (7, 3, 1), se.SE_FP32), ((3, 3, 3), 9, (9, 5, 1), se.SE_FP32),
+             ((4, 4, 4), 7, (7, 5, 3, 1), se.SE_FP64)]
+    probs = [problem(se, torch, nel, p, 40 + i, sch, prec) for i, (nel, p, sch, prec) in enumerate(specs)]
+    try:
+        alone = []
+        for m, P, b, info in probs:
+            x = torch.zeros_like(b)
+            st = se.se_solve(m, P, b, x, tol=1e-8, graph_capture=1)
+            alone.append((st.iterations, x.cpu().numpy()))
+        xs = [torch.zeros_like(b) for (_, _, b, _) in probs]
+        B = se.se_batch_create([(m, P, b, x) for (m, P, b, _), x in zip(probs, xs)], tol=1e-8)
+        try:
+            for rep in range(2):
+                for x in xs:
+                    x.zero_()
+                se.se_batch_run(B)
+                stats = se.se_batch_stats(B, len(probs))
+                for (it, xa), st, x in zip(alone, stats, xs):
+                    assert st.rel_residual <= 1e-8
+                    assert st.iterations == it
+                    assert rel_err(x.cpu().numpy(), xa) <= 1e-14
+        finally:
+            se.se_batch_destroy(B)
+        # one-call form
+        for x in xs:
+            x.zero_()
+        stats = se.se_batch_solve([(m, P, b, x) for (m, P, b, _), x in zip(probs, xs)], tol=1e-8)
+        assert [s.iterations for s in stats] == [a[0] for a in alone]
+    finally:
+        for m, P, b, info in probs:
+            se.se_pmg_destroy(P)
+            se.se_mesh_destroy(m)
+
+
+def test_batch_problem_matches_oracle():
+    c = Case((3, 3, 3), 5, pert=0.05, seed=12)
+    se, torch = c.se, c.torch
+    P = se.se_pmg_setup(c.m, se.pmg_desc((5, 3, 1), se.SE_SMOOTH_RAS, 2))
+    try:
+        f = wl.f_rhs(*c.lv.X)
+        b = c.empty()
+        se.se_mesh_rhs(c.m, c.to_gpu(f), b)
+        x = c.empty().zero_()
+        st = se.se_batch_solve([(c.m, P, b, x)], tol=1e-8)[0]
+        lvo, bo = o.problem(c.V, c.nel, c.p, amp=c.amp)
+        pmg = o.pmg_setup(c.V, c.nel, (5, 3, 1), smoother="ras", order=2, amp=c.amp)
+        xo, it_o, _ = o.solve(lvo, bo, pmg, tol=1e-8)
+        assert abs(st.iterations - it_o) <= 1
+        r = bo - o.ax(lvo, c.to_np(x))
+        assert math.sqrt(o.dot(lvo, r, r) / o.dot(lvo, bo, bo)) <= 1.5e-8
+    finally:
+        se.se_pmg_destroy(P)
+        c.close()
+
+
+def test_batch_rejects_shared_mesh():
+    torch, se = gpu()
+    m, P, b, info = problem(se, torch, (2, 2, 2), 3, 1, (3, 1), se.SE_FP64)
+    try:
+        x1, x2 = torch.zeros_like(b), torch.zeros_like(b)
+        with pytest.raises(se.SeError) as e:
+            se.se_batch_create([(m, P, b, x1), (m, P, b, x2)])
+        assert e.value.code == se.SE_EINVAL
+    finally:
+        se.se_pmg_destroy(P)
+        se.se_mesh_destroy(m)
