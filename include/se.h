@@ -226,6 +226,24 @@ int se_batch_destroy(se_batch_t batch);
 /* create + run + stats + destroy; ms_total of every entry is the wall time of the whole batch. */
 int se_batch_solve(int n, const se_problem* probs, const se_solve_opts* opts, se_solve_stats* out);
 
+/* ---------------------------------------------------------------- launch-tile autotuner */
+/* Elements per thread block of the operator (Ax) and FDM kernels for one polynomial order and
+ * precision.  se_tune times every valid candidate on a scratch problem of about 2M points
+ * (allocating its own buffers), keeps the fastest in the process-wide table used by all later
+ * launches, and reports it with the measured per-launch times.  se_tune_get reports the
+ * values in use (the built-in heuristic until tuned); se_tune_set installs given values
+ * (0 = heuristic). */
+typedef struct se_tile_cfg {
+  int p;
+  int precision;              /* SE_FP64 or SE_FP32 */
+  int ax_elems_per_block;
+  int fdm_elems_per_block;
+  double ax_ms, fdm_ms;       /* per launch on the tuning problem (se_tune only) */
+} se_tile_cfg;
+int se_tune(int p, int precision, se_tile_cfg* out);
+int se_tune_get(int p, int precision, se_tile_cfg* out);
+int se_tune_set(const se_tile_cfg* cfg);
+
 /* ---------------------------------------------------------------- profiling */
 /* Kernel classes timed with CUDA events on their launch stream while profiling is enabled. */
 enum {

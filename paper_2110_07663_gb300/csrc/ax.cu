@@ -99,16 +99,20 @@ __global__ void __launch_bounds__(512) ax_local_kernel(int64_t E, int NE, const 
   }
 }
 
-// Elements per block for N*N threads per element.
-static int ax_elems_per_block(int N) {
-  int ne = 256 / (N * N);
+// Elements per block for N*N threads per element: the tuned value if one is set and valid,
+// else enough elements for about 256 threads.
+int ax_elems_per_block(int p, bool fp32) {
+  const int N = p + 1;
+  const int t = tile_get(p, fp32).ax_ne;
+  if (t >= 1 && t * N * N <= 512) return t;
+  const int ne = 256 / (N * N);
   return ne < 1 ? 1 : ne;
 }
 
 template <int N, typename T>
 static int launch_ax(const Level& lv, const T* u, T* y, const T* G, const T* D,
                      const uint8_t* pflag, cudaStream_t s) {
-  const int NE = ax_elems_per_block(N);
+  const int NE = ax_elems_per_block(N - 1, sizeof(T) == 4);
   const int threads = NE * N * N;
   const size_t smem = (N * N + (size_t)NE * 3 * N * N * N) * sizeof(T);
   static bool attr_set = false;

@@ -126,6 +126,22 @@ int scratch_alloc(Allocs& a, Scratch* s) {
   return SE_OK;
 }
 
+// ------------------------------------------------------------------ launch tiles
+static std::mutex g_tile_mu;
+static TileCfg g_tiles[SE_MAX_ORDER + 1][2];
+
+TileCfg tile_get(int p, bool fp32) {
+  if (p < 0 || p > SE_MAX_ORDER) return TileCfg();
+  std::lock_guard<std::mutex> g(g_tile_mu);
+  return g_tiles[p][fp32 ? 1 : 0];
+}
+
+void tile_set(int p, bool fp32, const TileCfg& c) {
+  if (p < 0 || p > SE_MAX_ORDER) return;
+  std::lock_guard<std::mutex> g(g_tile_mu);
+  g_tiles[p][fp32 ? 1 : 0] = c;
+}
+
 // ------------------------------------------------------------------ profiling
 struct ProfEntry {
   int kind, variant;

@@ -377,8 +377,12 @@ __global__ void __launch_bounds__(512) fdm_kernel(int64_t E, int NE, const int* 
   }
 }
 
-// Elements per block: about 400 lines per phase, at most 16 elements.
-static int fdm_elems_per_block(int PB) {
+// Elements per block: the tuned value if one is set and valid, else about 400 lines per phase
+// (at most 16 elements).
+int fdm_elems_per_block(int p, bool fp32) {
+  const int PB = p + 3;
+  const int t = tile_get(p, fp32).fdm_ne;
+  if (t >= 1 && t * PB * PB <= 512) return t;
   int ne = 400 / (PB * PB);
   return ne < 1 ? 1 : (ne > 16 ? 16 : ne);
 }
@@ -387,7 +391,7 @@ template <int P, typename T, int MODE>
 static int launch_fdm(const Level& lv, const T* in, const T* S, const T* lam, T* out,
                       cudaStream_t s) {
   constexpr int PB = P + 3;
-  const int NE = fdm_elems_per_block(PB);
+  const int NE = fdm_elems_per_block(P, sizeof(T) == 4);
   const int threads = ((NE * PB * PB + 31) / 32) * 32;
   const size_t smem = (size_t)NE * (2 * PB * PB * PB + 3 * PB * PB + 3 * PB) * sizeof(T) +
                       (size_t)NE * 27 * sizeof(int);
@@ -503,4 +507,14 @@ template int schwarz_apply<float>(const Level&, int, const float*, float*, cudaS
 template int gather_ext<double>(const Level&, const double*, double*, cudaStream_t);
 template int fdm_apply_ext<double>(const Level&, const double*, double*, cudaStream_t);
 
+}  // namespace se
+
+namespace se {
+// RAS local solves only (own outputs weighted by 1/multiplicity, no QQ^T): used to time tiles.
+template <class T>
+int fdm_ras_local(const Level& lv, const T* r, T* out, cudaStream_t s) {
+  return dispatch_fdm<T, FDM_RAS>(lv, r, out, s);
+}
+template int fdm_ras_local<double>(const Level&, const double*, double*, cudaStream_t);
+template int fdm_ras_local<float>(const Level&, const float*, float*, cudaStream_t);
 }  // namespace se

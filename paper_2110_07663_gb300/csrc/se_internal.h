@@ -268,6 +268,18 @@ struct ProfScope {
   ~ProfScope();
 };
 
+// ------------------------------------------------------------------ launch tiles (common.cu)
+// Elements per block of the operator and FDM kernels for one (order, precision); 0 = the built-in
+// heuristic.  se_tune measures the candidates and stores the fastest here.
+struct TileCfg {
+  int ax_ne = 0;
+  int fdm_ne = 0;
+};
+TileCfg tile_get(int p, bool fp32);
+void tile_set(int p, bool fp32, const TileCfg& c);
+int ax_elems_per_block(int p, bool fp32);
+int fdm_elems_per_block(int p, bool fp32);
+
 inline unsigned grid_for(int64_t n, int threads, int64_t max_blocks = 1 << 30) {
   int64_t b = (n + threads - 1) / threads;
   if (b < 1) b = 1;

@@ -62,6 +62,11 @@ class se_problem(C.Structure):
     _fields_ = [("mesh", C.c_void_p), ("pmg", C.c_void_p), ("b", C.c_void_p), ("x", C.c_void_p)]
 
 
+class se_tile_cfg(C.Structure):
+    _fields_ = [("p", C.c_int), ("precision", C.c_int), ("ax_elems_per_block", C.c_int),
+                ("fdm_elems_per_block", C.c_int), ("ax_ms", C.c_double), ("fdm_ms", C.c_double)]
+
+
 class se_solve_stats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("status", C.c_int), ("rel_residual", C.c_double),
                 ("ms_total", C.c_double), ("ms_precond", C.c_double), ("ms_operator", C.c_double)]
@@ -105,6 +110,9 @@ _SIGS = {
     "se_batch_stats": ([_vp, _vp, C.POINTER(se_solve_stats)], C.c_int),
     "se_batch_destroy": ([_vp], C.c_int),
     "se_batch_solve": ([_ip, C.POINTER(se_problem), C.POINTER(se_solve_opts), C.POINTER(se_solve_stats)], C.c_int),
+    "se_tune": ([_ip, _ip, C.POINTER(se_tile_cfg)], C.c_int),
+    "se_tune_get": ([_ip, _ip, C.POINTER(se_tile_cfg)], C.c_int),
+    "se_tune_set": ([C.POINTER(se_tile_cfg)], C.c_int),
     "se_prof_enable": ([_ip], C.c_int),
     "se_prof_reset": ([], C.c_int),
     "se_prof_query": ([_ip, _dp, C.POINTER(C.c_int64), _dp, _dp, _dp], C.c_int),
@@ -337,6 +345,26 @@ def se_batch_solve(problems, tol=1e-8, maxit=1000, stream=None, allow_notconv=Fa
     _check(lib.se_batch_solve(len(problems), arr, C.byref(_opts(tol, maxit, stream)), out),
            allow=(SE_ENOTCONV,) if allow_notconv else ())
     return list(out)
+
+
+# ----------------------------------------------------------------------------- tile autotuner
+def se_tune(p, precision=SE_FP64) -> se_tile_cfg:
+    out = se_tile_cfg()
+    _check(lib.se_tune(p, precision, C.byref(out)))
+    return out
+
+
+def se_tune_get(p, precision=SE_FP64) -> se_tile_cfg:
+    out = se_tile_cfg()
+    _check(lib.se_tune_get(p, precision, C.byref(out)))
+    return out
+
+
+def se_tune_set(p, precision, ax_elems_per_block, fdm_elems_per_block):
+    c = se_tile_cfg()
+    c.p, c.precision = p, precision
+    c.ax_elems_per_block, c.fdm_elems_per_block = ax_elems_per_block, fdm_elems_per_block
+    _check(lib.se_tune_set(C.byref(c)))
 
 
 # ----------------------------------------------------------------------------- profiling
