@@ -416,6 +416,76 @@ def run_batch(args):
     print(json.dumps(out))
 
 
+SERVE_SCHEDULES = {5: (5, 3, 1), 7: (7, 3, 1), 9: (9, 5, 1)}
+
+
+def serve_stream(se, reqs, budget, slots, precision, t_scale=1.0):
+    """Submit `reqs` at their (scaled) arrival times, wait for all, return the server summary."""
+    import workloads as wl
+    S = se.se_serve_create(budget, slots)
+    tickets, keep = [], []
+    refused = 0
+    t0 = time.perf_counter()
+    for r in reqs:
+        delay = t0 + r["t"] * t_scale - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        m = r["mesh"]
+        md = se.mesh_desc(m["nel"], m["p"], perturb_frac=m["perturb_frac"], seed=m["seed"],
+                          deform_amp=wl.DEFORM_AMP)
+        pd = se.pmg_desc(SERVE_SCHEDULES[m["p"]], se.SE_SMOOTH_RAS, 2, precision=precision)
+        modes, amp = wl.request_modes(r["rhs_seed"])
+        key = hash((tuple(m["nel"]), m["p"], m["seed"])) & ((1 << 63) - 1)
+        q = se.make_request(md, key, pd, modes=modes, amplitude=amp, tol=1e-8)
+        keep.append(q)
+        try:
+            tickets.append(se.se_serve_submit(S, q))
+        except se.SeError:
+            refused += 1
+    results = [se.se_serve_wait(S, t, 3.6e6, allow=(se.SE_ENOTCONV,)) for t in tickets]
+    wall = time.perf_counter() - t0
+    st = se.se_serve_stats(S)
+    se.se_serve_destroy(S)
+    its = [r.iterations for r in results]
+    worst = max(r.rel_residual for r in results) if results else None
+    setups = [r.setup_ms for r in results if r.new_mesh]
+    solves = [r.solve_ms for r in results]
+    return {"requests": len(reqs), "completed": st.completed, "refused": st.refused + refused,
+            "failed": st.failed, "solves_per_s": round(st.solves_per_s, 2),
+            "p50_ms": round(st.p50_ms, 1), "p99_ms": round(st.p99_ms, 1), "mean_ms": round(st.mean_ms, 1),
+            "max_concurrent": st.max_concurrent, "meshes_created": st.meshes_created,
+            "mesh_reuses": st.mesh_reuses, "evictions": st.evictions, "wall_s": round(wall, 1),
+            "iterations_min_max": [min(its), max(its)] if its else None, "worst_rel_residual": worst,
+            "mean_setup_ms_new_mesh": round(statistics.mean(setups), 1) if setups else None,
+            "mean_solve_ms": round(statistics.mean(solves), 1) if solves else None}
+
+
+def run_serve(args):
+    """Poisson-arrival stream of solve requests (E log-uniform in [512, 65536], p in {5,7,9},
+    30% on a resident mesh with a new right-hand side) through the continuous-batching server
+    (FP32 V-cycle / FP64 Krylov, admission by HBM footprint), against the same stream through a
+    one-slot server with the plain FP64 method."""
+    import torch
+    from paper_2110_07663_gb300 import se
+    import workloads as wl
+    torch.cuda.set_device(0)
+    free, total = torch.cuda.mem_get_info()
+    budget = int(0.8 * free)
+    reqs = wl.serve_requests(n=args.serve, rate=args.rate, seed=0)
+    with ClockSampler(0) as clk:
+        served = serve_stream(se, reqs, budget, args.slots, se.SE_FP32)
+    base_reqs = reqs[:args.serve_baseline] if args.serve_baseline else reqs
+    serial = serve_stream(se, base_reqs, budget, 1, se.SE_FP64)
+    out = {"metric": "served Poisson solves: solves/s, p50/p99 latency", "value": served["solves_per_s"],
+           "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32 V-cycle / f64 Krylov",
+           "data": "synthetic",
+           "config": {"workload": f"{len(reqs)} requests, Poisson arrivals at {args.rate}/s, E log-uniform "
+                                  f"[512, 65536], p in {{5,7,9}}, 30% resident-mesh reuse, tol 1e-8",
+                      "slots": args.slots, "hbm_budget_GB": round(budget / 2 ** 30, 1)},
+           "served": served, "serial_fp64": serial, "clocks": clk.summary()}
+    print(json.dumps(out))
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -459,6 +529,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-timeout", type=float, default=240.0)
     ap.add_argument("--batch", type=int, default=0, help="run the batched workload of N problems")
+    ap.add_argument("--serve", type=int, default=0, help="run the serving workload of N requests")
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--serve-baseline", type=int, default=0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         ap.error("--warmup must be >= 3")
@@ -466,6 +540,8 @@ def main():
         run_reference(args)
     elif args.batch:
         run_batch(args)
+    elif args.serve:
+        run_serve(args)
     else:
         run_gpu(args)
 

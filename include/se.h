@@ -79,8 +79,9 @@ typedef struct se_mesh_desc {
   double perturb_frac;     /* used only when vertex_xyz == NULL */
   uint64_t seed;
   int bc[6];               /* faces x-, x+, y-, y+, z-, z+: SE_BC_DIRICHLET or SE_BC_NEUMANN */
-  int flags;               /* reserved, 0 */
+  int flags;               /* SE_MESH_NONBLOCKING_STREAM: the handle's stream is non-blocking */
 } se_mesh_desc;
+enum { SE_MESH_NONBLOCKING_STREAM = 1 };
 
 typedef struct se_mesh_info {
   int64_t E, N, L, n_global;  /* elements, points per direction, local points, global nodes */
@@ -243,6 +244,65 @@ typedef struct se_tile_cfg {
 int se_tune(int p, int precision, se_tile_cfg* out);
 int se_tune_get(int p, int precision, se_tile_cfg* out);
 int se_tune_set(const se_tile_cfg* cfg);
+
+/* ---------------------------------------------------------------- serving */
+/* Estimated device bytes of a mesh with its preconditioner and solve work space (the sizes the
+ * library allocates, plus the transient Arnoldi vectors of the set-up). */
+int se_mesh_footprint_bytes(const se_mesh_desc* desc, const se_pmg_desc* pmg, size_t* out);
+
+/* A solve server with continuous batching: submitted requests are admitted by a scheduler thread
+ * as slots and device memory free up; resident meshes (keyed by the client) are reused with
+ * their geometry, smoother data and captured solve graph; the device-driven solves of admitted
+ * requests run concurrently on separate non-blocking streams.  Requests whose estimated
+ * footprint exceeds the whole budget are refused at submission (SE_EREFUSED). */
+enum { SE_RHS_MODES = 0, SE_RHS_HOST = 1 };
+typedef struct se_request {
+  se_mesh_desc mesh;       /* mesh to build when mesh_key is not resident (vertex_xyz unused) */
+  uint64_t mesh_key;       /* client-chosen identity: requests with the same key share a mesh */
+  se_pmg_desc pmg;         /* preconditioner of a newly built mesh */
+  int rhs_kind;            /* SE_RHS_MODES: manufactured u* = amplitude prod_c sin(modes[c] pi x_c);
+                              SE_RHS_HOST: b_host holds b (L-vector), copied at submission */
+  int modes[3];
+  double amplitude;
+  const double* b_host;
+  double* x_host;          /* optional host buffer (L doubles) that receives the solution */
+  double tol;
+  int maxit;
+} se_request;
+typedef struct se_result {
+  int status;
+  int iterations;
+  double rel_residual;
+  double latency_ms;       /* completion - submission */
+  double queue_ms;         /* start of the solve - submission */
+  int new_mesh;            /* 1 if the request built its mesh */
+  double setup_ms;         /* time spent building the mesh and preconditioner (0 if reused) */
+  double solve_ms;         /* completion - start of the solve */
+} se_result;
+typedef struct se_serve_cfg {
+  size_t hbm_budget;       /* bytes of device memory the resident meshes may occupy */
+  int max_slots;           /* requests solved concurrently */
+} se_serve_cfg;
+typedef struct se_serve_stats {
+  int64_t submitted, completed, refused, failed, pending;
+  double solves_per_s;     /* completed / (last completion - first submission) */
+  double p50_ms, p99_ms, mean_ms;
+  int max_concurrent;
+  int64_t meshes_created, mesh_reuses, evictions;
+  size_t resident_bytes;
+} se_serve_summary;
+typedef struct se_server_s* se_server_t;
+int se_serve_create(const se_serve_cfg* cfg, se_server_t* out);
+/* Queues a request; *ticket identifies it.  SE_EINVAL for a malformed request, SE_EREFUSED if it
+ * can never fit the budget. */
+int se_serve_submit(se_server_t s, const se_request* req, uint64_t* ticket);
+/* SE_EBUSY while pending; otherwise the request's status with *res filled. */
+int se_serve_poll(se_server_t s, uint64_t ticket, se_result* res);
+/* Blocks up to timeout_ms (SE_ETIMEOUT if still pending). */
+int se_serve_wait(se_server_t s, uint64_t ticket, double timeout_ms, se_result* res);
+int se_serve_stats(se_server_t s, se_serve_summary* out);
+/* Stops the scheduler, waits for running solves, frees every resident mesh. */
+int se_serve_destroy(se_server_t s);
 
 /* ---------------------------------------------------------------- profiling */
 /* Kernel classes timed with CUDA events on their launch stream while profiling is enabled. */

@@ -4,7 +4,7 @@
 #include <cmath>
 #include <cstring>
 
-#include "se_internal.h"
+#include "pmg_internal.h"
 
 namespace se {
 
@@ -160,6 +160,15 @@ __global__ void mass_times_kernel(int64_t L, const double* __restrict__ B,
                                   const double* __restrict__ f, double* __restrict__ b) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx < L) b[idx] = B[idx] * f[idx];
+}
+
+__global__ void modes_rhs_kernel(int64_t L, const double* __restrict__ X, const double* __restrict__ B,
+                                 int k1, int k2, int k3, double a, double* __restrict__ b) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= L) return;
+  const double f = M_PI * M_PI * (double)(k1 * k1 + k2 * k2 + k3 * k3) * a *
+                   sinpi(k1 * X[idx]) * sinpi(k2 * X[L + idx]) * sinpi(k3 * X[2 * L + idx]);
+  b[idx] = B[idx] * f;
 }
 
 __global__ void diag_from_inv_kernel(int64_t L, const double* __restrict__ dinv,
@@ -330,6 +339,13 @@ int local_to_global(const Level& lv, int* l2g, cudaStream_t s) {
   return SE_OK;
 }
 
+int rhs_modes(se_mesh_s* m, const int k[3], double a, double* b, cudaStream_t s) {
+  const Level& lv = m->fine;
+  modes_rhs_kernel<<<grid_for(lv.L, 256), 256, 0, s>>>(lv.L, lv.X, lv.B, k[0], k[1], k[2], a, b);
+  SE_LAUNCH_CHECK();
+  return gs_apply<double>(lv, b, true, s);
+}
+
 int make_fp32_geometry(Level& lv, Allocs& allocs, cudaStream_t s) {
   if (lv.G32) return SE_OK;
   SE_TRY(dmalloc(allocs, &lv.G32, 6 * (size_t)lv.L));
@@ -422,7 +438,8 @@ int se_mesh_create(const se_mesh_desc* desc, se_mesh_t* out) {
     delete m;
     return code;
   };
-  if (cudaStreamCreate(&m->stream) != cudaSuccess) {
+  const unsigned sflags = (desc->flags & SE_MESH_NONBLOCKING_STREAM) ? cudaStreamNonBlocking : cudaStreamDefault;
+  if (cudaStreamCreateWithFlags(&m->stream, sflags) != cudaSuccess) {
     set_error("se_mesh_create: cudaStreamCreate failed");
     return fail(SE_ECUDA);
   }

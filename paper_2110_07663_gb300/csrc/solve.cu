@@ -331,12 +331,13 @@ static int read_graph_stats(se_mesh_s* m, cudaStream_t s, se_solve_stats* out, d
   return SE_OK;
 }
 
-// se_solve with graph_capture: build (or reuse) this mesh's solve graph and launch it once.
-int graph_solve(se_mesh_s* m, se_pmg_s* P, const double* b, double* x, const se_solve_opts& o,
-                cudaStream_t s, se_solve_stats* st) {
+// Builds (or reuses) this mesh's solve graph for (P, b, x, tol, maxit) and launches it on s
+// without waiting.  read_graph_stats collects the result.
+int graph_solve_launch(se_mesh_s* m, se_pmg_s* P, const double* b, double* x, double tol,
+                       int maxit, cudaStream_t s) {
   SE_TRY(prepare_graph_solve(m));
   const bool same = m->gexec && m->gkey[0] == P && m->gkey[1] == b && m->gkey[2] == x &&
-                    m->gtol == o.tol && m->gmaxit == o.maxit;
+                    m->gtol == tol && m->gmaxit == maxit;
   if (!same) {
     if (m->gexec) cudaGraphExecDestroy(m->gexec);
     m->gexec = nullptr;
@@ -344,7 +345,7 @@ int graph_solve(se_mesh_s* m, se_pmg_s* P, const double* b, double* x, const se_
     SE_CUDA(cudaGraphCreate(&G, 0));
     cudaStream_t cs;
     SE_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    int rc = append_fpcg_solve(G, cs, m, P, b, x, o.tol, o.maxit);
+    int rc = append_fpcg_solve(G, cs, m, P, b, x, tol, maxit);
     cudaStreamDestroy(cs);
     if (rc == SE_OK) {
       cudaError_t e = cudaGraphInstantiate(&m->gexec, G, 0);
@@ -359,10 +360,21 @@ int graph_solve(se_mesh_s* m, se_pmg_s* P, const double* b, double* x, const se_
     m->gkey[0] = P;
     m->gkey[1] = b;
     m->gkey[2] = x;
-    m->gtol = o.tol;
-    m->gmaxit = o.maxit;
+    m->gtol = tol;
+    m->gmaxit = maxit;
   }
   SE_CUDA(cudaGraphLaunch(m->gexec, s));
+  return SE_OK;
+}
+
+int graph_solve_result(se_mesh_s* m, cudaStream_t s, double tol, int maxit, se_solve_stats* st) {
+  return read_graph_stats(m, s, st, tol, maxit);
+}
+
+// se_solve with graph_capture: one launch of the cached graph, then its statistics.
+int graph_solve(se_mesh_s* m, se_pmg_s* P, const double* b, double* x, const se_solve_opts& o,
+                cudaStream_t s, se_solve_stats* st) {
+  SE_TRY(graph_solve_launch(m, P, b, x, o.tol, o.maxit, s));
   return read_graph_stats(m, s, st, o.tol, o.maxit);
 }
 

@@ -19,6 +19,8 @@ SE_FP64, SE_FP32 = 0, 1
 SE_SMOOTH_JACOBI, SE_SMOOTH_RAS, SE_SMOOTH_ASM = 0, 1, 2
 SE_FPCG, SE_FGMRES = 0, 1
 SE_AX_ASSEMBLE, SE_AX_MASK, SE_AX_FP32 = 1, 2, 4
+SE_MESH_NONBLOCKING_STREAM = 1
+SE_RHS_MODES, SE_RHS_HOST = 0, 1
 SE_MAX_LEVELS, SE_MAX_ORDER = 8, 10
 (SE_K_AX, SE_K_GS, SE_K_FDM, SE_K_CHEBY_UPD, SE_K_RESTRICT, SE_K_PROLONG, SE_K_COARSE,
  SE_K_KRYLOV, SE_K_JACOBI, SE_K_COUNT) = range(10)
@@ -67,6 +69,31 @@ class se_tile_cfg(C.Structure):
                 ("fdm_elems_per_block", C.c_int), ("ax_ms", C.c_double), ("fdm_ms", C.c_double)]
 
 
+class se_request(C.Structure):
+    _fields_ = [("mesh", se_mesh_desc), ("mesh_key", C.c_uint64), ("pmg", se_pmg_desc),
+                ("rhs_kind", C.c_int), ("modes", C.c_int * 3), ("amplitude", C.c_double),
+                ("b_host", C.POINTER(C.c_double)), ("x_host", C.POINTER(C.c_double)),
+                ("tol", C.c_double), ("maxit", C.c_int)]
+
+
+class se_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("rel_residual", C.c_double),
+                ("latency_ms", C.c_double), ("queue_ms", C.c_double), ("new_mesh", C.c_int),
+                ("setup_ms", C.c_double), ("solve_ms", C.c_double)]
+
+
+class se_serve_cfg(C.Structure):
+    _fields_ = [("hbm_budget", C.c_size_t), ("max_slots", C.c_int)]
+
+
+class se_serve_summary(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("refused", C.c_int64),
+                ("failed", C.c_int64), ("pending", C.c_int64), ("solves_per_s", C.c_double),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double),
+                ("max_concurrent", C.c_int), ("meshes_created", C.c_int64),
+                ("mesh_reuses", C.c_int64), ("evictions", C.c_int64), ("resident_bytes", C.c_size_t)]
+
+
 class se_solve_stats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("status", C.c_int), ("rel_residual", C.c_double),
                 ("ms_total", C.c_double), ("ms_precond", C.c_double), ("ms_operator", C.c_double)]
@@ -113,6 +140,13 @@ _SIGS = {
     "se_tune": ([_ip, _ip, C.POINTER(se_tile_cfg)], C.c_int),
     "se_tune_get": ([_ip, _ip, C.POINTER(se_tile_cfg)], C.c_int),
     "se_tune_set": ([C.POINTER(se_tile_cfg)], C.c_int),
+    "se_mesh_footprint_bytes": ([C.POINTER(se_mesh_desc), C.POINTER(se_pmg_desc), C.POINTER(C.c_size_t)], C.c_int),
+    "se_serve_create": ([C.POINTER(se_serve_cfg), C.POINTER(_vp)], C.c_int),
+    "se_serve_submit": ([_vp, C.POINTER(se_request), C.POINTER(C.c_uint64)], C.c_int),
+    "se_serve_poll": ([_vp, C.c_uint64, C.POINTER(se_result)], C.c_int),
+    "se_serve_wait": ([_vp, C.c_uint64, C.c_double, C.POINTER(se_result)], C.c_int),
+    "se_serve_stats": ([_vp, C.POINTER(se_serve_summary)], C.c_int),
+    "se_serve_destroy": ([_vp], C.c_int),
     "se_prof_enable": ([_ip], C.c_int),
     "se_prof_reset": ([], C.c_int),
     "se_prof_query": ([_ip, _dp, C.POINTER(C.c_int64), _dp, _dp, _dp], C.c_int),
@@ -365,6 +399,77 @@ def se_tune_set(p, precision, ax_elems_per_block, fdm_elems_per_block):
     c.p, c.precision = p, precision
     c.ax_elems_per_block, c.fdm_elems_per_block = ax_elems_per_block, fdm_elems_per_block
     _check(lib.se_tune_set(C.byref(c)))
+
+
+# ----------------------------------------------------------------------------- serving
+def mesh_desc(nel, p, perturb_frac=0.0, seed=0, deform_amp=0.05, bc=(SE_BC_DIRICHLET,) * 6, flags=0):
+    d = se_mesh_desc()
+    d.nel[:] = list(nel)
+    d.p, d.deform_amp, d.perturb_frac, d.seed, d.flags = p, deform_amp, perturb_frac, seed, flags
+    d.bc[:] = list(bc)
+    return d
+
+
+def se_mesh_footprint_bytes(mdesc: se_mesh_desc, pdesc: se_pmg_desc) -> int:
+    out = C.c_size_t()
+    _check(lib.se_mesh_footprint_bytes(C.byref(mdesc), C.byref(pdesc), C.byref(out)))
+    return out.value
+
+
+def make_request(mdesc, mesh_key, pdesc, modes=(1, 1, 1), amplitude=1.0, b_host=None,
+                 x_host=None, tol=1e-8, maxit=500) -> se_request:
+    """Request for se_serve_submit; b_host / x_host are numpy float64 arrays (kept alive by the
+    caller until the request completes; b_host is copied at submission)."""
+    q = se_request()
+    q.mesh, q.mesh_key, q.pmg = mdesc, mesh_key, pdesc
+    q.rhs_kind = SE_RHS_HOST if b_host is not None else SE_RHS_MODES
+    q.modes[:] = list(modes)
+    q.amplitude = amplitude
+    if b_host is not None:
+        q.b_host = b_host.ctypes.data_as(C.POINTER(C.c_double))
+    if x_host is not None:
+        q.x_host = x_host.ctypes.data_as(C.POINTER(C.c_double))
+    q.tol, q.maxit = tol, maxit
+    return q
+
+
+def se_serve_create(hbm_budget, max_slots):
+    c = se_serve_cfg()
+    c.hbm_budget, c.max_slots = int(hbm_budget), int(max_slots)
+    h = _vp()
+    _check(lib.se_serve_create(C.byref(c), C.byref(h)))
+    return h.value
+
+
+def se_serve_submit(S, req: se_request) -> int:
+    t = C.c_uint64()
+    _check(lib.se_serve_submit(S, C.byref(req), C.byref(t)))
+    return t.value
+
+
+def se_serve_poll(S, ticket):
+    """(status, se_result) with status SE_EBUSY while pending."""
+    r = se_result()
+    rc = lib.se_serve_poll(S, ticket, C.byref(r))
+    if rc not in (SE_OK, SE_EBUSY, SE_ENOTCONV):
+        raise SeError(rc, se_last_error())
+    return rc, r
+
+
+def se_serve_wait(S, ticket, timeout_ms=60000.0, allow=()):
+    r = se_result()
+    _check(lib.se_serve_wait(S, ticket, timeout_ms, C.byref(r)), allow=allow)
+    return r
+
+
+def se_serve_stats(S) -> se_serve_summary:
+    out = se_serve_summary()
+    _check(lib.se_serve_stats(S, C.byref(out)))
+    return out
+
+
+def se_serve_destroy(S):
+    _check(lib.se_serve_destroy(S))
 
 
 # ----------------------------------------------------------------------------- profiling
