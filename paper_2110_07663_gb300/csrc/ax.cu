@@ -144,6 +144,9 @@ int ax_local(const Level& lv, const T* u, T* y, bool mask_in, cudaStream_t s) {
   ProfScope prof(SE_K_AX, s, pts, pts * 8.0 * sizeof(T), pts * (12.0 * N + 15.0),
                  prof_variant<T>(lv.p));
   const uint8_t* pf = mask_in ? lv.pflag : nullptr;
+  if constexpr (sizeof(T) == 4) {
+    if (!mask_in && ax_tma_supported(lv.p)) return ax_local_tma(lv, u, y, s);
+  }
   switch (N) {
     case 2: return launch_ax<2, T>(lv, u, y, G, D, pf, s);
     case 3: return launch_ax<3, T>(lv, u, y, G, D, pf, s);

@@ -196,8 +196,39 @@ __device__ __forceinline__ int64_t window_source(const int* __restrict__ nb, int
 
 // NE elements per block.  Each contraction phase gives one thread per line of every element
 // (lines numbered element-major), so active threads form a contiguous prefix and only the last
-// warp of a phase can be partly idle; with NE * pbar^2 near a multiple of 32 the FP64 pipe
-// wastes few lane slots (one element per 128-thread block left 28 of 128 lanes idle at p = 7).
+// warp of a phase can be partly idle (one element per 128-thread block left 28 of 128 lanes
+// idle at p = 7).  S and S^T sit in shared memory with rows padded to a multiple of 4 entries
+// and are read as 16-byte vectors (4 FP32 or 2 FP64 values per load) against register lines
+// padded with zeros: the forward transform uses rows of S^T, the backward one rows of S.
+template <int PB>
+struct FdmDims {
+  static constexpr int PBP = (PB + 3) / 4 * 4;            // padded row length
+  static constexpr int PB3 = PB * PB * PB;
+  static constexpr int PB3P = (PB3 + 3) / 4 * 4;           // buffer length, 16-byte multiple
+  static constexpr int SROW = 3 * PB * PBP;                // S or S^T of 3 directions
+};
+
+// One FMA per multiply-add.  FP32: 16-byte loads of the padded row (the FP32 kernel is not
+// ALU-bound; padding entries are zero).  FP64 (ALU-bound): scalar loads of the PB real entries.
+template <int PB, int PBP, typename T>
+__device__ __forceinline__ T dot_row(const T* __restrict__ row, const T (&v)[PBP]) {
+  T acc = T(0);
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int a = 0; a < PBP; a += 4) {
+      const float4 s = *reinterpret_cast<const float4*>(row + a);
+      acc = fmaf(s.x, v[a], acc);
+      acc = fmaf(s.y, v[a + 1], acc);
+      acc = fmaf(s.z, v[a + 2], acc);
+      acc = fmaf(s.w, v[a + 3], acc);
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < PB; ++a) acc = fma(row[a], v[a], acc);
+  }
+  return acc;
+}
+
 template <int P, typename T, int MODE>
 __global__ void __launch_bounds__(512) fdm_kernel(int64_t E, int NE, const int* __restrict__ nbr,
                                                   const T* __restrict__ in,
@@ -207,7 +238,10 @@ __global__ void __launch_bounds__(512) fdm_kernel(int64_t E, int NE, const int* 
                                                   const uint8_t* __restrict__ pflag,
                                                   T* __restrict__ out) {
   constexpr int N = P + 1, PB = P + 3, PB2 = PB * PB, PB3 = PB * PB * PB;
-  constexpr int PER = 2 * PB3 + 3 * PB2 + 3 * PB;  // shared values per element
+  using Dm = FdmDims<PB>;
+  constexpr int PBP = Dm::PBP, PB3P = Dm::PB3P, SROW = Dm::SROW;
+  constexpr int LAMP = (3 * PB + 3) / 4 * 4;
+  constexpr int PER = 2 * PB3P + 2 * SROW + LAMP;  // shared values per element
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sbase = reinterpret_cast<T*>(smem_raw);
   int* snb = reinterpret_cast<int*>(sbase + (size_t)NE * PER);  // [NE][27]
@@ -215,13 +249,19 @@ __global__ void __launch_bounds__(512) fdm_kernel(int64_t E, int NE, const int* 
   const int ne = (int)((E - e0) < NE ? (E - e0) : NE);             // elements in this block
   const int tid = threadIdx.x, nt = blockDim.x;
   auto B0 = [&](int le) { return sbase + (size_t)le * PER; };
-  auto B1 = [&](int le) { return sbase + (size_t)le * PER + PB3; };
-  auto SS = [&](int le) { return sbase + (size_t)le * PER + 2 * PB3; };
-  auto SL = [&](int le) { return sbase + (size_t)le * PER + 2 * PB3 + 3 * PB2; };
+  auto B1 = [&](int le) { return sbase + (size_t)le * PER + PB3P; };
+  auto ST = [&](int le) { return sbase + (size_t)le * PER + 2 * PB3P; };          // S^T rows
+  auto SR = [&](int le) { return sbase + (size_t)le * PER + 2 * PB3P + SROW; };   // S rows
+  auto SL = [&](int le) { return sbase + (size_t)le * PER + 2 * PB3P + 2 * SROW; };
   if constexpr (MODE != FDM_GATHER) {
-    for (int q = tid; q < ne * 3 * PB2; q += nt) {
-      const int le = q / (3 * PB2), r = q - le * 3 * PB2;
-      SS(le)[r] = Sg[(e0 + le) * 3 * PB2 + r];
+    // S[d][row][col] (row = window point, col = mode) -> S^T[d][col][row], S[d][row][col], padded
+    for (int q = tid; q < ne * 3 * PB * PBP; q += nt) {
+      const int le = q / (3 * PB * PBP), r = q - le * 3 * PB * PBP;
+      const int d = r / (PB * PBP), rr = r - d * PB * PBP;
+      const int i = rr / PBP, j = rr - i * PBP;
+      const T* S = Sg + ((e0 + le) * 3 + d) * PB2;
+      ST(le)[r] = j < PB ? S[j * PB + i] : T(0);
+      SR(le)[r] = j < PB ? S[i * PB + j] : T(0);
     }
     for (int q = tid; q < ne * 3 * PB; q += nt) {
       const int le = q / (3 * PB), r = q - le * 3 * PB;
@@ -256,13 +296,16 @@ __global__ void __launch_bounds__(512) fdm_kernel(int64_t E, int NE, const int* 
     return;
   } else {
     __syncthreads();
-    T v[PB];
+    T v[PBP];
+#pragma unroll
+    for (int a = PB; a < PBP; ++a) v[a] = T(0);
     const bool full_line = tid < ne * PB2;
     const int le = full_line ? tid / PB2 : 0;
     const int ql = tid - le * PB2;
-    const T* Sx = SS(le);
-    const T* Sy = Sx + PB2;
-    const T* Sz = Sx + 2 * PB2;
+    const T* STx = ST(le);
+    const T* STy = STx + PB * PBP;
+    const T* STz = STx + 2 * PB * PBP;
+    const T* SRz = SR(le) + 2 * PB * PBP;
     const T* sl = SL(le);
     T* b0 = B0(le);
     T* b1 = B1(le);
@@ -272,12 +315,7 @@ __global__ void __launch_bounds__(512) fdm_kernel(int64_t E, int NE, const int* 
 #pragma unroll
       for (int a = 0; a < PB; ++a) v[a] = b0[a + PB * (b + PB * c)];
 #pragma unroll
-      for (int al = 0; al < PB; ++al) {
-        T acc = T(0);
-#pragma unroll
-        for (int a = 0; a < PB; ++a) acc += Sx[a * PB + al] * v[a];
-        b1[al + PB * (b + PB * c)] = acc;
-      }
+      for (int al = 0; al < PB; ++al) b1[al + PB * (b + PB * c)] = dot_row<PB, PBP>(STx + al * PBP, v);
     }
     __syncthreads();
     // ---- forward: S_y^T along b (line (alpha, c))
@@ -286,12 +324,7 @@ __global__ void __launch_bounds__(512) fdm_kernel(int64_t E, int NE, const int* 
 #pragma unroll
       for (int b = 0; b < PB; ++b) v[b] = b1[al + PB * (b + PB * c)];
 #pragma unroll
-      for (int be = 0; be < PB; ++be) {
-        T acc = T(0);
-#pragma unroll
-        for (int b = 0; b < PB; ++b) acc += Sy[b * PB + be] * v[b];
-        b0[al + PB * (be + PB * c)] = acc;
-      }
+      for (int be = 0; be < PB; ++be) b0[al + PB * (be + PB * c)] = dot_row<PB, PBP>(STy + be * PBP, v);
     }
     __syncthreads();
     // ---- forward: S_z^T along c, then D^-1 (line (alpha, beta))
@@ -302,13 +335,11 @@ __global__ void __launch_bounds__(512) fdm_kernel(int64_t E, int NE, const int* 
       const T lxy = sl[al] + sl[PB + be];
 #pragma unroll
       for (int ga = 0; ga < PB; ++ga) {
-        T acc = T(0);
-#pragma unroll
-        for (int c = 0; c < PB; ++c) acc += Sz[c * PB + ga] * v[c];
+        const T acc = dot_row<PB, PBP>(STz + ga * PBP, v);
         const int q = al + PB * (be + PB * ga);
         T dv;
         if constexpr (sizeof(T) == 8) dv = dinvg[(e0 + le) * PB3 + q];
-        else dv = T(1) / (lxy + sl[2 * PB + ga]);
+        else dv = __frcp_rn(lxy + sl[2 * PB + ga]);
         b1[q] = acc * dv;
       }
     }
@@ -323,10 +354,7 @@ __global__ void __launch_bounds__(512) fdm_kernel(int64_t E, int NE, const int* 
 #pragma unroll
       for (int cc = 0; cc < NC; ++cc) {
         const int c = C0 + cc;
-        T acc = T(0);
-#pragma unroll
-        for (int ga = 0; ga < PB; ++ga) acc += Sz[c * PB + ga] * v[ga];
-        b0[al + PB * (be + PB * c)] = acc;
+        b0[al + PB * (be + PB * c)] = dot_row<PB, PBP>(SRz + c * PBP, v);
       }
     }
     __syncthreads();
@@ -334,7 +362,7 @@ __global__ void __launch_bounds__(512) fdm_kernel(int64_t E, int NE, const int* 
     if (tid < ne * PB * NC) {
       const int le2 = tid / (PB * NC), q2 = tid - le2 * PB * NC;
       const int al = q2 % PB, c = C0 + q2 / PB;
-      const T* Sy2 = SS(le2) + PB2;
+      const T* SRy = SR(le2) + PB * PBP;
       T* b0e = B0(le2);
       T* b1e = B1(le2);
 #pragma unroll
@@ -342,10 +370,7 @@ __global__ void __launch_bounds__(512) fdm_kernel(int64_t E, int NE, const int* 
 #pragma unroll
       for (int bb = 0; bb < NC; ++bb) {
         const int b = C0 + bb;
-        T acc = T(0);
-#pragma unroll
-        for (int be = 0; be < PB; ++be) acc += Sy2[b * PB + be] * v[be];
-        b1e[al + PB * (b + PB * c)] = acc;
+        b1e[al + PB * (b + PB * c)] = dot_row<PB, PBP>(SRy + b * PBP, v);
       }
     }
     __syncthreads();
@@ -353,7 +378,7 @@ __global__ void __launch_bounds__(512) fdm_kernel(int64_t E, int NE, const int* 
     if (tid < ne * NC * NC) {
       const int le3 = tid / (NC * NC), q3 = tid - le3 * NC * NC;
       const int b = C0 + q3 % NC, c = C0 + q3 / NC;
-      const T* Sx3 = SS(le3);
+      const T* SRx = SR(le3);
       const T* b1e = B1(le3);
       const int64_t e = e0 + le3;
 #pragma unroll
@@ -361,9 +386,7 @@ __global__ void __launch_bounds__(512) fdm_kernel(int64_t E, int NE, const int* 
 #pragma unroll
       for (int aa = 0; aa < NC; ++aa) {
         const int a = C0 + aa;
-        T acc = T(0);
-#pragma unroll
-        for (int al = 0; al < PB; ++al) acc += Sx3[a * PB + al] * v[al];
+        const T acc = dot_row<PB, PBP>(SRx + a * PBP, v);
         if constexpr (MODE == FDM_RAS) {
           const int64_t li = e * (N * N * N) + (a - 1) + N * ((b - 1) + N * (c - 1));
           const int mlog = __ffs(pflag[li] & 0x0F) - 1;   // 1/multiplicity: exact power of 2
@@ -377,14 +400,36 @@ __global__ void __launch_bounds__(512) fdm_kernel(int64_t E, int NE, const int* 
   }
 }
 
+// Shared bytes per element of fdm_kernel<P, T, *> (plus 27 neighbour ids).
+template <int P, typename T>
+constexpr size_t fdm_smem_per_element() {
+  using Dm = FdmDims<P + 3>;
+  return (2 * Dm::PB3P + 2 * Dm::SROW + (3 * (P + 3) + 3) / 4 * 4) * sizeof(T) + 27 * sizeof(int);
+}
+
+size_t fdm_smem_bytes(int p, bool fp32, int ne) {
+  size_t per = 0;
+  switch (p) {
+#define SE_FDM_SM(PP) \
+  case PP: per = fp32 ? fdm_smem_per_element<PP, float>() : fdm_smem_per_element<PP, double>(); break;
+    SE_FDM_SM(1) SE_FDM_SM(2) SE_FDM_SM(3) SE_FDM_SM(4) SE_FDM_SM(5)
+    SE_FDM_SM(6) SE_FDM_SM(7) SE_FDM_SM(8) SE_FDM_SM(9) SE_FDM_SM(10)
+#undef SE_FDM_SM
+    default: per = 0;
+  }
+  return per * ne;
+}
+
 // Elements per block: the tuned value if one is set and valid, else about 400 lines per phase
 // (at most 16 elements).
 int fdm_elems_per_block(int p, bool fp32) {
   const int PB = p + 3;
   const int t = tile_get(p, fp32).fdm_ne;
-  if (t >= 1 && t * PB * PB <= 512) return t;
+  if (t >= 1 && t * PB * PB <= 512 && fdm_smem_bytes(p, fp32, t) <= 200 * 1024) return t;
   int ne = 400 / (PB * PB);
-  return ne < 1 ? 1 : (ne > 16 ? 16 : ne);
+  ne = ne < 1 ? 1 : (ne > 16 ? 16 : ne);
+  while (ne > 1 && fdm_smem_bytes(p, fp32, ne) > 200 * 1024) --ne;
+  return ne;
 }
 
 template <int P, typename T, int MODE>
@@ -393,8 +438,7 @@ static int launch_fdm(const Level& lv, const T* in, const T* S, const T* lam, T*
   constexpr int PB = P + 3;
   const int NE = fdm_elems_per_block(P, sizeof(T) == 4);
   const int threads = ((NE * PB * PB + 31) / 32) * 32;
-  const size_t smem = (size_t)NE * (2 * PB * PB * PB + 3 * PB * PB + 3 * PB) * sizeof(T) +
-                      (size_t)NE * 27 * sizeof(int);
+  const size_t smem = fdm_smem_bytes(P, sizeof(T) == 4, NE);
   static bool attr = false;
   if (!attr) {
     SE_CUDA(cudaFuncSetAttribute(fdm_kernel<P, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,

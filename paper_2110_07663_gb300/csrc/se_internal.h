@@ -278,7 +278,13 @@ struct TileCfg {
 TileCfg tile_get(int p, bool fp32);
 void tile_set(int p, bool fp32, const TileCfg& c);
 int ax_elems_per_block(int p, bool fp32);
+// FP32 Ax pipelined with TMA bulk copies (even N only); device status of its bounded waits.
+bool ax_tma_supported(int p);
+int ax_tma_group(int p);
+int ax_local_tma(const Level& lv, const float* u, float* y, cudaStream_t s);
+int pipeline_status_take(int* status);
 int fdm_elems_per_block(int p, bool fp32);
+size_t fdm_smem_bytes(int p, bool fp32, int ne);
 
 inline unsigned grid_for(int64_t n, int threads, int64_t max_blocks = 1 << 30) {
   int64_t b = (n + threads - 1) / threads;

@@ -189,6 +189,11 @@ extern "C" int se_solve(se_mesh_t m, se_pmg_t P, const double* b, double* x,
   cudaEventSynchronize(m->ev1);
   float ms = 0.f;
   cudaEventElapsedTime(&ms, m->ev0, m->ev1);
+  int pipe = 0;
+  if (pipeline_status_take(&pipe) == SE_OK && pipe != 0) {
+    set_error("se_solve: a pipelined kernel's bounded wait expired (results invalid)");
+    rc = SE_ETIMEOUT;
+  }
   st.ms_total = ms;
   st.status = rc;
   if (stats) *stats = st;

@@ -60,7 +60,7 @@ static int tune_typed(se_pmg_s* P, int p, se_tile_cfg* out) {
   tile_set(p, fp32, best);
   const bool have_fdm = fp32 ? lv.S32 != nullptr : lv.S64 != nullptr;
   for (int ne = 1; ne <= 16 && have_fdm && rc == SE_OK; ++ne) {
-    const size_t smem = (size_t)ne * (2 * PB * PB * PB + 3 * PB * PB + 3 * PB) * sizeof(T) + ne * 27 * 4;
+    const size_t smem = fdm_smem_bytes(p, fp32, ne);
     if (ne * PB * PB > 512 || smem > 200 * 1024) continue;
     TileCfg c = best;
     c.fdm_ne = ne;

@@ -68,6 +68,23 @@ def test_ax_fp64(nel, p, bc):
         c.close()
 
 
+@pytest.mark.parametrize("nel,p", [((1, 1, 1), 1), ((3, 2, 2), 3), ((3, 3, 2), 5), ((3, 1, 2), 7),
+                                   ((1, 2, 2), 9), ((7, 5, 3), 3), ((4, 4, 5), 7)])
+def test_ax_fp32_pipelined_path(nel, p):
+    # FP32, no input mask, even N: the TMA-pipelined kernel (groups, ragged last group)
+    c = Case(nel, p, seed=30 + p)
+    try:
+        u = c.random_continuous(4, masked=False)
+        y = c.empty()
+        se = c.se
+        se.se_ax(c.m, c.to_gpu(u), y, se.SE_AX_FP32)
+        assert rel_err(c.to_np(y), o.ax_local(c.lv, u)) <= 2e-5
+        se.se_ax(c.m, c.to_gpu(u), y, se.SE_AX_FP32 | se.SE_AX_ASSEMBLE)
+        assert rel_err(c.to_np(y), o.ax(c.lv, u, mask=False)) <= 2e-5
+    finally:
+        c.close()
+
+
 def test_neumann_nullspace_and_symmetry_on_gpu():
     c = Case((3, 2, 2), 5, bc=("N",) * 6)
     try:
