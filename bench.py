@@ -486,6 +486,53 @@ def run_serve(args):
     print(json.dumps(out))
 
 
+def run_precision_study(args):
+    """FP32 V-cycle / FP64 Krylov against the all-FP64 method on the 4^3-element box at p = 7 and
+    p = 9: iterations, solve time, and the error of each solution against the FP64 oracle
+    solution and against the manufactured solution."""
+    import numpy as np
+    import torch
+    import oracle as o
+    from paper_2110_07663_gb300 import se
+    import workloads as wl
+    torch.cuda.set_device(0)
+    nel = (4, 4, 4)
+    V = wl.vertex_lattice(nel)
+    rows = []
+    for p, sched in [(7, (7, 3, 1)), (9, (9, 5, 1)), (9, (9, 7, 5, 1))]:
+        m = se.se_mesh_create(nel, p, vertex_xyz=V, deform_amp=wl.DEFORM_AMP)
+        info = se.se_mesh_get_info(m)
+        xyz = torch.empty(3 * info.L, dtype=torch.float64, device="cuda")
+        se.se_mesh_nodes(m, xyz)
+        X = xyz.view(3, -1).cpu().numpy()
+        b = torch.empty(info.L, dtype=torch.float64, device="cuda")
+        se.se_mesh_rhs(m, torch.from_numpy(wl.f_rhs(X[0], X[1], X[2])).cuda(), b)
+        lv, bo = o.problem(V, nel, p, amp=wl.DEFORM_AMP)
+        pmg = o.pmg_setup(V, nel, sched, smoother="ras", order=2, amp=wl.DEFORM_AMP)
+        xo, it_o, _ = o.solve(lv, bo, pmg, tol=1e-8)
+        ustar = wl.u_exact(*lv.X).reshape(-1)
+        row = {"p": p, "schedule": list(sched), "oracle_iterations": it_o}
+        for name, prec in (("fp64", se.SE_FP64), ("fp32_vcycle", se.SE_FP32)):
+            P = se.se_pmg_setup(m, se.pmg_desc(sched, se.SE_SMOOTH_RAS, 2, precision=prec))
+            x = torch.zeros_like(b)
+            for _ in range(3):
+                x.zero_()
+                st = se.se_solve(m, P, b, x, tol=1e-8, graph_capture=1)
+            xg = x.cpu().numpy()
+            r = bo.reshape(-1) - o.ax(lv, xg.reshape(lv.gid.shape)).reshape(-1)
+            row[name] = {"iterations": st.iterations, "ms": round(st.ms_total, 3),
+                         "rel_residual": st.rel_residual,
+                         "true_rel_residual": float(np.sqrt(o.dot(lv, r.reshape(lv.gid.shape), r.reshape(lv.gid.shape)) / o.dot(lv, bo, bo))),
+                         "max_err_vs_oracle_solution": float(np.max(np.abs(xg - xo.reshape(-1))) / np.max(np.abs(xo))),
+                         "max_err_vs_exact": float(np.max(np.abs(xg - ustar)))}
+            se.se_pmg_destroy(P)
+        rows.append(row)
+        se.se_mesh_destroy(m)
+    print(json.dumps({"metric": "mixed-precision preconditioner: iterations and error vs FP64 oracle",
+                      "config": {"workload": "4x4x4-element box, smooth map, Cheby-RAS(2) pMG, FPCG tol 1e-8"},
+                      "rows": rows}))
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -533,6 +580,7 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--serve-baseline", type=int, default=0)
+    ap.add_argument("--precision-study", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         ap.error("--warmup must be >= 3")
@@ -542,6 +590,8 @@ def main():
         run_batch(args)
     elif args.serve:
         run_serve(args)
+    elif args.precision_study:
+        run_precision_study(args)
     else:
         run_gpu(args)
 
