@@ -146,6 +146,8 @@ int ax_local(const Level& lv, const T* u, T* y, bool mask_in, cudaStream_t s) {
   const uint8_t* pf = mask_in ? lv.pflag : nullptr;
   if constexpr (sizeof(T) == 4) {
     if (!mask_in && ax_tma_supported(lv.p)) return ax_local_tma(lv, u, y, s);
+  } else {
+    if (!mask_in && ax_eo_supported(lv.p) && lv.eo64) return ax_local_eo(lv, u, y, s);
   }
   switch (N) {
     case 2: return launch_ax<2, T>(lv, u, y, G, D, pf, s);

@@ -290,6 +290,13 @@ int build_level(se_mesh_s* m, int p, Level* lvp, Allocs& allocs, cudaStream_t s)
   SE_CUDA(cudaMemcpy(lv.D32, D32h, N * N * sizeof(float), cudaMemcpyHostToDevice));
   SE_CUDA(cudaMemcpy(dxi, lv.basis.xi, N * sizeof(double), cudaMemcpyHostToDevice));
   SE_CUDA(cudaMemcpy(dw, lv.basis.w, N * sizeof(double), cudaMemcpyHostToDevice));
+  if (ax_eo_supported(p)) {
+    const int H = N / 2;
+    double tab[4 * (SE_MAX_ORDER + 1) * (SE_MAX_ORDER + 1) / 4 + 4];
+    ax_eo_tables(lv.basis, tab);
+    SE_TRY(dmalloc(allocs, &lv.eo64, 4 * H * H));
+    SE_CUDA(cudaMemcpy(lv.eo64, tab, 4 * H * H * sizeof(double), cudaMemcpyHostToDevice));
+  }
 
   // geometry
   double* dverts = nullptr;

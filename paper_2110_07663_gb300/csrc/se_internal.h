@@ -97,6 +97,7 @@ struct Level {
   float* dinv32 = nullptr;
   uint8_t* pflag = nullptr;  // multiplicity and free bit [L]
   double* D64 = nullptr;     // derivative matrix on the device [N*N]
+  double* eo64 = nullptr;    // even-odd folded D and D^T tables [4][N/2][N/2] (even N)
   float* D32 = nullptr;
   // QQ^T index map, groups sorted by global id within each class: pairs, quads, octets of
   // local ids sharing a global node (first id stored as ~id when the node is on a Dirichlet
@@ -282,6 +283,10 @@ int ax_elems_per_block(int p, bool fp32);
 bool ax_tma_supported(int p);
 int ax_tma_group(int p);
 int ax_local_tma(const Level& lv, const float* u, float* y, cudaStream_t s);
+// FP64 Ax with even-odd folded contractions (even N).
+bool ax_eo_supported(int p);
+void ax_eo_tables(const Basis1D& b, double* out);
+int ax_local_eo(const Level& lv, const double* u, double* y, cudaStream_t s);
 int pipeline_status_take(int* status);
 int fdm_elems_per_block(int p, bool fp32);
 size_t fdm_smem_bytes(int p, bool fp32, int ne);
