@@ -190,15 +190,45 @@ __device__ __forceinline__ void gs_group(const int* __restrict__ g, T* __restric
   for (int q = 0; q < M; ++q) u[id[q]] = sacc;
 }
 
+// Pairs (the bulk of the groups) are processed four per thread, interleaved: thread t of T
+// takes pairs t, t+T, t+2T, t+3T, so every load instruction of a warp still covers 32
+// neighbouring pairs (shared sectors) while each thread keeps eight independent value loads in
+// flight.  Quads, octets and single Dirichlet copies follow, one group per thread.
+constexpr int GS_PAIRS_PER_THREAD = 4;
+
 template <typename T>
 __global__ void gs_kernel(int64_t n2, int64_t n4, int64_t n8, int64_t n1,
                           const int* __restrict__ ids, T* __restrict__ u, bool mask) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n2) {
-    gs_group<T, 2>(ids + 2 * t, u, mask);
+  const int64_t T2 = (n2 + GS_PAIRS_PER_THREAD - 1) / GS_PAIRS_PER_THREAD;
+  if (t < T2) {
+    int a[GS_PAIRS_PER_THREAD], b[GS_PAIRS_PER_THREAD];
+    bool m[GS_PAIRS_PER_THREAD], on[GS_PAIRS_PER_THREAD];
+#pragma unroll
+    for (int k = 0; k < GS_PAIRS_PER_THREAD; ++k) {
+      const int64_t g = t + k * T2;
+      on[k] = g < n2;
+      const int2 q = on[k] ? *reinterpret_cast<const int2*>(ids + 2 * g) : make_int2(0, 0);
+      m[k] = q.x < 0;
+      a[k] = m[k] ? ~q.x : q.x;
+      b[k] = q.y;
+    }
+    T va[GS_PAIRS_PER_THREAD], vb[GS_PAIRS_PER_THREAD];
+#pragma unroll
+    for (int k = 0; k < GS_PAIRS_PER_THREAD; ++k) {
+      va[k] = on[k] ? u[a[k]] : T(0);
+      vb[k] = on[k] ? u[b[k]] : T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < GS_PAIRS_PER_THREAD; ++k) {
+      if (!on[k]) continue;
+      const T sum = (m[k] && mask) ? T(0) : va[k] + vb[k];
+      u[a[k]] = sum;
+      u[b[k]] = sum;
+    }
     return;
   }
-  t -= n2;
+  t -= T2;
   ids += 2 * n2;
   if (t < n4) {
     gs_group<T, 4>(ids + 4 * t, u, mask);
@@ -217,8 +247,9 @@ __global__ void gs_kernel(int64_t n2, int64_t n4, int64_t n8, int64_t n1,
 
 template <class T>
 int gs_apply(const Level& lv, T* u, bool mask, cudaStream_t s) {
-  const int64_t n = lv.n_pairs + lv.n_quads + lv.n_octs + lv.n_masked;
-  if (n == 0) return SE_OK;
+  const int64_t n = (lv.n_pairs + GS_PAIRS_PER_THREAD - 1) / GS_PAIRS_PER_THREAD + lv.n_quads +
+                    lv.n_octs + lv.n_masked;
+  if (lv.n_pairs + n == 0) return SE_OK;
   const double entries = 2.0 * lv.n_pairs + 4.0 * lv.n_quads + 8.0 * lv.n_octs;
   ProfScope prof(SE_K_GS, s, entries, entries * (2.0 * sizeof(T) + 4.0) + lv.n_masked * (4.0 + sizeof(T)),
                  entries, prof_variant<T>(lv.p));
