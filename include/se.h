@@ -159,14 +159,15 @@ int se_pmg_cheby(se_pmg_t pmg, int lvl, const double* res, double* x, void* stre
 int se_pmg_restrict(se_pmg_t pmg, int lvl, const double* rf, double* rc, void* stream);
 int se_pmg_prolong(se_pmg_t pmg, int lvl, const double* ec, double* ef, void* stream);
 /* Coarsest level: x = A_c^-1 r by Jacobi-PCG to coarse_tol (FP64, one persistent cooperative
- * launch).  *iters receives the iteration count (synchronises). */
+ * launch, pipelined form of the iteration: one grid synchronisation per iteration).  *iters
+ * receives the iteration count (synchronises). */
 int se_pmg_coarse_solve(se_pmg_t pmg, const double* r, double* x, int* iters, void* stream);
 /* Same coarse solve as se_pmg_coarse_solve, for callers that must not allocate device memory
  * during the call: code running after its memory pool is fixed (an application or framework
  * that reserved the device memory up front and owns every later allocation), or a steady-state
  * loop whose allocations were all made at start-up.  The paper has no counterpart; this is a
  * library convenience.  It calls no cudaMalloc/cudaFree: the CG vectors, partial sums and
- * barrier words live in one static device array of the library (about 5.3 MB, held by every
+ * barrier words live in one static device array of the library (about 9.5 MB, held by every
  * GPU that loads the library until the process exits), so the coarsest level may have at most
  * 131072 global nodes; larger problems get SE_EINVAL.  The first call on each device looks up
  * the array's device address with that device current; make that first call before any stream
@@ -237,8 +238,9 @@ int se_batch_solve(int n, const se_problem* probs, const se_solve_opts* opts, se
 typedef struct se_tile_cfg {
   int p;
   int precision;              /* SE_FP64 or SE_FP32 */
-  int ax_elems_per_block;
-  int fdm_elems_per_block;
+  int ax_elems_per_block;     /* elements * (p+1)^2 <= 512 threads */
+  int fdm_elems_per_block;    /* FP64: elements * (p+3)^2 <= 512 threads (one per line);
+                                 FP32: 1..8 elements, one warp each */
   double ax_ms, fdm_ms;       /* per launch on the tuning problem (se_tune only) */
 } se_tile_cfg;
 int se_tune(int p, int precision, se_tile_cfg* out);

@@ -4,9 +4,12 @@
 // library; here the coarse problem is solved by Jacobi-preconditioned CG to a relative tolerance.
 // The p = 1 element matrices are assembled into rows over global lattice nodes (27 entries each,
 // summed over the up to 8 elements sharing the row node in a fixed order: deterministic), and the
-// whole CG iteration runs in ONE cooperative launch: blocks meet at a grid barrier between the
-// matrix-vector product and each inner product.  Every wait is bounded by a wall-clock limit after
-// which the kernel records SE_ETIMEOUT and returns.
+// whole CG iteration runs in ONE cooperative launch.  On this part a grid-wide synchronisation
+// costs microseconds and a chain of dependent FP64 operations about 0.1 us per link, so the
+// iteration is the pipelined form of preconditioned CG (one synchronisation per iteration, which
+// carries all three inner products and orders the neighbour reads of the operator product).
+// Every wait is bounded by a wall-clock limit after which the kernel records SE_ETIMEOUT and
+// returns.
 #include <cooperative_groups.h>
 
 #include <mutex>
@@ -23,34 +26,122 @@ __device__ __forceinline__ long long global_ns() {
   return t;
 }
 
-// Grid barrier over `nblocks` blocks: bar[0] arrival count, bar[1] generation.  Returns false if
-// this or another block gave up waiting (status[0] != 0).
-__device__ bool grid_barrier(unsigned* bar, int* status, unsigned nblocks, long long timeout_ns) {
+constexpr int CG_THREADS = 256;
+
+// Sums of three values over the block, left in thread 0.  Every thread posts its values to shared
+// memory and one warp adds them, lane l taking entries l, l + 32, ... in order, then a shuffle
+// tree: a fixed order (deterministic) and a short chain of dependent FP64 additions.
+__device__ __forceinline__ void block_sum3(double (&v)[3], double* red) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) red[k * blockDim.x + threadIdx.x] = v[k];
   __syncthreads();
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      double acc = red[k * blockDim.x + threadIdx.x];
+      for (unsigned i = threadIdx.x + 32; i < blockDim.x; i += 32) acc += red[k * blockDim.x + i];
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+      v[k] = acc;
+    }
+  }
+}
+
+__device__ __forceinline__ unsigned atomic_add_release(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ unsigned load_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid barrier that sums three values over the grid.  count is a monotonic arrival counter
+// (zeroed before the launch): the k-th call of every block is complete once count reaches
+// (k + 1) * nblocks.  Each block posts its sums to part[parity][block] (4 doubles, the 4th
+// unused) and arrives with a release add; then every block waits for the count with acquire loads
+// and adds all blocks' partials itself, in block order (lane l: blocks l, l + 32, ..., then a
+// shuffle tree), so all blocks get bitwise the same sums with no second round trip through a
+// published result.  Partials alternate between two buffers: a block can post the partials of
+// call k + 2 (same buffer as call k) only after every block has arrived at call k + 1, that is
+// after every block has read the partials of call k.  Thread 0 of each block then evaluates
+// post(v) (the scalar recurrence coefficients: FP64 divisions once per block, not per thread),
+// which may rewrite v and returns one more value; every thread receives v and that value.  A
+// wait gives up after timeout_ns and records SE_ETIMEOUT in status[0]; the function returns false
+// once status[0] is set.
+template <class Post>
+__device__ bool grid_sum3(unsigned* count, unsigned call, int* status, unsigned nblocks,
+                          long long timeout_ns, double* part, double (&v)[3], double& post_value,
+                          double* red, Post post) {
+  __shared__ double s_out[4];
+  block_sum3(v, red);
+  double* buf = part + (size_t)(call & 1u) * 4 * nblocks;
   if (threadIdx.x == 0) {
-    volatile unsigned* vgen = bar + 1;
-    const unsigned gen = *vgen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(bar, 1u) + 1u;
-    if (arrived == nblocks) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      const long long t0 = global_ns();
-      while (*vgen == gen) {
-        __nanosleep(64);
-        if (*(volatile int*)status != 0) break;
-        if (global_ns() - t0 > timeout_ns) {
-          atomicExch(status, SE_ETIMEOUT);
-          break;
-        }
+    reinterpret_cast<double2*>(buf)[2 * blockIdx.x] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(buf)[2 * blockIdx.x + 1] = make_double2(v[2], 0.0);
+    atomic_add_release(count, 1u);
+    const unsigned target = (call + 1u) * nblocks;
+    const long long t0 = global_ns();
+    while ((int)(load_acquire(count) - target) < 0) {
+      __nanosleep(32);
+      if (*(volatile int*)status != 0) break;
+      if (global_ns() - t0 > timeout_ns) {
+        atomicExch(status, SE_ETIMEOUT);
+        break;
       }
     }
-    __threadfence();
   }
   __syncthreads();
-  return *(volatile int*)status == 0;
+  if (threadIdx.x < 32) {
+    // all loads of the lane issued together: at most 10 blocks per lane in the first pass
+    constexpr int UNR = 10;
+    double2 lo[UNR], hi[UNR];
+#pragma unroll
+    for (int i = 0; i < UNR; ++i) {
+      const unsigned k = threadIdx.x + 32u * i;
+      lo[i] = k < nblocks ? __ldcg(reinterpret_cast<const double2*>(buf) + 2 * k) : make_double2(0.0, 0.0);
+      hi[i] = k < nblocks ? __ldcg(reinterpret_cast<const double2*>(buf) + 2 * k + 1) : make_double2(0.0, 0.0);
+    }
+    double s0 = lo[0].x, s1 = lo[0].y, s2 = hi[0].x;  // nblocks >= 1: lane 0 has a block
+#pragma unroll
+    for (int i = 1; i < UNR; ++i) {
+      if (threadIdx.x + 32u * i < nblocks) {
+        s0 += lo[i].x;
+        s1 += lo[i].y;
+        s2 += hi[i].x;
+      }
+    }
+    for (unsigned k = threadIdx.x + 32u * UNR; k < nblocks; k += 32) {
+      const double2 l = __ldcg(reinterpret_cast<const double2*>(buf) + 2 * k);
+      const double2 h = __ldcg(reinterpret_cast<const double2*>(buf) + 2 * k + 1);
+      s0 += l.x;
+      s1 += l.y;
+      s2 += h.x;
+    }
+    if (threadIdx.x >= nblocks) s0 = s1 = s2 = 0.0;  // lanes without a block
+    for (int o = 16; o > 0; o >>= 1) {
+      s0 += __shfl_down_sync(0xffffffffu, s0, o);
+      s1 += __shfl_down_sync(0xffffffffu, s1, o);
+      s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    }
+    if (threadIdx.x == 0) {
+      double w[3] = {s0, s1, s2};
+      const double pv = post(w);
+      s_out[0] = w[0];
+      s_out[1] = w[1];
+      s_out[2] = w[2];
+      s_out[3] = pv;
+    }
+  }
+  __syncthreads();
+  v[0] = s_out[0];
+  v[1] = s_out[1];
+  v[2] = s_out[2];
+  post_value = s_out[3];
+  const bool ok = *(volatile int*)status == 0;
+  __syncthreads();
+  return ok;
 }
 
 // ------------------------------------------------------------------ assembly
@@ -114,6 +205,20 @@ __global__ void coarse_assemble_kernel(int nx, int ny, int nz, int64_t n, int64_
   }
 }
 
+// Ahat = A D^-1 (column g' of row g scaled by dinv[g']): the pipelined iteration needs A applied
+// only to D^-1-scaled vectors.  Slots whose neighbour lies outside the lattice hold 0 already.
+__global__ void coarse_scale_columns_kernel(int NX, int NY, int64_t n, const double* __restrict__ dinv,
+                                            double* __restrict__ A) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 27 * n) return;
+  const int slot = (int)(t / n);
+  const int64_t g = t - (int64_t)slot * n;
+  const int dI = slot % 3 - 1, dJ = (slot / 3) % 3 - 1, dK = slot / 9 - 1;
+  int64_t gc = g + dI + (int64_t)NX * (dJ + (int64_t)NY * dK);
+  gc = gc < 0 ? 0 : (gc >= n ? n - 1 : gc);
+  A[t] *= dinv[gc];
+}
+
 int coarse_setup(Level& lv, Allocs& allocs, cudaStream_t s) {
   SE_CHECK(lv.p == 1, SE_EINVAL, "coarse level must have p = 1 (got %d)", lv.p);
   const int64_t n = lv.n_global;
@@ -125,165 +230,150 @@ int coarse_setup(Level& lv, Allocs& allocs, cudaStream_t s) {
                                                               lv.L, lv.G64, lv.pflag, lv.Ac,
                                                               lv.cdinv, lv.g2l);
   SE_LAUNCH_CHECK();
+  coarse_scale_columns_kernel<<<grid_for(27 * n, 256), 256, 0, s>>>(lv.NX, lv.NY, n, lv.cdinv, lv.Ac);
+  SE_LAUNCH_CHECK();
   return local_to_global(lv, lv.l2g, s);
 }
 
 // ------------------------------------------------------------------ persistent Jacobi-PCG
 template <class T>
 struct CoarseArgs {
-  int64_t n, L;
-  int NX, NY, NZ;
-  const double* A;
+  int n, L;
+  int NX, NY;
+  const double* Ah;    // A D^-1, [27][n]
   const double* dinv;
   const int* g2l;
   const int* l2g;
   const T* rin;
   T* xout;
-  double *x, *r, *z, *p, *q, *partA, *partB;
-  unsigned* bar;
+  double *x, *r, *u, *p, *q, *s, *z, *w0, *w1, *part;
+  unsigned* count;
   int* status;
   double tol;
   int maxit;
   long long timeout_ns;
 };
 
-constexpr int CG_THREADS = 256;
-
-__device__ __forceinline__ void block_reduce2(double& a, double& b, double* sh) {
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_down_sync(0xffffffffu, a, o);
-    b += __shfl_down_sync(0xffffffffu, b, o);
+// (Ahat v)_g over the 27 lattice neighbours of g.  A slot whose neighbour lies outside the lattice
+// holds 0 (assembly), so its index is only clamped into the array: the product adds exactly 0.
+__device__ __forceinline__ double coarse_row(const double* __restrict__ Ah, const double* v, int n,
+                                             int NX, int NXY, int g) {
+  double acc = 0.0;
+#pragma unroll
+  for (int sl = 0; sl < 27; ++sl) {
+    const int dI = sl % 3 - 1, dJ = (sl / 3) % 3 - 1, dK = sl / 9 - 1;
+    const int gi = min(max(g + dI + NX * dJ + NXY * dK, 0), n - 1);
+    acc = fma(Ah[(int64_t)sl * n + g], v[gi], acc);
   }
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) {
-    sh[2 * w] = a;
-    sh[2 * w + 1] = b;
-  }
-  __syncthreads();
-  if (w == 0) {
-    a = lane < CG_THREADS / 32 ? sh[2 * lane] : 0.0;
-    b = lane < CG_THREADS / 32 ? sh[2 * lane + 1] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_down_sync(0xffffffffu, a, o);
-      b += __shfl_down_sync(0xffffffffu, b, o);
-    }
-  }
-  __syncthreads();
+  return acc;
 }
 
-// Every block sums the per-block partials in block order with one warp (same result everywhere).
-__device__ __forceinline__ void sum_partials(const double* part, int nb, double& a, double& b,
-                                             double* sh) {
-  if (threadIdx.x < 32) {
-    double sa = 0.0, sb = 0.0;
-    for (int k = threadIdx.x; k < nb; k += 32) {
-      sa += __ldcg(part + 2 * k);
-      sb += __ldcg(part + 2 * k + 1);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      sa += __shfl_down_sync(0xffffffffu, sa, o);
-      sb += __shfl_down_sync(0xffffffffu, sb, o);
-    }
-    if (threadIdx.x == 0) {
-      sh[0] = sa;
-      sh[1] = sb;
-    }
-  }
-  __syncthreads();
-  a = sh[0];
-  b = sh[1];
-  __syncthreads();
-}
-
+// Pipelined Jacobi-preconditioned CG (Ghysels and Vanroose, Parallel Computing 40, 2014,
+// preconditioned pipelined CG), M^-1 = D^-1:
+//   r = b, u = D^-1 r, w = A u
+//   loop: gamma = (r, u), delta = (w, u)                         [one synchronisation]
+//         beta = gamma / gamma_prev, alpha = gamma / (delta - beta gamma / alpha_prev)
+//                                            (first pass: beta = 0, alpha = gamma / delta)
+//         m = D^-1 w, n = A m (= Ahat w)
+//         z = n + beta z, q = m + beta q, s = w + beta s, p = u + beta p
+//         x += alpha p, r -= alpha s, u -= alpha q, w -= alpha z
+// In exact arithmetic it produces the iterates of textbook PCG.  The synchronisation that sums
+// (gamma, delta, (r, r)) also orders the neighbour reads of Ahat w: w alternates between two
+// arrays (read one, write the other).  The stopping rule is that of the textbook loop: stop
+// after the update that brings (r, r) to tol^2 (b, b) or below, or after maxit updates.
 template <class T>
 __global__ void __launch_bounds__(CG_THREADS) coarse_pcg_kernel(CoarseArgs<T> c) {
-  __shared__ double sh[2 * CG_THREADS / 32 + 2];
+  __shared__ double red[3 * CG_THREADS];
   const unsigned nb = gridDim.x;
-  const int64_t stride = (int64_t)gridDim.x * CG_THREADS;
-  const int64_t t0 = (int64_t)blockIdx.x * CG_THREADS + threadIdx.x;
-  double a0 = 0.0, a1 = 0.0;
-  for (int64_t g = t0; g < c.n; g += stride) {
+  const int stride = (int)gridDim.x * CG_THREADS;
+  const int t0 = (int)blockIdx.x * CG_THREADS + threadIdx.x;
+  const int NXY = c.NX * c.NY;
+  unsigned call = 0;
+  double v[3] = {0.0, 0.0, 0.0}, unused;
+  // r = b, u = D^-1 r, x = 0; (r, r)
+  for (int g = t0; g < c.n; g += stride) {
     const double rv = (double)c.rin[c.g2l[g]];
-    const double zv = c.dinv[g] * rv;
     c.r[g] = rv;
+    c.u[g] = c.dinv[g] * rv;
     c.x[g] = 0.0;
-    c.z[g] = zv;
-    c.p[g] = zv;
-    a0 = fma(rv, zv, a0);
-    a1 = fma(rv, rv, a1);
+    v[2] = fma(rv, rv, v[2]);
   }
-  block_reduce2(a0, a1, sh);
-  if (threadIdx.x == 0) {
-    c.partB[2 * blockIdx.x] = a0;
-    c.partB[2 * blockIdx.x + 1] = a1;
+  bool ok = grid_sum3(c.count, call++, c.status, nb, c.timeout_ns, c.part, v, unused, red,
+                      [](double (&)[3]) { return 0.0; });
+  const double rr0 = v[2];
+  const double tol2 = c.tol * c.tol * rr0;
+  // w = A u = Ahat r; gamma = (r, u), delta = (w, u)
+  v[0] = v[1] = v[2] = 0.0;
+  if (ok) {
+    for (int g = t0; g < c.n; g += stride) {
+      const double wv = coarse_row(c.Ah, c.r, c.n, c.NX, NXY, g);
+      const double uv = c.u[g], rv = c.r[g];
+      c.w0[g] = wv;
+      v[0] = fma(rv, uv, v[0]);
+      v[1] = fma(wv, uv, v[1]);
+    }
   }
   int it = 0;
-  if (grid_barrier(c.bar, c.status, nb, c.timeout_ns)) {
-    double rz, rr0;
-    sum_partials(c.partB, nb, rz, rr0, sh);
-    const double tol2 = c.tol * c.tol * rr0;
-    bool ok = true;
-    while (rr0 > 0.0 && it < c.maxit) {
-      // q = A p, (p, q)
-      a0 = 0.0;
-      for (int64_t g = t0; g < c.n; g += stride) {
-        const int I = (int)(g % c.NX), J = (int)((g / c.NX) % c.NY), K = (int)(g / ((int64_t)c.NX * c.NY));
-        double acc = 0.0;
-#pragma unroll
-        for (int sl = 0; sl < 27; ++sl) {
-          const int dI = sl % 3 - 1, dJ = (sl / 3) % 3 - 1, dK = sl / 9 - 1;
-          const int I2 = I + dI, J2 = J + dJ, K2 = K + dK;
-          if (I2 < 0 || I2 >= c.NX || J2 < 0 || J2 >= c.NY || K2 < 0 || K2 >= c.NZ) continue;
-          acc = fma(c.A[sl * c.n + g], c.p[g + dI + (int64_t)c.NX * (dJ + (int64_t)c.NY * dK)], acc);
-        }
-        c.q[g] = acc;
-        a0 = fma(c.p[g], acc, a0);
-      }
-      a1 = 0.0;
-      block_reduce2(a0, a1, sh);
-      if (threadIdx.x == 0) {
-        c.partA[2 * blockIdx.x] = a0;
-        c.partA[2 * blockIdx.x + 1] = 0.0;
-      }
-      if (!(ok = grid_barrier(c.bar, c.status, nb, c.timeout_ns))) break;
-      double pq, unused;
-      sum_partials(c.partA, nb, pq, unused, sh);
-      const double alpha = rz / pq;
-      a0 = 0.0;
-      a1 = 0.0;
-      for (int64_t g = t0; g < c.n; g += stride) {
-        c.x[g] = fma(alpha, c.p[g], c.x[g]);
-        const double rv = fma(-alpha, c.q[g], c.r[g]);
-        c.r[g] = rv;
-        const double zv = c.dinv[g] * rv;
-        c.z[g] = zv;
-        a0 = fma(rv, zv, a0);
-        a1 = fma(rv, rv, a1);
-      }
-      block_reduce2(a0, a1, sh);
-      if (threadIdx.x == 0) {
-        c.partB[2 * blockIdx.x] = a0;
-        c.partB[2 * blockIdx.x + 1] = a1;
-      }
-      if (!(ok = grid_barrier(c.bar, c.status, nb, c.timeout_ns))) break;
-      double rz_new, rr;
-      sum_partials(c.partB, nb, rz_new, rr, sh);
-      ++it;
-      if (rr <= tol2) break;
-      const double beta = rz_new / rz;
-      rz = rz_new;
-      for (int64_t g = t0; g < c.n; g += stride) c.p[g] = fma(beta, c.p[g], c.z[g]);
-      if (!(ok = grid_barrier(c.bar, c.status, nb, c.timeout_ns))) break;
+  double gamma = 0.0, alpha = 0.0;
+  while (ok && rr0 > 0.0) {
+    // v = (gamma, delta, (r, r)) -> (alpha, beta, (r, r)); post returns gamma
+    const double g_prev = gamma, a_prev = alpha;
+    const bool first = it == 0;
+    ok = grid_sum3(c.count, call++, c.status, nb, c.timeout_ns, c.part, v, gamma, red,
+                   [=](double (&w)[3]) {
+                     const double gm = w[0], dl = w[1];
+                     const double be = first ? 0.0 : gm / g_prev;
+                     w[0] = first ? gm / dl : gm / (dl - be * gm / a_prev);
+                     w[1] = be;
+                     return gm;
+                   });
+    if (!ok) break;
+    // after a synchronisation, so x is complete whichever way the loop ends
+    if (!first && v[2] <= tol2) break;  // (r, r) of the last update
+    if (it >= c.maxit) break;
+    alpha = v[0];
+    const double beta = v[1];
+    const double* wr = (it & 1) ? c.w1 : c.w0;
+    double* ww = (it & 1) ? c.w0 : c.w1;
+    v[0] = v[1] = v[2] = 0.0;
+    for (int g = t0; g < c.n; g += stride) {
+      const double wv = wr[g];
+      const double mv = c.dinv[g] * wv;
+      const double nv = coarse_row(c.Ah, wr, c.n, c.NX, NXY, g);
+      const double zv = first ? nv : fma(beta, c.z[g], nv);
+      const double qv = first ? mv : fma(beta, c.q[g], mv);
+      const double sv = first ? wv : fma(beta, c.s[g], wv);
+      const double pv = first ? c.u[g] : fma(beta, c.p[g], c.u[g]);
+      c.z[g] = zv;
+      c.q[g] = qv;
+      c.s[g] = sv;
+      c.p[g] = pv;
+      c.x[g] = fma(alpha, pv, c.x[g]);
+      const double rv = fma(-alpha, sv, c.r[g]);
+      const double uv = fma(-alpha, qv, c.u[g]);
+      const double wn = fma(-alpha, zv, wv);
+      c.r[g] = rv;
+      c.u[g] = uv;
+      ww[g] = wn;
+      v[0] = fma(rv, uv, v[0]);
+      v[1] = fma(wn, uv, v[1]);
+      v[2] = fma(rv, rv, v[2]);
     }
-    if (ok) {
-      for (int64_t l = t0; l < c.L; l += stride) c.xout[l] = (T)c.x[c.l2g[l]];
-    }
+    ++it;
+  }
+  if (ok) {
+    for (int l = t0; l < c.L; l += stride) c.xout[l] = (T)c.x[c.l2g[l]];
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) c.status[1] = it;
 }
 
+// Partial sums of the summing barrier: two buffers of 4 doubles per block.
+size_t coarse_partial_doubles(int nblocks) { return 8 * (size_t)nblocks; }
+
 int coarse_alloc(const Level& lv, Allocs& allocs, CoarseWork* w) {
   const int64_t n = lv.n_global;
+  SE_CHECK(lv.L < (int64_t)1 << 31 && 27 * n < (int64_t)1 << 40, SE_EINVAL,
+           "coarse level with %lld points is too large for 32-bit node indices", (long long)lv.L);
   int dev = 0, sms = 0, per_sm = 0;
   SE_CUDA(cudaGetDevice(&dev));
   SE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -292,17 +382,17 @@ int coarse_alloc(const Level& lv, Allocs& allocs, CoarseWork* w) {
   SE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm32, coarse_pcg_kernel<float>, CG_THREADS, 0));
   if (per_sm32 < per_sm) per_sm = per_sm32;
   SE_CHECK(per_sm >= 1, SE_ECUDA, "coarse solver kernel cannot be resident");
+  // one point per thread where possible; a grid of more than half the SMs is rounded up to a
+  // multiple of the SM count so that the FP64 work spreads evenly
   int64_t want = (n + CG_THREADS - 1) / CG_THREADS;
+  if (want > sms / 2) want = (want + sms - 1) / sms * sms;
   const int64_t cap = (int64_t)sms * (per_sm < 2 ? per_sm : 2);
   if (want > cap) want = cap;
   if (want < 1) want = 1;
   w->nblocks = (int)want;
-  SE_TRY(dmalloc(allocs, &w->x, n));
-  SE_TRY(dmalloc(allocs, &w->r, n));
-  SE_TRY(dmalloc(allocs, &w->z, n));
-  SE_TRY(dmalloc(allocs, &w->p, n));
-  SE_TRY(dmalloc(allocs, &w->q, n));
-  SE_TRY(dmalloc(allocs, &w->partial, 4 * (size_t)w->nblocks));
+  for (double** v : {&w->x, &w->r, &w->u, &w->p, &w->q, &w->s, &w->z, &w->w0, &w->w1})
+    SE_TRY(dmalloc(allocs, v, n));
+  SE_TRY(dmalloc(allocs, &w->partial, coarse_partial_doubles(w->nblocks)));
   SE_TRY(dmalloc(allocs, &w->bar, 2));
   SE_TRY(dmalloc(allocs, &w->status, 2));
   SE_CUDA(cudaMemset(w->bar, 0, 2 * sizeof(unsigned)));
@@ -314,12 +404,11 @@ template <class T>
 int coarse_solve(const Level& lv, CoarseWork& w, const T* r_l, T* x_l, double tol, int maxit,
                  cudaStream_t s) {
   CoarseArgs<T> a;
-  a.n = lv.n_global;
-  a.L = lv.L;
+  a.n = (int)lv.n_global;
+  a.L = (int)lv.L;
   a.NX = lv.NX;
   a.NY = lv.NY;
-  a.NZ = lv.NZ;
-  a.A = lv.Ac;
+  a.Ah = lv.Ac;
   a.dinv = lv.cdinv;
   a.g2l = lv.g2l;
   a.l2g = lv.l2g;
@@ -327,12 +416,15 @@ int coarse_solve(const Level& lv, CoarseWork& w, const T* r_l, T* x_l, double to
   a.xout = x_l;
   a.x = w.x;
   a.r = w.r;
-  a.z = w.z;
+  a.u = w.u;
   a.p = w.p;
   a.q = w.q;
-  a.partA = w.partial;
-  a.partB = w.partial + 2 * w.nblocks;
-  a.bar = w.bar;
+  a.s = w.s;
+  a.z = w.z;
+  a.w0 = w.w0;
+  a.w1 = w.w1;
+  a.part = w.partial;
+  a.count = w.bar;
   a.status = w.status;
   a.tol = tol;
   a.maxit = maxit;
@@ -350,9 +442,12 @@ template int coarse_solve<double>(const Level&, CoarseWork&, const double*, doub
 template int coarse_solve<float>(const Level&, CoarseWork&, const float*, float*, double, int, cudaStream_t);
 
 // ------------------------------------------------------------------ self-test of the wait limit
-__global__ void barrier_timeout_kernel(unsigned* bar, int* status, long long timeout_ns) {
-  // one more arrival is expected than blocks exist: nobody can pass, every block times out
-  grid_barrier(bar, status, gridDim.x + 1, timeout_ns);
+__global__ void barrier_timeout_kernel(unsigned* count, int* status, double* part, long long timeout_ns) {
+  // one more arrival is expected than blocks exist: the count never reaches its target
+  __shared__ double red[3 * 32];
+  double v[3] = {1.0, 0.0, 0.0}, pv = 0.0;
+  grid_sum3(count, 0u, status, gridDim.x + 1, timeout_ns, part, v, pv, red,
+            [](double (&)[3]) { return 0.0; });
 }
 
 }  // namespace se
@@ -363,16 +458,20 @@ extern "C" int se_selftest_wait_timeout(double timeout_ms) {
   SE_CHECK(timeout_ms > 0 && timeout_ms <= 5000, SE_EINVAL, "timeout_ms must be in (0, 5000]");
   unsigned* bar = nullptr;
   int* status = nullptr;
+  double* part = nullptr;
+  constexpr int NB = 4;
   SE_CUDA(cudaMalloc(&bar, 2 * sizeof(unsigned)));
   SE_CUDA(cudaMalloc(&status, 2 * sizeof(int)));
+  SE_CUDA(cudaMalloc(&part, coarse_partial_doubles(NB + 1) * sizeof(double)));
   SE_CUDA(cudaMemset(bar, 0, 2 * sizeof(unsigned)));
   SE_CUDA(cudaMemset(status, 0, 2 * sizeof(int)));
-  barrier_timeout_kernel<<<4, 32>>>(bar, status, (long long)(timeout_ms * 1e6));
+  barrier_timeout_kernel<<<NB, 32>>>(bar, status, part, (long long)(timeout_ms * 1e6));
   cudaError_t e = cudaDeviceSynchronize();
   int h[2] = {0, 0};
   cudaMemcpy(h, status, sizeof(h), cudaMemcpyDeviceToHost);
   cudaFree(bar);
   cudaFree(status);
+  cudaFree(part);
   SE_CHECK(e == cudaSuccess, SE_ECUDA, "selftest kernel failed: %s", cudaGetErrorString(e));
   if (h[0] == SE_ETIMEOUT) {
     set_error("device wait gave up after %.1f ms (expected in this self-test)", timeout_ms);
@@ -383,14 +482,16 @@ extern "C" int se_selftest_wait_timeout(double timeout_ms) {
 }
 
 // ------------------------------------------------------------------ coarse solve, no allocation
-// Scratch of se_pmg_coarse_solve_noalloc: the five CG vectors (x, r, z, p, q) of at most
-// NOALLOC_MAX_N coarse nodes, the per-block partial sums, and four 32-bit words at the end
-// (barrier count and generation, status, iteration count).  It lives in the library's static
-// device memory: every GPU that loads the library holds it until the process exits.
+// Scratch of se_pmg_coarse_solve_noalloc: the nine pipelined-CG vectors (x, r, u, p, q, s, z and
+// the two alternating w) of at most NOALLOC_MAX_N coarse nodes, the per-block partial sums
+// (two buffers of 4 doubles per block), and four 32-bit words at the end (barrier count and an
+// unused word, status, iteration count).  It lives in the library's static device memory: every
+// GPU that loads the library holds it until the process exits.
 namespace se {
 constexpr int64_t NOALLOC_MAX_N = 1 << 17;        // 131072 coarse (p = 1) global nodes
 constexpr int NOALLOC_MAX_BLOCKS = 1024;
-constexpr int64_t NOALLOC_WORDS = 5 * NOALLOC_MAX_N + 4 * NOALLOC_MAX_BLOCKS + 2;
+constexpr int NOALLOC_VECTORS = 9;
+constexpr int64_t NOALLOC_WORDS = NOALLOC_VECTORS * NOALLOC_MAX_N + 8 * NOALLOC_MAX_BLOCKS + 2;
 static __device__ __align__(256) double g_coarse_scratch[NOALLOC_WORDS];
 
 static std::mutex g_noalloc_mu;
@@ -428,13 +529,10 @@ extern "C" int se_pmg_coarse_solve_noalloc(se_pmg_t P, const double* r, double* 
   cudaStream_t s = as_stream(stream, P->stream);
   CoarseWork w;
   w.nblocks = P->cw.nblocks;  // same grid as se_pmg_coarse_solve: same summation order
-  w.x = base;
-  w.r = base + NOALLOC_MAX_N;
-  w.z = base + 2 * NOALLOC_MAX_N;
-  w.p = base + 3 * NOALLOC_MAX_N;
-  w.q = base + 4 * NOALLOC_MAX_N;
-  w.partial = base + 5 * NOALLOC_MAX_N;
-  w.bar = reinterpret_cast<unsigned*>(base + 5 * NOALLOC_MAX_N + 4 * NOALLOC_MAX_BLOCKS);
+  double** vecs[NOALLOC_VECTORS] = {&w.x, &w.r, &w.u, &w.p, &w.q, &w.s, &w.z, &w.w0, &w.w1};
+  for (int k = 0; k < NOALLOC_VECTORS; ++k) *vecs[k] = base + k * NOALLOC_MAX_N;
+  w.partial = base + NOALLOC_VECTORS * NOALLOC_MAX_N;  // coarse_partial_doubles(nblocks) <= 8 * 1024
+  w.bar = reinterpret_cast<unsigned*>(base + NOALLOC_VECTORS * NOALLOC_MAX_N + 8 * NOALLOC_MAX_BLOCKS);
   w.status = reinterpret_cast<int*>(w.bar + 2);
   // coarse_solve zeroes the barrier and status words before its launch; the vectors are fully
   // written before they are read

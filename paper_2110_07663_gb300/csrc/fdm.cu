@@ -400,33 +400,404 @@ __global__ void __launch_bounds__(512) fdm_kernel(int64_t E, int NE, const int* 
   }
 }
 
-// Shared bytes per element of fdm_kernel<P, T, *> (plus 27 neighbour ids).
+// ------------------------------------------------------------------ FP32: one warp per element
+// The FP32 solve is not bound by the FMA pipe but by instruction issue and shared-memory
+// wavefronts, so its kernel is laid out to issue as few of both as possible:
+//  * one warp owns one element, so phases are ordered by __syncwarp alone, and each row of S is
+//    read once per warp (a broadcast) and applied to every line the lane holds (ceil(PB^2/32)
+//    lines per lane) instead of once per line;
+//  * one window buffer, updated in place: within a phase every lane reads its whole lines before
+//    it writes them back, and no two lanes share a line (lanes past the last line read line 0
+//    and discard what they compute);
+//  * the forward z transform, D^-1 and the backward z transform run on the same lines, so the
+//    eigen-space values stay in registers between them;
+//  * layout a + PB b + PS c with the plane stride PS padded (PS >= PB^2) to the value with the
+//    fewest bank conflicts over this kernel's access patterns, found by counting them for every
+//    candidate PS in [PB^2, PB^2 + 32);
+//  * where each window point comes from (neighbour slot, point in that element, buffer offset)
+//    depends only on p: the block tabulates it once in shared memory, and every element's
+//    gather is a table walk of cp.async copies, all in flight at once; the RAS outputs leave
+//    through shared memory as contiguous, coalesced stores.
+// Per output the arithmetic is one FMA chain over the contracted index in ascending order; D^-1
+// is applied as a product with the hardware reciprocal of lambda_x + lambda_y + lambda_z (one
+// rounding more than a division: far below the FP32 preconditioner's tolerance).
+__host__ __device__ constexpr int fdm32_plane_stride(int PB) {
+  return PB == 4 ? 19 : PB == 5 ? 25 : PB == 6 ? 37 : PB == 7 ? 52 : PB == 8 ? 79 : PB == 9 ? 81
+       : PB == 10 ? 107 : PB == 11 ? 121 : PB == 12 ? 145 : PB * PB;
+}
+
+template <int PB>
+struct Fdm32Dims {
+  static constexpr int N = PB - 2;
+  static constexpr int PS = fdm32_plane_stride(PB);
+  static constexpr int BUF = (PS * PB + 3) / 4 * 4;       // window buffer (16-byte multiple)
+  static constexpr int PBP = (PB + 3) / 4 * 4;             // padded row of S
+  static constexpr int SMAT = PB * PBP;                    // S of one direction
+  static constexpr int LAMP = (3 * PB + 3) / 4 * 4;
+  static constexpr int PER = BUF + 3 * SMAT + LAMP + 28;   // floats per element (+27 neighbour ids)
+  // block tables: window point -> buffer offset | slot << 12 | source point << 17 (PB^3 words),
+  // own point -> buffer offset (N^3 half-words)
+  static constexpr int TAB_BYTES = (PB * PB * PB * 4 + N * N * N * 2 + 15) / 16 * 16;
+  static_assert(PS >= PB * PB, "plane stride below the plane size");
+  static_assert(PS * PB <= 4096 && N * N * N <= 2048, "window table fields overflow");
+};
+
+// acc[j][o] += S[r][o] x[j], o < PB: one padded row of S (float4 reads), NL lines.
+template <int PB, int PBP, int NL>
+__device__ __forceinline__ void fdm32_axpy_row(const float* __restrict__ row, const float (&x)[NL],
+                                               float (&acc)[NL][PB]) {
+#pragma unroll
+  for (int o4 = 0; o4 < PBP; o4 += 4) {
+    const float4 s4 = *reinterpret_cast<const float4*>(row + o4);
+    const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (o4 + k < PB) {
+#pragma unroll
+        for (int j = 0; j < NL; ++j) acc[j][o4 + k] = fmaf(sv[k], x[j], acc[j][o4 + k]);
+      }
+    }
+  }
+}
+
+// out[j] = sum_o S[r][o] v[j][o] (ascending o): one padded row of S, NL lines.
+template <int PB, int PBP, int NL>
+__device__ __forceinline__ void fdm32_dot_row(const float* __restrict__ row, const float (&v)[NL][PB],
+                                              float (&out)[NL]) {
+#pragma unroll
+  for (int j = 0; j < NL; ++j) out[j] = 0.f;
+#pragma unroll
+  for (int o4 = 0; o4 < PBP; o4 += 4) {
+    const float4 s4 = *reinterpret_cast<const float4*>(row + o4);
+    const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (o4 + k < PB) {
+#pragma unroll
+        for (int j = 0; j < NL; ++j) out[j] = fmaf(sv[k], v[j][o4 + k], out[j]);
+      }
+    }
+  }
+}
+
+// 4-byte asynchronous global -> shared copy; valid == false fills the word with zero and reads
+// nothing (src must still be a mapped address).
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Lines of one phase: lane l holds lines l, l + 32, ..., l + 32 (NL - 1); the ones past `count`
+// are read as line 0 and never written.
+template <int NL>
+struct LaneLines {
+  int base[NL];
+  bool ok[NL];
+};
+
+template <int P, int MODE>
+__global__ void __launch_bounds__(256, P <= 6 ? 4 : (P <= 8 ? 3 : 2)) fdm32_warp_kernel(int64_t E, const int* __restrict__ nbr,
+                                                         const float* __restrict__ in,
+                                                         const float* __restrict__ Sg,
+                                                         const float* __restrict__ lamg,
+                                                         const uint8_t* __restrict__ pflag,
+                                                         float* __restrict__ out) {
+  static_assert(MODE == FDM_RAS || MODE == FDM_FULL, "FP32 warp kernel: RAS or full window");
+  constexpr int N = P + 1, N2 = N * N, N3 = N2 * N, PB = P + 3, PB2 = PB * PB, PB3 = PB2 * PB;
+  using Dm = Fdm32Dims<PB>;
+  constexpr int RS = PB, PS = Dm::PS, PBP = Dm::PBP, SMAT = Dm::SMAT;
+  constexpr int C0 = MODE == FDM_RAS ? 1 : 0;
+  constexpr int NC = MODE == FDM_RAS ? N : PB;
+  constexpr int NL = (PB2 + 31) / 32;         // lines per lane: PB^2 lines
+  constexpr int NL2 = (PB * NC + 31) / 32;    // backward y: PB * NC lines
+  constexpr int NL1 = (NC * NC + 31) / 32;    // backward x: NC^2 lines
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned* wtab = reinterpret_cast<unsigned*>(smem_raw);
+  uint16_t* otab = reinterpret_cast<uint16_t*>(wtab + PB3);
+  // ---- block tables (the same for every element of every block)
+  for (int q = threadIdx.x; q < PB3; q += blockDim.x) {
+    const int c = q / PB2, r2 = q - c * PB2, b = r2 / PB, a = r2 - b * PB;
+    const int da = a == 0 ? -1 : (a == PB - 1 ? 1 : 0);
+    const int db = b == 0 ? -1 : (b == PB - 1 ? 1 : 0);
+    const int dc = c == 0 ? -1 : (c == PB - 1 ? 1 : 0);
+    const int ia = da < 0 ? P - 1 : (da > 0 ? 1 : a - 1);
+    const int ib = db < 0 ? P - 1 : (db > 0 ? 1 : b - 1);
+    const int ic = dc < 0 ? P - 1 : (dc > 0 ? 1 : c - 1);
+    const unsigned slot = (unsigned)((da + 1) + 3 * (db + 1) + 9 * (dc + 1));
+    const unsigned src = (unsigned)(ia + N * (ib + N * ic));
+    wtab[q] = (unsigned)(a + RS * b + PS * c) | (slot << 12) | (src << 17);
+  }
+  if constexpr (MODE == FDM_RAS) {
+    for (int q = threadIdx.x; q < N3; q += blockDim.x) {
+      const int k = q / N2, r2 = q - k * N2, j = r2 / N, i = r2 - j * N;
+      otab[q] = (uint16_t)((i + 1) + RS * (j + 1) + PS * (k + 1));
+    }
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (e >= E) return;  // whole warps leave; nothing below synchronises beyond the warp
+  float* buf = reinterpret_cast<float*>(smem_raw + Dm::TAB_BYTES) + (size_t)warp * Dm::PER;
+  float* sS = buf + Dm::BUF;                  // [3][PB][PBP]: S[d][row = window point][mode]
+  float* sl = sS + 3 * SMAT;                  // [3][PB] eigenvalues
+  int* snb = reinterpret_cast<int*>(sl + Dm::LAMP);
+  // All of the element's inputs move by cp.async, so that every copy of the warp is in flight at
+  // once (one memory latency per element rather than one per loop trip).
+  if (lane < 27) snb[lane] = nbr[27 * e + lane];
+  for (int q = lane; q < 3 * SMAT; q += 32) {
+    const int d = q / SMAT, rr = q - d * SMAT, i = rr / PBP, j = rr - i * PBP;
+    if (j < PB) cp_async4(sS + q, Sg + (e * 3 + d) * PB2 + i * PB + j, true);
+    else sS[q] = 0.f;
+  }
+  for (int q = lane; q < 3 * PB; q += 32) cp_async4(sl + q, lamg + e * 3 * PB + q, true);
+  __syncwarp();
+  // ---- gather the extended window (zero outside the domain; Dirichlet values are zero in r)
+#pragma unroll 8
+  for (int q = lane; q < PB3; q += 32) {
+    const unsigned w = wtab[q];
+    const int nb = snb[(w >> 12) & 31u];
+    cp_async4(buf + (w & 4095u), nb >= 0 ? in + ((int64_t)nb * N3 + (w >> 17)) : in, nb >= 0);
+  }
+  cp_async_wait_all();
+  __syncwarp();
+  // ---- forward S_x^T along a: lines (b, c)
+  {
+    float acc[NL][PB];
+    int base[NL];
+    bool ok[NL];
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+      const int ql = lane + 32 * j;
+      ok[j] = ql < PB2;
+      const int c = ql / PB, b = ql - c * PB;
+      base[j] = ok[j] ? RS * b + PS * c : 0;
+#pragma unroll
+      for (int o = 0; o < PB; ++o) acc[j][o] = 0.f;
+    }
+#pragma unroll 2
+    for (int a = 0; a < PB; ++a) {
+      float x[NL];
+#pragma unroll
+      for (int j = 0; j < NL; ++j) x[j] = buf[base[j] + a];
+      fdm32_axpy_row<PB, PBP, NL>(sS + a * PBP, x, acc);
+    }
+#pragma unroll
+    for (int j = 0; j < NL; ++j)
+      if (ok[j]) {
+#pragma unroll
+        for (int o = 0; o < PB; ++o) buf[base[j] + o] = acc[j][o];
+      }
+  }
+  __syncwarp();
+  // ---- forward S_y^T along b: lines (alpha, c)
+  {
+    float acc[NL][PB];
+    int base[NL];
+    bool ok[NL];
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+      const int ql = lane + 32 * j;
+      ok[j] = ql < PB2;
+      const int c = ql / PB, al = ql - c * PB;
+      base[j] = ok[j] ? al + PS * c : 0;
+#pragma unroll
+      for (int o = 0; o < PB; ++o) acc[j][o] = 0.f;
+    }
+#pragma unroll 2
+    for (int b = 0; b < PB; ++b) {
+      float x[NL];
+#pragma unroll
+      for (int j = 0; j < NL; ++j) x[j] = buf[base[j] + RS * b];
+      fdm32_axpy_row<PB, PBP, NL>(sS + SMAT + b * PBP, x, acc);
+    }
+#pragma unroll
+    for (int j = 0; j < NL; ++j)
+      if (ok[j]) {
+#pragma unroll
+        for (int o = 0; o < PB; ++o) buf[base[j] + RS * o] = acc[j][o];
+      }
+  }
+  __syncwarp();
+  // ---- forward S_z^T along c, D^-1, backward S_z along gamma: lines (alpha, beta)
+  {
+    float acc[NL][PB];
+    int base[NL];
+    bool ok[NL];
+    float lxy[NL];
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+      const int ql = lane + 32 * j;
+      ok[j] = ql < PB2;
+      const int be = ql / PB, al = ql - be * PB;
+      base[j] = ok[j] ? al + RS * be : 0;
+      lxy[j] = ok[j] ? sl[al] + sl[PB + be] : 1.f;
+#pragma unroll
+      for (int o = 0; o < PB; ++o) acc[j][o] = 0.f;
+    }
+#pragma unroll 2
+    for (int c = 0; c < PB; ++c) {
+      float x[NL];
+#pragma unroll
+      for (int j = 0; j < NL; ++j) x[j] = buf[base[j] + PS * c];
+      fdm32_axpy_row<PB, PBP, NL>(sS + 2 * SMAT + c * PBP, x, acc);
+    }
+#pragma unroll
+    for (int ga = 0; ga < PB; ++ga) {
+      const float lz = sl[2 * PB + ga];
+#pragma unroll
+      for (int j = 0; j < NL; ++j) acc[j][ga] = acc[j][ga] * rcp_approx(lxy[j] + lz);
+    }
+#pragma unroll 2
+    for (int cc = 0; cc < NC; ++cc) {
+      const int c = C0 + cc;
+      float o[NL];
+      fdm32_dot_row<PB, PBP, NL>(sS + 2 * SMAT + c * PBP, acc, o);
+#pragma unroll
+      for (int j = 0; j < NL; ++j)
+        if (ok[j]) buf[base[j] + PS * c] = o[j];
+    }
+  }
+  __syncwarp();
+  // ---- backward S_y along beta: lines (alpha, c) with c in the output range
+  {
+    float v[NL2][PB];
+    int base[NL2];
+    bool ok[NL2];
+#pragma unroll
+    for (int j = 0; j < NL2; ++j) {
+      const int ql = lane + 32 * j;
+      ok[j] = ql < PB * NC;
+      const int cc = ql / PB, al = ql - cc * PB;
+      base[j] = ok[j] ? al + PS * (C0 + cc) : 0;
+#pragma unroll
+      for (int be = 0; be < PB; ++be) v[j][be] = buf[base[j] + RS * be];
+    }
+#pragma unroll 2
+    for (int bb = 0; bb < NC; ++bb) {
+      const int b = C0 + bb;
+      float o[NL2];
+      fdm32_dot_row<PB, PBP, NL2>(sS + SMAT + b * PBP, v, o);
+#pragma unroll
+      for (int j = 0; j < NL2; ++j)
+        if (ok[j]) buf[base[j] + RS * b] = o[j];
+    }
+  }
+  __syncwarp();
+  // RAS weights of the element's own points (four flag bytes per register), fetched before the
+  // last contraction to hide their latency
+  constexpr int NQ = MODE == FDM_RAS ? (N3 + 31) / 32 : 1;
+  unsigned pf[(NQ + 3) / 4];
+#pragma unroll
+  for (int i = 0; i < (NQ + 3) / 4; ++i) pf[i] = 0u;
+  if constexpr (MODE == FDM_RAS) {
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) {
+      const int q = lane + 32 * i;
+      const unsigned f = q < N3 ? pflag[e * N3 + q] : 0u;
+      pf[i / 4] |= f << (8 * (i % 4));
+    }
+  }
+  // ---- backward S_x along alpha: lines (b, c), both in the output range
+  {
+    float v[NL1][PB];
+    int base[NL1];
+    bool ok[NL1];
+#pragma unroll
+    for (int j = 0; j < NL1; ++j) {
+      const int ql = lane + 32 * j;
+      ok[j] = ql < NC * NC;
+      const int cc = ql / NC, bb = ql - cc * NC;
+      base[j] = ok[j] ? RS * (C0 + bb) + PS * (C0 + cc) : 0;
+#pragma unroll
+      for (int al = 0; al < PB; ++al) v[j][al] = buf[base[j] + al];
+    }
+#pragma unroll 2
+    for (int aa = 0; aa < NC; ++aa) {
+      const int a = C0 + aa;
+      float o[NL1];
+      fdm32_dot_row<PB, PBP, NL1>(sS + a * PBP, v, o);
+#pragma unroll
+      for (int j = 0; j < NL1; ++j)
+        if (ok[j]) buf[base[j] + a] = o[j];
+    }
+  }
+  __syncwarp();
+  // ---- write out, contiguous
+  if constexpr (MODE == FDM_RAS) {
+#pragma unroll
+    for (int n = 0; n < NQ; ++n) {
+      const int q = lane + 32 * n;
+      if (q < N3) {
+        // 1/multiplicity = 2^-mlog, mlog = index of the lowest set bit of the flag's low nibble
+        const int mlog = __ffs((pf[n / 4] >> (8 * (n % 4))) & 0x0F) - 1;
+        const float wt = __int_as_float((127 - mlog) << 23);
+        out[e * N3 + q] = buf[otab[q]] * wt;
+      }
+    }
+  } else {
+    for (int q = lane; q < PB3; q += 32) out[e * PB3 + q] = buf[wtab[q] & 4095u];
+  }
+}
+
+// Shared bytes per element: fdm_kernel<P, double, *> (two window buffers, S^T and S, the
+// eigenvalues, 27 neighbour ids) or fdm32_warp_kernel<P, *> (Fdm32Dims<P + 3>::PER floats, and
+// the block's window tables once per block).
 template <int P, typename T>
 constexpr size_t fdm_smem_per_element() {
-  using Dm = FdmDims<P + 3>;
-  return (2 * Dm::PB3P + 2 * Dm::SROW + (3 * (P + 3) + 3) / 4 * 4) * sizeof(T) + 27 * sizeof(int);
+  if constexpr (sizeof(T) == 4) {
+    return Fdm32Dims<P + 3>::PER * sizeof(float);
+  } else {
+    using Dm = FdmDims<P + 3>;
+    return (2 * Dm::PB3P + 2 * Dm::SROW + (3 * (P + 3) + 3) / 4 * 4) * sizeof(T) + 27 * sizeof(int);
+  }
 }
 
 size_t fdm_smem_bytes(int p, bool fp32, int ne) {
-  size_t per = 0;
+  size_t per = 0, fixed = 0;  // per element; per block (the FP32 kernel's window tables)
   switch (p) {
-#define SE_FDM_SM(PP) \
-  case PP: per = fp32 ? fdm_smem_per_element<PP, float>() : fdm_smem_per_element<PP, double>(); break;
+#define SE_FDM_SM(PP)                                   \
+  case PP:                                              \
+    if (fp32) {                                         \
+      per = fdm_smem_per_element<PP, float>();          \
+      fixed = Fdm32Dims<PP + 3>::TAB_BYTES;             \
+    } else {                                            \
+      per = fdm_smem_per_element<PP, double>();         \
+    }                                                   \
+    break;
     SE_FDM_SM(1) SE_FDM_SM(2) SE_FDM_SM(3) SE_FDM_SM(4) SE_FDM_SM(5)
     SE_FDM_SM(6) SE_FDM_SM(7) SE_FDM_SM(8) SE_FDM_SM(9) SE_FDM_SM(10)
 #undef SE_FDM_SM
     default: per = 0;
   }
-  return per * ne;
+  return per * ne + fixed;
 }
 
-// Elements per block: the tuned value if one is set and valid, else about 400 lines per phase
-// (at most 16 elements).
+// Largest block: 256 threads for fdm32_warp_kernel (its launch bounds), 512 for fdm_kernel.
+int fdm_max_threads(bool fp32) { return fp32 ? 256 : 512; }
+
+// Threads of a block with ne elements: FP32 one warp per element, FP64 one per line of a phase.
+int fdm_block_threads(int p, bool fp32, int ne) {
+  const int PB = p + 3;
+  return fp32 ? 32 * ne : (ne * PB * PB + 31) / 32 * 32;
+}
+
+// Elements per block: the tuned value if one is set and valid; else FP32 8 (one warp each),
+// FP64 about 400 lines per phase (at most 16 elements).
 int fdm_elems_per_block(int p, bool fp32) {
   const int PB = p + 3;
   const int t = tile_get(p, fp32).fdm_ne;
-  if (t >= 1 && t * PB * PB <= 512 && fdm_smem_bytes(p, fp32, t) <= 200 * 1024) return t;
-  int ne = 400 / (PB * PB);
+  if (t >= 1 && t <= 16 && fdm_block_threads(p, fp32, t) <= fdm_max_threads(fp32) &&
+      fdm_smem_bytes(p, fp32, t) <= 200 * 1024)
+    return t;
+  int ne = fp32 ? 8 : 400 / (PB * PB);
   ne = ne < 1 ? 1 : (ne > 16 ? 16 : ne);
   while (ne > 1 && fdm_smem_bytes(p, fp32, ne) > 200 * 1024) --ne;
   return ne;
@@ -435,19 +806,29 @@ int fdm_elems_per_block(int p, bool fp32) {
 template <int P, typename T, int MODE>
 static int launch_fdm(const Level& lv, const T* in, const T* S, const T* lam, T* out,
                       cudaStream_t s) {
-  constexpr int PB = P + 3;
   const int NE = fdm_elems_per_block(P, sizeof(T) == 4);
-  const int threads = ((NE * PB * PB + 31) / 32) * 32;
+  const int threads = fdm_block_threads(P, sizeof(T) == 4, NE);
   const size_t smem = fdm_smem_bytes(P, sizeof(T) == 4, NE);
-  static bool attr = false;
-  if (!attr) {
-    SE_CUDA(cudaFuncSetAttribute(fdm_kernel<P, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 200 * 1024));
-    attr = true;
-  }
   const unsigned blocks = (unsigned)((lv.E + NE - 1) / NE);
-  fdm_kernel<P, T, MODE><<<blocks, threads, smem, s>>>(lv.E, NE, lv.nbr, in, S, lam,
-                                                        lv.fdm_dinv64, lv.pflag, out);
+  if constexpr (sizeof(T) == 4) {
+    static_assert(MODE == FDM_RAS || MODE == FDM_FULL, "FP32 FDM: RAS or full window only");
+    static bool attr = false;
+    if (!attr) {
+      SE_CUDA(cudaFuncSetAttribute(fdm32_warp_kernel<P, MODE>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      attr = true;
+    }
+    fdm32_warp_kernel<P, MODE><<<blocks, threads, smem, s>>>(lv.E, lv.nbr, in, S, lam, lv.pflag, out);
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      SE_CUDA(cudaFuncSetAttribute(fdm_kernel<P, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   200 * 1024));
+      attr = true;
+    }
+    fdm_kernel<P, T, MODE><<<blocks, threads, smem, s>>>(lv.E, NE, lv.nbr, in, S, lam,
+                                                          lv.fdm_dinv64, lv.pflag, out);
+  }
   SE_LAUNCH_CHECK();
   return SE_OK;
 }

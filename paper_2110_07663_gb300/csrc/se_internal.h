@@ -114,7 +114,7 @@ struct Level {
   double* ext64 = nullptr;   // full-window work buffer [E][pb^3] (additive Schwarz)
   float* ext32 = nullptr;
   // assembled operator of the coarsest level: 27-point rows over global nodes
-  double* Ac = nullptr;      // [27][n_global]
+  double* Ac = nullptr;      // [27][n_global]: A D^-1 (columns scaled by cdinv)
   double* cdinv = nullptr;   // [n_global]
   int* g2l = nullptr;        // first local copy of each global node [n_global]
   int* l2g = nullptr;        // global node of each local node [L]
@@ -241,11 +241,13 @@ int prolong_apply(const Level& f, const Level& c, const T* J, const T* ec, T* ef
 // Coarse solve (coarse.cu)
 int coarse_setup(Level& lv, Allocs& allocs, cudaStream_t s);
 struct CoarseWork {
-  double *x, *r, *z, *p, *q, *partial;
-  unsigned* bar;  // [2]: arrival count, generation
-  int* status;    // [2]: error flag, iterations
+  double *x, *r, *u, *p, *q, *s, *z, *w0, *w1;  // pipelined-CG vectors (w alternates)
+  double* partial;  // coarse_partial_doubles(nblocks)
+  unsigned* bar;    // [2]: arrival count (monotonic within a launch), unused
+  int* status;      // [2]: error flag, iterations
   int nblocks;
 };
+size_t coarse_partial_doubles(int nblocks);
 int coarse_alloc(const Level& lv, Allocs& allocs, CoarseWork* w);
 template <class T>
 int coarse_solve(const Level& lv, CoarseWork& w, const T* r_l, T* x_l, double tol, int maxit,
@@ -290,6 +292,8 @@ int ax_local_eo(const Level& lv, const double* u, double* y, cudaStream_t s);
 int pipeline_status_take(int* status);
 int fdm_elems_per_block(int p, bool fp32);
 size_t fdm_smem_bytes(int p, bool fp32, int ne);
+int fdm_block_threads(int p, bool fp32, int ne);
+int fdm_max_threads(bool fp32);
 
 inline unsigned grid_for(int64_t n, int threads, int64_t max_blocks = 1 << 30) {
   int64_t b = (n + threads - 1) / threads;

@@ -55,7 +55,7 @@ size_t footprint_bytes(const se_mesh_desc& d, const se_pmg_desc& pd) {
     }
     if (l + 1 == pd.nlev) {
       const double n = (d.nel[0] + 1.0) * (d.nel[1] + 1.0) * (d.nel[2] + 1.0);
-      total += n * (27 * 8 + 8 + 4 + 5 * 8) + L * 4;
+      total += n * (27 * 8 + 8 + 4 + 9 * 8) + L * 4;
     }
   }
   total += E * 27 * 4 + 1024 * 1024;                               // neighbours, small buffers

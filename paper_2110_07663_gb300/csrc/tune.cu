@@ -41,7 +41,7 @@ static int tune_typed(se_pmg_s* P, int p, se_tile_cfg* out) {
     return SE_ENOMEM;
   }
   int rc = convert<double, T>(lv.X, u, L, s);  // any smooth data of the right size
-  const int N = p + 1, PB = p + 3;
+  const int N = p + 1;
   TileCfg best = tile_get(p, fp32);
   double best_ax = 1e30, best_fdm = 1e30;
   const int ax_cand[] = {1, 2, 3, 4, 6, 8, 12, 16};
@@ -61,7 +61,7 @@ static int tune_typed(se_pmg_s* P, int p, se_tile_cfg* out) {
   const bool have_fdm = fp32 ? lv.S32 != nullptr : lv.S64 != nullptr;
   for (int ne = 1; ne <= 16 && have_fdm && rc == SE_OK; ++ne) {
     const size_t smem = fdm_smem_bytes(p, fp32, ne);
-    if (ne * PB * PB > 512 || smem > 200 * 1024) continue;
+    if (fdm_block_threads(p, fp32, ne) > fdm_max_threads(fp32) || smem > 200 * 1024) continue;
     TileCfg c = best;
     c.fdm_ne = ne;
     tile_set(p, fp32, c);

@@ -97,7 +97,7 @@ def test_pmg_building_blocks(nel, p, schedule, smoother):
         c.close()
 
 
-@pytest.mark.parametrize("smoother", ["ras", "jacobi"])
+@pytest.mark.parametrize("smoother", ["ras", "jacobi", "asm"])
 def test_fp32_vcycle_against_fp64_oracle(smoother):
     c, P, pmg = build((3, 2, 2), 7, (7, 3, 1), smoother, precision=1)
     try:
@@ -107,6 +107,37 @@ def test_fp32_vcycle_against_fp64_oracle(smoother):
         zref = o.vcycle(pmg, r0)
         assert rel_err(c.to_np(z), zref) <= 1e-4
         assert abs(c.se.se_pmg_lambda(P, 0) - pmg.lam[0]) <= 1e-9 * pmg.lam[0]
+    finally:
+        c.se.se_pmg_destroy(P)
+        c.close()
+
+
+@pytest.mark.parametrize("p", range(2, 11))
+@pytest.mark.parametrize("smoother", ["ras", "asm"])
+def test_fp32_schwarz_smoother_all_orders(p, smoother):
+    """FP32 Schwarz smoother (one warp per element: gather, six contractions, D^-1, RAS
+    weights or ASM combine, QQ^T) at every order the library takes, on 12 elements (a block of
+    8 and a partial one), against the FP64 oracle at the FP32 preconditioner tolerance 1e-4."""
+    c, P, pmg = build((3, 2, 2), p, (p, 1), smoother, precision=1)
+    try:
+        r = c.random_continuous(95 + p)
+        out = c.empty()
+        c.se.se_pmg_smooth(P, 0, c.to_gpu(r), out)
+        ref = o.smoother_op(pmg, 0)(r)
+        assert rel_err(c.to_np(out), ref) <= 1e-4
+    finally:
+        c.se.se_pmg_destroy(P)
+        c.close()
+
+
+def test_fp32_ras_mixed_boundaries():
+    bc = ("D", "N", "N", "D", "N", "D")
+    c, P, pmg = build((2, 3, 2), 7, (7, 3, 1), "ras", precision=1, bc=bc)
+    try:
+        r = c.random_continuous(97)
+        out = c.empty()
+        c.se.se_pmg_smooth(P, 0, c.to_gpu(r), out)
+        assert rel_err(c.to_np(out), o.smoother_op(pmg, 0)(r)) <= 1e-4
     finally:
         c.se.se_pmg_destroy(P)
         c.close()

@@ -22,11 +22,13 @@ def test_tune_valid_and_results_tile_independent(p, prec):
         cfg = se.se_tune(p, prec)
         N, PB = p + 1, p + 3
         assert 1 <= cfg.ax_elems_per_block and cfg.ax_elems_per_block * N * N <= 512
-        assert 1 <= cfg.fdm_elems_per_block and cfg.fdm_elems_per_block * PB * PB <= 512
+        # FP64 FDM: one thread per line of every element in the block; FP32: one warp per element
+        fdm_threads = cfg.fdm_elems_per_block * (32 if prec else PB * PB)
+        assert 1 <= cfg.fdm_elems_per_block <= 16 and fdm_threads <= (256 if prec else 512)
         assert cfg.ax_ms > 0 and cfg.fdm_ms > 0
         got = se.se_tune_get(p, prec)
         assert (got.ax_elems_per_block, got.fdm_elems_per_block) == (cfg.ax_elems_per_block, cfg.fdm_elems_per_block)
-        for ax_ne, fdm_ne in [(1, 1), (2, 3)]:
+        for ax_ne, fdm_ne in [(1, 1), (2, 3), (3, 8 if prec else 2)]:
             se.se_tune_set(p, prec, ax_ne, fdm_ne)
             se.se_ax(c.m, u, y1, flags)
             se.se_pmg_smooth(P, 0, u, z1)
