@@ -254,9 +254,11 @@ int se_mesh_footprint_bytes(const se_mesh_desc* desc, const se_pmg_desc* pmg, si
 
 /* A solve server with continuous batching: submitted requests are admitted by a scheduler thread
  * as slots and device memory free up; resident meshes (keyed by the client) are reused with
- * their geometry, smoother data and captured solve graph; the device-driven solves of admitted
- * requests run concurrently on separate non-blocking streams.  Requests whose estimated
- * footprint exceeds the whole budget are refused at submission (SE_EREFUSED). */
+ * their geometry, smoother data and captured solve graph; meshes that are not resident are built
+ * by a pool of builder threads while the scheduler keeps admitting and completing; the
+ * device-driven solves of admitted requests run concurrently on separate non-blocking streams.
+ * Requests whose estimated footprint exceeds the whole budget are refused at submission
+ * (SE_EREFUSED). */
 enum { SE_RHS_MODES = 0, SE_RHS_HOST = 1 };
 typedef struct se_request {
   se_mesh_desc mesh;       /* mesh to build when mesh_key is not resident (vertex_xyz unused) */
@@ -283,7 +285,8 @@ typedef struct se_result {
 } se_result;
 typedef struct se_serve_cfg {
   size_t hbm_budget;       /* bytes of device memory the resident meshes may occupy */
-  int max_slots;           /* requests solved concurrently */
+  int max_slots;           /* requests in flight (being set up or solved) at once */
+  int builders;            /* threads that build new meshes concurrently (0: min(4, max_slots)) */
 } se_serve_cfg;
 typedef struct se_serve_stats {
   int64_t submitted, completed, refused, failed, pending;

@@ -115,12 +115,10 @@ static int launch_ax(const Level& lv, const T* u, T* y, const T* G, const T* D,
   const int NE = ax_elems_per_block(N - 1, sizeof(T) == 4);
   const int threads = NE * N * N;
   const size_t smem = (N * N + (size_t)NE * 3 * N * N * N) * sizeof(T);
-  static bool attr_set = false;
-  if (!attr_set) {
-    SE_CUDA(cudaFuncSetAttribute(ax_local_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 200 * 1024));
-    attr_set = true;
-  }
+  // set once per kernel (thread-safe static initialisation)
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      ax_local_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  SE_CUDA(attr);
   const unsigned blocks = (unsigned)((lv.E + NE - 1) / NE);
   ax_local_kernel<N, T><<<blocks, threads, smem, s>>>(lv.E, NE, u, G, lv.L, D, y, pflag);
   SE_LAUNCH_CHECK();

@@ -141,12 +141,9 @@ static int launch_ax_eo(const Level& lv, const double* u, double* y, const doubl
   const int NE = ax_elems_per_block(N - 1, false);
   const int threads = NE * N * N;
   const size_t smem = (4 * H * H + (size_t)NE * 5 * N * N * N) * sizeof(double);
-  static bool attr = false;
-  if (!attr) {
-    SE_CUDA(cudaFuncSetAttribute(ax_eo_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 200 * 1024));
-    attr = true;
-  }
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(ax_eo_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  SE_CUDA(attr);
   const unsigned blocks = (unsigned)((lv.E + NE - 1) / NE);
   ax_eo_kernel<N><<<blocks, threads, smem, s>>>(lv.E, NE, u, lv.G64, lv.L, tables, y);
   SE_LAUNCH_CHECK();

@@ -185,17 +185,11 @@ static int launch_ax_tma(const Level& lv, const float* u, float* y, int NE, cuda
   constexpr int N3 = N * N * N;
   const int threads = NE * N * N;
   const size_t smem = (size_t)(16 * NE * N3 + ((N * N + 3) / 4) * 4 + 4) * sizeof(float) + 2 * sizeof(uint64_t);
-  static bool attr = false;
-  static int per_sm = 0;
-  static int attr_ne = -1;
-  if (!attr) {
-    SE_CUDA(cudaFuncSetAttribute(ax_tma_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-    attr = true;
-  }
-  if (attr_ne != NE) {
-    SE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ax_tma_kernel<N>, threads, smem));
-    attr_ne = NE;
-  }
+  static const cudaError_t attr =
+      cudaFuncSetAttribute(ax_tma_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  SE_CUDA(attr);
+  int per_sm = 0;
+  SE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ax_tma_kernel<N>, threads, smem));
   SE_CHECK(per_sm >= 1, SE_ECUDA, "ax_tma: no resident block fits (NE=%d)", NE);
   int dev = 0, sms = 0;
   SE_CUDA(cudaGetDevice(&dev));

@@ -1,4 +1,5 @@
 // Errors, allocations, 1D GLL basis, SplitMix64, reduction scratch and kernel profiling.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
@@ -20,22 +21,60 @@ void set_error(const char* fmt, ...) {
 }
 
 void Allocs::release() {
-  for (void* p : ptrs) cudaFree(p);
+  for (void* p : ptrs) cudaFreeAsync(p, stream);
   ptrs.clear();
   bytes = 0;
 }
 
-int dmalloc_bytes(Allocs& a, void** p, size_t bytes) {
-  cudaError_t e = cudaMalloc(p, bytes);
+int dmalloc_transient(void** p, size_t bytes, cudaStream_t s) {
+  cudaError_t e = cudaMallocAsync(p, bytes, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    set_error("cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    set_error("device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    if (*p) cudaFreeAsync(*p, s);
     *p = nullptr;
     return SE_ENOMEM;
   }
+  return SE_OK;
+}
+
+int dmalloc_bytes(Allocs& a, void** p, size_t bytes) {
+  *p = nullptr;
+  SE_TRY(dmalloc_transient(p, bytes, a.stream));
   a.ptrs.push_back(*p);
   a.bytes += bytes;
   return SE_OK;
+}
+
+void dfree(Allocs& a, void* p, size_t bytes) {
+  auto it = std::find(a.ptrs.begin(), a.ptrs.end(), p);
+  if (it == a.ptrs.end()) return;
+  a.ptrs.erase(it);
+  a.bytes -= bytes;
+  cudaFreeAsync(p, a.stream);
+}
+
+static std::mutex g_pin_mu;
+static std::vector<double*> g_pin_free;
+
+int pinned_scalars(double** out) {
+  {
+    std::lock_guard<std::mutex> g(g_pin_mu);
+    if (!g_pin_free.empty()) {
+      *out = g_pin_free.back();
+      g_pin_free.pop_back();
+      return SE_OK;
+    }
+  }
+  SE_CUDA(cudaMallocHost(out, SCAL_SLOTS * sizeof(double)));
+  return SE_OK;
+}
+
+void pinned_release(double* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> g(g_pin_mu);
+  g_pin_free.push_back(p);
 }
 
 // ------------------------------------------------------------------ GLL basis (Sec. 2.1)
@@ -122,7 +161,7 @@ int scratch_alloc(Allocs& a, Scratch* s) {
   SE_TRY(dmalloc(a, &s->scal, SCAL_SLOTS));
   SE_CUDA(cudaMemset(s->counter, 0, sizeof(unsigned)));
   SE_CUDA(cudaMemset(s->scal, 0, SCAL_SLOTS * sizeof(double)));
-  SE_CUDA(cudaMallocHost(&s->hscal, SCAL_SLOTS * sizeof(double)));
+  SE_TRY(pinned_scalars(&s->hscal));
   return SE_OK;
 }
 

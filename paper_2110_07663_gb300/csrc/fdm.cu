@@ -812,20 +812,14 @@ static int launch_fdm(const Level& lv, const T* in, const T* S, const T* lam, T*
   const unsigned blocks = (unsigned)((lv.E + NE - 1) / NE);
   if constexpr (sizeof(T) == 4) {
     static_assert(MODE == FDM_RAS || MODE == FDM_FULL, "FP32 FDM: RAS or full window only");
-    static bool attr = false;
-    if (!attr) {
-      SE_CUDA(cudaFuncSetAttribute(fdm32_warp_kernel<P, MODE>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      attr = true;
-    }
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        fdm32_warp_kernel<P, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    SE_CUDA(attr);
     fdm32_warp_kernel<P, MODE><<<blocks, threads, smem, s>>>(lv.E, lv.nbr, in, S, lam, lv.pflag, out);
   } else {
-    static bool attr = false;
-    if (!attr) {
-      SE_CUDA(cudaFuncSetAttribute(fdm_kernel<P, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   200 * 1024));
-      attr = true;
-    }
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        fdm_kernel<P, T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    SE_CUDA(attr);
     fdm_kernel<P, T, MODE><<<blocks, threads, smem, s>>>(lv.E, NE, lv.nbr, in, S, lam,
                                                           lv.fdm_dinv64, lv.pflag, out);
   }

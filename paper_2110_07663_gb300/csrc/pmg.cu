@@ -182,19 +182,21 @@ static int arnoldi_level(se_pmg_s* P, int l, cudaStream_t s, double* lam_out) {
   std::vector<double*> Vv(steps + 1, nullptr);
   double *w = nullptr, *sv = nullptr;
   int st = SE_OK;
+  // transient vectors, stream-ordered on s (freeing them does not wait for other streams)
   auto cleanup = [&]() {
     for (double* v : Vv)
-      if (v) cudaFree(v);
-    if (w) cudaFree(w);
-    if (sv) cudaFree(sv);
+      if (v) cudaFreeAsync(v, s);
+    if (w) cudaFreeAsync(w, s);
+    if (sv) cudaFreeAsync(sv, s);
   };
   for (auto& v : Vv)
-    if (cudaMalloc(&v, L * sizeof(double)) != cudaSuccess) {
+    if (dmalloc_transient(reinterpret_cast<void**>(&v), L * sizeof(double), s) != SE_OK) {
       cleanup();
       set_error("Arnoldi: out of device memory");
       return SE_ENOMEM;
     }
-  if (cudaMalloc(&w, L * sizeof(double)) != cudaSuccess || cudaMalloc(&sv, L * sizeof(double)) != cudaSuccess) {
+  if (dmalloc_transient(reinterpret_cast<void**>(&w), L * sizeof(double), s) != SE_OK ||
+      dmalloc_transient(reinterpret_cast<void**>(&sv), L * sizeof(double), s) != SE_OK) {
     cleanup();
     set_error("Arnoldi: out of device memory");
     return SE_ENOMEM;
@@ -364,11 +366,12 @@ int se_pmg_setup(se_mesh_t m, const se_pmg_desc* desc, se_pmg_t* out) {
   P->desc = d;
   P->nlev = d.nlev;
   P->stream = m->stream;
+  P->allocs.stream = P->stream;
   int st = pmg_build(P);
   if (st != SE_OK) {
     cudaStreamSynchronize(P->stream);
     P->allocs.release();
-    if (P->scratch.hscal) cudaFreeHost(P->scratch.hscal);
+    pinned_release(P->scratch.hscal);
     delete P;
     return st;
   }
@@ -381,7 +384,7 @@ int se_pmg_destroy(se_pmg_t P) {
   cudaStreamSynchronize(P->stream);
   P->release_graph();
   P->allocs.release();
-  if (P->scratch.hscal) cudaFreeHost(P->scratch.hscal);
+  pinned_release(P->scratch.hscal);
   delete P;
   return SE_OK;
 }

@@ -43,13 +43,24 @@ void set_error(const char* fmt, ...);
 #define SE_LAUNCH_CHECK() SE_CUDA(cudaGetLastError())
 
 // ------------------------------------------------------------------ device allocations
+// Device allocations of one handle, stream-ordered on the handle's stream: allocating waits for
+// that stream only, and freeing (release, dfree) is queued on it, so neither waits for the rest of
+// the device (a plain cudaFree would wait for every stream, e.g. other requests' solves).
 struct Allocs {
   std::vector<void*> ptrs;
   size_t bytes = 0;
+  cudaStream_t stream = nullptr;  // owner's stream; set before the first allocation
   void release();
 };
 
 int dmalloc_bytes(Allocs& a, void** p, size_t bytes);
+void dfree(Allocs& a, void* p, size_t bytes);
+// Stream-ordered device buffer outside any handle (usable on every stream once this returns).
+int dmalloc_transient(void** p, size_t bytes, cudaStream_t s);
+// Pinned host scalars, recycled through a process-wide free list (cudaFreeHost may wait for the
+// whole device).
+int pinned_scalars(double** out);
+void pinned_release(double* p);
 template <class T>
 inline int dmalloc(Allocs& a, T** p, size_t count) {
   return dmalloc_bytes(a, reinterpret_cast<void**>(p), count * sizeof(T) + (count == 0));

@@ -3,11 +3,14 @@
 // Requests (a mesh description with a client-chosen key, a preconditioner description and a
 // right-hand side) are queued at submission.  A scheduler thread admits them as slots and device
 // memory free up: a request whose mesh is resident reuses it (geometry, FDM factors, Krylov work
-// space and its captured solve graph stay on the device); otherwise the mesh is built if its
-// estimated footprint fits the HBM budget, evicting idle resident meshes least recently used
-// first.  Each admitted request launches its device-driven solve graph on its mesh's own
-// non-blocking stream, so solves of different requests overlap on the GPU; completions are
-// detected with events.  Latency = completion time - submission time.
+// space and its captured solve graph stay on the device); otherwise the mesh is handed to a pool
+// of builder threads if its estimated footprint fits the HBM budget (reserved while it is built),
+// evicting idle resident meshes least recently used first.  The scheduler keeps admitting and
+// completing while meshes are built, and a request for a key that is being built waits for it.
+// Each admitted request launches its device-driven solve graph on its mesh's own non-blocking
+// stream, so solves and set-ups of different requests overlap on the GPU; device memory is
+// allocated and freed in stream order, so neither set-up nor eviction waits for other requests'
+// work.  Completions are detected with events.  Latency = completion time - submission time.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -94,6 +97,10 @@ struct se_server_s {
   std::mutex mu;
   std::condition_variable cv;
   std::thread thr;
+  std::vector<std::thread> builders;
+  std::deque<se::Ticket*> build_q;      // new meshes waiting for a builder
+  std::vector<uint64_t> building_keys;  // keys being built (queued or in progress)
+  int building = 0;
   bool stop = false;
   uint64_t next_id = 1;
   std::deque<se::Ticket*> queue;
@@ -112,9 +119,11 @@ namespace se {
 
 static void destroy_resident(Resident* r) {
   if (r->P) se_pmg_destroy(r->P);
-  if (r->m) se_mesh_destroy(r->m);
-  if (r->b) cudaFree(r->b);
-  if (r->x) cudaFree(r->x);
+  if (r->m) {
+    if (r->b) cudaFreeAsync(r->b, r->m->stream);
+    if (r->x) cudaFreeAsync(r->x, r->m->stream);
+    se_mesh_destroy(r->m);
+  }
   delete r;
 }
 
@@ -142,8 +151,8 @@ static int build_resident(const se_request& q, Resident** out) {
   if (rc == SE_OK) rc = se_pmg_setup(r->m, &q.pmg, &r->P);
   if (rc == SE_OK) {
     r->L = r->m->fine.L;
-    if (cudaMalloc(&r->b, r->L * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&r->x, r->L * sizeof(double)) != cudaSuccess) {
+    if (dmalloc_transient(reinterpret_cast<void**>(&r->b), r->L * sizeof(double), r->m->stream) != SE_OK ||
+        dmalloc_transient(reinterpret_cast<void**>(&r->x), r->L * sizeof(double), r->m->stream) != SE_OK) {
       set_error("server: out of device memory for a request's vectors");
       rc = SE_ENOMEM;
     }
@@ -217,14 +226,17 @@ static void scheduler(se_server_s* S) {
       }
     }
     if (progress) S->cv.notify_all();
-    // admissions (in arrival order; a request whose mesh is busy waits without blocking others)
+    // admissions (in arrival order; a request whose mesh is busy or being built waits without
+    // blocking others)
     size_t qi = 0;
-    while (qi < S->queue.size() && (int)S->running.size() < S->cfg.max_slots) {
+    while (qi < S->queue.size() && (int)S->running.size() + S->building < S->cfg.max_slots) {
       Ticket* t = S->queue[qi];
       Resident* r = nullptr;
       for (Resident* x : S->residents)
         if (x->key == t->req.mesh_key) r = x;
-      if (r && r->busy) {
+      const bool key_building = std::find(S->building_keys.begin(), S->building_keys.end(),
+                                          t->req.mesh_key) != S->building_keys.end();
+      if ((r && r->busy) || key_building) {
         ++qi;
         continue;
       }
@@ -232,30 +244,16 @@ static void scheduler(se_server_s* S) {
         const size_t need = footprint_bytes(t->req.mesh, t->req.pmg);
         if (!make_room(S, need)) break;  // wait for memory to free up
         S->queue.erase(S->queue.begin() + qi);
-        S->used += need;                 // reserved while the mesh is built without the lock
-        lk.unlock();
-        const double tb = now_ms();
-        int rc = build_resident(t->req, &r);
-        t->setup_ms = now_ms() - tb;
-        lk.lock();
-        S->used -= need;
-        if (rc != SE_OK) {
-          t->status = rc;
-          t->done = true;
-          t->t_done = now_ms();
-          ++S->failed;
-          S->cv.notify_all();
-          progress = true;
-          continue;
-        }
-        S->residents.push_back(r);
-        S->used += r->bytes;
-        ++S->created;
-        t->is_new_mesh = true;
-      } else {
-        S->queue.erase(S->queue.begin() + qi);
-        ++S->reused;
+        S->used += need;                 // reserved while the mesh is built
+        ++S->building;
+        S->building_keys.push_back(t->req.mesh_key);
+        S->build_q.push_back(t);
+        S->cv.notify_all();
+        progress = true;
+        continue;
       }
+      S->queue.erase(S->queue.begin() + qi);
+      ++S->reused;
       r->busy = true;
       t->res = r;
       t->t_start = now_ms();
@@ -282,6 +280,53 @@ static void scheduler(se_server_s* S) {
   (void)dev;
 }
 
+// Builds the meshes of queued requests (set-up kernels on the new mesh's own stream), starts
+// their solves, and hands them to the scheduler's running list.
+static void builder(se_server_s* S) {
+  std::unique_lock<std::mutex> lk(S->mu);
+  for (;;) {
+    S->cv.wait(lk, [S] { return S->stop || !S->build_q.empty(); });
+    if (S->build_q.empty()) break;  // stopping, nothing left to build
+    Ticket* t = S->build_q.front();
+    S->build_q.pop_front();
+    const size_t need = footprint_bytes(t->req.mesh, t->req.pmg);
+    lk.unlock();
+    const double tb = now_ms();
+    Resident* r = nullptr;
+    int rc = build_resident(t->req, &r);
+    t->setup_ms = now_ms() - tb;
+    if (rc == SE_OK) {
+      // not yet visible to the scheduler: its first solve starts outside the lock
+      r->busy = true;
+      t->res = r;
+      t->t_start = now_ms();
+      rc = start_ticket(t);
+      if (rc != SE_OK) r->busy = false;
+    }
+    lk.lock();
+    S->used -= need;
+    --S->building;
+    auto it = std::find(S->building_keys.begin(), S->building_keys.end(), t->req.mesh_key);
+    if (it != S->building_keys.end()) S->building_keys.erase(it);
+    if (r) {
+      S->residents.push_back(r);
+      S->used += r->bytes;
+      ++S->created;
+      t->is_new_mesh = true;
+    }
+    if (rc != SE_OK) {
+      t->status = rc;
+      t->done = true;
+      t->t_done = now_ms();
+      ++S->failed;
+    } else {
+      S->running.push_back(t);
+      S->max_running = std::max(S->max_running, (int)S->running.size());
+    }
+    S->cv.notify_all();
+  }
+}
+
 }  // namespace se
 
 using namespace se;
@@ -297,15 +342,22 @@ int se_mesh_footprint_bytes(const se_mesh_desc* desc, const se_pmg_desc* pmg, si
 int se_serve_create(const se_serve_cfg* cfg, se_server_t* out) {
   SE_CHECK(cfg && out, SE_EINVAL, "se_serve_create: null argument");
   SE_CHECK(cfg->max_slots >= 1 && cfg->max_slots <= 256, SE_EINVAL, "se_serve_create: max_slots");
+  SE_CHECK(cfg->builders >= 0 && cfg->builders <= 64, SE_EINVAL, "se_serve_create: builders");
   SE_CHECK(cfg->hbm_budget > 0, SE_EINVAL, "se_serve_create: hbm_budget");
   auto* S = new se_server_s();
   S->cfg = *cfg;
   int dev = 0;
   cudaGetDevice(&dev);
+  const int nb = cfg->builders > 0 ? cfg->builders : std::min(4, cfg->max_slots);
   S->thr = std::thread([S, dev] {
     cudaSetDevice(dev);
     scheduler(S);
   });
+  for (int i = 0; i < nb; ++i)
+    S->builders.emplace_back([S, dev] {
+      cudaSetDevice(dev);
+      builder(S);
+    });
   *out = S;
   return SE_OK;
 }
@@ -403,7 +455,7 @@ int se_serve_stats(se_server_t S, se_serve_summary* out) {
   out->completed = S->completed;
   out->refused = S->refused;
   out->failed = S->failed;
-  out->pending = (int64_t)S->queue.size() + (int64_t)S->running.size();
+  out->pending = (int64_t)S->queue.size() + (int64_t)S->running.size() + S->building;
   out->p50_ms = pct(0.50);
   out->p99_ms = pct(0.99);
   out->mean_ms = lat.empty() ? 0.0 : mean / lat.size();
@@ -424,6 +476,7 @@ int se_serve_destroy(se_server_t S) {
     S->stop = true;
     S->cv.notify_all();
   }
+  for (auto& b : S->builders) b.join();  // builders finish the meshes already handed to them
   S->thr.join();
   for (Ticket* t : S->running) cudaEventSynchronize(t->ev);
   for (auto& kv : S->tickets) {

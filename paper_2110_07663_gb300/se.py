@@ -83,7 +83,7 @@ class se_result(C.Structure):
 
 
 class se_serve_cfg(C.Structure):
-    _fields_ = [("hbm_budget", C.c_size_t), ("max_slots", C.c_int)]
+    _fields_ = [("hbm_budget", C.c_size_t), ("max_slots", C.c_int), ("builders", C.c_int)]
 
 
 class se_serve_summary(C.Structure):
@@ -433,9 +433,9 @@ def make_request(mdesc, mesh_key, pdesc, modes=(1, 1, 1), amplitude=1.0, b_host=
     return q
 
 
-def se_serve_create(hbm_budget, max_slots):
+def se_serve_create(hbm_budget, max_slots, builders=0):
     c = se_serve_cfg()
-    c.hbm_budget, c.max_slots = int(hbm_budget), int(max_slots)
+    c.hbm_budget, c.max_slots, c.builders = int(hbm_budget), int(max_slots), int(builders)
     h = _vp()
     _check(lib.se_serve_create(C.byref(c), C.byref(h)))
     return h.value
