@@ -163,98 +163,196 @@ int ax_local(const Level& lv, const T* u, T* y, bool mask_in, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ QQ^T + mask
-// One thread per group of local copies of a global node; the copies are summed in index order
-// (deterministic) and the sum written back to each.  Groups on Dirichlet faces (first id stored
-// as ~id) are zeroed when masking; single-copy Dirichlet nodes follow the groups.
-template <typename T, int M>
-__device__ __forceinline__ void gs_group(const int* __restrict__ g, T* __restrict__ u, bool mask) {
-  int id[M];
+// The mesh is a box lattice of elements, so the copies of a global node are the products of its
+// per-direction copies, and QQ^T factors into three sweeps, one per direction: a sweep adds the
+// two copies on either side of every element interface normal to its direction and writes the
+// sum to both.  After the x sweep each copy holds the sum over its x-neighbours; the y sweep adds
+// those partial sums across y-interfaces (edge nodes: 4 copies); the z sweep across z-interfaces
+// (corners: 8).  Every copy ends with the sum over all copies of its node, and all copies of a
+// node hold bitwise the same value (each pair writes one sum to both sides).  No index map is
+// read, and every access is laid out for the element-major, i-fastest layout:
+//   x: a warp holds whole rows of one k-plane for a run of elements along x and exchanges the
+//      interface copies by shuffles (below);
+//   y: lanes run along i: rows of N contiguous copies;
+//   z: lanes run along (i, j): planes of N^2 contiguous copies.
+// Masking (Dirichlet) zeroes the copies on Dirichlet faces first (a node on such a face has all
+// its copies there), so the sweeps then add zeros for masked nodes.
+constexpr int GS_X_SEG = 8;  // x-interfaces per warp
+
+// x sweep: a warp holds R = 32/N consecutive rows (j, k) of an element (lane = (row, i); the
+// element's N^2 rows are contiguous) for a run of consecutive elements along x, loaded coalesced
+// (R N contiguous values per element), one value per lane per element kept in registers; the
+// two copies of each x-interface (lane i = p of element m, lane i = 0 of element m + 1, same
+// row) swap by one shuffle and both store their sum (a + b == b + a exactly: both copies get the
+// same bits).  Every value of the vector
+// is read once, in full sectors.  A warp takes a run of GS_X_SEG interfaces (runs of one x-row
+// overlap by one element, and no two runs write the same copy: a run writes the row ends of its
+// interfaces only); it always loads GS_X_SEG + 1 elements (indices clamped to the last element of
+// the row) so that all loads are issued back to back.
+template <typename T, int N>
+__global__ void __launch_bounds__(256) gs_sweep_x(int nx, int ny, int nz, T* __restrict__ u) {
+  constexpr int N3 = N * N * N, R = 32 / N, NG = (N * N + R - 1) / R, SEG = GS_X_SEG;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int nseg = (nx - 1 + SEG - 1) / SEG;
+  const int64_t items = (int64_t)ny * nz * NG * nseg;  // (row group, run, element row along x)
+  if (warp >= items) return;                           // whole warps
+  const int grp = (int)(warp % NG);
+  const int64_t q = warp / NG;
+  const int seg = (int)(q % nseg);
+  const int64_t row_e = q / nseg;                      // ey + ny ez
+  const int r = lane / N, i = lane - r * N;
+  const int jk = grp * R + r;                          // row j + N k of the element
+  const bool on = r < R && jk < N * N;
+  const int rowbase = r * N;                           // lane of (row r, i = 0)
+  const int64_t off = on ? (int64_t)i + (int64_t)N * jk : 0;
+  const int ex0 = seg * SEG;
+  const int cnt = min(SEG, nx - 1 - ex0);              // interfaces of this run
+  const int64_t e0 = (int64_t)nx * row_e + ex0;
+  T v[SEG + 1];
 #pragma unroll
-  for (int q = 0; q < M; ++q) id[q] = g[q];
-  const bool msk = id[0] < 0;
-  if (msk) id[0] = ~id[0];
-  if (msk && mask) {
+  for (int m = 0; m <= SEG; ++m) v[m] = u[(e0 + min(m, cnt)) * N3 + off];
+  // lane (r, p) holds the left copy (element m), lane (r, 0) the right copy (element m + 1):
+  // one shuffle swaps them, one store writes both (each lane its own element)
+  const bool left = i == N - 1, right = i == 0;
+  const int partner = min(left ? rowbase : rowbase + N - 1, 31);
 #pragma unroll
-    for (int q = 0; q < M; ++q) u[id[q]] = T(0);
-    return;
+  for (int m = 0; m < SEG; ++m) {
+    if (m >= cnt) break;
+    const T mine = right ? v[m + 1] : v[m];
+    const T other = __shfl_sync(0xffffffffu, mine, partner);
+    if (on && (left || right)) u[(e0 + m + (right ? 1 : 0)) * N3 + off] = mine + other;
   }
-  T v[M];
-#pragma unroll
-  for (int q = 0; q < M; ++q) v[q] = u[id[q]];
-  T sacc = v[0];
-#pragma unroll
-  for (int q = 1; q < M; ++q) sacc += v[q];
-#pragma unroll
-  for (int q = 0; q < M; ++q) u[id[q]] = sacc;
 }
 
-// Pairs (the bulk of the groups) are processed four per thread, interleaved: thread t of T
-// takes pairs t, t+T, t+2T, t+3T, so every load instruction of a warp still covers 32
-// neighbouring pairs (shared sectors) while each thread keeps eight independent value loads in
-// flight.  Quads, octets and single Dirichlet copies follow, one group per thread.
-constexpr int GS_PAIRS_PER_THREAD = 4;
+template <typename T, int N>
+__global__ void gs_sweep_y(int nx, int ny, int nz, T* __restrict__ u) {
+  constexpr int N3 = N * N * N;
+  const int nif = ny - 1;
+  const int64_t total = (int64_t)N * N * nx * nif * nz;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const int i = (int)(t % N);
+  int64_t q = t / N;
+  const int k = (int)(q % N);
+  q /= N;
+  const int ex = (int)(q % nx);
+  q /= nx;
+  const int ey = (int)(q % nif);
+  const int ez = (int)(q / nif);
+  const int64_t e = ex + (int64_t)nx * (ey + (int64_t)ny * ez);
+  const int64_t ia = e * N3 + i + N * ((N - 1) + N * k);      // element e, j = p
+  const int64_t ib = (e + nx) * N3 + i + (int64_t)N * N * k;  // element e + nx, j = 0
+  const T sum = u[ia] + u[ib];
+  u[ia] = sum;
+  u[ib] = sum;
+}
 
-template <typename T>
-__global__ void gs_kernel(int64_t n2, int64_t n4, int64_t n8, int64_t n1,
-                          const int* __restrict__ ids, T* __restrict__ u, bool mask) {
-  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t T2 = (n2 + GS_PAIRS_PER_THREAD - 1) / GS_PAIRS_PER_THREAD;
-  if (t < T2) {
-    int a[GS_PAIRS_PER_THREAD], b[GS_PAIRS_PER_THREAD];
-    bool m[GS_PAIRS_PER_THREAD], on[GS_PAIRS_PER_THREAD];
-#pragma unroll
-    for (int k = 0; k < GS_PAIRS_PER_THREAD; ++k) {
-      const int64_t g = t + k * T2;
-      on[k] = g < n2;
-      const int2 q = on[k] ? *reinterpret_cast<const int2*>(ids + 2 * g) : make_int2(0, 0);
-      m[k] = q.x < 0;
-      a[k] = m[k] ? ~q.x : q.x;
-      b[k] = q.y;
-    }
-    T va[GS_PAIRS_PER_THREAD], vb[GS_PAIRS_PER_THREAD];
-#pragma unroll
-    for (int k = 0; k < GS_PAIRS_PER_THREAD; ++k) {
-      va[k] = on[k] ? u[a[k]] : T(0);
-      vb[k] = on[k] ? u[b[k]] : T(0);
-    }
-#pragma unroll
-    for (int k = 0; k < GS_PAIRS_PER_THREAD; ++k) {
-      if (!on[k]) continue;
-      const T sum = (m[k] && mask) ? T(0) : va[k] + vb[k];
-      u[a[k]] = sum;
-      u[b[k]] = sum;
-    }
+template <typename T, int N>
+__global__ void gs_sweep_z(int nx, int ny, int nz, T* __restrict__ u) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  const int nif = nz - 1;
+  const int64_t total = (int64_t)N2 * nx * ny * nif;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const int ij = (int)(t % N2);
+  const int64_t e = t / N2;  // elements with ez < nz - 1, in order
+  const int64_t ia = e * N3 + ij + N2 * (N - 1);          // element e, k = p
+  const int64_t ib = (e + (int64_t)nx * ny) * N3 + ij;    // element e + nx ny, k = 0
+  const T sum = u[ia] + u[ib];
+  u[ia] = sum;
+  u[ib] = sum;
+}
+
+// Zero the copies on the Dirichlet faces (bit f of `bits`: face f = x0, x1, y0, y1, z0, z1).
+// Thread: (face, element on the face, point of the element's face).
+template <typename T, int N>
+__global__ void gs_mask_faces(int nx, int ny, int nz, int bits, T* __restrict__ u) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t fx = (int64_t)ny * nz * N2, fy = (int64_t)nx * nz * N2, fz = (int64_t)nx * ny * N2;
+  int64_t r = t;
+  int f;
+  if (r < 2 * fx) {
+    f = r < fx ? 0 : 1;
+    r -= f * fx;
+  } else if ((r -= 2 * fx) < 2 * fy) {
+    f = r < fy ? 2 : 3;
+    r -= (f - 2) * fy;
+  } else if ((r -= 2 * fy) < 2 * fz) {
+    f = r < fz ? 4 : 5;
+    r -= (f - 4) * fz;
+  } else {
     return;
   }
-  t -= T2;
-  ids += 2 * n2;
-  if (t < n4) {
-    gs_group<T, 4>(ids + 4 * t, u, mask);
-    return;
+  if (!((bits >> f) & 1)) return;
+  const int a = (int)(r % N), b = (int)((r / N) % N);
+  const int64_t el = r / N2;  // element index along the face's two directions
+  int ex, ey, ez, i, j, k;
+  const int side = f & 1;
+  if (f < 2) {
+    ey = (int)(el % ny); ez = (int)(el / ny); ex = side ? nx - 1 : 0;
+    i = side ? N - 1 : 0; j = a; k = b;
+  } else if (f < 4) {
+    ex = (int)(el % nx); ez = (int)(el / nx); ey = side ? ny - 1 : 0;
+    j = side ? N - 1 : 0; i = a; k = b;
+  } else {
+    ex = (int)(el % nx); ey = (int)(el / nx); ez = side ? nz - 1 : 0;
+    k = side ? N - 1 : 0; i = a; j = b;
   }
-  t -= n4;
-  ids += 4 * n4;
-  if (t < n8) {
-    gs_group<T, 8>(ids + 8 * t, u, mask);
-    return;
+  const int64_t e = ex + (int64_t)nx * (ey + (int64_t)ny * ez);
+  u[e * N3 + i + N * (j + N * k)] = T(0);
+}
+
+template <typename T, int N>
+static int gs_sweeps(const Level& lv, T* u, bool mask, cudaStream_t s) {
+  const int nx = lv.nel[0], ny = lv.nel[1], nz = lv.nel[2];
+  constexpr int N2 = N * N;
+  if (mask) {
+    int bits = 0;
+    for (int f = 0; f < 6; ++f)
+      if (lv.bc[f] == SE_BC_DIRICHLET) bits |= 1 << f;
+    if (bits) {
+      const int64_t n = 2 * N2 * ((int64_t)ny * nz + (int64_t)nx * nz + (int64_t)nx * ny);
+      gs_mask_faces<T, N><<<grid_for(n, 256), 256, 0, s>>>(nx, ny, nz, bits, u);
+    }
   }
-  t -= n8;
-  ids += 8 * n8;
-  if (t < n1 && mask) u[ids[t]] = T(0);
+  if (nx > 1) {
+    constexpr int R = 32 / N, NG = (N * N + R - 1) / R;
+    const int64_t warps = (int64_t)ny * nz * NG * ((nx - 1 + GS_X_SEG - 1) / GS_X_SEG);
+    gs_sweep_x<T, N><<<grid_for(32 * warps, 256), 256, 0, s>>>(nx, ny, nz, u);
+  }
+  if (ny > 1) {
+    const int64_t n = (int64_t)N2 * nx * (ny - 1) * nz;
+    gs_sweep_y<T, N><<<grid_for(n, 256), 256, 0, s>>>(nx, ny, nz, u);
+  }
+  if (nz > 1) {
+    const int64_t n = (int64_t)N2 * nx * ny * (nz - 1);
+    gs_sweep_z<T, N><<<grid_for(n, 256), 256, 0, s>>>(nx, ny, nz, u);
+  }
+  SE_LAUNCH_CHECK();
+  return SE_OK;
+}
+
+// Copies on element interfaces (each is read and written once by the algorithm).
+static double interface_copies(const Level& lv) {
+  double inner = 1.0;  // local points on no interface: product over directions
+  for (int d = 0; d < 3; ++d) inner *= (double)lv.nel[d] * lv.N - 2.0 * (lv.nel[d] - 1);
+  return (double)lv.L - inner;
 }
 
 template <class T>
 int gs_apply(const Level& lv, T* u, bool mask, cudaStream_t s) {
-  const int64_t n = (lv.n_pairs + GS_PAIRS_PER_THREAD - 1) / GS_PAIRS_PER_THREAD + lv.n_quads +
-                    lv.n_octs + lv.n_masked;
-  if (lv.n_pairs + n == 0) return SE_OK;
-  const double entries = 2.0 * lv.n_pairs + 4.0 * lv.n_quads + 8.0 * lv.n_octs;
-  ProfScope prof(SE_K_GS, s, entries, entries * (2.0 * sizeof(T) + 4.0) + lv.n_masked * (4.0 + sizeof(T)),
-                 entries, prof_variant<T>(lv.p));
-  gs_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(lv.n_pairs, lv.n_quads, lv.n_octs, lv.n_masked,
-                                                 lv.gs_ids, u, mask);
-  SE_LAUNCH_CHECK();
-  return SE_OK;
+  const double shared = interface_copies(lv);
+  ProfScope prof(SE_K_GS, s, shared, shared * 2.0 * sizeof(T), shared, prof_variant<T>(lv.p));
+  switch (lv.N) {
+#define SE_GS_CASE(NN) \
+  case NN: return gs_sweeps<T, NN>(lv, u, mask, s);
+    SE_GS_CASE(2) SE_GS_CASE(3) SE_GS_CASE(4) SE_GS_CASE(5) SE_GS_CASE(6)
+    SE_GS_CASE(7) SE_GS_CASE(8) SE_GS_CASE(9) SE_GS_CASE(10) SE_GS_CASE(11)
+#undef SE_GS_CASE
+    default: set_error("gs: unsupported N=%d", lv.N); return SE_EINVAL;
+  }
 }
 
 template <typename T>

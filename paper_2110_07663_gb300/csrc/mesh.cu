@@ -190,145 +190,6 @@ static int bc_mask_bits(const int bc[6]) {
   return m;
 }
 
-// ------------------------------------------------------------------ QQ^T index map
-// For every global lattice node (I, J, K) the local copies are the products of the per-direction
-// options: an element-boundary lattice line interior to the box belongs to two elements.
-// Groups of 2, 4 and 8 copies are stored in global-id order; a group whose node lies on a
-// Dirichlet face has its first id stored as ~id.  Dirichlet nodes with a single copy form the
-// singles list.  Built on the GPU in two passes over the nodes (one thread per node, blocks in
-// node order): pass 1 counts each group kind per block, the host scans those counts (a few
-// numbers per 1024 nodes), pass 2 writes every group at its rank.  The result is the same as a
-// sequential walk over the nodes.
-constexpr int GSB = 1024;  // nodes per block
-
-__device__ __forceinline__ int gs_options(int I, int p, int ne, int* el, int* loc) {
-  int c = 0;
-  const int q = I / p, rm = I - q * p;
-  if (rm == 0) {
-    if (q > 0) { el[c] = q - 1; loc[c] = p; ++c; }
-    if (q < ne) { el[c] = q; loc[c] = 0; ++c; }
-  } else {
-    el[c] = q; loc[c] = rm; ++c;
-  }
-  return c;
-}
-
-// Kind of node g: 0 none (one free copy), 1 single (one Dirichlet copy), 2 pair, 3 quad, 4 octet.
-struct GsNode {
-  int kind, n;
-  bool masked;
-};
-__device__ __forceinline__ GsNode gs_classify(int64_t g, int p, int nx, int ny, int nz, int NX,
-                                              int NY, int NZ, int bits) {
-  const int I = (int)(g % NX), J = (int)((g / NX) % NY), K = (int)(g / ((int64_t)NX * NY));
-  auto count = [p](int X, int ne) { return (X % p == 0) ? ((X / p > 0) + (X / p < ne)) : 1; };
-  const int mult = count(I, nx) * count(J, ny) * count(K, nz);
-  const bool msk = ((bits & 1) && I == 0) || ((bits & 2) && I == NX - 1) ||
-                   ((bits & 4) && J == 0) || ((bits & 8) && J == NY - 1) ||
-                   ((bits & 16) && K == 0) || ((bits & 32) && K == NZ - 1);
-  GsNode r;
-  r.n = mult;
-  r.masked = msk;
-  r.kind = mult == 1 ? (msk ? 1 : 0) : (mult == 2 ? 2 : (mult == 4 ? 3 : 4));
-  return r;
-}
-
-__global__ void __launch_bounds__(GSB) gs_count_kernel(int64_t n, int p, int nx, int ny, int nz,
-                                                       int NX, int NY, int NZ, int bits,
-                                                       int* __restrict__ counts) {
-  const int64_t g = (int64_t)blockIdx.x * GSB + threadIdx.x;
-  const int kind = g < n ? gs_classify(g, p, nx, ny, nz, NX, NY, NZ, bits).kind : 0;
-  const int c1 = __syncthreads_count(kind == 1), c2 = __syncthreads_count(kind == 2);
-  const int c3 = __syncthreads_count(kind == 3), c4 = __syncthreads_count(kind == 4);
-  if (threadIdx.x == 0) {
-    counts[4 * blockIdx.x + 0] = c2;
-    counts[4 * blockIdx.x + 1] = c3;
-    counts[4 * blockIdx.x + 2] = c4;
-    counts[4 * blockIdx.x + 3] = c1;
-  }
-}
-
-// offs[4 * block + k]: first group index of kind k (pairs, quads, octets, singles) in the block;
-// base[k]: first id of kind k's region of ids.
-__global__ void __launch_bounds__(GSB) gs_write_kernel(int64_t n, int p, int N, int nx, int ny,
-                                                       int nz, int NX, int NY, int NZ, int bits,
-                                                       const int64_t* __restrict__ offs,
-                                                       int64_t base0, int64_t base1, int64_t base2,
-                                                       int64_t base3, int* __restrict__ ids) {
-  __shared__ int wcount[GSB / 32][4];
-  const int64_t g = (int64_t)blockIdx.x * GSB + threadIdx.x;
-  const GsNode nd = g < n ? gs_classify(g, p, nx, ny, nz, NX, NY, NZ, bits) : GsNode{0, 1, false};
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const unsigned lt = (1u << lane) - 1u;
-  int my_rank = 0;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const int kind = k == 3 ? 1 : k + 2;
-    const unsigned m = __ballot_sync(0xffffffffu, nd.kind == kind);
-    if (nd.kind == kind) my_rank = __popc(m & lt);
-    if (lane == 0) wcount[w][k] = __popc(m);
-  }
-  __syncthreads();
-  if (nd.kind == 0) return;
-  const int k = nd.kind == 1 ? 3 : nd.kind - 2;
-  for (int v = 0; v < w; ++v) my_rank += wcount[v][k];
-  const int64_t grp = offs[4 * blockIdx.x + k] + my_rank;
-  const int64_t at = (k == 0 ? base0 : k == 1 ? base1 : k == 2 ? base2 : base3) + grp * nd.n;
-  const int I = (int)(g % NX), J = (int)((g / NX) % NY), K = (int)(g / ((int64_t)NX * NY));
-  int ex[2], ix[2], ey[2], iy[2], ez[2], iz[2];
-  const int cx = gs_options(I, p, nx, ex, ix), cy = gs_options(J, p, ny, ey, iy);
-  const int cz = gs_options(K, p, nz, ez, iz);
-  int q = 0;
-  for (int a = 0; a < cz; ++a)
-    for (int b = 0; b < cy; ++b)
-      for (int c = 0; c < cx; ++c) {
-        const int64_t e = ex[c] + (int64_t)nx * (ey[b] + (int64_t)ny * ez[a]);
-        int id = (int)(e * N * N * N + ix[c] + N * (iy[b] + N * iz[a]));
-        if (q == 0 && nd.masked && nd.n > 1) id = ~id;
-        ids[at + q] = id;
-        ++q;
-      }
-}
-
-static int build_gs_map(Level& lv, Allocs& allocs, cudaStream_t s) {
-  const int64_t n = lv.n_global;
-  const int64_t nb = (n + GSB - 1) / GSB;
-  const int bits = bc_mask_bits(lv.bc);
-  int* dcounts = nullptr;
-  int64_t* doffs = nullptr;
-  SE_TRY(dmalloc_transient(reinterpret_cast<void**>(&dcounts), 4 * nb * sizeof(int), s));
-  gs_count_kernel<<<(unsigned)nb, GSB, 0, s>>>(n, lv.p, lv.nel[0], lv.nel[1], lv.nel[2], lv.NX,
-                                               lv.NY, lv.NZ, bits, dcounts);
-  SE_LAUNCH_CHECK();
-  std::vector<int> counts(4 * nb);
-  SE_CUDA(cudaMemcpyAsync(counts.data(), dcounts, counts.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
-  SE_CUDA(cudaStreamSynchronize(s));
-  std::vector<int64_t> offs(4 * nb);
-  int64_t tot[4] = {0, 0, 0, 0};
-  for (int64_t b = 0; b < nb; ++b)
-    for (int k = 0; k < 4; ++k) {
-      offs[4 * b + k] = tot[k];
-      tot[k] += counts[4 * b + k];
-    }
-  lv.n_pairs = tot[0];
-  lv.n_quads = tot[1];
-  lv.n_octs = tot[2];
-  lv.n_masked = tot[3];
-  const int64_t base1 = 2 * tot[0], base2 = base1 + 4 * tot[1], base3 = base2 + 8 * tot[2];
-  const int64_t total = base3 + tot[3];
-  SE_TRY(dmalloc(allocs, &lv.gs_ids, (size_t)total));
-  SE_TRY(dmalloc_transient(reinterpret_cast<void**>(&doffs), offs.size() * sizeof(int64_t), s));
-  SE_CUDA(cudaMemcpyAsync(doffs, offs.data(), offs.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-  gs_write_kernel<<<(unsigned)nb, GSB, 0, s>>>(n, lv.p, lv.N, lv.nel[0], lv.nel[1], lv.nel[2],
-                                               lv.NX, lv.NY, lv.NZ, bits, doffs, 0, base1, base2,
-                                               base3, lv.gs_ids);
-  SE_LAUNCH_CHECK();
-  cudaFreeAsync(dcounts, s);
-  cudaFreeAsync(doffs, s);
-  SE_CUDA(cudaStreamSynchronize(s));  // offs (host) must outlive the copy
-  return SE_OK;
-}
-
 int build_level(se_mesh_s* m, int p, Level* lvp, Allocs& allocs, cudaStream_t s) {
   Level& lv = *lvp;
   lv.p = p;
@@ -383,7 +244,6 @@ int build_level(se_mesh_s* m, int p, Level* lvp, Allocs& allocs, cudaStream_t s)
   pointflag_kernel<<<grid_for(lv.L, 256), 256, 0, s>>>(N, lv.nel[0], lv.nel[1], lv.nel[2], lv.L,
                                                       bc_mask_bits(lv.bc), lv.pflag, nullptr);
   SE_LAUNCH_CHECK();
-  SE_TRY(build_gs_map(lv, allocs, s));
   return SE_OK;
 }
 

@@ -110,11 +110,6 @@ struct Level {
   double* D64 = nullptr;     // derivative matrix on the device [N*N]
   double* eo64 = nullptr;    // even-odd folded D and D^T tables [4][N/2][N/2] (even N)
   float* D32 = nullptr;
-  // QQ^T index map, groups sorted by global id within each class: pairs, quads, octets of
-  // local ids sharing a global node (first id stored as ~id when the node is on a Dirichlet
-  // face), then the single-copy Dirichlet nodes (n_masked of them).
-  int64_t n_pairs = 0, n_quads = 0, n_octs = 0, n_masked = 0;
-  int* gs_ids = nullptr;
   const int* nbr = nullptr;  // element neighbours [E][27] (owned by the mesh)
   // fast diagonalisation factors (all levels but the coarsest)
   double* S64 = nullptr;     // [E][3][pb][pb], S[row = window point][col = mode]
