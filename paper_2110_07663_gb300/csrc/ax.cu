@@ -304,33 +304,43 @@ __global__ void gs_mask_faces(int nx, int ny, int nz, int bits, T* __restrict__ 
   u[e * N3 + i + N * (j + N * k)] = T(0);
 }
 
+// One profiling scope per launch (so launch counts are exact); the algorithmic bytes of QQ^T
+// (every interface copy read and written once) are attributed to the x sweep.
 template <typename T, int N>
-static int gs_sweeps(const Level& lv, T* u, bool mask, cudaStream_t s) {
+static int gs_sweeps(const Level& lv, T* u, bool mask, double bytes, double flops, cudaStream_t s) {
   const int nx = lv.nel[0], ny = lv.nel[1], nz = lv.nel[2];
   constexpr int N2 = N * N;
+  const int var = prof_variant<T>(lv.p);
   if (mask) {
     int bits = 0;
     for (int f = 0; f < 6; ++f)
       if (lv.bc[f] == SE_BC_DIRICHLET) bits |= 1 << f;
     if (bits) {
       const int64_t n = 2 * N2 * ((int64_t)ny * nz + (int64_t)nx * nz + (int64_t)nx * ny);
+      ProfScope prof(SE_K_GS, s, (double)n, 0.0, 0.0, var);
       gs_mask_faces<T, N><<<grid_for(n, 256), 256, 0, s>>>(nx, ny, nz, bits, u);
+      SE_LAUNCH_CHECK();
     }
   }
   if (nx > 1) {
     constexpr int R = 32 / N, NG = (N * N + R - 1) / R;
     const int64_t warps = (int64_t)ny * nz * NG * ((nx - 1 + GS_X_SEG - 1) / GS_X_SEG);
+    ProfScope prof(SE_K_GS, s, (double)lv.L, bytes, flops, var);
     gs_sweep_x<T, N><<<grid_for(32 * warps, 256), 256, 0, s>>>(nx, ny, nz, u);
+    SE_LAUNCH_CHECK();
   }
   if (ny > 1) {
     const int64_t n = (int64_t)N2 * nx * (ny - 1) * nz;
+    ProfScope prof(SE_K_GS, s, (double)n, 0.0, 0.0, var);
     gs_sweep_y<T, N><<<grid_for(n, 256), 256, 0, s>>>(nx, ny, nz, u);
+    SE_LAUNCH_CHECK();
   }
   if (nz > 1) {
     const int64_t n = (int64_t)N2 * nx * ny * (nz - 1);
+    ProfScope prof(SE_K_GS, s, (double)n, 0.0, 0.0, var);
     gs_sweep_z<T, N><<<grid_for(n, 256), 256, 0, s>>>(nx, ny, nz, u);
+    SE_LAUNCH_CHECK();
   }
-  SE_LAUNCH_CHECK();
   return SE_OK;
 }
 
@@ -344,10 +354,10 @@ static double interface_copies(const Level& lv) {
 template <class T>
 int gs_apply(const Level& lv, T* u, bool mask, cudaStream_t s) {
   const double shared = interface_copies(lv);
-  ProfScope prof(SE_K_GS, s, shared, shared * 2.0 * sizeof(T), shared, prof_variant<T>(lv.p));
+  const double bytes = shared * 2.0 * sizeof(T), flops = shared;
   switch (lv.N) {
 #define SE_GS_CASE(NN) \
-  case NN: return gs_sweeps<T, NN>(lv, u, mask, s);
+  case NN: return gs_sweeps<T, NN>(lv, u, mask, bytes, flops, s);
     SE_GS_CASE(2) SE_GS_CASE(3) SE_GS_CASE(4) SE_GS_CASE(5) SE_GS_CASE(6)
     SE_GS_CASE(7) SE_GS_CASE(8) SE_GS_CASE(9) SE_GS_CASE(10) SE_GS_CASE(11)
 #undef SE_GS_CASE
