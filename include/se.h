@@ -136,7 +136,10 @@ typedef struct se_pmg_desc {
  * from Arnoldi on S A at every level but the coarsest.  Synchronises. */
 int se_pmg_setup(se_mesh_t m, const se_pmg_desc* desc, se_pmg_t* out);
 int se_pmg_destroy(se_pmg_t pmg);
-/* z = M r: one V-cycle (Algorithm 1) with x = 0 on entry.  r, z: fine-level L-vectors. */
+/* z = M r: one V-cycle (Algorithm 1) with x = 0 on entry.  r, z: fine-level L-vectors; r must be
+ * continuous (all copies of a node equal, as every QQ^T output and every residual of an assembled
+ * right-hand side is): the V-cycle forms its residuals b - A x in one operator pass that relies
+ * on it. */
 int se_pmg_apply(se_pmg_t pmg, const double* r, double* z, void* stream);
 /* lambda-tilde of level lvl (largest |Ritz value| of Arnoldi on S A, Sec. 2.3.3). */
 int se_pmg_lambda(se_pmg_t pmg, int lvl, double* lam);

@@ -15,7 +15,8 @@ __global__ void __launch_bounds__(512) ax_local_kernel(int64_t E, int NE, const 
                                                        const T* __restrict__ G, int64_t L,
                                                        const T* __restrict__ Dg,
                                                        T* __restrict__ y,
-                                                       const uint8_t* __restrict__ pflag) {
+                                                       const uint8_t* __restrict__ pflag,
+                                                       bool mask_in, const T* __restrict__ sub) {
   constexpr int N2 = N * N, N3 = N * N * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sD = reinterpret_cast<T*>(smem_raw);
@@ -35,7 +36,7 @@ __global__ void __launch_bounds__(512) ax_local_kernel(int64_t E, int NE, const 
     T v = T(0);
     if (valid) {
       v = u[eb + ij + N2 * k];
-      if (pflag && !(pflag[eb + ij + N2 * k] & PF_FREE)) v = T(0);
+      if (mask_in && !(pflag[eb + ij + N2 * k] & PF_FREE)) v = T(0);
     }
     ru[k] = v;
     if (le < NE) su[ij + N2 * k] = v;
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(512) ax_local_kernel(int64_t E, int NE, const 
       acc += Dci[l] * swr[l + N * j + N2 * k];
       acc += Dcj[l] * sws[i + N * l + N2 * k];
     }
-    if (valid) y[eb + ij + N2 * k] = acc;
+    if (valid) y[eb + ij + N2 * k] = ax_output(acc, sub, pflag, eb + ij + N2 * k);
   }
 }
 
@@ -110,8 +111,8 @@ int ax_elems_per_block(int p, bool fp32) {
 }
 
 template <int N, typename T>
-static int launch_ax(const Level& lv, const T* u, T* y, const T* G, const T* D,
-                     const uint8_t* pflag, cudaStream_t s) {
+static int launch_ax(const Level& lv, const T* u, T* y, const T* G, const T* D, bool mask_in,
+                     const T* sub, cudaStream_t s) {
   const int NE = ax_elems_per_block(N - 1, sizeof(T) == 4);
   const int threads = NE * N * N;
   const size_t smem = (N * N + (size_t)NE * 3 * N * N * N) * sizeof(T);
@@ -120,13 +121,14 @@ static int launch_ax(const Level& lv, const T* u, T* y, const T* G, const T* D,
       ax_local_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   SE_CUDA(attr);
   const unsigned blocks = (unsigned)((lv.E + NE - 1) / NE);
-  ax_local_kernel<N, T><<<blocks, threads, smem, s>>>(lv.E, NE, u, G, lv.L, D, y, pflag);
+  ax_local_kernel<N, T><<<blocks, threads, smem, s>>>(lv.E, NE, u, G, lv.L, D, y, lv.pflag, mask_in,
+                                                       sub);
   SE_LAUNCH_CHECK();
   return SE_OK;
 }
 
 template <class T>
-int ax_local(const Level& lv, const T* u, T* y, bool mask_in, cudaStream_t s) {
+int ax_local(const Level& lv, const T* u, T* y, bool mask_in, cudaStream_t s, const T* sub) {
   const T* G;
   const T* D;
   if constexpr (sizeof(T) == 8) {
@@ -139,25 +141,24 @@ int ax_local(const Level& lv, const T* u, T* y, bool mask_in, cudaStream_t s) {
   SE_CHECK(G != nullptr, SE_EINVAL, "ax_local: geometric factors for this precision missing");
   const int N = lv.N;
   const double pts = (double)lv.L;
-  ProfScope prof(SE_K_AX, s, pts, pts * 8.0 * sizeof(T), pts * (12.0 * N + 15.0),
-                 prof_variant<T>(lv.p));
-  const uint8_t* pf = mask_in ? lv.pflag : nullptr;
+  ProfScope prof(SE_K_AX, s, pts, pts * ((sub ? 9.0 : 8.0) * sizeof(T) + (sub ? 1.0 : 0.0)),
+                 pts * (12.0 * N + 15.0), prof_variant<T>(lv.p));
   if constexpr (sizeof(T) == 4) {
-    if (!mask_in && ax_tma_supported(lv.p)) return ax_local_tma(lv, u, y, s);
+    if (!mask_in && ax_tma_supported(lv.p)) return ax_local_tma(lv, u, y, s, sub);
   } else {
-    if (!mask_in && ax_eo_supported(lv.p) && lv.eo64) return ax_local_eo(lv, u, y, s);
+    if (!mask_in && ax_eo_supported(lv.p) && lv.eo64) return ax_local_eo(lv, u, y, s, sub);
   }
   switch (N) {
-    case 2: return launch_ax<2, T>(lv, u, y, G, D, pf, s);
-    case 3: return launch_ax<3, T>(lv, u, y, G, D, pf, s);
-    case 4: return launch_ax<4, T>(lv, u, y, G, D, pf, s);
-    case 5: return launch_ax<5, T>(lv, u, y, G, D, pf, s);
-    case 6: return launch_ax<6, T>(lv, u, y, G, D, pf, s);
-    case 7: return launch_ax<7, T>(lv, u, y, G, D, pf, s);
-    case 8: return launch_ax<8, T>(lv, u, y, G, D, pf, s);
-    case 9: return launch_ax<9, T>(lv, u, y, G, D, pf, s);
-    case 10: return launch_ax<10, T>(lv, u, y, G, D, pf, s);
-    case 11: return launch_ax<11, T>(lv, u, y, G, D, pf, s);
+    case 2: return launch_ax<2, T>(lv, u, y, G, D, mask_in, sub, s);
+    case 3: return launch_ax<3, T>(lv, u, y, G, D, mask_in, sub, s);
+    case 4: return launch_ax<4, T>(lv, u, y, G, D, mask_in, sub, s);
+    case 5: return launch_ax<5, T>(lv, u, y, G, D, mask_in, sub, s);
+    case 6: return launch_ax<6, T>(lv, u, y, G, D, mask_in, sub, s);
+    case 7: return launch_ax<7, T>(lv, u, y, G, D, mask_in, sub, s);
+    case 8: return launch_ax<8, T>(lv, u, y, G, D, mask_in, sub, s);
+    case 9: return launch_ax<9, T>(lv, u, y, G, D, mask_in, sub, s);
+    case 10: return launch_ax<10, T>(lv, u, y, G, D, mask_in, sub, s);
+    case 11: return launch_ax<11, T>(lv, u, y, G, D, mask_in, sub, s);
     default: set_error("ax_local: unsupported N=%d", N); return SE_EINVAL;
   }
 }
@@ -371,8 +372,8 @@ __global__ void mask_kernel(int64_t L, const uint8_t* __restrict__ pflag, T* __r
   if (idx < L && !(pflag[idx] & PF_FREE)) u[idx] = T(0);
 }
 
-template int ax_local<double>(const Level&, const double*, double*, bool, cudaStream_t);
-template int ax_local<float>(const Level&, const float*, float*, bool, cudaStream_t);
+template int ax_local<double>(const Level&, const double*, double*, bool, cudaStream_t, const double*);
+template int ax_local<float>(const Level&, const float*, float*, bool, cudaStream_t, const float*);
 template int gs_apply<double>(const Level&, double*, bool, cudaStream_t);
 template int gs_apply<float>(const Level&, float*, bool, cudaStream_t);
 

@@ -41,7 +41,9 @@ template <int N>
 __global__ void __launch_bounds__(512) ax_eo_kernel(int64_t E, int NE, const double* __restrict__ u,
                                                     const double* __restrict__ G, int64_t L,
                                                     const double* __restrict__ tables,
-                                                    double* __restrict__ y) {
+                                                    double* __restrict__ y,
+                                                    const uint8_t* __restrict__ pflag,
+                                                    const double* __restrict__ sub) {
   constexpr int N2 = N * N, N3 = N * N * N, H = N / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* tab = reinterpret_cast<double*>(smem_raw);          // 4 H^2
@@ -130,13 +132,13 @@ __global__ void __launch_bounds__(512) ax_eo_kernel(int64_t E, int NE, const dou
   __syncthreads();
   if (valid) {
 #pragma unroll
-    for (int q = 0; q < N; ++q) y[eb + t + N2 * q] = sy[t + N2 * q];
+    for (int q = 0; q < N; ++q) y[eb + t + N2 * q] = ax_output(sy[t + N2 * q], sub, pflag, eb + t + N2 * q);
   }
 }
 
 template <int N>
 static int launch_ax_eo(const Level& lv, const double* u, double* y, const double* tables,
-                        cudaStream_t s) {
+                        const double* sub, cudaStream_t s) {
   constexpr int H = N / 2;
   const int NE = ax_elems_per_block(N - 1, false);
   const int threads = NE * N * N;
@@ -145,7 +147,7 @@ static int launch_ax_eo(const Level& lv, const double* u, double* y, const doubl
       cudaFuncSetAttribute(ax_eo_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   SE_CUDA(attr);
   const unsigned blocks = (unsigned)((lv.E + NE - 1) / NE);
-  ax_eo_kernel<N><<<blocks, threads, smem, s>>>(lv.E, NE, u, lv.G64, lv.L, tables, y);
+  ax_eo_kernel<N><<<blocks, threads, smem, s>>>(lv.E, NE, u, lv.G64, lv.L, tables, y, lv.pflag, sub);
   SE_LAUNCH_CHECK();
   return SE_OK;
 }
@@ -164,14 +166,14 @@ void ax_eo_tables(const Basis1D& b, double* out) {
       }
 }
 
-int ax_local_eo(const Level& lv, const double* u, double* y, cudaStream_t s) {
+int ax_local_eo(const Level& lv, const double* u, double* y, cudaStream_t s, const double* sub) {
   SE_CHECK(lv.eo64 != nullptr, SE_EINVAL, "ax_eo: folded tables missing");
   switch (lv.N) {
-    case 2: return launch_ax_eo<2>(lv, u, y, lv.eo64, s);
-    case 4: return launch_ax_eo<4>(lv, u, y, lv.eo64, s);
-    case 6: return launch_ax_eo<6>(lv, u, y, lv.eo64, s);
-    case 8: return launch_ax_eo<8>(lv, u, y, lv.eo64, s);
-    case 10: return launch_ax_eo<10>(lv, u, y, lv.eo64, s);
+    case 2: return launch_ax_eo<2>(lv, u, y, lv.eo64, sub, s);
+    case 4: return launch_ax_eo<4>(lv, u, y, lv.eo64, sub, s);
+    case 6: return launch_ax_eo<6>(lv, u, y, lv.eo64, sub, s);
+    case 8: return launch_ax_eo<8>(lv, u, y, lv.eo64, sub, s);
+    case 10: return launch_ax_eo<10>(lv, u, y, lv.eo64, sub, s);
     default: set_error("ax_eo: unsupported N=%d", lv.N); return SE_EINVAL;
   }
 }

@@ -64,17 +64,22 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
 
 constexpr long long PIPE_LIMIT_NS = 1000000000LL;
 
-template <int N>
+// Residual form (RES): an eighth block per group, b, comes through the same pipeline, and the
+// output is b / multiplicity - A_L u; the multiplicity follows from the element's place in the
+// lattice (copies = product over directions of 2 on an interior element interface, else 1).
+template <int N, bool RES>
 __global__ void __launch_bounds__(512) ax_tma_kernel(int64_t E, int NE, int64_t ngroups,
                                                      const float* __restrict__ u,
                                                      const float* __restrict__ G, int64_t L,
                                                      const float* __restrict__ Dg,
-                                                     float* __restrict__ y) {
-  constexpr int N2 = N * N, N3 = N * N * N;
+                                                     float* __restrict__ y,
+                                                     const float* __restrict__ sub, int nx,
+                                                     int ny, int nz) {
+  constexpr int N2 = N * N, N3 = N * N * N, A = RES ? 8 : 7;  // blocks per stage
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int S = NE * N3;                       // floats per element-group block
-  float* stage0 = reinterpret_cast<float*>(smem_raw);   // stage s: u at s*7S, G at s*7S + S
-  float* swr = stage0 + 14 * S;
+  float* stage0 = reinterpret_cast<float*>(smem_raw);   // stage s: u at s*A*S, G at +S, b at +7S
+  float* swr = stage0 + 2 * A * S;
   float* sws = swr + S;
   float* sD = sws + S;
   uint64_t* bars = reinterpret_cast<uint64_t*>(sD + ((N2 + 3) / 4) * 4 + 4);
@@ -92,11 +97,12 @@ __global__ void __launch_bounds__(512) ax_tma_kernel(int64_t E, int NE, int64_t 
     const int64_t e0 = g * NE;
     const int ne = (int)((E - e0) < NE ? (E - e0) : NE);
     const unsigned bytes = (unsigned)(ne * N3 * sizeof(float));
-    float* dst = stage0 + st * 7 * S;
-    mbar_arrive_expect_tx(&bars[st], 7u * bytes);
+    float* dst = stage0 + st * A * S;
+    mbar_arrive_expect_tx(&bars[st], (unsigned)A * bytes);
     bulk_load(dst, u + e0 * N3, bytes, &bars[st]);
 #pragma unroll
     for (int c = 0; c < 6; ++c) bulk_load(dst + (c + 1) * S, G + c * L + e0 * N3, bytes, &bars[st]);
+    if (RES) bulk_load(dst + 7 * S, sub + e0 * N3, bytes, &bars[st]);
   };
   int64_t g = blockIdx.x;
   if (tid == 0) {
@@ -123,8 +129,19 @@ __global__ void __launch_bounds__(512) ax_tma_kernel(int64_t E, int NE, int64_t 
     phases ^= 1u << st;
     const int64_t e0 = g * NE;
     const bool valid = (e0 + le) < E;
-    const float* cu = stage0 + st * 7 * S + le * N3;
+    const float* cu = stage0 + st * A * S + le * N3;
     const float* cg = cu + S;
+    // residual form: b / multiplicity of this thread's outputs, read from the stage before the
+    // stage is handed to the next copy
+    float bw[N];
+    if (RES && valid) {
+      const int64_t e = e0 + le;
+      const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
+      auto shared2 = [](int a, int ea, int na) { return (a == 0 && ea > 0) || (a == N - 1 && ea < na - 1); };
+      const float wxy = (shared2(i, ex, nx) ? 0.5f : 1.f) * (shared2(j, ey, ny) ? 0.5f : 1.f);
+#pragma unroll
+      for (int k = 0; k < N; ++k) bw[k] = cu[7 * S + ij + N2 * k] * (wxy * (shared2(k, ez, nz) ? 0.5f : 1.f));
+    }
     float ru[N], ry[N];
 #pragma unroll
     for (int k = 0; k < N; ++k) {
@@ -168,7 +185,7 @@ __global__ void __launch_bounds__(512) ax_tma_kernel(int64_t E, int NE, int64_t 
           acc += Dci[l] * cwr[l + N * j + N2 * k];
           acc += Dcj[l] * cws[i + N * l + N2 * k];
         }
-        yo[ij + N2 * k] = acc;
+        yo[ij + N2 * k] = RES ? bw[k] - acc : acc;
       }
     }
     __syncthreads();  // swr/sws free for the next group
@@ -180,16 +197,18 @@ __global__ void __launch_bounds__(512) ax_tma_kernel(int64_t E, int NE, int64_t 
   }
 }
 
-template <int N>
-static int launch_ax_tma(const Level& lv, const float* u, float* y, int NE, cudaStream_t s) {
-  constexpr int N3 = N * N * N;
+template <int N, bool RES>
+static int launch_ax_tma_t(const Level& lv, const float* u, float* y, int NE, const float* sub,
+                           cudaStream_t s) {
+  constexpr int N3 = N * N * N, A = RES ? 8 : 7;
   const int threads = NE * N * N;
-  const size_t smem = (size_t)(16 * NE * N3 + ((N * N + 3) / 4) * 4 + 4) * sizeof(float) + 2 * sizeof(uint64_t);
-  static const cudaError_t attr =
-      cudaFuncSetAttribute(ax_tma_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  const size_t smem = (size_t)((2 * A + 2) * NE * N3 + ((N * N + 3) / 4) * 4 + 4) * sizeof(float) +
+                      2 * sizeof(uint64_t);
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      ax_tma_kernel<N, RES>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   SE_CUDA(attr);
   int per_sm = 0;
-  SE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ax_tma_kernel<N>, threads, smem));
+  SE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ax_tma_kernel<N, RES>, threads, smem));
   SE_CHECK(per_sm >= 1, SE_ECUDA, "ax_tma: no resident block fits (NE=%d)", NE);
   int dev = 0, sms = 0;
   SE_CUDA(cudaGetDevice(&dev));
@@ -197,32 +216,42 @@ static int launch_ax_tma(const Level& lv, const float* u, float* y, int NE, cuda
   const int64_t groups = (lv.E + NE - 1) / NE;
   int64_t grid = (int64_t)sms * per_sm;
   if (grid > groups) grid = groups;
-  ax_tma_kernel<N><<<(unsigned)grid, threads, smem, s>>>(lv.E, NE, groups, u, lv.G32, lv.L, lv.D32, y);
+  ax_tma_kernel<N, RES><<<(unsigned)grid, threads, smem, s>>>(lv.E, NE, groups, u, lv.G32, lv.L,
+                                                               lv.D32, y, sub, lv.nel[0],
+                                                               lv.nel[1], lv.nel[2]);
   SE_LAUNCH_CHECK();
   return SE_OK;
+}
+
+template <int N>
+static int launch_ax_tma(const Level& lv, const float* u, float* y, int NE, const float* sub,
+                         cudaStream_t s) {
+  return sub ? launch_ax_tma_t<N, true>(lv, u, y, NE, sub, s)
+             : launch_ax_tma_t<N, false>(lv, u, y, NE, sub, s);
 }
 
 // Elements per group of the pipelined kernel (tuned value, else 2 groups of N^2 threads).
 int ax_tma_group(int p) {
   const int N = p + 1;
   const int t = tile_get(p, true).ax_ne;
-  if (t >= 1 && t * N * N <= 512 && 16 * t * N * N * N * 4 <= 200 * 1024) return t;
+  // shared memory for the residual form (18 blocks of the group): the plain form (16) then fits too
+  if (t >= 1 && t * N * N <= 512 && 18 * t * N * N * N * 4 <= 200 * 1024) return t;
   int ne = 256 / (N * N);
   if (ne < 1) ne = 1;
-  while (ne > 1 && 16 * ne * N * N * N * 4 > 200 * 1024) --ne;
+  while (ne > 1 && 18 * ne * N * N * N * 4 > 200 * 1024) --ne;
   return ne;
 }
 
 bool ax_tma_supported(int p) { return (p + 1) % 2 == 0 && p + 1 >= 2 && p + 1 <= 10; }
 
-int ax_local_tma(const Level& lv, const float* u, float* y, cudaStream_t s) {
+int ax_local_tma(const Level& lv, const float* u, float* y, cudaStream_t s, const float* sub) {
   const int NE = ax_tma_group(lv.p);
   switch (lv.N) {
-    case 2: return launch_ax_tma<2>(lv, u, y, NE, s);
-    case 4: return launch_ax_tma<4>(lv, u, y, NE, s);
-    case 6: return launch_ax_tma<6>(lv, u, y, NE, s);
-    case 8: return launch_ax_tma<8>(lv, u, y, NE, s);
-    case 10: return launch_ax_tma<10>(lv, u, y, NE, s);
+    case 2: return launch_ax_tma<2>(lv, u, y, NE, sub, s);
+    case 4: return launch_ax_tma<4>(lv, u, y, NE, sub, s);
+    case 6: return launch_ax_tma<6>(lv, u, y, NE, sub, s);
+    case 8: return launch_ax_tma<8>(lv, u, y, NE, sub, s);
+    case 10: return launch_ax_tma<10>(lv, u, y, NE, sub, s);
     default: set_error("ax_tma: unsupported N=%d", lv.N); return SE_EINVAL;
   }
 }

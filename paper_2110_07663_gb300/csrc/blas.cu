@@ -179,32 +179,65 @@ template int scale_mul<float>(const float*, const float*, float*, int64_t, cudaS
 // Chebyshev recurrence step of Algorithm 2 (one pass):
 //   s = dinv .* sv (Jacobi surrogate) or s = sv (Schwarz output, already S A d)
 //   x = x + d (x = d when `first`), r = r - s, d = c1 d + c2 r
-template <class T>
+// from_r (the first step): d is not stored; d = scale r and s = scale (S A r) (the operator and
+// smoother were applied to r itself: by linearity S A (scale r) = scale S A r).
+// last: the final x += d of Algorithm 2 is done here, and r and d (no longer needed) are not
+// written: x = (x + d) + (c1 d + c2 r).
+template <class T, bool FIRST, bool FROM_R, bool LAST>
 __global__ void cheb_update_kernel(T* __restrict__ x, T* __restrict__ d, T* __restrict__ r,
                                    const T* __restrict__ sv, const T* __restrict__ dinv, int64_t n,
-                                   T c1, T c2, bool first) {
+                                   T c1, T c2, T scale) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const T dv = d[i];
-  const T sval = dinv ? dinv[i] * sv[i] : sv[i];
-  x[i] = first ? dv : x[i] + dv;
-  const T rv = r[i] - sval;
-  r[i] = rv;
-  d[i] = c1 * dv + c2 * rv;
+  // every load of this instantiation is unconditional, so all are in flight together
+  const T r0 = r[i];
+  const T s0 = sv[i];
+  const T di = dinv ? dinv[i] : T(1);
+  const T d0 = FROM_R ? T(0) : d[i];
+  const T x0 = FIRST ? T(0) : x[i];
+  T sval = dinv ? di * s0 : s0;
+  T dv;
+  if (FROM_R) {
+    dv = r0 * scale;
+    sval = sval * scale;
+  } else {
+    dv = d0;
+  }
+  const T xv = FIRST ? dv : x0 + dv;
+  const T rv = r0 - sval;
+  const T dn = c1 * dv + c2 * rv;
+  if (LAST) {
+    x[i] = xv + dn;
+  } else {
+    x[i] = xv;
+    r[i] = rv;
+    d[i] = dn;
+  }
 }
 template <class T>
 int cheb_update(T* x, T* d, T* r, const T* sv, const T* dinv, int64_t n, T c1, T c2, bool first,
-                cudaStream_t s) {
-  ProfScope prof(SE_K_CHEBY_UPD, s, (double)n, (first ? 6.0 : 7.0) * n * sizeof(T), 6.0 * n,
-                 prof_variant<T>(0));
-  cheb_update_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(x, d, r, sv, dinv, n, c1, c2, first);
+                cudaStream_t s, T scale, bool from_r, bool last) {
+  const double words = 2.0 + (dinv ? 1.0 : 0.0) + (from_r ? 0.0 : 1.0) + (first ? 0.0 : 1.0) +
+                       (last ? 1.0 : 3.0);
+  ProfScope prof(SE_K_CHEBY_UPD, s, (double)n, words * n * sizeof(T), 6.0 * n, prof_variant<T>(0));
+  const unsigned g = grid_for(n, 256);
+  const int key = (first ? 4 : 0) + (from_r ? 2 : 0) + (last ? 1 : 0);
+  switch (key) {
+#define SE_CHEB_CASE(K, F, R, L) \
+  case K: cheb_update_kernel<T, F, R, L><<<g, 256, 0, s>>>(x, d, r, sv, dinv, n, c1, c2, scale); break;
+    SE_CHEB_CASE(0, false, false, false) SE_CHEB_CASE(1, false, false, true)
+    SE_CHEB_CASE(2, false, true, false) SE_CHEB_CASE(3, false, true, true)
+    SE_CHEB_CASE(4, true, false, false) SE_CHEB_CASE(5, true, false, true)
+    SE_CHEB_CASE(6, true, true, false) SE_CHEB_CASE(7, true, true, true)
+#undef SE_CHEB_CASE
+  }
   SE_LAUNCH_CHECK();
   return SE_OK;
 }
 template int cheb_update<double>(double*, double*, double*, const double*, const double*, int64_t,
-                                 double, double, bool, cudaStream_t);
+                                 double, double, bool, cudaStream_t, double, bool, bool);
 template int cheb_update<float>(float*, float*, float*, const float*, const float*, int64_t, float,
-                                float, bool, cudaStream_t);
+                                float, bool, cudaStream_t, float, bool, bool);
 
 // ------------------------------------------------------------------ FPCG kernels (FP64)
 struct AlphaOp {  // pw = (p, w); alpha = rz / pw

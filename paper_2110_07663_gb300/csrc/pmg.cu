@@ -113,25 +113,28 @@ int cheby(se_pmg_s* P, int l, const T* res, T* x, bool first, cudaStream_t s) {
   double rho = 1.0 / sigma;
   const int order = P->desc.cheb_order[l];
   SE_TRY(smooth<T>(P, l, res, V.cr, s));                         // r = S res
-  SE_TRY(axpby<T>(T(1.0 / theta), V.cr, T(0), V.cr, V.cd, lv.L, s));  // d = r / theta
+  const T inv_theta = T(1.0 / theta);
+  if (order == 0) {                                              // x (+)= r / theta
+    if (first) return axpby<T>(inv_theta, V.cr, T(0), V.cr, x, lv.L, s);
+    return axpby<T>(inv_theta, V.cr, T(1), x, x, lv.L, s);
+  }
   const bool jac = P->desc.smoother == SE_SMOOTH_JACOBI;
+  // d = r / theta is not stored: the first step applies A (and S) to r and scales by 1/theta
   for (int k = 0; k < order; ++k) {
-    SE_TRY(ax_apply<T>(lv, V.cd, V.w, s));                       // A d
+    const bool from_r = k == 0, last = k == order - 1;
+    SE_TRY(ax_apply<T>(lv, from_r ? V.cr : V.cd, V.w, s));       // A d  (A r for the first step)
     const double rho_new = 1.0 / (2.0 * sigma - rho);
     const T c1 = T(rho_new * rho), c2 = T(2.0 * rho_new / delta);
-    if (jac) {
-      SE_TRY(cheb_update<T>(x, V.cd, V.cr, V.w, dinv_of<T>(lv), lv.L, c1, c2, first && k == 0, s));
-    } else {
+    const T* sa = V.w;                                           // Jacobi: dinv .* A d in the update
+    if (!jac) {
       SE_TRY(smooth<T>(P, l, V.w, V.sv, s));                     // S A d
-      SE_TRY(cheb_update<T>(x, V.cd, V.cr, V.sv, (const T*)nullptr, lv.L, c1, c2, first && k == 0, s));
+      sa = V.sv;
     }
+    SE_TRY(cheb_update<T>(x, V.cd, V.cr, sa, jac ? dinv_of<T>(lv) : (const T*)nullptr, lv.L, c1, c2,
+                          first && k == 0, s, inv_theta, from_r, last));  // last: also x += d
     rho = rho_new;
   }
-  if (first && order == 0) {
-    SE_CUDA(cudaMemcpyAsync(x, V.cd, lv.L * sizeof(T), cudaMemcpyDeviceToDevice, s));
-    return SE_OK;
-  }
-  return axpby<T>(T(1), x, T(1), V.cd, x, lv.L, s);              // final x += d
+  return SE_OK;
 }
 
 template <class T>
@@ -150,13 +153,11 @@ int vcycle(se_pmg_s* P, int l, cudaStream_t s) {
   LevelVecs<T>& C = P->vecs<T>(l + 1);
   const Level& lc = *P->lv[l + 1];
   SE_TRY(cheby<T>(P, l, V.b, V.x, true, s));                    // x = M b
-  SE_TRY(ax_apply<T>(lv, V.x, V.w, s));
-  SE_TRY(axpby<T>(T(1), V.b, T(-1), V.w, V.r, lv.L, s));         // r = b - A x
+  SE_TRY(residual_apply<T>(lv, V.b, V.x, V.r, s));               // r = b - A x
   SE_TRY(restrict_apply<T>(lv, lc, jmat<T>(P, l), V.r, C.b, s)); // r_C = P^T r
   SE_TRY(vcycle<T>(P, l + 1, s));                               // e_C
   SE_TRY(prolong_apply<T>(lv, lc, jmat<T>(P, l), C.x, V.x, true, s));  // x += P e_C
-  SE_TRY(ax_apply<T>(lv, V.x, V.w, s));
-  SE_TRY(axpby<T>(T(1), V.b, T(-1), V.w, V.r, lv.L, s));         // b - A x
+  SE_TRY(residual_apply<T>(lv, V.b, V.x, V.r, s));               // b - A x
   return cheby<T>(P, l, V.r, V.x, false, s);                    // x += M (b - A x)
 }
 

@@ -187,15 +187,34 @@ int make_fp32_geometry(Level& lv, Allocs& allocs, cudaStream_t s);
 int local_to_global(const Level& lv, int* l2g, cudaStream_t s);
 
 // ------------------------------------------------------------------ kernels' host launchers
-// Operator: y_L = A_L u (local), optionally followed by QQ^T + mask.
+// Operator: y_L = A_L u (local), optionally followed by QQ^T + mask.  With `sub` (a continuous
+// L-vector b), the local output is b / multiplicity - A_L u instead, so that QQ^T of it is the
+// residual b - QQ^T A_L u (QQ^T (b / mult) = b for continuous b).
 template <class T>
-int ax_local(const Level& lv, const T* u, T* y, bool mask_in, cudaStream_t s);
+int ax_local(const Level& lv, const T* u, T* y, bool mask_in, cudaStream_t s,
+             const T* sub = nullptr);
 template <class T>
 int gs_apply(const Level& lv, T* u, bool mask, cudaStream_t s);
 template <class T>
 inline int ax_apply(const Level& lv, const T* u, T* y, cudaStream_t s) {
   SE_TRY(ax_local<T>(lv, u, y, false, s));
   return gs_apply<T>(lv, y, true, s);
+}
+// r = b - A u (masked), one operator pass: no separate subtraction over the vector.
+template <class T>
+inline int residual_apply(const Level& lv, const T* b, const T* u, T* r, cudaStream_t s) {
+  SE_TRY(ax_local<T>(lv, u, r, false, s, b));
+  return gs_apply<T>(lv, r, true, s);
+}
+
+// Output of an operator kernel at local point idx: acc, or b / multiplicity - acc.
+template <class T>
+__device__ __forceinline__ T ax_output(T acc, const T* __restrict__ sub,
+                                       const uint8_t* __restrict__ pflag, int64_t idx) {
+  if (!sub) return acc;
+  const int mlog = __ffs(pflag[idx] & 0x0F) - 1;  // 1/multiplicity = 2^-mlog, exact
+  const T w = mlog == 0 ? T(1) : (mlog == 1 ? T(0.5) : (mlog == 2 ? T(0.25) : T(0.125)));
+  return sub[idx] * w - acc;
 }
 // Elementwise and reduction kernels (blas.cu)
 int dot_weighted(const Level& lv, const double* a, const double* b, double* dst_dev,
@@ -208,7 +227,7 @@ template <class T>
 int axpby(T a, const T* x, T b, const T* y, T* out, int64_t n, cudaStream_t s);  // out=a x+b y
 template <class T>
 int cheb_update(T* x, T* d, T* r, const T* sv, const T* dinv, int64_t n, T c1, T c2,
-                bool first, cudaStream_t s);
+                bool first, cudaStream_t s, T scale = T(1), bool from_r = false, bool last = false);
 template <class T>
 int scale_mul(const T* a, const T* b, T* out, int64_t n, cudaStream_t s);  // out = a*b
 // FP64 Krylov kernels with device scalars (slots of Scratch::scal)
@@ -290,11 +309,11 @@ int ax_elems_per_block(int p, bool fp32);
 // FP32 Ax pipelined with TMA bulk copies (even N only); device status of its bounded waits.
 bool ax_tma_supported(int p);
 int ax_tma_group(int p);
-int ax_local_tma(const Level& lv, const float* u, float* y, cudaStream_t s);
+int ax_local_tma(const Level& lv, const float* u, float* y, cudaStream_t s, const float* sub);
 // FP64 Ax with even-odd folded contractions (even N).
 bool ax_eo_supported(int p);
 void ax_eo_tables(const Basis1D& b, double* out);
-int ax_local_eo(const Level& lv, const double* u, double* y, cudaStream_t s);
+int ax_local_eo(const Level& lv, const double* u, double* y, cudaStream_t s, const double* sub);
 int pipeline_status_take(int* status);
 int fdm_elems_per_block(int p, bool fp32);
 size_t fdm_smem_bytes(int p, bool fp32, int ne);

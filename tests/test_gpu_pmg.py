@@ -112,6 +112,27 @@ def test_fp32_vcycle_against_fp64_oracle(smoother):
         c.close()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("order", [0, 1, 2, 3])
+@pytest.mark.parametrize("smoother", ["ras", "jacobi"])
+def test_chebyshev_orders(order, smoother, precision):
+    """Algorithm 2 at every Chebyshev order the tests use (0 = the plain smoother step r/theta);
+    the first step applies A and S to r and scales by 1/theta, the last one folds in the final
+    x += d.  FP64 1e-9 (as the other smoother checks); FP32 1e-4."""
+    c, P, pmg = build((3, 2, 2), 5, (5, 3, 1), smoother, order=order, precision=precision)
+    try:
+        lv = pmg.levels[0]
+        r = c.random_continuous(33)
+        out = c.empty()
+        c.se.se_pmg_cheby(P, 0, c.to_gpu(r), out)
+        lmin, lmax = pmg.bounds[0]
+        ref = o.chebyshev(r, lambda u: o.ax(lv, u), o.smoother_op(pmg, 0), lmin, lmax, order)
+        assert rel_err(c.to_np(out, lv.gid.shape), ref) <= (1e-4 if precision else 1e-9)
+    finally:
+        c.se.se_pmg_destroy(P)
+        c.close()
+
+
 @pytest.mark.parametrize("p", range(2, 11))
 @pytest.mark.parametrize("smoother", ["ras", "asm"])
 def test_fp32_schwarz_smoother_all_orders(p, smoother):
