@@ -176,8 +176,9 @@ int ax_local(const Level& lv, const T* u, T* y, bool mask_in, cudaStream_t s, co
 //      interface copies by shuffles (below);
 //   y: lanes run along i: rows of N contiguous copies;
 //   z: lanes run along (i, j): planes of N^2 contiguous copies.
-// Masking (Dirichlet) zeroes the copies on Dirichlet faces first (a node on such a face has all
-// its copies there), so the sweeps then add zeros for masked nodes.
+// Masking (Dirichlet) zeroes the copies on Dirichlet faces within the x sweep, before any sum (a
+// node on such a face has all its copies there), so the sweeps then add zeros for masked nodes;
+// a lattice one element wide in x has a separate mask kernel.
 constexpr int GS_X_SEG = 8;  // x-interfaces per warp
 
 // x sweep: a warp holds R = 32/N consecutive rows (j, k) of an element (lane = (row, i); the
@@ -190,8 +191,11 @@ constexpr int GS_X_SEG = 8;  // x-interfaces per warp
 // overlap by one element, and no two runs write the same copy: a run writes the row ends of its
 // interfaces only); it always loads GS_X_SEG + 1 elements (indices clamped to the last element of
 // the row) so that all loads are issued back to back.
+// With Dirichlet bits (mask), the x sweep also applies the mask: a copy whose node lies on a
+// Dirichlet face is zeroed before the sums and stored as zero (every copy of every element passes
+// through some run, and a node's copies are all masked or none, so overlapping runs agree).
 template <typename T, int N>
-__global__ void __launch_bounds__(256) gs_sweep_x(int nx, int ny, int nz, T* __restrict__ u) {
+__global__ void __launch_bounds__(256) gs_sweep_x(int nx, int ny, int nz, int bits, T* __restrict__ u) {
   constexpr int N3 = N * N * N, R = 32 / N, NG = (N * N + R - 1) / R, SEG = GS_X_SEG;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -213,6 +217,22 @@ __global__ void __launch_bounds__(256) gs_sweep_x(int nx, int ny, int nz, T* __r
   T v[SEG + 1];
 #pragma unroll
   for (int m = 0; m <= SEG; ++m) v[m] = u[(e0 + min(m, cnt)) * N3 + off];
+  if (bits) {
+    const int j = jk % N, k = jk / N;
+    const int ey = (int)(row_e % ny), ez = (int)(row_e / ny);
+    const bool myz = ((bits & 4) && j == 0 && ey == 0) || ((bits & 8) && j == N - 1 && ey == ny - 1) ||
+                     ((bits & 16) && k == 0 && ez == 0) || ((bits & 32) && k == N - 1 && ez == nz - 1);
+#pragma unroll
+    for (int m = 0; m <= SEG; ++m) {
+      if (m > cnt) break;
+      const int ex = ex0 + m;
+      const bool msk = myz || ((bits & 1) && i == 0 && ex == 0) || ((bits & 2) && i == N - 1 && ex == nx - 1);
+      if (on && msk) {
+        v[m] = T(0);
+        u[(e0 + m) * N3 + off] = T(0);
+      }
+    }
+  }
   // lane (r, p) holds the left copy (element m), lane (r, 0) the right copy (element m + 1):
   // one shuffle swaps them, one store writes both (each lane its own element)
   const bool left = i == N - 1, right = i == 0;
@@ -312,11 +332,12 @@ static int gs_sweeps(const Level& lv, T* u, bool mask, double bytes, double flop
   const int nx = lv.nel[0], ny = lv.nel[1], nz = lv.nel[2];
   constexpr int N2 = N * N;
   const int var = prof_variant<T>(lv.p);
-  if (mask) {
-    int bits = 0;
+  int bits = 0;
+  if (mask)
     for (int f = 0; f < 6; ++f)
       if (lv.bc[f] == SE_BC_DIRICHLET) bits |= 1 << f;
-    if (bits) {
+  if (bits && nx == 1) {  // no x sweep to carry the mask
+    {
       const int64_t n = 2 * N2 * ((int64_t)ny * nz + (int64_t)nx * nz + (int64_t)nx * ny);
       ProfScope prof(SE_K_GS, s, (double)n, 0.0, 0.0, var);
       gs_mask_faces<T, N><<<grid_for(n, 256), 256, 0, s>>>(nx, ny, nz, bits, u);
@@ -327,7 +348,7 @@ static int gs_sweeps(const Level& lv, T* u, bool mask, double bytes, double flop
     constexpr int R = 32 / N, NG = (N * N + R - 1) / R;
     const int64_t warps = (int64_t)ny * nz * NG * ((nx - 1 + GS_X_SEG - 1) / GS_X_SEG);
     ProfScope prof(SE_K_GS, s, (double)lv.L, bytes, flops, var);
-    gs_sweep_x<T, N><<<grid_for(32 * warps, 256), 256, 0, s>>>(nx, ny, nz, u);
+    gs_sweep_x<T, N><<<grid_for(32 * warps, 256), 256, 0, s>>>(nx, ny, nz, bits, u);
     SE_LAUNCH_CHECK();
   }
   if (ny > 1) {
