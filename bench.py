@@ -443,10 +443,10 @@ def run_batch(args):
 SERVE_SCHEDULES = {5: (5, 3, 1), 7: (7, 3, 1), 9: (9, 5, 1)}
 
 
-def serve_stream(se, reqs, budget, slots, precision, t_scale=1.0):
+def serve_stream(se, reqs, budget, slots, precision, t_scale=1.0, proj=0):
     """Submit `reqs` at their (scaled) arrival times, wait for all, return the server summary."""
     import workloads as wl
-    S = se.se_serve_create(budget, slots)
+    S = se.se_serve_create(budget, slots, proj_vectors=proj)
     tickets, keep = [], []
     refused = 0
     t0 = time.perf_counter()
@@ -481,7 +481,9 @@ def serve_stream(se, reqs, budget, slots, precision, t_scale=1.0):
             "mesh_reuses": st.mesh_reuses, "evictions": st.evictions, "wall_s": round(wall, 1),
             "iterations_min_max": [min(its), max(its)] if its else None, "worst_rel_residual": worst,
             "mean_setup_ms_new_mesh": round(statistics.mean(setups), 1) if setups else None,
-            "mean_solve_ms": round(statistics.mean(solves), 1) if solves else None}
+            "mean_solve_ms": round(statistics.mean(solves), 1) if solves else None,
+            "proj_vectors": proj, "projected": st.projected,
+            "mean_iterations": round(statistics.mean(its), 2) if its else None}
 
 
 def run_serve(args):
@@ -497,7 +499,12 @@ def run_serve(args):
     budget = int(0.8 * free)
     reqs = wl.serve_requests(n=args.serve, rate=args.rate, seed=0)
     with ClockSampler(0) as clk:
-        served = serve_stream(se, reqs, budget, args.slots, se.SE_FP32)
+        served = serve_stream(se, reqs, budget, args.slots, se.SE_FP32, proj=args.proj)
+    low = None
+    if args.low_rate > 0:  # the same kind of stream at a rate below capacity: latency unqueued
+        low_reqs = wl.serve_requests(n=args.low_n, rate=args.low_rate, seed=1)
+        low = serve_stream(se, low_reqs, budget, args.slots, se.SE_FP32, proj=args.proj)
+        low["rate"] = args.low_rate
     base_reqs = reqs[:args.serve_baseline] if args.serve_baseline else reqs
     serial = serve_stream(se, base_reqs, budget, 1, se.SE_FP64)
     out = {"metric": "served Poisson solves: solves/s, p50/p99 latency", "value": served["solves_per_s"],
@@ -507,6 +514,8 @@ def run_serve(args):
                                   f"[512, 65536], p in {{5,7,9}}, 30% resident-mesh reuse, tol 1e-8",
                       "slots": args.slots, "hbm_budget_GB": round(budget / 2 ** 30, 1)},
            "served": served, "serial_fp64": serial, "clocks": clk.summary()}
+    if low is not None:
+        out["served_below_capacity"] = low
     print(json.dumps(out))
 
 
@@ -604,6 +613,11 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--serve-baseline", type=int, default=0)
+    ap.add_argument("--low-rate", type=float, default=0.0,
+                    help="serving: also run a stream at this (below-capacity) rate")
+    ap.add_argument("--low-n", type=int, default=100)
+    ap.add_argument("--proj", type=int, default=0,
+                    help="serving: prior solutions kept per resident mesh for the initial guess")
     ap.add_argument("--precision-study", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":

@@ -185,19 +185,23 @@ int se_pmg_coarse_solve_noalloc(se_pmg_t pmg, const double* r, double* x, int* i
 typedef struct se_solve_opts {
   int method;        /* SE_FPCG (flexible CG) or SE_FGMRES (right-preconditioned, flexible) */
   int restart;       /* FGMRES restart length m (paper: 20) */
-  double tol;        /* stop when ||r_k||_2 / ||r_0||_2 <= tol (unique-node 2-norm) */
+  double tol;        /* stop when ||r_k||_2 / ||r_0||_2 <= tol (unique-node 2-norm; see tol_norm) */
   int maxit;
   int graph_capture; /* 1 (SE_FPCG only): the whole solve runs as one CUDA graph launch whose
                         iteration loop is a device-side WHILE node (no host round trip per
                         iteration); the graph is cached per mesh for the same pmg, b, x, tol,
                         maxit and rebuilt when one of them changes */
   void* stream;      /* NULL: the mesh's stream */
+  int tol_norm;      /* SE_TOL_R0 (0): stop when ||r_k|| <= tol ||r_0||; SE_TOL_B (1): when
+                        ||r_k|| <= tol ||b|| (for an initial guess from se_proj_guess: the same
+                        accuracy whatever the guess; 0 iterations if the guess already meets it) */
 } se_solve_opts;
+enum { SE_TOL_R0 = 0, SE_TOL_B = 1 };
 
 typedef struct se_solve_stats {
   int iterations;
   int status;
-  double rel_residual;   /* final ||r||/||r_0|| as tracked by the method */
+  double rel_residual;   /* final ||r||/||r_0|| (SE_TOL_B: ||r||/||b||) as tracked by the method */
   double ms_total;       /* wall time of the solve (events on the stream) */
   double ms_precond;     /* time inside preconditioner applications */
   double ms_operator;    /* time inside outer operator applications */
@@ -207,6 +211,24 @@ typedef struct se_solve_stats {
  * Returns SE_ENOTCONV (stats filled) if maxit is reached.  Synchronises. */
 int se_solve(se_mesh_t m, se_pmg_t pmg, const double* b, double* x, const se_solve_opts* opts,
              se_solve_stats* stats);
+
+/* ---------------------------------------------------------------- projection (Sec. 4) */
+/* A space of up to max_vectors (1..16) prior solutions of A x = b on mesh m, for successive
+ * right-hand sides (the paper projects each pressure solve onto up to 10 prior solutions,
+ * Fischer's method): kept A-orthonormal, x_i^T A x_j = delta_ij, with the images A x_i.  Device
+ * memory 2 * max_vectors * L doubles, owned by the handle.  The calls below use the mesh's
+ * reduction scratch: do not overlap them with a solve on the same mesh. */
+typedef struct se_proj_s* se_proj_t;
+int se_proj_create(se_mesh_t m, int max_vectors, se_proj_t* out);
+int se_proj_destroy(se_proj_t proj);
+/* x = sum_i (x_i, b) x_i: the element of the space closest to A^-1 b in the A-norm (no operator
+ * application); x = 0 for an empty space.  Solve from this x with tol_norm = SE_TOL_B. */
+int se_proj_guess(se_proj_t proj, const double* b, double* x, void* stream);
+/* Adds the solution x (FP64 L-vector, continuous): A-orthogonalised against the space by two
+ * modified Gram-Schmidt passes, its image by one operator application, normalised.  A full space
+ * restarts from x alone; a remainder below 1e-7 of ||x||_A (x already in the space) is not
+ * added.  *size (optional) receives the vectors held.  Synchronises the stream. */
+int se_proj_update(se_proj_t proj, const double* x, int* size, void* stream);
 
 /* ---------------------------------------------------------------- batched solves */
 /* Many independent problems solved together (flexible PCG, device-driven): every problem's
@@ -290,6 +312,10 @@ typedef struct se_serve_cfg {
   size_t hbm_budget;       /* bytes of device memory the resident meshes may occupy */
   int max_slots;           /* requests in flight (being set up or solved) at once */
   int builders;            /* threads that build new meshes concurrently (0: min(4, max_slots)) */
+  int proj_vectors;        /* 0: every solve starts from x = 0; 1..16: each resident mesh keeps a
+                              projection space of that many prior solutions (se_proj_*), a
+                              request on it starts from the projected guess and stops when
+                              ||r|| <= tol ||b|| (counted in the footprint) */
 } se_serve_cfg;
 typedef struct se_serve_stats {
   int64_t submitted, completed, refused, failed, pending;
@@ -298,6 +324,7 @@ typedef struct se_serve_stats {
   int max_concurrent;
   int64_t meshes_created, mesh_reuses, evictions;
   size_t resident_bytes;
+  int64_t projected;       /* requests that started from a non-zero projected guess */
 } se_serve_summary;
 typedef struct se_server_s* se_server_t;
 int se_serve_create(const se_serve_cfg* cfg, se_server_t* out);

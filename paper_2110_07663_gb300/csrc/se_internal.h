@@ -176,6 +176,7 @@ struct se_mesh_s {
   const void* gkey[4] = {nullptr, nullptr, nullptr, nullptr};  // pmg, b, x, opts hash
   double gtol = 0.0;
   int gmaxit = 0;
+  int gtolnorm = 0;
 };
 
 namespace se {

@@ -69,6 +69,8 @@ struct Resident {
   uint64_t key = 0;
   se_mesh_t m = nullptr;
   se_pmg_t P = nullptr;
+  se_proj_t proj = nullptr;    // prior solutions (server option)
+  bool has_solution = false;   // x holds the last completed solve, not yet in proj
   double* b = nullptr;
   double* x = nullptr;
   size_t bytes = 0;
@@ -88,6 +90,7 @@ struct Ticket {
   double rel = 0.0;
   Resident* res = nullptr;
   cudaEvent_t ev = nullptr;
+  int proj_size = 0;           // vectors in the mesh's projection space when the solve started
 };
 
 }  // namespace se
@@ -109,7 +112,7 @@ struct se_server_s {
   std::vector<se::Resident*> residents;
   size_t used = 0;
   int64_t submitted = 0, completed = 0, refused = 0, failed = 0, created = 0, reused = 0,
-          evicted = 0;
+          evicted = 0, projected = 0;
   int max_running = 0;
   double t_first = 0, t_last = 0;
   std::vector<double> latencies;
@@ -118,6 +121,7 @@ struct se_server_s {
 namespace se {
 
 static void destroy_resident(Resident* r) {
+  if (r->proj) se_proj_destroy(r->proj);
   if (r->P) se_pmg_destroy(r->P);
   if (r->m) {
     if (r->b) cudaFreeAsync(r->b, r->m->stream);
@@ -142,7 +146,14 @@ static bool make_room(se_server_s* S, size_t need) {
   return true;
 }
 
-static int build_resident(const se_request& q, Resident** out) {
+// Device bytes of a request's mesh as this server keeps it (with its projection space).
+static size_t need_bytes(const se_server_s* S, const se_request& q) {
+  const double L = (double)q.mesh.nel[0] * q.mesh.nel[1] * q.mesh.nel[2] * (q.mesh.p + 1) *
+                   (q.mesh.p + 1) * (q.mesh.p + 1);
+  return footprint_bytes(q.mesh, q.pmg) + (size_t)(2.0 * S->cfg.proj_vectors * L * sizeof(double));
+}
+
+static int build_resident(const se_request& q, int proj_vectors, Resident** out) {
   se_mesh_desc d = q.mesh;
   d.flags |= SE_MESH_NONBLOCKING_STREAM;
   auto* r = new Resident();
@@ -157,11 +168,13 @@ static int build_resident(const se_request& q, Resident** out) {
       rc = SE_ENOMEM;
     }
   }
+  if (rc == SE_OK && proj_vectors > 0) rc = se_proj_create(r->m, proj_vectors, &r->proj);
   if (rc != SE_OK) {
     destroy_resident(r);
     return rc;
   }
-  r->bytes = r->m->allocs.bytes + r->P->allocs.bytes + 2 * r->L * sizeof(double);
+  r->bytes = r->m->allocs.bytes + r->P->allocs.bytes + 2 * r->L * sizeof(double) +
+             (size_t)(r->proj ? 2.0 * proj_vectors * r->L * sizeof(double) : 0.0);
   *out = r;
   return SE_OK;
 }
@@ -169,13 +182,22 @@ static int build_resident(const se_request& q, Resident** out) {
 static int start_ticket(Ticket* t) {
   Resident* r = t->res;
   cudaStream_t s = r->m->stream;
+  if (r->proj && r->has_solution) {  // the previous request's solution joins the space
+    SE_TRY(se_proj_update(r->proj, r->x, &t->proj_size, s));
+    r->has_solution = false;
+  }
   if (t->req.rhs_kind == SE_RHS_HOST) {
     SE_CUDA(cudaMemcpyAsync(r->b, t->b_host.data(), r->L * sizeof(double), cudaMemcpyHostToDevice, s));
   } else {
     SE_TRY(rhs_modes(r->m, t->req.modes, t->req.amplitude, r->b, s));
   }
-  SE_CUDA(cudaMemsetAsync(r->x, 0, r->L * sizeof(double), s));
-  SE_TRY(graph_solve_launch(r->m, r->P, r->b, r->x, t->req.tol, t->req.maxit, s));
+  if (r->proj) {
+    SE_TRY(se_proj_guess(r->proj, r->b, r->x, s));
+  } else {
+    SE_CUDA(cudaMemsetAsync(r->x, 0, r->L * sizeof(double), s));
+  }
+  SE_TRY(graph_solve_launch(r->m, r->P, r->b, r->x, t->req.tol, t->req.maxit, s,
+                            r->proj ? SE_TOL_B : SE_TOL_R0));
   if (!t->ev) SE_CUDA(cudaEventCreateWithFlags(&t->ev, cudaEventDisableTiming));
   SE_CUDA(cudaEventRecord(t->ev, s));
   return SE_OK;
@@ -194,6 +216,8 @@ static void finish_ticket(se_server_s* S, Ticket* t) {
   t->t_done = now_ms();
   t->done = true;
   r->busy = false;
+  r->has_solution = r->proj && rc == SE_OK;
+  if (t->proj_size > 0) ++S->projected;
   r->last_used = t->t_done;
   if (rc == SE_OK) {
     ++S->completed;
@@ -241,7 +265,7 @@ static void scheduler(se_server_s* S) {
         continue;
       }
       if (!r) {
-        const size_t need = footprint_bytes(t->req.mesh, t->req.pmg);
+        const size_t need = need_bytes(S, t->req);
         if (!make_room(S, need)) break;  // wait for memory to free up
         S->queue.erase(S->queue.begin() + qi);
         S->used += need;                 // reserved while the mesh is built
@@ -289,11 +313,11 @@ static void builder(se_server_s* S) {
     if (S->build_q.empty()) break;  // stopping, nothing left to build
     Ticket* t = S->build_q.front();
     S->build_q.pop_front();
-    const size_t need = footprint_bytes(t->req.mesh, t->req.pmg);
+    const size_t need = need_bytes(S, t->req);
     lk.unlock();
     const double tb = now_ms();
     Resident* r = nullptr;
-    int rc = build_resident(t->req, &r);
+    int rc = build_resident(t->req, S->cfg.proj_vectors, &r);
     t->setup_ms = now_ms() - tb;
     if (rc == SE_OK) {
       // not yet visible to the scheduler: its first solve starts outside the lock
@@ -343,6 +367,8 @@ int se_serve_create(const se_serve_cfg* cfg, se_server_t* out) {
   SE_CHECK(cfg && out, SE_EINVAL, "se_serve_create: null argument");
   SE_CHECK(cfg->max_slots >= 1 && cfg->max_slots <= 256, SE_EINVAL, "se_serve_create: max_slots");
   SE_CHECK(cfg->builders >= 0 && cfg->builders <= 64, SE_EINVAL, "se_serve_create: builders");
+  SE_CHECK(cfg->proj_vectors >= 0 && cfg->proj_vectors <= 16, SE_EINVAL,
+           "se_serve_create: proj_vectors");
   SE_CHECK(cfg->hbm_budget > 0, SE_EINVAL, "se_serve_create: hbm_budget");
   auto* S = new se_server_s();
   S->cfg = *cfg;
@@ -371,7 +397,7 @@ int se_serve_submit(se_server_t S, const se_request* req, uint64_t* ticket) {
   if (ok && q.rhs_kind == SE_RHS_HOST) ok = q.b_host != nullptr;
   SE_CHECK(ok, SE_EINVAL, "se_serve_submit: malformed request");
   const double t_arrival = now_ms();
-  const size_t need = footprint_bytes(q.mesh, q.pmg);
+  const size_t need = need_bytes(S, q);
   std::lock_guard<std::mutex> g(S->mu);
   ++S->submitted;
   if (need > S->cfg.hbm_budget) {
@@ -466,6 +492,7 @@ int se_serve_stats(se_server_t S, se_serve_summary* out) {
   out->mesh_reuses = S->reused;
   out->evictions = S->evicted;
   out->resident_bytes = S->used;
+  out->projected = S->projected;
   return SE_OK;
 }
 

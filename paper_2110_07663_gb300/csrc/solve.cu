@@ -52,12 +52,13 @@ static int fpcg(se_mesh_s* m, se_pmg_s* P, const double* b, double* x, const se_
   SE_TRY(axpby<double>(1.0, b, -1.0, w, r, lv.L, s));         // r = b - A x
   SE_TRY(precondition(m, P, r, z, s));
   SE_TRY(fpcg_init(lv, r, z, sc, s));                           // rz, rr, r0
+  if (o.tol_norm == SE_TOL_B) SE_TRY(dot_to_slot(lv, b, b, sc, SC_R0, s));  // reference ||b||
   SE_CUDA(cudaMemcpyAsync(p, z, lv.L * sizeof(double), cudaMemcpyDeviceToDevice, s));
   SE_TRY(read_scalars(m, s, SC_R0 + 1));
   const double r0 = std::sqrt(sc.hscal[SC_R0]);
   st->iterations = 0;
-  st->rel_residual = r0 > 0 ? 1.0 : 0.0;
-  if (r0 == 0.0) return SE_OK;
+  st->rel_residual = r0 > 0 ? std::sqrt(sc.hscal[SC_RR]) / r0 : 0.0;
+  if (r0 == 0.0 || st->rel_residual <= o.tol) return SE_OK;
   for (int it = 1; it <= o.maxit; ++it) {
     SE_TRY(ax_apply<double>(lv, p, w, s));                      // w = A p
     SE_TRY(fpcg_alpha(lv, p, w, sc, s));                        // alpha = rz / (p, w)
@@ -97,12 +98,13 @@ static int fgmres(se_mesh_s* m, se_pmg_s* P, const double* b, double* x, const s
   SE_TRY(ax_apply<double>(lv, x, w, s));
   SE_TRY(axpby<double>(1.0, b, -1.0, w, r, L, s));
   SE_TRY(dot_to_slot(lv, r, r, sc, SC_NORM, s));
+  if (o.tol_norm == SE_TOL_B) SE_TRY(dot_to_slot(lv, b, b, sc, SC_TMP, s));
   SE_TRY(read_scalars(m, s, SC_NORM + 1));
-  const double r0 = std::sqrt(sc.hscal[SC_NORM]);
-  double beta = r0;
+  double beta = std::sqrt(sc.hscal[SC_NORM]);
+  const double r0 = o.tol_norm == SE_TOL_B ? std::sqrt(sc.hscal[SC_TMP]) : beta;  // reference
   st->iterations = 0;
-  st->rel_residual = r0 > 0 ? 1.0 : 0.0;
-  if (r0 == 0.0) return SE_OK;
+  st->rel_residual = r0 > 0 ? beta / r0 : 0.0;
+  if (r0 == 0.0 || beta == 0.0 || st->rel_residual <= o.tol) return SE_OK;
   std::vector<double> H((mr + 1) * mr), cs(mr), sn(mr), g(mr + 1), y(mr);
   int total = 0;
   while (total < o.maxit) {
@@ -177,6 +179,7 @@ extern "C" int se_solve(se_mesh_t m, se_pmg_t P, const double* b, double* x,
   se_solve_opts o = *opts;
   SE_CHECK(o.method == SE_FPCG || o.method == SE_FGMRES, SE_EINVAL, "se_solve: bad method");
   SE_CHECK(o.tol > 0 && o.maxit >= 1, SE_EINVAL, "se_solve: bad tolerance or maxit");
+  SE_CHECK(o.tol_norm == SE_TOL_R0 || o.tol_norm == SE_TOL_B, SE_EINVAL, "se_solve: bad tol_norm");
   if (o.method == SE_FGMRES) SE_CHECK(o.restart >= 1 && o.restart <= 200, SE_EINVAL, "se_solve: restart");
   cudaStream_t s = as_stream(o.stream, m->stream);
   SE_TRY(ensure_solve_work(m, o.restart, o.method == SE_FGMRES));
@@ -214,13 +217,14 @@ struct DevStats {
   double rel;
 };
 
-__global__ void fpcg_graph_init_kernel(const double* __restrict__ scal, DevStats* st, int maxit,
-                                       cudaGraphConditionalHandle hw) {
-  const double r0 = scal[SC_R0];
+__global__ void fpcg_graph_init_kernel(const double* __restrict__ scal, DevStats* st, double tol,
+                                       int maxit, cudaGraphConditionalHandle hw) {
+  const double ref = scal[SC_R0];  // ||r_0||^2, or ||b||^2 (SE_TOL_B)
+  const double rel = ref > 0.0 ? sqrt(scal[SC_RR] / ref) : 0.0;
   st->iterations = 0;
   st->status = 0;
-  st->rel = r0 > 0.0 ? 1.0 : 0.0;
-  cudaGraphSetConditional(hw, (r0 > 0.0 && maxit > 0) ? 1u : 0u);
+  st->rel = rel;
+  cudaGraphSetConditional(hw, (ref > 0.0 && rel > tol && maxit > 0) ? 1u : 0u);
 }
 
 __global__ void fpcg_graph_check_kernel(const double* __restrict__ scal, DevStats* st, double tol,
@@ -259,7 +263,7 @@ static int add_conditional(cudaStream_t cs, cudaGraphConditionalHandle h,
 // Appends one whole FPCG solve (x0 = the content of x at launch) to graph G, independent of the
 // rest of G.  All buffers must already exist: nothing is allocated while capturing.
 static int append_fpcg_solve(cudaGraph_t G, cudaStream_t cs, se_mesh_s* m, se_pmg_s* P,
-                             const double* b, double* x, double tol, int maxit) {
+                             const double* b, double* x, double tol, int maxit, int tol_norm) {
   const Level& lv = m->fine;
   Scratch& sc = m->scratch;
   double *r = m->sr, *r_old = m->sr2, *z = m->sz, *p = m->sp, *w = m->sw;
@@ -275,12 +279,13 @@ static int append_fpcg_solve(cudaGraph_t G, cudaStream_t cs, se_mesh_s* m, se_pm
     if ((rc = axpby<double>(1.0, b, -1.0, w, r, lv.L, cs)) != SE_OK) break;
     if ((rc = precondition(m, P, r, z, cs)) != SE_OK) break;
     if ((rc = fpcg_init(lv, r, z, sc, cs)) != SE_OK) break;
+    if (tol_norm == SE_TOL_B && (rc = dot_to_slot(lv, b, b, sc, SC_R0, cs)) != SE_OK) break;
     if (cudaMemcpyAsync(p, z, lv.L * sizeof(double), cudaMemcpyDeviceToDevice, cs) != cudaSuccess) {
       set_error("graph build: copy capture failed");
       rc = SE_ECUDA;
       break;
     }
-    fpcg_graph_init_kernel<<<1, 1, 0, cs>>>(sc.scal, st, maxit, hw);
+    fpcg_graph_init_kernel<<<1, 1, 0, cs>>>(sc.scal, st, tol, maxit, hw);
     rc = add_conditional(cs, hw, cudaGraphCondTypeWhile, &wbody);
   } while (0);
   cudaGraph_t out = nullptr;
@@ -339,10 +344,10 @@ static int read_graph_stats(se_mesh_s* m, cudaStream_t s, se_solve_stats* out, d
 // Builds (or reuses) this mesh's solve graph for (P, b, x, tol, maxit) and launches it on s
 // without waiting.  read_graph_stats collects the result.
 int graph_solve_launch(se_mesh_s* m, se_pmg_s* P, const double* b, double* x, double tol,
-                       int maxit, cudaStream_t s) {
+                       int maxit, cudaStream_t s, int tol_norm) {
   SE_TRY(prepare_graph_solve(m));
   const bool same = m->gexec && m->gkey[0] == P && m->gkey[1] == b && m->gkey[2] == x &&
-                    m->gtol == tol && m->gmaxit == maxit;
+                    m->gtol == tol && m->gmaxit == maxit && m->gtolnorm == tol_norm;
   if (!same) {
     if (m->gexec) cudaGraphExecDestroy(m->gexec);
     m->gexec = nullptr;
@@ -350,7 +355,7 @@ int graph_solve_launch(se_mesh_s* m, se_pmg_s* P, const double* b, double* x, do
     SE_CUDA(cudaGraphCreate(&G, 0));
     cudaStream_t cs;
     SE_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    int rc = append_fpcg_solve(G, cs, m, P, b, x, tol, maxit);
+    int rc = append_fpcg_solve(G, cs, m, P, b, x, tol, maxit, tol_norm);
     cudaStreamDestroy(cs);
     if (rc == SE_OK) {
       cudaError_t e = cudaGraphInstantiate(&m->gexec, G, 0);
@@ -367,6 +372,7 @@ int graph_solve_launch(se_mesh_s* m, se_pmg_s* P, const double* b, double* x, do
     m->gkey[2] = x;
     m->gtol = tol;
     m->gmaxit = maxit;
+    m->gtolnorm = tol_norm;
   }
   SE_CUDA(cudaGraphLaunch(m->gexec, s));
   return SE_OK;
@@ -379,7 +385,7 @@ int graph_solve_result(se_mesh_s* m, cudaStream_t s, double tol, int maxit, se_s
 // se_solve with graph_capture: one launch of the cached graph, then its statistics.
 int graph_solve(se_mesh_s* m, se_pmg_s* P, const double* b, double* x, const se_solve_opts& o,
                 cudaStream_t s, se_solve_stats* st) {
-  SE_TRY(graph_solve_launch(m, P, b, x, o.tol, o.maxit, s));
+  SE_TRY(graph_solve_launch(m, P, b, x, o.tol, o.maxit, s, o.tol_norm));
   return read_graph_stats(m, s, st, o.tol, o.maxit);
 }
 
@@ -397,6 +403,8 @@ int se_batch_create(int n, const se_problem* probs, const se_solve_opts* opts, s
   SE_CHECK(n >= 1 && probs && opts && out, SE_EINVAL, "se_batch_create: bad argument");
   SE_CHECK(opts->method == SE_FPCG, SE_EINVAL, "se_batch_create: batched solves use SE_FPCG");
   SE_CHECK(opts->tol > 0 && opts->maxit >= 1, SE_EINVAL, "se_batch_create: bad tolerance or maxit");
+  SE_CHECK(opts->tol_norm == SE_TOL_R0 || opts->tol_norm == SE_TOL_B, SE_EINVAL,
+           "se_batch_create: bad tol_norm");
   for (int i = 0; i < n; ++i) {
     SE_CHECK(probs[i].mesh && probs[i].b && probs[i].x, SE_EINVAL, "se_batch_create: problem %d incomplete", i);
     SE_CHECK(!probs[i].pmg || probs[i].pmg->mesh == probs[i].mesh, SE_EINVAL,
@@ -420,7 +428,7 @@ int se_batch_create(int n, const se_problem* probs, const se_solve_opts* opts, s
   int rc = SE_OK;
   for (int i = 0; i < n && rc == SE_OK; ++i)
     rc = append_fpcg_solve(G, cs, probs[i].mesh, probs[i].pmg, probs[i].b, probs[i].x, opts->tol,
-                           opts->maxit);
+                           opts->maxit, opts->tol_norm);
   cudaStreamDestroy(cs);
   if (rc == SE_OK && cudaGraphInstantiate(&B->exec, G, 0) != cudaSuccess) {
     set_error("se_batch_create: cudaGraphInstantiate: %s", cudaGetErrorString(cudaGetLastError()));

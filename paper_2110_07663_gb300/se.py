@@ -18,6 +18,7 @@ SE_BC_DIRICHLET, SE_BC_NEUMANN = 0, 1
 SE_FP64, SE_FP32 = 0, 1
 SE_SMOOTH_JACOBI, SE_SMOOTH_RAS, SE_SMOOTH_ASM = 0, 1, 2
 SE_FPCG, SE_FGMRES = 0, 1
+SE_TOL_R0, SE_TOL_B = 0, 1
 SE_AX_ASSEMBLE, SE_AX_MASK, SE_AX_FP32 = 1, 2, 4
 SE_MESH_NONBLOCKING_STREAM = 1
 SE_RHS_MODES, SE_RHS_HOST = 0, 1
@@ -57,7 +58,8 @@ class se_pmg_desc(C.Structure):
 
 class se_solve_opts(C.Structure):
     _fields_ = [("method", C.c_int), ("restart", C.c_int), ("tol", C.c_double),
-                ("maxit", C.c_int), ("graph_capture", C.c_int), ("stream", C.c_void_p)]
+                ("maxit", C.c_int), ("graph_capture", C.c_int), ("stream", C.c_void_p),
+                ("tol_norm", C.c_int)]
 
 
 class se_problem(C.Structure):
@@ -83,7 +85,8 @@ class se_result(C.Structure):
 
 
 class se_serve_cfg(C.Structure):
-    _fields_ = [("hbm_budget", C.c_size_t), ("max_slots", C.c_int), ("builders", C.c_int)]
+    _fields_ = [("hbm_budget", C.c_size_t), ("max_slots", C.c_int), ("builders", C.c_int),
+                ("proj_vectors", C.c_int)]
 
 
 class se_serve_summary(C.Structure):
@@ -91,7 +94,8 @@ class se_serve_summary(C.Structure):
                 ("failed", C.c_int64), ("pending", C.c_int64), ("solves_per_s", C.c_double),
                 ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double),
                 ("max_concurrent", C.c_int), ("meshes_created", C.c_int64),
-                ("mesh_reuses", C.c_int64), ("evictions", C.c_int64), ("resident_bytes", C.c_size_t)]
+                ("mesh_reuses", C.c_int64), ("evictions", C.c_int64), ("resident_bytes", C.c_size_t),
+                ("projected", C.c_int64)]
 
 
 class se_solve_stats(C.Structure):
@@ -141,6 +145,10 @@ _SIGS = {
     "se_tune_get": ([_ip, _ip, C.POINTER(se_tile_cfg)], C.c_int),
     "se_tune_set": ([C.POINTER(se_tile_cfg)], C.c_int),
     "se_mesh_footprint_bytes": ([C.POINTER(se_mesh_desc), C.POINTER(se_pmg_desc), C.POINTER(C.c_size_t)], C.c_int),
+    "se_proj_create": ([_vp, C.c_int, C.POINTER(_vp)], C.c_int),
+    "se_proj_destroy": ([_vp], C.c_int),
+    "se_proj_guess": ([_vp, _vp, _vp, _vp], C.c_int),
+    "se_proj_update": ([_vp, _vp, C.POINTER(C.c_int), _vp], C.c_int),
     "se_serve_create": ([C.POINTER(se_serve_cfg), C.POINTER(_vp)], C.c_int),
     "se_serve_submit": ([_vp, C.POINTER(se_request), C.POINTER(C.c_uint64)], C.c_int),
     "se_serve_poll": ([_vp, C.c_uint64, C.POINTER(se_result)], C.c_int),
@@ -326,14 +334,36 @@ def se_pmg_coarse_solve_noalloc(P, r, x, stream=None) -> int:
 
 # ----------------------------------------------------------------------------- solve
 def se_solve(m, P, b, x, method=SE_FPCG, tol=1e-8, maxit=1000, restart=20, graph_capture=0,
-             stream=None, allow_notconv=False) -> se_solve_stats:
+             stream=None, allow_notconv=False, tol_norm=0) -> se_solve_stats:
     o = se_solve_opts()
     o.method, o.restart, o.tol, o.maxit, o.graph_capture = method, restart, tol, maxit, graph_capture
+    o.tol_norm = tol_norm
     o.stream = _stream(stream)
     st = se_solve_stats()
     _check(lib.se_solve(m, P, _ptr(b), _ptr(x), C.byref(o), C.byref(st)),
            allow=(SE_ENOTCONV,) if allow_notconv else ())
     return st
+
+
+# ----------------------------------------------------------------------------- projection
+def se_proj_create(m, max_vectors=10):
+    h = _vp()
+    _check(lib.se_proj_create(m, int(max_vectors), C.byref(h)))
+    return h.value
+
+
+def se_proj_destroy(p):
+    _check(lib.se_proj_destroy(p))
+
+
+def se_proj_guess(p, b, x, stream=None):
+    _check(lib.se_proj_guess(p, _ptr(b), _ptr(x), _stream(stream)))
+
+
+def se_proj_update(p, x, stream=None) -> int:
+    n = C.c_int()
+    _check(lib.se_proj_update(p, _ptr(x), C.byref(n), _stream(stream)))
+    return n.value
 
 
 # ----------------------------------------------------------------------------- batched solves
@@ -344,9 +374,10 @@ def _problems(problems):
     return arr
 
 
-def _opts(tol, maxit, stream, method=SE_FPCG, restart=20, graph_capture=1):
+def _opts(tol, maxit, stream, method=SE_FPCG, restart=20, graph_capture=1, tol_norm=0):
     o = se_solve_opts()
     o.method, o.restart, o.tol, o.maxit, o.graph_capture = method, restart, tol, maxit, graph_capture
+    o.tol_norm = tol_norm
     o.stream = _stream(stream)
     return o
 
@@ -433,9 +464,10 @@ def make_request(mdesc, mesh_key, pdesc, modes=(1, 1, 1), amplitude=1.0, b_host=
     return q
 
 
-def se_serve_create(hbm_budget, max_slots, builders=0):
+def se_serve_create(hbm_budget, max_slots, builders=0, proj_vectors=0):
     c = se_serve_cfg()
     c.hbm_budget, c.max_slots, c.builders = int(hbm_budget), int(max_slots), int(builders)
+    c.proj_vectors = int(proj_vectors)
     h = _vp()
     _check(lib.se_serve_create(C.byref(c), C.byref(h)))
     return h.value

@@ -93,3 +93,38 @@ def test_budget_refusal_and_eviction():
         assert st.evictions >= 1 and st.resident_bytes <= 1.5 * need
     finally:
         se.se_serve_destroy(S)
+
+
+def test_projection_in_the_server():
+    """Requests on one resident mesh with right-hand sides from a small space: with projection
+    (proj_vectors = 4) later requests start from the projected guess and need (almost) no
+    iterations; every result meets the tolerance relative to ||b|| and agrees with the solve
+    from zero to the accuracy the tolerance gives."""
+    torch, se = gpu()
+    md = se.mesh_desc((3, 3, 3), 5, perturb_frac=0.05, seed=5)
+    pd = se.pmg_desc((5, 3, 1), se.SE_SMOOTH_RAS, 2, precision=se.SE_FP32)
+    L = 27 * 6 ** 3
+    modes = [(1, 1, 1), (2, 1, 1), (1, 1, 1), (2, 1, 1), (1, 1, 1), (1, 1, 1)]
+    amps = [1.0, 0.6, 1.7, 1.2, 0.4, 2.0]
+    out = {}
+    for nv in (0, 4):
+        S = se.se_serve_create(32 << 30, 2, proj_vectors=nv)
+        try:
+            xs, its = [], []
+            for k, a in zip(modes, amps):
+                x = np.full(L, np.nan)
+                q = se.make_request(md, 77, pd, modes=k, amplitude=a, x_host=x, tol=1e-8)
+                r = se.se_serve_wait(S, se.se_serve_submit(S, q))   # one at a time, in order
+                assert r.status == 0 and r.rel_residual <= 1e-8
+                xs.append(x)
+                its.append(r.iterations)
+            out[nv] = (xs, its, se.se_serve_stats(S))
+        finally:
+            se.se_serve_destroy(S)
+    xs0, its0, st0 = out[0]
+    xs4, its4, st4 = out[4]
+    assert st0.projected == 0 and st4.projected == len(modes) - 1
+    assert its4[0] == its0[0]
+    assert all(i <= 1 for i in its4[2:])        # b in the span of prior right-hand sides
+    for a, b in zip(xs4, xs0):
+        assert np.max(np.abs(a - b)) <= 1e-6 * np.max(np.abs(b))
