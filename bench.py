@@ -566,6 +566,57 @@ def run_precision_study(args):
                       "rows": rows}))
 
 
+def run_autotune(args):
+    """Run-time preconditioner selection (Sec. 6, Table 4 without SEMFEM) on the bench workload:
+    every candidate of the default space (and, with --autotune-orders, Cheby-RAS(k) and
+    Cheby-Jac(k) for k = 1..3 on the same schedules) set up and timed on the first solve, for the
+    FP64 and the FP32 V-cycle; prints the timed table and the choice."""
+    import torch
+    from paper_2110_07663_gb300 import se
+    import workloads as wl
+    torch.cuda.set_device(0)
+    wk = WORKLOADS[args.workload]
+    nel, p = wk["nel"], wk["p"]
+    m = se.se_mesh_create(nel, p, perturb_frac=wk["perturb"], seed=wk["seed"], deform_amp=wl.DEFORM_AMP)
+    info = se.se_mesh_get_info(m)
+    xyz = torch.empty(3 * info.L, dtype=torch.float64, device="cuda")
+    se.se_mesh_nodes(m, xyz)
+    X = xyz.view(3, -1)
+    f = 3.0 * math.pi ** 2 * torch.sin(math.pi * X[0]) * torch.sin(math.pi * X[1]) * torch.sin(math.pi * X[2])
+    b = torch.empty(info.L, dtype=torch.float64, device="cuda")
+    se.se_mesh_rhs(m, f.contiguous(), b)
+    del xyz, X, f
+    names = {se.SE_SMOOTH_ASM: "Cheby-ASM", se.SE_SMOOTH_RAS: "Cheby-RAS", se.SE_SMOOTH_JACOBI: "Cheby-Jac"}
+    out = []
+    for prec_name, prec in (("fp64", se.SE_FP64), ("fp32_vcycle", se.SE_FP32)):
+        cands = se.se_pmg_autotune_space(p, prec)
+        if args.autotune_orders:
+            for base in (cands[1], cands[2]):
+                for k in (1, 2, 3):
+                    if k == 2:
+                        continue
+                    c = se.se_tune_candidate()
+                    c.pmg = se.pmg_desc(list(base.pmg.schedule[:base.pmg.nlev]), base.pmg.smoother, k,
+                                        precision=prec)
+                    cands.append(c)
+        t0 = time.perf_counter()
+        best, timed, P = se.se_pmg_autotune(m, b, cands, repeats=args.steps, tol=1e-8, maxit=500,
+                                            keep=False)
+        wall = time.perf_counter() - t0
+        rows = [{"preconditioner": f"{names[c.pmg.smoother]}({c.pmg.cheb_order[0]})",
+                 "schedule": list(c.pmg.schedule[:c.pmg.nlev]),
+                 "setup_ms": round(c.setup_ms, 1), "solve_ms": round(c.ms, 2),
+                 "iterations": c.iterations, "status": c.status} for c in timed]
+        out.append({"precision": prec_name, "chosen": rows[best], "search_wall_s": round(wall, 2),
+                    "candidates": rows})
+    se.se_mesh_destroy(m)
+    print(json.dumps({"metric": "run-time preconditioner selection: time to solution per candidate",
+                      "config": {"workload": f"{args.workload}: {nel[0]}x{nel[1]}x{nel[2]} elements, "
+                                             f"p={p}, FPCG to 1e-8, graph solve, "
+                                             f"{args.steps} timed solves per candidate"},
+                      "searches": out}))
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -619,6 +670,10 @@ def main():
     ap.add_argument("--proj", type=int, default=0,
                     help="serving: prior solutions kept per resident mesh for the initial guess")
     ap.add_argument("--precision-study", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time the preconditioner candidates of Table 4 on the workload")
+    ap.add_argument("--autotune-orders", action="store_true",
+                    help="autotune: add Chebyshev orders 1 and 3 for RAS and Jacobi")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         ap.error("--warmup must be >= 3")
@@ -630,6 +685,8 @@ def main():
         run_serve(args)
     elif args.precision_study:
         run_precision_study(args)
+    elif args.autotune:
+        run_autotune(args)
     else:
         run_gpu(args)
 

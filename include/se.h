@@ -272,6 +272,29 @@ int se_tune(int p, int precision, se_tile_cfg* out);
 int se_tune_get(int p, int precision, se_tile_cfg* out);
 int se_tune_set(const se_tile_cfg* cfg);
 
+/* ---------------------------------------------------------------- preconditioner autotuner */
+/* The paper's run-time preconditioner selection (Sec. 6, Table 4 without SEMFEM): an exhaustive
+ * timed search on the first solve.  A candidate is a preconditioner description; the search
+ * fills its timings. */
+typedef struct se_tune_candidate {
+  se_pmg_desc pmg;
+  double setup_ms;   /* se_pmg_setup */
+  double ms;         /* mean time to solution over the timed solves */
+  int iterations;
+  int status;        /* SE_OK, or the error of its set-up or solve */
+} se_tune_candidate;
+/* The default space for order p: for p = 7 Cheby-ASM(2),(7,3,1), Cheby-RAS(2),(7,3,1),
+ * Cheby-Jac(2),(7,5,3,1); for p = 9 (9,5,1), (9,5,1), (9,7,5,1); other orders the analogous
+ * three.  Bounds, Arnoldi and coarse settings are the paper's defaults; precision as given.
+ * Writes 3 candidates (cap >= 3). */
+int se_pmg_autotune_space(int p, int precision, se_tune_candidate* out, int cap, int* n);
+/* For each candidate: set up, one untimed solve of A x = b from x = 0 with `opts` (captures the
+ * graph when opts->graph_capture), then `repeats` timed solves.  *best receives the index of the
+ * fastest converged candidate; with out_pmg, the caller receives that candidate's preconditioner
+ * (the others are destroyed).  Returns SE_ENOTCONV if none converged.  Synchronises. */
+int se_pmg_autotune(se_mesh_t m, const double* b, const se_solve_opts* opts, int repeats,
+                    se_tune_candidate* cands, int n, int* best, se_pmg_t* out_pmg);
+
 /* ---------------------------------------------------------------- serving */
 /* Estimated device bytes of a mesh with its preconditioner and solve work space (the sizes the
  * library allocates, plus the transient Arnoldi vectors of the set-up). */

@@ -2,6 +2,7 @@
 // (Algorithm 2), single-pass V-cycle (Algorithm 1), Chebyshev bounds from Arnoldi on S A.
 #include <algorithm>
 #include <cmath>
+#include <atomic>
 #include <complex>
 #include <cstring>
 #include <vector>
@@ -362,8 +363,10 @@ int se_pmg_setup(se_mesh_t m, const se_pmg_desc* desc, se_pmg_t* out) {
   SE_CHECK(d.arnoldi_steps >= 1 && d.arnoldi_steps <= 100, SE_EINVAL, "se_pmg_setup: arnoldi_steps");
   SE_CHECK(d.coarse_tol > 0 && d.coarse_maxit >= 1, SE_EINVAL, "se_pmg_setup: coarse tolerance");
   SE_CHECK(d.precision == SE_FP64 || d.precision == SE_FP32, SE_EINVAL, "se_pmg_setup: precision");
+  static std::atomic<uint64_t> next_uid{0};
   auto* P = new se_pmg_s();
   P->mesh = m;
+  P->uid = ++next_uid;
   P->desc = d;
   P->nlev = d.nlev;
   P->stream = m->stream;
@@ -383,6 +386,13 @@ int se_pmg_setup(se_mesh_t m, const se_pmg_desc* desc, se_pmg_t* out) {
 int se_pmg_destroy(se_pmg_t P) {
   if (!P) return SE_OK;
   cudaStreamSynchronize(P->stream);
+  se_mesh_s* m = P->mesh;
+  if (m && m->gexec && m->gpmg_uid == P->uid) {  // the mesh's cached solve graph uses this handle
+    cudaGraphExecDestroy(m->gexec);
+    m->gexec = nullptr;
+    m->gkey[0] = nullptr;
+    m->gpmg_uid = 0;
+  }
   P->release_graph();
   P->allocs.release();
   pinned_release(P->scratch.hscal);

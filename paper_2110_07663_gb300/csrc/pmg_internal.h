@@ -22,6 +22,8 @@ int rhs_modes(se_mesh_s* m, const int k[3], double a, double* b, cudaStream_t s)
 
 struct se_pmg_s {
   se_mesh_s* mesh = nullptr;
+  uint64_t uid = 0;  // unique per handle: the mesh's cached solve graph is keyed by it, not by
+                     // the address (a later handle may reuse a destroyed one's address)
   se_pmg_desc desc;
   int nlev = 0;
   cudaStream_t stream = nullptr;

@@ -174,6 +174,7 @@ struct se_mesh_s {
   void* gstats = nullptr;        // se::DevStats
   cudaGraphExec_t gexec = nullptr;
   const void* gkey[4] = {nullptr, nullptr, nullptr, nullptr};  // pmg, b, x, opts hash
+  uint64_t gpmg_uid = 0;     // uid of the preconditioner the cached graph was built with
   double gtol = 0.0;
   int gmaxit = 0;
   int gtolnorm = 0;

@@ -346,7 +346,8 @@ static int read_graph_stats(se_mesh_s* m, cudaStream_t s, se_solve_stats* out, d
 int graph_solve_launch(se_mesh_s* m, se_pmg_s* P, const double* b, double* x, double tol,
                        int maxit, cudaStream_t s, int tol_norm) {
   SE_TRY(prepare_graph_solve(m));
-  const bool same = m->gexec && m->gkey[0] == P && m->gkey[1] == b && m->gkey[2] == x &&
+  const uint64_t uid = P ? P->uid : 0;
+  const bool same = m->gexec && m->gkey[0] == P && m->gpmg_uid == uid && m->gkey[1] == b && m->gkey[2] == x &&
                     m->gtol == tol && m->gmaxit == maxit && m->gtolnorm == tol_norm;
   if (!same) {
     if (m->gexec) cudaGraphExecDestroy(m->gexec);
@@ -368,6 +369,7 @@ int graph_solve_launch(se_mesh_s* m, se_pmg_s* P, const double* b, double* x, do
     cudaGraphDestroy(G);
     if (rc != SE_OK) return rc;
     m->gkey[0] = P;
+    m->gpmg_uid = uid;
     m->gkey[1] = b;
     m->gkey[2] = x;
     m->gtol = tol;

@@ -103,6 +103,11 @@ class se_solve_stats(C.Structure):
                 ("ms_total", C.c_double), ("ms_precond", C.c_double), ("ms_operator", C.c_double)]
 
 
+class se_tune_candidate(C.Structure):
+    _fields_ = [("pmg", se_pmg_desc), ("setup_ms", C.c_double), ("ms", C.c_double),
+                ("iterations", C.c_int), ("status", C.c_int)]
+
+
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libse.so is not built ({LIB_PATH}); run __graft_entry__.build() first")
 lib = C.CDLL(LIB_PATH)
@@ -144,6 +149,9 @@ _SIGS = {
     "se_tune": ([_ip, _ip, C.POINTER(se_tile_cfg)], C.c_int),
     "se_tune_get": ([_ip, _ip, C.POINTER(se_tile_cfg)], C.c_int),
     "se_tune_set": ([C.POINTER(se_tile_cfg)], C.c_int),
+    "se_pmg_autotune_space": ([_ip, _ip, C.POINTER(se_tune_candidate), _ip, C.POINTER(C.c_int)], C.c_int),
+    "se_pmg_autotune": ([_vp, _vp, C.POINTER(se_solve_opts), _ip, C.POINTER(se_tune_candidate), _ip,
+                         C.POINTER(C.c_int), C.POINTER(_vp)], C.c_int),
     "se_mesh_footprint_bytes": ([C.POINTER(se_mesh_desc), C.POINTER(se_pmg_desc), C.POINTER(C.c_size_t)], C.c_int),
     "se_proj_create": ([_vp, C.c_int, C.POINTER(_vp)], C.c_int),
     "se_proj_destroy": ([_vp], C.c_int),
@@ -343,6 +351,29 @@ def se_solve(m, P, b, x, method=SE_FPCG, tol=1e-8, maxit=1000, restart=20, graph
     _check(lib.se_solve(m, P, _ptr(b), _ptr(x), C.byref(o), C.byref(st)),
            allow=(SE_ENOTCONV,) if allow_notconv else ())
     return st
+
+
+# ----------------------------------------------------------------------------- preconditioner autotuner
+def se_pmg_autotune_space(p, precision=SE_FP64):
+    """The default candidate space for order p (Sec. 6, Table 4 without SEMFEM)."""
+    arr = (se_tune_candidate * 8)()
+    n = C.c_int()
+    _check(lib.se_pmg_autotune_space(int(p), int(precision), arr, 8, C.byref(n)))
+    return [arr[i] for i in range(n.value)]
+
+
+def se_pmg_autotune(m, b, candidates, repeats=2, method=SE_FPCG, tol=1e-8, maxit=1000, restart=20,
+                    graph_capture=1, tol_norm=0, keep=True):
+    """Times every candidate; returns (best index, timed candidates, best preconditioner or None)."""
+    o = se_solve_opts()
+    o.method, o.restart, o.tol, o.maxit, o.graph_capture = method, restart, tol, maxit, graph_capture
+    o.tol_norm = tol_norm
+    arr = (se_tune_candidate * len(candidates))(*candidates)
+    best = C.c_int(-1)
+    h = _vp()
+    _check(lib.se_pmg_autotune(m, _ptr(b), C.byref(o), int(repeats), arr, len(candidates),
+                               C.byref(best), C.byref(h) if keep else None))
+    return best.value, [arr[i] for i in range(len(candidates))], h.value if keep else None
 
 
 # ----------------------------------------------------------------------------- projection
