@@ -567,7 +567,7 @@ def run_precision_study(args):
 
 
 def run_autotune(args):
-    """Run-time preconditioner selection (Sec. 6, Table 4 without SEMFEM) on the bench workload:
+    """Run-time preconditioner selection (Sec. 5, Table 5 without SEMFEM) on the bench workload:
     every candidate of the default space (and, with --autotune-orders, Cheby-RAS(k) and
     Cheby-Jac(k) for k = 1..3 on the same schedules) set up and timed on the first solve, for the
     FP64 and the FP32 V-cycle; prints the timed table and the choice."""
@@ -671,7 +671,7 @@ def main():
                     help="serving: prior solutions kept per resident mesh for the initial guess")
     ap.add_argument("--precision-study", action="store_true")
     ap.add_argument("--autotune", action="store_true",
-                    help="time the preconditioner candidates of Table 4 on the workload")
+                    help="time the preconditioner candidates of Table 5 on the workload")
     ap.add_argument("--autotune-orders", action="store_true",
                     help="autotune: add Chebyshev orders 1 and 3 for RAS and Jacobi")
     args = ap.parse_args()

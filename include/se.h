@@ -5,7 +5,7 @@
  * "Tuning Spectral Element Preconditioners for Parallel Scalability on GPUs" (arXiv 2110.07663):
  * the matrix-free spectral element operator (Sec. 2.1), the p-multigrid V-cycle (Algorithm 1)
  * with Chebyshev acceleration (Algorithm 2) of restrictive/additive Schwarz smoothers built on
- * fast-diagonalisation local solves (Sec. 2.3.2, eqs 4-9) or of Jacobi smoothing, and flexible
+ * fast-diagonalisation local solves (Sec. 2.2.2, eqs 4-9) or of Jacobi smoothing, and flexible
  * Krylov outer solvers (Sec. 2.2).  One GPU, hand-written CUDA kernels for sm_103a.
  *
  * Conventions for every call:
@@ -112,11 +112,11 @@ int se_gs(se_mesh_t m, double* u, int mask, void* stream);
 /* Unique-node inner product sum_l a_l b_l / mult_l of two continuous L-vectors (FP64,
  * deterministic order).  Synchronises the stream; result written to *out_host. */
 int se_dot(se_mesh_t m, const double* a, const double* b, double* out_host, void* stream);
-/* Assembled, masked diagonal of A (Jacobi surrogate, Sec. 2.3.3) as an L-vector; Dirichlet
+/* Assembled, masked diagonal of A (Jacobi surrogate, Sec. 2.2.3) as an L-vector; Dirichlet
  * nodes get 1. */
 int se_jacobi_diag(se_mesh_t m, double* d_dev, void* stream);
 
-/* ---------------------------------------------------------------- p-multigrid (Sec. 2.3) */
+/* ---------------------------------------------------------------- p-multigrid (Sec. 2.2) */
 typedef struct se_pmg_desc {
   int nlev;                      /* levels, 2..SE_MAX_LEVELS */
   int schedule[SE_MAX_LEVELS];   /* orders, schedule[0] == mesh p, strictly decreasing */
@@ -141,7 +141,7 @@ int se_pmg_destroy(se_pmg_t pmg);
  * right-hand side is): the V-cycle forms its residuals b - A x in one operator pass that relies
  * on it. */
 int se_pmg_apply(se_pmg_t pmg, const double* r, double* z, void* stream);
-/* lambda-tilde of level lvl (largest |Ritz value| of Arnoldi on S A, Sec. 2.3.3). */
+/* lambda-tilde of level lvl (largest |Ritz value| of Arnoldi on S A, Sec. 2.2.3). */
 int se_pmg_lambda(se_pmg_t pmg, int lvl, double* lam);
 int se_pmg_level_info(se_pmg_t pmg, int lvl, se_mesh_info* info);
 /* Level-lvl building blocks, all on level-lvl L-vectors (FP64 in/out; computed in the pmg's
@@ -212,7 +212,7 @@ typedef struct se_solve_stats {
 int se_solve(se_mesh_t m, se_pmg_t pmg, const double* b, double* x, const se_solve_opts* opts,
              se_solve_stats* stats);
 
-/* ---------------------------------------------------------------- projection (Sec. 4) */
+/* ---------------------------------------------------------------- projection (Secs. 3.2 and 4.2) */
 /* A space of up to max_vectors (1..16) prior solutions of A x = b on mesh m, for successive
  * right-hand sides (the paper projects each pressure solve onto up to 10 prior solutions,
  * Fischer's method): kept A-orthonormal, x_i^T A x_j = delta_ij, with the images A x_i.  Device
@@ -273,7 +273,7 @@ int se_tune_get(int p, int precision, se_tile_cfg* out);
 int se_tune_set(const se_tile_cfg* cfg);
 
 /* ---------------------------------------------------------------- preconditioner autotuner */
-/* The paper's run-time preconditioner selection (Sec. 6, Table 4 without SEMFEM): an exhaustive
+/* The paper's run-time preconditioner selection (Sec. 5, Table 5 without SEMFEM): an exhaustive
  * timed search on the first solve.  A candidate is a preconditioner description; the search
  * fills its timings. */
 typedef struct se_tune_candidate {

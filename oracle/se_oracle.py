@@ -281,7 +281,7 @@ def rhs(lv, f_nodes):
 
 
 def jacobi_diag(lv):
-    """diag(A) = QQ^T diag(A_L) (Sec. 2.3.3, Jacobi surrogate), element diagonal in closed form:
+    """diag(A) = QQ^T diag(A_L) (Sec. 2.2.3, Jacobi surrogate), element diagonal in closed form:
     sum_l D_li^2 G_rr(l,j,k) + ... + 2 D_ii D_jj G_rs(i,j,k) + 2 D_ii D_kk G_rt + 2 D_jj D_kk G_st."""
     D = lv.D
     D2 = D * D
@@ -297,12 +297,12 @@ def jacobi_diag(lv):
 
 
 # =============================================================================================
-# Overlapping Schwarz smoother with fast-diagonalisation local solves (Sec. 2.3.2, eqs 4-9).
+# Overlapping Schwarz smoother with fast-diagonalisation local solves (Sec. 2.2.2, eqs 4-9).
 # =============================================================================================
 
 
 def element_box_lengths(V, nel, amp=0.05):
-    """Box-like approximation of each deformed element (Sec. 2.3.2, Fig. 1a).
+    """Box-like approximation of each deformed element (Sec. 2.2.2, Fig. 1a).
 
     READING: length along direction d = mean of the 4 corner-to-corner edge lengths of the mapped
     element along d (corners after the smooth map).  Returns array (E, 3).
@@ -317,7 +317,7 @@ def element_box_lengths(V, nel, amp=0.05):
 
 
 def fdm_1d(p, lengths, has_left, has_right, dir_left, dir_right):
-    """Extended 1D stiffness/mass pairs (A_*, B_*) of element directions (Sec. 2.3.2).
+    """Extended 1D stiffness/mass pairs (A_*, B_*) of element directions (Sec. 2.2.2).
 
     For each row of ``lengths`` = (l_left, l, l_right), the 1D GLL stiffness (2/l) D^T W D and
     mass (l/2) W are assembled over the left neighbour, the element and the right neighbour; the
@@ -409,7 +409,7 @@ def fdm_setup(lv, V, amp=0.05):
 
 
 def extended_gather(lv, r):
-    """R_e r for every element: the pbar^3 window of the assembled residual (Sec. 2.3.2, eq 4).
+    """R_e r for every element: the pbar^3 window of the assembled residual (Sec. 2.2.2, eq 4).
 
     The window of element (ex,ey,ez) is the lattice box I in [ex p - 1, ex p + p + 1] (and
     likewise for J, K); points outside the domain read 0.  Returns (E, pbar, pbar, pbar).
@@ -444,7 +444,7 @@ def fdm_apply(S, Lm, rbar):
 
 
 def ras(lv, r):
-    """Restrictive additive Schwarz (Sec. 2.3.2, after eq 9): only each element's own nodes of
+    """Restrictive additive Schwarz (Sec. 2.2.2, after eq 9): only each element's own nodes of
     its local solve are kept, weighted by 1/(number of elements sharing the node), then summed.
     READING: 'changing W_e' is the partition-of-unity weight 1/mult on own nodes, 0 on overlap."""
     S, Lm = lv.extra["fdm"]
@@ -456,7 +456,7 @@ def ras(lv, r):
 
 def asm(lv, r):
     """Additive Schwarz, eq 4: s = W sum_e R_e^T Abar_e^-1 R_e r with W post-multiplying by the
-    inverse of the number of subdomains covering each node (Sec. 2.3.2)."""
+    inverse of the number of subdomains covering each node (Sec. 2.2.2)."""
     S, Lm = lv.extra["fdm"]
     z = fdm_apply(S, Lm, extended_gather(lv, r))
     p = lv.p
@@ -475,12 +475,12 @@ def asm(lv, r):
 
 
 def jacobi(lv, r):
-    """Jacobi surrogate S = diag(A)^-1 (Sec. 2.3.3)."""
+    """Jacobi surrogate S = diag(A)^-1 (Sec. 2.2.3)."""
     return lv.mask * r / lv.extra["diag"]
 
 
 # =============================================================================================
-# Chebyshev acceleration (Sec. 2.3.3, Algorithm 2) and the Arnoldi bound estimate.
+# Chebyshev acceleration (Sec. 2.2.3, Algorithm 2) and the Arnoldi bound estimate.
 # =============================================================================================
 
 
@@ -510,7 +510,7 @@ def chebyshev(res, A, S, lmin, lmax, order):
 
 def arnoldi_lambda(A, S, v0, dotf, steps=10):
     """lambda-tilde: largest |Ritz value| after ``steps`` rounds of Arnoldi (modified
-    Gram-Schmidt) on S A (Sec. 2.3.3).  Stops early if the Krylov space is exhausted
+    Gram-Schmidt) on S A (Sec. 2.2.3).  Stops early if the Krylov space is exhausted
     (subdiagonal <= 1e-12 of the largest |H| entry)."""
     v = v0 / math.sqrt(dotf(v0, v0))
     Vs = [v]
@@ -531,7 +531,7 @@ def arnoldi_lambda(A, S, v0, dotf, steps=10):
 
 
 # =============================================================================================
-# p-multigrid (Sec. 2.3.2, Algorithm 1): transfers, coarse solve, V-cycle.
+# p-multigrid (Sec. 2.2.2, Algorithm 1): transfers, coarse solve, V-cycle.
 # =============================================================================================
 
 
@@ -605,11 +605,11 @@ def smoother_op(pmg, l):
 def pmg_setup(V, nel, schedule, smoother="ras", order=2, bc=("D",) * 6, amp=0.05,
               eig_lo=0.1, eig_hi=1.1, arnoldi_steps=10, seed=0, coarse_tol=1e-4, coarse_maxit=500,
               start_vectors=None):
-    """Levels of the schedule, smoother data and Chebyshev bounds (Sec. 2.3.2-2.3.3).
+    """Levels of the schedule, smoother data and Chebyshev bounds (Sec. 2.2.2-2.3.3).
 
     READING: every level is rediscretised on the same mapped mesh at its own order (geometry
     from the map evaluated at that level's GLL points).  Bounds (lmin, lmax) = (eig_lo, eig_hi)
-    lambda-tilde (Sec. 2.3.3).  ``start_vectors[l]`` is the global start vector of level l
+    lambda-tilde (Sec. 2.2.3).  ``start_vectors[l]`` is the global start vector of level l
     (from workloads.arnoldi_start_global).
     """
     from workloads import arnoldi_start_global, arnoldi_seed  # seeded inputs only
@@ -636,7 +636,7 @@ def pmg_setup(V, nel, schedule, smoother="ras", order=2, bc=("D",) * 6, amp=0.05
 
 def coarse_solve(pmg, b):
     """Coarsest level (p = 1): Jacobi-PCG to relative residual coarse_tol.
-    READING: replaces the paper's single BoomerAMG V-cycle (Sec. 2.3.2), which needs a
+    READING: replaces the paper's single BoomerAMG V-cycle (Sec. 2.2.2), which needs a
     third-party AMG library."""
     lv = pmg.levels[-1]
     x, it = pcg(lambda u: ax(lv, u), lambda r: jacobi(lv, r), b,

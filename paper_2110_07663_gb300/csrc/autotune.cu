@@ -1,6 +1,6 @@
-// Run-time preconditioner selection (the paper, Sec. 6 and Table 4): an exhaustive timed search
+// Run-time preconditioner selection (the paper, Sec. 5 and Table 5): an exhaustive timed search
 // on the first solve over a small space of p-multigrid preconditioners, keeping the one with the
-// shortest time to solution.  The default space is Table 4 without SEMFEM: for p = 7,
+// shortest time to solution.  The default space is Table 5 without SEMFEM: for p = 7,
 // Cheby-ASM(2),(7,3,1), Cheby-RAS(2),(7,3,1), Cheby-Jac(2),(7,5,3,1); for p = 9 the same with
 // (9,5,1), (9,5,1), (9,7,5,1).  Other orders get the analogous three: Schwarz through the
 // largest odd order <= ceil(p/2) (the rule that gives 3 for p = 7 and 5 for p = 9), Jacobi in
@@ -45,7 +45,7 @@ int se_pmg_autotune_space(int p, int precision, se_tune_candidate* out, int cap,
   if (mid > 1) schwarz.push_back(mid);
   schwarz.push_back(1);
   if (p == 9) {
-    jac = {9, 7, 5, 1};  // Table 4
+    jac = {9, 7, 5, 1};  // Table 5
   } else {
     for (int q = p; q > 1; q -= 2) jac.push_back(q);
     jac.push_back(1);

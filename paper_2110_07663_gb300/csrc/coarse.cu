@@ -1,6 +1,6 @@
 // Coarsest level (p = 1): assembled 27-point operator and a persistent Jacobi-PCG solve.
 //
-// The paper solves the coarse system with one BoomerAMG V-cycle (Sec. 2.3.2), a third-party
+// The paper solves the coarse system with one BoomerAMG V-cycle (Sec. 2.2.2), a third-party
 // library; here the coarse problem is solved by Jacobi-preconditioned CG to a relative tolerance.
 // The p = 1 element matrices are assembled into rows over global lattice nodes (27 entries each,
 // summed over the up to 8 elements sharing the row node in a fixed order: deterministic), and the

@@ -1,4 +1,4 @@
-// Overlapping Schwarz smoother with fast-diagonalisation local solves (Sec. 2.3.2, eqs 4-9).
+// Overlapping Schwarz smoother with fast-diagonalisation local solves (Sec. 2.2.2, eqs 4-9).
 //
 // Set-up: for every element and direction, the extended 1D stiffness/mass pair over
 // [left neighbour, element, right neighbour] (box lengths from the mapped corners), restricted to

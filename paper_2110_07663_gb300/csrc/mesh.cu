@@ -288,7 +288,7 @@ int make_fp32_geometry(Level& lv, Allocs& allocs, cudaStream_t s) {
 }
 
 // Mean length of the 4 mapped corner-to-corner edges of each element along each direction
-// (box-like approximation of Sec. 2.3.2, Fig. 1a).
+// (box-like approximation of Sec. 2.2.2, Fig. 1a).
 static void box_lengths(se_mesh_s* m) {
   const int nx = m->desc.nel[0], ny = m->desc.nel[1], nz = m->desc.nel[2];
   const double amp = m->desc.deform_amp;

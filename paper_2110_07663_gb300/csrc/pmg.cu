@@ -1,4 +1,4 @@
-// p-multigrid preconditioner (Sec. 2.3): level hierarchy, Chebyshev-accelerated smoothing
+// p-multigrid preconditioner (Sec. 2.2): level hierarchy, Chebyshev-accelerated smoothing
 // (Algorithm 2), single-pass V-cycle (Algorithm 1), Chebyshev bounds from Arnoldi on S A.
 #include <algorithm>
 #include <cmath>

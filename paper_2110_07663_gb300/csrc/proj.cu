@@ -1,4 +1,4 @@
-// Projection onto prior solutions (the paper, Sec. 4: every pressure solve starts from the
+// Projection onto prior solutions (the paper, Secs. 3.2 and 4.2: every pressure solve starts from the
 // projection of its right-hand side onto a space of up to 10 prior solutions, Fischer's method
 // for successive right-hand sides).
 //

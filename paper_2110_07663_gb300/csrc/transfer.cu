@@ -1,4 +1,4 @@
-// p-multigrid transfers between GLL bases (Algorithm 1, Sec. 2.3.2):
+// p-multigrid transfers between GLL bases (Algorithm 1, Sec. 2.2.2):
 //   prolongation  e_f = (J x J x J) e_c            element by element
 //   restriction   r_c = M_c QQ^T_c (J^T x J^T x J^T)(r_f / mult_f)
 // with J_ij = h^c_j(xi^f_i).  For a continuous r_f the restriction is the transpose of the

@@ -355,7 +355,7 @@ def se_solve(m, P, b, x, method=SE_FPCG, tol=1e-8, maxit=1000, restart=20, graph
 
 # ----------------------------------------------------------------------------- preconditioner autotuner
 def se_pmg_autotune_space(p, precision=SE_FP64):
-    """The default candidate space for order p (Sec. 6, Table 4 without SEMFEM)."""
+    """The default candidate space for order p (Sec. 5, Table 5 without SEMFEM)."""
     arr = (se_tune_candidate * 8)()
     n = C.c_int()
     _check(lib.se_pmg_autotune_space(int(p), int(precision), arr, 8, C.byref(n)))

@@ -31,7 +31,7 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_autotune_space_is_table_4():
-    """The default preconditioner space (host only, no GPU call): Sec. 6, Table 4 without
+    """The default preconditioner space (host only, no GPU call): Sec. 5, Table 5 without
     SEMFEM for p = 7 and p = 9, and the same rule for other orders."""
     from paper_2110_07663_gb300 import se
     want = {

@@ -1,4 +1,4 @@
-"""Run-time preconditioner selection (Sec. 6, Table 4): an exhaustive timed search over a small
+"""Run-time preconditioner selection (Sec. 5, Table 5): an exhaustive timed search over a small
 space of p-multigrid preconditioners on the first solve.
 
 Checks: every candidate is set up and solved to the tolerance (true residual through the

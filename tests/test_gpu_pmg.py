@@ -1,4 +1,4 @@
-"""GPU parity of the p-multigrid building blocks (Sec. 2.3, Algorithms 1-2, eqs 4-9).
+"""GPU parity of the p-multigrid building blocks (Sec. 2.2, Algorithms 1-2, eqs 4-9).
 
 Tolerances (relative, max-norm): gather and transfers 1e-13; smoothers, FDM, Chebyshev 1e-10
 (the local eigen-decompositions are computed by different algorithms: cyclic Jacobi rotations

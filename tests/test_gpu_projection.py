@@ -1,4 +1,4 @@
-"""Projection onto prior solutions (Sec. 4, Fischer's method for successive right-hand sides)
+"""Projection onto prior solutions (Secs. 3.2 and 4.2, Fischer's method for successive right-hand sides)
 and the ||b||-relative stopping rule it is used with.
 
 Checks: a right-hand side in the span of prior ones is solved by the guess alone (0 iterations,

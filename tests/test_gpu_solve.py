@@ -1,4 +1,4 @@
-"""GPU parity of whole solves (Sec. 2.2 outer Krylov with the Sec. 2.3 preconditioners).
+"""GPU parity of whole solves (Sec. 2.2 outer Krylov with the Sec. 2.2 preconditioners).
 
 Bar: the GPU solution meets the requested relative residual 1e-8 (checked with the ORACLE's
 operator on the GPU solution), and its iteration count is within +-1 of the oracle's on the
