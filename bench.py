@@ -617,6 +617,101 @@ def run_autotune(args):
                       "searches": out}))
 
 
+def skewed_problem(se, torch, nel, p, eps, segments=2):
+    """Mesh on the skewed lattice (workloads.skewed_lattice, no smooth map) and b for
+    f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z)."""
+    import workloads as wl
+    m = se.se_mesh_create(nel, p, vertex_xyz=wl.skewed_lattice(nel, eps, segments), deform_amp=0.0)
+    info = se.se_mesh_get_info(m)
+    xyz = torch.empty(3 * info.L, dtype=torch.float64, device="cuda")
+    se.se_mesh_nodes(m, xyz)
+    X = xyz.view(3, -1)
+    f = 3.0 * math.pi ** 2 * torch.sin(math.pi * X[0]) * torch.sin(math.pi * X[1]) * torch.sin(math.pi * X[2])
+    b = torch.empty(info.L, dtype=torch.float64, device="cuda")
+    se.se_mesh_rhs(m, f.contiguous(), b)
+    return m, info, b
+
+
+def study_solve(se, torch, m, b, desc, method, maxit):
+    """Set up, solve from x = 0 to 1e-8 (not converging within maxit is a result, not an error)."""
+    P = se.se_pmg_setup(m, desc)
+    x = torch.zeros_like(b)
+    st = se.se_solve(m, P, b, x, method=method, tol=1e-8, maxit=maxit, restart=20,
+                     allow_notconv=True)
+    se.se_pmg_destroy(P)
+    ok = st.status == se.SE_OK and st.rel_residual <= 1e-8
+    return ok, st
+
+
+def run_lambda_study(args):
+    """Synthetic analogue of Table 1: iterations to 1e-8 of GMRES(20) with the pMG (7,3,1)
+    Cheby-ASM(2) preconditioner for Chebyshev bounds (lo, hi) x lambda-tilde, on the skewed
+    lattice (eps = 0.3, 24^3 elements, p = 7 by default); '-' = not converged within maxit."""
+    import torch
+    from paper_2110_07663_gb300 import se
+    torch.cuda.set_device(0)
+    nel = (args.study_nel,) * 3
+    m, info, b = skewed_problem(se, torch, nel, 7, args.study_eps, args.study_segments)
+    prec = se.SE_FP32 if args.study_fp32 else se.SE_FP64
+    lows = [0.0, 0.025, 0.05, 0.1, 0.2, 0.25]
+    highs = [0.9, 0.95, 1.0, 1.1, 1.2, 1.3]
+    grid, times = [], []
+    t0 = time.perf_counter()
+    for lo in lows:
+        row, trow = [], []
+        for hi in highs:
+            d = se.pmg_desc((7, 3, 1), se.SE_SMOOTH_ASM, 2, eig_lo=lo, eig_hi=hi, precision=prec)
+            ok, st = study_solve(se, torch, m, b, d, se.SE_FGMRES, args.study_maxit)
+            row.append(st.iterations if ok else "-")
+            trow.append(round(st.ms_total, 1))
+        grid.append(row)
+        times.append(trow)
+    se.se_mesh_destroy(m)
+    print(json.dumps({
+        "metric": "iterations to 1e-8 vs Chebyshev bounds (synthetic analogue of Table 1)",
+        "config": {"workload": f"skewed lattice eps={args.study_eps} segments={args.study_segments}, "
+                               f"{nel[0]}^3 elements, p=7, "
+                               f"pMG (7,3,1) Cheby-ASM(2), FGMRES(20), maxit {args.study_maxit}",
+                   "precision": "fp32_vcycle" if args.study_fp32 else "fp64"},
+        "lambda_min_multipliers": lows, "lambda_max_multipliers": highs,
+        "iterations": grid, "solve_ms": times, "wall_s": round(time.perf_counter() - t0, 1)}))
+
+
+def run_order_study(args):
+    """Synthetic analogue of the paper's order study (Sec. 4.1): fixed n = E p^3, p = 3..10, on
+    the skewed lattice for eps in {1, 0.3, 0.05}, with the three pMG preconditioners of the
+    autotuner space; iterations of GMRES(20) to 1e-8 and time per solve."""
+    import torch
+    from paper_2110_07663_gb300 import se
+    torch.cuda.set_device(0)
+    prec = se.SE_FP32 if args.study_fp32 else se.SE_FP64
+    names = {se.SE_SMOOTH_ASM: "Cheby-ASM(2)", se.SE_SMOOTH_RAS: "Cheby-RAS(2)",
+             se.SE_SMOOTH_JACOBI: "Cheby-Jac(2)"}
+    rows = []
+    t0 = time.perf_counter()
+    for eps in args.study_eps_list:
+        for p in range(3, 11):
+            ne = max(2, round((args.study_n / p ** 3) ** (1.0 / 3.0)))
+            nel = (ne, ne, ne)
+            m, info, b = skewed_problem(se, torch, nel, p, eps, args.study_segments)
+            for c in se.se_pmg_autotune_space(p, prec):
+                ok, st = study_solve(se, torch, m, b, c.pmg, se.SE_FGMRES, args.study_maxit)
+                rows.append({"eps": eps, "p": p, "E": ne ** 3, "n": ne ** 3 * p ** 3,
+                             "preconditioner": names[c.pmg.smoother],
+                             "schedule": list(c.pmg.schedule[:c.pmg.nlev]),
+                             "iterations": st.iterations if ok else "-",
+                             "solve_ms": round(st.ms_total, 2),
+                             "gdof_per_s": round(ne ** 3 * p ** 3 / st.ms_total * 1e-6, 4) if ok else None})
+            se.se_mesh_destroy(m)
+    print(json.dumps({
+        "metric": "iterations and time per solve vs polynomial order (synthetic analogue of the order study)",
+        "config": {"workload": f"skewed lattice segments={args.study_segments}, n = E p^3 ~ "
+                               f"{args.study_n:.3g}, FGMRES(20) to 1e-8, "
+                               f"maxit {args.study_maxit}",
+                   "precision": "fp32_vcycle" if args.study_fp32 else "fp64"},
+        "rows": rows, "wall_s": round(time.perf_counter() - t0, 1)}))
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -674,6 +769,17 @@ def main():
                     help="time the preconditioner candidates of Table 5 on the workload")
     ap.add_argument("--autotune-orders", action="store_true",
                     help="autotune: add Chebyshev orders 1 and 3 for RAS and Jacobi")
+    ap.add_argument("--lambda-study", action="store_true",
+                    help="iterations vs Chebyshev bounds on the skewed lattice (Table 1 analogue)")
+    ap.add_argument("--order-study", action="store_true",
+                    help="iterations and time vs p at fixed n on the skewed lattice")
+    ap.add_argument("--study-nel", type=int, default=24)
+    ap.add_argument("--study-eps", type=float, default=0.3)
+    ap.add_argument("--study-segments", type=int, default=2)
+    ap.add_argument("--study-n", type=float, default=2.88e6)
+    ap.add_argument("--study-eps-list", type=float, nargs="+", default=[1.0, 0.3, 0.05])
+    ap.add_argument("--study-maxit", type=int, default=1000)
+    ap.add_argument("--study-fp32", action="store_true", help="studies: FP32 V-cycle")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         ap.error("--warmup must be >= 3")
@@ -687,6 +793,10 @@ def main():
         run_precision_study(args)
     elif args.autotune:
         run_autotune(args)
+    elif args.lambda_study:
+        run_lambda_study(args)
+    elif args.order_study:
+        run_order_study(args)
     else:
         run_gpu(args)
 

@@ -122,7 +122,8 @@ typedef struct se_pmg_desc {
   int schedule[SE_MAX_LEVELS];   /* orders, schedule[0] == mesh p, strictly decreasing */
   int smoother;                  /* SE_SMOOTH_RAS, SE_SMOOTH_ASM or SE_SMOOTH_JACOBI */
   int cheb_order[SE_MAX_LEVELS]; /* Chebyshev order (loop count of Algorithm 2) per level */
-  double eig_lo, eig_hi;         /* bounds (eig_lo, eig_hi)*lambda-tilde; paper: (0.1, 1.1) */
+  double eig_lo, eig_hi;         /* bounds (eig_lo, eig_hi)*lambda-tilde; paper: (0.1, 1.1);
+                                    0 <= eig_lo < eig_hi */
   int arnoldi_steps;             /* Arnoldi rounds for lambda-tilde; paper: 10 */
   uint64_t seed;                 /* start-vector stream: level l uses 1000 + l + 7919*seed */
   double coarse_tol;             /* coarsest-level Jacobi-PCG relative tolerance (1e-4) */

@@ -605,7 +605,7 @@ def smoother_op(pmg, l):
 def pmg_setup(V, nel, schedule, smoother="ras", order=2, bc=("D",) * 6, amp=0.05,
               eig_lo=0.1, eig_hi=1.1, arnoldi_steps=10, seed=0, coarse_tol=1e-4, coarse_maxit=500,
               start_vectors=None):
-    """Levels of the schedule, smoother data and Chebyshev bounds (Sec. 2.2.2-2.3.3).
+    """Levels of the schedule, smoother data and Chebyshev bounds (Secs. 2.2.2-2.2.3).
 
     READING: every level is rediscretised on the same mapped mesh at its own order (geometry
     from the map evaluated at that level's GLL points).  Bounds (lmin, lmax) = (eig_lo, eig_hi)

@@ -359,7 +359,9 @@ int se_pmg_setup(se_mesh_t m, const se_pmg_desc* desc, se_pmg_t* out) {
   for (int l = 0; l + 1 < d.nlev; ++l)
     SE_CHECK(d.cheb_order[l] >= 0 && d.cheb_order[l] <= 32, SE_EINVAL,
              "se_pmg_setup: Chebyshev order %d out of range", d.cheb_order[l]);
-  SE_CHECK(d.eig_hi > d.eig_lo && d.eig_lo > 0, SE_EINVAL, "se_pmg_setup: need 0 < eig_lo < eig_hi");
+  // eig_lo = 0 is allowed (Table 1's first row): sigma = 1 and the Chebyshev polynomial no longer
+  // damps, but the recurrence stays finite
+  SE_CHECK(d.eig_hi > d.eig_lo && d.eig_lo >= 0, SE_EINVAL, "se_pmg_setup: need 0 <= eig_lo < eig_hi");
   SE_CHECK(d.arnoldi_steps >= 1 && d.arnoldi_steps <= 100, SE_EINVAL, "se_pmg_setup: arnoldi_steps");
   SE_CHECK(d.coarse_tol > 0 && d.coarse_maxit >= 1, SE_EINVAL, "se_pmg_setup: coarse tolerance");
   SE_CHECK(d.precision == SE_FP64 || d.precision == SE_FP32, SE_EINVAL, "se_pmg_setup: precision");

@@ -69,6 +69,50 @@ def vertex_lattice(nel, perturb_frac: float = 0.0, seed: int = 0) -> np.ndarray:
     return V
 
 
+def _zigzag(t, segments):
+    """Piecewise-linear wave on [0,1]: +1 at t = 0, alternating -1/+1 at t = k/segments."""
+    s = np.asarray(t) * segments
+    k = np.clip(np.floor(s), 0, segments - 1)
+    f = s - k
+    sign = np.where(k % 2 == 0, 1.0, -1.0)
+    return sign * (1.0 - 2.0 * f)
+
+
+def _split_map(v, t):
+    """Monotone piecewise-linear map of [0,1] onto itself sending 1/2 to t (0 < t < 1)."""
+    return np.where(v <= 0.5, 2.0 * t * v, t + 2.0 * (1.0 - t) * (v - 0.5))
+
+
+def skewed_lattice(nel, eps: float, segments: int = 2) -> np.ndarray:
+    """A strongly skewed vertex lattice of [0,1]^3, a stand-in for the paper's Kershaw meshes
+    (Sec. 3.1; the paper does not give their map): eps = 1 is the uniform box, smaller eps squeezes
+    half of each column of elements and stretches the other half, with the split point moving
+    along a zigzag in the other coordinates, so that elements are sheared and their aspect
+    ratios reach (2 - eps)/eps and their shear dy/dx up to 2 segments (1 - eps) v.  With the
+    default two pieces, eps = 0.3 converges in about 30 iterations of the paper's default
+    preconditioner, the range the paper reports for its moderately skewed mesh (six pieces,
+    shear up to 4.2, take about 200).
+
+    x = a;  y = split(b, t1(a));  z = split(c, t2(a, b)), with split the monotone
+    piecewise-linear map sending 1/2 to t, t1 = 1/2 + (1 - eps)/2 zigzag(a),
+    t2 = 1/2 + (1 - eps)/2 zigzag(a) zigzag(b), and zigzag the +-1 wave with ``segments`` linear
+    pieces.  Same layout as ``vertex_lattice``; the boundary faces stay on the unit cube.
+    """
+    assert 0.0 < eps <= 1.0
+    nx, ny, nz = nel
+    a = (np.arange(nx + 1) / nx)[None, None, :]
+    b = (np.arange(ny + 1) / ny)[None, :, None]
+    c = (np.arange(nz + 1) / nz)[:, None, None]
+    amp = 0.5 * (1.0 - eps)
+    t1 = 0.5 + amp * _zigzag(a, segments)
+    t2 = 0.5 + amp * _zigzag(a, segments) * _zigzag(b, segments)
+    V = np.empty((nz + 1, ny + 1, nx + 1, 3))
+    V[..., 0] = np.broadcast_to(a, V.shape[:3])
+    V[..., 1] = np.broadcast_to(_split_map(b, t1), V.shape[:3])
+    V[..., 2] = np.broadcast_to(_split_map(c, t2), V.shape[:3])
+    return V
+
+
 def arnoldi_start_global(seed: int, n_global: int) -> np.ndarray:
     """Start vector of the Chebyshev bound estimate: 2U-1 per global node id (stream ``seed``)."""
     return 2.0 * uniform01(seed, np.arange(n_global, dtype=np.uint64)) - 1.0
