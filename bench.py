@@ -123,9 +123,16 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def alu_peak_tflops(fp32, sm_max_mhz):
-    """Derived ALU peak: 152 SMs x (128 FP32 | 2 FP64) FMA lanes per clock x 2 flop x clock."""
-    return N_SMS * (128 if fp32 else FP64_FMA_PER_CLK_PER_SM) * 2 * sm_max_mhz * 1e6 / 1e12
+VARIANT_KIND = ("f64", "f32", "df64")
+DF64_INSTR_PER_FLOP = 7.5   # a df64 FMA (2 flops) is 15 FP32 instructions (see csrc/df64.h)
+
+
+def alu_peak_tflops(kind, sm_max_mhz):
+    """Derived ALU peak: 152 SMs x (128 FP32 | 2 FP64) FMA lanes per clock x 2 flop x clock;
+    df64: the FP32 instruction rate (152 x 128 x clock) / 7.5 FP32 instructions per df64 flop."""
+    if kind == "df64":
+        return N_SMS * 128 * sm_max_mhz * 1e6 / DF64_INSTR_PER_FLOP / 1e12
+    return N_SMS * (128 if kind == "f32" else FP64_FMA_PER_CLK_PER_SM) * 2 * sm_max_mhz * 1e6 / 1e12
 
 
 def dram_traffic(kernel, variant):
@@ -143,24 +150,27 @@ def dram_traffic(kernel, variant):
 
 def roofline(kernel, variant, d, pk, pk_kind):
     """Bound = the roof that takes longer for this kernel's algorithmic bytes and flops."""
-    fp32 = variant >= 32
+    kind = VARIANT_KIND[variant // 32]
+    fp32 = kind == "f32"
     sm_max = pk.get("sm_max_mhz", 2070.0)
-    alu = alu_peak_tflops(fp32, sm_max)
+    alu = alu_peak_tflops(kind, sm_max)
     hbm = pk["hbm_gbs"]
     n = max(d["launches"], 1)
     avg_s = d["ms"] / n * 1e-3
     t_alu = d["flops"] / (alu * 1e12)
     t_hbm = d["bytes"] / (hbm * 1e9)
     traffic, src = dram_traffic(kernel, variant)
-    name = f"{kernel} p={variant % 32} {'f32' if fp32 else 'f64'}"
+    name = f"{kernel} p={variant % 32} {kind}"
     if t_alu >= t_hbm:
         achieved = d["flops"] / n / avg_s / 1e12
         return {"bound": "alu", "kernel": name, "achieved": round(achieved, 4), "peak": round(alu, 4),
                 "unit": "TFLOP/s", "frac": round(achieved / alu, 4), "traffic": traffic,
                 "algorithmic_bytes_per_launch": d["bytes"] / n, "flops_per_launch": d["flops"] / n,
                 "avg_launch_ms": round(avg_s * 1e3, 4), "traffic_source": src,
-                "peak_source": f"derived: 152 SMs x {128 if fp32 else 2} {'FP32' if fp32 else 'FP64'} "
-                               f"FMA/clk x 2 flop x {sm_max:.0f} MHz"}
+                "peak_source": (f"derived: 152 SMs x 128 FP32 instr/clk x {sm_max:.0f} MHz / "
+                                f"{DF64_INSTR_PER_FLOP} FP32 instr per df64 flop") if kind == "df64" else
+                               (f"derived: 152 SMs x {128 if fp32 else 2} {'FP32' if fp32 else 'FP64'} "
+                                f"FMA/clk x 2 flop x {sm_max:.0f} MHz")}
     achieved = d["bytes"] / n / avg_s / 1e9
     return {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": hbm,
             "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic,
@@ -197,7 +207,8 @@ def run_gpu(args):
     se.se_mesh_rhs(m, f.contiguous(), b)
     del xyz, X, f
     smoother = {"ras": se.SE_SMOOTH_RAS, "jacobi": se.SE_SMOOTH_JACOBI, "asm": se.SE_SMOOTH_ASM}[args.smoother]
-    prec = se.SE_FP32 if args.precond_fp32 else se.SE_FP64
+    prec = se.SE_FP32 if args.precond_fp32 else (se.SE_DF64 if args.df64 else se.SE_FP64)
+    op_df = 1 if (args.df64 or args.operator_df64) else 0
     t_setup0 = time.perf_counter()
     P = se.se_pmg_setup(m, se.pmg_desc(wk["schedule"], smoother, args.cheb_order, precision=prec))
     torch.cuda.synchronize()
@@ -210,7 +221,8 @@ def run_gpu(args):
     # round trip per iteration); the graph is captured on the first call and replayed after.
     def step(graph=1):
         x.zero_()
-        return se.se_solve(m, P, b, x, tol=1e-8, maxit=500, stream=stream, graph_capture=graph)
+        return se.se_solve(m, P, b, x, tol=1e-8, maxit=500, stream=stream, graph_capture=graph,
+                           operator_df64=op_df)
 
     for _ in range(args.warmup):
         st = step()
@@ -246,7 +258,7 @@ def run_gpu(args):
     prof = {se.KERNEL_NAMES[k]: se.se_prof_query(k) for k in range(se.SE_K_COUNT)}
     variants = {}
     for k in range(se.SE_K_COUNT):
-        for v in range(64):
+        for v in range(96):
             q = se.se_prof_query_variant(k, v)
             if q["launches"]:
                 variants[(se.KERNEL_NAMES[k], v)] = q
@@ -262,13 +274,15 @@ def run_gpu(args):
     e2e_steps = max(1, min(args.steps, 3))
     b_dev.copy_(b_host, non_blocking=True)
     x.zero_()
-    se.se_solve(m, P, b_dev, x, tol=1e-8, maxit=500, stream=stream, graph_capture=1)  # captures
+    se.se_solve(m, P, b_dev, x, tol=1e-8, maxit=500, stream=stream, graph_capture=1,
+                operator_df64=op_df)  # captures
     torch.cuda.synchronize()
     f0.record(stream)
     for _ in range(e2e_steps):
         b_dev.copy_(b_host, non_blocking=True)
         x.zero_()
-        se.se_solve(m, P, b_dev, x, tol=1e-8, maxit=500, stream=stream, graph_capture=1)
+        se.se_solve(m, P, b_dev, x, tol=1e-8, maxit=500, stream=stream, graph_capture=1,
+                    operator_df64=op_df)
         x_host.copy_(x, non_blocking=True)
     f1.record(stream)
     torch.cuda.synchronize()
@@ -277,24 +291,29 @@ def run_gpu(args):
     total_dof = sum_over_ranks(float(n_dof), world)
     value = total_dof / (ms_max * 1e-3) / 1e9
     e2e_value = total_dof / (e2e_ms * 1e-3) / 1e9
+    prec_name = {se.SE_FP64: "FP64", se.SE_FP32: "FP32", se.SE_DF64: "df64"}[prec]
+    op_name = "df64" if op_df else "FP64"
+    dtype = {se.SE_FP64: "f64", se.SE_FP32: "f64+f32", se.SE_DF64: "f64+df64"}[prec]
+    if prec == se.SE_FP64 and op_df:
+        dtype = "f64+df64"
     # ---- roofline of the dominant kernel (kernel class x level order x precision)
     pk, pk_kind = peaks()
     (dom, dvar), d = max(variants.items(), key=lambda kv: kv[1]["ms"])
     roof = roofline(dom, dvar, d, pk, pk_kind)
     tot_ms = max(sum(v["ms"] for v in variants.values()), 1e-9)
-    kernels = {f"{k} p={v % 32} {'f32' if v >= 32 else 'f64'}":
+    kernels = {f"{k} p={v % 32} {VARIANT_KIND[v // 32]}":
                {"ms_per_step": round(q["ms"] / args.steps, 3),
                 "launches_per_step": q["launches"] / args.steps, "share": round(q["ms"] / tot_ms, 4)}
                for (k, v), q in sorted(variants.items(), key=lambda kv: -kv[1]["ms"])}
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": "GDOF/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 3),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
         "data": "synthetic",
         "config": {"workload": f"{args.workload}: deformed box {nel[0]}x{nel[1]}x{nel[2]} hex, p={p}, "
                                f"n={n_dof} (E p^3), pMG {'-'.join(map(str, wk['schedule']))} "
                                f"Cheby-{args.smoother.upper()}({args.cheb_order}), "
-                               f"FPCG tol 1e-8, {'FP32' if args.precond_fp32 else 'FP64'} preconditioner",
+                               f"FPCG tol 1e-8, {prec_name} preconditioner, {op_name} outer operator",
                    "iterations": iters, "setup_s": round(setup_s, 2),
                    "solve_path": "se_solve graph_capture=1 (device-driven CUDA graph)",
                    "profiled_pass_ms_per_step": round(host_loop_ms, 3),
@@ -752,6 +771,9 @@ def main():
     ap.add_argument("--smoother", default="ras", choices=["ras", "jacobi", "asm"])
     ap.add_argument("--cheb-order", type=int, default=2)
     ap.add_argument("--precond-fp32", action="store_true")
+    ap.add_argument("--df64", action="store_true",
+                    help="SE_DF64 preconditioner and df64 outer operator (FP64 vectors)")
+    ap.add_argument("--operator-df64", action="store_true", help="df64 outer operator only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-timeout", type=float, default=240.0)
     ap.add_argument("--batch", type=int, default=0, help="run the batched workload of N problems")

@@ -47,11 +47,15 @@ enum se_status {
 };
 
 enum { SE_BC_DIRICHLET = 0, SE_BC_NEUMANN = 1 };
-enum { SE_FP64 = 0, SE_FP32 = 1 };
+/* Arithmetic of a preconditioner (se_pmg_desc.precision).  SE_DF64: FP64 vectors throughout, the
+ * operator and FDM kernels of the smoothed levels (odd orders) compute in double-float
+ * arithmetic on the FP32 pipe (pairs of FP32 values, about 48 significant bits); even orders
+ * fall back to FP64 arithmetic. */
+enum { SE_FP64 = 0, SE_FP32 = 1, SE_DF64 = 2 };
 enum { SE_SMOOTH_JACOBI = 0, SE_SMOOTH_RAS = 1, SE_SMOOTH_ASM = 2 };
 enum { SE_FPCG = 0, SE_FGMRES = 1 };
 /* se_ax flags */
-enum { SE_AX_ASSEMBLE = 1, SE_AX_MASK = 2, SE_AX_FP32 = 4 };
+enum { SE_AX_ASSEMBLE = 1, SE_AX_MASK = 2, SE_AX_FP32 = 4, SE_AX_DF64 = 8 };
 
 #define SE_MAX_LEVELS 8
 #define SE_MAX_ORDER 10
@@ -104,7 +108,9 @@ int se_mesh_rhs(se_mesh_t m, const double* f_dev, double* b_dev, void* stream);
 /* ---------------------------------------------------------------- operator (Sec. 2.1) */
 /* y = [M] [QQ^T] A_L [M] u.  flags: SE_AX_ASSEMBLE applies QQ^T (direct stiffness
  * summation), SE_AX_MASK zeroes Dirichlet nodes of input and output, SE_AX_FP32 computes in
- * FP32 (inputs and outputs stay FP64).  A_L is applied by tensor-product sum factorisation
+ * FP32, SE_AX_DF64 in double-float arithmetic (odd p only; SE_EINVAL otherwise; the first call
+ * allocates df64 copies of the geometric factors, 6 L x 8 bytes, owned by the mesh); inputs and
+ * outputs stay FP64.  A_L is applied by tensor-product sum factorisation
  * (Sec. 1: ~7E(p+1)^3 reads, 12E(p+1)^4 operations).  u and y must not overlap. */
 int se_ax(se_mesh_t m, const double* u, double* y, int flags, void* stream);
 /* In place u <- [M] QQ^T u (Sec. 2.1, gather-scatter); mask != 0 also zeroes Dirichlet nodes. */
@@ -128,8 +134,9 @@ typedef struct se_pmg_desc {
   uint64_t seed;                 /* start-vector stream: level l uses 1000 + l + 7919*seed */
   double coarse_tol;             /* coarsest-level Jacobi-PCG relative tolerance (1e-4) */
   int coarse_maxit;              /* and iteration cap (500) */
-  int precision;                 /* SE_FP64, or SE_FP32 for the whole V-cycle except the
-                                    coarse solve (Arnoldi and coarse solve stay FP64) */
+  int precision;                 /* SE_FP64; SE_FP32 for the whole V-cycle except the coarse
+                                    solve (Arnoldi and coarse solve stay FP64); SE_DF64: FP64
+                                    vectors, operator and FDM kernels in double-float */
 } se_pmg_desc;
 
 /* Builds the levels (each rediscretised on the same mapped mesh), Jacobi diagonals, FDM
@@ -196,6 +203,8 @@ typedef struct se_solve_opts {
   int tol_norm;      /* SE_TOL_R0 (0): stop when ||r_k|| <= tol ||r_0||; SE_TOL_B (1): when
                         ||r_k|| <= tol ||b|| (for an initial guess from se_proj_guess: the same
                         accuracy whatever the guess; 0 iterations if the guess already meets it) */
+  int operator_df64; /* 1: the outer operator A x computes in double-float arithmetic (odd p;
+                        FP64 otherwise), as se_ax with SE_AX_DF64 */
 } se_solve_opts;
 enum { SE_TOL_R0 = 0, SE_TOL_B = 1 };
 

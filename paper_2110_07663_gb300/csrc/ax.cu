@@ -141,11 +141,14 @@ int ax_local(const Level& lv, const T* u, T* y, bool mask_in, cudaStream_t s, co
   SE_CHECK(G != nullptr, SE_EINVAL, "ax_local: geometric factors for this precision missing");
   const int N = lv.N;
   const double pts = (double)lv.L;
+  bool use_df = false;
+  if constexpr (sizeof(T) == 8) use_df = !mask_in && ax_df_route(lv);
   ProfScope prof(SE_K_AX, s, pts, pts * ((sub ? 9.0 : 8.0) * sizeof(T) + (sub ? 1.0 : 0.0)),
-                 pts * (12.0 * N + 15.0), prof_variant<T>(lv.p));
+                 pts * (12.0 * N + 15.0), use_df ? lv.p + 64 : prof_variant<T>(lv.p));
   if constexpr (sizeof(T) == 4) {
     if (!mask_in && ax_tma_supported(lv.p)) return ax_local_tma(lv, u, y, s, sub);
   } else {
+    if (use_df) return ax_local_eo_df(lv, u, y, s, sub);
     if (!mask_in && ax_eo_supported(lv.p) && lv.eo64) return ax_local_eo(lv, u, y, s, sub);
   }
   switch (N) {
@@ -424,6 +427,22 @@ int se_ax(se_mesh_t m, const double* u, double* y, int flags, void* stream) {
     if (assemble) SE_TRY(gs_apply<float>(lv, m->tmpb32, mask, s));
     SE_TRY((convert<float, double>(m->tmpb32, y, lv.L, s)));
     if (!assemble && mask) SE_TRY(apply_mask64(lv, y, s));
+    return SE_OK;
+  }
+  if (flags & SE_AX_DF64) {
+    SE_CHECK(ax_eo_supported(lv.p), SE_EINVAL, "se_ax: SE_AX_DF64 needs an odd order (p=%d)", lv.p);
+    SE_TRY(make_df_geometry(lv, m->allocs, s));
+    Level ld = lv;
+    ld.df = true;
+    const double* in = u;
+    if (mask) {  // masked input through the mesh's work vector
+      SE_CUDA(cudaMemcpyAsync(m->tmp64, u, lv.L * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      SE_TRY(apply_mask64(lv, m->tmp64, s));
+      in = m->tmp64;
+    }
+    SE_TRY(ax_local<double>(ld, in, y, false, s));
+    if (assemble) return gs_apply<double>(ld, y, mask, s);
+    if (mask) return apply_mask64(lv, y, s);
     return SE_OK;
   }
   SE_TRY(ax_local<double>(lv, u, y, mask, s));

@@ -9,15 +9,17 @@
 // this kernel is bound by the FP64 pipe; shared memory (all lines and intermediates of the element
 // are staged there) has ample headroom.  Same sum factorisation as ax_local_kernel:
 //   (ur, us, ut) = (D_r u, D_s u, D_t u);  w = G (ur, us, ut);  y = D_r^T wr + D_s^T ws + D_t^T wt.
+// The arithmetic type T is double, or df64 (double-float on the FP32 pipe, about 48 bits): u and
+// y stay FP64 in memory either way; the df64 instance reads df64 copies of G and the tables.
 #include "se_internal.h"
 
 namespace se {
 
-template <int N>
-__device__ __forceinline__ void eo_line(const double* __restrict__ Ep, const double* __restrict__ Om,
-                                        const double (&v)[N], double (&out)[N]) {
+template <int N, typename T>
+__device__ __forceinline__ void eo_line(const T* __restrict__ Ep, const T* __restrict__ Om,
+                                        const T (&v)[N], T (&out)[N]) {
   constexpr int H = N / 2;
-  double e[H], o[H];
+  T e[H], o[H];
 #pragma unroll
   for (int l = 0; l < H; ++l) {
     e[l] = v[l] + v[N - 1 - l];
@@ -25,7 +27,7 @@ __device__ __forceinline__ void eo_line(const double* __restrict__ Ep, const dou
   }
 #pragma unroll
   for (int k = 0; k < H; ++k) {
-    double E = 0.0, O = 0.0;
+    T E = T(0.0), O = T(0.0);
 #pragma unroll
     for (int l = 0; l < H; ++l) {
       E = fma(Ep[k * H + l], e[l], E);
@@ -37,38 +39,38 @@ __device__ __forceinline__ void eo_line(const double* __restrict__ Ep, const dou
 }
 
 // tables: [0] Ep(D), [1] Om(D), [2] Ep(D^T), [3] Om(D^T), each H*H
-template <int N>
+template <int N, typename T>
 __global__ void __launch_bounds__(512) ax_eo_kernel(int64_t E, int NE, const double* __restrict__ u,
-                                                    const double* __restrict__ G, int64_t L,
-                                                    const double* __restrict__ tables,
+                                                    const T* __restrict__ G, int64_t L,
+                                                    const T* __restrict__ tables,
                                                     double* __restrict__ y,
                                                     const uint8_t* __restrict__ pflag,
                                                     const double* __restrict__ sub) {
   constexpr int N2 = N * N, N3 = N * N * N, H = N / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* tab = reinterpret_cast<double*>(smem_raw);          // 4 H^2
+  T* tab = reinterpret_cast<T*>(smem_raw);                    // 4 H^2
   const int le = threadIdx.x / N2;
   const int t = threadIdx.x - le * N2;
-  double* su = tab + 4 * H * H + (size_t)le * 5 * N3;
-  double* sr = su + N3;
-  double* ss = sr + N3;
-  double* st = ss + N3;
-  double* sy = st + N3;
+  T* su = tab + 4 * H * H + (size_t)le * 5 * N3;
+  T* sr = su + N3;
+  T* ss = sr + N3;
+  T* st = ss + N3;
+  T* sy = st + N3;
   for (int q = threadIdx.x; q < 4 * H * H; q += blockDim.x) tab[q] = tables[q];
   const int64_t e = (int64_t)blockIdx.x * NE + le;
   const bool valid = (le < NE) && (e < E);
   const int64_t eb = e * N3;
   if (valid) {
 #pragma unroll
-    for (int q = 0; q < N; ++q) su[t + N2 * q] = u[eb + t + N2 * q];
+    for (int q = 0; q < N; ++q) su[t + N2 * q] = T(u[eb + t + N2 * q]);
   }
   __syncthreads();
-  const double* EpD = tab;
-  const double* OmD = tab + H * H;
-  const double* EpT = tab + 2 * H * H;
-  const double* OmT = tab + 3 * H * H;
+  const T* EpD = tab;
+  const T* OmD = tab + H * H;
+  const T* EpT = tab + 2 * H * H;
+  const T* OmT = tab + 3 * H * H;
   const int a = t % N, b = t / N;
-  double v[N], out[N];
+  T v[N], out[N];
   if (valid) {
     // r-lines (j = a, k = b)
 #pragma unroll
@@ -96,12 +98,12 @@ __global__ void __launch_bounds__(512) ax_eo_kernel(int64_t E, int NE, const dou
     for (int q = 0; q < N; ++q) {
       const int pt = t + N2 * q;
       const int64_t gi = eb + pt;
-      const double ur = sr[pt], us = ss[pt], ut = st[pt];
-      const double grr = G[gi], grs = G[L + gi], grt = G[2 * L + gi];
-      const double gss = G[3 * L + gi], gst = G[4 * L + gi], gtt = G[5 * L + gi];
-      sr[pt] = grr * ur + grs * us + grt * ut;
-      ss[pt] = grs * ur + gss * us + gst * ut;
-      st[pt] = grt * ur + gst * us + gtt * ut;
+      const T ur = sr[pt], us = ss[pt], ut = st[pt];
+      const T grr = G[gi], grs = G[L + gi], grt = G[2 * L + gi];
+      const T gss = G[3 * L + gi], gst = G[4 * L + gi], gtt = G[5 * L + gi];
+      sr[pt] = fma(grt, ut, fma(grs, us, grr * ur));
+      ss[pt] = fma(gst, ut, fma(gss, us, grs * ur));
+      st[pt] = fma(gtt, ut, fma(gst, us, grt * ur));
     }
   }
   __syncthreads();
@@ -119,7 +121,7 @@ __global__ void __launch_bounds__(512) ax_eo_kernel(int64_t E, int NE, const dou
     for (int l = 0; l < N; ++l) v[l] = ss[a + N * l + N2 * b];
     eo_line<N>(EpT, OmT, v, out);
 #pragma unroll
-    for (int l = 0; l < N; ++l) sy[a + N * l + N2 * b] += out[l];
+    for (int l = 0; l < N; ++l) sy[a + N * l + N2 * b] = sy[a + N * l + N2 * b] + out[l];
   }
   __syncthreads();
   if (valid) {
@@ -127,27 +129,28 @@ __global__ void __launch_bounds__(512) ax_eo_kernel(int64_t E, int NE, const dou
     for (int l = 0; l < N; ++l) v[l] = st[a + N * b + N2 * l];
     eo_line<N>(EpT, OmT, v, out);
 #pragma unroll
-    for (int l = 0; l < N; ++l) sy[a + N * b + N2 * l] += out[l];
+    for (int l = 0; l < N; ++l) sy[a + N * b + N2 * l] = sy[a + N * b + N2 * l] + out[l];
   }
   __syncthreads();
   if (valid) {
 #pragma unroll
-    for (int q = 0; q < N; ++q) y[eb + t + N2 * q] = ax_output(sy[t + N2 * q], sub, pflag, eb + t + N2 * q);
+    for (int q = 0; q < N; ++q)
+      y[eb + t + N2 * q] = ax_output(io_cast<double>(sy[t + N2 * q]), sub, pflag, eb + t + N2 * q);
   }
 }
 
-template <int N>
-static int launch_ax_eo(const Level& lv, const double* u, double* y, const double* tables,
+template <int N, typename T>
+static int launch_ax_eo(const Level& lv, const double* u, double* y, const T* G, const T* tables,
                         const double* sub, cudaStream_t s) {
   constexpr int H = N / 2;
   const int NE = ax_elems_per_block(N - 1, false);
   const int threads = NE * N * N;
-  const size_t smem = (4 * H * H + (size_t)NE * 5 * N * N * N) * sizeof(double);
-  static const cudaError_t attr =
-      cudaFuncSetAttribute(ax_eo_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  const size_t smem = (4 * H * H + (size_t)NE * 5 * N * N * N) * sizeof(T);
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      ax_eo_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   SE_CUDA(attr);
   const unsigned blocks = (unsigned)((lv.E + NE - 1) / NE);
-  ax_eo_kernel<N><<<blocks, threads, smem, s>>>(lv.E, NE, u, lv.G64, lv.L, tables, y, lv.pflag, sub);
+  ax_eo_kernel<N, T><<<blocks, threads, smem, s>>>(lv.E, NE, u, G, lv.L, tables, y, lv.pflag, sub);
   SE_LAUNCH_CHECK();
   return SE_OK;
 }
@@ -166,16 +169,52 @@ void ax_eo_tables(const Basis1D& b, double* out) {
       }
 }
 
-int ax_local_eo(const Level& lv, const double* u, double* y, cudaStream_t s, const double* sub) {
-  SE_CHECK(lv.eo64 != nullptr, SE_EINVAL, "ax_eo: folded tables missing");
+template <typename T>
+static int ax_eo_dispatch(const Level& lv, const double* u, double* y, const T* G, const T* tab,
+                          cudaStream_t s, const double* sub) {
   switch (lv.N) {
-    case 2: return launch_ax_eo<2>(lv, u, y, lv.eo64, sub, s);
-    case 4: return launch_ax_eo<4>(lv, u, y, lv.eo64, sub, s);
-    case 6: return launch_ax_eo<6>(lv, u, y, lv.eo64, sub, s);
-    case 8: return launch_ax_eo<8>(lv, u, y, lv.eo64, sub, s);
-    case 10: return launch_ax_eo<10>(lv, u, y, lv.eo64, sub, s);
+    case 2: return launch_ax_eo<2, T>(lv, u, y, G, tab, sub, s);
+    case 4: return launch_ax_eo<4, T>(lv, u, y, G, tab, sub, s);
+    case 6: return launch_ax_eo<6, T>(lv, u, y, G, tab, sub, s);
+    case 8: return launch_ax_eo<8, T>(lv, u, y, G, tab, sub, s);
+    case 10: return launch_ax_eo<10, T>(lv, u, y, G, tab, sub, s);
     default: set_error("ax_eo: unsupported N=%d", lv.N); return SE_EINVAL;
   }
+}
+
+int ax_local_eo(const Level& lv, const double* u, double* y, cudaStream_t s, const double* sub) {
+  SE_CHECK(lv.eo64 != nullptr, SE_EINVAL, "ax_eo: folded tables missing");
+  return ax_eo_dispatch<double>(lv, u, y, lv.G64, lv.eo64, s, sub);
+}
+
+int ax_local_eo_df(const Level& lv, const double* u, double* y, cudaStream_t s, const double* sub) {
+  SE_CHECK(lv.Gdf != nullptr && lv.eodf != nullptr, SE_EINVAL, "ax_eo_df: df64 geometry missing");
+  return ax_eo_dispatch<df64>(lv, u, y, lv.Gdf, lv.eodf, s, sub);
+}
+
+__global__ void split_df_kernel(int64_t n, const double* __restrict__ a, df64* __restrict__ b) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = df64(a[i]);
+}
+
+int split_df(const double* a, df64* b, int64_t n, cudaStream_t s) {
+  if (n <= 0) return SE_OK;
+  split_df_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, a, b);
+  SE_LAUNCH_CHECK();
+  return SE_OK;
+}
+
+int make_df_geometry(Level& lv, Allocs& allocs, cudaStream_t s) {
+  if (!lv.Gdf) {
+    SE_TRY(dmalloc(allocs, &lv.Gdf, 6 * (size_t)lv.L));
+    SE_TRY(split_df(lv.G64, lv.Gdf, 6 * lv.L, s));
+  }
+  if (!lv.eodf && ax_eo_supported(lv.p) && lv.eo64) {
+    const int H = lv.N / 2;
+    SE_TRY(dmalloc(allocs, &lv.eodf, 4 * (size_t)H * H));
+    SE_TRY(split_df(lv.eo64, lv.eodf, 4 * H * H, s));
+  }
+  return SE_OK;
 }
 
 }  // namespace se

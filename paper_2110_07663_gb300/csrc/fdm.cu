@@ -132,7 +132,8 @@ __global__ void cast_kernel(int64_t n, const double* __restrict__ a, T* __restri
   if (i < n) b[i] = (T)a[i];
 }
 
-int fdm_setup(const se_mesh_s* m, Level& lv, Allocs& allocs, bool want32, cudaStream_t s) {
+int fdm_setup(const se_mesh_s* m, Level& lv, Allocs& allocs, bool want32, cudaStream_t s,
+              bool want_df) {
   const int P = lv.p, N = P + 1, PB = P + 3;
   const int64_t E = lv.E;
   // 1D GLL stiffness D^T W D (reference element)
@@ -168,6 +169,12 @@ int fdm_setup(const se_mesh_s* m, Level& lv, Allocs& allocs, bool want32, cudaSt
     cast_kernel<float><<<grid_for(3 * E * PB * PB, 256), 256, 0, s>>>(3 * E * PB * PB, lv.S64, lv.S32);
     cast_kernel<float><<<grid_for(3 * E * PB, 256), 256, 0, s>>>(3 * E * PB, lv.lam64, lv.lam32);
     SE_LAUNCH_CHECK();
+  }
+  if (want_df) {
+    SE_TRY(dmalloc(allocs, &lv.Sdf, 3 * E * PB * PB));
+    SE_TRY(dmalloc(allocs, &lv.lamdf, 3 * E * PB));
+    SE_TRY(split_df(lv.S64, lv.Sdf, 3 * E * PB * PB, s));
+    SE_TRY(split_df(lv.lam64, lv.lamdf, 3 * E * PB, s));
   }
   return SE_OK;
 }
@@ -229,14 +236,16 @@ __device__ __forceinline__ T dot_row(const T* __restrict__ row, const T (&v)[PBP
   return acc;
 }
 
-template <int P, typename T, int MODE>
+// T is the arithmetic type (double, or df64: double-float on the FP32 pipe) and IO the type of
+// the vectors in memory (T, or double for df64).
+template <int P, typename T, int MODE, typename IO = T>
 __global__ void __launch_bounds__(512) fdm_kernel(int64_t E, int NE, const int* __restrict__ nbr,
-                                                  const T* __restrict__ in,
+                                                  const IO* __restrict__ in,
                                                   const T* __restrict__ Sg,
                                                   const T* __restrict__ lamg,
                                                   const double* __restrict__ dinvg,
                                                   const uint8_t* __restrict__ pflag,
-                                                  T* __restrict__ out) {
+                                                  IO* __restrict__ out) {
   constexpr int N = P + 1, PB = P + 3, PB2 = PB * PB, PB3 = PB * PB * PB;
   using Dm = FdmDims<PB>;
   constexpr int PBP = Dm::PBP, PB3P = Dm::PB3P, SROW = Dm::SROW;
@@ -274,7 +283,7 @@ __global__ void __launch_bounds__(512) fdm_kernel(int64_t E, int NE, const int* 
   if constexpr (MODE == FDM_EXT_IN) {
     for (int q = tid; q < ne * PB3; q += nt) {
       const int le = q / PB3;
-      B0(le)[q - le * PB3] = in[e0 * PB3 + q];
+      B0(le)[q - le * PB3] = T(in[e0 * PB3 + q]);
     }
   } else {
     if (tid < ne * PB2) {
@@ -283,7 +292,7 @@ __global__ void __launch_bounds__(512) fdm_kernel(int64_t E, int NE, const int* 
       T* b0 = B0(le);
       for (int c = 0; c < PB; ++c) {
         const int64_t src = window_source<P>(snb + 27 * le, e0 + le, a, b, c);
-        b0[a + PB * (b + PB * c)] = src >= 0 ? in[src] : T(0);
+        b0[a + PB * (b + PB * c)] = src >= 0 ? T(in[src]) : T(0);
       }
     }
   }
@@ -291,7 +300,7 @@ __global__ void __launch_bounds__(512) fdm_kernel(int64_t E, int NE, const int* 
     __syncthreads();
     for (int q = tid; q < ne * PB3; q += nt) {
       const int le = q / PB3;
-      out[e0 * PB3 + q] = B0(le)[q - le * PB3];
+      out[e0 * PB3 + q] = io_cast<IO>(B0(le)[q - le * PB3]);
     }
     return;
   } else {
@@ -338,7 +347,7 @@ __global__ void __launch_bounds__(512) fdm_kernel(int64_t E, int NE, const int* 
         const T acc = dot_row<PB, PBP>(STz + ga * PBP, v);
         const int q = al + PB * (be + PB * ga);
         T dv;
-        if constexpr (sizeof(T) == 8) dv = dinvg[(e0 + le) * PB3 + q];
+        if constexpr (sizeof(T) == 8) dv = T(dinvg[(e0 + le) * PB3 + q]);
         else dv = __frcp_rn(lxy + sl[2 * PB + ga]);
         b1[q] = acc * dv;
       }
@@ -391,9 +400,9 @@ __global__ void __launch_bounds__(512) fdm_kernel(int64_t E, int NE, const int* 
           const int64_t li = e * (N * N * N) + (a - 1) + N * ((b - 1) + N * (c - 1));
           const int mlog = __ffs(pflag[li] & 0x0F) - 1;   // 1/multiplicity: exact power of 2
           const T wt = mlog == 0 ? T(1) : (mlog == 1 ? T(0.5) : (mlog == 2 ? T(0.25) : T(0.125)));
-          out[li] = acc * wt;
+          out[li] = io_cast<IO>(acc * wt);
         } else {
-          out[e * PB3 + a + PB * (b + PB * c)] = acc;
+          out[e * PB3 + a + PB * (b + PB * c)] = io_cast<IO>(acc);
         }
       }
     }
@@ -827,6 +836,23 @@ static int launch_fdm(const Level& lv, const T* in, const T* S, const T* lam, T*
   return SE_OK;
 }
 
+// df64 arithmetic on FP64 vectors: the FP64 kernel's layout and launch shape (df64 values are
+// 8 bytes, as FP64 ones), its S and Lambda from the df64 copies.
+template <int P, int MODE>
+static int launch_fdm_df(const Level& lv, const double* in, double* out, cudaStream_t s) {
+  const int NE = fdm_elems_per_block(P, false);
+  const int threads = fdm_block_threads(P, false, NE);
+  const size_t smem = fdm_smem_bytes(P, false, NE);
+  const unsigned blocks = (unsigned)((lv.E + NE - 1) / NE);
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      fdm_kernel<P, df64, MODE, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  SE_CUDA(attr);
+  fdm_kernel<P, df64, MODE, double><<<blocks, threads, smem, s>>>(lv.E, NE, lv.nbr, in, lv.Sdf, lv.lamdf,
+                                                                   lv.fdm_dinv64, lv.pflag, out);
+  SE_LAUNCH_CHECK();
+  return SE_OK;
+}
+
 template <typename T, int MODE>
 static int dispatch_fdm(const Level& lv, const T* in, T* out, cudaStream_t s) {
   const T* S;
@@ -842,7 +868,21 @@ static int dispatch_fdm(const Level& lv, const T* in, T* out, cudaStream_t s) {
   const double PB = lv.p + 3.0, N = lv.N;
   const double fl = 2.0 * (3.0 * PB * PB * PB * PB + PB * PB * PB * N + PB * PB * N * N + PB * N * N * N) + PB * PB * PB;
   const double by = (PB * PB * PB + N * N * N + 3 * PB * PB + 3 * PB + (sizeof(T) == 8 ? PB * PB * PB : 0)) * sizeof(T);
-  ProfScope prof(SE_K_FDM, s, (double)lv.E, by * lv.E, fl * lv.E, prof_variant<T>(lv.p));
+  bool use_df = false;
+  if constexpr (sizeof(T) == 8) use_df = MODE != FDM_GATHER && lv.df && lv.Sdf && (lv.p % 2 == 1);
+  ProfScope prof(SE_K_FDM, s, (double)lv.E, by * lv.E, fl * lv.E,
+                 use_df ? lv.p + 64 : prof_variant<T>(lv.p));
+  if constexpr (sizeof(T) == 8 && MODE != FDM_GATHER) {
+    if (use_df) {
+      switch (lv.p) {
+#define SE_FDM_DF(PP) \
+  case PP: return launch_fdm_df<PP, MODE>(lv, in, out, s);
+        SE_FDM_DF(1) SE_FDM_DF(3) SE_FDM_DF(5) SE_FDM_DF(7) SE_FDM_DF(9)
+#undef SE_FDM_DF
+        default: break;
+      }
+    }
+  }
   switch (lv.p) {
 #define SE_FDM_CASE(PP) \
   case PP: return launch_fdm<PP, T, MODE>(lv, in, S, lam, out, s);

@@ -271,7 +271,10 @@ static int pmg_build(se_pmg_s* P) {
   cudaStream_t s = P->stream;
   const se_pmg_desc& d = P->desc;
   const bool fp32 = d.precision == SE_FP32;
+  const bool df = d.precision == SE_DF64;
   SE_TRY(scratch_alloc(P->allocs, &P->scratch));
+  // df64 copies of the fine geometry belong to the mesh (the outer operator may use them too)
+  if (df && ax_eo_supported(m->fine.p)) SE_TRY(make_df_geometry(m->fine, m->allocs, s));
   P->owned[0] = m->fine;  // shallow copy: shares the mesh's geometry and maps
   P->owned[0].G32 = nullptr;
   P->lv[0] = &P->owned[0];
@@ -284,8 +287,12 @@ static int pmg_build(se_pmg_s* P) {
     Level& lv = *P->lv[l];
     const bool coarsest = l == P->nlev - 1;
     if (fp32 && !coarsest) SE_TRY(make_fp32_geometry(lv, P->allocs, s));
+    if (df && !coarsest && ax_eo_supported(lv.p)) {
+      SE_TRY(make_df_geometry(lv, P->allocs, s));
+      lv.df = true;
+    }
     if (!coarsest && d.smoother != SE_SMOOTH_JACOBI) {
-      SE_TRY(fdm_setup(m, lv, P->allocs, fp32, s));
+      SE_TRY(fdm_setup(m, lv, P->allocs, fp32, s, df && ax_eo_supported(lv.p)));
       if (d.smoother == SE_SMOOTH_ASM) {
         const int64_t n3 = lv.E * (int64_t)(lv.p + 3) * (lv.p + 3) * (lv.p + 3);
         SE_TRY(dmalloc(P->allocs, &lv.ext64, n3));
@@ -364,7 +371,8 @@ int se_pmg_setup(se_mesh_t m, const se_pmg_desc* desc, se_pmg_t* out) {
   SE_CHECK(d.eig_hi > d.eig_lo && d.eig_lo >= 0, SE_EINVAL, "se_pmg_setup: need 0 <= eig_lo < eig_hi");
   SE_CHECK(d.arnoldi_steps >= 1 && d.arnoldi_steps <= 100, SE_EINVAL, "se_pmg_setup: arnoldi_steps");
   SE_CHECK(d.coarse_tol > 0 && d.coarse_maxit >= 1, SE_EINVAL, "se_pmg_setup: coarse tolerance");
-  SE_CHECK(d.precision == SE_FP64 || d.precision == SE_FP32, SE_EINVAL, "se_pmg_setup: precision");
+  SE_CHECK(d.precision == SE_FP64 || d.precision == SE_FP32 || d.precision == SE_DF64, SE_EINVAL,
+           "se_pmg_setup: precision");
   static std::atomic<uint64_t> next_uid{0};
   auto* P = new se_pmg_s();
   P->mesh = m;
@@ -444,7 +452,7 @@ int se_pmg_cheby(se_pmg_t P, int lvl, const double* r, double* x, void* stream) 
   SE_CHECK(P && r && x && lvl >= 0 && lvl + 1 < P->nlev, SE_EINVAL, "se_pmg_cheby: bad argument");
   SE_CHECK(r != x, SE_EINVAL, "se_pmg_cheby: r and x must differ");
   cudaStream_t s = as_stream(stream, P->stream);
-  if (P->desc.precision == SE_FP64) {
+  if (P->desc.precision != SE_FP32) {
     // the level's b vector holds a copy of r so that the caller's r is never written
     LevelVecs<double>& V = P->vecs<double>(lvl);
     SE_CUDA(cudaMemcpyAsync(V.b, r, P->lv[lvl]->L * sizeof(double), cudaMemcpyDeviceToDevice, s));

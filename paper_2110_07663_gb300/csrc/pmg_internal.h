@@ -12,7 +12,7 @@ struct LevelVecs {
 
 int pmg_apply(se_pmg_s* P, const double* r, double* z, cudaStream_t s);
 int graph_solve_launch(se_mesh_s* m, se_pmg_s* P, const double* b, double* x, double tol,
-                       int maxit, cudaStream_t s, int tol_norm = SE_TOL_R0);
+                       int maxit, cudaStream_t s, int tol_norm = SE_TOL_R0, int op_df = 0);
 int graph_solve_result(se_mesh_s* m, cudaStream_t s, double tol, int maxit, se_solve_stats* st);
 // b = M QQ^T B_L f for f = pi^2 (k1^2+k2^2+k3^2) a sin(k1 pi x) sin(k2 pi y) sin(k3 pi z), the
 // right-hand side of the manufactured solution u* = a sin(k1 pi x) sin(k2 pi y) sin(k3 pi z).

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "se.h"
+#include "df64.h"
 
 namespace se {
 
@@ -109,6 +110,13 @@ struct Level {
   uint8_t* pflag = nullptr;  // multiplicity and free bit [L]
   double* D64 = nullptr;     // derivative matrix on the device [N*N]
   double* eo64 = nullptr;    // even-odd folded D and D^T tables [4][N/2][N/2] (even N)
+  // double-float copies for the operator and FDM kernels of SE_DF64 levels (FP64 vectors,
+  // df64 arithmetic); `df` routes those two kernels of this level to them
+  bool df = false;
+  df64* Gdf = nullptr;       // [6][L]
+  df64* eodf = nullptr;      // [4][N/2][N/2]
+  df64* Sdf = nullptr;       // [E][3][pb][pb]
+  df64* lamdf = nullptr;     // [E][3][pb]
   float* D32 = nullptr;
   const int* nbr = nullptr;  // element neighbours [E][27] (owned by the mesh)
   // fast diagonalisation factors (all levels but the coarsest)
@@ -178,6 +186,7 @@ struct se_mesh_s {
   double gtol = 0.0;
   int gmaxit = 0;
   int gtolnorm = 0;
+  int gopdf = 0;
 };
 
 namespace se {
@@ -256,7 +265,8 @@ template <class T>
 int gather_ext(const Level& lv, const T* r, T* rbar, cudaStream_t s);
 template <class T>
 int fdm_apply_ext(const Level& lv, const T* rbar, T* zbar, cudaStream_t s);
-int fdm_setup(const se_mesh_s* m, Level& lv, Allocs& allocs, bool want32, cudaStream_t s);
+int fdm_setup(const se_mesh_s* m, Level& lv, Allocs& allocs, bool want32, cudaStream_t s,
+              bool want_df = false);
 int asm_weights(Level& lv, Allocs& allocs, cudaStream_t s);
 // Transfers (transfer.cu): level f (fine) <-> level c (coarse)
 template <class T>
@@ -281,8 +291,9 @@ int coarse_solve(const Level& lv, CoarseWork& w, const T* r_l, T* x_l, double to
                  cudaStream_t s);
 
 // ------------------------------------------------------------------ profiling (common.cu)
-// Profiling variant of a launch: polynomial order p (0..31) plus 32 for FP32 arithmetic.
-constexpr int PROF_VARIANTS = 64;
+// Profiling variant of a launch: polynomial order p (0..31) plus 32 for FP32 arithmetic, plus 64
+// for double-float (df64) arithmetic on FP64 vectors.
+constexpr int PROF_VARIANTS = 96;
 template <class T>
 inline int prof_variant(int p) {
   return (p & 31) + (sizeof(T) == 4 ? 32 : 0);
@@ -316,6 +327,13 @@ int ax_local_tma(const Level& lv, const float* u, float* y, cudaStream_t s, cons
 bool ax_eo_supported(int p);
 void ax_eo_tables(const Basis1D& b, double* out);
 int ax_local_eo(const Level& lv, const double* u, double* y, cudaStream_t s, const double* sub);
+// The same contractions in df64 arithmetic (FP64 in and out); needs lv.Gdf and lv.eodf.
+int ax_local_eo_df(const Level& lv, const double* u, double* y, cudaStream_t s, const double* sub);
+// b[i] = nearest df64 of a[i] (device arrays, stream-ordered).
+int split_df(const double* a, df64* b, int64_t n, cudaStream_t s);
+// df64 copies of a level's geometric factors and folded tables (no-op if present).
+int make_df_geometry(Level& lv, Allocs& allocs, cudaStream_t s);
+inline bool ax_df_route(const Level& lv) { return lv.df && lv.Gdf && lv.eodf && ax_eo_supported(lv.p); }
 int pipeline_status_take(int* status);
 int fdm_elems_per_block(int p, bool fp32);
 size_t fdm_smem_bytes(int p, bool fp32, int ne);

@@ -42,10 +42,18 @@ static int read_scalars(se_mesh_s* m, cudaStream_t s, int count) {
   return SE_OK;
 }
 
+// The fine level as the outer operator sees it: FP64 arithmetic, or df64 (operator_df64) where
+// the mesh holds df64 geometry.
+static Level outer_level(const se_mesh_s* m, int op_df) {
+  Level lv = m->fine;
+  lv.df = op_df != 0;
+  return lv;
+}
+
 // Flexible PCG: beta = (z_{k+1}, r_{k+1} - r_k) / (z_k, r_k).
 static int fpcg(se_mesh_s* m, se_pmg_s* P, const double* b, double* x, const se_solve_opts& o,
                 cudaStream_t s, se_solve_stats* st) {
-  const Level& lv = m->fine;
+  const Level lv = outer_level(m, o.operator_df64);
   Scratch& sc = m->scratch;
   double *r = m->sr, *r2 = m->sr2, *z = m->sz, *p = m->sp, *w = m->sw;
   SE_TRY(ax_apply<double>(lv, x, w, s));
@@ -87,7 +95,7 @@ static int fpcg(se_mesh_s* m, se_pmg_s* P, const double* b, double* x, const se_
 // Givens rotations on the host; x += Z y at the end of each cycle.
 static int fgmres(se_mesh_s* m, se_pmg_s* P, const double* b, double* x, const se_solve_opts& o,
                   cudaStream_t s, se_solve_stats* st) {
-  const Level& lv = m->fine;
+  const Level lv = outer_level(m, o.operator_df64);
   const int64_t L = lv.L;
   Scratch& sc = m->scratch;
   const int mr = o.restart;
@@ -181,8 +189,10 @@ extern "C" int se_solve(se_mesh_t m, se_pmg_t P, const double* b, double* x,
   SE_CHECK(o.tol > 0 && o.maxit >= 1, SE_EINVAL, "se_solve: bad tolerance or maxit");
   SE_CHECK(o.tol_norm == SE_TOL_R0 || o.tol_norm == SE_TOL_B, SE_EINVAL, "se_solve: bad tol_norm");
   if (o.method == SE_FGMRES) SE_CHECK(o.restart >= 1 && o.restart <= 200, SE_EINVAL, "se_solve: restart");
+  SE_CHECK(o.operator_df64 == 0 || o.operator_df64 == 1, SE_EINVAL, "se_solve: operator_df64");
   cudaStream_t s = as_stream(o.stream, m->stream);
   SE_TRY(ensure_solve_work(m, o.restart, o.method == SE_FGMRES));
+  if (o.operator_df64 && ax_eo_supported(m->fine.p)) SE_TRY(make_df_geometry(m->fine, m->allocs, s));
   se_solve_stats st{};
   SE_CUDA(cudaEventRecord(m->ev0, s));
   int rc;
@@ -263,8 +273,9 @@ static int add_conditional(cudaStream_t cs, cudaGraphConditionalHandle h,
 // Appends one whole FPCG solve (x0 = the content of x at launch) to graph G, independent of the
 // rest of G.  All buffers must already exist: nothing is allocated while capturing.
 static int append_fpcg_solve(cudaGraph_t G, cudaStream_t cs, se_mesh_s* m, se_pmg_s* P,
-                             const double* b, double* x, double tol, int maxit, int tol_norm) {
-  const Level& lv = m->fine;
+                             const double* b, double* x, double tol, int maxit, int tol_norm,
+                             int op_df) {
+  const Level lv = outer_level(m, op_df);
   Scratch& sc = m->scratch;
   double *r = m->sr, *r_old = m->sr2, *z = m->sz, *p = m->sp, *w = m->sw;
   DevStats* st = static_cast<DevStats*>(m->gstats);
@@ -344,11 +355,12 @@ static int read_graph_stats(se_mesh_s* m, cudaStream_t s, se_solve_stats* out, d
 // Builds (or reuses) this mesh's solve graph for (P, b, x, tol, maxit) and launches it on s
 // without waiting.  read_graph_stats collects the result.
 int graph_solve_launch(se_mesh_s* m, se_pmg_s* P, const double* b, double* x, double tol,
-                       int maxit, cudaStream_t s, int tol_norm) {
+                       int maxit, cudaStream_t s, int tol_norm, int op_df) {
   SE_TRY(prepare_graph_solve(m));
   const uint64_t uid = P ? P->uid : 0;
   const bool same = m->gexec && m->gkey[0] == P && m->gpmg_uid == uid && m->gkey[1] == b && m->gkey[2] == x &&
-                    m->gtol == tol && m->gmaxit == maxit && m->gtolnorm == tol_norm;
+                    m->gtol == tol && m->gmaxit == maxit && m->gtolnorm == tol_norm &&
+                    m->gopdf == op_df;
   if (!same) {
     if (m->gexec) cudaGraphExecDestroy(m->gexec);
     m->gexec = nullptr;
@@ -356,7 +368,7 @@ int graph_solve_launch(se_mesh_s* m, se_pmg_s* P, const double* b, double* x, do
     SE_CUDA(cudaGraphCreate(&G, 0));
     cudaStream_t cs;
     SE_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    int rc = append_fpcg_solve(G, cs, m, P, b, x, tol, maxit, tol_norm);
+    int rc = append_fpcg_solve(G, cs, m, P, b, x, tol, maxit, tol_norm, op_df);
     cudaStreamDestroy(cs);
     if (rc == SE_OK) {
       cudaError_t e = cudaGraphInstantiate(&m->gexec, G, 0);
@@ -375,6 +387,7 @@ int graph_solve_launch(se_mesh_s* m, se_pmg_s* P, const double* b, double* x, do
     m->gtol = tol;
     m->gmaxit = maxit;
     m->gtolnorm = tol_norm;
+    m->gopdf = op_df;
   }
   SE_CUDA(cudaGraphLaunch(m->gexec, s));
   return SE_OK;
@@ -387,7 +400,7 @@ int graph_solve_result(se_mesh_s* m, cudaStream_t s, double tol, int maxit, se_s
 // se_solve with graph_capture: one launch of the cached graph, then its statistics.
 int graph_solve(se_mesh_s* m, se_pmg_s* P, const double* b, double* x, const se_solve_opts& o,
                 cudaStream_t s, se_solve_stats* st) {
-  SE_TRY(graph_solve_launch(m, P, b, x, o.tol, o.maxit, s, o.tol_norm));
+  SE_TRY(graph_solve_launch(m, P, b, x, o.tol, o.maxit, s, o.tol_norm, o.operator_df64));
   return read_graph_stats(m, s, st, o.tol, o.maxit);
 }
 
@@ -415,6 +428,8 @@ int se_batch_create(int n, const se_problem* probs, const se_solve_opts* opts, s
       SE_CHECK(probs[j].mesh != probs[i].mesh, SE_EINVAL,
                "se_batch_create: problems %d and %d share a mesh (its work space)", j, i);
     SE_TRY(prepare_graph_solve(probs[i].mesh));
+    if (opts->operator_df64 && ax_eo_supported(probs[i].mesh->fine.p))
+      SE_TRY(make_df_geometry(probs[i].mesh->fine, probs[i].mesh->allocs, probs[i].mesh->stream));
   }
   auto* B = new se_batch_s();
   B->probs.assign(probs, probs + n);
@@ -430,7 +445,7 @@ int se_batch_create(int n, const se_problem* probs, const se_solve_opts* opts, s
   int rc = SE_OK;
   for (int i = 0; i < n && rc == SE_OK; ++i)
     rc = append_fpcg_solve(G, cs, probs[i].mesh, probs[i].pmg, probs[i].b, probs[i].x, opts->tol,
-                           opts->maxit, opts->tol_norm);
+                           opts->maxit, opts->tol_norm, opts->operator_df64);
   cudaStreamDestroy(cs);
   if (rc == SE_OK && cudaGraphInstantiate(&B->exec, G, 0) != cudaSuccess) {
     set_error("se_batch_create: cudaGraphInstantiate: %s", cudaGetErrorString(cudaGetLastError()));

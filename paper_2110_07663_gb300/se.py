@@ -15,11 +15,11 @@ LIB_PATH = os.path.join(HERE, "libse.so")
 
 SE_OK, SE_EINVAL, SE_ENOMEM, SE_ENOTCONV, SE_ECUDA, SE_ETIMEOUT, SE_EBUSY, SE_EREFUSED = range(8)
 SE_BC_DIRICHLET, SE_BC_NEUMANN = 0, 1
-SE_FP64, SE_FP32 = 0, 1
+SE_FP64, SE_FP32, SE_DF64 = 0, 1, 2
 SE_SMOOTH_JACOBI, SE_SMOOTH_RAS, SE_SMOOTH_ASM = 0, 1, 2
 SE_FPCG, SE_FGMRES = 0, 1
 SE_TOL_R0, SE_TOL_B = 0, 1
-SE_AX_ASSEMBLE, SE_AX_MASK, SE_AX_FP32 = 1, 2, 4
+SE_AX_ASSEMBLE, SE_AX_MASK, SE_AX_FP32, SE_AX_DF64 = 1, 2, 4, 8
 SE_MESH_NONBLOCKING_STREAM = 1
 SE_RHS_MODES, SE_RHS_HOST = 0, 1
 SE_MAX_LEVELS, SE_MAX_ORDER = 8, 10
@@ -59,7 +59,7 @@ class se_pmg_desc(C.Structure):
 class se_solve_opts(C.Structure):
     _fields_ = [("method", C.c_int), ("restart", C.c_int), ("tol", C.c_double),
                 ("maxit", C.c_int), ("graph_capture", C.c_int), ("stream", C.c_void_p),
-                ("tol_norm", C.c_int)]
+                ("tol_norm", C.c_int), ("operator_df64", C.c_int)]
 
 
 class se_problem(C.Structure):
@@ -342,10 +342,11 @@ def se_pmg_coarse_solve_noalloc(P, r, x, stream=None) -> int:
 
 # ----------------------------------------------------------------------------- solve
 def se_solve(m, P, b, x, method=SE_FPCG, tol=1e-8, maxit=1000, restart=20, graph_capture=0,
-             stream=None, allow_notconv=False, tol_norm=0) -> se_solve_stats:
+             stream=None, allow_notconv=False, tol_norm=0, operator_df64=0) -> se_solve_stats:
     o = se_solve_opts()
     o.method, o.restart, o.tol, o.maxit, o.graph_capture = method, restart, tol, maxit, graph_capture
     o.tol_norm = tol_norm
+    o.operator_df64 = operator_df64
     o.stream = _stream(stream)
     st = se_solve_stats()
     _check(lib.se_solve(m, P, _ptr(b), _ptr(x), C.byref(o), C.byref(st)),
