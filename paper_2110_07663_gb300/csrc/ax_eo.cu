@@ -38,6 +38,53 @@ __device__ __forceinline__ void eo_line(const T* __restrict__ Ep, const T* __res
   }
 }
 
+// One line contraction from shared memory to shared memory: points base + stride * l.
+// df64: the output index loop is not unrolled and each output pair goes straight to shared
+// memory, so the folded tables are not held in registers across the six contractions (the
+// unrolled form needs 128 registers in df64 and limits the SM to 16 warps).
+template <int N, bool ACC, typename T>
+__device__ __forceinline__ void eo_apply(const T* __restrict__ Ep, const T* __restrict__ Om,
+                                         const T* src, T* dst, int base, int stride) {
+  T v[N];
+#pragma unroll
+  for (int l = 0; l < N; ++l) v[l] = src[base + stride * l];
+  if constexpr (is_df64<T>::value) {
+    constexpr int H = N / 2;
+    T e[H], o[H];
+#pragma unroll
+    for (int l = 0; l < H; ++l) {
+      e[l] = v[l] + v[N - 1 - l];
+      o[l] = v[l] - v[N - 1 - l];
+    }
+#pragma unroll 1
+    for (int k = 0; k < H; ++k) {
+      T E = Ep[k * H] * e[0], O = Om[k * H] * o[0];
+#pragma unroll
+      for (int l = 1; l < H; ++l) {
+        E = fma(Ep[k * H + l], e[l], E);
+        O = fma(Om[k * H + l], o[l], O);
+      }
+      T* d0 = dst + base + stride * k;
+      T* d1 = dst + base + stride * (N - 1 - k);
+      if constexpr (ACC) {
+        *d0 = *d0 + (E + O);
+        *d1 = *d1 + (O - E);
+      } else {
+        *d0 = E + O;
+        *d1 = O - E;
+      }
+    }
+  } else {
+    T out[N];
+    eo_line<N>(Ep, Om, v, out);
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      if constexpr (ACC) dst[base + stride * l] += out[l];
+      else dst[base + stride * l] = out[l];
+    }
+  }
+}
+
 // tables: [0] Ep(D), [1] Om(D), [2] Ep(D^T), [3] Om(D^T), each H*H
 template <int N, typename T>
 __global__ void __launch_bounds__(512) ax_eo_kernel(int64_t E, int NE, const double* __restrict__ u,
@@ -51,18 +98,18 @@ __global__ void __launch_bounds__(512) ax_eo_kernel(int64_t E, int NE, const dou
   T* tab = reinterpret_cast<T*>(smem_raw);                    // 4 H^2
   const int le = threadIdx.x / N2;
   const int t = threadIdx.x - le * N2;
-  T* su = tab + 4 * H * H + (size_t)le * 5 * N3;
+  T* su = tab + 4 * H * H + (size_t)le * 4 * N3;
   T* sr = su + N3;
   T* ss = sr + N3;
   T* st = ss + N3;
-  T* sy = st + N3;
+  T* sy = su;  // u is dead once the forward contractions are done
   for (int q = threadIdx.x; q < 4 * H * H; q += blockDim.x) tab[q] = tables[q];
   const int64_t e = (int64_t)blockIdx.x * NE + le;
   const bool valid = (le < NE) && (e < E);
   const int64_t eb = e * N3;
   if (valid) {
 #pragma unroll
-    for (int q = 0; q < N; ++q) su[t + N2 * q] = T(u[eb + t + N2 * q]);
+    for (int q = 0; q < N; ++q) su[t + N2 * q] = from_io<T>(u[eb + t + N2 * q]);
   }
   __syncthreads();
   const T* EpD = tab;
@@ -70,26 +117,10 @@ __global__ void __launch_bounds__(512) ax_eo_kernel(int64_t E, int NE, const dou
   const T* EpT = tab + 2 * H * H;
   const T* OmT = tab + 3 * H * H;
   const int a = t % N, b = t / N;
-  T v[N], out[N];
   if (valid) {
-    // r-lines (j = a, k = b)
-#pragma unroll
-    for (int l = 0; l < N; ++l) v[l] = su[l + N * a + N2 * b];
-    eo_line<N>(EpD, OmD, v, out);
-#pragma unroll
-    for (int l = 0; l < N; ++l) sr[l + N * a + N2 * b] = out[l];
-    // s-lines (i = a, k = b)
-#pragma unroll
-    for (int l = 0; l < N; ++l) v[l] = su[a + N * l + N2 * b];
-    eo_line<N>(EpD, OmD, v, out);
-#pragma unroll
-    for (int l = 0; l < N; ++l) ss[a + N * l + N2 * b] = out[l];
-    // t-lines (i = a, j = b)
-#pragma unroll
-    for (int l = 0; l < N; ++l) v[l] = su[a + N * b + N2 * l];
-    eo_line<N>(EpD, OmD, v, out);
-#pragma unroll
-    for (int l = 0; l < N; ++l) st[a + N * b + N2 * l] = out[l];
+    eo_apply<N, false>(EpD, OmD, su, sr, N * a + N2 * b, 1);   // r-lines (j = a, k = b)
+    eo_apply<N, false>(EpD, OmD, su, ss, a + N2 * b, N);       // s-lines (i = a, k = b)
+    eo_apply<N, false>(EpD, OmD, su, st, a + N * b, N2);       // t-lines (i = a, j = b)
   }
   __syncthreads();
   // pointwise geometric factors: points t + N2 q
@@ -108,29 +139,11 @@ __global__ void __launch_bounds__(512) ax_eo_kernel(int64_t E, int NE, const dou
   }
   __syncthreads();
   // transposed contractions: y = D_r^T wr (r-lines), then += D_s^T ws, then += D_t^T wt
-  if (valid) {
-#pragma unroll
-    for (int l = 0; l < N; ++l) v[l] = sr[l + N * a + N2 * b];
-    eo_line<N>(EpT, OmT, v, out);
-#pragma unroll
-    for (int l = 0; l < N; ++l) sy[l + N * a + N2 * b] = out[l];
-  }
+  if (valid) eo_apply<N, false>(EpT, OmT, sr, sy, N * a + N2 * b, 1);
   __syncthreads();
-  if (valid) {
-#pragma unroll
-    for (int l = 0; l < N; ++l) v[l] = ss[a + N * l + N2 * b];
-    eo_line<N>(EpT, OmT, v, out);
-#pragma unroll
-    for (int l = 0; l < N; ++l) sy[a + N * l + N2 * b] = sy[a + N * l + N2 * b] + out[l];
-  }
+  if (valid) eo_apply<N, true>(EpT, OmT, ss, sy, a + N2 * b, N);
   __syncthreads();
-  if (valid) {
-#pragma unroll
-    for (int l = 0; l < N; ++l) v[l] = st[a + N * b + N2 * l];
-    eo_line<N>(EpT, OmT, v, out);
-#pragma unroll
-    for (int l = 0; l < N; ++l) sy[a + N * b + N2 * l] = sy[a + N * b + N2 * l] + out[l];
-  }
+  if (valid) eo_apply<N, true>(EpT, OmT, st, sy, a + N * b, N2);
   __syncthreads();
   if (valid) {
 #pragma unroll
@@ -145,7 +158,7 @@ static int launch_ax_eo(const Level& lv, const double* u, double* y, const T* G,
   constexpr int H = N / 2;
   const int NE = ax_elems_per_block(N - 1, false);
   const int threads = NE * N * N;
-  const size_t smem = (4 * H * H + (size_t)NE * 5 * N * N * N) * sizeof(T);
+  const size_t smem = (4 * H * H + (size_t)NE * 4 * N * N * N) * sizeof(T);
   static const cudaError_t attr = cudaFuncSetAttribute(
       ax_eo_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   SE_CUDA(attr);

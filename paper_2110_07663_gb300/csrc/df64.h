@@ -76,10 +76,42 @@ __device__ __forceinline__ df64 fma(df64 a, df64 b, df64 c) {
   return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e, c.lo)));
 }
 
-// Conversion between a kernel's storage type IO and its arithmetic type T.
-template <class IO, class T>
-__device__ __forceinline__ IO io_cast(T v) {
-  return static_cast<IO>(v);
+// ---- conversions without the FP64 pipe
+// GB300's FP64 pipe (2 lanes per clock per SM) also executes the FP32 <-> FP64 conversions, so
+// converting every operand of a df64 kernel that way (4 FP64-pipe instructions per value in,
+// 3 out) kept that pipe 40% busy and stalled the FP32 work.  These conversions use integer and
+// FP32 instructions on the bit patterns instead.
+
+// FP64 -> df64: hi = the FP64 value truncated to 24 significant bits (exponent rebiased), lo =
+// the next 23 bits of its significand, scaled (|lo| < ulp(hi); about 47 bits in all).  Values
+// outside 2^-103 <= |d| < 2^128 (zero, tiny, huge, inf, NaN) take the FP64 route above.
+__device__ __forceinline__ df64 df_from_double(double d) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(d);
+  const unsigned hw = (unsigned)(bits >> 32), lw = (unsigned)bits;
+  const int ex = (int)((hw >> 20) & 0x7FFu);
+  if (ex < 920 || ex > 1150) return df64(d);
+  const unsigned sign = hw & 0x80000000u;
+  const unsigned mh = ((hw & 0xFFFFFu) << 3) | (lw >> 29);                    // top 23 bits
+  const float hi = __uint_as_float(sign | ((unsigned)(ex - 896) << 23) | mh);
+  const float frac = __fsub_rn(__uint_as_float(0x3F800000u | ((lw >> 6) & 0x7FFFFFu)), 1.0f);
+  const float scale = __uint_as_float(sign | ((unsigned)(ex - 919) << 23));   // 2^(ex - 1046)
+  return df64(hi, __fmul_rn(frac, scale));
+}
+
+// FP32 -> FP64 bit pattern (exact for normal numbers; FP32 subnormals become signed zero).
+__device__ __forceinline__ double f32_to_f64_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xFFu;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned long long mant = (unsigned long long)(u & 0x7FFFFFu) << 29;
+  const unsigned long long e64 = ex == 255u ? 2047ull : (unsigned long long)(ex + 896u);
+  const unsigned long long b = ex == 0u ? sign : (sign | (e64 << 52) | mant);
+  return __longlong_as_double((long long)b);
+}
+
+// df64 -> FP64: one FP64 addition of the two exactly converted parts.
+__device__ __forceinline__ double df_to_double(df64 v) {
+  return f32_to_f64_bits(v.hi) + f32_to_f64_bits(v.lo);
 }
 
 template <class T>
@@ -90,5 +122,17 @@ template <>
 struct is_df64<df64> {
   static constexpr bool value = true;
 };
+
+// Conversion between a kernel's storage type IO and its arithmetic type T.
+template <class IO, class T>
+__device__ __forceinline__ IO io_cast(T v) {
+  if constexpr (is_df64<T>::value && !is_df64<IO>::value) return df_to_double(v);
+  else return static_cast<IO>(v);
+}
+template <class T, class IO>
+__device__ __forceinline__ T from_io(IO v) {
+  if constexpr (is_df64<T>::value && !is_df64<IO>::value) return df_from_double((double)v);
+  else return T(v);
+}
 
 }  // namespace se

@@ -229,6 +229,17 @@ __device__ __forceinline__ T dot_row(const T* __restrict__ row, const T (&v)[PBP
       acc = fmaf(s.z, v[a + 2], acc);
       acc = fmaf(s.w, v[a + 3], acc);
     }
+  } else if constexpr (is_df64<T>::value) {
+    // two independent accumulation chains (a df64 FMA is a chain of about 13 dependent FP32
+    // operations, so one chain per row would leave the FP32 pipe waiting on latency)
+    T acc1 = T(0.0);
+#pragma unroll
+    for (int a = 0; a + 1 < PB; a += 2) {
+      acc = fma(row[a], v[a], acc);
+      acc1 = fma(row[a + 1], v[a + 1], acc1);
+    }
+    if constexpr (PB % 2 == 1) acc = fma(row[PB - 1], v[PB - 1], acc);
+    acc = acc + acc1;
   } else {
 #pragma unroll
     for (int a = 0; a < PB; ++a) acc = fma(row[a], v[a], acc);
@@ -251,6 +262,9 @@ __global__ void __launch_bounds__(512) fdm_kernel(int64_t E, int NE, const int* 
   constexpr int PBP = Dm::PBP, PB3P = Dm::PB3P, SROW = Dm::SROW;
   constexpr int LAMP = (3 * PB + 3) / 4 * 4;
   constexpr int PER = 2 * PB3P + 2 * SROW + LAMP;  // shared values per element
+  // output loops: fully unrolled in FP64; df64 unrolls them twice only (a df64 row dot product
+  // is about 150 instructions, and the fully unrolled kernel overflows the instruction cache)
+  constexpr int OUT_UNR = is_df64<T>::value ? 2 : PB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sbase = reinterpret_cast<T*>(smem_raw);
   int* snb = reinterpret_cast<int*>(sbase + (size_t)NE * PER);  // [NE][27]
@@ -283,7 +297,7 @@ __global__ void __launch_bounds__(512) fdm_kernel(int64_t E, int NE, const int* 
   if constexpr (MODE == FDM_EXT_IN) {
     for (int q = tid; q < ne * PB3; q += nt) {
       const int le = q / PB3;
-      B0(le)[q - le * PB3] = T(in[e0 * PB3 + q]);
+      B0(le)[q - le * PB3] = from_io<T>(in[e0 * PB3 + q]);
     }
   } else {
     if (tid < ne * PB2) {
@@ -292,7 +306,7 @@ __global__ void __launch_bounds__(512) fdm_kernel(int64_t E, int NE, const int* 
       T* b0 = B0(le);
       for (int c = 0; c < PB; ++c) {
         const int64_t src = window_source<P>(snb + 27 * le, e0 + le, a, b, c);
-        b0[a + PB * (b + PB * c)] = src >= 0 ? T(in[src]) : T(0);
+        b0[a + PB * (b + PB * c)] = src >= 0 ? from_io<T>(in[src]) : T(0);
       }
     }
   }
@@ -323,7 +337,7 @@ __global__ void __launch_bounds__(512) fdm_kernel(int64_t E, int NE, const int* 
       const int b = ql % PB, c = ql / PB;
 #pragma unroll
       for (int a = 0; a < PB; ++a) v[a] = b0[a + PB * (b + PB * c)];
-#pragma unroll
+#pragma unroll OUT_UNR
       for (int al = 0; al < PB; ++al) b1[al + PB * (b + PB * c)] = dot_row<PB, PBP>(STx + al * PBP, v);
     }
     __syncthreads();
@@ -332,7 +346,7 @@ __global__ void __launch_bounds__(512) fdm_kernel(int64_t E, int NE, const int* 
       const int al = ql % PB, c = ql / PB;
 #pragma unroll
       for (int b = 0; b < PB; ++b) v[b] = b1[al + PB * (b + PB * c)];
-#pragma unroll
+#pragma unroll OUT_UNR
       for (int be = 0; be < PB; ++be) b0[al + PB * (be + PB * c)] = dot_row<PB, PBP>(STy + be * PBP, v);
     }
     __syncthreads();
@@ -342,12 +356,12 @@ __global__ void __launch_bounds__(512) fdm_kernel(int64_t E, int NE, const int* 
 #pragma unroll
       for (int c = 0; c < PB; ++c) v[c] = b0[al + PB * (be + PB * c)];
       const T lxy = sl[al] + sl[PB + be];
-#pragma unroll
+#pragma unroll OUT_UNR
       for (int ga = 0; ga < PB; ++ga) {
         const T acc = dot_row<PB, PBP>(STz + ga * PBP, v);
         const int q = al + PB * (be + PB * ga);
         T dv;
-        if constexpr (sizeof(T) == 8) dv = T(dinvg[(e0 + le) * PB3 + q]);
+        if constexpr (sizeof(T) == 8) dv = from_io<T>(dinvg[(e0 + le) * PB3 + q]);
         else dv = __frcp_rn(lxy + sl[2 * PB + ga]);
         b1[q] = acc * dv;
       }
@@ -360,7 +374,7 @@ __global__ void __launch_bounds__(512) fdm_kernel(int64_t E, int NE, const int* 
       const int al = ql % PB, be = ql / PB;
 #pragma unroll
       for (int ga = 0; ga < PB; ++ga) v[ga] = b1[al + PB * (be + PB * ga)];
-#pragma unroll
+#pragma unroll OUT_UNR
       for (int cc = 0; cc < NC; ++cc) {
         const int c = C0 + cc;
         b0[al + PB * (be + PB * c)] = dot_row<PB, PBP>(SRz + c * PBP, v);
@@ -376,7 +390,7 @@ __global__ void __launch_bounds__(512) fdm_kernel(int64_t E, int NE, const int* 
       T* b1e = B1(le2);
 #pragma unroll
       for (int be = 0; be < PB; ++be) v[be] = b0e[al + PB * (be + PB * c)];
-#pragma unroll
+#pragma unroll OUT_UNR
       for (int bb = 0; bb < NC; ++bb) {
         const int b = C0 + bb;
         b1e[al + PB * (b + PB * c)] = dot_row<PB, PBP>(SRy + b * PBP, v);
@@ -392,7 +406,7 @@ __global__ void __launch_bounds__(512) fdm_kernel(int64_t E, int NE, const int* 
       const int64_t e = e0 + le3;
 #pragma unroll
       for (int al = 0; al < PB; ++al) v[al] = b1e[al + PB * (b + PB * c)];
-#pragma unroll
+#pragma unroll OUT_UNR
       for (int aa = 0; aa < NC; ++aa) {
         const int a = C0 + aa;
         const T acc = dot_row<PB, PBP>(SRx + a * PBP, v);
@@ -836,11 +850,24 @@ static int launch_fdm(const Level& lv, const T* in, const T* S, const T* lam, T*
   return SE_OK;
 }
 
-// df64 arithmetic on FP64 vectors: the FP64 kernel's layout and launch shape (df64 values are
-// 8 bytes, as FP64 ones), its S and Lambda from the df64 copies.
+// df64 arithmetic on FP64 vectors: the FP64 kernel's layout (df64 values are 8 bytes, as FP64
+// ones), its S and Lambda from the df64 copies.  Fewer elements per block than FP64 (measured
+// on GB300 at 32^3 elements: p = 7 3 elements, 1.31 ms against 1.47 ms with FP64's 4; p = 5 3;
+// p = 3 6), unless a tile is set for FP64.
+static int fdm_df_elems_per_block(int p) {
+  if (tile_get(p, false).fdm_ne > 0) return fdm_elems_per_block(p, false);
+  switch (p) {
+    case 1: return 16;
+    case 3: return 6;
+    case 5: return 3;
+    case 7: return 3;
+    default: return 2;
+  }
+}
+
 template <int P, int MODE>
 static int launch_fdm_df(const Level& lv, const double* in, double* out, cudaStream_t s) {
-  const int NE = fdm_elems_per_block(P, false);
+  const int NE = fdm_df_elems_per_block(P);
   const int threads = fdm_block_threads(P, false, NE);
   const size_t smem = fdm_smem_bytes(P, false, NE);
   const unsigned blocks = (unsigned)((lv.E + NE - 1) / NE);
