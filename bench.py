@@ -404,7 +404,9 @@ def run_batch(args):
         total_dof += info.n_dof
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
-    B = se.se_batch_create([(m, P32, b, x) for (m, P32, P64, b, x, info) in probs], tol=1e-8, maxit=500)
+    op_df = 1 if args.operator_df64 else 0
+    B = se.se_batch_create([(m, P32, b, x) for (m, P32, P64, b, x, info) in probs], tol=1e-8, maxit=500,
+                           operator_df64=op_df)
     stream = torch.cuda.current_stream()
 
     def batch_step():
@@ -445,7 +447,7 @@ def run_batch(args):
         "metric": "batched Poisson solves: total time & aggregate GDOF/s", "value": round(total_dof / (ms * 1e-3) / 1e9, 4),
         "unit": "GDOF/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(ms, 2), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 V-cycle / f64 Krylov", "data": "synthetic",
+        "dtype": "f32 V-cycle / f64 Krylov" + (" (df64 operator)" if op_df else ""), "data": "synthetic",
         "config": {"workload": f"{len(probs)} problems, E in {{8^3..24^3}}, p in {{3,5,7,9}}, "
                                f"n total {total_dof}, Cheby-RAS(2) pMG, FPCG tol 1e-8, one graph launch",
                    "iterations_min_max": [min(its), max(its)], "worst_rel_residual": worst,
@@ -462,10 +464,10 @@ def run_batch(args):
 SERVE_SCHEDULES = {5: (5, 3, 1), 7: (7, 3, 1), 9: (9, 5, 1)}
 
 
-def serve_stream(se, reqs, budget, slots, precision, t_scale=1.0, proj=0):
+def serve_stream(se, reqs, budget, slots, precision, t_scale=1.0, proj=0, op_df=0):
     """Submit `reqs` at their (scaled) arrival times, wait for all, return the server summary."""
     import workloads as wl
-    S = se.se_serve_create(budget, slots, proj_vectors=proj)
+    S = se.se_serve_create(budget, slots, proj_vectors=proj, operator_df64=op_df)
     tickets, keep = [], []
     refused = 0
     t0 = time.perf_counter()
@@ -476,7 +478,8 @@ def serve_stream(se, reqs, budget, slots, precision, t_scale=1.0, proj=0):
         m = r["mesh"]
         md = se.mesh_desc(m["nel"], m["p"], perturb_frac=m["perturb_frac"], seed=m["seed"],
                           deform_amp=wl.DEFORM_AMP)
-        pd = se.pmg_desc(SERVE_SCHEDULES[m["p"]], se.SE_SMOOTH_RAS, 2, precision=precision)
+        pd = se.pmg_desc(SERVE_SCHEDULES[m["p"]], se.SE_SMOOTH_RAS, 2, precision=precision,
+                         arnoldi_df64=op_df)
         modes, amp = wl.request_modes(r["rhs_seed"])
         key = hash((tuple(m["nel"]), m["p"], m["seed"])) & ((1 << 63) - 1)
         q = se.make_request(md, key, pd, modes=modes, amplitude=amp, tol=1e-8)
@@ -518,16 +521,19 @@ def run_serve(args):
     budget = int(0.8 * free)
     reqs = wl.serve_requests(n=args.serve, rate=args.rate, seed=0)
     with ClockSampler(0) as clk:
-        served = serve_stream(se, reqs, budget, args.slots, se.SE_FP32, proj=args.proj)
+        served = serve_stream(se, reqs, budget, args.slots, se.SE_FP32, proj=args.proj,
+                              op_df=1 if args.operator_df64 else 0)
     low = None
     if args.low_rate > 0:  # the same kind of stream at a rate below capacity: latency unqueued
         low_reqs = wl.serve_requests(n=args.low_n, rate=args.low_rate, seed=1)
-        low = serve_stream(se, low_reqs, budget, args.slots, se.SE_FP32, proj=args.proj)
+        low = serve_stream(se, low_reqs, budget, args.slots, se.SE_FP32, proj=args.proj,
+                           op_df=1 if args.operator_df64 else 0)
         low["rate"] = args.low_rate
     base_reqs = reqs[:args.serve_baseline] if args.serve_baseline else reqs
     serial = serve_stream(se, base_reqs, budget, 1, se.SE_FP64)
     out = {"metric": "served Poisson solves: solves/s, p50/p99 latency", "value": served["solves_per_s"],
-           "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32 V-cycle / f64 Krylov",
+           "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
+           "dtype": "f32 V-cycle / f64 Krylov" + (" (df64 operator)" if args.operator_df64 else ""),
            "data": "synthetic",
            "config": {"workload": f"{len(reqs)} requests, Poisson arrivals at {args.rate}/s, E log-uniform "
                                   f"[512, 65536], p in {{5,7,9}}, 30% resident-mesh reuse, tol 1e-8",
@@ -773,7 +779,8 @@ def main():
     ap.add_argument("--precond-fp32", action="store_true")
     ap.add_argument("--df64", action="store_true",
                     help="SE_DF64 preconditioner and df64 outer operator (FP64 vectors)")
-    ap.add_argument("--operator-df64", action="store_true", help="df64 outer operator only")
+    ap.add_argument("--operator-df64", action="store_true",
+                    help="df64 outer operator (solve, batch, serve); serve: also df64 Arnoldi set-up")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-timeout", type=float, default=240.0)
     ap.add_argument("--batch", type=int, default=0, help="run the batched workload of N problems")

@@ -137,6 +137,10 @@ typedef struct se_pmg_desc {
   int precision;                 /* SE_FP64; SE_FP32 for the whole V-cycle except the coarse
                                     solve (Arnoldi and coarse solve stay FP64); SE_DF64: FP64
                                     vectors, operator and FDM kernels in double-float */
+  int arnoldi_df64;              /* 1: the Arnoldi rounds of an SE_FP64 or SE_FP32 preconditioner
+                                    apply the operator and FDM kernels in double-float (FP64
+                                    vectors; odd orders; df64 copies of the level data exist
+                                    only during the set-up).  SE_DF64 always does. */
 } se_pmg_desc;
 
 /* Builds the levels (each rediscretised on the same mapped mesh), Jacobi diagonals, FDM
@@ -349,6 +353,8 @@ typedef struct se_serve_cfg {
                               projection space of that many prior solutions (se_proj_*), a
                               request on it starts from the projected guess and stops when
                               ||r|| <= tol ||b|| (counted in the footprint) */
+  int operator_df64;       /* 1: outer operators of odd-order meshes compute in double-float
+                              (df64 copies of the geometry, 48 bytes per point, counted) */
 } se_serve_cfg;
 typedef struct se_serve_stats {
   int64_t submitted, completed, refused, failed, pending;

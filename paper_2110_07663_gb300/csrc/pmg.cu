@@ -258,6 +258,48 @@ static int arnoldi_level(se_pmg_s* P, int l, cudaStream_t s, double* lam_out) {
 }
 
 // ------------------------------------------------------------------ set-up
+// df64 arithmetic for the Arnoldi rounds of an FP64 or FP32 preconditioner: df64 copies of the
+// smoothed levels' geometry and FDM factors live only while the bounds are estimated (copies
+// the mesh already holds for its outer operator are used as they are).
+static int df_transient(const double* src, df64** dst, int64_t n, cudaStream_t s,
+                        std::vector<void*>& keep) {
+  void* p = nullptr;
+  SE_TRY(dmalloc_transient(&p, (size_t)n * sizeof(df64), s));
+  keep.push_back(p);
+  *dst = static_cast<df64*>(p);
+  return split_df(src, *dst, n, s);
+}
+
+static int arnoldi_df_begin(se_pmg_s* P, cudaStream_t s, std::vector<void*>& keep) {
+  for (int l = 0; l + 1 < P->nlev; ++l) {
+    Level& lv = *P->lv[l];
+    if (!ax_eo_supported(lv.p) || !lv.eo64) continue;
+    const int H = lv.N / 2, PB = lv.p + 3;
+    if (!lv.Gdf) SE_TRY(df_transient(lv.G64, &lv.Gdf, 6 * lv.L, s, keep));
+    if (!lv.eodf) SE_TRY(df_transient(lv.eo64, &lv.eodf, 4 * H * H, s, keep));
+    if (lv.S64 && !lv.Sdf) {
+      SE_TRY(df_transient(lv.S64, &lv.Sdf, 3 * lv.E * PB * PB, s, keep));
+      SE_TRY(df_transient(lv.lam64, &lv.lamdf, 3 * lv.E * PB, s, keep));
+    }
+    lv.df = true;
+  }
+  return SE_OK;
+}
+
+static void arnoldi_df_end(se_pmg_s* P, cudaStream_t s, std::vector<void*>& keep) {
+  auto owned = [&](void* p) { return std::find(keep.begin(), keep.end(), p) != keep.end(); };
+  for (int l = 0; l + 1 < P->nlev; ++l) {
+    Level& lv = *P->lv[l];
+    lv.df = false;
+    if (owned(lv.Gdf)) lv.Gdf = nullptr;
+    if (owned(lv.eodf)) lv.eodf = nullptr;
+    if (owned(lv.Sdf)) lv.Sdf = nullptr;
+    if (owned(lv.lamdf)) lv.lamdf = nullptr;
+  }
+  for (void* p : keep) cudaFreeAsync(p, s);
+  keep.clear();
+}
+
 template <class T>
 static int alloc_vecs(se_pmg_s* P, int l) {
   LevelVecs<T>& V = P->vecs<T>(l);
@@ -318,14 +360,26 @@ static int pmg_build(se_pmg_s* P) {
     else SE_TRY(alloc_vecs<double>(P, l));
   }
   // the coarse level always solves in FP64 from the V-cycle's precision; Arnoldi needs FP64
+  // vectors (and FP64 or df64 arithmetic)
+  std::vector<void*> transient;
+  if (!df && d.arnoldi_df64) {
+    const int rb = arnoldi_df_begin(P, s, transient);
+    if (rb != SE_OK) {
+      arnoldi_df_end(P, s, transient);
+      return rb;
+    }
+  }
   SE_CUDA(cudaStreamSynchronize(s));
-  for (int l = 0; l + 1 < P->nlev; ++l) {
+  int rc = SE_OK;
+  for (int l = 0; l + 1 < P->nlev && rc == SE_OK; ++l) {
     double lam = 0.0;
-    SE_TRY(arnoldi_level(P, l, s, &lam));
+    rc = arnoldi_level(P, l, s, &lam);
     P->lam[l] = lam;
     P->lmin[l] = d.eig_lo * lam;
     P->lmax[l] = d.eig_hi * lam;
   }
+  if (!df && d.arnoldi_df64) arnoldi_df_end(P, s, transient);
+  SE_TRY(rc);
   SE_CUDA(cudaStreamSynchronize(s));
   return SE_OK;
 }
@@ -373,6 +427,7 @@ int se_pmg_setup(se_mesh_t m, const se_pmg_desc* desc, se_pmg_t* out) {
   SE_CHECK(d.coarse_tol > 0 && d.coarse_maxit >= 1, SE_EINVAL, "se_pmg_setup: coarse tolerance");
   SE_CHECK(d.precision == SE_FP64 || d.precision == SE_FP32 || d.precision == SE_DF64, SE_EINVAL,
            "se_pmg_setup: precision");
+  SE_CHECK(d.arnoldi_df64 == 0 || d.arnoldi_df64 == 1, SE_EINVAL, "se_pmg_setup: arnoldi_df64");
   static std::atomic<uint64_t> next_uid{0};
   auto* P = new se_pmg_s();
   P->mesh = m;

@@ -77,6 +77,7 @@ struct Resident {
   bool busy = false;
   double last_used = 0.0;
   int64_t L = 0;
+  int op_df = 0;               // outer operator in df64 (server option, odd p)
 };
 
 struct Ticket {
@@ -150,10 +151,12 @@ static bool make_room(se_server_s* S, size_t need) {
 static size_t need_bytes(const se_server_s* S, const se_request& q) {
   const double L = (double)q.mesh.nel[0] * q.mesh.nel[1] * q.mesh.nel[2] * (q.mesh.p + 1) *
                    (q.mesh.p + 1) * (q.mesh.p + 1);
-  return footprint_bytes(q.mesh, q.pmg) + (size_t)(2.0 * S->cfg.proj_vectors * L * sizeof(double));
+  const bool df = S->cfg.operator_df64 && ax_eo_supported(q.mesh.p);
+  return footprint_bytes(q.mesh, q.pmg) + (size_t)(2.0 * S->cfg.proj_vectors * L * sizeof(double)) +
+         (size_t)(df ? 6.0 * L * sizeof(df64) : 0.0);
 }
 
-static int build_resident(const se_request& q, int proj_vectors, Resident** out) {
+static int build_resident(const se_request& q, int proj_vectors, int op_df, Resident** out) {
   se_mesh_desc d = q.mesh;
   d.flags |= SE_MESH_NONBLOCKING_STREAM;
   auto* r = new Resident();
@@ -169,6 +172,10 @@ static int build_resident(const se_request& q, int proj_vectors, Resident** out)
     }
   }
   if (rc == SE_OK && proj_vectors > 0) rc = se_proj_create(r->m, proj_vectors, &r->proj);
+  if (rc == SE_OK && op_df && ax_eo_supported(r->m->fine.p)) {
+    rc = make_df_geometry(r->m->fine, r->m->allocs, r->m->stream);
+    r->op_df = 1;
+  }
   if (rc != SE_OK) {
     destroy_resident(r);
     return rc;
@@ -197,7 +204,7 @@ static int start_ticket(Ticket* t) {
     SE_CUDA(cudaMemsetAsync(r->x, 0, r->L * sizeof(double), s));
   }
   SE_TRY(graph_solve_launch(r->m, r->P, r->b, r->x, t->req.tol, t->req.maxit, s,
-                            r->proj ? SE_TOL_B : SE_TOL_R0));
+                            r->proj ? SE_TOL_B : SE_TOL_R0, r->op_df));
   if (!t->ev) SE_CUDA(cudaEventCreateWithFlags(&t->ev, cudaEventDisableTiming));
   SE_CUDA(cudaEventRecord(t->ev, s));
   return SE_OK;
@@ -317,7 +324,7 @@ static void builder(se_server_s* S) {
     lk.unlock();
     const double tb = now_ms();
     Resident* r = nullptr;
-    int rc = build_resident(t->req, S->cfg.proj_vectors, &r);
+    int rc = build_resident(t->req, S->cfg.proj_vectors, S->cfg.operator_df64, &r);
     t->setup_ms = now_ms() - tb;
     if (rc == SE_OK) {
       // not yet visible to the scheduler: its first solve starts outside the lock
@@ -369,6 +376,8 @@ int se_serve_create(const se_serve_cfg* cfg, se_server_t* out) {
   SE_CHECK(cfg->builders >= 0 && cfg->builders <= 64, SE_EINVAL, "se_serve_create: builders");
   SE_CHECK(cfg->proj_vectors >= 0 && cfg->proj_vectors <= 16, SE_EINVAL,
            "se_serve_create: proj_vectors");
+  SE_CHECK(cfg->operator_df64 == 0 || cfg->operator_df64 == 1, SE_EINVAL,
+           "se_serve_create: operator_df64");
   SE_CHECK(cfg->hbm_budget > 0, SE_EINVAL, "se_serve_create: hbm_budget");
   auto* S = new se_server_s();
   S->cfg = *cfg;

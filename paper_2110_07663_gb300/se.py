@@ -53,7 +53,8 @@ class se_pmg_desc(C.Structure):
     _fields_ = [("nlev", C.c_int), ("schedule", C.c_int * SE_MAX_LEVELS), ("smoother", C.c_int),
                 ("cheb_order", C.c_int * SE_MAX_LEVELS), ("eig_lo", C.c_double),
                 ("eig_hi", C.c_double), ("arnoldi_steps", C.c_int), ("seed", C.c_uint64),
-                ("coarse_tol", C.c_double), ("coarse_maxit", C.c_int), ("precision", C.c_int)]
+                ("coarse_tol", C.c_double), ("coarse_maxit", C.c_int), ("precision", C.c_int),
+                ("arnoldi_df64", C.c_int)]
 
 
 class se_solve_opts(C.Structure):
@@ -86,7 +87,7 @@ class se_result(C.Structure):
 
 class se_serve_cfg(C.Structure):
     _fields_ = [("hbm_budget", C.c_size_t), ("max_slots", C.c_int), ("builders", C.c_int),
-                ("proj_vectors", C.c_int)]
+                ("proj_vectors", C.c_int), ("operator_df64", C.c_int)]
 
 
 class se_serve_summary(C.Structure):
@@ -271,7 +272,8 @@ def se_jacobi_diag(m, d, stream=None):
 
 # ----------------------------------------------------------------------------- p-multigrid
 def pmg_desc(schedule, smoother=SE_SMOOTH_RAS, cheb_order=2, eig_lo=0.1, eig_hi=1.1,
-             arnoldi_steps=10, seed=0, coarse_tol=1e-4, coarse_maxit=500, precision=SE_FP64):
+             arnoldi_steps=10, seed=0, coarse_tol=1e-4, coarse_maxit=500, precision=SE_FP64,
+             arnoldi_df64=0):
     d = se_pmg_desc()
     d.nlev = len(schedule)
     d.schedule[:len(schedule)] = list(schedule)
@@ -283,6 +285,7 @@ def pmg_desc(schedule, smoother=SE_SMOOTH_RAS, cheb_order=2, eig_lo=0.1, eig_hi=
     d.seed = seed
     d.coarse_tol, d.coarse_maxit = coarse_tol, coarse_maxit
     d.precision = precision
+    d.arnoldi_df64 = arnoldi_df64
     return d
 
 
@@ -414,11 +417,13 @@ def _opts(tol, maxit, stream, method=SE_FPCG, restart=20, graph_capture=1, tol_n
     return o
 
 
-def se_batch_create(problems, tol=1e-8, maxit=1000, stream=None):
+def se_batch_create(problems, tol=1e-8, maxit=1000, stream=None, operator_df64=0):
     """problems: list of (mesh, pmg or None, b, x).  Returns the batch handle."""
     arr = _problems(problems)
     h = _vp()
-    _check(lib.se_batch_create(len(problems), arr, C.byref(_opts(tol, maxit, stream)), C.byref(h)))
+    o = _opts(tol, maxit, stream)
+    o.operator_df64 = operator_df64
+    _check(lib.se_batch_create(len(problems), arr, C.byref(o), C.byref(h)))
     return h.value
 
 
@@ -496,10 +501,11 @@ def make_request(mdesc, mesh_key, pdesc, modes=(1, 1, 1), amplitude=1.0, b_host=
     return q
 
 
-def se_serve_create(hbm_budget, max_slots, builders=0, proj_vectors=0):
+def se_serve_create(hbm_budget, max_slots, builders=0, proj_vectors=0, operator_df64=0):
     c = se_serve_cfg()
     c.hbm_budget, c.max_slots, c.builders = int(hbm_budget), int(max_slots), int(builders)
     c.proj_vectors = int(proj_vectors)
+    c.operator_df64 = int(operator_df64)
     h = _vp()
     _check(lib.se_serve_create(C.byref(c), C.byref(h)))
     return h.value

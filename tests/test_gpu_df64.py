@@ -123,3 +123,60 @@ def test_df64_solve_parity(smoother, method):
     finally:
         se.se_pmg_destroy(P)
         c.close()
+
+
+def test_df64_operator_in_a_batch_equals_each_solve_alone():
+    """Batched graph solves with the df64 outer operator: each problem bit for bit as its own graph
+    solve with the same options, and within the tolerance of the FP64-operator solve."""
+    from tests.gpu_common import gpu
+    torch, se = gpu()
+    probs = []
+    try:
+        for nel, p, sched, seed in [((3, 3, 2), 5, (5, 3, 1), 1), ((2, 3, 3), 7, (7, 3, 1), 2)]:
+            c = Case(nel, p, seed=seed)
+            P = se.se_pmg_setup(c.m, se.pmg_desc(sched, se.SE_SMOOTH_RAS, 2, precision=se.SE_FP32))
+            probs.append((c, P, gpu_rhs(c), c.empty().zero_()))
+        B = se.se_batch_create([(c.m, P, b, x) for c, P, b, x in probs], tol=1e-8, maxit=200,
+                               operator_df64=1)
+        se.se_batch_run(B)
+        torch.cuda.synchronize()
+        se.se_batch_destroy(B)
+        for c, P, b, x in probs:
+            xa = c.empty().zero_()
+            st = se.se_solve(c.m, P, b, xa, tol=1e-8, graph_capture=1, operator_df64=1)
+            assert torch.equal(xa, x)
+            x64 = c.empty().zero_()
+            st64 = se.se_solve(c.m, P, b, x64, tol=1e-8)
+            assert abs(st.iterations - st64.iterations) <= 1
+            assert rel_err(c.to_np(x), c.to_np(x64)) <= 1e-6
+    finally:
+        for c, P, b, x in probs:
+            se.se_pmg_destroy(P)
+            c.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_arnoldi_in_df64_gives_the_same_bounds(precision):
+    """arnoldi_df64: the eigenvalue estimate of an FP64 or FP32 preconditioner with df64 operator
+    and FDM arithmetic agrees with the FP64 one and the oracle's to 1e-9 (the df64 copies are
+    set-up transients); the V-cycle itself is unchanged: bit for bit the same as without."""
+    c = Case((3, 2, 3), 7, seed=4)
+    se = c.se
+    sched = (7, 3, 1)
+    P0 = se.se_pmg_setup(c.m, se.pmg_desc(sched, se.SE_SMOOTH_RAS, 2, precision=precision))
+    P1 = se.se_pmg_setup(c.m, se.pmg_desc(sched, se.SE_SMOOTH_RAS, 2, precision=precision,
+                                          arnoldi_df64=1))
+    pmg = o.pmg_setup(c.V, c.nel, sched, smoother="ras", order=2, amp=c.amp)
+    try:
+        for l in range(len(sched) - 1):
+            l0, l1 = se.se_pmg_lambda(P0, l), se.se_pmg_lambda(P1, l)
+            assert abs(l1 - l0) <= 1e-11 * l0 and abs(l1 - pmg.lam[l]) <= 1e-9 * pmg.lam[l]
+        r = c.to_gpu(c.random_continuous(12))
+        z0, z1 = c.empty(), c.empty()
+        se.se_pmg_smooth(P0, 0, r, z0)
+        se.se_pmg_smooth(P1, 0, r, z1)
+        assert c.torch.equal(z0, z1)
+    finally:
+        se.se_pmg_destroy(P0)
+        se.se_pmg_destroy(P1)
+        c.close()

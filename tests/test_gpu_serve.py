@@ -22,8 +22,8 @@ def stream_specs():
     return [(meshes[k], k, ((i % 3) + 1, (i % 2) + 1, 1), 0.5 + 0.1 * i) for i, k in enumerate(order)]
 
 
-def run_stream(se, specs, slots, precision, budget=32 << 30, serial=False):
-    S = se.se_serve_create(budget, slots)
+def run_stream(se, specs, slots, precision, budget=32 << 30, serial=False, op_df=0):
+    S = se.se_serve_create(budget, slots, operator_df64=op_df)
     try:
         xs, tickets, keep = [], [], []
         for (nel, p, seed), key, modes, amp in specs:
@@ -44,12 +44,13 @@ def run_stream(se, specs, slots, precision, budget=32 << 30, serial=False):
         se.se_serve_destroy(S)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_same_alone_and_in_the_mix(precision):
+@pytest.mark.parametrize("precision,op_df", [(0, 0), (1, 0), (1, 1)])
+def test_same_alone_and_in_the_mix(precision, op_df):
+    """op_df = 1: the outer operators in df64 (the p = 3, 5, 7 meshes all have df64 kernels)."""
     torch, se = gpu()
     specs = stream_specs()
-    x_mix, r_mix, st = run_stream(se, specs, slots=4, precision=precision)
-    x_one, r_one, _ = run_stream(se, specs, slots=1, precision=precision, serial=True)
+    x_mix, r_mix, st = run_stream(se, specs, slots=4, precision=precision, op_df=op_df)
+    x_one, r_one, _ = run_stream(se, specs, slots=1, precision=precision, serial=True, op_df=op_df)
     for a, b, ra, rb in zip(x_mix, x_one, r_mix, r_one):
         assert ra.status == 0 and rb.status == 0
         assert ra.rel_residual <= 1e-8 and ra.iterations == rb.iterations
