@@ -49,8 +49,11 @@ enum se_status {
 enum { SE_BC_DIRICHLET = 0, SE_BC_NEUMANN = 1 };
 /* Arithmetic of a preconditioner (se_pmg_desc.precision).  SE_DF64: FP64 vectors throughout, the
  * operator and FDM kernels of the smoothed levels (odd orders) compute in double-float
- * arithmetic on the FP32 pipe (pairs of FP32 values, about 48 significant bits); even orders
- * fall back to FP64 arithmetic. */
+ * arithmetic on the FP32 pipe (pairs of FP32 values, about 47-48 significant bits); even orders
+ * fall back to FP64 arithmetic.  Every df64 path (SE_DF64, SE_AX_DF64, operator_df64,
+ * arnoldi_df64) takes operands of magnitude in [2^-103, 2^128) (about 1e-31 to 3e38) at that
+ * accuracy; smaller values keep FP32 accuracy relative to themselves (below 2^-126 they are
+ * zero) and larger ones overflow, so a problem scaled outside that range needs FP64. */
 enum { SE_FP64 = 0, SE_FP32 = 1, SE_DF64 = 2 };
 enum { SE_SMOOTH_JACOBI = 0, SE_SMOOTH_RAS = 1, SE_SMOOTH_ASM = 2 };
 enum { SE_FPCG = 0, SE_FGMRES = 1 };

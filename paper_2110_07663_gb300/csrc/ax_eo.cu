@@ -58,12 +58,13 @@ __device__ __forceinline__ void eo_apply(const T* __restrict__ Ep, const T* __re
     }
 #pragma unroll 1
     for (int k = 0; k < H; ++k) {
-      T E = Ep[k * H] * e[0], O = Om[k * H] * o[0];
+      df_acc AE, AO;
 #pragma unroll
-      for (int l = 1; l < H; ++l) {
-        E = fma(Ep[k * H + l], e[l], E);
-        O = fma(Om[k * H + l], o[l], O);
+      for (int l = 0; l < H; ++l) {
+        df_acc_fma(AE, Ep[k * H + l], e[l]);
+        df_acc_fma(AO, Om[k * H + l], o[l]);
       }
+      const T E = df_acc_value(AE), O = df_acc_value(AO);
       T* d0 = dst + base + stride * k;
       T* d1 = dst + base + stride * (N - 1 - k);
       if constexpr (ACC) {

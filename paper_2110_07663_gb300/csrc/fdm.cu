@@ -230,16 +230,19 @@ __device__ __forceinline__ T dot_row(const T* __restrict__ row, const T (&v)[PBP
       acc = fmaf(s.w, v[a + 3], acc);
     }
   } else if constexpr (is_df64<T>::value) {
-    // two independent accumulation chains (a df64 FMA is a chain of about 13 dependent FP32
-    // operations, so one chain per row would leave the FP32 pipe waiting on latency)
-    T acc1 = T(0.0);
+    // two independent accumulation chains (a df64 product-accumulate is a chain of about 10
+    // dependent FP32 operations, so one chain per row would leave the FP32 pipe waiting on
+    // latency), renormalised once at the end
+    df_acc A0, A1;
 #pragma unroll
     for (int a = 0; a + 1 < PB; a += 2) {
-      acc = fma(row[a], v[a], acc);
-      acc1 = fma(row[a + 1], v[a + 1], acc1);
+      // rows are padded to PBP (a multiple of 4) entries: two df64 values per 16-byte load
+      const float4 q = *reinterpret_cast<const float4*>(row + a);
+      df_acc_fma(A0, df64(q.x, q.y), v[a]);
+      df_acc_fma(A1, df64(q.z, q.w), v[a + 1]);
     }
-    if constexpr (PB % 2 == 1) acc = fma(row[PB - 1], v[PB - 1], acc);
-    acc = acc + acc1;
+    if constexpr (PB % 2 == 1) df_acc_fma(A0, row[PB - 1], v[PB - 1]);
+    acc = df_acc_merge(A0, A1);
   } else {
 #pragma unroll
     for (int a = 0; a < PB; ++a) acc = fma(row[a], v[a], acc);

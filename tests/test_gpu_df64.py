@@ -180,3 +180,20 @@ def test_arnoldi_in_df64_gives_the_same_bounds(precision):
         se.se_pmg_destroy(P0)
         se.se_pmg_destroy(P1)
         c.close()
+
+
+@pytest.mark.parametrize("scale", [2.0 ** -70, 2.0 ** -30, 1.0, 2.0 ** 40])
+def test_df64_operator_across_the_supported_range(scale):
+    """Inputs anywhere in the df64 range (|u| in [2^-103, 2^128), operator output within it too)
+    keep the FP64 bar; exact zeros (the Dirichlet copies of a masked vector) stay exact."""
+    c = Case((3, 2, 2), 5, seed=21)
+    se = c.se
+    try:
+        u = c.random_continuous(3) * scale
+        y = c.empty()
+        se.se_ax(c.m, c.to_gpu(u), y, se.SE_AX_ASSEMBLE | se.SE_AX_MASK | se.SE_AX_DF64)
+        ref = o.ax(c.lv, u)
+        assert rel_err(c.to_np(y), ref) <= 1e-12
+        assert (c.to_np(y)[c.lv.mask == 0] == 0).all()
+    finally:
+        c.close()
