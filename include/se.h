@@ -48,9 +48,9 @@ enum se_status {
 
 enum { SE_BC_DIRICHLET = 0, SE_BC_NEUMANN = 1 };
 /* Arithmetic of a preconditioner (se_pmg_desc.precision).  SE_DF64: FP64 vectors throughout, the
- * operator and FDM kernels of the smoothed levels (odd orders) compute in double-float
- * arithmetic on the FP32 pipe (pairs of FP32 values, about 47-48 significant bits); even orders
- * fall back to FP64 arithmetic.  Every df64 path (SE_DF64, SE_AX_DF64, operator_df64,
+ * operator and FDM kernels of the smoothed levels compute in double-float arithmetic on the FP32
+ * pipe (pairs of FP32 values, about 47-48 significant bits; odd orders use the even-odd folded
+ * operator, even orders the plain sum factorisation).  Every df64 path (SE_DF64, SE_AX_DF64, operator_df64,
  * arnoldi_df64) takes operands of magnitude in [2^-103, 2^128) (about 1e-31 to 3e38) at that
  * accuracy; smaller values keep FP32 accuracy relative to themselves (below 2^-126 they are
  * zero) and larger ones overflow, so a problem scaled outside that range needs FP64. */
@@ -111,7 +111,7 @@ int se_mesh_rhs(se_mesh_t m, const double* f_dev, double* b_dev, void* stream);
 /* ---------------------------------------------------------------- operator (Sec. 2.1) */
 /* y = [M] [QQ^T] A_L [M] u.  flags: SE_AX_ASSEMBLE applies QQ^T (direct stiffness
  * summation), SE_AX_MASK zeroes Dirichlet nodes of input and output, SE_AX_FP32 computes in
- * FP32, SE_AX_DF64 in double-float arithmetic (odd p only; SE_EINVAL otherwise; the first call
+ * FP32, SE_AX_DF64 in double-float arithmetic (the first call
  * allocates df64 copies of the geometric factors, 6 L x 8 bytes, owned by the mesh); inputs and
  * outputs stay FP64.  A_L is applied by tensor-product sum factorisation
  * (Sec. 1: ~7E(p+1)^3 reads, 12E(p+1)^4 operations).  u and y must not overlap. */
@@ -142,7 +142,7 @@ typedef struct se_pmg_desc {
                                     vectors, operator and FDM kernels in double-float */
   int arnoldi_df64;              /* 1: the Arnoldi rounds of an SE_FP64 or SE_FP32 preconditioner
                                     apply the operator and FDM kernels in double-float (FP64
-                                    vectors; odd orders; df64 copies of the level data exist
+                                    vectors; df64 copies of the level data exist
                                     only during the set-up).  SE_DF64 always does. */
 } se_pmg_desc;
 
@@ -210,8 +210,8 @@ typedef struct se_solve_opts {
   int tol_norm;      /* SE_TOL_R0 (0): stop when ||r_k|| <= tol ||r_0||; SE_TOL_B (1): when
                         ||r_k|| <= tol ||b|| (for an initial guess from se_proj_guess: the same
                         accuracy whatever the guess; 0 iterations if the guess already meets it) */
-  int operator_df64; /* 1: the outer operator A x computes in double-float arithmetic (odd p;
-                        FP64 otherwise), as se_ax with SE_AX_DF64 */
+  int operator_df64; /* 1: the outer operator A x computes in double-float arithmetic, as se_ax
+                        with SE_AX_DF64 */
 } se_solve_opts;
 enum { SE_TOL_R0 = 0, SE_TOL_B = 1 };
 
@@ -356,7 +356,7 @@ typedef struct se_serve_cfg {
                               projection space of that many prior solutions (se_proj_*), a
                               request on it starts from the projected guess and stops when
                               ||r|| <= tol ||b|| (counted in the footprint) */
-  int operator_df64;       /* 1: outer operators of odd-order meshes compute in double-float
+  int operator_df64;       /* 1: outer operators of resident meshes compute in double-float
                               (df64 copies of the geometry, 48 bytes per point, counted) */
 } se_serve_cfg;
 typedef struct se_serve_stats {

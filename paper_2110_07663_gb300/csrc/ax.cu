@@ -9,14 +9,15 @@ namespace se {
 //   ur = D_r u, us = D_s u, ut = D_t u         (the t contraction runs in registers)
 //   (wr, ws, wt) = G (ur, us, ut), G symmetric with 6 stored factors per point
 //   y = D_r^T wr + D_s^T ws + D_t^T wt         (the t part accumulates in registers)
-// 12N+15 flops per point; reads u and G (7 values) and writes y once.
-template <int N, typename T>
-__global__ void __launch_bounds__(512) ax_local_kernel(int64_t E, int NE, const T* __restrict__ u,
+// 12N+15 flops per point; reads u and G (7 values) and writes y once.  T is the arithmetic type,
+// IO the type of u, y and sub in memory (T, or double for T = df64).
+template <int N, typename T, typename IO = T>
+__global__ void __launch_bounds__(512) ax_local_kernel(int64_t E, int NE, const IO* __restrict__ u,
                                                        const T* __restrict__ G, int64_t L,
                                                        const T* __restrict__ Dg,
-                                                       T* __restrict__ y,
+                                                       IO* __restrict__ y,
                                                        const uint8_t* __restrict__ pflag,
-                                                       bool mask_in, const T* __restrict__ sub) {
+                                                       bool mask_in, const IO* __restrict__ sub) {
   constexpr int N2 = N * N, N3 = N * N * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sD = reinterpret_cast<T*>(smem_raw);
@@ -35,7 +36,7 @@ __global__ void __launch_bounds__(512) ax_local_kernel(int64_t E, int NE, const 
   for (int k = 0; k < N; ++k) {
     T v = T(0);
     if (valid) {
-      v = u[eb + ij + N2 * k];
+      v = from_io<T>(u[eb + ij + N2 * k]);
       if (mask_in && !(pflag[eb + ij + N2 * k] & PF_FREE)) v = T(0);
     }
     ru[k] = v;
@@ -96,7 +97,7 @@ __global__ void __launch_bounds__(512) ax_local_kernel(int64_t E, int NE, const 
       acc += Dci[l] * swr[l + N * j + N2 * k];
       acc += Dcj[l] * sws[i + N * l + N2 * k];
     }
-    if (valid) y[eb + ij + N2 * k] = ax_output(acc, sub, pflag, eb + ij + N2 * k);
+    if (valid) y[eb + ij + N2 * k] = ax_output(io_cast<IO>(acc), sub, pflag, eb + ij + N2 * k);
   }
 }
 
@@ -127,6 +128,36 @@ static int launch_ax(const Level& lv, const T* u, T* y, const T* G, const T* D, 
   return SE_OK;
 }
 
+// df64 arithmetic on FP64 vectors, odd N (even orders; even N uses the folded kernel).
+template <int N>
+static int launch_ax_df(const Level& lv, const double* u, double* y, const double* sub,
+                        cudaStream_t s) {
+  const int NE = ax_elems_per_block(N - 1, false);
+  const int threads = NE * N * N;
+  const size_t smem = (N * N + (size_t)NE * 3 * N * N * N) * sizeof(df64);
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      ax_local_kernel<N, df64, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  SE_CUDA(attr);
+  const unsigned blocks = (unsigned)((lv.E + NE - 1) / NE);
+  ax_local_kernel<N, df64, double><<<blocks, threads, smem, s>>>(lv.E, NE, u, lv.Gdf, lv.L, lv.Ddf, y,
+                                                                  lv.pflag, false, sub);
+  SE_LAUNCH_CHECK();
+  return SE_OK;
+}
+
+static int ax_local_generic_df(const Level& lv, const double* u, double* y, const double* sub,
+                               cudaStream_t s) {
+  SE_CHECK(lv.Gdf != nullptr && lv.Ddf != nullptr, SE_EINVAL, "ax_df: df64 geometry missing");
+  switch (lv.N) {
+    case 3: return launch_ax_df<3>(lv, u, y, sub, s);
+    case 5: return launch_ax_df<5>(lv, u, y, sub, s);
+    case 7: return launch_ax_df<7>(lv, u, y, sub, s);
+    case 9: return launch_ax_df<9>(lv, u, y, sub, s);
+    case 11: return launch_ax_df<11>(lv, u, y, sub, s);
+    default: set_error("ax_df: unsupported N=%d", lv.N); return SE_EINVAL;
+  }
+}
+
 template <class T>
 int ax_local(const Level& lv, const T* u, T* y, bool mask_in, cudaStream_t s, const T* sub) {
   const T* G;
@@ -148,7 +179,10 @@ int ax_local(const Level& lv, const T* u, T* y, bool mask_in, cudaStream_t s, co
   if constexpr (sizeof(T) == 4) {
     if (!mask_in && ax_tma_supported(lv.p)) return ax_local_tma(lv, u, y, s, sub);
   } else {
-    if (use_df) return ax_local_eo_df(lv, u, y, s, sub);
+    if (use_df) {
+      if (ax_eo_supported(lv.p)) return ax_local_eo_df(lv, u, y, s, sub);
+      return ax_local_generic_df(lv, u, y, sub, s);
+    }
     if (!mask_in && ax_eo_supported(lv.p) && lv.eo64) return ax_local_eo(lv, u, y, s, sub);
   }
   switch (N) {
@@ -430,7 +464,6 @@ int se_ax(se_mesh_t m, const double* u, double* y, int flags, void* stream) {
     return SE_OK;
   }
   if (flags & SE_AX_DF64) {
-    SE_CHECK(ax_eo_supported(lv.p), SE_EINVAL, "se_ax: SE_AX_DF64 needs an odd order (p=%d)", lv.p);
     SE_TRY(make_df_geometry(lv, m->allocs, s));
     Level ld = lv;
     ld.df = true;

@@ -219,15 +219,23 @@ int split_df(const double* a, df64* b, int64_t n, cudaStream_t s) {
 }
 
 int make_df_geometry(Level& lv, Allocs& allocs, cudaStream_t s) {
+  const bool eo = ax_eo_supported(lv.p) && lv.eo64;
+  if (lv.Gdf && (eo ? lv.eodf != nullptr : lv.Ddf != nullptr)) return SE_OK;
   if (!lv.Gdf) {
     SE_TRY(dmalloc(allocs, &lv.Gdf, 6 * (size_t)lv.L));
     SE_TRY(split_df(lv.G64, lv.Gdf, 6 * lv.L, s));
   }
-  if (!lv.eodf && ax_eo_supported(lv.p) && lv.eo64) {
+  if (eo && !lv.eodf) {
     const int H = lv.N / 2;
     SE_TRY(dmalloc(allocs, &lv.eodf, 4 * (size_t)H * H));
     SE_TRY(split_df(lv.eo64, lv.eodf, 4 * H * H, s));
   }
+  if (!eo && !lv.Ddf) {
+    SE_TRY(dmalloc(allocs, &lv.Ddf, (size_t)lv.N * lv.N));
+    SE_TRY(split_df(lv.D64, lv.Ddf, (int64_t)lv.N * lv.N, s));
+  }
+  // made once and then read from any stream: complete before the first use
+  SE_CUDA(cudaStreamSynchronize(s));
   return SE_OK;
 }
 

@@ -861,8 +861,11 @@ static int fdm_df_elems_per_block(int p) {
   if (tile_get(p, false).fdm_ne > 0) return fdm_elems_per_block(p, false);
   switch (p) {
     case 1: return 16;
+    case 2: return 10;
     case 3: return 6;
+    case 4: return 5;
     case 5: return 3;
+    case 6: return 3;
     case 7: return 3;
     default: return 2;
   }
@@ -899,7 +902,7 @@ static int dispatch_fdm(const Level& lv, const T* in, T* out, cudaStream_t s) {
   const double fl = 2.0 * (3.0 * PB * PB * PB * PB + PB * PB * PB * N + PB * PB * N * N + PB * N * N * N) + PB * PB * PB;
   const double by = (PB * PB * PB + N * N * N + 3 * PB * PB + 3 * PB + (sizeof(T) == 8 ? PB * PB * PB : 0)) * sizeof(T);
   bool use_df = false;
-  if constexpr (sizeof(T) == 8) use_df = MODE != FDM_GATHER && lv.df && lv.Sdf && (lv.p % 2 == 1);
+  if constexpr (sizeof(T) == 8) use_df = MODE != FDM_GATHER && lv.df && lv.Sdf;
   ProfScope prof(SE_K_FDM, s, (double)lv.E, by * lv.E, fl * lv.E,
                  use_df ? lv.p + 64 : prof_variant<T>(lv.p));
   if constexpr (sizeof(T) == 8 && MODE != FDM_GATHER) {
@@ -907,7 +910,8 @@ static int dispatch_fdm(const Level& lv, const T* in, T* out, cudaStream_t s) {
       switch (lv.p) {
 #define SE_FDM_DF(PP) \
   case PP: return launch_fdm_df<PP, MODE>(lv, in, out, s);
-        SE_FDM_DF(1) SE_FDM_DF(3) SE_FDM_DF(5) SE_FDM_DF(7) SE_FDM_DF(9)
+        SE_FDM_DF(1) SE_FDM_DF(2) SE_FDM_DF(3) SE_FDM_DF(4) SE_FDM_DF(5)
+        SE_FDM_DF(6) SE_FDM_DF(7) SE_FDM_DF(8) SE_FDM_DF(9) SE_FDM_DF(10)
 #undef SE_FDM_DF
         default: break;
       }

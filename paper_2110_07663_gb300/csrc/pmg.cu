@@ -273,10 +273,11 @@ static int df_transient(const double* src, df64** dst, int64_t n, cudaStream_t s
 static int arnoldi_df_begin(se_pmg_s* P, cudaStream_t s, std::vector<void*>& keep) {
   for (int l = 0; l + 1 < P->nlev; ++l) {
     Level& lv = *P->lv[l];
-    if (!ax_eo_supported(lv.p) || !lv.eo64) continue;
     const int H = lv.N / 2, PB = lv.p + 3;
+    const bool eo = ax_eo_supported(lv.p) && lv.eo64;
     if (!lv.Gdf) SE_TRY(df_transient(lv.G64, &lv.Gdf, 6 * lv.L, s, keep));
-    if (!lv.eodf) SE_TRY(df_transient(lv.eo64, &lv.eodf, 4 * H * H, s, keep));
+    if (eo && !lv.eodf) SE_TRY(df_transient(lv.eo64, &lv.eodf, 4 * H * H, s, keep));
+    if (!eo && !lv.Ddf) SE_TRY(df_transient(lv.D64, &lv.Ddf, (int64_t)lv.N * lv.N, s, keep));
     if (lv.S64 && !lv.Sdf) {
       SE_TRY(df_transient(lv.S64, &lv.Sdf, 3 * lv.E * PB * PB, s, keep));
       SE_TRY(df_transient(lv.lam64, &lv.lamdf, 3 * lv.E * PB, s, keep));
@@ -293,6 +294,7 @@ static void arnoldi_df_end(se_pmg_s* P, cudaStream_t s, std::vector<void*>& keep
     lv.df = false;
     if (owned(lv.Gdf)) lv.Gdf = nullptr;
     if (owned(lv.eodf)) lv.eodf = nullptr;
+    if (owned(lv.Ddf)) lv.Ddf = nullptr;
     if (owned(lv.Sdf)) lv.Sdf = nullptr;
     if (owned(lv.lamdf)) lv.lamdf = nullptr;
   }
@@ -316,7 +318,7 @@ static int pmg_build(se_pmg_s* P) {
   const bool df = d.precision == SE_DF64;
   SE_TRY(scratch_alloc(P->allocs, &P->scratch));
   // df64 copies of the fine geometry belong to the mesh (the outer operator may use them too)
-  if (df && ax_eo_supported(m->fine.p)) SE_TRY(make_df_geometry(m->fine, m->allocs, s));
+  if (df) SE_TRY(make_df_geometry(m->fine, m->allocs, s));
   P->owned[0] = m->fine;  // shallow copy: shares the mesh's geometry and maps
   P->owned[0].G32 = nullptr;
   P->lv[0] = &P->owned[0];
@@ -329,12 +331,12 @@ static int pmg_build(se_pmg_s* P) {
     Level& lv = *P->lv[l];
     const bool coarsest = l == P->nlev - 1;
     if (fp32 && !coarsest) SE_TRY(make_fp32_geometry(lv, P->allocs, s));
-    if (df && !coarsest && ax_eo_supported(lv.p)) {
+    if (df && !coarsest) {
       SE_TRY(make_df_geometry(lv, P->allocs, s));
       lv.df = true;
     }
     if (!coarsest && d.smoother != SE_SMOOTH_JACOBI) {
-      SE_TRY(fdm_setup(m, lv, P->allocs, fp32, s, df && ax_eo_supported(lv.p)));
+      SE_TRY(fdm_setup(m, lv, P->allocs, fp32, s, df));
       if (d.smoother == SE_SMOOTH_ASM) {
         const int64_t n3 = lv.E * (int64_t)(lv.p + 3) * (lv.p + 3) * (lv.p + 3);
         SE_TRY(dmalloc(P->allocs, &lv.ext64, n3));

@@ -114,7 +114,8 @@ struct Level {
   // df64 arithmetic); `df` routes those two kernels of this level to them
   bool df = false;
   df64* Gdf = nullptr;       // [6][L]
-  df64* eodf = nullptr;      // [4][N/2][N/2]
+  df64* eodf = nullptr;      // [4][N/2][N/2] (even N)
+  df64* Ddf = nullptr;       // [N][N] (odd N)
   df64* Sdf = nullptr;       // [E][3][pb][pb]
   df64* lamdf = nullptr;     // [E][3][pb]
   float* D32 = nullptr;
@@ -333,7 +334,9 @@ int ax_local_eo_df(const Level& lv, const double* u, double* y, cudaStream_t s, 
 int split_df(const double* a, df64* b, int64_t n, cudaStream_t s);
 // df64 copies of a level's geometric factors and folded tables (no-op if present).
 int make_df_geometry(Level& lv, Allocs& allocs, cudaStream_t s);
-inline bool ax_df_route(const Level& lv) { return lv.df && lv.Gdf && lv.eodf && ax_eo_supported(lv.p); }
+inline bool ax_df_route(const Level& lv) {
+  return lv.df && lv.Gdf && (ax_eo_supported(lv.p) ? lv.eodf != nullptr : lv.Ddf != nullptr);
+}
 int pipeline_status_take(int* status);
 int fdm_elems_per_block(int p, bool fp32);
 size_t fdm_smem_bytes(int p, bool fp32, int ne);

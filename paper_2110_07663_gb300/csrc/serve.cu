@@ -77,7 +77,7 @@ struct Resident {
   bool busy = false;
   double last_used = 0.0;
   int64_t L = 0;
-  int op_df = 0;               // outer operator in df64 (server option, odd p)
+  int op_df = 0;               // outer operator in df64 (server option)
 };
 
 struct Ticket {
@@ -151,7 +151,7 @@ static bool make_room(se_server_s* S, size_t need) {
 static size_t need_bytes(const se_server_s* S, const se_request& q) {
   const double L = (double)q.mesh.nel[0] * q.mesh.nel[1] * q.mesh.nel[2] * (q.mesh.p + 1) *
                    (q.mesh.p + 1) * (q.mesh.p + 1);
-  const bool df = S->cfg.operator_df64 && ax_eo_supported(q.mesh.p);
+  const bool df = S->cfg.operator_df64 != 0;
   return footprint_bytes(q.mesh, q.pmg) + (size_t)(2.0 * S->cfg.proj_vectors * L * sizeof(double)) +
          (size_t)(df ? 6.0 * L * sizeof(df64) : 0.0);
 }
@@ -172,7 +172,7 @@ static int build_resident(const se_request& q, int proj_vectors, int op_df, Resi
     }
   }
   if (rc == SE_OK && proj_vectors > 0) rc = se_proj_create(r->m, proj_vectors, &r->proj);
-  if (rc == SE_OK && op_df && ax_eo_supported(r->m->fine.p)) {
+  if (rc == SE_OK && op_df) {
     rc = make_df_geometry(r->m->fine, r->m->allocs, r->m->stream);
     r->op_df = 1;
   }

@@ -192,7 +192,7 @@ extern "C" int se_solve(se_mesh_t m, se_pmg_t P, const double* b, double* x,
   SE_CHECK(o.operator_df64 == 0 || o.operator_df64 == 1, SE_EINVAL, "se_solve: operator_df64");
   cudaStream_t s = as_stream(o.stream, m->stream);
   SE_TRY(ensure_solve_work(m, o.restart, o.method == SE_FGMRES));
-  if (o.operator_df64 && ax_eo_supported(m->fine.p)) SE_TRY(make_df_geometry(m->fine, m->allocs, s));
+  if (o.operator_df64) SE_TRY(make_df_geometry(m->fine, m->allocs, s));
   se_solve_stats st{};
   SE_CUDA(cudaEventRecord(m->ev0, s));
   int rc;
@@ -428,7 +428,7 @@ int se_batch_create(int n, const se_problem* probs, const se_solve_opts* opts, s
       SE_CHECK(probs[j].mesh != probs[i].mesh, SE_EINVAL,
                "se_batch_create: problems %d and %d share a mesh (its work space)", j, i);
     SE_TRY(prepare_graph_solve(probs[i].mesh));
-    if (opts->operator_df64 && ax_eo_supported(probs[i].mesh->fine.p))
+    if (opts->operator_df64)
       SE_TRY(make_df_geometry(probs[i].mesh->fine, probs[i].mesh->allocs, probs[i].mesh->stream));
   }
   auto* B = new se_batch_s();

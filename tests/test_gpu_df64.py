@@ -2,12 +2,12 @@
 
 GB300 runs FP32 FMAs at 64 times its FP64 rate, so the sum-factorised operator and the FDM
 solves also run in df64 (pairs of FP32 values, about 48 significant bits) on FP64 vectors.  The
-bar is the FP64 one: operator relative error <= 1e-12 (every odd p, ragged meshes, all flag
+bar is the FP64 one: operator relative error <= 1e-12 (every p = 1..10, ragged meshes, all flag
 combinations, Neumann and Dirichlet faces); FDM smoother <= 1e-10 and Chebyshev <= 1e-9 as for
 FP64; whole solves with the SE_DF64 preconditioner and the df64 outer operator: iteration counts
 within +-1 of the oracle, true residual <= 1.5e-8, and the device-driven graph equal to the host
-loop bit for bit.  Even orders have no df64 kernels: se_ax refuses the flag, SE_DF64 levels fall
-back to FP64 arithmetic.
+loop bit for bit.  Odd orders use the even-odd folded operator, even orders the plain sum
+factorisation kernel in df64.
 """
 import math
 
@@ -19,11 +19,12 @@ from tests.gpu_common import Case, rel_err
 
 pytestmark = pytest.mark.gpu
 
-ODD = [((1, 1, 1), 1), ((3, 2, 2), 3), ((2, 3, 3), 5), ((3, 1, 2), 7), ((2, 2, 1), 9),
-       ((5, 4, 3), 3), ((4, 3, 4), 7)]
+ORDERS = [((1, 1, 1), 1), ((3, 2, 2), 3), ((2, 3, 3), 5), ((3, 1, 2), 7), ((2, 2, 1), 9),
+          ((5, 4, 3), 3), ((4, 3, 4), 7), ((2, 2, 2), 2), ((3, 2, 2), 4), ((2, 3, 1), 6),
+          ((2, 1, 2), 8), ((1, 2, 1), 10)]
 
 
-@pytest.mark.parametrize("nel,p", ODD)
+@pytest.mark.parametrize("nel,p", ORDERS)
 @pytest.mark.parametrize("bc", [("D",) * 6, ("N", "D", "N", "N", "D", "N")])
 def test_df64_operator(nel, p, bc):
     c = Case(nel, p, seed=50 + p, bc=bc)
@@ -46,21 +47,12 @@ def test_df64_operator(nel, p, bc):
         c.close()
 
 
-def test_df64_operator_refuses_even_orders():
-    c = Case((2, 2, 2), 4)
-    se = c.se
-    try:
-        with pytest.raises(se.SeError):
-            se.se_ax(c.m, c.empty().zero_(), c.empty(), se.SE_AX_DF64)
-    finally:
-        c.close()
-
-
 SMOOTHERS = {"ras": 1, "asm": 2, "jacobi": 0}
 
 
 @pytest.mark.parametrize("nel,p,schedule", [((3, 2, 2), 5, (5, 3, 1)), ((2, 3, 2), 7, (7, 3, 1)),
-                                            ((2, 2, 2), 9, (9, 5, 1)), ((2, 2, 3), 6, (6, 3, 1))])
+                                            ((2, 2, 2), 9, (9, 5, 1)), ((2, 2, 3), 6, (6, 3, 1)),
+                                            ((2, 2, 2), 10, (10, 4, 2, 1))])
 @pytest.mark.parametrize("smoother", ["ras", "asm"])
 def test_df64_smoother_and_chebyshev(nel, p, schedule, smoother):
     c = Case(nel, p, seed=3)
