@@ -8,7 +8,7 @@ direction, pbar = p+3 points per direction of an extended Schwarz subdomain.  A 
 fastest), which flattens to idx = i + N(j + N(k + N e)).  Element e = ex + nx(ey + ny ez) of a
 box lattice of nx*ny*nz hexahedra.
 
-Readings of points where the paper is silent are marked READING and listed in the design doc.
+Readings of points where the paper is silent are marked READING at the code that takes them.
 Parity unpinned against printed results: the paper prints none for these meshes.
 """
 from __future__ import annotations
@@ -749,6 +749,25 @@ def fgmres(A, M, b, x0, dotf, m=20, tol=1e-8, maxit=1000):
         r = b - A(x)
         beta = math.sqrt(dotf(r, r))
     return x, total, rel
+
+
+# =============================================================================================
+# Projection onto prior solutions (Secs. 3.2 and 4.2): the initial guess for a new right-hand
+# side is the element of span{x_1..x_m} closest to A^-1 b in the A-norm.
+# =============================================================================================
+
+
+def projection_guess(lv, xs, b):
+    """The A-orthogonal projection of A^-1 b onto span(xs), by its definition: xbar = X a with the
+    Galerkin system (x_i, A x_j) a_j = (x_i, b) (inner products counting each global node once),
+    solved by least squares so that a dependent set still defines the same projection."""
+    if not xs:
+        return np.zeros_like(b)
+    Ax = [ax(lv, x) for x in xs]
+    G = np.array([[dot(lv, xi, Axj) for Axj in Ax] for xi in xs])
+    c = np.array([dot(lv, xi, b) for xi in xs])
+    a = np.linalg.lstsq(G, c, rcond=1e-13)[0]
+    return sum(ai * xi for ai, xi in zip(a, xs))
 
 
 # =============================================================================================

@@ -145,3 +145,25 @@ def test_space_restarts_when_full_and_skips_a_held_solution():
         se.se_proj_destroy(proj)
         c.se.se_pmg_destroy(P)
         c.close()
+
+
+def test_guess_equals_the_oracle_projection():
+    """se_proj_guess against the oracle's A-orthogonal projection of A^-1 b onto the span of the
+    prior solutions (its plain definition, a Galerkin solve), for arbitrary prior vectors and a
+    right-hand side outside their span: 1e-9 relative."""
+    c, P = setup_case(p=5, nel=(3, 2, 2), schedule=(5, 3, 1), seed=3)
+    se = c.se
+    proj = se.se_proj_create(c.m, 6)
+    try:
+        xs = [c.random_continuous(100 + k) for k in range(4)]
+        for x in xs:
+            se.se_proj_update(proj, c.to_gpu(x))
+        b = o.ax(c.lv, c.random_continuous(200))
+        g = c.empty()
+        se.se_proj_guess(proj, c.to_gpu(b), g)
+        ref = o.projection_guess(c.lv, xs, b)
+        assert rel_err(c.to_np(g), ref) <= 1e-9
+    finally:
+        se.se_proj_destroy(proj)
+        c.se.se_pmg_destroy(P)
+        c.close()

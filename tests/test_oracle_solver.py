@@ -276,3 +276,37 @@ def test_spectral_convergence():
     for a, b_ in zip(errs, errs[1:]):
         assert b_ < a / 8.0
     assert errs[-1] < 5e-5
+
+
+def test_projection_guess_is_the_a_orthogonal_projection():
+    """The projection onto prior solutions (Secs. 3.2 and 4.2): exact for a right-hand side whose
+    solution lies in the span; otherwise the error A^-1 b - xbar is A-orthogonal to every prior
+    solution (Galerkin condition) and no element of the span is closer in the A-norm."""
+    import numpy as np
+    import oracle as o
+    import workloads as wl
+    nel, p = (2, 2, 1), 3
+    V = wl.vertex_lattice(nel, 0.05, seed=4)
+    lv = o.make_level(V, nel, p)
+    def cont(seed):
+        return lv.mask * o.from_global(lv, wl.random_lvector(lv.n_global, seed))
+    xs = [cont(s) for s in (1, 2, 3)]
+    # solution in the span: recovered exactly
+    xt = 0.7 * xs[0] - 1.3 * xs[1] + 0.2 * xs[2]
+    assert np.max(np.abs(o.projection_guess(lv, xs, o.ax(lv, xt)) - xt)) <= 1e-12 * np.max(np.abs(xt))
+    # a dependent set (a repeated direction) defines the same projection
+    b = o.ax(lv, cont(9))
+    g = o.projection_guess(lv, xs, b)
+    g2 = o.projection_guess(lv, xs + [2.0 * xs[1]], b)
+    assert np.max(np.abs(g - g2)) <= 1e-10 * np.max(np.abs(g))
+    # Galerkin: (x_i, b - A xbar) = 0, and perturbing xbar inside the span raises the A-norm error
+    r = b - o.ax(lv, g)
+    for x in xs:
+        assert abs(o.dot(lv, x, r)) <= 1e-12 * np.sqrt(o.dot(lv, b, b) * o.dot(lv, x, x))
+    xstar = cont(9)
+    def err(y):
+        e = xstar - y
+        return o.dot(lv, e, o.ax(lv, e))
+    for x in xs:
+        assert err(g + 1e-3 * x) > err(g) and err(g - 1e-3 * x) > err(g)
+    assert np.array_equal(o.projection_guess(lv, [], b), np.zeros_like(b))
