@@ -595,7 +595,8 @@ def run_autotune(args):
     """Run-time preconditioner selection (Sec. 5, Table 5 without SEMFEM) on the bench workload:
     every candidate of the default space (and, with --autotune-orders, Cheby-RAS(k) and
     Cheby-Jac(k) for k = 1..3 on the same schedules) set up and timed on the first solve, for the
-    FP64 and the FP32 V-cycle; prints the timed table and the choice."""
+    FP64 V-cycle, the df64 one (with the df64 outer operator) and the FP32 one; prints the timed
+    table and the choice."""
     import torch
     from paper_2110_07663_gb300 import se
     import workloads as wl
@@ -613,7 +614,7 @@ def run_autotune(args):
     del xyz, X, f
     names = {se.SE_SMOOTH_ASM: "Cheby-ASM", se.SE_SMOOTH_RAS: "Cheby-RAS", se.SE_SMOOTH_JACOBI: "Cheby-Jac"}
     out = []
-    for prec_name, prec in (("fp64", se.SE_FP64), ("fp32_vcycle", se.SE_FP32)):
+    for prec_name, prec in (("fp64", se.SE_FP64), ("df64", se.SE_DF64), ("fp32_vcycle", se.SE_FP32)):
         cands = se.se_pmg_autotune_space(p, prec)
         if args.autotune_orders:
             for base in (cands[1], cands[2]):
@@ -626,7 +627,7 @@ def run_autotune(args):
                     cands.append(c)
         t0 = time.perf_counter()
         best, timed, P = se.se_pmg_autotune(m, b, cands, repeats=args.steps, tol=1e-8, maxit=500,
-                                            keep=False)
+                                            keep=False, operator_df64=1 if prec == se.SE_DF64 else 0)
         wall = time.perf_counter() - t0
         rows = [{"preconditioner": f"{names[c.pmg.smoother]}({c.pmg.cheb_order[0]})",
                  "schedule": list(c.pmg.schedule[:c.pmg.nlev]),

@@ -38,7 +38,8 @@ int se_pmg_autotune_space(int p, int precision, se_tune_candidate* out, int cap,
   SE_CHECK(out && n && cap >= 3, SE_EINVAL, "se_pmg_autotune_space: need room for 3 candidates");
   SE_CHECK(p >= 2 && p <= SE_MAX_ORDER, SE_EINVAL, "se_pmg_autotune_space: p=%d not in 2..%d", p,
            SE_MAX_ORDER);
-  SE_CHECK(precision == SE_FP64 || precision == SE_FP32, SE_EINVAL, "se_pmg_autotune_space: precision");
+  SE_CHECK(precision == SE_FP64 || precision == SE_FP32 || precision == SE_DF64, SE_EINVAL,
+           "se_pmg_autotune_space: precision");
   std::vector<int> schwarz{p}, jac;
   int mid = (p + 1) / 2;
   if (mid % 2 == 0) --mid;

@@ -367,11 +367,12 @@ def se_pmg_autotune_space(p, precision=SE_FP64):
 
 
 def se_pmg_autotune(m, b, candidates, repeats=2, method=SE_FPCG, tol=1e-8, maxit=1000, restart=20,
-                    graph_capture=1, tol_norm=0, keep=True):
+                    graph_capture=1, tol_norm=0, keep=True, operator_df64=0):
     """Times every candidate; returns (best index, timed candidates, best preconditioner or None)."""
     o = se_solve_opts()
     o.method, o.restart, o.tol, o.maxit, o.graph_capture = method, restart, tol, maxit, graph_capture
     o.tol_norm = tol_norm
+    o.operator_df64 = operator_df64
     arr = (se_tune_candidate * len(candidates))(*candidates)
     best = C.c_int(-1)
     h = _vp()
