@@ -643,6 +643,50 @@ def run_autotune(args):
                       "searches": out}))
 
 
+def run_smoother_sweep(args):
+    """The bench workload's full smoother set: Cheby-RAS(k) and Cheby-Jac(k), k = 1, 2, 3, on the
+    pMG schedule 7-5-3-1, FPCG to 1e-8 (graph solves, mean of --steps timed solves after one
+    untimed), in FP64, df64 (with the df64 outer operator) and the FP32 V-cycle."""
+    import torch
+    from paper_2110_07663_gb300 import se
+    import workloads as wl
+    torch.cuda.set_device(0)
+    wk = WORKLOADS[args.workload]
+    nel, p, sched = wk["nel"], wk["p"], wk["schedule"]
+    m = se.se_mesh_create(nel, p, perturb_frac=wk["perturb"], seed=wk["seed"], deform_amp=wl.DEFORM_AMP)
+    info = se.se_mesh_get_info(m)
+    xyz = torch.empty(3 * info.L, dtype=torch.float64, device="cuda")
+    se.se_mesh_nodes(m, xyz)
+    X = xyz.view(3, -1)
+    f = 3.0 * math.pi ** 2 * torch.sin(math.pi * X[0]) * torch.sin(math.pi * X[1]) * torch.sin(math.pi * X[2])
+    b = torch.empty(info.L, dtype=torch.float64, device="cuda")
+    se.se_mesh_rhs(m, f.contiguous(), b)
+    del xyz, X, f
+    rows = []
+    for prec_name, prec in (("fp64", se.SE_FP64), ("df64", se.SE_DF64), ("fp32_vcycle", se.SE_FP32)):
+        cands = []
+        for sm in (se.SE_SMOOTH_RAS, se.SE_SMOOTH_JACOBI):
+            for k in (1, 2, 3):
+                c = se.se_tune_candidate()
+                c.pmg = se.pmg_desc(sched, sm, k, precision=prec)
+                cands.append(c)
+        best, timed, _ = se.se_pmg_autotune(m, b, cands, repeats=args.steps, tol=1e-8, maxit=500,
+                                            keep=False, operator_df64=1 if prec == se.SE_DF64 else 0)
+        for c in timed:
+            rows.append({"arithmetic": prec_name,
+                         "preconditioner": f"Cheby-{'RAS' if c.pmg.smoother == se.SE_SMOOTH_RAS else 'Jac'}"
+                                           f"({c.pmg.cheb_order[0]})",
+                         "iterations": c.iterations, "solve_ms": round(c.ms, 2),
+                         "gdof_per_s": round(info.n_dof / (c.ms * 1e-3) / 1e9, 4),
+                         "setup_ms": round(c.setup_ms, 1), "status": c.status})
+    se.se_mesh_destroy(m)
+    print(json.dumps({"metric": "Poisson solve time per smoother (Cheby-RAS(k), Cheby-Jac(k), k = 1..3)",
+                      "config": {"workload": f"{args.workload}: {nel[0]}x{nel[1]}x{nel[2]} elements, p={p}, "
+                                             f"n={info.n_dof}, pMG {'-'.join(map(str, sched))}, FPCG to 1e-8, "
+                                             f"graph solves, {args.steps} timed per entry"},
+                      "rows": rows}))
+
+
 def skewed_problem(se, torch, nel, p, eps, segments=2):
     """Mesh on the skewed lattice (workloads.skewed_lattice, no smooth map) and b for
     f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z)."""
@@ -799,6 +843,8 @@ def main():
                     help="time the preconditioner candidates of Table 5 on the workload")
     ap.add_argument("--autotune-orders", action="store_true",
                     help="autotune: add Chebyshev orders 1 and 3 for RAS and Jacobi")
+    ap.add_argument("--smoother-sweep", action="store_true",
+                    help="Cheby-RAS(k) and Cheby-Jac(k), k = 1..3, on the workload's schedule")
     ap.add_argument("--lambda-study", action="store_true",
                     help="iterations vs Chebyshev bounds on the skewed lattice (Table 1 analogue)")
     ap.add_argument("--order-study", action="store_true",
@@ -823,6 +869,8 @@ def main():
         run_precision_study(args)
     elif args.autotune:
         run_autotune(args)
+    elif args.smoother_sweep:
+        run_smoother_sweep(args)
     elif args.lambda_study:
         run_lambda_study(args)
     elif args.order_study:
