@@ -1,8 +1,10 @@
 """Benchmark: Poisson solves of the 32^3-element, p=7 deformed box (FP64 method).
 
 One step = one whole solve (x0 = 0) of the pressure-Poisson problem with flexible PCG to a
-relative residual of 1e-8, preconditioned by the p-multigrid V-cycle 7->5->3->1 with
-2nd-order Chebyshev-accelerated RAS smoothing and a p=1 Jacobi-PCG coarse solve, all in FP64.
+relative residual of 1e-8, preconditioned by the p-multigrid V-cycle 7->5->3->1 with a
+Chebyshev-accelerated RAS or Jacobi smoother of order 1..3 (chosen during set-up by the paper's
+run-time preconditioner search, Sec. 5; --smoother fixes it) and a p=1 Jacobi-PCG coarse solve,
+all in FP64.
 value = gridpoints solved per second, n = E p^3 per solve (the paper's work-rate measure),
 summed over ranks.  Inputs (mesh, geometry, FDM factors, right-hand side) are resident in HBM
 before the timed region; every step works on ~12 GB of state, far larger than L2.
@@ -206,11 +208,30 @@ def run_gpu(args):
     b = torch.empty(L, dtype=torch.float64, device=dev)
     se.se_mesh_rhs(m, f.contiguous(), b)
     del xyz, X, f
-    smoother = {"ras": se.SE_SMOOTH_RAS, "jacobi": se.SE_SMOOTH_JACOBI, "asm": se.SE_SMOOTH_ASM}[args.smoother]
     prec = se.SE_FP32 if args.precond_fp32 else (se.SE_DF64 if args.df64 else se.SE_FP64)
     op_df = 1 if (args.df64 or args.operator_df64) else 0
+    sm_names = {se.SE_SMOOTH_RAS: "RAS", se.SE_SMOOTH_JACOBI: "Jac", se.SE_SMOOTH_ASM: "ASM"}
     t_setup0 = time.perf_counter()
-    P = se.se_pmg_setup(m, se.pmg_desc(wk["schedule"], smoother, args.cheb_order, precision=prec))
+    search = None
+    if args.smoother == "auto":
+        # the method's run-time preconditioner selection (Sec. 5) over the workload's smoother set,
+        # Cheby-RAS(k) and Cheby-Jac(k), k = 1..3: each set up and timed on the first solves
+        # (untimed here, part of the set-up); the fastest is kept for the timed steps
+        cands = []
+        for sm in (se.SE_SMOOTH_RAS, se.SE_SMOOTH_JACOBI):
+            for k in (1, 2, 3):
+                c = se.se_tune_candidate()
+                c.pmg = se.pmg_desc(wk["schedule"], sm, k, precision=prec)
+                cands.append(c)
+        best, timed, P = se.se_pmg_autotune(m, b, cands, repeats=2, tol=1e-8, maxit=500,
+                                            operator_df64=op_df)
+        search = [{"preconditioner": f"Cheby-{sm_names[c.pmg.smoother]}({c.pmg.cheb_order[0]})",
+                   "solve_ms": round(c.ms, 2), "iterations": c.iterations} for c in timed]
+        smoother, cheb_order = timed[best].pmg.smoother, timed[best].pmg.cheb_order[0]
+    else:
+        smoother = {"ras": se.SE_SMOOTH_RAS, "jacobi": se.SE_SMOOTH_JACOBI, "asm": se.SE_SMOOTH_ASM}[args.smoother]
+        cheb_order = args.cheb_order
+        P = se.se_pmg_setup(m, se.pmg_desc(wk["schedule"], smoother, cheb_order, precision=prec))
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t_setup0
     x = torch.zeros(L, dtype=torch.float64, device=dev)
@@ -248,11 +269,13 @@ def run_gpu(args):
     se.se_prof_reset()
     se.se_prof_enable(True)
     p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("profiled_pass")  # lets a profiler select exactly these launches
     p0.record(stream)
     for _ in range(args.steps):
         step(graph=0)
     p1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     se.se_prof_enable(False)
     host_loop_ms = p0.elapsed_time(p1) / args.steps
     prof = {se.KERNEL_NAMES[k]: se.se_prof_query(k) for k in range(se.SE_K_COUNT)}
@@ -312,9 +335,12 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {"workload": f"{args.workload}: deformed box {nel[0]}x{nel[1]}x{nel[2]} hex, p={p}, "
                                f"n={n_dof} (E p^3), pMG {'-'.join(map(str, wk['schedule']))} "
-                               f"Cheby-{args.smoother.upper()}({args.cheb_order}), "
+                               f"Cheby-{sm_names[smoother]}({cheb_order}), "
                                f"FPCG tol 1e-8, {prec_name} preconditioner, {op_name} outer operator",
                    "iterations": iters, "setup_s": round(setup_s, 2),
+                   "preconditioner_choice": ("run-time search (Sec. 5) over Cheby-RAS(k), Cheby-Jac(k), "
+                                             "k = 1..3, inside set-up" if search else "fixed by --smoother"),
+                   "preconditioner_search": search,
                    "solve_path": "se_solve graph_capture=1 (device-driven CUDA graph)",
                    "profiled_pass_ms_per_step": round(host_loop_ms, 3),
                    "profiled_pass": "same solve host-driven, per-kernel CUDA events (kernels, roofline)",
@@ -328,7 +354,7 @@ def run_gpu(args):
         "clocks": clk.summary(),
     }
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        out["cpu_baseline"] = cpu_baseline_subprocess(args.cpu_timeout)
+        out["cpu_baseline"] = cpu_baseline_subprocess(args.cpu_timeout, sm_names[smoother], cheb_order)
     se.se_pmg_destroy(P)
     se.se_mesh_destroy(m)
     if rank == 0:
@@ -338,14 +364,19 @@ def run_gpu(args):
 
 
 # --------------------------------------------------------------------------------- CPU oracle
-def oracle_sample(timeout_s):
-    """Oracle solve of the bounded sample (same method and tolerance, 6^3 elements)."""
+ORACLE_SMOOTHERS = {"ras": "ras", "jacobi": "jacobi", "asm": "asm", "RAS": "ras", "Jac": "jacobi",
+                    "ASM": "asm"}
+
+
+def oracle_sample(timeout_s, smoother="ras", order=2):
+    """Oracle solve of the bounded sample (same method and tolerance, 10^3 elements)."""
     import numpy as np
     import oracle as o
     import workloads as wl
     V = wl.vertex_lattice(SAMPLE["nel"], SAMPLE["perturb"], SAMPLE["seed"])
     lv, b = o.problem(V, SAMPLE["nel"], SAMPLE["p"], amp=wl.DEFORM_AMP)
-    pmg = o.pmg_setup(V, SAMPLE["nel"], SAMPLE["schedule"], smoother="ras", order=2, amp=wl.DEFORM_AMP)
+    pmg = o.pmg_setup(V, SAMPLE["nel"], SAMPLE["schedule"], smoother=ORACLE_SMOOTHERS[smoother],
+                      order=order, amp=wl.DEFORM_AMP)
     t0 = time.perf_counter()
     x, it, rel = o.solve(lv, b, pmg, tol=1e-8)
     t = time.perf_counter() - t0
@@ -353,10 +384,11 @@ def oracle_sample(timeout_s):
     return n / t / 1e9, t, it
 
 
-def cpu_baseline_subprocess(timeout_s):
+def cpu_baseline_subprocess(timeout_s, smoother="ras", order=2):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     code = ("import sys, json; sys.path.insert(0, %r); import bench; "
-            "v, t, it = bench.oracle_sample(0); print(json.dumps([v, t, it]))" % ROOT)
+            "v, t, it = bench.oracle_sample(0, %r, %d); print(json.dumps([v, t, it]))"
+            % (ROOT, smoother, order))
     try:
         r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
                            timeout=timeout_s, env=env)
@@ -366,8 +398,8 @@ def cpu_baseline_subprocess(timeout_s):
                 "sample": f"failed: {type(e).__name__}"}
     return {"value": round(v, 6), "unit": "GDOF/s", "cores": 1, "kind": "oracle",
             "sample": f"one full solve of a 10x10x10-element p=7 piece of the same workload "
-                      f"(same map, schedule, smoother, tolerance): {it} iterations in {t:.1f} s, "
-                      f"single thread"}
+                      f"(same map, schedule, smoother Cheby-{smoother}({order}), tolerance): {it} "
+                      f"iterations in {t:.1f} s, single thread"}
 
 
 def run_batch(args):
@@ -787,10 +819,26 @@ def run_reference(args):
     if rank != 0:
         return
     env_threads = 1
+    search = None
+    if args.smoother == "auto":
+        # the same run-time search as the GPU arm, on the oracle: each candidate solves the
+        # sample once (untimed set-up), the fastest is then timed
+        search = []
+        for sm in ("ras", "jacobi"):
+            for k in (1, 2, 3):
+                v, t, it = oracle_sample(0, sm, k)
+                search.append({"preconditioner": f"Cheby-{sm}({k})", "solve_s": round(t, 2),
+                               "iterations": it, "sm": sm, "k": k})
+        bestc = min(search, key=lambda r: r["solve_s"])
+        smoother, order = bestc["sm"], bestc["k"]
+        for r in search:
+            del r["sm"], r["k"]
+    else:
+        smoother, order = args.smoother, args.cheb_order
     vals = []
     t_total = 0.0
     for _ in range(args.steps):
-        v, t, it = oracle_sample(0)
+        v, t, it = oracle_sample(0, smoother, order)
         vals.append(v)
         t_total += t
     value = statistics.median(vals)
@@ -800,12 +848,13 @@ def run_reference(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"{args.workload} (oracle on a bounded 10x10x10-element p=7 sample)",
-                   "parallelism": "cpu"},
+        "config": {"workload": f"{args.workload} (oracle on a bounded 10x10x10-element p=7 sample), "
+                               f"Cheby-{smoother}({order})",
+                   "preconditioner_search": search, "parallelism": "cpu"},
         "cpu_baseline": {"value": round(value, 6), "unit": "GDOF/s", "cores": env_threads,
                          "kind": "oracle",
-                         "sample": "each step one full oracle solve of a 10x10x10-element p=7 piece "
-                                   "of the workload"},
+                         "sample": f"each step one full oracle solve of a 10x10x10-element p=7 piece "
+                                   f"of the workload with Cheby-{smoother}({order})"},
         "e2e": {"value": round(value, 6), "unit": "GDOF/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -819,7 +868,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="box32_p7", choices=sorted(WORKLOADS))
-    ap.add_argument("--smoother", default="ras", choices=["ras", "jacobi", "asm"])
+    ap.add_argument("--smoother", default="auto", choices=["auto", "ras", "jacobi", "asm"],
+                    help="auto: the run-time preconditioner search over Cheby-RAS(k), Cheby-Jac(k)")
     ap.add_argument("--cheb-order", type=int, default=2)
     ap.add_argument("--precond-fp32", action="store_true")
     ap.add_argument("--df64", action="store_true",
