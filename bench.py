@@ -198,7 +198,7 @@ def run_gpu(args):
     wk = WORKLOADS[args.workload]
     nel, p = wk["nel"], wk["p"]
     m = se.se_mesh_create(nel, p, perturb_frac=wk["perturb"], seed=wk["seed"] + rank,
-                          deform_amp=wl.DEFORM_AMP)
+                          deform_amp=wl.DEFORM_AMP, flags=se.SE_MESH_GS_MAP if args.gs_map else 0)
     info = se.se_mesh_get_info(m)
     L = info.L
     xyz = torch.empty(3 * L, dtype=torch.float64, device=dev)
@@ -324,10 +324,14 @@ def run_gpu(args):
     (dom, dvar), d = max(variants.items(), key=lambda kv: kv[1]["ms"])
     roof = roofline(dom, dvar, d, pk, pk_kind)
     tot_ms = max(sum(v["ms"] for v in variants.values()), 1e-9)
-    kernels = {f"{k} p={v % 32} {VARIANT_KIND[v // 32]}":
-               {"ms_per_step": round(q["ms"] / args.steps, 3),
-                "launches_per_step": q["launches"] / args.steps, "share": round(q["ms"] / tot_ms, 4)}
-               for (k, v), q in sorted(variants.items(), key=lambda kv: -kv[1]["ms"])}
+    kernels = {}
+    for (k, v), q in sorted(variants.items(), key=lambda kv: -kv[1]["ms"]):
+        r = roofline(k, v, q, pk, pk_kind) if q["ms"] > 0 and (q["bytes"] > 0 or q["flops"] > 0) else None
+        kernels[f"{k} p={v % 32} {VARIANT_KIND[v // 32]}"] = {
+            "ms_per_step": round(q["ms"] / args.steps, 3),
+            "launches_per_step": q["launches"] / args.steps, "share": round(q["ms"] / tot_ms, 4),
+            # each kernel against its own binding roof (algorithmic bytes or flops per launch)
+            "bound": r["bound"] if r else None, "roof_frac": r["frac"] if r else None}
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": "GDOF/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 3),
@@ -342,6 +346,8 @@ def run_gpu(args):
                                              "k = 1..3, inside set-up" if search else "fixed by --smoother"),
                    "preconditioner_search": search,
                    "solve_path": "se_solve graph_capture=1 (device-driven CUDA graph)",
+                   "qqt": ("sorted index map (SE_MESH_GS_MAP)" if args.gs_map
+                           else "direction sweeps over the box lattice"),
                    "profiled_pass_ms_per_step": round(host_loop_ms, 3),
                    "profiled_pass": "same solve host-driven, per-kernel CUDA events (kernels, roofline)",
                    "l2": "inputs larger than L2 (about 12 GB of resident state per solve)",
@@ -872,6 +878,8 @@ def main():
                     help="auto: the run-time preconditioner search over Cheby-RAS(k), Cheby-Jac(k)")
     ap.add_argument("--cheb-order", type=int, default=2)
     ap.add_argument("--precond-fp32", action="store_true")
+    ap.add_argument("--gs-map", action="store_true",
+                    help="QQ^T of every level from the sorted index map instead of the sweeps")
     ap.add_argument("--df64", action="store_true",
                     help="SE_DF64 preconditioner and df64 outer operator (FP64 vectors)")
     ap.add_argument("--operator-df64", action="store_true",

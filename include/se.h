@@ -86,9 +86,12 @@ typedef struct se_mesh_desc {
   double perturb_frac;     /* used only when vertex_xyz == NULL */
   uint64_t seed;
   int bc[6];               /* faces x-, x+, y-, y+, z-, z+: SE_BC_DIRICHLET or SE_BC_NEUMANN */
-  int flags;               /* SE_MESH_NONBLOCKING_STREAM: the handle's stream is non-blocking */
+  int flags;               /* SE_MESH_NONBLOCKING_STREAM: the handle's stream is non-blocking;
+                              SE_MESH_GS_MAP: QQ^T of this mesh and of every preconditioner level
+                              built on it runs from a sorted index map (as se_gsmap_*) instead of
+                              the direction sweeps over the box lattice (the default) */
 } se_mesh_desc;
-enum { SE_MESH_NONBLOCKING_STREAM = 1 };
+enum { SE_MESH_NONBLOCKING_STREAM = 1, SE_MESH_GS_MAP = 2 };
 
 typedef struct se_mesh_info {
   int64_t E, N, L, n_global;  /* elements, points per direction, local points, global nodes */
@@ -97,7 +100,8 @@ typedef struct se_mesh_info {
   int nel[3];
 } se_mesh_info;
 
-/* Builds geometry, the QQ^T index map, masks and the Jacobi diagonal on the device. */
+/* Builds geometry, point flags (multiplicity, Dirichlet), element neighbours and the Jacobi
+ * diagonal on the device (and the QQ^T index map with SE_MESH_GS_MAP). */
 int se_mesh_create(const se_mesh_desc* desc, se_mesh_t* out);
 int se_mesh_destroy(se_mesh_t m);
 int se_mesh_get_info(se_mesh_t m, se_mesh_info* info);
@@ -118,6 +122,32 @@ int se_mesh_rhs(se_mesh_t m, const double* f_dev, double* b_dev, void* stream);
 int se_ax(se_mesh_t m, const double* u, double* y, int flags, void* stream);
 /* In place u <- [M] QQ^T u (Sec. 2.1, gather-scatter); mask != 0 also zeroes Dirichlet nodes. */
 int se_gs(se_mesh_t m, double* u, int mask, void* stream);
+/* ---------------------------------------------------------------- QQ^T index map (Sec. 2.1) */
+/* Direct stiffness summation QQ^T driven by a precomputed sorted index map, for ANY element
+ * connectivity (se_gs uses direction sweeps that need the box lattice).  Q is given by the global
+ * node id of every local point: (QQ^T u)_l = sum of u over the local copies of l's global node.
+ *  gid:       HOST array of L int64 global ids, each >= 0 (any labels; compact labels below
+ *             2L + 1024 are grouped by counting sort, others by sorting).
+ *  dirichlet: HOST array of L bytes or NULL; a global node is Dirichlet when any of its copies
+ *             has a non-zero byte; apply with mask != 0 sets all its copies to zero.
+ * The map keeps, per global node with two or more copies, its local ids in ascending order
+ * (int32, so L < 2^31), bucketed by multiplicity (2, 4, 8 and other counts), plus the single
+ * copies of Dirichlet nodes; the copies are summed in ascending local id order from the first, so
+ * the result equals the sequential sum in local-id order bitwise.  The handle owns its device
+ * memory and stream (non-blocking).  Errors: SE_EINVAL for L outside [1, 2^31), a null gid or a
+ * negative id (checked before any device work), SE_ENOMEM, SE_ECUDA. */
+typedef struct se_gsmap_s* se_gsmap_t;
+int se_gsmap_create(int64_t L, const int64_t* gid, const uint8_t* dirichlet, se_gsmap_t* out);
+/* In place u <- [M] QQ^T u on a device vector of L values (FP64, or FP32 for _f32). */
+int se_gsmap_apply(se_gsmap_t g, double* u, int mask, void* stream);
+int se_gsmap_apply_f32(se_gsmap_t g, float* u, int mask, void* stream);
+/* counts[5]: groups of 2, 4 and 8 copies, groups of other multiplicities (>= 2), single copies
+ * of Dirichlet nodes. */
+int se_gsmap_info(se_gsmap_t g, int64_t* counts);
+/* Host only (no device call): the counts se_gsmap_create would produce for these arguments. */
+int se_gsmap_count(int64_t L, const int64_t* gid, const uint8_t* dirichlet, int64_t* counts);
+int se_gsmap_destroy(se_gsmap_t g);
+
 /* Unique-node inner product sum_l a_l b_l / mult_l of two continuous L-vectors (FP64,
  * deterministic order).  Synchronises the stream; result written to *out_host. */
 int se_dot(se_mesh_t m, const double* a, const double* b, double* out_host, void* stream);

@@ -412,6 +412,7 @@ static double interface_copies(const Level& lv) {
 
 template <class T>
 int gs_apply(const Level& lv, T* u, bool mask, cudaStream_t s) {
+  if (lv.gsm_ids) return gsmap_apply<T>(lv, u, mask, s);
   const double shared = interface_copies(lv);
   const double bytes = shared * 2.0 * sizeof(T), flops = shared;
   switch (lv.N) {

@@ -244,6 +244,7 @@ int build_level(se_mesh_s* m, int p, Level* lvp, Allocs& allocs, cudaStream_t s)
   pointflag_kernel<<<grid_for(lv.L, 256), 256, 0, s>>>(N, lv.nel[0], lv.nel[1], lv.nel[2], lv.L,
                                                       bc_mask_bits(lv.bc), lv.pflag, nullptr);
   SE_LAUNCH_CHECK();
+  if (m->desc.flags & SE_MESH_GS_MAP) SE_TRY(build_level_gsmap(lv, allocs, s));
   return SE_OK;
 }
 

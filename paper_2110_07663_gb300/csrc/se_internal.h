@@ -133,6 +133,12 @@ struct Level {
   double* cdinv = nullptr;   // [n_global]
   int* g2l = nullptr;        // first local copy of each global node [n_global]
   int* l2g = nullptr;        // global node of each local node [L]
+  // QQ^T index map (SE_MESH_GS_MAP meshes, se_gsmap handles; gsmap.cu); null: QQ^T by sweeps
+  int* gsm_ids = nullptr;    // buckets of local ids, bucket b starting at gsm_seg[b]
+  int* gsm_goff = nullptr;   // CSR offsets of the groups of other multiplicities [gsm_n[3] + 1]
+  int64_t gsm_n[5] = {0, 0, 0, 0, 0};    // groups of 2, 4, 8, other copies; masked single copies
+  int64_t gsm_seg[5] = {0, 0, 0, 0, 0};
+  int64_t gsm_entries = 0;   // local ids in groups of two or more
 };
 
 // ------------------------------------------------------------------ reduction scratch
@@ -207,6 +213,11 @@ int ax_local(const Level& lv, const T* u, T* y, bool mask_in, cudaStream_t s,
              const T* sub = nullptr);
 template <class T>
 int gs_apply(const Level& lv, T* u, bool mask, cudaStream_t s);
+// QQ^T by the index map of lv (gsm_ids set); gs_apply dispatches to it.
+template <class T>
+int gsmap_apply(const Level& lv, T* u, bool mask, cudaStream_t s);
+// Builds lv's index map from its lattice numbering (SE_MESH_GS_MAP).
+int build_level_gsmap(Level& lv, Allocs& allocs, cudaStream_t s);
 template <class T>
 inline int ax_apply(const Level& lv, const T* u, T* y, cudaStream_t s) {
   SE_TRY(ax_local<T>(lv, u, y, false, s));

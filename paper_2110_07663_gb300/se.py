@@ -20,7 +20,7 @@ SE_SMOOTH_JACOBI, SE_SMOOTH_RAS, SE_SMOOTH_ASM = 0, 1, 2
 SE_FPCG, SE_FGMRES = 0, 1
 SE_TOL_R0, SE_TOL_B = 0, 1
 SE_AX_ASSEMBLE, SE_AX_MASK, SE_AX_FP32, SE_AX_DF64 = 1, 2, 4, 8
-SE_MESH_NONBLOCKING_STREAM = 1
+SE_MESH_NONBLOCKING_STREAM, SE_MESH_GS_MAP = 1, 2
 SE_RHS_MODES, SE_RHS_HOST = 0, 1
 SE_MAX_LEVELS, SE_MAX_ORDER = 8, 10
 (SE_K_AX, SE_K_GS, SE_K_FDM, SE_K_CHEBY_UPD, SE_K_RESTRICT, SE_K_PROLONG, SE_K_COARSE,
@@ -125,6 +125,12 @@ _SIGS = {
     "se_mesh_rhs": ([_vp, _vp, _vp, _vp], C.c_int),
     "se_ax": ([_vp, _vp, _vp, _ip, _vp], C.c_int),
     "se_gs": ([_vp, _vp, _ip, _vp], C.c_int),
+    "se_gsmap_create": ([C.c_int64, _vp, _vp, C.POINTER(_vp)], C.c_int),
+    "se_gsmap_apply": ([_vp, _vp, _ip, _vp], C.c_int),
+    "se_gsmap_apply_f32": ([_vp, _vp, _ip, _vp], C.c_int),
+    "se_gsmap_info": ([_vp, C.POINTER(C.c_int64)], C.c_int),
+    "se_gsmap_count": ([C.c_int64, _vp, _vp, C.POINTER(C.c_int64)], C.c_int),
+    "se_gsmap_destroy": ([_vp], C.c_int),
     "se_dot": ([_vp, _vp, _vp, _dp, _vp], C.c_int),
     "se_jacobi_diag": ([_vp, _vp, _vp], C.c_int),
     "se_pmg_setup": ([_vp, C.POINTER(se_pmg_desc), C.POINTER(_vp)], C.c_int),
@@ -211,7 +217,7 @@ def _stream(s):
 
 # ----------------------------------------------------------------------------- mesh / operator
 def se_mesh_create(nel, p, *, vertex_xyz=None, deform_amp=0.05, perturb_frac=0.0, seed=0,
-                   bc=(SE_BC_DIRICHLET,) * 6):
+                   bc=(SE_BC_DIRICHLET,) * 6, flags=0):
     """Create a mesh; vertex_xyz is an optional host float64 array of shape (V, 3)."""
     d = se_mesh_desc()
     d.nel[:] = list(nel)
@@ -225,6 +231,7 @@ def se_mesh_create(nel, p, *, vertex_xyz=None, deform_amp=0.05, perturb_frac=0.0
     d.perturb_frac = perturb_frac
     d.seed = seed
     d.bc[:] = list(bc)
+    d.flags = flags
     h = _vp()
     _check(lib.se_mesh_create(C.byref(d), C.byref(h)))
     return h.value
@@ -258,6 +265,49 @@ def se_ax(m, u, y, flags=SE_AX_ASSEMBLE | SE_AX_MASK, stream=None):
 
 def se_gs(m, u, mask=1, stream=None):
     _check(lib.se_gs(m, _ptr(u), mask, _stream(stream)))
+
+
+# ----------------------------------------------------------------------------- QQ^T index map
+def _gsmap_host_args(gid, dirichlet):
+    import numpy as np
+    g = np.ascontiguousarray(gid, dtype=np.int64).reshape(-1)
+    d = None if dirichlet is None else np.ascontiguousarray(dirichlet, dtype=np.uint8).reshape(-1)
+    if d is not None and d.size != g.size:
+        raise ValueError("dirichlet must have one byte per local point")
+    return g, d, g.ctypes.data, (None if d is None else d.ctypes.data)
+
+
+def se_gsmap_create(gid, dirichlet=None):
+    """Index-map QQ^T for the global ids `gid` (host array, one per local point)."""
+    g, d, gp, dp = _gsmap_host_args(gid, dirichlet)
+    h = _vp()
+    _check(lib.se_gsmap_create(g.size, gp, dp, C.byref(h)))
+    return h.value
+
+
+def se_gsmap_apply(g, u, mask=1, stream=None):
+    """In place u <- [M] QQ^T u; u is a float64 or float32 CUDA tensor."""
+    import torch
+    fn = lib.se_gsmap_apply_f32 if u.dtype == torch.float32 else lib.se_gsmap_apply
+    _check(fn(g, _ptr(u), mask, _stream(stream)))
+
+
+def se_gsmap_info(g):
+    c = (C.c_int64 * 5)()
+    _check(lib.se_gsmap_info(g, c))
+    return tuple(c)
+
+
+def se_gsmap_count(gid, dirichlet=None):
+    """Bucket counts (pairs, quads, octets, other groups, masked singles); host only."""
+    g, d, gp, dp = _gsmap_host_args(gid, dirichlet)
+    c = (C.c_int64 * 5)()
+    _check(lib.se_gsmap_count(g.size, gp, dp, c))
+    return tuple(c)
+
+
+def se_gsmap_destroy(g):
+    _check(lib.se_gsmap_destroy(g))
 
 
 def se_dot(m, a, b, stream=None) -> float:

@@ -20,12 +20,13 @@ def gpu():
 class Case:
     """A mesh on the GPU (through the C ABI) and the same mesh in the oracle."""
 
-    def __init__(self, nel, p, pert=0.05, seed=0, bc=("D",) * 6, amp=wl.DEFORM_AMP, V=None):
+    def __init__(self, nel, p, pert=0.05, seed=0, bc=("D",) * 6, amp=wl.DEFORM_AMP, V=None,
+                 flags=0):
         self.torch, self.se = gpu()
         self.nel, self.p, self.bc, self.amp = tuple(nel), p, tuple(bc), amp
         self.V = wl.vertex_lattice(nel, pert, seed) if V is None else V
         self.m = self.se.se_mesh_create(nel, p, vertex_xyz=self.V, deform_amp=amp,
-                                        bc=[BC[c] for c in bc])
+                                        bc=[BC[c] for c in bc], flags=flags)
         self.info = self.se.se_mesh_get_info(self.m)
         self.lv = o.make_level(self.V, nel, p, bc, amp)
         self.dev = self.torch.device("cuda:0")
