@@ -182,11 +182,17 @@ template int scale_mul<float>(const float*, const float*, float*, int64_t, cudaS
 // from_r (the first step): d is not stored; d = scale r and s = scale (S A r) (the operator and
 // smoother were applied to r itself: by linearity S A (scale r) = scale S A r).
 // last: the final x += d of Algorithm 2 is done here, and r and d (no longer needed) are not
-// written: x = (x + d) + (c1 d + c2 r).
+// written: x = x + d + (c1 d + c2 r).
+// GB300 issues FP64 at 2 instructions/clk/SM, below the rate at which HBM delivers this
+// kernel's 4-6 words per point, so the recurrence is evaluated with its constants folded into
+// FMAs (3-5 FP64 instructions per point instead of 6-8): mathematically the same update, with
+// the rounding of an FMA chain.  The constants are formed on the host in FP64:
+//   k_d = 1 + c1, k_r = scale (1 + c1) + c2, c1s = c1 scale, k_s = -scale,
+//   k_sl = -c2 scale (from_r) or -c2, the weight of the surrogate output in the last update.
 template <class T, bool FIRST, bool FROM_R, bool LAST>
 __global__ void cheb_update_kernel(T* __restrict__ x, T* __restrict__ d, T* __restrict__ r,
                                    const T* __restrict__ sv, const T* __restrict__ dinv, int64_t n,
-                                   T c1, T c2, T scale) {
+                                   T c1, T c2, T scale, T k_d, T k_r, T c1s, T k_s, T k_sl) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   // every load of this instantiation is unconditional, so all are in flight together
@@ -195,23 +201,24 @@ __global__ void cheb_update_kernel(T* __restrict__ x, T* __restrict__ d, T* __re
   const T di = dinv ? dinv[i] : T(1);
   const T d0 = FROM_R ? T(0) : d[i];
   const T x0 = FIRST ? T(0) : x[i];
-  T sval = dinv ? di * s0 : s0;
-  T dv;
-  if (FROM_R) {
-    dv = r0 * scale;
-    sval = sval * scale;
-  } else {
-    dv = d0;
-  }
-  const T xv = FIRST ? dv : x0 + dv;
-  const T rv = r0 - sval;
-  const T dn = c1 * dv + c2 * rv;
-  if (LAST) {
-    x[i] = xv + dn;
-  } else {
-    x[i] = xv;
+  if constexpr (LAST) {
+    // x + d + c1 d + c2 (r - s)
+    const T w = dinv ? k_sl * di : k_sl;
+    const T t = FIRST ? w * s0 : fma(w, s0, x0);
+    x[i] = FROM_R ? fma(k_r, r0, t) : fma(k_d, d0, fma(c2, r0, t));
+  } else if constexpr (FROM_R) {
+    // d = scale r: x + d, r - scale s, c1 d + c2 r'
+    const T w = dinv ? k_s * di : k_s;
+    const T rv = fma(w, s0, r0);
+    x[i] = FIRST ? scale * r0 : fma(scale, r0, x0);
     r[i] = rv;
-    d[i] = dn;
+    d[i] = fma(c1s, r0, c2 * rv);
+  } else {
+    const T sval = dinv ? di * s0 : s0;
+    const T rv = r0 - sval;
+    x[i] = FIRST ? d0 : x0 + d0;
+    r[i] = rv;
+    d[i] = fma(c1, d0, c2 * rv);
   }
 }
 template <class T>
@@ -222,9 +229,15 @@ int cheb_update(T* x, T* d, T* r, const T* sv, const T* dinv, int64_t n, T c1, T
   ProfScope prof(SE_K_CHEBY_UPD, s, (double)n, words * n * sizeof(T), 6.0 * n, prof_variant<T>(0));
   const unsigned g = grid_for(n, 256);
   const int key = (first ? 4 : 0) + (from_r ? 2 : 0) + (last ? 1 : 0);
+  const double C1 = (double)c1, C2 = (double)c2, SC = (double)scale;
+  const T k_d = T(1.0 + C1), k_r = T(SC * (1.0 + C1) + C2), c1s = T(C1 * SC), k_s = T(-SC);
+  const T k_sl = T(from_r ? -C2 * SC : -C2);
   switch (key) {
-#define SE_CHEB_CASE(K, F, R, L) \
-  case K: cheb_update_kernel<T, F, R, L><<<g, 256, 0, s>>>(x, d, r, sv, dinv, n, c1, c2, scale); break;
+#define SE_CHEB_CASE(K, F, R, L)                                                                 \
+  case K:                                                                                        \
+    cheb_update_kernel<T, F, R, L><<<g, 256, 0, s>>>(x, d, r, sv, dinv, n, c1, c2, scale, k_d, k_r, \
+                                                     c1s, k_s, k_sl);                            \
+    break;
     SE_CHEB_CASE(0, false, false, false) SE_CHEB_CASE(1, false, false, true)
     SE_CHEB_CASE(2, false, true, false) SE_CHEB_CASE(3, false, true, true)
     SE_CHEB_CASE(4, true, false, false) SE_CHEB_CASE(5, true, false, true)
