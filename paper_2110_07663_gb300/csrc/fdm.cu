@@ -444,7 +444,8 @@ __global__ void __launch_bounds__(512) fdm_kernel(int64_t E, int NE, const int* 
 //    depends only on p: the block tabulates it once in shared memory, and every element's
 //    gather is a table walk of cp.async copies, all in flight at once; the RAS outputs leave
 //    through shared memory as contiguous, coalesced stores.
-// Per output the arithmetic is one FMA chain over the contracted index in ascending order; D^-1
+// Per output the arithmetic is one FMA chain over the contracted index in ascending order (the
+// backward contractions: two, over even and odd indices, added at the end); D^-1
 // is applied as a product with the hardware reciprocal of lambda_x + lambda_y + lambda_z (one
 // rounding more than a division: far below the FP32 preconditioner's tolerance).
 __host__ __device__ constexpr int fdm32_plane_stride(int PB) {
@@ -468,42 +469,66 @@ struct Fdm32Dims {
   static_assert(PS * PB <= 4096 && N * N * N <= 2048, "window table fields overflow");
 };
 
-// acc[j][o] += S[r][o] x[j], o < PB: one padded row of S (float4 reads), NL lines.
+// The row contractions below use Blackwell's packed FP32 FMA (two lanes per instruction,
+// fma.rn.f32x2 through __ffma2_rn): this kernel is bound by instruction issue, not by the FMA
+// pipe, so halving the FMA instruction count is what shortens it.
+
+// acc[j][o] += S[r][o] x[j], o < PB: one padded row of S (float4 reads), NL lines; outputs in
+// pairs (o, o + 1).
 template <int PB, int PBP, int NL>
 __device__ __forceinline__ void fdm32_axpy_row(const float* __restrict__ row, const float (&x)[NL],
                                                float (&acc)[NL][PB]) {
 #pragma unroll
   for (int o4 = 0; o4 < PBP; o4 += 4) {
     const float4 s4 = *reinterpret_cast<const float4*>(row + o4);
-    const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (o4 + k < PB) {
+    for (int h = 0; h < 2; ++h) {
+      const int o = o4 + 2 * h;
+      const float2 s2 = h ? make_float2(s4.z, s4.w) : make_float2(s4.x, s4.y);
+      if (o + 1 < PB) {
 #pragma unroll
-        for (int j = 0; j < NL; ++j) acc[j][o4 + k] = fmaf(sv[k], x[j], acc[j][o4 + k]);
+        for (int j = 0; j < NL; ++j) {
+          const float2 a = __ffma2_rn(s2, make_float2(x[j], x[j]), make_float2(acc[j][o], acc[j][o + 1]));
+          acc[j][o] = a.x;
+          acc[j][o + 1] = a.y;
+        }
+      } else if (o < PB) {
+#pragma unroll
+        for (int j = 0; j < NL; ++j) acc[j][o] = fmaf(s2.x, x[j], acc[j][o]);
       }
     }
   }
 }
 
-// out[j] = sum_o S[r][o] v[j][o] (ascending o): one padded row of S, NL lines.
+// out[j] = sum_o S[r][o] v[j][o]: one padded row of S, NL lines; even and odd o accumulate in
+// the two lanes of a packed FMA (each in ascending o) and are added at the end.
 template <int PB, int PBP, int NL>
 __device__ __forceinline__ void fdm32_dot_row(const float* __restrict__ row, const float (&v)[NL][PB],
                                               float (&out)[NL]) {
+  float2 acc[NL];
 #pragma unroll
-  for (int j = 0; j < NL; ++j) out[j] = 0.f;
+  for (int j = 0; j < NL; ++j) acc[j] = make_float2(0.f, 0.f);
+  float tail[NL];
+#pragma unroll
+  for (int j = 0; j < NL; ++j) tail[j] = 0.f;
 #pragma unroll
   for (int o4 = 0; o4 < PBP; o4 += 4) {
     const float4 s4 = *reinterpret_cast<const float4*>(row + o4);
-    const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (o4 + k < PB) {
+    for (int h = 0; h < 2; ++h) {
+      const int o = o4 + 2 * h;
+      const float2 s2 = h ? make_float2(s4.z, s4.w) : make_float2(s4.x, s4.y);
+      if (o + 1 < PB) {
 #pragma unroll
-        for (int j = 0; j < NL; ++j) out[j] = fmaf(sv[k], v[j][o4 + k], out[j]);
+        for (int j = 0; j < NL; ++j) acc[j] = __ffma2_rn(s2, make_float2(v[j][o], v[j][o + 1]), acc[j]);
+      } else if (o < PB) {
+#pragma unroll
+        for (int j = 0; j < NL; ++j) tail[j] = s2.x * v[j][o];
       }
     }
   }
+#pragma unroll
+  for (int j = 0; j < NL; ++j) out[j] = (acc[j].x + acc[j].y) + tail[j];
 }
 
 // 4-byte asynchronous global -> shared copy; valid == false fills the word with zero and reads

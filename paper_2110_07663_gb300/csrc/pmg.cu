@@ -166,6 +166,20 @@ template <class T>
 int apply_typed(se_pmg_s* P, const double* r, double* z, cudaStream_t s) {
   LevelVecs<T>& V = P->vecs<T>(0);
   const int64_t L = P->lv[0]->L;
+  if constexpr (sizeof(T) == 8) {
+    // FP64: the V-cycle reads the finest right-hand side without writing it and writes only its
+    // result, so it runs on r and z themselves (no copies in or out) unless they are one vector
+    if (r != z) {
+      double* const b0 = V.b;
+      double* const x0 = V.x;
+      V.b = const_cast<double*>(r);
+      V.x = z;
+      const int st = vcycle<T>(P, 0, s);
+      V.b = b0;
+      V.x = x0;
+      return st;
+    }
+  }
   SE_TRY((convert<double, T>(r, V.b, L, s)));
   SE_TRY(vcycle<T>(P, 0, s));
   return convert<T, double>(V.x, z, L, s);
