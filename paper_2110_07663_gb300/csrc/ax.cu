@@ -107,6 +107,11 @@ int ax_elems_per_block(int p, bool fp32) {
   const int N = p + 1;
   const int t = tile_get(p, fp32).ax_ne;
   if (t >= 1 && t * N * N <= 512) return t;
+  // FP64 even N (the folded kernel): measured on GB300 at 32^3 elements, elements per block
+  // N = 4: 8 (16: 0.144 -> 0.138 ms), N = 6: 8 (7: 0.543 -> 0.525 ms), N = 10: 3 (2: 3.38 ->
+  // 3.26 ms); N = 8 keeps 4 (1 to 4 within 0.5%)
+  if (!fp32 && (N == 4 || N == 6)) return 8;
+  if (!fp32 && N == 10) return 3;
   const int ne = 256 / (N * N);
   return ne < 1 ? 1 : ne;
 }

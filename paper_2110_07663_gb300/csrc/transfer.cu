@@ -164,8 +164,13 @@ static int launch_transfer_eo(const Level& f, const T* J, const T* in, const uin
   constexpr int NI = RESTRICT ? NF : NC, NO = RESTRICT ? NC : NF;
   constexpr int A = (NI * NI * NI > NO * NO * NI ? NI * NI * NI : NO * NO * NI);
   constexpr int B = (NO * NI * NI > NO * NO * NO ? NO * NI * NI : NO * NO * NO);
-  // about 256 lines of the first direction per block
-  constexpr int NE = (256 / (NI * NI)) < 1 ? 1 : (256 / (NI * NI));
+  // about 256 lines of the first direction per block, and at most 96 KB of shared memory (the
+  // prolongation from N = 2 to 8 or 10 would need more than the 200 KB a block may have)
+  constexpr int NE_LINES = (256 / (NI * NI)) < 1 ? 1 : (256 / (NI * NI));
+  constexpr int NE_SMEM = (int)((96 * 1024) / ((A + B) * sizeof(T))) < 1 ? 1 : (int)((96 * 1024) / ((A + B) * sizeof(T)));
+  constexpr int NE = NE_LINES < NE_SMEM ? NE_LINES : NE_SMEM;
+  static_assert((2 * (NO / 2) * (NI / 2) + (size_t)NE * (A + B)) * sizeof(T) <= 200 * 1024,
+                "transfer block exceeds the shared memory limit");
   const size_t smem = (2 * (NO / 2) * (NI / 2) + (size_t)NE * (A + B)) * sizeof(T);
   static const cudaError_t attr = cudaFuncSetAttribute(
       transfer_eo_kernel<T, NF, NC, RESTRICT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
