@@ -151,6 +151,26 @@ def test_fp32_schwarz_smoother_all_orders(p, smoother):
         c.close()
 
 
+@pytest.mark.parametrize("p", range(2, 11))
+@pytest.mark.parametrize("smoother", ["ras", "asm", "jacobi"])
+def test_fp64_smoother_all_orders(p, smoother):
+    """FP64 smoothers (Schwarz: window gather, FDM, RAS weights or ASM combine, QQ^T; Jacobi)
+    and their Arnoldi bound at every order the library takes, odd and even p, on 12 elements
+    with mixed boundary conditions, against the oracle at the FP64 smoother bar 1e-10."""
+    bc = ("D", "N", "D", "D", "N", "D")
+    c, P, pmg = build((3, 2, 2), p, (p, 1), smoother, bc=bc)
+    try:
+        r = c.random_continuous(195 + p)
+        out = c.empty()
+        c.se.se_pmg_smooth(P, 0, c.to_gpu(r), out)
+        assert rel_err(c.to_np(out), o.smoother_op(pmg, 0)(r)) <= 1e-10
+        lam = c.se.se_pmg_lambda(P, 0)
+        assert abs(lam - pmg.lam[0]) <= 1e-9 * pmg.lam[0]
+    finally:
+        c.se.se_pmg_destroy(P)
+        c.close()
+
+
 def test_fp32_ras_mixed_boundaries():
     bc = ("D", "N", "N", "D", "N", "D")
     c, P, pmg = build((2, 3, 2), 7, (7, 3, 1), "ras", precision=1, bc=bc)
