@@ -94,6 +94,31 @@ def test_handle_on_arbitrary_connectivity(seed):
         se.se_gsmap_destroy(g)
 
 
+@pytest.mark.parametrize("case", ["one_node_1000_copies", "single_point", "single_masked_point",
+                                  "no_shared_node"])
+def test_handle_degenerate_maps(case):
+    """Degenerate numberings: one global node shared by every local point (one CSR group of 1000
+    copies), a single local point with and without the Dirichlet flag, and no shared node."""
+    torch, se = gpu()
+    gid, dirichlet = {
+        "one_node_1000_copies": (np.zeros(1000, dtype=np.int64), None),
+        "single_point": (np.array([7]), None),
+        "single_masked_point": (np.array([7]), np.array([1], dtype=np.uint8)),
+        "no_shared_node": (np.arange(50) * 3, (np.arange(50) % 2).astype(np.uint8)),
+    }[case]
+    g = se.se_gsmap_create(gid, dirichlet)
+    try:
+        assert se.se_gsmap_info(g) == se.se_gsmap_count(gid, dirichlet)
+        u = wl.random_lvector(gid.size, 3)
+        _, comp = np.unique(gid, return_inverse=True)
+        for mask in (0, 1):
+            t = torch.from_numpy(u.copy()).cuda()
+            se.se_gsmap_apply(g, t, mask)
+            assert np.array_equal(t.cpu().numpy(), qqt_reference(comp, u, dirichlet, bool(mask)))
+    finally:
+        se.se_gsmap_destroy(g)
+
+
 def gpu_problem(c):
     xyz = c.empty(3 * c.info.L)
     c.se.se_mesh_nodes(c.m, xyz)
