@@ -134,7 +134,8 @@ int se_gs(se_mesh_t m, double* u, int mask, void* stream);
  * (int32, so L < 2^31), bucketed by multiplicity (2, 4, 8 and other counts), plus the single
  * copies of Dirichlet nodes; the copies are summed in ascending local id order from the first, so
  * the result equals the sequential sum in local-id order bitwise.  The handle owns its device
- * memory and stream (non-blocking).  Errors: SE_EINVAL for L outside [1, 2^31), a null gid or a
+ * memory and its stream (blocking, like a mesh's: stream == NULL orders the call with the legacy
+ * default stream).  Errors: SE_EINVAL for L outside [1, 2^31), a null gid or a
  * negative id (checked before any device work), SE_ENOMEM, SE_ECUDA. */
 typedef struct se_gsmap_s* se_gsmap_t;
 int se_gsmap_create(int64_t L, const int64_t* gid, const uint8_t* dirichlet, se_gsmap_t* out);

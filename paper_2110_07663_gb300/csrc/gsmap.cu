@@ -292,7 +292,9 @@ int se_gsmap_create(int64_t L, const int64_t* gid, const uint8_t* dirichlet, se_
   SE_TRY(gsmap_build_host(L, gid, dirichlet, h));  // validates before any device work
   se_gsmap_s* g = new (std::nothrow) se_gsmap_s();
   SE_CHECK(g != nullptr, SE_ENOMEM, "se_gsmap_create: out of host memory");
-  if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess) {
+  // a blocking stream, as for meshes: work the caller enqueues with stream == NULL is ordered with
+  // the legacy default stream
+  if (cudaStreamCreateWithFlags(&g->stream, cudaStreamDefault) != cudaSuccess) {
     delete g;
     set_error("se_gsmap_create: stream creation failed");
     return SE_ECUDA;
