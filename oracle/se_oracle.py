@@ -591,6 +591,7 @@ class PMG:
     coarse_tol: float = 1e-4
     coarse_maxit: int = 500
     coarse_iters: list = field(default_factory=list)
+    cycle: str = "mult"      # 'mult' (Algorithm 1) or 'additive' (Sec. 2.2.2, no Chebyshev)
 
 
 def smoother_op(pmg, l):
@@ -604,7 +605,7 @@ def smoother_op(pmg, l):
 
 def pmg_setup(V, nel, schedule, smoother="ras", order=2, bc=("D",) * 6, amp=0.05,
               eig_lo=0.1, eig_hi=1.1, arnoldi_steps=10, seed=0, coarse_tol=1e-4, coarse_maxit=500,
-              start_vectors=None):
+              start_vectors=None, cycle="mult"):
     """Levels of the schedule, smoother data and Chebyshev bounds (Secs. 2.2.2-2.2.3).
 
     READING: every level is rediscretised on the same mapped mesh at its own order (geometry
@@ -618,7 +619,7 @@ def pmg_setup(V, nel, schedule, smoother="ras", order=2, bc=("D",) * 6, amp=0.05
     for lv in levels:
         lv.extra["diag"] = jacobi_diag(lv)
     pmg = PMG(levels=levels, smoother=smoother, order=list(orders), bounds=[], lam=[],
-              coarse_tol=coarse_tol, coarse_maxit=coarse_maxit)
+              coarse_tol=coarse_tol, coarse_maxit=coarse_maxit, cycle=cycle)
     for l, lv in enumerate(levels[:-1]):
         if smoother in ("ras", "asm"):
             lv.extra["fdm"] = fdm_setup(lv, V, amp)
@@ -645,8 +646,25 @@ def coarse_solve(pmg, b):
     return x
 
 
+def vcycle_additive(pmg, b, l=0):
+    """Additive V-cycle (Sec. 2.2.2): with ASM or RAS smoothers without Chebyshev acceleration
+    the paper applies the smoother and the coarse correction to the same residual, with no
+    post-smoothing, so that the residual is not re-evaluated:  x = S b + P V(P^T b).
+    READING: S is the smoother itself (no Chebyshev polynomial, no 1/theta scaling); the same
+    rule applies on every level, the coarsest solved as in Algorithm 1."""
+    if l == len(pmg.levels) - 1:
+        return coarse_solve(pmg, b)
+    lv, lc = pmg.levels[l], pmg.levels[l + 1]
+    x = smoother_op(pmg, l)(b)                                # smooth the residual itself
+    ec = vcycle_additive(pmg, restrict(lv, lc, b), l + 1)     # coarse correction of the same b
+    return x + prolong(lv, lc, ec)
+
+
 def vcycle(pmg, b, l=0):
-    """Algorithm 1 with x = 0 on entry; M is the Chebyshev-accelerated smoother of Algorithm 2."""
+    """Algorithm 1 with x = 0 on entry; M is the Chebyshev-accelerated smoother of Algorithm 2.
+    A preconditioner set up with cycle='additive' runs vcycle_additive instead."""
+    if pmg.cycle == "additive":
+        return vcycle_additive(pmg, b, l)
     if l == len(pmg.levels) - 1:
         return coarse_solve(pmg, b)
     lv = pmg.levels[l]

@@ -310,3 +310,56 @@ def test_projection_guess_is_the_a_orthogonal_projection():
     for x in xs:
         assert err(g + 1e-3 * x) > err(g) and err(g - 1e-3 * x) > err(g)
     assert np.array_equal(o.projection_guess(lv, [], b), np.zeros_like(b))
+
+
+def map_matrix(lin, lout, fn):
+    """Matrix of a linear map between continuous L-vectors of two levels, on free global nodes."""
+    cin, cout = free_nodes(lin), free_nodes(lout)
+    M = np.zeros((len(cout), len(cin)))
+    for n, g in enumerate(cin):
+        ug = np.zeros(lin.n_global)
+        ug[g] = 1.0
+        M[:, n] = o.to_global(lout, fn(lin.mask * o.from_global(lin, ug)))[cout]
+    return M
+
+
+@pytest.mark.parametrize("smoother", ["ras", "asm"])
+def test_additive_vcycle_is_the_sum_of_subspace_corrections(smoother):
+    """Sec. 2.2.2: without Chebyshev acceleration the Schwarz smoothers use an additive V-cycle,
+    smoother and coarse correction applied to the same residual with no post-smoothing.  With an
+    exact coarse solve its operator is the sum of the level corrections,
+    M = S_0 + P_0 (S_1 + P_1 A_c^-1 P_1^T) P_0^T, built here from the dense matrices of each
+    step; the multiplicative cycle of Algorithm 1 is a different operator."""
+    nel = (3, 2, 2)
+    V = wl.vertex_lattice(nel, 0.05, seed=8)
+    pmg = o.pmg_setup(V, nel, (3, 2, 1), smoother=smoother, order=2, coarse_tol=1e-14,
+                      coarse_maxit=2000, cycle="additive")
+    l0, l1, l2 = pmg.levels
+    S0 = map_matrix(l0, l0, o.smoother_op(pmg, 0))
+    S1 = map_matrix(l1, l1, o.smoother_op(pmg, 1))
+    R0 = map_matrix(l0, l1, lambda r: o.restrict(l0, l1, r))
+    R1 = map_matrix(l1, l2, lambda r: o.restrict(l1, l2, r))
+    P0 = map_matrix(l1, l0, lambda e: o.prolong(l0, l1, e))
+    P1 = map_matrix(l2, l1, lambda e: o.prolong(l1, l2, e))
+    Ac = map_matrix(l2, l2, lambda u: o.ax(l2, u))
+    Mdef = S0 + P0 @ (S1 + P1 @ np.linalg.solve(Ac, R1)) @ R0
+    Madd = map_matrix(l0, l0, lambda r: o.vcycle(pmg, r))
+    assert np.allclose(Madd, Mdef, rtol=0, atol=1e-10 * np.abs(Mdef).max())
+    pmg.cycle = "mult"
+    Mmult = map_matrix(l0, l0, lambda r: o.vcycle(pmg, r))
+    assert not np.allclose(Mmult, Mdef, rtol=0, atol=1e-3 * np.abs(Mdef).max())
+
+
+@pytest.mark.parametrize("method", ["fpcg", "fgmres"])
+@pytest.mark.parametrize("pre", ["ras", "asm"])
+def test_additive_cycle_solution_matches_direct_solve(mg_case, method, pre):
+    V, nel = mg_case
+    lv, b = o.problem(V, nel, 5)
+    pmg = o.pmg_setup(V, nel, (5, 3, 1), smoother=pre, order=0, cycle="additive")
+    xsol, it, rel = o.solve(lv, b, pmg, method=method, tol=1e-10)
+    assert rel <= 1e-10 and it < 400
+    cols = free_nodes(lv)
+    xg, wg = o.gll(5)
+    Af = assembled_stiffness(lv, xg, wg)[np.ix_(cols, cols)]
+    xd = np.linalg.solve(Af, o.to_global(lv, b)[cols])
+    assert np.allclose(o.to_global(lv, xsol)[cols], xd, rtol=0, atol=1e-8 * np.abs(xd).max())
