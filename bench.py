@@ -231,7 +231,9 @@ def run_gpu(args):
     else:
         smoother = {"ras": se.SE_SMOOTH_RAS, "jacobi": se.SE_SMOOTH_JACOBI, "asm": se.SE_SMOOTH_ASM}[args.smoother]
         cheb_order = args.cheb_order
-        P = se.se_pmg_setup(m, se.pmg_desc(wk["schedule"], smoother, cheb_order, precision=prec))
+        P = se.se_pmg_setup(m, se.pmg_desc(wk["schedule"], smoother, cheb_order, precision=prec,
+                                           cycle=se.SE_CYCLE_ADDITIVE if args.cycle == "additive"
+                                           else se.SE_CYCLE_MULTIPLICATIVE))
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t_setup0
     x = torch.zeros(L, dtype=torch.float64, device=dev)
@@ -339,8 +341,9 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {"workload": f"{args.workload}: deformed box {nel[0]}x{nel[1]}x{nel[2]} hex, p={p}, "
                                f"n={n_dof} (E p^3), pMG {'-'.join(map(str, wk['schedule']))} "
-                               f"Cheby-{sm_names[smoother]}({cheb_order}), "
-                               f"FPCG tol 1e-8, {prec_name} preconditioner, {op_name} outer operator",
+                               + (f"{sm_names[smoother]}, additive V-cycle (no Chebyshev), " if args.cycle == "additive"
+                                  else f"Cheby-{sm_names[smoother]}({cheb_order}), ")
+                               + f"FPCG tol 1e-8, {prec_name} preconditioner, {op_name} outer operator",
                    "iterations": iters, "setup_s": round(setup_s, 2),
                    "preconditioner_choice": ("run-time search (Sec. 5) over Cheby-RAS(k), Cheby-Jac(k), "
                                              "k = 1..3, inside set-up" if search else "fixed by --smoother"),
@@ -877,6 +880,9 @@ def main():
     ap.add_argument("--smoother", default="auto", choices=["auto", "ras", "jacobi", "asm"],
                     help="auto: the run-time preconditioner search over Cheby-RAS(k), Cheby-Jac(k)")
     ap.add_argument("--cheb-order", type=int, default=2)
+    ap.add_argument("--cycle", default="mult", choices=["mult", "additive"],
+                    help="additive: the additive V-cycle of Schwarz smoothers without Chebyshev "
+                         "(needs --smoother ras or asm)")
     ap.add_argument("--precond-fp32", action="store_true")
     ap.add_argument("--gs-map", action="store_true",
                     help="QQ^T of every level from the sorted index map instead of the sweeps")

@@ -175,7 +175,14 @@ typedef struct se_pmg_desc {
                                     apply the operator and FDM kernels in double-float (FP64
                                     vectors; df64 copies of the level data exist
                                     only during the set-up).  SE_DF64 always does. */
+  int cycle;                     /* SE_CYCLE_MULTIPLICATIVE (0): Algorithm 1 with the Chebyshev
+                                    smoother.  SE_CYCLE_ADDITIVE (1): the additive V-cycle the
+                                    paper uses for Schwarz smoothers without Chebyshev
+                                    acceleration (Sec. 2.2.2): on every level x = S b + P V(P^T b),
+                                    S the smoother itself (cheb_order, eig_lo/hi unused), no
+                                    residual re-evaluation, no post-smoothing. */
 } se_pmg_desc;
+enum { SE_CYCLE_MULTIPLICATIVE = 0, SE_CYCLE_ADDITIVE = 1 };
 
 /* Builds the levels (each rediscretised on the same mapped mesh), Jacobi diagonals, FDM
  * factors S and Lambda (eqs 6-7), the assembled coarsest operator, and the Chebyshev bounds

@@ -162,6 +162,28 @@ int vcycle(se_pmg_s* P, int l, cudaStream_t s) {
   return cheby<T>(P, l, V.r, V.x, false, s);                    // x += M (b - A x)
 }
 
+// Additive V-cycle on level l (Sec. 2.2.2, Schwarz smoothers without Chebyshev acceleration):
+// the smoother and the coarse correction act on the same right-hand side, x = S b + P V(P^T b),
+// with no residual re-evaluation and no post-smoothing.
+template <class T>
+int vcycle_additive(se_pmg_s* P, int l, cudaStream_t s) {
+  LevelVecs<T>& V = P->vecs<T>(l);
+  const Level& lv = *P->lv[l];
+  if (l == P->nlev - 1)
+    return coarse_solve<T>(lv, P->cw, V.b, V.x, P->desc.coarse_tol, P->desc.coarse_maxit, s);
+  LevelVecs<T>& C = P->vecs<T>(l + 1);
+  const Level& lc = *P->lv[l + 1];
+  SE_TRY(smooth<T>(P, l, V.b, V.x, s));                          // x = S b
+  SE_TRY(restrict_apply<T>(lv, lc, jmat<T>(P, l), V.b, C.b, s)); // r_C = P^T b
+  SE_TRY(vcycle_additive<T>(P, l + 1, s));                       // e_C
+  return prolong_apply<T>(lv, lc, jmat<T>(P, l), C.x, V.x, true, s);  // x += P e_C
+}
+
+template <class T>
+int cycle(se_pmg_s* P, cudaStream_t s) {
+  return P->desc.cycle == SE_CYCLE_ADDITIVE ? vcycle_additive<T>(P, 0, s) : vcycle<T>(P, 0, s);
+}
+
 template <class T>
 int apply_typed(se_pmg_s* P, const double* r, double* z, cudaStream_t s) {
   LevelVecs<T>& V = P->vecs<T>(0);
@@ -174,14 +196,14 @@ int apply_typed(se_pmg_s* P, const double* r, double* z, cudaStream_t s) {
       double* const x0 = V.x;
       V.b = const_cast<double*>(r);
       V.x = z;
-      const int st = vcycle<T>(P, 0, s);
+      const int st = cycle<T>(P, s);
       V.b = b0;
       V.x = x0;
       return st;
     }
   }
   SE_TRY((convert<double, T>(r, V.b, L, s)));
-  SE_TRY(vcycle<T>(P, 0, s));
+  SE_TRY(cycle<T>(P, s));
   return convert<T, double>(V.x, z, L, s);
 }
 
@@ -443,6 +465,8 @@ int se_pmg_setup(se_mesh_t m, const se_pmg_desc* desc, se_pmg_t* out) {
   SE_CHECK(d.coarse_tol > 0 && d.coarse_maxit >= 1, SE_EINVAL, "se_pmg_setup: coarse tolerance");
   SE_CHECK(d.precision == SE_FP64 || d.precision == SE_FP32 || d.precision == SE_DF64, SE_EINVAL,
            "se_pmg_setup: precision");
+  SE_CHECK(d.cycle == SE_CYCLE_MULTIPLICATIVE || d.cycle == SE_CYCLE_ADDITIVE, SE_EINVAL,
+           "se_pmg_setup: cycle %d", d.cycle);
   SE_CHECK(d.arnoldi_df64 == 0 || d.arnoldi_df64 == 1, SE_EINVAL, "se_pmg_setup: arnoldi_df64");
   static std::atomic<uint64_t> next_uid{0};
   auto* P = new se_pmg_s();

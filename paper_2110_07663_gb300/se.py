@@ -17,6 +17,7 @@ SE_OK, SE_EINVAL, SE_ENOMEM, SE_ENOTCONV, SE_ECUDA, SE_ETIMEOUT, SE_EBUSY, SE_ER
 SE_BC_DIRICHLET, SE_BC_NEUMANN = 0, 1
 SE_FP64, SE_FP32, SE_DF64 = 0, 1, 2
 SE_SMOOTH_JACOBI, SE_SMOOTH_RAS, SE_SMOOTH_ASM = 0, 1, 2
+SE_CYCLE_MULTIPLICATIVE, SE_CYCLE_ADDITIVE = 0, 1
 SE_FPCG, SE_FGMRES = 0, 1
 SE_TOL_R0, SE_TOL_B = 0, 1
 SE_AX_ASSEMBLE, SE_AX_MASK, SE_AX_FP32, SE_AX_DF64 = 1, 2, 4, 8
@@ -54,7 +55,7 @@ class se_pmg_desc(C.Structure):
                 ("cheb_order", C.c_int * SE_MAX_LEVELS), ("eig_lo", C.c_double),
                 ("eig_hi", C.c_double), ("arnoldi_steps", C.c_int), ("seed", C.c_uint64),
                 ("coarse_tol", C.c_double), ("coarse_maxit", C.c_int), ("precision", C.c_int),
-                ("arnoldi_df64", C.c_int)]
+                ("arnoldi_df64", C.c_int), ("cycle", C.c_int)]
 
 
 class se_solve_opts(C.Structure):
@@ -323,7 +324,7 @@ def se_jacobi_diag(m, d, stream=None):
 # ----------------------------------------------------------------------------- p-multigrid
 def pmg_desc(schedule, smoother=SE_SMOOTH_RAS, cheb_order=2, eig_lo=0.1, eig_hi=1.1,
              arnoldi_steps=10, seed=0, coarse_tol=1e-4, coarse_maxit=500, precision=SE_FP64,
-             arnoldi_df64=0):
+             arnoldi_df64=0, cycle=SE_CYCLE_MULTIPLICATIVE):
     d = se_pmg_desc()
     d.nlev = len(schedule)
     d.schedule[:len(schedule)] = list(schedule)
@@ -336,6 +337,7 @@ def pmg_desc(schedule, smoother=SE_SMOOTH_RAS, cheb_order=2, eig_lo=0.1, eig_hi=
     d.coarse_tol, d.coarse_maxit = coarse_tol, coarse_maxit
     d.precision = precision
     d.arnoldi_df64 = arnoldi_df64
+    d.cycle = cycle
     return d
 
 

@@ -6,6 +6,8 @@ on the GPU, LAPACK eigh in the oracle; the FDM result is invariant to them up to
 times the local condition number); lambda-tilde 1e-9; V-cycle 1e-8 when both coarse solves
 take the same number of iterations.  FP32 preconditioner against the FP64 oracle: 1e-4.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -109,6 +111,58 @@ def test_fp32_vcycle_against_fp64_oracle(smoother):
         assert abs(c.se.se_pmg_lambda(P, 0) - pmg.lam[0]) <= 1e-9 * pmg.lam[0]
     finally:
         c.se.se_pmg_destroy(P)
+        c.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+@pytest.mark.parametrize("smoother", ["ras", "asm"])
+def test_additive_vcycle_against_oracle(smoother, precision):
+    """The additive V-cycle (Sec. 2.2.2: Schwarz smoothers without Chebyshev acceleration,
+    x = S b + P V(P^T b), no post-smoothing) through se_pmg_apply, against the oracle's:
+    FP64 and df64 within the V-cycle bar 1e-6 (the coarse Jacobi-PCG iterations may differ by
+    one), the FP32 V-cycle within 1e-4."""
+    nel, p, sched = (3, 2, 2), 7, (7, 3, 1)
+    c = Case(nel, p, seed=3)
+    se = c.se
+    P = se.se_pmg_setup(c.m, se.pmg_desc(sched, SMOOTHERS[smoother], 0, precision=precision,
+                                          cycle=se.SE_CYCLE_ADDITIVE))
+    pmg = o.pmg_setup(c.V, nel, sched, smoother=smoother, order=0, amp=c.amp, cycle="additive")
+    try:
+        r = c.random_continuous(77)
+        z = c.empty()
+        se.se_pmg_apply(P, c.to_gpu(r), z)
+        assert rel_err(c.to_np(z), o.vcycle(pmg, r)) <= (1e-4 if precision == 1 else 1e-6)
+    finally:
+        se.se_pmg_destroy(P)
+        c.close()
+
+
+@pytest.mark.parametrize("method", ["fpcg", "fgmres"])
+def test_additive_vcycle_solve(method):
+    """FPCG / FGMRES(20) preconditioned by the additive RAS cycle on the 4^3 p = 7 box: the
+    oracle's iteration count within one, the tolerance met by the true residual."""
+    c = Case((4, 4, 4), 7, pert=0.0)
+    se = c.se
+    sched = (7, 3, 1)
+    P = se.se_pmg_setup(c.m, se.pmg_desc(sched, se.SE_SMOOTH_RAS, 0, cycle=se.SE_CYCLE_ADDITIVE))
+    try:
+        xyz = c.empty(3 * c.info.L)
+        se.se_mesh_nodes(c.m, xyz)
+        X = xyz.cpu().numpy().reshape(3, -1)
+        b = c.empty()
+        se.se_mesh_rhs(c.m, c.to_gpu(wl.f_rhs(X[0], X[1], X[2])), b)
+        x = c.empty().zero_()
+        meth = se.SE_FPCG if method == "fpcg" else se.SE_FGMRES
+        st = se.se_solve(c.m, P, b, x, method=meth, tol=1e-8, maxit=500, restart=20)
+        lvo, bo = o.problem(c.V, c.nel, c.p, amp=c.amp)
+        pmg = o.pmg_setup(c.V, c.nel, sched, smoother="ras", order=0, amp=c.amp, cycle="additive")
+        xo, it_o, _ = o.solve(lvo, bo, pmg, method=method, tol=1e-8, maxit=500)
+        assert abs(st.iterations - it_o) <= 1, (st.iterations, it_o)
+        r = bo - o.ax(lvo, c.to_np(x))
+        assert math.sqrt(o.dot(lvo, r, r) / o.dot(lvo, bo, bo)) <= 1.5e-8
+        assert rel_err(c.to_np(x), xo) <= 1e-5
+    finally:
+        se.se_pmg_destroy(P)
         c.close()
 
 
