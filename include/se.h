@@ -43,7 +43,8 @@ enum se_status {
   SE_ECUDA = 4,     /* a CUDA runtime call failed; se_last_error() names it */
   SE_ETIMEOUT = 5,  /* a bounded device-side wait ran out (no hang: the kernel returned) */
   SE_EBUSY = 6,     /* served request still pending */
-  SE_EREFUSED = 7   /* served request can never fit the HBM budget */
+  SE_EREFUSED = 7,  /* served request can never fit the HBM budget */
+  SE_ECANCELED = 8  /* served request removed from the queue by se_serve_cancel before it started */
 };
 
 enum { SE_BC_DIRICHLET = 0, SE_BC_NEUMANN = 1 };
@@ -405,6 +406,7 @@ typedef struct se_serve_stats {
   int64_t meshes_created, mesh_reuses, evictions;
   size_t resident_bytes;
   int64_t projected;       /* requests that started from a non-zero projected guess */
+  int64_t cancelled;       /* requests removed from the queue by se_serve_cancel */
 } se_serve_summary;
 typedef struct se_server_s* se_server_t;
 int se_serve_create(const se_serve_cfg* cfg, se_server_t* out);
@@ -415,6 +417,11 @@ int se_serve_submit(se_server_t s, const se_request* req, uint64_t* ticket);
 int se_serve_poll(se_server_t s, uint64_t ticket, se_result* res);
 /* Blocks up to timeout_ms (SE_ETIMEOUT if still pending). */
 int se_serve_wait(se_server_t s, uint64_t ticket, double timeout_ms, se_result* res);
+/* Cancels a request that is still queued (not yet admitted: no mesh set-up or solve of it has
+ * started): SE_OK, and its result then carries status SE_ECANCELED.  A request whose set-up or
+ * solve has started is not interrupted: SE_EBUSY, and it completes normally.  SE_EINVAL for an
+ * unknown ticket or one that has finished. */
+int se_serve_cancel(se_server_t s, uint64_t ticket);
 int se_serve_stats(se_server_t s, se_serve_summary* out);
 /* Stops the scheduler, waits for running solves, frees every resident mesh. */
 int se_serve_destroy(se_server_t s);

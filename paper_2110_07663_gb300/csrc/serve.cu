@@ -113,7 +113,7 @@ struct se_server_s {
   std::vector<se::Resident*> residents;
   size_t used = 0;
   int64_t submitted = 0, completed = 0, refused = 0, failed = 0, created = 0, reused = 0,
-          evicted = 0, projected = 0;
+          evicted = 0, projected = 0, cancelled = 0;
   int max_running = 0;
   double t_first = 0, t_last = 0;
   std::vector<double> latencies;
@@ -474,6 +474,28 @@ int se_serve_wait(se_server_t S, uint64_t ticket, double timeout_ms, se_result* 
   return t->status;
 }
 
+int se_serve_cancel(se_server_t S, uint64_t ticket) {
+  SE_CHECK(S, SE_EINVAL, "se_serve_cancel: null server");
+  std::lock_guard<std::mutex> g(S->mu);
+  auto it = S->tickets.find(ticket);
+  SE_CHECK(it != S->tickets.end(), SE_EINVAL, "se_serve_cancel: unknown ticket %llu",
+           (unsigned long long)ticket);
+  Ticket* t = it->second;
+  SE_CHECK(!t->done, SE_EINVAL, "se_serve_cancel: ticket %llu has finished", (unsigned long long)ticket);
+  auto q = std::find(S->queue.begin(), S->queue.end(), t);
+  if (q == S->queue.end()) {
+    set_error("se_serve_cancel: ticket %llu has started", (unsigned long long)ticket);
+    return SE_EBUSY;  // being built or solved: it completes normally
+  }
+  S->queue.erase(q);
+  t->status = SE_ECANCELED;
+  t->t_done = now_ms();
+  t->done = true;
+  ++S->cancelled;
+  S->cv.notify_all();
+  return SE_OK;
+}
+
 int se_serve_stats(se_server_t S, se_serve_summary* out) {
   SE_CHECK(S && out, SE_EINVAL, "se_serve_stats: null argument");
   std::lock_guard<std::mutex> g(S->mu);
@@ -502,6 +524,7 @@ int se_serve_stats(se_server_t S, se_serve_summary* out) {
   out->evictions = S->evicted;
   out->resident_bytes = S->used;
   out->projected = S->projected;
+  out->cancelled = S->cancelled;
   return SE_OK;
 }
 

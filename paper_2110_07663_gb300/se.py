@@ -13,7 +13,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libse.so")
 
-SE_OK, SE_EINVAL, SE_ENOMEM, SE_ENOTCONV, SE_ECUDA, SE_ETIMEOUT, SE_EBUSY, SE_EREFUSED = range(8)
+SE_OK, SE_EINVAL, SE_ENOMEM, SE_ENOTCONV, SE_ECUDA, SE_ETIMEOUT, SE_EBUSY, SE_EREFUSED, SE_ECANCELED = range(9)
 SE_BC_DIRICHLET, SE_BC_NEUMANN = 0, 1
 SE_FP64, SE_FP32, SE_DF64 = 0, 1, 2
 SE_SMOOTH_JACOBI, SE_SMOOTH_RAS, SE_SMOOTH_ASM = 0, 1, 2
@@ -30,7 +30,7 @@ KERNEL_NAMES = ["ax", "gs", "fdm", "cheby_update", "restrict", "prolong", "coars
                 "jacobi"]
 
 STATUS_NAMES = {0: "SE_OK", 1: "SE_EINVAL", 2: "SE_ENOMEM", 3: "SE_ENOTCONV", 4: "SE_ECUDA",
-                5: "SE_ETIMEOUT", 6: "SE_EBUSY", 7: "SE_EREFUSED"}
+                5: "SE_ETIMEOUT", 6: "SE_EBUSY", 7: "SE_EREFUSED", 8: "SE_ECANCELED"}
 
 
 class SeError(RuntimeError):
@@ -97,7 +97,7 @@ class se_serve_summary(C.Structure):
                 ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("mean_ms", C.c_double),
                 ("max_concurrent", C.c_int), ("meshes_created", C.c_int64),
                 ("mesh_reuses", C.c_int64), ("evictions", C.c_int64), ("resident_bytes", C.c_size_t),
-                ("projected", C.c_int64)]
+                ("projected", C.c_int64), ("cancelled", C.c_int64)]
 
 
 class se_solve_stats(C.Structure):
@@ -170,6 +170,7 @@ _SIGS = {
     "se_serve_poll": ([_vp, C.c_uint64, C.POINTER(se_result)], C.c_int),
     "se_serve_wait": ([_vp, C.c_uint64, C.c_double, C.POINTER(se_result)], C.c_int),
     "se_serve_stats": ([_vp, C.POINTER(se_serve_summary)], C.c_int),
+    "se_serve_cancel": ([_vp, C.c_uint64], C.c_int),
     "se_serve_destroy": ([_vp], C.c_int),
     "se_prof_enable": ([_ip], C.c_int),
     "se_prof_reset": ([], C.c_int),
@@ -574,7 +575,7 @@ def se_serve_poll(S, ticket):
     """(status, se_result) with status SE_EBUSY while pending."""
     r = se_result()
     rc = lib.se_serve_poll(S, ticket, C.byref(r))
-    if rc not in (SE_OK, SE_EBUSY, SE_ENOTCONV):
+    if rc not in (SE_OK, SE_EBUSY, SE_ENOTCONV, SE_ECANCELED):
         raise SeError(rc, se_last_error())
     return rc, r
 
@@ -583,6 +584,12 @@ def se_serve_wait(S, ticket, timeout_ms=60000.0, allow=()):
     r = se_result()
     _check(lib.se_serve_wait(S, ticket, timeout_ms, C.byref(r)), allow=allow)
     return r
+
+
+def se_serve_cancel(S, ticket) -> int:
+    """SE_OK if the queued request was removed (its result: SE_ECANCELED), SE_EBUSY if it has
+    started (it completes normally)."""
+    return _check(lib.se_serve_cancel(S, ticket), allow=(SE_EBUSY,))
 
 
 def se_serve_stats(S) -> se_serve_summary:

@@ -96,6 +96,40 @@ def test_budget_refusal_and_eviction():
         se.se_serve_destroy(S)
 
 
+def test_cancel_queued_request():
+    """A request still in the queue is removed by se_serve_cancel (result SE_ECANCELED, no solve);
+    one that has started is not interrupted (SE_EBUSY) and completes; finished or unknown tickets
+    are rejected (SE_EINVAL).  One slot: the first request's mesh set-up holds it while the
+    others wait in the queue."""
+    import time
+    torch, se = gpu()
+    pd = se.pmg_desc((7, 3, 1), se.SE_SMOOTH_RAS, 2, precision=se.SE_FP32)
+    pd9 = se.pmg_desc((9, 5, 1), se.SE_SMOOTH_RAS, 2, precision=se.SE_FP32)
+    big = se.mesh_desc((40, 40, 40), 9, perturb_frac=0.05, seed=41)  # set-up about 0.4 s
+    small = [se.mesh_desc((4, 4, 4), 7, perturb_frac=0.05, seed=42 + k) for k in range(2)]
+    S = se.se_serve_create(se.se_mesh_footprint_bytes(big, pd9) * 4, 1)
+    try:
+        t1 = se.se_serve_submit(S, se.make_request(big, 301, pd9))
+        t2 = se.se_serve_submit(S, se.make_request(small[0], 302, pd))
+        t3 = se.se_serve_submit(S, se.make_request(small[1], 303, pd))
+        assert se.se_serve_cancel(S, t3) == se.SE_OK
+        r3 = se.se_serve_wait(S, t3, allow=(se.SE_ECANCELED,))
+        assert r3.status == se.SE_ECANCELED and r3.iterations == 0
+        time.sleep(0.1)  # the scheduler admits within milliseconds; the set-up takes longer
+        assert se.se_serve_cancel(S, t1) == se.SE_EBUSY
+        r1, r2 = se.se_serve_wait(S, t1), se.se_serve_wait(S, t2)
+        assert r1.status == 0 and r1.rel_residual <= 1e-8
+        assert r2.status == 0 and r2.rel_residual <= 1e-8
+        for t in (t1, t3, 987654):
+            with pytest.raises(se.SeError) as e:
+                se.se_serve_cancel(S, t)
+            assert e.value.code == se.SE_EINVAL
+        st = se.se_serve_stats(S)
+        assert st.cancelled == 1 and st.completed == 2 and st.pending == 0
+    finally:
+        se.se_serve_destroy(S)
+
+
 def test_projection_in_the_server():
     """Requests on one resident mesh with right-hand sides from a small space: with projection
     (proj_vectors = 4) later requests start from the projected guess and need (almost) no
