@@ -448,6 +448,10 @@ int se_prof_query_variant(int kind, int variant, double* ms_total, int64_t* laun
  * block can ever pass it; each block gives up after timeout_ms and the call returns
  * SE_ETIMEOUT.  Checks the wait-limit path without hanging the GPU. */
 int se_selftest_wait_timeout(double timeout_ms);
+/* Host-side fault injection for the allocation failure paths: the n-th device allocation the
+ * library makes after this call (n >= 1) fails with SE_ENOMEM before any CUDA call, as if the
+ * device were out of memory; n = 0 disarms.  Process-wide, for tests. */
+int se_selftest_fail_alloc(int n);
 
 #ifdef __cplusplus
 }

@@ -1,5 +1,6 @@
 // Errors, allocations, 1D GLL basis, SplitMix64, reduction scratch and kernel profiling.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
@@ -26,7 +27,24 @@ void Allocs::release() {
   bytes = 0;
 }
 
+// Self-test of the allocation failure paths (se_selftest_fail_alloc): while the countdown is
+// positive every device allocation decrements it, and the one that brings it to zero fails with
+// SE_ENOMEM before any CUDA call.
+static std::atomic<int> g_fail_alloc_countdown{0};
+
+static bool injected_alloc_failure() {
+  int c = g_fail_alloc_countdown.load();
+  while (c > 0 && !g_fail_alloc_countdown.compare_exchange_weak(c, c - 1)) {
+  }
+  return c == 1;
+}
+
 int dmalloc_transient(void** p, size_t bytes, cudaStream_t s) {
+  if (injected_alloc_failure()) {
+    *p = nullptr;
+    set_error("device allocation of %zu bytes failed: injected by se_selftest_fail_alloc", bytes);
+    return SE_ENOMEM;
+  }
   cudaError_t e = cudaMallocAsync(p, bytes, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
@@ -301,3 +319,9 @@ int se_prof_query_variant(int kind, int variant, double* ms_total, int64_t* laun
 }
 
 }  // extern "C"
+
+extern "C" int se_selftest_fail_alloc(int n) {
+  SE_CHECK(n >= 0, SE_EINVAL, "se_selftest_fail_alloc: n = %d < 0", n);
+  se::g_fail_alloc_countdown.store(n);
+  return SE_OK;
+}

@@ -177,6 +177,7 @@ _SIGS = {
     "se_prof_query": ([_ip, _dp, C.POINTER(C.c_int64), _dp, _dp, _dp], C.c_int),
     "se_prof_query_variant": ([_ip, _ip, _dp, C.POINTER(C.c_int64), _dp, _dp, _dp], C.c_int),
     "se_selftest_wait_timeout": ([C.c_double], C.c_int),
+    "se_selftest_fail_alloc": ([C.c_int], C.c_int),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -626,3 +627,8 @@ def se_prof_query_variant(kind, variant):
 
 def se_selftest_wait_timeout(timeout_ms=100.0) -> int:
     return lib.se_selftest_wait_timeout(timeout_ms)
+
+
+def se_selftest_fail_alloc(n):
+    """Arm (n >= 1) or disarm (0) the injected failure of the n-th following device allocation."""
+    _check(lib.se_selftest_fail_alloc(int(n)))

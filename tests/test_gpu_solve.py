@@ -131,3 +131,52 @@ def test_not_converged_status():
         assert st.iterations == 3 and st.status == se.SE_ENOTCONV
     finally:
         c.close()
+
+
+def test_injected_allocation_failures_leave_the_library_usable():
+    """Host-side fault injection (no device fault): se_selftest_fail_alloc(n) makes the n-th
+    following device allocation fail with SE_ENOMEM before any CUDA call.  Sweeping n over every
+    allocation of a mesh set-up, an FP32-V-cycle preconditioner set-up and a first graph solve,
+    each run fails with SE_ENOMEM from the call that allocates (the handles it built are freed),
+    and afterwards the library builds and solves the same problem to the same bits."""
+    torch, se = Case((1, 1, 1), 1).torch, Case((1, 1, 1), 1).se
+    nel, p = (2, 2, 2), 5
+    V = wl.vertex_lattice(nel, 0.05, seed=1)
+
+    def run():
+        m = se.se_mesh_create(nel, p, vertex_xyz=V, deform_amp=wl.DEFORM_AMP)
+        P = None
+        try:
+            L = se.se_mesh_get_info(m).L
+            xyz = torch.empty(3 * L, dtype=torch.float64, device="cuda")
+            se.se_mesh_nodes(m, xyz)
+            X = xyz.cpu().numpy().reshape(3, -1)
+            b = torch.empty(L, dtype=torch.float64, device="cuda")
+            se.se_mesh_rhs(m, torch.from_numpy(wl.f_rhs(X[0], X[1], X[2])).cuda(), b)
+            P = se.se_pmg_setup(m, se.pmg_desc((5, 3, 1), se.SE_SMOOTH_RAS, 2, precision=se.SE_FP32))
+            x = torch.zeros_like(b)
+            st = se.se_solve(m, P, b, x, tol=1e-8, graph_capture=1)
+            return x.cpu().numpy(), st.iterations
+        finally:
+            if P:
+                se.se_pmg_destroy(P)
+            se.se_mesh_destroy(m)
+
+    ref, it_ref = run()
+    failures = 0
+    for n in range(1, 500):
+        se.se_selftest_fail_alloc(n)
+        try:
+            run()
+        except se.SeError as e:
+            assert e.code == se.SE_ENOMEM, (n, str(e))
+            failures += 1
+            continue
+        finally:
+            se.se_selftest_fail_alloc(0)
+        break  # n is past the sequence's last allocation: the run completed
+    assert failures >= 20, failures
+    x, it = run()
+    assert it == it_ref and np.array_equal(x, ref)
+    with pytest.raises(se.SeError):
+        se.se_selftest_fail_alloc(-1)
