@@ -817,10 +817,10 @@ __global__ void __launch_bounds__(256, P <= 6 ? 4 : (P <= 8 ? 3 : 2)) fdm32_warp
 // sums as the warp kernel (forward: one packed chain per pair of modes in ascending order;
 // backward: even and odd terms in the two lanes, added at the end).
 // Used for p = 3 and 5 (measured on GB300 at 32^3 elements, FP32 V-cycle: p = 5 0.066 ms per
-// launch against 0.080 for the warp kernel, p = 3 0.037 against 0.050).  At p = 7 a plane and
-// S_x take 254 registers, so only 8 warps per SM hide the gather's latency and the warp kernel
-// stays faster (0.175 against 0.193 ms), although this one issues 2.6x fewer instructions and
-// 5x fewer shared-memory wavefronts per element.
+// launch against 0.080 for the warp kernel and 0.072 for fdm32_plane_smem_kernel, p = 3 0.037
+// against 0.050 and 0.038).  At p = 7 a plane and S_x take 254 registers, so only 8 warps per SM
+// hide the gather's latency (0.193 ms against the warp kernel's 0.175); p = 7 uses
+// fdm32_plane_smem_kernel below (0.150 ms).
 template <int PB>
 struct Fdm32PlaneDims {
   static_assert(PB == 6 || PB == 8 || PB == 10, "plane kernel: pbar 6, 8 or 10 (odd p <= 7)");
@@ -1042,6 +1042,193 @@ __global__ void __launch_bounds__(128, 2) fdm32_plane_kernel(int64_t E, const in
   }
 }
 
+// The same algorithm with the window kept in shared memory: a thread holds only S (packed pairs)
+// and the line it contracts, so it needs 167 registers instead of 254 at p = 7 (12 warps per SM
+// instead of 8) and its line loops need not be unrolled.  Used for p = 7.  Every shared access pattern is one
+// of those the strides were chosen for (plane-per-thread rows and columns, column-per-thread
+// planes), so each stays conflict-free.  Same arithmetic per output as fdm32_plane_kernel.
+template <int PB>
+__device__ __forceinline__ void smem_line_fwd(const float2 (&S2)[PB][PB / 2], float* base, int stride) {
+  constexpr int H = PB / 2;
+  float v[PB];
+#pragma unroll
+  for (int a = 0; a < PB; ++a) v[a] = base[a * stride];
+  float2 acc[H];
+#pragma unroll
+  for (int k = 0; k < H; ++k) acc[k] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int a = 0; a < PB; ++a) {
+    const float2 vv = make_float2(v[a], v[a]);
+#pragma unroll
+    for (int k = 0; k < H; ++k) acc[k] = __ffma2_rn(S2[a][k], vv, acc[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    base[(2 * k) * stride] = acc[k].x;
+    base[(2 * k + 1) * stride] = acc[k].y;
+  }
+}
+
+// out[i] = sum_m S[1 + i][m] v[m], i < N, in place at base[(1 + i) stride] (own rows only).
+template <int PB>
+__device__ __forceinline__ void smem_line_bwd_own(const float2 (&S2)[PB][PB / 2], float* base,
+                                                  int stride, float (&o)[PB - 2]) {
+  constexpr int H = PB / 2, N = PB - 2;
+  float v[PB];
+#pragma unroll
+  for (int m = 0; m < PB; ++m) v[m] = base[m * stride];
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    float2 z = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < H; ++k) z = __ffma2_rn(S2[i + 1][k], make_float2(v[2 * k], v[2 * k + 1]), z);
+    o[i] = z.x + z.y;
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(128, 3) fdm32_plane_smem_kernel(int64_t E, const int* __restrict__ nbr,
+                                                                  const float* __restrict__ in,
+                                                                  const float* __restrict__ Sg,
+                                                                  const float* __restrict__ lamg,
+                                                                  const uint8_t* __restrict__ pflag,
+                                                                  float* __restrict__ out) {
+  constexpr int PB = P + 3, N = P + 1, N2 = N * N, N3 = N2 * N, PB2 = PB * PB, H = PB / 2;
+  using D = Fdm32PlaneDims<PB>;
+  constexpr int PSN = D::PSN;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gw = lane / PB, t = lane - gw * PB;
+  const bool lane_on = gw < D::EW;
+  const int g = warp * D::EW + (lane_on ? gw : 0);
+  const int64_t e = (int64_t)blockIdx.x * D::NE + g;
+  const bool on = lane_on && e < E;
+  float* W = reinterpret_cast<float*>(smem_raw) + (size_t)g * D::TOT;
+  int* snb = reinterpret_cast<int*>(W + D::OFF_NB);
+  float* sS = W + D::OFF_S;
+  float* sl = W + D::OFF_L;
+  if (on) {
+    for (int q = t; q < 27; q += PB) snb[q] = nbr[27 * e + q];
+    for (int q = t; q < 3 * PB2; q += PB) sS[q] = Sg[e * 3 * PB2 + q];
+    for (int q = t; q < 3 * PB; q += PB) sl[q] = lamg[e * 3 * PB + q];
+  }
+  __syncwarp();
+  float2 S2[PB][H];
+  // ---- 1. gather (as fdm32_plane_kernel): column a = t of every row (b, c) of the window
+  if (on) {
+    const int da = t == 0 ? -1 : (t == PB - 1 ? 1 : 0);
+    const int ia = da < 0 ? P - 1 : (da > 0 ? 1 : t - 1);
+    int nb9[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) nb9[k][j] = snb[(da + 1) + 3 * j + 9 * k];
+    const float* src_a = in + ia;
+#pragma unroll
+    for (int c = 0; c < PB; ++c) {
+      const int dc = c == 0 ? -1 : (c == PB - 1 ? 1 : 0);
+      const int ic = dc < 0 ? P - 1 : (dc > 0 ? 1 : c - 1);
+#pragma unroll
+      for (int b = 0; b < PB; ++b) {
+        const int db = b == 0 ? -1 : (b == PB - 1 ? 1 : 0);
+        const int ib = db < 0 ? P - 1 : (db > 0 ? 1 : b - 1);
+        const int nb = nb9[dc + 1][db + 1];
+        cp_async4(W + c * PSN + b * PB + t, nb >= 0 ? src_a + (int64_t)nb * N3 + N * ib + N2 * ic : in,
+                  nb >= 0);
+      }
+    }
+    cp_async_wait_all();
+  }
+  __syncwarp();
+  // ---- 2. own plane c = t: S_x^T along rows, then S_y^T along columns
+  if (on) {
+    float* plane = W + t * PSN;
+    plane_load_S<PB>(sS, 0, S2);
+#pragma unroll 1
+    for (int b = 0; b < PB; ++b) smem_line_fwd<PB>(S2, plane + b * PB, 1);
+    plane_load_S<PB>(sS, 1, S2);
+#pragma unroll 1
+    for (int a = 0; a < PB; ++a) smem_line_fwd<PB>(S2, plane + a, PB);
+  }
+  __syncwarp();
+  // ---- 3. columns col = t + pbar j: S_z^T, D^-1, S_z for the own planes
+  if (on) {
+    plane_load_S<PB>(sS, 2, S2);
+#pragma unroll 1
+    for (int j = 0; j < PB; ++j) {
+      const int col = t + PB * j;
+      float* cb = W + col;
+      float v[PB];
+#pragma unroll
+      for (int c = 0; c < PB; ++c) v[c] = cb[c * PSN];
+      float2 acc[H];
+#pragma unroll
+      for (int k = 0; k < H; ++k) acc[k] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int c = 0; c < PB; ++c) {
+        const float2 vv = make_float2(v[c], v[c]);
+#pragma unroll
+        for (int k = 0; k < H; ++k) acc[k] = __ffma2_rn(S2[c][k], vv, acc[k]);
+      }
+      const int be = col / PB, al = col - be * PB;
+      const float lxy = sl[al] + sl[PB + be];
+#pragma unroll
+      for (int k = 0; k < H; ++k) {
+        v[2 * k] = acc[k].x * rcp_approx(lxy + sl[2 * PB + 2 * k]);
+        v[2 * k + 1] = acc[k].y * rcp_approx(lxy + sl[2 * PB + 2 * k + 1]);
+      }
+#pragma unroll
+      for (int cc = 1; cc <= N; ++cc) {
+        float2 z = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < H; ++k) z = __ffma2_rn(S2[cc][k], make_float2(v[2 * k], v[2 * k + 1]), z);
+        cb[cc * PSN] = z.x + z.y;
+      }
+    }
+  }
+  __syncwarp();
+  // ---- 4. own plane c' = t + 1: S_y (own rows) per column, S_x (own columns) per own row
+  if (on && t < N) {
+    float* plane = W + (t + 1) * PSN;
+    plane_load_S<PB>(sS, 1, S2);
+#pragma unroll 1
+    for (int a = 0; a < PB; ++a) {
+      float o[N];
+      smem_line_bwd_own<PB>(S2, plane + a, PB, o);
+#pragma unroll
+      for (int i = 0; i < N; ++i) plane[(1 + i) * PB + a] = o[i];
+    }
+    plane_load_S<PB>(sS, 0, S2);
+    const int64_t ob = e * N3 + (int64_t)N2 * t;
+#pragma unroll 1
+    for (int bb = 0; bb < N; ++bb) {
+      float o[N];
+      smem_line_bwd_own<PB>(S2, plane + (1 + bb) * PB, 1, o);
+      // own points (i, j, k) = (aa, bb, t), weighted by 1/multiplicity; a row of N values starts
+      // on a 16-byte boundary when N is a multiple of 4
+      if constexpr (N % 4 == 0) {
+#pragma unroll
+        for (int q4 = 0; q4 < N / 4; ++q4) {
+          const uint32_t f4 = *reinterpret_cast<const uint32_t*>(pflag + ob + N * bb + 4 * q4);
+          float w[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int mlog = __ffs((f4 >> (8 * u)) & 0x0Fu) - 1;
+            w[u] = o[4 * q4 + u] * __int_as_float((127 - mlog) << 23);
+          }
+          *reinterpret_cast<float4*>(out + ob + N * bb + 4 * q4) = make_float4(w[0], w[1], w[2], w[3]);
+        }
+      } else {
+#pragma unroll
+        for (int aa = 0; aa < N; ++aa) {
+          const int mlog = __ffs(pflag[ob + N * bb + aa] & 0x0F) - 1;
+          out[ob + N * bb + aa] = o[aa] * __int_as_float((127 - mlog) << 23);
+        }
+      }
+    }
+  }
+}
+
 // Shared bytes per element: fdm_kernel<P, double, *> (two window buffers, S^T and S, the
 // eigenvalues, 27 neighbour ids) or fdm32_warp_kernel<P, *> (Fdm32Dims<P + 3>::PER floats, and
 // the block's window tables once per block).
@@ -1107,6 +1294,16 @@ static int launch_fdm(const Level& lv, const T* in, const T* S, const T* lam, T*
   const unsigned blocks = (unsigned)((lv.E + NE - 1) / NE);
   if constexpr (sizeof(T) == 4) {
     static_assert(MODE == FDM_RAS || MODE == FDM_FULL, "FP32 FDM: RAS or full window only");
+    if constexpr (MODE == FDM_RAS && P == 7) {
+      using PD = Fdm32PlaneDims<P + 3>;
+      static const cudaError_t pattr = cudaFuncSetAttribute(
+          fdm32_plane_smem_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PD::SMEM);
+      SE_CUDA(pattr);
+      const unsigned pblocks = (unsigned)((lv.E + PD::NE - 1) / PD::NE);
+      fdm32_plane_smem_kernel<P><<<pblocks, 128, PD::SMEM, s>>>(lv.E, lv.nbr, in, S, lam, lv.pflag, out);
+      SE_LAUNCH_CHECK();
+      return SE_OK;
+    }
     if constexpr (MODE == FDM_RAS && (P == 3 || P == 5)) {
       using PD = Fdm32PlaneDims<P + 3>;
       static const cudaError_t pattr = cudaFuncSetAttribute(
