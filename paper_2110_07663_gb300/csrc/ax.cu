@@ -239,15 +239,17 @@ constexpr int GS_X_SEG = 8;  // x-interfaces per warp
 template <typename T, int N>
 __global__ void __launch_bounds__(256) gs_sweep_x(int nx, int ny, int nz, int bits, T* __restrict__ u) {
   constexpr int N3 = N * N * N, R = 32 / N, NG = (N * N + R - 1) / R, SEG = GS_X_SEG;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  // index decomposition in 32-bit integers (every count here is below L < 2^31; a 64-bit
+  // division by a run-time value costs an order of magnitude more instructions)
+  const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   const int nseg = (nx - 1 + SEG - 1) / SEG;
-  const int64_t items = (int64_t)ny * nz * NG * nseg;  // (row group, run, element row along x)
+  const int items = ny * nz * NG * nseg;               // (row group, run, element row along x)
   if (warp >= items) return;                           // whole warps
-  const int grp = (int)(warp % NG);
-  const int64_t q = warp / NG;
-  const int seg = (int)(q % nseg);
-  const int64_t row_e = q / nseg;                      // ey + ny ez
+  const int grp = warp % NG;
+  const int q = warp / NG;
+  const int seg = q % nseg;
+  const int row_e = q / nseg;                          // ey + ny ez
   const int r = lane / N, i = lane - r * N;
   const int jk = grp * R + r;                          // row j + N k of the element
   const bool on = r < R && jk < N * N;
@@ -261,17 +263,21 @@ __global__ void __launch_bounds__(256) gs_sweep_x(int nx, int ny, int nz, int bi
   for (int m = 0; m <= SEG; ++m) v[m] = u[(e0 + min(m, cnt)) * N3 + off];
   if (bits) {
     const int j = jk % N, k = jk / N;
-    const int ey = (int)(row_e % ny), ez = (int)(row_e / ny);
+    const int ey = row_e % ny, ez = row_e / ny;
+    // a lane's copies are masked in every element of the run (a Dirichlet y or z face), or only
+    // in the run's first element (x = 0 face) or last one (x = 1 face): tested once per lane
     const bool myz = ((bits & 4) && j == 0 && ey == 0) || ((bits & 8) && j == N - 1 && ey == ny - 1) ||
                      ((bits & 16) && k == 0 && ez == 0) || ((bits & 32) && k == N - 1 && ez == nz - 1);
+    const bool mx0 = (bits & 1) && i == 0 && ex0 == 0;
+    const bool mx1 = (bits & 2) && i == N - 1 && ex0 + cnt == nx - 1;
+    if (on && (myz || mx0 || mx1)) {
 #pragma unroll
-    for (int m = 0; m <= SEG; ++m) {
-      if (m > cnt) break;
-      const int ex = ex0 + m;
-      const bool msk = myz || ((bits & 1) && i == 0 && ex == 0) || ((bits & 2) && i == N - 1 && ex == nx - 1);
-      if (on && msk) {
-        v[m] = T(0);
-        u[(e0 + m) * N3 + off] = T(0);
+      for (int m = 0; m <= SEG; ++m) {
+        if (m > cnt) break;
+        if (myz || (m == 0 && mx0) || (m == cnt && mx1)) {
+          v[m] = T(0);
+          u[(e0 + m) * N3 + off] = T(0);
+        }
       }
     }
   }
@@ -288,43 +294,80 @@ __global__ void __launch_bounds__(256) gs_sweep_x(int nx, int ny, int nz, int bi
   }
 }
 
+// y and z sweeps: each thread adds GS_YZ_PAIRS interface pairs, strided so that a warp's
+// accesses stay contiguous, all loads issued before any store (these kernels are bound by memory
+// latency, not bandwidth).
+constexpr int GS_YZ_PAIRS = 4;
+
 template <typename T, int N>
 __global__ void gs_sweep_y(int nx, int ny, int nz, T* __restrict__ u) {
-  constexpr int N3 = N * N * N;
+  constexpr int N3 = N * N * N, K = GS_YZ_PAIRS;
   const int nif = ny - 1;
-  const int64_t total = (int64_t)N * N * nx * nif * nz;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= total) return;
-  const int i = (int)(t % N);
-  int64_t q = t / N;
-  const int k = (int)(q % N);
-  q /= N;
-  const int ex = (int)(q % nx);
-  q /= nx;
-  const int ey = (int)(q % nif);
-  const int ez = (int)(q / nif);
-  const int64_t e = ex + (int64_t)nx * (ey + (int64_t)ny * ez);
-  const int64_t ia = e * N3 + i + N * ((N - 1) + N * k);      // element e, j = p
-  const int64_t ib = (e + nx) * N3 + i + (int64_t)N * N * k;  // element e + nx, j = 0
-  const T sum = u[ia] + u[ib];
-  u[ia] = sum;
-  u[ib] = sum;
+  const int total = N * N * nx * nif * nz;  // < L < 2^31: 32-bit index arithmetic
+  const int nthr = (total + K - 1) / K;
+  const int t0 = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (t0 >= nthr) return;
+  int64_t ia[K], ib[K];
+  T a[K], b[K];
+#pragma unroll
+  for (int kk = 0; kk < K; ++kk) {
+    const int t = t0 + kk * nthr;
+    ia[kk] = -1;
+    if (t < total) {
+      const int i = t % N;
+      int q = t / N;
+      const int k = q % N;
+      q /= N;
+      const int ex = q % nx;
+      q /= nx;
+      const int ey = q % nif;
+      const int ez = q / nif;
+      const int64_t e = ex + (int64_t)nx * (ey + (int64_t)ny * ez);
+      ia[kk] = e * N3 + i + N * ((N - 1) + N * k);      // element e, j = p
+      ib[kk] = (e + nx) * N3 + i + (int64_t)N * N * k;  // element e + nx, j = 0
+      a[kk] = u[ia[kk]];
+      b[kk] = u[ib[kk]];
+    }
+  }
+#pragma unroll
+  for (int kk = 0; kk < K; ++kk) {
+    if (ia[kk] < 0) continue;
+    const T sum = a[kk] + b[kk];
+    u[ia[kk]] = sum;
+    u[ib[kk]] = sum;
+  }
 }
 
 template <typename T, int N>
 __global__ void gs_sweep_z(int nx, int ny, int nz, T* __restrict__ u) {
-  constexpr int N2 = N * N, N3 = N2 * N;
+  constexpr int N2 = N * N, N3 = N2 * N, K = GS_YZ_PAIRS;
   const int nif = nz - 1;
-  const int64_t total = (int64_t)N2 * nx * ny * nif;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= total) return;
-  const int ij = (int)(t % N2);
-  const int64_t e = t / N2;  // elements with ez < nz - 1, in order
-  const int64_t ia = e * N3 + ij + N2 * (N - 1);          // element e, k = p
-  const int64_t ib = (e + (int64_t)nx * ny) * N3 + ij;    // element e + nx ny, k = 0
-  const T sum = u[ia] + u[ib];
-  u[ia] = sum;
-  u[ib] = sum;
+  const int total = N2 * nx * ny * nif;  // < L < 2^31: 32-bit index arithmetic
+  const int nthr = (total + K - 1) / K;
+  const int t0 = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (t0 >= nthr) return;
+  int64_t ia[K], ib[K];
+  T a[K], b[K];
+#pragma unroll
+  for (int kk = 0; kk < K; ++kk) {
+    const int t = t0 + kk * nthr;
+    ia[kk] = -1;
+    if (t < total) {
+      const int ij = t % N2;
+      const int64_t e = t / N2;  // elements with ez < nz - 1, in order
+      ia[kk] = e * N3 + ij + N2 * (N - 1);            // element e, k = p
+      ib[kk] = (e + (int64_t)nx * ny) * N3 + ij;      // element e + nx ny, k = 0
+      a[kk] = u[ia[kk]];
+      b[kk] = u[ib[kk]];
+    }
+  }
+#pragma unroll
+  for (int kk = 0; kk < K; ++kk) {
+    if (ia[kk] < 0) continue;
+    const T sum = a[kk] + b[kk];
+    u[ia[kk]] = sum;
+    u[ib[kk]] = sum;
+  }
 }
 
 // Zero the copies on the Dirichlet faces (bit f of `bits`: face f = x0, x1, y0, y1, z0, z1).
@@ -396,13 +439,13 @@ static int gs_sweeps(const Level& lv, T* u, bool mask, double bytes, double flop
   if (ny > 1) {
     const int64_t n = (int64_t)N2 * nx * (ny - 1) * nz;
     ProfScope prof(SE_K_GS, s, (double)n, 0.0, 0.0, var);
-    gs_sweep_y<T, N><<<grid_for(n, 256), 256, 0, s>>>(nx, ny, nz, u);
+    gs_sweep_y<T, N><<<grid_for((n + GS_YZ_PAIRS - 1) / GS_YZ_PAIRS, 256), 256, 0, s>>>(nx, ny, nz, u);
     SE_LAUNCH_CHECK();
   }
   if (nz > 1) {
     const int64_t n = (int64_t)N2 * nx * ny * (nz - 1);
     ProfScope prof(SE_K_GS, s, (double)n, 0.0, 0.0, var);
-    gs_sweep_z<T, N><<<grid_for(n, 256), 256, 0, s>>>(nx, ny, nz, u);
+    gs_sweep_z<T, N><<<grid_for((n + GS_YZ_PAIRS - 1) / GS_YZ_PAIRS, 256), 256, 0, s>>>(nx, ny, nz, u);
     SE_LAUNCH_CHECK();
   }
   return SE_OK;
