@@ -221,7 +221,10 @@ int ax_local(const Level& lv, const T* u, T* y, bool mask_in, cudaStream_t s, co
 // Masking (Dirichlet) zeroes the copies on Dirichlet faces within the x sweep, before any sum (a
 // node on such a face has all its copies there), so the sweeps then add zeros for masked nodes;
 // a lattice one element wide in x has a separate mask kernel.
-constexpr int GS_X_SEG = 8;  // x-interfaces per warp
+// x-interfaces per warp: 16 in FP32 (halves the per-warp index and mask work, which bounds the
+// FP32 sweep), 8 in FP64
+template <typename T>
+constexpr int gs_x_seg() { return sizeof(T) == 4 ? 16 : 8; }
 
 // x sweep: a warp holds R = 32/N consecutive rows (j, k) of an element (lane = (row, i); the
 // element's N^2 rows are contiguous) for a run of consecutive elements along x, loaded coalesced
@@ -229,16 +232,16 @@ constexpr int GS_X_SEG = 8;  // x-interfaces per warp
 // two copies of each x-interface (lane i = p of element m, lane i = 0 of element m + 1, same
 // row) swap by one shuffle and both store their sum (a + b == b + a exactly: both copies get the
 // same bits).  Every value of the vector
-// is read once, in full sectors.  A warp takes a run of GS_X_SEG interfaces (runs of one x-row
+// is read once, in full sectors.  A warp takes a run of gs_x_seg<T>() interfaces (runs of one x-row
 // overlap by one element, and no two runs write the same copy: a run writes the row ends of its
-// interfaces only); it always loads GS_X_SEG + 1 elements (indices clamped to the last element of
+// interfaces only); it always loads gs_x_seg<T>() + 1 elements (indices clamped to the last element of
 // the row) so that all loads are issued back to back.
 // With Dirichlet bits (mask), the x sweep also applies the mask: a copy whose node lies on a
 // Dirichlet face is zeroed before the sums and stored as zero (every copy of every element passes
 // through some run, and a node's copies are all masked or none, so overlapping runs agree).
 template <typename T, int N>
 __global__ void __launch_bounds__(256) gs_sweep_x(int nx, int ny, int nz, int bits, T* __restrict__ u) {
-  constexpr int N3 = N * N * N, R = 32 / N, NG = (N * N + R - 1) / R, SEG = GS_X_SEG;
+  constexpr int N3 = N * N * N, R = 32 / N, NG = (N * N + R - 1) / R, SEG = gs_x_seg<T>();
   // index decomposition in 32-bit integers (every count here is below L < 2^31; a 64-bit
   // division by a run-time value costs an order of magnitude more instructions)
   const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -431,7 +434,8 @@ static int gs_sweeps(const Level& lv, T* u, bool mask, double bytes, double flop
   }
   if (nx > 1) {
     constexpr int R = 32 / N, NG = (N * N + R - 1) / R;
-    const int64_t warps = (int64_t)ny * nz * NG * ((nx - 1 + GS_X_SEG - 1) / GS_X_SEG);
+    constexpr int SEG = gs_x_seg<T>();
+    const int64_t warps = (int64_t)ny * nz * NG * ((nx - 1 + SEG - 1) / SEG);
     ProfScope prof(SE_K_GS, s, (double)lv.L, bytes, flops, var);
     gs_sweep_x<T, N><<<grid_for(32 * warps, 256), 256, 0, s>>>(nx, ny, nz, bits, u);
     SE_LAUNCH_CHECK();
