@@ -224,7 +224,7 @@ int ax_local(const Level& lv, const T* u, T* y, bool mask_in, cudaStream_t s, co
 // x-interfaces per warp: 16 in FP32 (halves the per-warp index and mask work, which bounds the
 // FP32 sweep), 8 in FP64
 template <typename T>
-constexpr int gs_x_seg() { return sizeof(T) == 4 ? 16 : 8; }
+__host__ __device__ constexpr int gs_x_seg() { return sizeof(T) == 4 ? 16 : 8; }
 
 // x sweep: a warp holds R = 32/N consecutive rows (j, k) of an element (lane = (row, i); the
 // element's N^2 rows are contiguous) for a run of consecutive elements along x, loaded coalesced
