@@ -180,3 +180,49 @@ def test_injected_allocation_failures_leave_the_library_usable():
     assert it == it_ref and np.array_equal(x, ref)
     with pytest.raises(se.SeError):
         se.se_selftest_fail_alloc(-1)
+
+
+@pytest.mark.parametrize("method", ["fpcg", "fgmres"])
+@pytest.mark.parametrize("graph", [0, 1])
+def test_degenerate_problems(method, graph):
+    """Zero right-hand side (the solution is x = 0: no iteration, no division by the zero initial
+    residual), a mesh whose every node is on the Dirichlet boundary (no unknown at all: one
+    element, p = 1) and one with a single unknown (one element, p = 2, pMG 2-1)."""
+    c = Case((2, 2, 1), 5, seed=4)
+    se = c.se
+    meth = se.SE_FPCG if method == "fpcg" else se.SE_FGMRES
+    if graph and method == "fgmres":
+        pytest.skip("the graph solve is FPCG")
+    P = se.se_pmg_setup(c.m, se.pmg_desc((5, 3, 1), se.SE_SMOOTH_RAS, 2))
+    try:
+        b = c.empty().zero_()
+        x = c.empty().zero_()
+        st = se.se_solve(c.m, P, b, x, method=meth, tol=1e-8, graph_capture=graph)
+        assert st.iterations == 0 and st.rel_residual == 0.0
+        assert float(x.abs().max()) == 0.0
+    finally:
+        se.se_pmg_destroy(P)
+        c.close()
+    for nel, p, sched in [((1, 1, 1), 1, None), ((1, 1, 1), 2, (2, 1))]:
+        c = Case(nel, p, seed=5)
+        P = se.se_pmg_setup(c.m, se.pmg_desc(sched, se.SE_SMOOTH_RAS, 2)) if sched else None
+        try:
+            xyz = c.empty(3 * c.info.L)
+            se.se_mesh_nodes(c.m, xyz)
+            X = xyz.cpu().numpy().reshape(3, -1)
+            b = c.empty()
+            se.se_mesh_rhs(c.m, c.to_gpu(wl.f_rhs(X[0], X[1], X[2])), b)
+            x = c.empty().zero_()
+            st = se.se_solve(c.m, P, b, x, method=meth, tol=1e-8, graph_capture=graph)
+            lvo, bo = o.problem(c.V, c.nel, c.p, amp=c.amp)
+            if np.max(np.abs(bo)) == 0.0:  # no unknown: nothing to solve
+                assert st.iterations == 0 and float(x.abs().max()) == 0.0
+            else:
+                xo, it_o, _ = o.solve(lvo, bo, o.pmg_setup(c.V, nel, sched, smoother="ras", order=2,
+                                                          amp=c.amp) if sched else None,
+                                      method=method, tol=1e-8)
+                assert st.rel_residual <= 1e-8 and rel_err(c.to_np(x), xo) <= 1e-8
+        finally:
+            if P:
+                se.se_pmg_destroy(P)
+            c.close()
