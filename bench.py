@@ -923,6 +923,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         ap.error("--warmup must be >= 3")
+    if args.cycle == "additive" and args.smoother not in ("ras", "asm"):
+        ap.error("--cycle additive needs --smoother ras or asm (the additive V-cycle has no Chebyshev)")
     if args.impl == "reference":
         run_reference(args)
     elif args.batch:
