@@ -6,8 +6,11 @@ eq 5 is exactly the Galerkin restriction R_e A R_e^T, so the fast-diagonalisatio
 Chebyshev (Algorithm 2): I - M A equals the scaled Chebyshev polynomial of SA, built here by the
 three-term recurrence and cosh(m arccosh sigma).  Arnoldi: exact once the Krylov space is
 exhausted.  Multigrid: the transfers are adjoint and reproduce coarse polynomials; the V-cycle
-(Algorithm 1) is linear with an exact coarse solve and contracts the error.  Solvers: the
-converged solution equals a dense direct solve; the discrete solution converges spectrally.
+(Algorithm 1) with an exact coarse solve equals the product of the error propagators of its
+steps (pre-smoothing, coarse correction with the re-evaluated residual, post-smoothing) built
+from dense matrices, and contracts the error.  Solvers: the converged solution equals a dense
+direct solve; the discrete solution converges spectrally; flexible CG reduces to textbook PCG
+for a fixed preconditioner and keeps consecutive directions conjugate for a varying one.
 """
 import math
 
@@ -363,3 +366,169 @@ def test_additive_cycle_solution_matches_direct_solve(mg_case, method, pre):
     Af = assembled_stiffness(lv, xg, wg)[np.ix_(cols, cols)]
     xd = np.linalg.solve(Af, o.to_global(lv, b)[cols])
     assert np.allclose(o.to_global(lv, xsol)[cols], xd, rtol=0, atol=1e-8 * np.abs(xd).max())
+
+
+def _level_matrices(pmg, l):
+    """Dense matrices of level l on its free global nodes: stiffness by brute-force quadrature
+    (no sum factorisation), the smoother S, and the transfers to level l+1."""
+    lv = pmg.levels[l]
+    x, w = o.gll(lv.p)
+    cols = free_nodes(lv)
+    A = assembled_stiffness(lv, x, w)[np.ix_(cols, cols)]
+    if l == len(pmg.levels) - 1:
+        return A, None, None, None
+    lc = pmg.levels[l + 1]
+    S = map_matrix(lv, lv, o.smoother_op(pmg, l))
+    R = map_matrix(lv, lc, lambda r: o.restrict(lv, lc, r))
+    P = map_matrix(lc, lv, lambda e: o.prolong(lv, lc, e))
+    return A, S, R, P
+
+
+def multiplicative_cycle_matrix(pmg):
+    """Algorithm 1 written as an error propagator, from dense matrices only.
+
+    On level l the Chebyshev smoother of Algorithm 2 is the linear map C_l with
+    I - C_l A_l = T_{k+1}((theta - S_l A_l)/delta) / T_{k+1}(theta/delta), the polynomial built
+    by the three-term recurrence (not by the oracle's Chebyshev routine).  Pre-smoothing, the
+    coarse-grid correction with the re-evaluated residual, and post-smoothing give
+        I - M_l A_l = (I - C_l A_l) (I - P_l M_{l+1} R_l A_l) (I - C_l A_l),
+    with M_coarsest = A_coarsest^-1 (exact coarse solve).  Returns M_0."""
+    mats = [_level_matrices(pmg, l) for l in range(len(pmg.levels))]
+    M = np.linalg.inv(mats[-1][0])
+    for l in range(len(pmg.levels) - 2, -1, -1):
+        A, S, R, P = mats[l]
+        lmin, lmax = pmg.bounds[l]
+        I = np.eye(len(A))
+        Esm = chebyshev_matrix_polynomial(S @ A, lmin, lmax, pmg.order[l] + 1)
+        Ecg = I - P @ M @ R @ A
+        M = (I - Esm @ Ecg @ Esm) @ np.linalg.inv(A)
+    return M, mats
+
+
+@pytest.mark.parametrize("smoother", ["jacobi", "ras", "asm"])
+def test_vcycle_is_the_composition_of_algorithm_1(smoother):
+    """Algorithm 1 (Sec. 2.2.2) with an exact coarse solve equals the product of its steps'
+    error propagators (pre-smoothing, coarse correction, post-smoothing) built from dense
+    matrices, on a three-level schedule.  A cycle that drops the post-smoothing, the
+    pre-smoothing or the residual re-evaluation is a different operator and fails here."""
+    nel = (3, 2, 2)
+    V = wl.vertex_lattice(nel, 0.05, seed=8)
+    pmg = o.pmg_setup(V, nel, (3, 2, 1), smoother=smoother, order=[2, 1, 0], coarse_tol=1e-14,
+                      coarse_maxit=2000)
+    l0 = pmg.levels[0]
+    Mdef, mats = multiplicative_cycle_matrix(pmg)
+    Mv = map_matrix(l0, l0, lambda r: o.vcycle(pmg, r))
+    scale = np.abs(Mdef).max()
+    assert np.allclose(Mv, Mdef, rtol=0, atol=1e-9 * scale)
+    if smoother == "jacobi":
+        # S = D^-1 and R = P^T make every step self-adjoint: the cycle is symmetric
+        assert np.allclose(Mv, Mv.T, rtol=0, atol=1e-9 * scale)
+        A0, S0, R0, P0 = mats[0]
+        assert np.allclose(R0, P0.T, rtol=0, atol=1e-13 * np.abs(P0).max())
+
+    # the same composition discriminates the variants of the cycle
+    A0, S0, R0, P0 = mats[0]
+    lmin, lmax = pmg.bounds[0]
+
+    def cheb(r):
+        return o.chebyshev(r, lambda u: o.ax(l0, u), o.smoother_op(pmg, 0), lmin, lmax,
+                           pmg.order[0])
+
+    def coarse(r):
+        return o.prolong(l0, pmg.levels[1], o.vcycle(pmg, o.restrict(l0, pmg.levels[1], r), 1))
+
+    def no_post(b):
+        x = cheb(b)
+        return x + coarse(b - o.ax(l0, x))
+
+    def no_pre(b):
+        x = coarse(b)
+        return x + cheb(b - o.ax(l0, x))
+
+    def stale_residual(b):
+        x = cheb(b)
+        x = x + coarse(b)
+        return x + cheb(b - o.ax(l0, x))
+
+    for variant in (no_post, no_pre, stale_residual):
+        Mw = map_matrix(l0, l0, variant)
+        assert not np.allclose(Mw, Mdef, rtol=0, atol=1e-4 * scale), variant.__name__
+
+
+def _textbook_pcg(A, Minv, b, dotf, iters):
+    """Preconditioned CG with beta = (z_{k+1}, r_{k+1}) / (z_k, r_k), x0 = 0, fixed count."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    z = Minv(r)
+    pv = z.copy()
+    rz = dotf(r, z)
+    for _ in range(iters):
+        w = A(pv)
+        alpha = rz / dotf(pv, w)
+        x = x + alpha * pv
+        r = r - alpha * w
+        z = Minv(r)
+        rz_new = dotf(r, z)
+        pv = z + (rz_new / rz) * pv
+        rz = rz_new
+    return x
+
+
+def _fpcg_case():
+    nel = (2, 2, 2)
+    V = wl.vertex_lattice(nel, 0.1, seed=4)
+    lv, b = o.problem(V, nel, 4)
+    d = o.jacobi_diag(lv)
+    return lv, b, d
+
+
+def test_fpcg_reduces_to_textbook_pcg_for_a_fixed_preconditioner():
+    """With a fixed symmetric positive definite preconditioner (z_{k+1}, r_k) = 0 in exact
+    arithmetic, so the flexible beta of Sec. 2.2 equals the textbook one and the iterates of
+    the two methods agree step by step."""
+    lv, b, d = _fpcg_case()
+    A = lambda u: o.ax(lv, u)
+    M = lambda r: lv.mask * r / d
+    dotf = lambda a, c: o.dot(lv, a, c)
+    for k in (1, 2, 5, 12, 20):
+        xf, it, _ = o.fpcg(A, M, b, np.zeros_like(b), dotf, tol=0.0, maxit=k)
+        assert it == k
+        xt = _textbook_pcg(A, M, b, dotf, k)
+        assert np.max(np.abs(xf - xt)) <= 1e-12 * np.max(np.abs(xt)), k
+
+
+def test_fpcg_keeps_consecutive_directions_conjugate_under_a_varying_preconditioner():
+    """The flexible beta = (z_{k+1}, r_{k+1} - r_k) / (z_k, r_k) is the one that makes each new
+    search direction A-conjugate to the previous one, (p_{k+1}, A p_k) = 0, whatever the
+    preconditioner does between iterations (here: a different positive diagonal scaling per
+    call).  The search directions are read off the operator's inputs.  The textbook beta loses
+    the property under the same preconditioner."""
+    lv, b, d = _fpcg_case()
+    dotf = lambda a, c: o.dot(lv, a, c)
+    rng = np.random.default_rng(11)
+
+    def run(method):
+        seen = []
+
+        def A(u):
+            seen.append(u.copy())
+            return o.ax(lv, u)
+
+        def M(r):
+            s = o.from_global(lv, rng.uniform(0.2, 5.0, lv.n_global))
+            return lv.mask * r * s / d
+
+        if method == "flexible":
+            o.fpcg(A, M, b, np.zeros_like(b), dotf, tol=0.0, maxit=8)
+            dirs = seen[1:]                       # the first call forms r_0 = b - A x_0
+        else:
+            _textbook_pcg(A, M, b, dotf, 8)
+            dirs = seen
+        cos = []
+        for pk, pn in zip(dirs, dirs[1:]):
+            Apk = o.ax(lv, pk)
+            cos.append(abs(dotf(pn, Apk)) / math.sqrt(dotf(pn, o.ax(lv, pn)) * dotf(pk, Apk)))
+        return np.array(cos)
+
+    assert run("flexible").max() <= 1e-12
+    assert run("textbook").max() >= 1e-3
