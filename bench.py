@@ -35,7 +35,7 @@ WORKLOADS = {
 SAMPLE = dict(nel=(10, 10, 10), p=7, perturb=0.05, seed=0, schedule=(7, 5, 3, 1))
 METRIC = "Poisson solve time & Ax/smoother GDOF/s (%HBM roof); served solves/s, p99"
 FP64_FMA_PER_CLK_PER_SM = 2      # GB300: 1.25 TFLOP/s FP64 nominal at 152 SMs x 2.07 GHz
-N_SMS = 152
+N_SMS_NOMINAL = 152              # used only when no device is there to ask (host-side tests)
 
 
 def peaks():
@@ -129,12 +129,13 @@ VARIANT_KIND = ("f64", "f32", "df64")
 DF64_INSTR_PER_FLOP = 7.5   # a df64 FMA (2 flops) is 15 FP32 instructions (see csrc/df64.h)
 
 
-def alu_peak_tflops(kind, sm_max_mhz):
-    """Derived ALU peak: 152 SMs x (128 FP32 | 2 FP64) FMA lanes per clock x 2 flop x clock;
-    df64: the FP32 instruction rate (152 x 128 x clock) / 7.5 FP32 instructions per df64 flop."""
+def alu_peak_tflops(kind, sm_max_mhz, sms=N_SMS_NOMINAL):
+    """Derived ALU peak: SMs x (128 FP32 | 2 FP64) FMA lanes per clock x 2 flop x clock;
+    df64: the FP32 instruction rate (SMs x 128 x clock) / 7.5 FP32 instructions per df64 flop.
+    The SM count is the device's (cudaDevAttrMultiProcessorCount) when a device is present."""
     if kind == "df64":
-        return N_SMS * 128 * sm_max_mhz * 1e6 / DF64_INSTR_PER_FLOP / 1e12
-    return N_SMS * (128 if kind == "f32" else FP64_FMA_PER_CLK_PER_SM) * 2 * sm_max_mhz * 1e6 / 1e12
+        return sms * 128 * sm_max_mhz * 1e6 / DF64_INSTR_PER_FLOP / 1e12
+    return sms * (128 if kind == "f32" else FP64_FMA_PER_CLK_PER_SM) * 2 * sm_max_mhz * 1e6 / 1e12
 
 
 def dram_traffic(kernel, variant):
@@ -155,7 +156,8 @@ def roofline(kernel, variant, d, pk, pk_kind):
     kind = VARIANT_KIND[variant // 32]
     fp32 = kind == "f32"
     sm_max = pk.get("sm_max_mhz", 2070.0)
-    alu = alu_peak_tflops(kind, sm_max)
+    sms = pk.get("sms", N_SMS_NOMINAL)
+    alu = alu_peak_tflops(kind, sm_max, sms)
     hbm = pk["hbm_gbs"]
     n = max(d["launches"], 1)
     avg_s = d["ms"] / n * 1e-3
@@ -169,10 +171,11 @@ def roofline(kernel, variant, d, pk, pk_kind):
                 "unit": "TFLOP/s", "frac": round(achieved / alu, 4), "traffic": traffic,
                 "algorithmic_bytes_per_launch": d["bytes"] / n, "flops_per_launch": d["flops"] / n,
                 "avg_launch_ms": round(avg_s * 1e3, 4), "traffic_source": src,
-                "peak_source": (f"derived: 152 SMs x 128 FP32 instr/clk x {sm_max:.0f} MHz / "
+                "peak_source": (f"derived: {sms} SMs x 128 FP32 instr/clk x {sm_max:.0f} MHz / "
                                 f"{DF64_INSTR_PER_FLOP} FP32 instr per df64 flop") if kind == "df64" else
-                               (f"derived: 152 SMs x {128 if fp32 else 2} {'FP32' if fp32 else 'FP64'} "
-                                f"FMA/clk x 2 flop x {sm_max:.0f} MHz")}
+                               (f"derived: {sms} SMs x {128 if fp32 else 2} {'FP32' if fp32 else 'FP64'} "
+                                f"FMA/clk x 2 flop x {sm_max:.0f} MHz"),
+                "measured_alu_tflops": pk.get("measured_alu_tflops")}
     achieved = d["bytes"] / n / avg_s / 1e9
     return {"bound": "hbm", "kernel": name, "achieved": round(achieved, 1), "peak": hbm,
             "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic,
@@ -180,6 +183,134 @@ def roofline(kernel, variant, d, pk, pk_kind):
             "avg_launch_ms": round(avg_s * 1e3, 4), "traffic_source": src,
             "peak_source": f"{pk_kind} (MEASURED_PEAKS.json hbm_gbs)" if pk_kind == "measured"
             else "fallback 6.8 TB/s"}
+
+
+def profiled_variants(se, solve, steps, stream):
+    """Runs `solve` (host-driven) `steps` times with every library launch bracketed by CUDA events
+    on its stream; returns (ms per solve of the pass, per-class totals, per-variant totals)."""
+    import torch
+    se.se_prof_reset()
+    se.se_prof_enable(True)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("profiled_pass")  # lets a profiler select exactly these launches
+    p0.record(stream)
+    for _ in range(steps):
+        solve()
+    p1.record(stream)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    se.se_prof_enable(False)
+    prof = {se.KERNEL_NAMES[k]: se.se_prof_query(k) for k in range(se.SE_K_COUNT)}
+    variants = {}
+    for k in range(se.SE_K_COUNT):
+        for v in range(96):
+            q = se.se_prof_query_variant(k, v)
+            if q["launches"]:
+                variants[(se.KERNEL_NAMES[k], v)] = q
+    return p0.elapsed_time(p1) / steps, prof, variants
+
+
+def kernel_table(variants, steps, pk, pk_kind):
+    """Per kernel class x level order x precision: time per step, launches, share, and the
+    fraction of its own binding roof (algorithmic bytes or flops per launch)."""
+    tot_ms = max(sum(v["ms"] for v in variants.values()), 1e-9)
+    kernels = {}
+    for (k, v), q in sorted(variants.items(), key=lambda kv: -kv[1]["ms"]):
+        r = roofline(k, v, q, pk, pk_kind) if q["ms"] > 0 and (q["bytes"] > 0 or q["flops"] > 0) else None
+        kernels[f"{k} p={v % 32} {VARIANT_KIND[v // 32]}"] = {
+            "ms_per_step": round(q["ms"] / steps, 3),
+            "launches_per_step": q["launches"] / steps, "share": round(q["ms"] / tot_ms, 4),
+            "bound": r["bound"] if r else None, "roof_frac": r["frac"] if r else None}
+    return kernels
+
+
+def measured_alu(se, stream):
+    """FMA throughput measured on this device (se_prof_fma_peak) and its SM count."""
+    out, sms = {}, None
+    for kind, name in ((0, "f64"), (1, "f32"), (2, "f32x2")):
+        t, sms = se.se_prof_fma_peak(kind, stream)
+        out[name] = round(t, 3)
+    return out, sms
+
+
+def schwarz_record(se, m, b, x, stream, wk, pk, pk_kind, op_df, steps):
+    """The paper's own smoother on the same mesh and right-hand side: Cheby-RAS(2) on the
+    workload's schedule, with the FP64 V-cycle and with the FP32 V-cycle (FP64 Krylov), each
+    timed as graph solves, then profiled host-driven for its FDM kernels' roof fractions."""
+    import torch
+    rec = {}
+    for name, prec in (("fp64", se.SE_FP64), ("fp32_vcycle", se.SE_FP32)):
+        t0 = time.perf_counter()
+        P = se.se_pmg_setup(m, se.pmg_desc(wk["schedule"], se.SE_SMOOTH_RAS, 2, precision=prec))
+        torch.cuda.synchronize()
+        setup_ms = (time.perf_counter() - t0) * 1e3
+        try:
+            def solve(graph=1):
+                x.zero_()
+                return se.se_solve(m, P, b, x, tol=1e-8, maxit=500, stream=stream,
+                                   graph_capture=graph, operator_df64=op_df)
+            for _ in range(2):
+                st = solve()
+            k = max(2, min(steps, 5))
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(k):
+                st = solve()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / k
+            solve(graph=0)
+            torch.cuda.synchronize()
+            _, _, variants = profiled_variants(se, lambda: solve(graph=0), 1, stream)
+            table = kernel_table(variants, 1, pk, pk_kind)
+            fdm = {}
+            for (kk, v), q in variants.items():
+                if kk == "fdm":
+                    r = roofline(kk, v, q, pk, pk_kind)
+                    fdm[r["kernel"]] = {"ms_per_launch": r["avg_launch_ms"],
+                                        "launches_per_solve": q["launches"], "bound": r["bound"],
+                                        "achieved": r["achieved"], "unit": r["unit"],
+                                        "peak": r["peak"], "roof_frac": r["frac"],
+                                        "algorithmic_bytes_per_launch": r["algorithmic_bytes_per_launch"],
+                                        "flops_per_launch": r["flops_per_launch"]}
+            rec[name] = {"preconditioner": "Cheby-RAS(2)", "schedule": list(wk["schedule"]),
+                         "precision": "FP64 V-cycle" if prec == se.SE_FP64
+                         else "FP32 V-cycle, FP64 Krylov/coarse/Arnoldi",
+                         "ms_per_solve": round(ms, 3), "timed_solves": k,
+                         "iterations": st.iterations, "rel_residual": st.rel_residual,
+                         "setup_ms": round(setup_ms, 1), "fdm": fdm,
+                         "kernels": dict(list(table.items())[:6])}
+        finally:
+            se.se_pmg_destroy(P)
+    return rec
+
+
+def run_peaks(args):
+    """ALU roofs of this GPU (FMA throughput, se_prof_fma_peak) next to the derived peaks the
+    roofline divides by, with the clocks sampled while the probes ran."""
+    import torch
+    from paper_2110_07663_gb300 import se
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    se.se_prof_fma_peak(1, stream)  # warm-up: clocks ramp, module load
+    with ClockSampler(0) as clk:
+        meas, sms = {}, None
+        for _ in range(3):
+            for kind, name in ((0, "f64"), (1, "f32"), (2, "f32x2")):
+                t, sms = se.se_prof_fma_peak(kind, stream)
+                meas[name] = max(meas.get(name, 0.0), round(t, 3))
+    pk, _ = peaks()
+    sm_max = pk.get("sm_max_mhz", 2070.0)
+    derived = {k: round(alu_peak_tflops(k, sm_max, sms), 4) for k in ("f64", "f32", "df64")}
+    print(json.dumps({"measured_fma_tflops": meas, "sms": sms, "derived_tflops": derived,
+                      "derived_from": f"{sms} SMs x FMA lanes/clk (FP64 2, FP32 128) x 2 flop x "
+                                      f"{sm_max:.0f} MHz",
+                      "frac_of_derived": {"f64": round(meas["f64"] / derived["f64"], 4),
+                                          "f32": round(meas["f32"] / derived["f32"], 4),
+                                          "f32x2": round(meas["f32x2"] / derived["f32"], 4)},
+                      "clocks": clk.summary(),
+                      "gpu": torch.cuda.get_device_name(0)}))
 
 
 def run_gpu(args):
@@ -268,25 +399,7 @@ def run_gpu(args):
     # bracketed by CUDA events on its stream; gives the per-kernel times and the roofline
     step(graph=0)
     torch.cuda.synchronize()
-    se.se_prof_reset()
-    se.se_prof_enable(True)
-    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.nvtx.range_push("profiled_pass")  # lets a profiler select exactly these launches
-    p0.record(stream)
-    for _ in range(args.steps):
-        step(graph=0)
-    p1.record(stream)
-    torch.cuda.synchronize()
-    torch.cuda.nvtx.range_pop()
-    se.se_prof_enable(False)
-    host_loop_ms = p0.elapsed_time(p1) / args.steps
-    prof = {se.KERNEL_NAMES[k]: se.se_prof_query(k) for k in range(se.SE_K_COUNT)}
-    variants = {}
-    for k in range(se.SE_K_COUNT):
-        for v in range(96):
-            q = se.se_prof_query_variant(k, v)
-            if q["launches"]:
-                variants[(se.KERNEL_NAMES[k], v)] = q
+    host_loop_ms, prof, variants = profiled_variants(se, lambda: step(graph=0), args.steps, stream)
     # our kernels per timed step: those of the profiled pass plus the graph's own control
     # kernels (one at the start, one convergence test per iteration)
     launches = sum(v["launches"] for v in prof.values()) + args.steps * (1 + iters)
@@ -323,17 +436,13 @@ def run_gpu(args):
         dtype = "f64+df64"
     # ---- roofline of the dominant kernel (kernel class x level order x precision)
     pk, pk_kind = peaks()
+    pk["measured_alu_tflops"], pk["sms"] = measured_alu(se, stream)
     (dom, dvar), d = max(variants.items(), key=lambda kv: kv[1]["ms"])
     roof = roofline(dom, dvar, d, pk, pk_kind)
-    tot_ms = max(sum(v["ms"] for v in variants.values()), 1e-9)
-    kernels = {}
-    for (k, v), q in sorted(variants.items(), key=lambda kv: -kv[1]["ms"]):
-        r = roofline(k, v, q, pk, pk_kind) if q["ms"] > 0 and (q["bytes"] > 0 or q["flops"] > 0) else None
-        kernels[f"{k} p={v % 32} {VARIANT_KIND[v // 32]}"] = {
-            "ms_per_step": round(q["ms"] / args.steps, 3),
-            "launches_per_step": q["launches"] / args.steps, "share": round(q["ms"] / tot_ms, 4),
-            # each kernel against its own binding roof (algorithmic bytes or flops per launch)
-            "bound": r["bound"] if r else None, "roof_frac": r["frac"] if r else None}
+    kernels = kernel_table(variants, args.steps, pk, pk_kind)
+    schwarz = None
+    if not args.no_schwarz:
+        schwarz = schwarz_record(se, m, b, x, stream, wk, pk, pk_kind, op_df, args.steps)
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": "GDOF/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 3),
@@ -345,6 +454,9 @@ def run_gpu(args):
                                   else f"Cheby-{sm_names[smoother]}({cheb_order}), ")
                                + f"FPCG tol 1e-8, {prec_name} preconditioner, {op_name} outer operator",
                    "iterations": iters, "setup_s": round(setup_s, 2),
+                   "time_to_solution_cold_s": round(setup_s + ms_max * 1e-3, 3),
+                   "e2e_scope": ("per step: b host->device, the graph solve, x device->host; mesh and "
+                                 "preconditioner set-up (setup_s, incl. the search) are outside it"),
                    "preconditioner_choice": ("run-time search (Sec. 5) over Cheby-RAS(k), Cheby-Jac(k), "
                                              "k = 1..3, inside set-up" if search else "fixed by --smoother"),
                    "preconditioner_search": search,
@@ -361,6 +473,7 @@ def run_gpu(args):
         "roofline": roof,
         "kernels": kernels,
         "clocks": clk.summary(),
+        "schwarz": schwarz,
     }
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline_subprocess(args.cpu_timeout, sm_names[smoother], cheb_order)
@@ -403,9 +516,10 @@ def cpu_baseline_subprocess(timeout_s, smoother="ras", order=2):
                            timeout=timeout_s, env=env)
         v, t, it = json.loads(r.stdout.strip().splitlines()[-1])
     except Exception as e:  # noqa: BLE001
-        return {"value": None, "unit": "GDOF/s", "cores": 1, "kind": "oracle",
-                "sample": f"failed: {type(e).__name__}"}
-    return {"value": round(v, 6), "unit": "GDOF/s", "cores": 1, "kind": "oracle",
+        return {"value": None, "unit": "GDOF/s", "cores": 1, "nproc": os.cpu_count(),
+                "kind": "oracle", "sample": f"failed: {type(e).__name__}"}
+    return {"value": round(v, 6), "unit": "GDOF/s", "cores": 1, "nproc": os.cpu_count(),
+            "kind": "oracle",
             "sample": f"one full solve of a 10x10x10-element p=7 piece of the same workload "
                       f"(same map, schedule, smoother Cheby-{smoother}({order}), tolerance): {it} "
                       f"iterations in {t:.1f} s, single thread"}
@@ -498,6 +612,7 @@ def run_batch(args):
                         "iterations_min_max": [min(its64), max(its64)],
                         "speedup_of_batch": round(ms64 / ms, 2)},
         "clocks": clk.summary(),
+        "schwarz": schwarz,
     }
     print(json.dumps(out))
 
@@ -861,7 +976,7 @@ def run_reference(args):
                                f"Cheby-{smoother}({order})",
                    "preconditioner_search": search, "parallelism": "cpu"},
         "cpu_baseline": {"value": round(value, 6), "unit": "GDOF/s", "cores": env_threads,
-                         "kind": "oracle",
+                         "nproc": os.cpu_count(), "kind": "oracle",
                          "sample": f"each step one full oracle solve of a 10x10x10-element p=7 piece "
                                    f"of the workload with Cheby-{smoother}({order})"},
         "e2e": {"value": round(value, 6), "unit": "GDOF/s", "h2d_bytes_per_step": 0,
@@ -891,6 +1006,10 @@ def main():
     ap.add_argument("--operator-df64", action="store_true",
                     help="df64 outer operator (solve, batch, serve); serve: also df64 Arnoldi set-up")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-schwarz", action="store_true",
+                    help="skip the Cheby-RAS(2) FP64 / FP32-V-cycle record of the headline line")
+    ap.add_argument("--peaks", action="store_true",
+                    help="measure the FP64 / FP32 / packed-FP32 FMA roofs of this GPU and exit")
     ap.add_argument("--cpu-timeout", type=float, default=240.0)
     ap.add_argument("--batch", type=int, default=0, help="run the batched workload of N problems")
     ap.add_argument("--serve", type=int, default=0, help="run the serving workload of N requests")
@@ -927,6 +1046,8 @@ def main():
         ap.error("--cycle additive needs --smoother ras or asm (the additive V-cycle has no Chebyshev)")
     if args.impl == "reference":
         run_reference(args)
+    elif args.peaks:
+        run_peaks(args)
     elif args.batch:
         run_batch(args)
     elif args.serve:

@@ -121,6 +121,13 @@ int se_mesh_rhs(se_mesh_t m, const double* f_dev, double* b_dev, void* stream);
  * outputs stay FP64.  A_L is applied by tensor-product sum factorisation
  * (Sec. 1: ~7E(p+1)^3 reads, 12E(p+1)^4 operations).  u and y must not overlap. */
 int se_ax(se_mesh_t m, const double* u, double* y, int flags, void* stream);
+/* Residual r = M (b - QQ^T A_L u), the step "r = b - A x" of Algorithm 1 (Sec. 2.2.2) in one
+ * operator pass: the local kernel outputs b / multiplicity - A_L u, whose QQ^T is the residual.
+ * b: continuous, masked L-vector; u: L-vector that is zero on Dirichlet nodes (it is used as
+ * given).  flags: 0 (FP64), SE_AX_FP32 (computed in FP32; the first such call allocates one more
+ * L-vector of floats, owned by the mesh) or SE_AX_DF64.  r must overlap neither b nor u;
+ * SE_EINVAL otherwise. */
+int se_residual(se_mesh_t m, const double* b, const double* u, double* r, int flags, void* stream);
 /* In place u <- [M] QQ^T u (Sec. 2.1, gather-scatter); mask != 0 also zeroes Dirichlet nodes. */
 int se_gs(se_mesh_t m, double* u, int mask, void* stream);
 /* ---------------------------------------------------------------- QQ^T index map (Sec. 2.1) */
@@ -228,7 +235,8 @@ int se_pmg_coarse_solve(se_pmg_t pmg, const double* r, double* x, int* iters, vo
  * GPU that loads the library until the process exits), so the coarsest level may have at most
  * 131072 global nodes; larger problems get SE_EINVAL.  The first call on each device looks up
  * the array's device address with that device current; make that first call before any stream
- * capture.  The caller passes r and x (coarse L-vectors) as for se_pmg_coarse_solve.  All calls
+ * capture.  The address is kept for the life of the process, so the entry point must not be
+ * called again after cudaDeviceReset on that device.  The caller passes r and x (coarse L-vectors) as for se_pmg_coarse_solve.  All calls
  * share the one array, which keeps the last call's contents (the call resets what must start at
  * zero): calls whose work overlaps on the GPU (other streams, other threads, other handles)
  * race and must be serialised by the caller.  Synchronises the stream. */
@@ -442,6 +450,13 @@ int se_prof_query(int kind, double* ms_total, int64_t* launches, double* units, 
  * FP32 arithmetic (e.g. 7 = FP64 kernels of p = 7 levels, 39 = FP32 kernels of p = 7 levels). */
 int se_prof_query_variant(int kind, int variant, double* ms_total, int64_t* launches,
                           double* units, double* bytes, double* flops);
+
+/* ALU roof of this GPU for the roofline of arithmetic-bound kernels (measurement only; the paper
+ * has no counterpart): fused multiply-add throughput with independent chains on every SM,
+ * kind 0 = FP64, 1 = FP32, 2 = FP32 in packed pairs (fma.rn.f32x2).  *tflops receives the best
+ * of three timed launches (2 flops per FMA), *sms (may be NULL) the device's SM count.  The
+ * launches go to `stream` (NULL: the legacy default stream); the call synchronises. */
+int se_prof_fma_peak(int kind, double* tflops, int* sms, void* stream);
 
 /* ---------------------------------------------------------------- self-test of bounded waits */
 /* Runs the library's grid barrier with one more expected arrival than blocks launched, so no

@@ -1,8 +1,8 @@
 """Compile libse.so (all CUDA sources under csrc/) for sm_103a with nvcc, in-tree.
 
 Translation units compile in parallel into _build/; the shared library is linked next to this
-file.  A unit is recompiled when it or any header under csrc/ or include/ is newer than its
-object file.
+file.  A unit is recompiled when it, any header under csrc/ or include/, or this script is newer
+than its object file.
 """
 from __future__ import annotations
 
@@ -28,14 +28,19 @@ def nvcc() -> str:
 
 
 def flags() -> list:
-    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
+    # host code: no floating-point contraction, so that set-up arithmetic (vertex lattice, box
+    # lengths, Hessenberg eigenvalues) gives the same bits on x86 and aarch64 (gcc contracts
+    # a*b+c into fma by default on aarch64)
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+                   "-Xcompiler", "-ffp-contract=off", "-I", INCLUDE,
                    "-I", CSRC, "--expt-relaxed-constexpr", "-Xcudafe", "--diag_suppress=177"]
 
 
 def _compile(src: str, extra: list) -> str:
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
     headers = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.h"))
-    newest = max([os.path.getmtime(src)] + [os.path.getmtime(h) for h in headers])
+    newest = max([os.path.getmtime(src), os.path.getmtime(__file__)] +
+                 [os.path.getmtime(h) for h in headers])
     if os.path.exists(obj) and os.path.getmtime(obj) >= newest:
         return obj
     cmd = [nvcc(), "-c", src, "-o", obj] + flags() + extra

@@ -537,6 +537,30 @@ int se_ax(se_mesh_t m, const double* u, double* y, int flags, void* stream) {
   return SE_OK;
 }
 
+int se_residual(se_mesh_t m, const double* b, const double* u, double* r, int flags, void* stream) {
+  SE_CHECK(m && b && u && r, SE_EINVAL, "se_residual: null argument");
+  SE_CHECK(r != u && r != b, SE_EINVAL, "se_residual: r must not overlap b or u");
+  SE_CHECK((flags & ~(SE_AX_FP32 | SE_AX_DF64)) == 0 && flags != (SE_AX_FP32 | SE_AX_DF64),
+           SE_EINVAL, "se_residual: flags must be 0, SE_AX_FP32 or SE_AX_DF64");
+  cudaStream_t s = as_stream(stream, m->stream);
+  Level& lv = m->fine;
+  if (flags & SE_AX_FP32) {
+    SE_TRY(make_fp32_geometry(lv, m->allocs, s));
+    if (!m->tmpc32) SE_TRY(dmalloc(m->allocs, &m->tmpc32, (size_t)lv.L));
+    SE_TRY((convert<double, float>(u, m->tmpa32, lv.L, s)));
+    SE_TRY((convert<double, float>(b, m->tmpc32, lv.L, s)));
+    SE_TRY(residual_apply<float>(lv, m->tmpc32, m->tmpa32, m->tmpb32, s));
+    return convert<float, double>(m->tmpb32, r, lv.L, s);
+  }
+  if (flags & SE_AX_DF64) {
+    SE_TRY(make_df_geometry(lv, m->allocs, s));
+    Level ld = lv;
+    ld.df = true;
+    return residual_apply<double>(ld, b, u, r, s);
+  }
+  return residual_apply<double>(lv, b, u, r, s);
+}
+
 int se_gs(se_mesh_t m, double* u, int mask, void* stream) {
   SE_CHECK(m && u, SE_EINVAL, "se_gs: null argument");
   return gs_apply<double>(m->fine, u, mask != 0, as_stream(stream, m->stream));

@@ -1,0 +1,110 @@
+// ALU roofs of this GPU for the roofline of the arithmetic-bound kernels (FP64 operator and FDM,
+// FP32 FDM): the fused multiply-add throughput in FP64, FP32, and FP32 in packed pairs
+// (fma.rn.f32x2, two lanes per instruction), measured with independent FMA chains per thread.
+// This is measurement infrastructure; the paper has no counterpart.
+#include <algorithm>
+
+#include "se_internal.h"
+
+namespace se {
+
+constexpr int PROBE_CHAINS = 8;
+__device__ float g_probe_sink32;   // written only if a chain reaches an impossible value: keeps
+__device__ double g_probe_sink64;  // the chains live without a store per thread
+
+template <int KIND>
+__global__ void __launch_bounds__(256) fma_probe_kernel(int iters, float a32, float b32, double a64,
+                                                        double b64) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if constexpr (KIND == 0) {
+    double x[PROBE_CHAINS];
+#pragma unroll
+    for (int c = 0; c < PROBE_CHAINS; ++c) x[c] = 1e-3 * (t + c);
+#pragma unroll 1
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+      for (int c = 0; c < PROBE_CHAINS; ++c) x[c] = fma(x[c], a64, b64);
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < PROBE_CHAINS; ++c) s += x[c];
+    if (s == 12345.678) g_probe_sink64 = s;  // never true (each chain tends to b / (1 - a))
+  } else if constexpr (KIND == 1) {
+    float x[PROBE_CHAINS];
+#pragma unroll
+    for (int c = 0; c < PROBE_CHAINS; ++c) x[c] = 1e-3f * (t + c);
+#pragma unroll 1
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+      for (int c = 0; c < PROBE_CHAINS; ++c) x[c] = fmaf(x[c], a32, b32);
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < PROBE_CHAINS; ++c) s += x[c];
+    if (s == 12345.678f) g_probe_sink32 = s;
+  } else {
+    float2 x[PROBE_CHAINS];
+#pragma unroll
+    for (int c = 0; c < PROBE_CHAINS; ++c) x[c] = make_float2(1e-3f * (t + c), 2e-3f * (t + c));
+    const float2 a2 = make_float2(a32, a32), b2 = make_float2(b32, b32);
+#pragma unroll 1
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+      for (int c = 0; c < PROBE_CHAINS; ++c) x[c] = __ffma2_rn(x[c], a2, b2);
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < PROBE_CHAINS; ++c) s += x[c].x + x[c].y;
+    if (s == 12345.678f) g_probe_sink32 = s;
+  }
+}
+
+template <int KIND>
+static int run_probe(int sms, cudaStream_t s, double* tflops) {
+  // FP64 issues at 1/64 of the FP32 rate: fewer iterations keep its launch near the others'
+  const int iters = KIND == 0 ? 1024 : 16384;
+  const int threads = 256;
+  int per_sm = 0;
+  SE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fma_probe_kernel<KIND>, threads, 0));
+  SE_CHECK(per_sm >= 1, SE_ECUDA, "fma probe: no resident block");
+  const int blocks = sms * per_sm;
+  cudaEvent_t e0, e1;
+  SE_CUDA(cudaEventCreate(&e0));
+  SE_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int st = SE_OK;
+  for (int rep = 0; rep < 4 && st == SE_OK; ++rep) {  // first launch warms up
+    cudaEventRecord(e0, s);
+    fma_probe_kernel<KIND><<<blocks, threads, 0, s>>>(iters, 0.999999f, 1e-7f, 0.999999999, 1e-9);
+    cudaEventRecord(e1, s);
+    if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+      set_error("fma probe: launch failed");
+      st = SE_ECUDA;
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0) best = std::min(best, ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != SE_OK) return st;
+  const double fmas = (double)blocks * threads * iters * PROBE_CHAINS * (KIND == 2 ? 2 : 1);
+  *tflops = 2.0 * fmas / (best * 1e-3) / 1e12;
+  return SE_OK;
+}
+
+}  // namespace se
+
+using namespace se;
+
+extern "C" int se_prof_fma_peak(int kind, double* tflops, int* sms, void* stream) {
+  SE_CHECK(tflops && kind >= 0 && kind <= 2, SE_EINVAL, "se_prof_fma_peak: bad argument");
+  int dev = 0, n = 0;
+  SE_CUDA(cudaGetDevice(&dev));
+  SE_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+  if (sms) *sms = n;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  switch (kind) {
+    case 0: return run_probe<0>(n, s, tflops);
+    case 1: return run_probe<1>(n, s, tflops);
+    default: return run_probe<2>(n, s, tflops);
+  }
+}

@@ -177,6 +177,7 @@ struct se_mesh_s {
   double* tmp64 = nullptr;       // [L] work vector
   float* tmpa32 = nullptr;       // [L]
   float* tmpb32 = nullptr;       // [L]
+  float* tmpc32 = nullptr;       // [L], allocated by the first FP32 se_residual
   // outer-solver work vectors, allocated on the first se_solve
   double *sr = nullptr, *sr2 = nullptr, *sz = nullptr, *sp = nullptr, *sw = nullptr;
   int gm_m = 0;                  // FGMRES restart length the V/Z blocks were sized for

@@ -125,6 +125,8 @@ _SIGS = {
     "se_mesh_vertices": ([_vp, _dp], C.c_int),
     "se_mesh_rhs": ([_vp, _vp, _vp, _vp], C.c_int),
     "se_ax": ([_vp, _vp, _vp, _ip, _vp], C.c_int),
+    "se_residual": ([_vp, _vp, _vp, _vp, _ip, _vp], C.c_int),
+    "se_prof_fma_peak": ([_ip, C.POINTER(C.c_double), C.POINTER(_ip), _vp], C.c_int),
     "se_gs": ([_vp, _vp, _ip, _vp], C.c_int),
     "se_gsmap_create": ([C.c_int64, _vp, _vp, C.POINTER(_vp)], C.c_int),
     "se_gsmap_apply": ([_vp, _vp, _ip, _vp], C.c_int),
@@ -264,6 +266,10 @@ def se_mesh_rhs(m, f, b, stream=None):
 
 def se_ax(m, u, y, flags=SE_AX_ASSEMBLE | SE_AX_MASK, stream=None):
     _check(lib.se_ax(m, _ptr(u), _ptr(y), flags, _stream(stream)))
+
+
+def se_residual(m, b, u, r, flags=0, stream=None):
+    _check(lib.se_residual(m, _ptr(b), _ptr(u), _ptr(r), flags, _stream(stream)))
 
 
 def se_gs(m, u, mask=1, stream=None):
@@ -627,6 +633,13 @@ def se_prof_query_variant(kind, variant):
 
 def se_selftest_wait_timeout(timeout_ms=100.0) -> int:
     return lib.se_selftest_wait_timeout(timeout_ms)
+
+
+def se_prof_fma_peak(kind, stream=None):
+    """Measured FMA throughput (TFLOP/s) and SM count: kind 0 FP64, 1 FP32, 2 packed FP32 pairs."""
+    t, n = C.c_double(), _ip()
+    _check(lib.se_prof_fma_peak(int(kind), C.byref(t), C.byref(n), _stream(stream)))
+    return t.value, n.value
 
 
 def se_selftest_fail_alloc(n):

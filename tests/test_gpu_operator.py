@@ -158,3 +158,37 @@ def test_invalid_arguments_are_rejected():
             se.se_pmg_setup(c.m, se.pmg_desc((3, 2)))             # coarsest must be p = 1
     finally:
         c.close()
+
+
+def test_fp32_pipelined_operator_steady_state_and_residual_forms():
+    """The persistent FP32 operator at p = 7 on a mesh large enough that every block loops over
+    at least three element groups (so the stage refills and the mbarrier phase flips run), with a
+    ragged last group (4095 elements is not a multiple of the group size), in its plain and its
+    fused-residual forms, against the oracle element by element.  The residual form is reached
+    through se_residual: r = M (b - QQ^T A_L u), the step r = b - A x of Algorithm 1.  The FP64
+    (even-odd folded) and df64 residual forms are checked on the same mesh."""
+    nel, p = (13, 15, 21), 7
+    c = Case(nel, p, seed=41)
+    try:
+        se = c.se
+        sms = c.torch.cuda.get_device_properties(0).multi_processor_count
+        groups = -(-c.info.E // 4)                     # default group of 4 elements at p = 7
+        assert groups >= 3 * sms and c.info.E % 4 != 0
+        u = c.random_continuous(4, masked=False)
+        ug, y = c.to_gpu(u), c.empty()
+        se.se_ax(c.m, ug, y, se.SE_AX_FP32)
+        assert rel_err(c.to_np(y), o.ax_local(c.lv, u)) <= 2e-5
+        se.se_ax(c.m, ug, y, se.SE_AX_FP32 | se.SE_AX_ASSEMBLE)
+        assert rel_err(c.to_np(y), o.ax(c.lv, u, mask=False)) <= 2e-5
+        um = c.random_continuous(5)
+        b = c.random_continuous(6)
+        ref = b - o.ax(c.lv, um)
+        r = c.empty()
+        for flags, tol in ((se.SE_AX_FP32, 2e-5), (0, 1e-12), (se.SE_AX_DF64, 1e-12)):
+            r.fill_(float("nan"))
+            se.se_residual(c.m, c.to_gpu(b), c.to_gpu(um), r, flags)
+            assert rel_err(c.to_np(r), ref) <= tol, flags
+        with pytest.raises(se.SeError):
+            se.se_residual(c.m, c.to_gpu(b), ug, ug, 0)
+    finally:
+        c.close()

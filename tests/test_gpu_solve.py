@@ -226,3 +226,52 @@ def test_degenerate_problems(method, graph):
             if P:
                 se.se_pmg_destroy(P)
             c.close()
+
+
+@pytest.mark.parametrize("graph", [0, 1])
+def test_headline_configuration_against_the_oracle(graph):
+    """The benchmark's own solve on a smaller piece of its workload: 6^3 elements of the map
+    with the interior lattice vertices perturbed by up to 5% of h (seed 0, the library's
+    generator), p = 7, pMG 7-5-3-1 with Chebyshev-Jacobi order 1 on every smoothed level
+    (Algorithms 1-2), coarse Jacobi-PCG, FPCG to 1e-8, host-driven and as one graph launch.
+    Iterations within one of the oracle's; true residual and solution checked with the
+    oracle's operator and solution."""
+    from tests.gpu_common import gpu
+    torch, se = gpu()
+    nel, p, sched = (6, 6, 6), 7, (7, 5, 3, 1)
+    m = se.se_mesh_create(nel, p, perturb_frac=0.05, seed=0, deform_amp=wl.DEFORM_AMP)
+    P = None
+    try:
+        V = wl.vertex_lattice(nel, 0.05, seed=0)
+        Vg = np.empty(V.size)
+        se.se_mesh_vertices(m, Vg)
+        assert np.array_equal(Vg, V.reshape(-1))
+        info = se.se_mesh_get_info(m)
+        dev = torch.device("cuda:0")
+        xyz = torch.empty(3 * info.L, dtype=torch.float64, device=dev)
+        se.se_mesh_nodes(m, xyz)
+        X = xyz.cpu().numpy().reshape(3, -1)
+        b = torch.empty(info.L, dtype=torch.float64, device=dev)
+        se.se_mesh_rhs(m, torch.from_numpy(wl.f_rhs(X[0], X[1], X[2])).to(dev), b)
+        P = se.se_pmg_setup(m, se.pmg_desc(sched, se.SE_SMOOTH_JACOBI, 1))
+        x = torch.zeros_like(b)
+        st = se.se_solve(m, P, b, x, method=se.SE_FPCG, tol=1e-8, graph_capture=graph)
+        lvo, bo = o.problem(V, nel, p, amp=wl.DEFORM_AMP)
+        pmg = o.pmg_setup(V, nel, sched, smoother="jacobi", order=1, amp=wl.DEFORM_AMP)
+        for l in range(len(sched) - 1):
+            lam = se.se_pmg_lambda(P, l)
+            assert abs(lam - pmg.lam[l]) <= 1e-9 * pmg.lam[l]
+        xo, it_o, _ = o.solve(lvo, bo, pmg, tol=1e-8)
+        xg = x.cpu().numpy().reshape(xo.shape)
+        assert np.max(np.abs(b.cpu().numpy().reshape(bo.shape) - bo)) <= 1e-13 * np.max(np.abs(bo))
+        assert st.rel_residual <= 1e-8
+        assert abs(st.iterations - it_o) <= 1, (st.iterations, it_o)
+        r = bo - o.ax(lvo, xg)
+        assert math.sqrt(o.dot(lvo, r, r) / o.dot(lvo, bo, bo)) <= 1.5e-8
+        assert rel_err(xg, xo) <= 1e-6
+        print(f"headline config 6^3 (graph={graph}): gpu {st.iterations} it, oracle {it_o} it, "
+              f"max rel diff {rel_err(xg, xo):.2e}")
+    finally:
+        if P:
+            se.se_pmg_destroy(P)
+        se.se_mesh_destroy(m)
