@@ -798,434 +798,256 @@ __global__ void __launch_bounds__(256, P <= 6 ? 4 : (P <= 8 ? 3 : 2)) fdm32_warp
   }
 }
 
-// ------------------------------------------------------------------ FP32 RAS, one thread per plane
-// For odd p (pbar = 6, 8, 10) the FP32 RAS solve gives each plane c of an element's window to one
-// thread (pbar threads per element, 32/pbar elements per warp):
-//  1. gather: the element's threads copy the window into shared memory with cp.async, thread t
-//     taking column a = t of every row (so a warp's copies read consecutive points of a row; the
-//     9 neighbours a column can touch are read once, every source offset is a constant of the
-//     unrolled loop plus one per-thread term), then each thread loads its plane c = t;
-//  2. S_x^T along a, then S_y^T along b, in registers, with S held in registers as packed pairs
-//     (fma.rn.f32x2 over two modes at a time);
-//  3. transpose through shared memory: the thread takes pbar columns (alpha, beta), applies S_z^T,
-//     D^-1 and S_z for the N own planes only;
-//  4. transpose back: thread t < N takes own plane t + 1, applies S_y then S_x for the own rows and
-//     columns only, weights by 1/multiplicity and stores the N^2 own points of the plane.
-// Shared memory holds only the window, the two transposes, S and Lambda; its strides make every
-// shared access of a warp fall in distinct banks (window plane stride PSN, element stride = pbar
-// mod 32, found by search over the three access patterns).  Per output the arithmetic is the same
-// sums as the warp kernel (forward: one packed chain per pair of modes in ascending order;
-// backward: even and odd terms in the two lanes, added at the end).
-// Used for p = 3 and 5 (measured on GB300 at 32^3 elements, FP32 V-cycle: p = 5 0.066 ms per
-// launch against 0.080 for the warp kernel and 0.072 for fdm32_plane_smem_kernel, p = 3 0.037
-// against 0.050 and 0.038).  At p = 7 a plane and S_x take 254 registers, so only 8 warps per SM
-// hide the gather's latency (0.193 ms against the warp kernel's 0.175); p = 7 uses
-// fdm32_plane_smem_kernel below (0.150 ms).
+// ------------------------------------------------------------------ FP32 RAS, plane/column per thread
+// GB300's FP32 pipe reaches its FMA rate only with packed pairs (fma.rn.f32x2: one instruction,
+// two lanes), and a warp alone cannot keep it busy (measured with independent chains per
+// thread: one warp per scheduler reaches about 60% of the packed rate, three about 90%).  This
+// kernel issues packed FMAs for every contraction and keeps as many warps per SM as its
+// registers and one window per element allow:
+//  * persistent blocks of independent warps; a warp owns EW = 32/pbar elements at a time (pbar
+//    lanes each) and walks the elements in steps of the grid's warp count; one shared-memory
+//    window per element and 8 warps per SM at p = 7, 12 at p = 3 and 5 (measured on GB300 at
+//    32^3 elements: faster than two stages per warp with 6 warps per SM, 0.150 ms at p = 7, and
+//    than 12 warps per SM at p = 7 with fewer registers per thread, 0.126 ms);
+//  * the window gather (cp.async, 4-byte copies, zero fill outside the domain), S and Lambda of a
+//    step are one cp.async group; the neighbour ids of the warp's next step are loaded into
+//    registers during the current step;
+//  * phase A, plane c = t per thread: the plane is read column by column into packed-pair
+//    accumulators (S_x^T, pairs of output modes), then S_y^T is applied in registers and the
+//    result written back in place;
+//  * phase B, the pbar columns (a = t, b) per thread: S_z^T into registers, D^-1 (hardware
+//    reciprocal of lambda_x + lambda_y + lambda_z), then S_z for the N own planes only;
+//  * phase C, own plane t + 1 per thread (t < N): the plane as row pairs and the own rows of S_x
+//    in registers; per own row, S_y then S_x (own columns), weights 1/multiplicity from the
+//    element's place in the lattice, contiguous stores;
+//  * outer loops stay rolled (small code), inner loops over registers are unrolled.
+// Shared strides: the window plane stride PSN and the element stride TOT = pbar (mod 32) put the
+// scalar accesses of every phase (plane rows, plane columns, columns across planes) of a warp's
+// active lanes in distinct banks.
 template <int PB>
-struct Fdm32PlaneDims {
-  static_assert(PB == 6 || PB == 8 || PB == 10, "plane kernel: pbar 6, 8 or 10 (odd p <= 7)");
-  static constexpr int N = PB - 2, H = PB / 2, EW = 32 / PB, WARPS = 4, NE = WARPS * EW;
-  static constexpr int PSN = PB == 6 ? 47 : (PB == 8 ? 65 : 111);  // window plane stride
-  static constexpr int OFF_NB = PB * PSN;                            // 27 neighbour ids (+1)
-  static constexpr int OFF_S = OFF_NB + 28;                          // [3][PB][PB]
+struct Fdm32PipeDims {
+  static_assert(PB == 6 || PB == 8 || PB == 10, "FP32 RAS plane/column kernel: pbar 6, 8 or 10");
+  static constexpr int N = PB - 2, H = PB / 2, EW = 32 / PB;
+  static constexpr int WARPS = 2;                                    // warps per block
+  static constexpr int BLOCKS_PER_SM = PB == 10 ? 4 : 6;             // 8 / 12 warps per SM
+  static constexpr int PSN = PB == 6 ? 47 : (PB == 8 ? 65 : 111);    // window plane stride
+  static constexpr int OFF_S = (PB * PSN + 1) / 2 * 2;               // [3][PB][PB], 8-byte aligned
   static constexpr int OFF_L = OFF_S + 3 * PB * PB;                  // [3][PB]
   static constexpr int RAW = OFF_L + 3 * PB;
-  static constexpr int TOT = RAW + ((PB - RAW % 32) % 32 + 32) % 32;  // floats per element, = PB mod 32
-  static constexpr size_t SMEM = (size_t)NE * TOT * sizeof(float);
-  static_assert(TOT % 2 == 0 && OFF_S % 2 == 0, "S pairs must be 8-byte aligned");
+  static constexpr int TOT = RAW + ((PB - RAW % 32) % 32 + 32) % 32;  // = PB (mod 32), even
+  static constexpr size_t SMEM = (size_t)WARPS * EW * TOT * sizeof(float);
+  static_assert(TOT % 2 == 0 && OFF_S % 2 == 0 && OFF_L % 2 == 0, "8-byte copies need even offsets");
 };
 
-template <int PB>
-__device__ __forceinline__ void plane_load_S(const float* __restrict__ sS, int d, float2 (&S2)[PB][PB / 2]) {
-#pragma unroll
-  for (int r = 0; r < PB; ++r)
-#pragma unroll
-    for (int k = 0; k < PB / 2; ++k)
-      S2[r][k] = *reinterpret_cast<const float2*>(sS + d * PB * PB + r * PB + 2 * k);
+__device__ __forceinline__ void cp_async8(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
 }
 
 template <int P>
-__global__ void __launch_bounds__(128, 2) fdm32_plane_kernel(int64_t E, const int* __restrict__ nbr,
-                                                             const float* __restrict__ in,
-                                                             const float* __restrict__ Sg,
-                                                             const float* __restrict__ lamg,
-                                                             const uint8_t* __restrict__ pflag,
-                                                             float* __restrict__ out) {
+__global__ void __launch_bounds__(64, Fdm32PipeDims<P + 3>::BLOCKS_PER_SM)
+    fdm32_pipe_kernel(int64_t E, int nx, int ny, int nz, const int* __restrict__ nbr,
+                      const float* __restrict__ in, const float* __restrict__ Sg,
+                      const float* __restrict__ lamg, float* __restrict__ out) {
   constexpr int PB = P + 3, N = P + 1, N2 = N * N, N3 = N2 * N, PB2 = PB * PB, H = PB / 2;
-  using D = Fdm32PlaneDims<PB>;
-  constexpr int PSN = D::PSN;
+  using D = Fdm32PipeDims<PB>;
+  constexpr int PSN = D::PSN, EW = D::EW;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int gw = lane / PB, t = lane - gw * PB;  // element within the warp, plane / column set
-  const bool lane_on = gw < D::EW;
-  const int g = warp * D::EW + (lane_on ? gw : 0);
-  const int64_t e = (int64_t)blockIdx.x * D::NE + g;
-  const bool on = lane_on && e < E;
-  float* W = reinterpret_cast<float*>(smem_raw) + (size_t)g * D::TOT;
-  int* snb = reinterpret_cast<int*>(W + D::OFF_NB);
-  float* sS = W + D::OFF_S;
-  float* sl = W + D::OFF_L;
-  if (on) {
-    for (int q = t; q < 27; q += PB) snb[q] = nbr[27 * e + q];
-    for (int q = t; q < 3 * PB2; q += PB) sS[q] = Sg[e * 3 * PB2 + q];
-    for (int q = t; q < 3 * PB; q += PB) sl[q] = lamg[e * 3 * PB + q];
-  }
-  __syncwarp();
-  float2 S2[PB][H];
-  float R[PB][PB];
-  // ---- 1. gather: thread t copies window column a = t of every row (b, c) into shared memory
-  //      (the element's threads read consecutive points of a row), then loads its plane c = t.
-  //      Point (a, b, c) comes from neighbour (da, db, dc), point (ia, ib, ic) of it (da = -1
-  //      for a = 0: point p - 1; +1 for a = pbar - 1: point 1); outside the domain it is zero.
-  if (on) {
-    const int da = t == 0 ? -1 : (t == PB - 1 ? 1 : 0);
-    const int ia = da < 0 ? P - 1 : (da > 0 ? 1 : t - 1);
-    int nb9[3][3];
+  const int g = lane / PB, t = lane - g * PB;
+  const bool lane_on = g < EW;
+  float* const W = reinterpret_cast<float*>(smem_raw) + (size_t)(warp * EW + (lane_on ? g : 0)) * D::TOT;
+  const float* const sS = W + D::OFF_S;
+  const float* const sl = W + D::OFF_L;
+  const int64_t nsteps = (E + EW - 1) / EW;
+  const int64_t w0 = (int64_t)blockIdx.x * D::WARPS + warp, nw = (int64_t)gridDim.x * D::WARPS;
+
+  // the column of the window this thread gathers: a = t (neighbour direction da)
+  const int da = t == 0 ? -1 : (t == PB - 1 ? 1 : 0);
+  const int ia = da < 0 ? P - 1 : (da > 0 ? 1 : t - 1);
+  int nb9[3][3];
+  auto load_nb = [&](int64_t q) {
+    const int64_t e = q * EW + g;
+    const bool on = lane_on && q < nsteps && e < E;
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) nb9[k][j] = snb[(da + 1) + 3 * j + 9 * k];
-    const float* src_a = in + ia;
+      for (int j = 0; j < 3; ++j) nb9[k][j] = on ? __ldg(nbr + 27 * e + (da + 1) + 3 * j + 9 * k) : -1;
+  };
+  load_nb(w0);
+  for (int64_t q = w0; q < nsteps; q += nw) {
+    const int64_t e = q * EW + g;
+    const bool on = lane_on && e < E;
+    // ---- gather: column a = t of every row (b, c) of the window; S and Lambda
+    if (on) {
+      const float* src_a = in + ia;
 #pragma unroll
-    for (int c = 0; c < PB; ++c) {
-      const int dc = c == 0 ? -1 : (c == PB - 1 ? 1 : 0);
-      const int ic = dc < 0 ? P - 1 : (dc > 0 ? 1 : c - 1);
+      for (int c = 0; c < PB; ++c) {
+        const int dc = c == 0 ? -1 : (c == PB - 1 ? 1 : 0);
+        const int ic = dc < 0 ? P - 1 : (dc > 0 ? 1 : c - 1);
 #pragma unroll
-      for (int b = 0; b < PB; ++b) {
-        const int db = b == 0 ? -1 : (b == PB - 1 ? 1 : 0);
-        const int ib = db < 0 ? P - 1 : (db > 0 ? 1 : b - 1);
-        const int nb = nb9[dc + 1][db + 1];
-        cp_async4(W + c * PSN + b * PB + t, nb >= 0 ? src_a + (int64_t)nb * N3 + N * ib + N2 * ic : in,
-                  nb >= 0);
+        for (int b = 0; b < PB; ++b) {
+          const int db = b == 0 ? -1 : (b == PB - 1 ? 1 : 0);
+          const int ib = db < 0 ? P - 1 : (db > 0 ? 1 : b - 1);
+          const int nb = nb9[dc + 1][db + 1];
+          cp_async4(W + c * PSN + b * PB + t,
+                    nb >= 0 ? src_a + (int64_t)nb * N3 + N * ib + N2 * ic : in, nb >= 0);
+        }
       }
+      const float* gS = Sg + e * 3 * PB2;
+      for (int q2 = t; q2 < 3 * PB2 / 2; q2 += PB) cp_async8(W + D::OFF_S + 2 * q2, gS + 2 * q2);
+      const float* gL = lamg + e * 3 * PB;
+      for (int q2 = t; q2 < 3 * PB / 2; q2 += PB) cp_async8(W + D::OFF_L + 2 * q2, gL + 2 * q2);
     }
+    load_nb(q + nw);     // ids of the next step, in flight during this one
     cp_async_wait_all();
-  }
-  __syncwarp();
-  if (on) {
+    __syncwarp();
+    // ---- phase A: plane c = t; S_x^T along a (output modes in pairs), then S_y^T along b
+    if (on) {
+      float* pl = W + t * PSN;
+      float2 acc[PB][H];
 #pragma unroll
-    for (int b = 0; b < PB; ++b)
+      for (int b = 0; b < PB; ++b)
 #pragma unroll
-      for (int a = 0; a < PB; ++a) R[b][a] = W[t * PSN + b * PB + a];
-    // ---- 2. S_x^T along a (lines b), then S_y^T along b (columns a)
-    plane_load_S<PB>(sS, 0, S2);
-#pragma unroll
-    for (int b = 0; b < PB; ++b) {
-      float2 acc[H];
-#pragma unroll
-      for (int k = 0; k < H; ++k) acc[k] = make_float2(0.f, 0.f);
-#pragma unroll
+        for (int k = 0; k < H; ++k) acc[b][k] = make_float2(0.f, 0.f);
+#pragma unroll 1
       for (int a = 0; a < PB; ++a) {
-        const float2 v = make_float2(R[b][a], R[b][a]);
+        float v[PB];
 #pragma unroll
-        for (int k = 0; k < H; ++k) acc[k] = __ffma2_rn(S2[a][k], v, acc[k]);
+        for (int b = 0; b < PB; ++b) v[b] = pl[b * PB + a];
+        float2 s2[H];
+#pragma unroll
+        for (int k = 0; k < H; ++k) s2[k] = *reinterpret_cast<const float2*>(sS + a * PB + 2 * k);
+#pragma unroll
+        for (int b = 0; b < PB; ++b) {
+          const float2 vv = make_float2(v[b], v[b]);
+#pragma unroll
+          for (int k = 0; k < H; ++k) acc[b][k] = __ffma2_rn(s2[k], vv, acc[b][k]);
+        }
       }
+#pragma unroll 1
+      for (int bq = 0; bq < PB; ++bq) {
+        float2 w[H];
 #pragma unroll
-      for (int k = 0; k < H; ++k) {
-        R[b][2 * k] = acc[k].x;
-        R[b][2 * k + 1] = acc[k].y;
+        for (int k = 0; k < H; ++k) w[k] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int b = 0; b < PB; ++b) {
+          const float s = sS[PB2 + b * PB + bq];
+          const float2 ss = make_float2(s, s);
+#pragma unroll
+          for (int k = 0; k < H; ++k) w[k] = __ffma2_rn(ss, acc[b][k], w[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+          pl[bq * PB + 2 * k] = w[k].x;
+          pl[bq * PB + 2 * k + 1] = w[k].y;
+        }
       }
     }
-    plane_load_S<PB>(sS, 1, S2);
+    __syncwarp();
+    // ---- phase B: columns (a = t, b = j): S_z^T, D^-1, S_z for the own planes
+    if (on) {
+      float* col = W + t;
+      float2 acc[PB][H];
 #pragma unroll
-    for (int a = 0; a < PB; ++a) {
-      float2 acc[H];
+      for (int j = 0; j < PB; ++j)
 #pragma unroll
-      for (int k = 0; k < H; ++k) acc[k] = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int b = 0; b < PB; ++b) {
-        const float2 v = make_float2(R[b][a], R[b][a]);
-#pragma unroll
-        for (int k = 0; k < H; ++k) acc[k] = __ffma2_rn(S2[b][k], v, acc[k]);
-      }
-#pragma unroll
-      for (int k = 0; k < H; ++k) {
-        R[2 * k][a] = acc[k].x;
-        R[2 * k + 1][a] = acc[k].y;
-      }
-    }
-#pragma unroll
-    for (int b = 0; b < PB; ++b)
-#pragma unroll
-      for (int a = 0; a < PB; ++a) W[t * PSN + b * PB + a] = R[b][a];
-  }
-  __syncwarp();
-  // ---- 3. columns col = t + pbar j (alpha = col mod pbar, beta = col / pbar): S_z^T, D^-1, S_z
-  if (on) {
-#pragma unroll
-    for (int j = 0; j < PB; ++j)
-#pragma unroll
-      for (int c = 0; c < PB; ++c) R[j][c] = W[c * PSN + t + PB * j];
-    plane_load_S<PB>(sS, 2, S2);
-#pragma unroll
-    for (int j = 0; j < PB; ++j) {
-      float2 acc[H];
-#pragma unroll
-      for (int k = 0; k < H; ++k) acc[k] = make_float2(0.f, 0.f);
-#pragma unroll
+        for (int k = 0; k < H; ++k) acc[j][k] = make_float2(0.f, 0.f);
+#pragma unroll 1
       for (int c = 0; c < PB; ++c) {
-        const float2 v = make_float2(R[j][c], R[j][c]);
+        float v[PB];
 #pragma unroll
-        for (int k = 0; k < H; ++k) acc[k] = __ffma2_rn(S2[c][k], v, acc[k]);
+        for (int j = 0; j < PB; ++j) v[j] = col[PB * j + PSN * c];
+        float2 s2[H];
+#pragma unroll
+        for (int k = 0; k < H; ++k) s2[k] = *reinterpret_cast<const float2*>(sS + 2 * PB2 + c * PB + 2 * k);
+#pragma unroll
+        for (int j = 0; j < PB; ++j) {
+          const float2 vv = make_float2(v[j], v[j]);
+#pragma unroll
+          for (int k = 0; k < H; ++k) acc[j][k] = __ffma2_rn(s2[k], vv, acc[j][k]);
+        }
       }
-      const int col = t + PB * j;
-      const int be = col / PB, al = col - be * PB;
-      const float lxy = sl[al] + sl[PB + be];
+      const float lx = sl[t];
+      float lz[PB];
 #pragma unroll
-      for (int k = 0; k < H; ++k) {
-        R[j][2 * k] = acc[k].x * rcp_approx(lxy + sl[2 * PB + 2 * k]);
-        R[j][2 * k + 1] = acc[k].y * rcp_approx(lxy + sl[2 * PB + 2 * k + 1]);
+      for (int c = 0; c < PB; ++c) lz[c] = sl[2 * PB + c];
+#pragma unroll
+      for (int j = 0; j < PB; ++j) {
+        const float lxy = lx + sl[PB + j];
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+          acc[j][k].x *= rcp_approx(lxy + lz[2 * k]);
+          acc[j][k].y *= rcp_approx(lxy + lz[2 * k + 1]);
+        }
       }
-      // S_z for the own planes c' = 1..N
-#pragma unroll
+#pragma unroll 1
       for (int cc = 1; cc <= N; ++cc) {
-        float2 z = make_float2(0.f, 0.f);
+        float2 s2[H];
 #pragma unroll
-        for (int k = 0; k < H; ++k) z = __ffma2_rn(S2[cc][k], make_float2(R[j][2 * k], R[j][2 * k + 1]), z);
-        W[cc * PSN + col] = z.x + z.y;
+        for (int k = 0; k < H; ++k) s2[k] = *reinterpret_cast<const float2*>(sS + 2 * PB2 + cc * PB + 2 * k);
+#pragma unroll
+        for (int j = 0; j < PB; ++j) {
+          float2 z = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int k = 0; k < H; ++k) z = __ffma2_rn(s2[k], acc[j][k], z);
+          col[PB * j + PSN * cc] = z.x + z.y;
+        }
       }
     }
-  }
-  __syncwarp();
-  // ---- 4. own plane c' = t + 1: S_y (own rows), S_x (own columns), weights, store
-  if (on && t < N) {
-    const int cp = t + 1;
+    __syncwarp();
+    // ---- phase C: own plane t + 1: S_y (own rows), S_x (own columns), weights, stores
+    if (on && t < N) {
+      const float* pl = W + (t + 1) * PSN;
+      float2 v2[H][PB];  // (v[2m][a], v[2m + 1][a])
 #pragma unroll
-    for (int b = 0; b < PB; ++b)
+      for (int m = 0; m < H; ++m)
 #pragma unroll
-      for (int a = 0; a < PB; ++a) R[b][a] = W[cp * PSN + b * PB + a];
-    plane_load_S<PB>(sS, 1, S2);
+        for (int a = 0; a < PB; ++a) v2[m][a] = make_float2(pl[2 * m * PB + a], pl[(2 * m + 1) * PB + a]);
+      float2 sx[N][H];   // own rows of S_x as pairs
 #pragma unroll
-    for (int a = 0; a < PB; ++a) {
-      float o[N];
+      for (int i = 0; i < N; ++i)
 #pragma unroll
+        for (int m = 0; m < H; ++m) sx[i][m] = *reinterpret_cast<const float2*>(sS + (1 + i) * PB + 2 * m);
+      const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
+      const float wz = ((t == 0 && ez > 0) || (t == N - 1 && ez < nz - 1)) ? 0.5f : 1.f;
+      const float wx0 = ex > 0 ? 0.5f : 1.f, wx1 = ex < nx - 1 ? 0.5f : 1.f;
+      float* orow = out + e * N3 + (int64_t)N2 * t;
+#pragma unroll 1
       for (int bb = 0; bb < N; ++bb) {
-        float2 z = make_float2(0.f, 0.f);
+        float2 sy[H];
 #pragma unroll
-        for (int k = 0; k < H; ++k) z = __ffma2_rn(S2[bb + 1][k], make_float2(R[2 * k][a], R[2 * k + 1][a]), z);
-        o[bb] = z.x + z.y;
-      }
+        for (int m = 0; m < H; ++m) sy[m] = *reinterpret_cast<const float2*>(sS + PB2 + (1 + bb) * PB + 2 * m);
+        float y2[PB];    // this own row after S_y
 #pragma unroll
-      for (int bb = 0; bb < N; ++bb) R[bb][a] = o[bb];
-    }
-    plane_load_S<PB>(sS, 0, S2);
+        for (int a = 0; a < PB; ++a) {
+          float2 z = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int bb = 0; bb < N; ++bb) {
-      float o[N];
-#pragma unroll
-      for (int aa = 0; aa < N; ++aa) {
-        float2 z = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int k = 0; k < H; ++k) z = __ffma2_rn(S2[aa + 1][k], make_float2(R[bb][2 * k], R[bb][2 * k + 1]), z);
-        o[aa] = z.x + z.y;
-      }
-#pragma unroll
-      for (int aa = 0; aa < N; ++aa) R[bb][aa] = o[aa];
-    }
-    // own point (i, j, k) = (aa, bb, t): N^2 contiguous values of plane t (16-byte aligned for
-    // even N), weighted by 1/multiplicity = 2^-mlog, mlog the lowest set bit of the flag's nibble
-    const int64_t ob = e * N3 + (int64_t)N2 * t;
-    const uint32_t* pf = reinterpret_cast<const uint32_t*>(pflag + ob);
-    float4* o4 = reinterpret_cast<float4*>(out + ob);
-#pragma unroll
-    for (int q4 = 0; q4 < N2 / 4; ++q4) {
-      const uint32_t f4 = pf[q4];
-      float v[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int q = 4 * q4 + u;
-        const int mlog = __ffs((f4 >> (8 * u)) & 0x0Fu) - 1;
-        v[u] = R[q / N][q % N] * __int_as_float((127 - mlog) << 23);
-      }
-      o4[q4] = make_float4(v[0], v[1], v[2], v[3]);
-    }
-  }
-}
-
-// The same algorithm with the window kept in shared memory: a thread holds only S (packed pairs)
-// and the line it contracts, so it needs 167 registers instead of 254 at p = 7 (12 warps per SM
-// instead of 8) and its line loops need not be unrolled.  Used for p = 7.  Every shared access pattern is one
-// of those the strides were chosen for (plane-per-thread rows and columns, column-per-thread
-// planes), so each stays conflict-free.  Same arithmetic per output as fdm32_plane_kernel.
-template <int PB>
-__device__ __forceinline__ void smem_line_fwd(const float2 (&S2)[PB][PB / 2], float* base, int stride) {
-  constexpr int H = PB / 2;
-  float v[PB];
-#pragma unroll
-  for (int a = 0; a < PB; ++a) v[a] = base[a * stride];
-  float2 acc[H];
-#pragma unroll
-  for (int k = 0; k < H; ++k) acc[k] = make_float2(0.f, 0.f);
-#pragma unroll
-  for (int a = 0; a < PB; ++a) {
-    const float2 vv = make_float2(v[a], v[a]);
-#pragma unroll
-    for (int k = 0; k < H; ++k) acc[k] = __ffma2_rn(S2[a][k], vv, acc[k]);
-  }
-#pragma unroll
-  for (int k = 0; k < H; ++k) {
-    base[(2 * k) * stride] = acc[k].x;
-    base[(2 * k + 1) * stride] = acc[k].y;
-  }
-}
-
-// out[i] = sum_m S[1 + i][m] v[m], i < N, in place at base[(1 + i) stride] (own rows only).
-template <int PB>
-__device__ __forceinline__ void smem_line_bwd_own(const float2 (&S2)[PB][PB / 2], float* base,
-                                                  int stride, float (&o)[PB - 2]) {
-  constexpr int H = PB / 2, N = PB - 2;
-  float v[PB];
-#pragma unroll
-  for (int m = 0; m < PB; ++m) v[m] = base[m * stride];
-#pragma unroll
-  for (int i = 0; i < N; ++i) {
-    float2 z = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int k = 0; k < H; ++k) z = __ffma2_rn(S2[i + 1][k], make_float2(v[2 * k], v[2 * k + 1]), z);
-    o[i] = z.x + z.y;
-  }
-}
-
-template <int P>
-__global__ void __launch_bounds__(128, 3) fdm32_plane_smem_kernel(int64_t E, const int* __restrict__ nbr,
-                                                                  const float* __restrict__ in,
-                                                                  const float* __restrict__ Sg,
-                                                                  const float* __restrict__ lamg,
-                                                                  const uint8_t* __restrict__ pflag,
-                                                                  float* __restrict__ out) {
-  constexpr int PB = P + 3, N = P + 1, N2 = N * N, N3 = N2 * N, PB2 = PB * PB, H = PB / 2;
-  using D = Fdm32PlaneDims<PB>;
-  constexpr int PSN = D::PSN;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int gw = lane / PB, t = lane - gw * PB;
-  const bool lane_on = gw < D::EW;
-  const int g = warp * D::EW + (lane_on ? gw : 0);
-  const int64_t e = (int64_t)blockIdx.x * D::NE + g;
-  const bool on = lane_on && e < E;
-  float* W = reinterpret_cast<float*>(smem_raw) + (size_t)g * D::TOT;
-  int* snb = reinterpret_cast<int*>(W + D::OFF_NB);
-  float* sS = W + D::OFF_S;
-  float* sl = W + D::OFF_L;
-  if (on) {
-    for (int q = t; q < 27; q += PB) snb[q] = nbr[27 * e + q];
-    for (int q = t; q < 3 * PB2; q += PB) sS[q] = Sg[e * 3 * PB2 + q];
-    for (int q = t; q < 3 * PB; q += PB) sl[q] = lamg[e * 3 * PB + q];
-  }
-  __syncwarp();
-  float2 S2[PB][H];
-  // ---- 1. gather (as fdm32_plane_kernel): column a = t of every row (b, c) of the window
-  if (on) {
-    const int da = t == 0 ? -1 : (t == PB - 1 ? 1 : 0);
-    const int ia = da < 0 ? P - 1 : (da > 0 ? 1 : t - 1);
-    int nb9[3][3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) nb9[k][j] = snb[(da + 1) + 3 * j + 9 * k];
-    const float* src_a = in + ia;
-#pragma unroll
-    for (int c = 0; c < PB; ++c) {
-      const int dc = c == 0 ? -1 : (c == PB - 1 ? 1 : 0);
-      const int ic = dc < 0 ? P - 1 : (dc > 0 ? 1 : c - 1);
-#pragma unroll
-      for (int b = 0; b < PB; ++b) {
-        const int db = b == 0 ? -1 : (b == PB - 1 ? 1 : 0);
-        const int ib = db < 0 ? P - 1 : (db > 0 ? 1 : b - 1);
-        const int nb = nb9[dc + 1][db + 1];
-        cp_async4(W + c * PSN + b * PB + t, nb >= 0 ? src_a + (int64_t)nb * N3 + N * ib + N2 * ic : in,
-                  nb >= 0);
-      }
-    }
-    cp_async_wait_all();
-  }
-  __syncwarp();
-  // ---- 2. own plane c = t: S_x^T along rows, then S_y^T along columns
-  if (on) {
-    float* plane = W + t * PSN;
-    plane_load_S<PB>(sS, 0, S2);
-#pragma unroll 1
-    for (int b = 0; b < PB; ++b) smem_line_fwd<PB>(S2, plane + b * PB, 1);
-    plane_load_S<PB>(sS, 1, S2);
-#pragma unroll 1
-    for (int a = 0; a < PB; ++a) smem_line_fwd<PB>(S2, plane + a, PB);
-  }
-  __syncwarp();
-  // ---- 3. columns col = t + pbar j: S_z^T, D^-1, S_z for the own planes
-  if (on) {
-    plane_load_S<PB>(sS, 2, S2);
-#pragma unroll 1
-    for (int j = 0; j < PB; ++j) {
-      const int col = t + PB * j;
-      float* cb = W + col;
-      float v[PB];
-#pragma unroll
-      for (int c = 0; c < PB; ++c) v[c] = cb[c * PSN];
-      float2 acc[H];
-#pragma unroll
-      for (int k = 0; k < H; ++k) acc[k] = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int c = 0; c < PB; ++c) {
-        const float2 vv = make_float2(v[c], v[c]);
-#pragma unroll
-        for (int k = 0; k < H; ++k) acc[k] = __ffma2_rn(S2[c][k], vv, acc[k]);
-      }
-      const int be = col / PB, al = col - be * PB;
-      const float lxy = sl[al] + sl[PB + be];
-#pragma unroll
-      for (int k = 0; k < H; ++k) {
-        v[2 * k] = acc[k].x * rcp_approx(lxy + sl[2 * PB + 2 * k]);
-        v[2 * k + 1] = acc[k].y * rcp_approx(lxy + sl[2 * PB + 2 * k + 1]);
-      }
-#pragma unroll
-      for (int cc = 1; cc <= N; ++cc) {
-        float2 z = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int k = 0; k < H; ++k) z = __ffma2_rn(S2[cc][k], make_float2(v[2 * k], v[2 * k + 1]), z);
-        cb[cc * PSN] = z.x + z.y;
-      }
-    }
-  }
-  __syncwarp();
-  // ---- 4. own plane c' = t + 1: S_y (own rows) per column, S_x (own columns) per own row
-  if (on && t < N) {
-    float* plane = W + (t + 1) * PSN;
-    plane_load_S<PB>(sS, 1, S2);
-#pragma unroll 1
-    for (int a = 0; a < PB; ++a) {
-      float o[N];
-      smem_line_bwd_own<PB>(S2, plane + a, PB, o);
-#pragma unroll
-      for (int i = 0; i < N; ++i) plane[(1 + i) * PB + a] = o[i];
-    }
-    plane_load_S<PB>(sS, 0, S2);
-    const int64_t ob = e * N3 + (int64_t)N2 * t;
-#pragma unroll 1
-    for (int bb = 0; bb < N; ++bb) {
-      float o[N];
-      smem_line_bwd_own<PB>(S2, plane + (1 + bb) * PB, 1, o);
-      // own points (i, j, k) = (aa, bb, t), weighted by 1/multiplicity; a row of N values starts
-      // on a 16-byte boundary when N is a multiple of 4
-      if constexpr (N % 4 == 0) {
-#pragma unroll
-        for (int q4 = 0; q4 < N / 4; ++q4) {
-          const uint32_t f4 = *reinterpret_cast<const uint32_t*>(pflag + ob + N * bb + 4 * q4);
-          float w[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int mlog = __ffs((f4 >> (8 * u)) & 0x0Fu) - 1;
-            w[u] = o[4 * q4 + u] * __int_as_float((127 - mlog) << 23);
-          }
-          *reinterpret_cast<float4*>(out + ob + N * bb + 4 * q4) = make_float4(w[0], w[1], w[2], w[3]);
+          for (int m = 0; m < H; ++m) z = __ffma2_rn(sy[m], v2[m][a], z);
+          y2[a] = z.x + z.y;
         }
-      } else {
+        const float wyz = wz * (((bb == 0 && ey > 0) || (bb == N - 1 && ey < ny - 1)) ? 0.5f : 1.f);
+        float o[N];
 #pragma unroll
-        for (int aa = 0; aa < N; ++aa) {
-          const int mlog = __ffs(pflag[ob + N * bb + aa] & 0x0F) - 1;
-          out[ob + N * bb + aa] = o[aa] * __int_as_float((127 - mlog) << 23);
+        for (int i = 0; i < N; ++i) {
+          float2 z = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int m = 0; m < H; ++m) z = __ffma2_rn(sx[i][m], make_float2(y2[2 * m], y2[2 * m + 1]), z);
+          const float wx = i == 0 ? wx0 : (i == N - 1 ? wx1 : 1.f);
+          o[i] = (z.x + z.y) * (wx * wyz);
+        }
+        float* dst = orow + N * bb;
+        if constexpr (N % 4 == 0) {
+#pragma unroll
+          for (int q4 = 0; q4 < N / 4; ++q4)
+            *reinterpret_cast<float4*>(dst + 4 * q4) = make_float4(o[4 * q4], o[4 * q4 + 1], o[4 * q4 + 2], o[4 * q4 + 3]);
+        } else {
+#pragma unroll
+          for (int q2 = 0; q2 < N / 2; ++q2) *reinterpret_cast<float2*>(dst + 2 * q2) = make_float2(o[2 * q2], o[2 * q2 + 1]);
         }
       }
     }
+    __syncwarp();  // the window is read completely before the next step's copies target it
   }
 }
 
@@ -1294,23 +1116,22 @@ static int launch_fdm(const Level& lv, const T* in, const T* S, const T* lam, T*
   const unsigned blocks = (unsigned)((lv.E + NE - 1) / NE);
   if constexpr (sizeof(T) == 4) {
     static_assert(MODE == FDM_RAS || MODE == FDM_FULL, "FP32 FDM: RAS or full window only");
-    if constexpr (MODE == FDM_RAS && P == 7) {
-      using PD = Fdm32PlaneDims<P + 3>;
+    if constexpr (MODE == FDM_RAS && (P == 3 || P == 5 || P == 7)) {
+      using PD = Fdm32PipeDims<P + 3>;
       static const cudaError_t pattr = cudaFuncSetAttribute(
-          fdm32_plane_smem_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PD::SMEM);
+          fdm32_pipe_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PD::SMEM);
       SE_CUDA(pattr);
-      const unsigned pblocks = (unsigned)((lv.E + PD::NE - 1) / PD::NE);
-      fdm32_plane_smem_kernel<P><<<pblocks, 128, PD::SMEM, s>>>(lv.E, lv.nbr, in, S, lam, lv.pflag, out);
-      SE_LAUNCH_CHECK();
-      return SE_OK;
-    }
-    if constexpr (MODE == FDM_RAS && (P == 3 || P == 5)) {
-      using PD = Fdm32PlaneDims<P + 3>;
-      static const cudaError_t pattr = cudaFuncSetAttribute(
-          fdm32_plane_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PD::SMEM);
-      SE_CUDA(pattr);
-      const unsigned pblocks = (unsigned)((lv.E + PD::NE - 1) / PD::NE);
-      fdm32_plane_kernel<P><<<pblocks, 128, PD::SMEM, s>>>(lv.E, lv.nbr, in, S, lam, lv.pflag, out);
+      int per_sm = 0, dev = 0, sms = 0;
+      SE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fdm32_pipe_kernel<P>,
+                                                            32 * PD::WARPS, PD::SMEM));
+      SE_CHECK(per_sm >= 1, SE_ECUDA, "fdm32_pipe: no resident block fits");
+      SE_CUDA(cudaGetDevice(&dev));
+      SE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      const int64_t steps = (lv.E + PD::EW - 1) / PD::EW;
+      int64_t pblocks = (int64_t)sms * per_sm;
+      if (pblocks > (steps + PD::WARPS - 1) / PD::WARPS) pblocks = (steps + PD::WARPS - 1) / PD::WARPS;
+      fdm32_pipe_kernel<P><<<(unsigned)pblocks, 32 * PD::WARPS, PD::SMEM, s>>>(
+          lv.E, lv.nel[0], lv.nel[1], lv.nel[2], lv.nbr, in, S, lam, out);
       SE_LAUNCH_CHECK();
       return SE_OK;
     }
