@@ -938,11 +938,37 @@ def run_order_study(args):
         "rows": rows, "wall_s": round(time.perf_counter() - t0, 1)}))
 
 
+def oracle_full(args):
+    """The oracle once on the whole workload (not a sample): set-up and one solve, timed."""
+    import numpy as np
+    import oracle as o
+    import workloads as wl
+    wk = WORKLOADS[args.workload]
+    sm = ORACLE_SMOOTHERS[args.smoother if args.smoother != "auto" else "jacobi"]
+    order = args.cheb_order if args.smoother != "auto" else 1
+    t0 = time.perf_counter()
+    V = wl.vertex_lattice(wk["nel"], wk["perturb"], wk["seed"])
+    lv, b = o.problem(V, wk["nel"], wk["p"], amp=wl.DEFORM_AMP)
+    pmg = o.pmg_setup(V, wk["nel"], wk["schedule"], smoother=sm, order=order, amp=wl.DEFORM_AMP)
+    t1 = time.perf_counter()
+    x, it, rel = o.solve(lv, b, pmg, tol=1e-8)
+    t2 = time.perf_counter()
+    n = int(np.prod(wk["nel"])) * wk["p"] ** 3
+    print(json.dumps({"impl": "reference", "oracle_full": {
+        "workload": args.workload, "preconditioner": f"Cheby-{sm}({order})",
+        "schedule": list(wk["schedule"]), "n_dof": n, "setup_s": round(t1 - t0, 1),
+        "solve_s": round(t2 - t1, 1), "iterations": it, "rel_residual": rel,
+        "gdof_per_s": round(n / (t2 - t1) / 1e9, 7), "cores": 1, "nproc": os.cpu_count()}}))
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
     env_threads = 1
+    if args.oracle_full:
+        oracle_full(args)
+        return
     search = None
     if args.smoother == "auto":
         # the same run-time search as the GPU arm, on the oracle: each candidate solves the
@@ -1008,6 +1034,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-schwarz", action="store_true",
                     help="skip the Cheby-RAS(2) FP64 / FP32-V-cycle record of the headline line")
+    ap.add_argument("--oracle-full", action="store_true",
+                    help="with --impl reference: time the oracle once on the whole workload")
     ap.add_argument("--peaks", action="store_true",
                     help="measure the FP64 / FP32 / packed-FP32 FMA roofs of this GPU and exit")
     ap.add_argument("--cpu-timeout", type=float, default=240.0)
@@ -1045,6 +1073,9 @@ def main():
     if args.cycle == "additive" and args.smoother not in ("ras", "asm"):
         ap.error("--cycle additive needs --smoother ras or asm (the additive V-cycle has no Chebyshev)")
     if args.impl == "reference":
+        # the oracle is timed on one host thread (numpy's BLAS included)
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[var] = "1"
         run_reference(args)
     elif args.peaks:
         run_peaks(args)
