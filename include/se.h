@@ -295,11 +295,19 @@ int se_proj_guess(se_proj_t proj, const double* b, double* x, void* stream);
 int se_proj_update(se_proj_t proj, const double* x, int* size, void* stream);
 
 /* ---------------------------------------------------------------- batched solves */
-/* Many independent problems solved together (flexible PCG, device-driven): every problem's
- * whole solve loop becomes one branch of a single CUDA graph, so one graph launch runs all of
- * them concurrently on the GPU; problems that converge early simply leave their loop.  Each
- * problem needs its own mesh handle (its work vectors live there); pmg may be NULL (Jacobi).
- * b and x are caller-owned device vectors of that mesh; x holds the initial guess at launch. */
+/* Many independent problems solved together by flexible PCG in one device-driven CUDA graph.
+ * Problems whose preconditioners share a configuration (schedule, smoother RAS or Jacobi,
+ * Chebyshev orders, bounds multipliers, coarse tolerance, FP64 or FP32 V-cycle, multiplicative
+ * cycle) form a group that is solved as one union problem: each phase of an iteration (outer
+ * operator, QQ^T, smoother, Chebyshev update, transfers, coarse solves) is one launch over all
+ * members' elements, inner products and convergence stay per problem (a converged problem keeps
+ * its iterate while the others continue), and each member's Chebyshev bounds (Sec. 2.2.3) are
+ * folded into its smoother.  Other problems (no preconditioner, ASM, additive cycle, df64) run
+ * their own solve loop as a branch of the same graph.  Results of grouped problems agree with
+ * se_solve of the same problem to within rounding (iteration counts can differ by one).  Each
+ * problem needs its own mesh and preconditioner handles; pmg may be NULL (Jacobi).  b and x are
+ * caller-owned device vectors of that mesh; x holds the initial guess at launch.  A group copies
+ * its members' level data (geometry, factors, maps) into union arrays owned by the batch. */
 typedef struct se_problem {
   se_mesh_t mesh;
   se_pmg_t pmg;
@@ -316,6 +324,8 @@ int se_batch_stats(se_batch_t batch, void* stream, se_solve_stats* out);
 int se_batch_destroy(se_batch_t batch);
 /* create + run + stats + destroy; ms_total of every entry is the wall time of the whole batch. */
 int se_batch_solve(int n, const se_problem* probs, const se_solve_opts* opts, se_solve_stats* out);
+/* Number of groups of the batch and of the problems they hold (the rest run alone). */
+int se_batch_info(se_batch_t batch, int* groups, int* grouped_problems);
 
 /* ---------------------------------------------------------------- launch-tile autotuner */
 /* Elements per thread block of the operator (Ax) and FDM kernels for one polynomial order and

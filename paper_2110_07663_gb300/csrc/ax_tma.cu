@@ -66,7 +66,8 @@ constexpr long long PIPE_LIMIT_NS = 1000000000LL;
 
 // Residual form (RES): an eighth block per group, b, comes through the same pipeline, and the
 // output is b / multiplicity - A_L u; the multiplicity follows from the element's place in the
-// lattice (copies = product over directions of 2 on an interior element interface, else 1).
+// lattice (copies = product over directions of 2 on an interior element interface, else 1), or,
+// for a level that is a union of several lattices (nx = 0), from the point flags.
 template <int N, bool RES>
 __global__ void __launch_bounds__(512) ax_tma_kernel(int64_t E, int NE, int64_t ngroups,
                                                      const float* __restrict__ u,
@@ -74,7 +75,8 @@ __global__ void __launch_bounds__(512) ax_tma_kernel(int64_t E, int NE, int64_t 
                                                      const float* __restrict__ Dg,
                                                      float* __restrict__ y,
                                                      const float* __restrict__ sub, int nx,
-                                                     int ny, int nz) {
+                                                     int ny, int nz,
+                                                     const uint8_t* __restrict__ pflag) {
   constexpr int N2 = N * N, N3 = N * N * N, A = RES ? 8 : 7;  // blocks per stage
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int S = NE * N3;                       // floats per element-group block
@@ -136,11 +138,19 @@ __global__ void __launch_bounds__(512) ax_tma_kernel(int64_t E, int NE, int64_t 
     float bw[N];
     if (RES && valid) {
       const int64_t e = e0 + le;
-      const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
-      auto shared2 = [](int a, int ea, int na) { return (a == 0 && ea > 0) || (a == N - 1 && ea < na - 1); };
-      const float wxy = (shared2(i, ex, nx) ? 0.5f : 1.f) * (shared2(j, ey, ny) ? 0.5f : 1.f);
+      if (nx > 0) {
+        const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
+        auto shared2 = [](int a, int ea, int na) { return (a == 0 && ea > 0) || (a == N - 1 && ea < na - 1); };
+        const float wxy = (shared2(i, ex, nx) ? 0.5f : 1.f) * (shared2(j, ey, ny) ? 0.5f : 1.f);
 #pragma unroll
-      for (int k = 0; k < N; ++k) bw[k] = cu[7 * S + ij + N2 * k] * (wxy * (shared2(k, ez, nz) ? 0.5f : 1.f));
+        for (int k = 0; k < N; ++k) bw[k] = cu[7 * S + ij + N2 * k] * (wxy * (shared2(k, ez, nz) ? 0.5f : 1.f));
+      } else {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          const int mlog = __ffs(pflag[e * N3 + ij + N2 * k] & 0x0F) - 1;
+          bw[k] = cu[7 * S + ij + N2 * k] * __int_as_float((127 - mlog) << 23);
+        }
+      }
     }
     float ru[N], ry[N];
 #pragma unroll
@@ -218,7 +228,7 @@ static int launch_ax_tma_t(const Level& lv, const float* u, float* y, int NE, co
   if (grid > groups) grid = groups;
   ax_tma_kernel<N, RES><<<(unsigned)grid, threads, smem, s>>>(lv.E, NE, groups, u, lv.G32, lv.L,
                                                                lv.D32, y, sub, lv.nel[0],
-                                                               lv.nel[1], lv.nel[2]);
+                                                               lv.nel[1], lv.nel[2], lv.pflag);
   SE_LAUNCH_CHECK();
   return SE_OK;
 }

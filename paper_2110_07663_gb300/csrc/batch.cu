@@ -1,0 +1,784 @@
+// Batched solves (se_batch_*): many independent Poisson problems in one device-driven launch.
+//
+// Problems whose preconditioners share a configuration (schedule, smoother, Chebyshev orders,
+// bounds multipliers, coarse tolerance, precision) form a group.  A group is solved as ONE union
+// problem: every level's elements of all members are laid end to end (geometry, point flags,
+// neighbour ids shifted by the member's first element, FDM factors, Jacobi diagonals), QQ^T of
+// each union level runs from a sorted index map over the members' global ids shifted apart, and
+// so each phase of the method (operator, QQ^T, smoother, Chebyshev update, transfers) is one
+// launch over all members' elements.  The members' Chebyshev bounds differ (lambda-tilde of
+// Sec. 2.2.3 per member and level); each member's smoother is scaled by 1/lambda-tilde (its FDM
+// eigenvalues multiplied by lambda-tilde, its Jacobi diagonal divided by it), which leaves the
+// Chebyshev polynomial of Algorithm 2 unchanged and gives every member the bounds
+// (eig_lo, eig_hi), so one recurrence serves the whole group.  What stays per member:
+//  * the outer flexible PCG's scalars: inner products over each member's point range
+//    (deterministic per-member reductions), its own alpha, beta, residual and convergence; a
+//    member that has converged keeps its iterate while the others continue;
+//  * the coarsest level: the members' Jacobi-PCG solves run together in one cooperative launch,
+//    each on its own blocks to its own tolerance.
+// The solve loop is a CUDA graph: WHILE any member is active, the iteration's launches run once
+// for the whole group.  Problems that do not fit a group (no preconditioner, ASM smoother,
+// additive cycle, df64 arithmetic) run their own graph branch, as se_solve with graph_capture.
+#include <cmath>
+#include <map>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "pmg_internal.h"
+#include "reduce.h"
+
+namespace se {
+
+// ------------------------------------------------------------------ per-member reductions
+constexpr int SEG_BLOCKS = 48;  // blocks per member of a per-member reduction
+enum { SG_RZ = 0, SG_PW, SG_ALPHA, SG_BETA, SG_RR, SG_R0, SG_SLOTS = 8 };
+
+// Fused elementwise + reduction over each member's point range [off[m], off[m + 1]): grid
+// (SEG_BLOCKS, members); per-member partial sums, summed in block order by the member's last
+// block (deterministic).  Members whose active flag is 0 are skipped entirely.
+template <class Op>
+__global__ void __launch_bounds__(RED_THREADS) seg_fused_kernel(Op op, const int64_t* __restrict__ off,
+                                                                const int* __restrict__ active,
+                                                                double* __restrict__ partial,
+                                                                unsigned* __restrict__ counter) {
+  constexpr int K = Op::K;
+  const int m = blockIdx.y;
+  if (active && !active[m]) return;  // uniform over the member's blocks
+  double acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) acc[k] = 0.0;
+  const int64_t lo = off[m], hi = off[m + 1];
+  const int64_t stride = (int64_t)gridDim.x * RED_THREADS;
+  for (int64_t i = lo + (int64_t)blockIdx.x * RED_THREADS + threadIdx.x; i < hi; i += stride)
+    op.point(i, m, acc);
+  __shared__ double sh[K][RED_THREADS / 32];
+  __shared__ bool last;
+  block_sum<K>(acc, sh);
+  double* part = partial + (int64_t)m * gridDim.x * K;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) part[(int64_t)blockIdx.x * K + k] = acc[k];
+    __threadfence();
+    const unsigned t = atomicAdd(counter + m, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double w[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) w[k] = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += RED_THREADS)
+#pragma unroll
+    for (int k = 0; k < K; ++k) w[k] += __ldcg(part + (int64_t)b * K + k);
+  block_sum<K>(w, sh);
+  if (threadIdx.x == 0) {
+    op.finalize(m, w);
+    counter[m] = 0u;
+  }
+}
+
+struct SegInitOp {  // rz = (r, z), rr = (r, r), r0 = rr
+  static constexpr int K = 2;
+  const double* r;
+  const double* z;
+  const uint8_t* pf;
+  double* scal;
+  __device__ void point(int64_t i, int, double (&acc)[2]) const {
+    const double rv = r[i];
+    const double rw = scale_pow2(rv, mult_log2(pf[i]));
+    acc[0] = fma(rw, z[i], acc[0]);
+    acc[1] = fma(rw, rv, acc[1]);
+  }
+  __device__ void finalize(int m, const double* s) const {
+    double* q = scal + m * SG_SLOTS;
+    q[SG_RZ] = s[0];
+    q[SG_RR] = s[1];
+    q[SG_R0] = s[1];
+  }
+};
+
+struct SegNormOp {  // r0 = (b, b): the reference of the ||b||-relative stopping rule
+  static constexpr int K = 1;
+  const double* b;
+  const uint8_t* pf;
+  double* scal;
+  __device__ void point(int64_t i, int, double (&acc)[1]) const {
+    acc[0] = fma(scale_pow2(b[i], mult_log2(pf[i])), b[i], acc[0]);
+  }
+  __device__ void finalize(int m, const double* s) const { scal[m * SG_SLOTS + SG_R0] = s[0]; }
+};
+
+struct SegAlphaOp {  // pw = (p, w); alpha = rz / pw
+  static constexpr int K = 1;
+  const double* p;
+  const double* w;
+  const uint8_t* pf;
+  double* scal;
+  __device__ void point(int64_t i, int, double (&acc)[1]) const {
+    acc[0] = fma(scale_pow2(p[i], mult_log2(pf[i])), w[i], acc[0]);
+  }
+  __device__ void finalize(int m, const double* s) const {
+    double* q = scal + m * SG_SLOTS;
+    q[SG_PW] = s[0];
+    q[SG_ALPHA] = q[SG_RZ] / s[0];
+  }
+};
+
+struct SegUpdateOp {  // x += alpha p; r_old = r; r -= alpha w; rr = (r, r)
+  static constexpr int K = 1;
+  double* x;
+  const double* p;
+  double* r;
+  const double* w;
+  double* r_old;
+  const uint8_t* pf;
+  double* scal;
+  __device__ void point(int64_t i, int m, double (&acc)[1]) const {
+    const double alpha = scal[m * SG_SLOTS + SG_ALPHA];
+    x[i] = fma(alpha, p[i], x[i]);
+    const double ro = r[i];
+    r_old[i] = ro;
+    const double rv = fma(-alpha, w[i], ro);
+    r[i] = rv;
+    acc[0] = fma(scale_pow2(rv, mult_log2(pf[i])), rv, acc[0]);
+  }
+  __device__ void finalize(int m, const double* s) const { scal[m * SG_SLOTS + SG_RR] = s[0]; }
+};
+
+struct SegBetaOp {  // zr = (z, r); zro = (z, r_old); beta = (zr - zro) / rz; rz = zr
+  static constexpr int K = 2;
+  const double* z;
+  const double* r;
+  const double* r_old;
+  const uint8_t* pf;
+  double* scal;
+  __device__ void point(int64_t i, int, double (&acc)[2]) const {
+    const double zw = scale_pow2(z[i], mult_log2(pf[i]));
+    acc[0] = fma(zw, r[i], acc[0]);
+    acc[1] = fma(zw, r_old[i], acc[1]);
+  }
+  __device__ void finalize(int m, const double* s) const {
+    double* q = scal + m * SG_SLOTS;
+    q[SG_BETA] = (s[0] - s[1]) / q[SG_RZ];
+    q[SG_RZ] = s[0];
+  }
+};
+
+__global__ void seg_pupdate_kernel(double* __restrict__ p, const double* __restrict__ z,
+                                   const double* __restrict__ scal, const int64_t* __restrict__ off,
+                                   const int* __restrict__ active) {
+  const int m = blockIdx.y;
+  if (!active[m]) return;
+  const double beta = scal[m * SG_SLOTS + SG_BETA];
+  const int64_t hi = off[m + 1];
+  for (int64_t i = off[m] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hi;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = fma(beta, p[i], z[i]);
+}
+
+// Members' vectors to and from the union vector: piece m of u is member m's vector.
+__global__ void seg_gather_kernel(double* __restrict__ u, const double* const* __restrict__ src,
+                                  const int64_t* __restrict__ off) {
+  const int m = blockIdx.y;
+  const double* a = src[m];
+  const int64_t lo = off[m], n = off[m + 1] - lo;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    u[lo + i] = a[i];
+}
+__global__ void seg_scatter_kernel(const double* __restrict__ u, double* const* __restrict__ dst,
+                                   const int64_t* __restrict__ off) {
+  const int m = blockIdx.y;
+  double* a = dst[m];
+  const int64_t lo = off[m], n = off[m + 1] - lo;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = u[lo + i];
+}
+
+struct SegStats {
+  int iterations;
+  int active;
+  double rel;
+};
+
+// After the first residual: every member's relative residual, active flag, and the loop's
+// condition (some member above tolerance).
+__global__ void seg_init_check_kernel(const double* __restrict__ scal, SegStats* st, int* active,
+                                      int n, double tol, int maxit, cudaGraphConditionalHandle hw) {
+  int any = 0;
+  for (int m = threadIdx.x; m < n; m += blockDim.x) {
+    const double ref = scal[m * SG_SLOTS + SG_R0];
+    const double rel = ref > 0.0 ? sqrt(scal[m * SG_SLOTS + SG_RR] / ref) : 0.0;
+    const int on = (ref > 0.0 && rel > tol && maxit > 0) ? 1 : 0;
+    st[m].iterations = 0;
+    st[m].rel = rel;
+    st[m].active = on;
+    active[m] = on;
+    any |= on;
+  }
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) cudaGraphSetConditional(hw, any ? 1u : 0u);
+}
+
+// After each update: the active members count the iteration and test their residual; the loop
+// (and the preconditioner of this iteration) continues while any member stays active.
+__global__ void seg_check_kernel(const double* __restrict__ scal, SegStats* st, int* active, int n,
+                                 double tol, int maxit, cudaGraphConditionalHandle hw,
+                                 cudaGraphConditionalHandle hif) {
+  int any = 0;
+  for (int m = threadIdx.x; m < n; m += blockDim.x) {
+    if (!active[m]) continue;
+    const int it = st[m].iterations + 1;
+    st[m].iterations = it;
+    const double rel = sqrt(scal[m * SG_SLOTS + SG_RR] / scal[m * SG_SLOTS + SG_R0]);
+    st[m].rel = rel;
+    const int on = (rel > tol && it < maxit) ? 1 : 0;  // a NaN residual stops the member too
+    st[m].active = on;
+    active[m] = on;
+    any |= on;
+  }
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) {
+    cudaGraphSetConditional(hw, any ? 1u : 0u);
+    cudaGraphSetConditional(hif, any ? 1u : 0u);
+  }
+}
+
+// Copy with a scale per member (piece m of dst = scale[m] x piece m of src).
+template <class T>
+__global__ void scaled_copy_kernel(T* __restrict__ dst, const T* __restrict__ src, int64_t n, double scale) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = (T)((double)src[i] * scale);
+}
+__global__ void shifted_ids_kernel(int* __restrict__ dst, const int* __restrict__ src, int64_t n, int shift) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[i] >= 0 ? src[i] + shift : -1;
+}
+
+// ------------------------------------------------------------------ one group
+struct BatchGroup {
+  std::vector<int> idx;        // the members' problem indices
+  int n = 0;
+  se_pmg_s* U = nullptr;       // union preconditioner: union levels, vectors, grouped coarse solve
+  Level fine;                  // union level 0 as the outer operator uses it (FP64)
+  std::vector<int64_t> hoff;   // level-0 point offsets of the members [n + 1]
+  int64_t* off = nullptr;      // device copy
+  double *b = nullptr, *x = nullptr, *r = nullptr, *r_old = nullptr, *z = nullptr, *p = nullptr,
+         *w = nullptr;
+  const double** bsrc = nullptr;  // device table of the members' b
+  double** xdst = nullptr;        // device table of the members' x
+  double* scal = nullptr;         // [n][SG_SLOTS]
+  int* active = nullptr;          // [n]
+  SegStats* stats = nullptr;      // [n]
+  double* partial = nullptr;      // [n][SEG_BLOCKS][2]
+  unsigned* counter = nullptr;    // [n]
+  CoarseGroup cg;
+};
+
+static int seg_blocks_x(const BatchGroup& G, int threads) {
+  int64_t mx = 1;
+  for (int m = 0; m < G.n; ++m) mx = std::max<int64_t>(mx, G.hoff[m + 1] - G.hoff[m]);
+  return (int)std::min<int64_t>(SEG_BLOCKS, (mx + threads - 1) / threads);
+}
+
+template <class Op>
+static int run_seg(const BatchGroup& G, const Op& op, bool skip_inactive, cudaStream_t s, double bytes) {
+  ProfScope prof(SE_K_KRYLOV, s, (double)G.fine.L, bytes, 2.0 * G.fine.L);
+  const dim3 grid(seg_blocks_x(G, RED_THREADS), G.n);
+  seg_fused_kernel<Op><<<grid, RED_THREADS, 0, s>>>(op, G.off, skip_inactive ? G.active : nullptr,
+                                                    G.partial, G.counter);
+  SE_LAUNCH_CHECK();
+  return SE_OK;
+}
+
+// The union of the members' levels l (see the file comment).  lam_scale[m]: member m's smoother
+// scale 1/lambda-tilde on this level (1 on the coarsest).
+static int build_union_level(se_pmg_s* U, int l, const std::vector<se_pmg_s*>& Pm, bool fp32,
+                             int smoother, cudaStream_t s) {
+  const int n = (int)Pm.size();
+  const bool coarsest = l == U->nlev - 1;
+  const Level& a0 = *Pm[0]->lv[l];
+  Level& u = U->owned[l];
+  u = Level();
+  u.p = a0.p;
+  u.N = a0.N;
+  u.basis = a0.basis;
+  u.D64 = a0.D64;   // derivative tables depend on p only: shared with member 0
+  u.D32 = a0.D32;
+  u.eo64 = a0.eo64;
+  for (int f = 0; f < 6; ++f) u.bc[f] = a0.bc[f];
+  for (const se_pmg_s* P : Pm) {
+    u.E += P->lv[l]->E;
+    u.L += P->lv[l]->L;
+    u.n_global += P->lv[l]->n_global;
+  }
+  SE_CHECK(u.L < ((int64_t)1 << 31), SE_EINVAL, "se_batch: a group's level %d has %lld points (limit 2^31)",
+           l, (long long)u.L);
+  Allocs& A = U->allocs;
+  const int N3 = u.N * u.N * u.N, PB = u.p + 3;
+  const bool want64 = l == 0 || (!fp32 && !coarsest);
+  const bool want32 = fp32 && !coarsest;
+  SE_TRY(dmalloc(A, &u.pflag, (size_t)u.L));
+  if (want64) SE_TRY(dmalloc(A, &u.G64, 6 * (size_t)u.L));
+  if (want32) SE_TRY(dmalloc(A, &u.G32, 6 * (size_t)u.L));
+  const bool ras = smoother == SE_SMOOTH_RAS && !coarsest;
+  const bool jac = smoother == SE_SMOOTH_JACOBI && !coarsest;
+  if (jac && !fp32) SE_TRY(dmalloc(A, &u.dinv64, (size_t)u.L));
+  if (jac && fp32) SE_TRY(dmalloc(A, &u.dinv32, (size_t)u.L));
+  int* nbr = nullptr;
+  if (ras) {
+    SE_TRY(dmalloc(A, &nbr, 27 * (size_t)u.E));
+    u.nbr = nbr;
+    if (fp32) {
+      SE_TRY(dmalloc(A, &u.S32, 3 * (size_t)u.E * PB * PB));
+      SE_TRY(dmalloc(A, &u.lam32, 3 * (size_t)u.E * PB));
+    } else {
+      SE_TRY(dmalloc(A, &u.S64, 3 * (size_t)u.E * PB * PB));
+      SE_TRY(dmalloc(A, &u.lam64, 3 * (size_t)u.E * PB));
+      SE_TRY(dmalloc(A, &u.fdm_dinv64, (size_t)u.E * PB * PB * PB));
+    }
+  }
+  std::vector<int64_t> gid((size_t)u.L);
+  std::vector<uint8_t> dir((size_t)u.L);
+  int64_t eo = 0, lo = 0, go = 0;
+  int* l2g = nullptr;
+  int64_t maxL = 0;
+  for (const se_pmg_s* P : Pm) maxL = std::max(maxL, P->lv[l]->L);
+  SE_TRY(dmalloc_transient(reinterpret_cast<void**>(&l2g), (size_t)maxL * sizeof(int), s));
+  std::vector<int> g32((size_t)maxL);
+  std::vector<uint8_t> pf((size_t)maxL);
+  int rc = SE_OK;
+  for (int m = 0; m < n && rc == SE_OK; ++m) {
+    const Level& a = *Pm[m]->lv[l];
+    const double inv_lam = coarsest ? 1.0 : 1.0 / Pm[m]->lam[l];
+    auto cp = [&](void* dst, const void* src, size_t bytes) {
+      if (rc == SE_OK && cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+        set_error("se_batch: copy failed");
+        rc = SE_ECUDA;
+      }
+    };
+    cp(u.pflag + lo, a.pflag, (size_t)a.L);
+    for (int c = 0; c < 6; ++c) {
+      if (want64) cp(u.G64 + c * u.L + lo, a.G64 + c * a.L, (size_t)a.L * sizeof(double));
+      if (want32) cp(u.G32 + c * u.L + lo, a.G32 + c * a.L, (size_t)a.L * sizeof(float));
+    }
+    if (jac && !fp32)
+      scaled_copy_kernel<double><<<grid_for(a.L, 256), 256, 0, s>>>(u.dinv64 + lo, a.dinv64, a.L, inv_lam);
+    if (jac && fp32)
+      scaled_copy_kernel<float><<<grid_for(a.L, 256), 256, 0, s>>>(u.dinv32 + lo, a.dinv32, a.L, inv_lam);
+    if (ras) {
+      shifted_ids_kernel<<<grid_for(27 * a.E, 256), 256, 0, s>>>(nbr + 27 * eo, a.nbr, 27 * a.E, (int)eo);
+      const int64_t ns = 3 * a.E * PB * PB, nl = 3 * a.E * PB;
+      if (fp32) {
+        cp(u.S32 + 3 * eo * PB * PB, a.S32, (size_t)ns * sizeof(float));
+        scaled_copy_kernel<float><<<grid_for(nl, 256), 256, 0, s>>>(u.lam32 + 3 * eo * PB, a.lam32, nl,
+                                                                   1.0 / inv_lam);
+      } else {
+        cp(u.S64 + 3 * eo * PB * PB, a.S64, (size_t)ns * sizeof(double));
+        scaled_copy_kernel<double><<<grid_for(nl, 256), 256, 0, s>>>(u.lam64 + 3 * eo * PB, a.lam64, nl,
+                                                                    1.0 / inv_lam);
+        const int64_t nd = a.E * PB * PB * PB;
+        scaled_copy_kernel<double><<<grid_for(nd, 256), 256, 0, s>>>(u.fdm_dinv64 + eo * PB * PB * PB,
+                                                                    a.fdm_dinv64, nd, inv_lam);
+      }
+    }
+    if (cudaGetLastError() != cudaSuccess && rc == SE_OK) {
+      set_error("se_batch: union level kernel launch failed");
+      rc = SE_ECUDA;
+    }
+    // global ids of the member's lattice, shifted past the previous members'
+    if (rc == SE_OK) rc = local_to_global(a, l2g, s);
+    if (rc == SE_OK &&
+        (cudaMemcpyAsync(g32.data(), l2g, (size_t)a.L * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+         cudaMemcpyAsync(pf.data(), a.pflag, (size_t)a.L, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+         cudaStreamSynchronize(s) != cudaSuccess)) {
+      set_error("se_batch: %s", cudaGetErrorString(cudaGetLastError()));
+      rc = SE_ECUDA;
+    }
+    for (int64_t q = 0; q < a.L && rc == SE_OK; ++q) {
+      gid[(size_t)(lo + q)] = go + g32[(size_t)q];
+      dir[(size_t)(lo + q)] = (pf[(size_t)q] & PF_FREE) ? 0 : 1;
+    }
+    eo += a.E;
+    lo += a.L;
+    go += a.n_global;
+    (void)N3;
+  }
+  cudaFreeAsync(l2g, s);
+  SE_TRY(rc);
+  SE_TRY(build_gsmap_from_gid(u, gid.data(), dir.data(), A, s));
+  U->lv[l] = &U->owned[l];
+  return SE_OK;
+}
+
+static void destroy_group(BatchGroup* G) {
+  if (!G) return;
+  if (G->U) {
+    cudaStreamSynchronize(G->U->stream);
+    G->U->allocs.release();
+    pinned_release(G->U->scratch.hscal);
+    cudaStream_t st = G->U->stream;
+    delete G->U;
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
+  delete G;
+}
+
+static int build_group(BatchGroup* G, const std::vector<se_problem>& probs) {
+  const int n = G->n = (int)G->idx.size();
+  std::vector<se_pmg_s*> Pm(n);
+  for (int m = 0; m < n; ++m) Pm[m] = probs[G->idx[m]].pmg;
+  const se_pmg_desc& d = Pm[0]->desc;
+  const bool fp32 = d.precision == SE_FP32;
+  auto* U = new se_pmg_s();
+  G->U = U;
+  SE_CUDA(cudaStreamCreateWithFlags(&U->stream, cudaStreamNonBlocking));
+  cudaStream_t s = U->stream;
+  U->allocs.stream = s;
+  U->desc = d;
+  U->nlev = d.nlev;
+  for (int m = 0; m < n; ++m)  // the members' set-up work must be complete
+    SE_CUDA(cudaStreamSynchronize(Pm[m]->stream));
+  SE_TRY(scratch_alloc(U->allocs, &U->scratch));
+  for (int l = 0; l < U->nlev; ++l) {
+    SE_TRY(build_union_level(U, l, Pm, fp32, d.smoother, s));
+    U->lam[l] = 1.0;
+    U->lmin[l] = d.eig_lo;
+    U->lmax[l] = d.eig_hi;
+    if (l + 1 < U->nlev) {
+      U->J64[l] = Pm[0]->J64[l];  // interpolation matrices depend on the orders only
+      U->J32[l] = Pm[0]->J32[l];
+    }
+    SE_TRY(pmg_alloc_vecs(U, l, fp32));
+  }
+  // coarse problems: the members' own coarse operators and work spaces, on the union vectors
+  const int lc = U->nlev - 1;
+  std::vector<const Level*> clv(n);
+  std::vector<CoarseWork*> cwk(n);
+  std::vector<int64_t> coff(n + 1, 0);
+  for (int m = 0; m < n; ++m) {
+    clv[m] = Pm[m]->lv[lc];
+    cwk[m] = &Pm[m]->cw;
+    coff[m + 1] = coff[m] + Pm[m]->lv[lc]->L;
+  }
+  const void* rin = fp32 ? (const void*)U->v32[lc].b : (const void*)U->v64[lc].b;
+  void* xout = fp32 ? (void*)U->v32[lc].x : (void*)U->v64[lc].x;
+  SE_TRY(coarse_group_setup(&G->cg, clv.data(), cwk.data(), n, fp32, rin, xout, coff.data(),
+                            d.coarse_tol, d.coarse_maxit, U->allocs, s));
+  U->cgroup = &G->cg;
+  // outer solver state
+  G->fine = U->owned[0];
+  const int64_t L = G->fine.L;
+  Allocs& A = U->allocs;
+  for (double** v : {&G->b, &G->x, &G->r, &G->r_old, &G->z, &G->p, &G->w}) SE_TRY(dmalloc(A, v, (size_t)L));
+  G->hoff.assign(n + 1, 0);
+  std::vector<const double*> bs(n);
+  std::vector<double*> xs(n);
+  for (int m = 0; m < n; ++m) {
+    G->hoff[m + 1] = G->hoff[m] + Pm[m]->lv[0]->L;
+    bs[m] = probs[G->idx[m]].b;
+    xs[m] = probs[G->idx[m]].x;
+  }
+  SE_TRY(dmalloc(A, &G->off, (size_t)n + 1));
+  SE_TRY(dmalloc(A, &G->bsrc, (size_t)n));
+  SE_TRY(dmalloc(A, &G->xdst, (size_t)n));
+  SE_TRY(dmalloc(A, &G->scal, (size_t)n * SG_SLOTS));
+  SE_TRY(dmalloc(A, &G->active, (size_t)n));
+  SE_TRY(dmalloc_bytes(A, reinterpret_cast<void**>(&G->stats), (size_t)n * sizeof(SegStats)));
+  SE_TRY(dmalloc(A, &G->partial, (size_t)n * SEG_BLOCKS * 2));
+  SE_TRY(dmalloc(A, &G->counter, (size_t)n));
+  SE_CUDA(cudaMemcpyAsync(G->off, G->hoff.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  SE_CUDA(cudaMemcpyAsync(G->bsrc, bs.data(), n * sizeof(double*), cudaMemcpyHostToDevice, s));
+  SE_CUDA(cudaMemcpyAsync(G->xdst, xs.data(), n * sizeof(double*), cudaMemcpyHostToDevice, s));
+  SE_CUDA(cudaMemsetAsync(G->counter, 0, n * sizeof(unsigned), s));
+  SE_CUDA(cudaMemsetAsync(G->scal, 0, n * SG_SLOTS * sizeof(double), s));
+  SE_CUDA(cudaMemsetAsync(G->stats, 0, n * sizeof(SegStats), s));
+  SE_CUDA(cudaStreamSynchronize(s));
+  return SE_OK;
+}
+
+// The group's whole solve as one branch of G (x0 = the members' x at launch).
+static int append_group_solve(cudaGraph_t Gr, cudaStream_t cs, BatchGroup* G, double tol, int maxit,
+                              int tol_norm) {
+  const Level& lv = G->fine;
+  const int64_t L = lv.L;
+  const dim3 vgrid(seg_blocks_x(*G, 256), G->n);
+  cudaGraphConditionalHandle hw, hif;
+  SE_CUDA(cudaGraphConditionalHandleCreate(&hw, Gr, 0, 0));
+  SE_CUDA(cudaStreamBeginCaptureToGraph(cs, Gr, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  int rc = SE_OK;
+  cudaGraph_t wbody = nullptr, ifbody = nullptr;
+  do {
+    seg_gather_kernel<<<vgrid, 256, 0, cs>>>(G->b, G->bsrc, G->off);
+    seg_gather_kernel<<<vgrid, 256, 0, cs>>>(G->x, const_cast<const double* const*>(G->xdst), G->off);
+    if ((rc = ax_apply<double>(lv, G->x, G->w, cs)) != SE_OK) break;
+    if ((rc = axpby<double>(1.0, G->b, -1.0, G->w, G->r, L, cs)) != SE_OK) break;  // r = b - A x
+    if ((rc = pmg_apply(G->U, G->r, G->z, cs)) != SE_OK) break;                    // z = M r
+    if ((rc = run_seg(*G, SegInitOp{G->r, G->z, lv.pflag, G->scal}, false, cs, 17.0 * L)) != SE_OK) break;
+    if (tol_norm == SE_TOL_B &&
+        (rc = run_seg(*G, SegNormOp{G->b, lv.pflag, G->scal}, false, cs, 9.0 * L)) != SE_OK)
+      break;
+    if (cudaMemcpyAsync(G->p, G->z, L * sizeof(double), cudaMemcpyDeviceToDevice, cs) != cudaSuccess) {
+      set_error("se_batch: copy capture failed");
+      rc = SE_ECUDA;
+      break;
+    }
+    seg_init_check_kernel<<<1, 256, 0, cs>>>(G->scal, G->stats, G->active, G->n, tol, maxit, hw);
+    if ((rc = add_conditional(cs, hw, cudaGraphCondTypeWhile, &wbody)) != SE_OK) break;
+    seg_scatter_kernel<<<vgrid, 256, 0, cs>>>(G->x, G->xdst, G->off);  // after the loop
+  } while (0);
+  cudaGraph_t out = nullptr;
+  cudaError_t ec = cudaStreamEndCapture(cs, &out);
+  if (rc != SE_OK) return rc;
+  SE_CHECK(ec == cudaSuccess, SE_ECUDA, "se_batch graph (init): %s", cudaGetErrorString(ec));
+  // WHILE body: w = A p, per-member alpha, x / r update, convergence test
+  SE_CUDA(cudaGraphConditionalHandleCreate(&hif, Gr, 0, 0));
+  SE_CUDA(cudaStreamBeginCaptureToGraph(cs, wbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  do {
+    if ((rc = ax_apply<double>(lv, G->p, G->w, cs)) != SE_OK) break;
+    if ((rc = run_seg(*G, SegAlphaOp{G->p, G->w, lv.pflag, G->scal}, true, cs, 17.0 * L)) != SE_OK) break;
+    if ((rc = run_seg(*G, SegUpdateOp{G->x, G->p, G->r, G->w, G->r_old, lv.pflag, G->scal}, true, cs,
+                      57.0 * L)) != SE_OK)
+      break;
+    seg_check_kernel<<<1, 256, 0, cs>>>(G->scal, G->stats, G->active, G->n, tol, maxit, hw, hif);
+    rc = add_conditional(cs, hif, cudaGraphCondTypeIf, &ifbody);
+  } while (0);
+  ec = cudaStreamEndCapture(cs, &out);
+  if (rc != SE_OK) return rc;
+  SE_CHECK(ec == cudaSuccess, SE_ECUDA, "se_batch graph (loop): %s", cudaGetErrorString(ec));
+  // IF body: z = M r for the union, per-member beta, p = z + beta p
+  SE_CUDA(cudaStreamBeginCaptureToGraph(cs, ifbody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  do {
+    if ((rc = pmg_apply(G->U, G->r, G->z, cs)) != SE_OK) break;
+    if ((rc = run_seg(*G, SegBetaOp{G->z, G->r, G->r_old, lv.pflag, G->scal}, true, cs, 25.0 * L)) != SE_OK)
+      break;
+    {
+      ProfScope prof(SE_K_KRYLOV, cs, (double)L, 24.0 * L, 2.0 * L);
+      seg_pupdate_kernel<<<vgrid, 256, 0, cs>>>(G->p, G->z, G->scal, G->off, G->active);
+      if (cudaGetLastError() != cudaSuccess) {
+        set_error("se_batch: launch failed");
+        rc = SE_ECUDA;
+      }
+    }
+  } while (0);
+  ec = cudaStreamEndCapture(cs, &out);
+  if (rc != SE_OK) return rc;
+  SE_CHECK(ec == cudaSuccess, SE_ECUDA, "se_batch graph (preconditioner): %s", cudaGetErrorString(ec));
+  return SE_OK;
+}
+
+// Problems that share a group: same preconditioner configuration, one of the supported kinds.
+static bool groupable(const se_problem& q, const se_solve_opts& o) {
+  if (!q.pmg || o.operator_df64) return false;
+  const se_pmg_desc& d = q.pmg->desc;
+  return (d.precision == SE_FP64 || d.precision == SE_FP32) && d.cycle == SE_CYCLE_MULTIPLICATIVE &&
+         (d.smoother == SE_SMOOTH_RAS || d.smoother == SE_SMOOTH_JACOBI);
+}
+
+static std::string group_key(const se_pmg_desc& d) {
+  std::string k = std::to_string(d.nlev) + ":" + std::to_string(d.smoother) + ":" +
+                  std::to_string(d.precision) + ":";
+  for (int l = 0; l < d.nlev; ++l) k += std::to_string(d.schedule[l]) + ",";
+  k += ":";
+  for (int l = 0; l + 1 < d.nlev; ++l) k += std::to_string(d.cheb_order[l]) + ",";
+  char buf[96];
+  snprintf(buf, sizeof(buf), ":%.17g:%.17g:%.17g:%d", d.eig_lo, d.eig_hi, d.coarse_tol, d.coarse_maxit);
+  return k + buf;
+}
+
+}  // namespace se
+
+using namespace se;
+
+struct se_batch_s {
+  std::vector<se_problem> probs;
+  se_solve_opts opts;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<BatchGroup*> groups;
+  std::vector<int> alone;          // problems with their own graph branch
+  std::vector<int> group_of, slot;  // per problem: group index (-1: alone) and member slot
+};
+
+static void batch_free(se_batch_s* B) {
+  if (!B) return;
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  for (BatchGroup* G : B->groups) destroy_group(G);
+  delete B;
+}
+
+extern "C" {
+
+int se_batch_create(int n, const se_problem* probs, const se_solve_opts* opts, se_batch_t* out) {
+  SE_CHECK(n >= 1 && probs && opts && out, SE_EINVAL, "se_batch_create: bad argument");
+  SE_CHECK(opts->method == SE_FPCG, SE_EINVAL, "se_batch_create: batched solves use SE_FPCG");
+  SE_CHECK(opts->tol > 0 && opts->maxit >= 1, SE_EINVAL, "se_batch_create: bad tolerance or maxit");
+  SE_CHECK(opts->tol_norm == SE_TOL_R0 || opts->tol_norm == SE_TOL_B, SE_EINVAL,
+           "se_batch_create: bad tol_norm");
+  for (int i = 0; i < n; ++i) {
+    SE_CHECK(probs[i].mesh && probs[i].b && probs[i].x, SE_EINVAL, "se_batch_create: problem %d incomplete", i);
+    SE_CHECK(!probs[i].pmg || probs[i].pmg->mesh == probs[i].mesh, SE_EINVAL,
+             "se_batch_create: problem %d: preconditioner of another mesh", i);
+    for (int j = 0; j < i; ++j) {
+      SE_CHECK(probs[j].mesh != probs[i].mesh, SE_EINVAL,
+               "se_batch_create: problems %d and %d share a mesh (its work space)", j, i);
+      SE_CHECK(!probs[i].pmg || probs[j].pmg != probs[i].pmg, SE_EINVAL,
+               "se_batch_create: problems %d and %d share a preconditioner", j, i);
+    }
+  }
+  auto* B = new se_batch_s();
+  B->probs.assign(probs, probs + n);
+  B->opts = *opts;
+  B->group_of.assign(n, -1);
+  B->slot.assign(n, -1);
+  std::map<std::string, int> keys;
+  std::vector<std::vector<int>> members;
+  for (int i = 0; i < n; ++i) {
+    if (!groupable(probs[i], *opts)) {
+      B->alone.push_back(i);
+      continue;
+    }
+    const std::string k = group_key(probs[i].pmg->desc);
+    auto it = keys.find(k);
+    if (it == keys.end()) {
+      it = keys.emplace(k, (int)members.size()).first;
+      members.emplace_back();
+    }
+    B->group_of[i] = it->second;
+    B->slot[i] = (int)members[it->second].size();
+    members[it->second].push_back(i);
+  }
+  int rc = SE_OK;
+  for (size_t g = 0; g < members.size() && rc == SE_OK; ++g) {
+    auto* G = new BatchGroup();
+    G->idx = members[g];
+    B->groups.push_back(G);
+    rc = build_group(G, B->probs);
+  }
+  for (int i : B->alone) {
+    if (rc != SE_OK) break;
+    rc = prepare_graph_solve(probs[i].mesh);
+    if (rc == SE_OK && opts->operator_df64)
+      rc = make_df_geometry(probs[i].mesh->fine, probs[i].mesh->allocs, probs[i].mesh->stream);
+  }
+  cudaGraph_t Gr = nullptr;
+  if (rc == SE_OK && cudaGraphCreate(&Gr, 0) != cudaSuccess) {
+    set_error("cudaGraphCreate failed");
+    rc = SE_ECUDA;
+  }
+  cudaStream_t cs = nullptr;
+  if (rc == SE_OK && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    set_error("se_batch_create: stream creation failed");
+    rc = SE_ECUDA;
+  }
+  for (BatchGroup* G : B->groups) {
+    if (rc != SE_OK) break;
+    rc = append_group_solve(Gr, cs, G, opts->tol, opts->maxit, opts->tol_norm);
+  }
+  for (int i : B->alone) {
+    if (rc != SE_OK) break;
+    rc = append_fpcg_solve(Gr, cs, probs[i].mesh, probs[i].pmg, probs[i].b, probs[i].x, opts->tol,
+                           opts->maxit, opts->tol_norm, opts->operator_df64);
+  }
+  if (cs) cudaStreamDestroy(cs);
+  if (rc == SE_OK && cudaGraphInstantiate(&B->exec, Gr, 0) != cudaSuccess) {
+    set_error("se_batch_create: cudaGraphInstantiate: %s", cudaGetErrorString(cudaGetLastError()));
+    rc = SE_ECUDA;
+    B->exec = nullptr;
+  }
+  if (Gr) cudaGraphDestroy(Gr);
+  if (rc != SE_OK) {
+    batch_free(B);
+    return rc;
+  }
+  *out = B;
+  return SE_OK;
+}
+
+int se_batch_run(se_batch_t B, void* stream) {
+  SE_CHECK(B, SE_EINVAL, "se_batch_run: null batch");
+  SE_CUDA(cudaGraphLaunch(B->exec, reinterpret_cast<cudaStream_t>(stream)));
+  return SE_OK;
+}
+
+int se_batch_stats(se_batch_t B, void* stream, se_solve_stats* out) {
+  SE_CHECK(B && out, SE_EINVAL, "se_batch_stats: null argument");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  SE_CUDA(cudaStreamSynchronize(s));
+  int worst = SE_OK;
+  std::vector<std::vector<SegStats>> gs(B->groups.size());
+  for (size_t g = 0; g < B->groups.size(); ++g) {
+    gs[g].resize(B->groups[g]->n);
+    SE_CUDA(cudaMemcpy(gs[g].data(), B->groups[g]->stats, gs[g].size() * sizeof(SegStats),
+                       cudaMemcpyDeviceToHost));
+  }
+  const double tol = B->opts.tol;
+  for (size_t i = 0; i < B->probs.size(); ++i) {
+    se_solve_stats st{};
+    int rc = SE_OK;
+    if (B->group_of[i] >= 0) {
+      const SegStats& q = gs[B->group_of[i]][B->slot[i]];
+      st.iterations = q.iterations;
+      st.rel_residual = q.rel;
+      if (std::isnan(q.rel)) {
+        set_error("se_batch: problem %zu: residual became NaN", i);
+        rc = SE_ENOTCONV;
+      } else if (q.rel > tol) {
+        set_error("se_batch: problem %zu: no convergence in %d iterations (rel. residual %.3e)", i,
+                  B->opts.maxit, q.rel);
+        rc = SE_ENOTCONV;
+      }
+    } else {
+      rc = read_graph_stats(B->probs[i].mesh, s, &st, tol, B->opts.maxit);
+    }
+    st.status = rc;
+    out[i] = st;
+    if (rc != SE_OK) worst = rc;
+  }
+  int pipe = 0;
+  if (pipeline_status_take(&pipe) == SE_OK && pipe != 0) {
+    set_error("se_batch: a pipelined kernel's bounded wait expired (results invalid)");
+    worst = SE_ETIMEOUT;
+  }
+  return worst;
+}
+
+int se_batch_destroy(se_batch_t B) {
+  if (!B) return SE_OK;
+  batch_free(B);
+  return SE_OK;
+}
+
+int se_batch_solve(int n, const se_problem* probs, const se_solve_opts* opts, se_solve_stats* out) {
+  se_batch_t B = nullptr;
+  SE_TRY(se_batch_create(n, probs, opts, &B));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(opts->stream);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+  int rc = se_batch_run(B, opts->stream);
+  cudaEventRecord(e1, s);
+  if (rc == SE_OK) rc = se_batch_stats(B, opts->stream, out);
+  float ms = 0.f;
+  cudaEventSynchronize(e1);
+  cudaEventElapsedTime(&ms, e0, e1);
+  for (int i = 0; i < n; ++i) out[i].ms_total = ms;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  se_batch_destroy(B);
+  return rc;
+}
+
+int se_batch_info(se_batch_t B, int* groups, int* grouped_problems) {
+  SE_CHECK(B, SE_EINVAL, "se_batch_info: null batch");
+  if (groups) *groups = (int)B->groups.size();
+  int k = 0;
+  for (const BatchGroup* G : B->groups) k += G->n;
+  if (grouped_problems) *grouped_problems = k;
+  return SE_OK;
+}
+
+}  // extern "C"

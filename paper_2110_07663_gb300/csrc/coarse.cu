@@ -12,7 +12,9 @@
 // returns.
 #include <cooperative_groups.h>
 
+#include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "pmg_internal.h"
 
@@ -59,7 +61,8 @@ __device__ __forceinline__ unsigned load_acquire(const unsigned* p) {
 
 // Grid barrier that sums three values over the grid.  count is a monotonic arrival counter
 // (zeroed before the launch): the k-th call of every block is complete once count reaches
-// (k + 1) * nblocks.  Each block posts its sums to part[parity][block] (4 doubles, the 4th
+// (k + 1) * nblocks.  Each block (index blk among the nblocks that share count) posts its sums
+// to part[parity][blk] (4 doubles, the 4th
 // unused) and arrives with a release add; then every block waits for the count with acquire loads
 // and adds all blocks' partials itself, in block order (lane l: blocks l, l + 32, ..., then a
 // shuffle tree), so all blocks get bitwise the same sums with no second round trip through a
@@ -73,13 +76,13 @@ __device__ __forceinline__ unsigned load_acquire(const unsigned* p) {
 template <class Post>
 __device__ bool grid_sum3(unsigned* count, unsigned call, int* status, unsigned nblocks,
                           long long timeout_ns, double* part, double (&v)[3], double& post_value,
-                          double* red, Post post) {
+                          double* red, Post post, unsigned blk) {
   __shared__ double s_out[4];
   block_sum3(v, red);
   double* buf = part + (size_t)(call & 1u) * 4 * nblocks;
   if (threadIdx.x == 0) {
-    reinterpret_cast<double2*>(buf)[2 * blockIdx.x] = make_double2(v[0], v[1]);
-    reinterpret_cast<double2*>(buf)[2 * blockIdx.x + 1] = make_double2(v[2], 0.0);
+    reinterpret_cast<double2*>(buf)[2 * blk] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(buf)[2 * blk + 1] = make_double2(v[2], 0.0);
     atomic_add_release(count, 1u);
     const unsigned target = (call + 1u) * nblocks;
     const long long t0 = global_ns();
@@ -281,12 +284,12 @@ __device__ __forceinline__ double coarse_row(const double* __restrict__ Ah, cons
 // (gamma, delta, (r, r)) also orders the neighbour reads of Ahat w: w alternates between two
 // arrays (read one, write the other).  The stopping rule is that of the textbook loop: stop
 // after the update that brings (r, r) to tol^2 (b, b) or below, or after maxit updates.
+// Run by the nb blocks of one coarse problem; blk is this block's index among them.
 template <class T>
-__global__ void __launch_bounds__(CG_THREADS) coarse_pcg_kernel(CoarseArgs<T> c) {
+__device__ __forceinline__ void coarse_pcg_run(const CoarseArgs<T>& c, unsigned blk, unsigned nb) {
   __shared__ double red[3 * CG_THREADS];
-  const unsigned nb = gridDim.x;
-  const int stride = (int)gridDim.x * CG_THREADS;
-  const int t0 = (int)blockIdx.x * CG_THREADS + threadIdx.x;
+  const int stride = (int)nb * CG_THREADS;
+  const int t0 = (int)blk * CG_THREADS + threadIdx.x;
   const int NXY = c.NX * c.NY;
   unsigned call = 0;
   double v[3] = {0.0, 0.0, 0.0}, unused;
@@ -299,7 +302,7 @@ __global__ void __launch_bounds__(CG_THREADS) coarse_pcg_kernel(CoarseArgs<T> c)
     v[2] = fma(rv, rv, v[2]);
   }
   bool ok = grid_sum3(c.count, call++, c.status, nb, c.timeout_ns, c.part, v, unused, red,
-                      [](double (&)[3]) { return 0.0; });
+                      [](double (&)[3]) { return 0.0; }, blk);
   const double rr0 = v[2];
   const double tol2 = c.tol * c.tol * rr0;
   // w = A u = Ahat r; gamma = (r, u), delta = (w, u)
@@ -326,7 +329,7 @@ __global__ void __launch_bounds__(CG_THREADS) coarse_pcg_kernel(CoarseArgs<T> c)
                      w[0] = first ? gm / dl : gm / (dl - be * gm / a_prev);
                      w[1] = be;
                      return gm;
-                   });
+                   }, blk);
     if (!ok) break;
     // after a synchronisation, so x is complete whichever way the loop ends
     if (!first && v[2] <= tol2) break;  // (r, r) of the last update
@@ -364,7 +367,34 @@ __global__ void __launch_bounds__(CG_THREADS) coarse_pcg_kernel(CoarseArgs<T> c)
   if (ok) {
     for (int l = t0; l < c.L; l += stride) c.xout[l] = (T)c.x[c.l2g[l]];
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) c.status[1] = it;
+  if (blk == 0 && threadIdx.x == 0) c.status[1] = it;
+}
+
+template <class T>
+__global__ void __launch_bounds__(CG_THREADS) coarse_pcg_kernel(CoarseArgs<T> c) {
+  coarse_pcg_run(c, blockIdx.x, gridDim.x);
+}
+
+// Many independent coarse problems in one cooperative launch: problem m runs on blocks
+// [boff[m], boff[m + 1]) with its own arrival counter, partial sums, status and tolerance, so
+// each iterates to its own stopping rule (the sub-grids never wait for one another).
+template <class T>
+__global__ void __launch_bounds__(CG_THREADS) coarse_group_kernel(const CoarseArgs<T>* __restrict__ args,
+                                                                  const int* __restrict__ boff, int n) {
+  int m = 0;
+  while (m + 1 < n && boff[m + 1] <= (int)blockIdx.x) ++m;
+  const CoarseArgs<T> c = args[m];
+  coarse_pcg_run(c, blockIdx.x - (unsigned)boff[m], (unsigned)(boff[m + 1] - boff[m]));
+}
+
+__global__ void coarse_group_reset_kernel(const CoarseArgs<double>* __restrict__ a64,
+                                          const CoarseArgs<float>* __restrict__ a32, int n) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n) return;
+  unsigned* count = a64 ? a64[m].count : a32[m].count;
+  int* status = a64 ? a64[m].status : a32[m].status;
+  count[0] = count[1] = 0u;
+  status[0] = status[1] = 0;
 }
 
 // Partial sums of the summing barrier: two buffers of 4 doubles per block.
@@ -438,6 +468,116 @@ int coarse_solve(const Level& lv, CoarseWork& w, const T* r_l, T* x_l, double to
   return SE_OK;
 }
 
+// ------------------------------------------------------------------ grouped coarse solves
+template <class T>
+static CoarseArgs<T> coarse_args(const Level& lv, const CoarseWork& w, const T* r_l, T* x_l,
+                                 double tol, int maxit) {
+  CoarseArgs<T> a;
+  a.n = (int)lv.n_global;
+  a.L = (int)lv.L;
+  a.NX = lv.NX;
+  a.NY = lv.NY;
+  a.Ah = lv.Ac;
+  a.dinv = lv.cdinv;
+  a.g2l = lv.g2l;
+  a.l2g = lv.l2g;
+  a.rin = r_l;
+  a.xout = x_l;
+  a.x = w.x;
+  a.r = w.r;
+  a.u = w.u;
+  a.p = w.p;
+  a.q = w.q;
+  a.s = w.s;
+  a.z = w.z;
+  a.w0 = w.w0;
+  a.w1 = w.w1;
+  a.part = w.partial;
+  a.count = w.bar;
+  a.status = w.status;
+  a.tol = tol;
+  a.maxit = maxit;
+  a.timeout_ns = BARRIER_TIMEOUT_NS;
+  return a;
+}
+
+template <class T>
+static int coarse_group_setup_t(CoarseGroup* g, const Level* const* lv, CoarseWork* const* w, int n,
+                                const T* rin, T* xout, const int64_t* loff, double tol, int maxit,
+                                Allocs& allocs, cudaStream_t s) {
+  int dev = 0, sms = 0, per_sm = 0;
+  SE_CUDA(cudaGetDevice(&dev));
+  SE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  SE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_group_kernel<T>, CG_THREADS, 0));
+  SE_CHECK(per_sm >= 1, SE_ECUDA, "grouped coarse solver kernel cannot be resident");
+  const int cap = sms * per_sm;
+  SE_CHECK(n <= cap, SE_EINVAL, "grouped coarse solve: %d problems above the %d resident blocks", n, cap);
+  // blocks per problem: about 16 nodes per thread, at most the problem's own work-space size;
+  // the total must be co-resident (cooperative launch)
+  std::vector<int> nb(n);
+  int total = 0;
+  for (int m = 0; m < n; ++m) {
+    const int64_t want = (lv[m]->n_global + 16 * CG_THREADS - 1) / (16 * CG_THREADS);
+    nb[m] = (int)std::max<int64_t>(1, std::min<int64_t>(want, w[m]->nblocks));
+    total += nb[m];
+  }
+  while (total > cap) {
+    int big = 0;
+    for (int m = 1; m < n; ++m)
+      if (nb[m] > nb[big]) big = m;
+    --nb[big];
+    --total;
+  }
+  std::vector<CoarseArgs<T>> args(n);
+  std::vector<int> boff(n + 1, 0);
+  double nodes = 0.0;
+  for (int m = 0; m < n; ++m) {
+    args[m] = coarse_args<T>(*lv[m], *w[m], rin + loff[m], xout + loff[m], tol, maxit);
+    boff[m + 1] = boff[m] + nb[m];
+    nodes += (double)lv[m]->n_global;
+  }
+  SE_TRY(dmalloc_bytes(allocs, &g->args, n * sizeof(CoarseArgs<T>)));
+  SE_TRY(dmalloc(allocs, &g->boff, n + 1));
+  SE_CUDA(cudaMemcpyAsync(g->args, args.data(), n * sizeof(CoarseArgs<T>), cudaMemcpyHostToDevice, s));
+  SE_CUDA(cudaMemcpyAsync(g->boff, boff.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  SE_CUDA(cudaStreamSynchronize(s));
+  g->n = n;
+  g->nblocks = total;
+  g->fp32 = sizeof(T) == 4;
+  g->nodes = nodes;
+  return SE_OK;
+}
+
+int coarse_group_setup(CoarseGroup* g, const Level* const* lv, CoarseWork* const* w, int n, bool fp32,
+                       const void* rin, void* xout, const int64_t* loff, double tol, int maxit,
+                       Allocs& allocs, cudaStream_t s) {
+  SE_CHECK(n >= 1, SE_EINVAL, "grouped coarse solve: no problem");
+  if (fp32)
+    return coarse_group_setup_t<float>(g, lv, w, n, static_cast<const float*>(rin),
+                                       static_cast<float*>(xout), loff, tol, maxit, allocs, s);
+  return coarse_group_setup_t<double>(g, lv, w, n, static_cast<const double*>(rin),
+                                      static_cast<double*>(xout), loff, tol, maxit, allocs, s);
+}
+
+template <class T>
+int coarse_group_solve(const CoarseGroup& g, cudaStream_t s) {
+  SE_CHECK(g.fp32 == (sizeof(T) == 4), SE_EINVAL, "grouped coarse solve: precision mismatch");
+  ProfScope prof(SE_K_COARSE, s, g.nodes, 0.0, 0.0);
+  const CoarseArgs<T>* args = static_cast<const CoarseArgs<T>*>(g.args);
+  coarse_group_reset_kernel<<<(g.n + 127) / 128, 128, 0, s>>>(
+      sizeof(T) == 8 ? reinterpret_cast<const CoarseArgs<double>*>(args) : nullptr,
+      sizeof(T) == 4 ? reinterpret_cast<const CoarseArgs<float>*>(args) : nullptr, g.n);
+  SE_LAUNCH_CHECK();
+  const int* boff = g.boff;
+  int n = g.n;
+  void* a[] = {(void*)&args, (void*)&boff, (void*)&n};
+  SE_CUDA(cudaLaunchCooperativeKernel((const void*)coarse_group_kernel<T>, dim3(g.nblocks),
+                                      dim3(CG_THREADS), a, 0, s));
+  return SE_OK;
+}
+template int coarse_group_solve<double>(const CoarseGroup&, cudaStream_t);
+template int coarse_group_solve<float>(const CoarseGroup&, cudaStream_t);
+
 template int coarse_solve<double>(const Level&, CoarseWork&, const double*, double*, double, int, cudaStream_t);
 template int coarse_solve<float>(const Level&, CoarseWork&, const float*, float*, double, int, cudaStream_t);
 
@@ -447,7 +587,7 @@ __global__ void barrier_timeout_kernel(unsigned* count, int* status, double* par
   __shared__ double red[3 * 32];
   double v[3] = {1.0, 0.0, 0.0}, pv = 0.0;
   grid_sum3(count, 0u, status, gridDim.x + 1, timeout_ns, part, v, pv, red,
-            [](double (&)[3]) { return 0.0; });
+            [](double (&)[3]) { return 0.0; }, blockIdx.x);
 }
 
 }  // namespace se

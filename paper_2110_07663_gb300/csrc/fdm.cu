@@ -848,7 +848,8 @@ template <int P>
 __global__ void __launch_bounds__(64, Fdm32PipeDims<P + 3>::BLOCKS_PER_SM)
     fdm32_pipe_kernel(int64_t E, int nx, int ny, int nz, const int* __restrict__ nbr,
                       const float* __restrict__ in, const float* __restrict__ Sg,
-                      const float* __restrict__ lamg, float* __restrict__ out) {
+                      const float* __restrict__ lamg, const uint8_t* __restrict__ pflag,
+                      float* __restrict__ out) {
   constexpr int PB = P + 3, N = P + 1, N2 = N * N, N3 = N2 * N, PB2 = PB * PB, H = PB / 2;
   using D = Fdm32PipeDims<PB>;
   constexpr int PSN = D::PSN, EW = D::EW;
@@ -1009,10 +1010,15 @@ __global__ void __launch_bounds__(64, Fdm32PipeDims<P + 3>::BLOCKS_PER_SM)
       for (int i = 0; i < N; ++i)
 #pragma unroll
         for (int m = 0; m < H; ++m) sx[i][m] = *reinterpret_cast<const float2*>(sS + (1 + i) * PB + 2 * m);
-      const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));
+      // weights from the element's place in the lattice, or (nx = 0: a level that is the union of
+      // several lattices) from the point flags
+      const bool lat = nx > 0;
+      const int ex = lat ? (int)(e % nx) : 0, ey = lat ? (int)((e / nx) % ny) : 0;
+      const int ez = lat ? (int)(e / ((int64_t)nx * ny)) : 0;
       const float wz = ((t == 0 && ez > 0) || (t == N - 1 && ez < nz - 1)) ? 0.5f : 1.f;
       const float wx0 = ex > 0 ? 0.5f : 1.f, wx1 = ex < nx - 1 ? 0.5f : 1.f;
       float* orow = out + e * N3 + (int64_t)N2 * t;
+      const uint8_t* frow = pflag + e * N3 + (int64_t)N2 * t;
 #pragma unroll 1
       for (int bb = 0; bb < N; ++bb) {
         float2 sy[H];
@@ -1034,7 +1040,8 @@ __global__ void __launch_bounds__(64, Fdm32PipeDims<P + 3>::BLOCKS_PER_SM)
 #pragma unroll
           for (int m = 0; m < H; ++m) z = __ffma2_rn(sx[i][m], make_float2(y2[2 * m], y2[2 * m + 1]), z);
           const float wx = i == 0 ? wx0 : (i == N - 1 ? wx1 : 1.f);
-          o[i] = (z.x + z.y) * (wx * wyz);
+          const float wf = lat ? wx * wyz : __int_as_float((127 - (__ffs(frow[N * bb + i] & 0x0F) - 1)) << 23);
+          o[i] = (z.x + z.y) * wf;
         }
         float* dst = orow + N * bb;
         if constexpr (N % 4 == 0) {
@@ -1131,7 +1138,7 @@ static int launch_fdm(const Level& lv, const T* in, const T* S, const T* lam, T*
       int64_t pblocks = (int64_t)sms * per_sm;
       if (pblocks > (steps + PD::WARPS - 1) / PD::WARPS) pblocks = (steps + PD::WARPS - 1) / PD::WARPS;
       fdm32_pipe_kernel<P><<<(unsigned)pblocks, 32 * PD::WARPS, PD::SMEM, s>>>(
-          lv.E, lv.nel[0], lv.nel[1], lv.nel[2], lv.nbr, in, S, lam, out);
+          lv.E, lv.nel[0], lv.nel[1], lv.nel[2], lv.nbr, in, S, lam, lv.pflag, out);
       SE_LAUNCH_CHECK();
       return SE_OK;
     }

@@ -149,8 +149,10 @@ template <class T>
 int vcycle(se_pmg_s* P, int l, cudaStream_t s) {
   LevelVecs<T>& V = P->vecs<T>(l);
   const Level& lv = *P->lv[l];
-  if (l == P->nlev - 1)
+  if (l == P->nlev - 1) {
+    if (P->cgroup) return coarse_group_solve<T>(*P->cgroup, s);  // reads V.b, writes V.x
     return coarse_solve<T>(lv, P->cw, V.b, V.x, P->desc.coarse_tol, P->desc.coarse_maxit, s);
+  }
   LevelVecs<T>& C = P->vecs<T>(l + 1);
   const Level& lc = *P->lv[l + 1];
   SE_TRY(cheby<T>(P, l, V.b, V.x, true, s));                    // x = M b
@@ -344,6 +346,10 @@ static int alloc_vecs(se_pmg_s* P, int l) {
   const int64_t L = P->lv[l]->L;
   for (T** q : {&V.b, &V.x, &V.r, &V.cr, &V.cd, &V.w, &V.sv}) SE_TRY(dmalloc(P->allocs, q, L));
   return SE_OK;
+}
+
+int pmg_alloc_vecs(se_pmg_s* P, int l, bool fp32) {
+  return fp32 ? alloc_vecs<float>(P, l) : alloc_vecs<double>(P, l);
 }
 
 static int pmg_build(se_pmg_s* P) {

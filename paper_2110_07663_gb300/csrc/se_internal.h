@@ -302,6 +302,25 @@ int coarse_alloc(const Level& lv, Allocs& allocs, CoarseWork* w);
 template <class T>
 int coarse_solve(const Level& lv, CoarseWork& w, const T* r_l, T* x_l, double tol, int maxit,
                  cudaStream_t s);
+// The coarse solves of several independent problems in one cooperative launch (batched solves):
+// problem m's coarsest level lv[m] with work space w[m]; its right-hand side and solution are the
+// L-vector pieces of rin / xout (FP32 when fp32) starting at loff[m] (host array).  Each problem
+// iterates to its own tolerance on its own sub-grid of blocks.
+struct CoarseGroup {
+  int n = 0, nblocks = 0;
+  bool fp32 = false;
+  void* args = nullptr;  // device array of the n problems' kernel arguments
+  int* boff = nullptr;   // device [n + 1]: first block of each problem
+  double nodes = 0.0;    // global nodes of all problems (profiling units)
+};
+int coarse_group_setup(CoarseGroup* g, const Level* const* lv, CoarseWork* const* w, int n, bool fp32,
+                       const void* rin, void* xout, const int64_t* loff, double tol, int maxit,
+                       Allocs& allocs, cudaStream_t s);
+template <class T>
+int coarse_group_solve(const CoarseGroup& g, cudaStream_t s);
+// QQ^T index map of a level from host global ids (any labels, int64) and Dirichlet bytes.
+int build_gsmap_from_gid(Level& lv, const int64_t* gid, const uint8_t* dirichlet, Allocs& allocs,
+                         cudaStream_t s);
 
 // ------------------------------------------------------------------ profiling (common.cu)
 // Profiling variant of a launch: polynomial order p (0..31) plus 32 for FP32 arithmetic, plus 64

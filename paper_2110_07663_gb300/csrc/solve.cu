@@ -250,7 +250,7 @@ __global__ void fpcg_graph_check_kernel(const double* __restrict__ scal, DevStat
 }
 
 // Adds a conditional node at the capture frontier of `cs` and moves the frontier after it.
-static int add_conditional(cudaStream_t cs, cudaGraphConditionalHandle h,
+int add_conditional(cudaStream_t cs, cudaGraphConditionalHandle h,
                            cudaGraphConditionalNodeType type, cudaGraph_t* body) {
   cudaStreamCaptureStatus st;
   cudaGraph_t g = nullptr;
@@ -272,7 +272,7 @@ static int add_conditional(cudaStream_t cs, cudaGraphConditionalHandle h,
 
 // Appends one whole FPCG solve (x0 = the content of x at launch) to graph G, independent of the
 // rest of G.  All buffers must already exist: nothing is allocated while capturing.
-static int append_fpcg_solve(cudaGraph_t G, cudaStream_t cs, se_mesh_s* m, se_pmg_s* P,
+int append_fpcg_solve(cudaGraph_t G, cudaStream_t cs, se_mesh_s* m, se_pmg_s* P,
                              const double* b, double* x, double tol, int maxit, int tol_norm,
                              int op_df) {
   const Level lv = outer_level(m, op_df);
@@ -329,13 +329,13 @@ static int append_fpcg_solve(cudaGraph_t G, cudaStream_t cs, se_mesh_s* m, se_pm
   return SE_OK;
 }
 
-static int prepare_graph_solve(se_mesh_s* m) {
+int prepare_graph_solve(se_mesh_s* m) {
   SE_TRY(ensure_solve_work(m, 0, false));
   if (!m->gstats) SE_TRY(dmalloc_bytes(m->allocs, &m->gstats, sizeof(DevStats)));
   return SE_OK;
 }
 
-static int read_graph_stats(se_mesh_s* m, cudaStream_t s, se_solve_stats* out, double tol, int maxit) {
+int read_graph_stats(se_mesh_s* m, cudaStream_t s, se_solve_stats* out, double tol, int maxit) {
   DevStats h{};
   SE_CUDA(cudaMemcpyAsync(&h, m->gstats, sizeof(h), cudaMemcpyDeviceToHost, s));
   SE_CUDA(cudaStreamSynchronize(s));
@@ -406,106 +406,3 @@ int graph_solve(se_mesh_s* m, se_pmg_s* P, const double* b, double* x, const se_
 
 }  // namespace se
 
-struct se_batch_s {
-  std::vector<se_problem> probs;
-  se_solve_opts opts;
-  cudaGraphExec_t exec = nullptr;
-};
-
-extern "C" {
-
-int se_batch_create(int n, const se_problem* probs, const se_solve_opts* opts, se_batch_t* out) {
-  SE_CHECK(n >= 1 && probs && opts && out, SE_EINVAL, "se_batch_create: bad argument");
-  SE_CHECK(opts->method == SE_FPCG, SE_EINVAL, "se_batch_create: batched solves use SE_FPCG");
-  SE_CHECK(opts->tol > 0 && opts->maxit >= 1, SE_EINVAL, "se_batch_create: bad tolerance or maxit");
-  SE_CHECK(opts->tol_norm == SE_TOL_R0 || opts->tol_norm == SE_TOL_B, SE_EINVAL,
-           "se_batch_create: bad tol_norm");
-  for (int i = 0; i < n; ++i) {
-    SE_CHECK(probs[i].mesh && probs[i].b && probs[i].x, SE_EINVAL, "se_batch_create: problem %d incomplete", i);
-    SE_CHECK(!probs[i].pmg || probs[i].pmg->mesh == probs[i].mesh, SE_EINVAL,
-             "se_batch_create: problem %d: preconditioner of another mesh", i);
-    for (int j = 0; j < i; ++j)
-      SE_CHECK(probs[j].mesh != probs[i].mesh, SE_EINVAL,
-               "se_batch_create: problems %d and %d share a mesh (its work space)", j, i);
-    SE_TRY(prepare_graph_solve(probs[i].mesh));
-    if (opts->operator_df64)
-      SE_TRY(make_df_geometry(probs[i].mesh->fine, probs[i].mesh->allocs, probs[i].mesh->stream));
-  }
-  auto* B = new se_batch_s();
-  B->probs.assign(probs, probs + n);
-  B->opts = *opts;
-  cudaGraph_t G;
-  if (cudaGraphCreate(&G, 0) != cudaSuccess) {
-    delete B;
-    set_error("cudaGraphCreate failed");
-    return SE_ECUDA;
-  }
-  cudaStream_t cs;
-  cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
-  int rc = SE_OK;
-  for (int i = 0; i < n && rc == SE_OK; ++i)
-    rc = append_fpcg_solve(G, cs, probs[i].mesh, probs[i].pmg, probs[i].b, probs[i].x, opts->tol,
-                           opts->maxit, opts->tol_norm, opts->operator_df64);
-  cudaStreamDestroy(cs);
-  if (rc == SE_OK && cudaGraphInstantiate(&B->exec, G, 0) != cudaSuccess) {
-    set_error("se_batch_create: cudaGraphInstantiate: %s", cudaGetErrorString(cudaGetLastError()));
-    rc = SE_ECUDA;
-  }
-  cudaGraphDestroy(G);
-  if (rc != SE_OK) {
-    delete B;
-    return rc;
-  }
-  *out = B;
-  return SE_OK;
-}
-
-int se_batch_run(se_batch_t B, void* stream) {
-  SE_CHECK(B, SE_EINVAL, "se_batch_run: null batch");
-  SE_CUDA(cudaGraphLaunch(B->exec, reinterpret_cast<cudaStream_t>(stream)));
-  return SE_OK;
-}
-
-int se_batch_stats(se_batch_t B, void* stream, se_solve_stats* out) {
-  SE_CHECK(B && out, SE_EINVAL, "se_batch_stats: null argument");
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  int worst = SE_OK;
-  for (size_t i = 0; i < B->probs.size(); ++i) {
-    se_solve_stats st{};
-    int rc = read_graph_stats(B->probs[i].mesh, s, &st, B->opts.tol, B->opts.maxit);
-    st.status = rc;
-    out[i] = st;
-    if (rc != SE_OK) worst = rc;
-  }
-  return worst;
-}
-
-int se_batch_destroy(se_batch_t B) {
-  if (!B) return SE_OK;
-  if (B->exec) cudaGraphExecDestroy(B->exec);
-  delete B;
-  return SE_OK;
-}
-
-int se_batch_solve(int n, const se_problem* probs, const se_solve_opts* opts, se_solve_stats* out) {
-  se_batch_t B = nullptr;
-  SE_TRY(se_batch_create(n, probs, opts, &B));
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(opts->stream);
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  cudaEventRecord(e0, s);
-  int rc = se_batch_run(B, opts->stream);
-  cudaEventRecord(e1, s);
-  if (rc == SE_OK) rc = se_batch_stats(B, opts->stream, out);
-  float ms = 0.f;
-  cudaEventSynchronize(e1);
-  cudaEventElapsedTime(&ms, e0, e1);
-  for (int i = 0; i < n; ++i) out[i].ms_total = ms;
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  se_batch_destroy(B);
-  return rc;
-}
-
-}  // extern "C"

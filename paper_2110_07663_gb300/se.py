@@ -156,6 +156,7 @@ _SIGS = {
     "se_batch_stats": ([_vp, _vp, C.POINTER(se_solve_stats)], C.c_int),
     "se_batch_destroy": ([_vp], C.c_int),
     "se_batch_solve": ([_ip, C.POINTER(se_problem), C.POINTER(se_solve_opts), C.POINTER(se_solve_stats)], C.c_int),
+    "se_batch_info": ([_vp, C.POINTER(_ip), C.POINTER(_ip)], C.c_int),
     "se_tune": ([_ip, _ip, C.POINTER(se_tile_cfg)], C.c_int),
     "se_tune_get": ([_ip, _ip, C.POINTER(se_tile_cfg)], C.c_int),
     "se_tune_set": ([C.POINTER(se_tile_cfg)], C.c_int),
@@ -478,11 +479,11 @@ def _opts(tol, maxit, stream, method=SE_FPCG, restart=20, graph_capture=1, tol_n
     return o
 
 
-def se_batch_create(problems, tol=1e-8, maxit=1000, stream=None, operator_df64=0):
+def se_batch_create(problems, tol=1e-8, maxit=1000, stream=None, operator_df64=0, tol_norm=0):
     """problems: list of (mesh, pmg or None, b, x).  Returns the batch handle."""
     arr = _problems(problems)
     h = _vp()
-    o = _opts(tol, maxit, stream)
+    o = _opts(tol, maxit, stream, tol_norm=tol_norm)
     o.operator_df64 = operator_df64
     _check(lib.se_batch_create(len(problems), arr, C.byref(o), C.byref(h)))
     return h.value
@@ -498,14 +499,21 @@ def se_batch_stats(B, n, stream=None, allow_notconv=False):
     return list(out)
 
 
+def se_batch_info(B):
+    """(groups, problems in groups) of a batch."""
+    g, k = _ip(), _ip()
+    _check(lib.se_batch_info(B, C.byref(g), C.byref(k)))
+    return g.value, k.value
+
+
 def se_batch_destroy(B):
     _check(lib.se_batch_destroy(B))
 
 
-def se_batch_solve(problems, tol=1e-8, maxit=1000, stream=None, allow_notconv=False):
+def se_batch_solve(problems, tol=1e-8, maxit=1000, stream=None, allow_notconv=False, tol_norm=0):
     arr = _problems(problems)
     out = (se_solve_stats * len(problems))()
-    _check(lib.se_batch_solve(len(problems), arr, C.byref(_opts(tol, maxit, stream)), out),
+    _check(lib.se_batch_solve(len(problems), arr, C.byref(_opts(tol, maxit, stream, tol_norm=tol_norm)), out),
            allow=(SE_ENOTCONV,) if allow_notconv else ())
     return list(out)
 
