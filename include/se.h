@@ -302,12 +302,14 @@ int se_proj_update(se_proj_t proj, const double* x, int* size, void* stream);
  * operator, QQ^T, smoother, Chebyshev update, transfers, coarse solves) is one launch over all
  * members' elements, inner products and convergence stay per problem (a converged problem keeps
  * its iterate while the others continue), and each member's Chebyshev bounds (Sec. 2.2.3) are
- * folded into its smoother.  Other problems (no preconditioner, ASM, additive cycle, df64) run
- * their own solve loop as a branch of the same graph.  Results of grouped problems agree with
+ * folded into its smoother.  Other problems (no preconditioner, ASM, additive cycle, SE_DF64
+ * V-cycle) run their own solve loop as a branch of the same graph.  Results of grouped problems agree with
  * se_solve of the same problem to within rounding (iteration counts can differ by one).  Each
  * problem needs its own mesh and preconditioner handles; pmg may be NULL (Jacobi).  b and x are
  * caller-owned device vectors of that mesh; x holds the initial guess at launch.  A group copies
- * its members' level data (geometry, factors, maps) into union arrays owned by the batch. */
+ * its members' level data (geometry, factors, maps) into union arrays owned by the batch.
+ * opts->graph_capture = 0 runs the same launches with the loops driven from the host (one read
+ * per iteration; se_batch_run then synchronises), e.g. to time each kernel with se_prof_*. */
 typedef struct se_problem {
   se_mesh_t mesh;
   se_pmg_t pmg;

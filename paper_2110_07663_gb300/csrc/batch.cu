@@ -18,7 +18,8 @@
 //    each on its own blocks to its own tolerance.
 // The solve loop is a CUDA graph: WHILE any member is active, the iteration's launches run once
 // for the whole group.  Problems that do not fit a group (no preconditioner, ASM smoother,
-// additive cycle, df64 arithmetic) run their own graph branch, as se_solve with graph_capture.
+// additive cycle, df64 V-cycle) run their own graph branch, as se_solve with graph_capture.
+// With graph_capture = 0 the same launches run with the loops driven from the host.
 #include <cmath>
 #include <map>
 #include <string>
@@ -32,37 +33,55 @@
 namespace se {
 
 // ------------------------------------------------------------------ per-member reductions
-constexpr int SEG_BLOCKS = 48;  // blocks per member of a per-member reduction
+// Block map of the per-member kernels: member m owns blocks [sboff[m], sboff[m + 1]) of a 1D grid,
+// each block a chunk of `chunk` consecutive points of the member's range [off[m], off[m + 1]), so
+// blocks are spread over the members in proportion to their sizes.
 enum { SG_RZ = 0, SG_PW, SG_ALPHA, SG_BETA, SG_RR, SG_R0, SG_SLOTS = 8 };
 
-// Fused elementwise + reduction over each member's point range [off[m], off[m + 1]): grid
-// (SEG_BLOCKS, members); per-member partial sums, summed in block order by the member's last
-// block (deterministic).  Members whose active flag is 0 are skipped entirely.
+struct SegMap {
+  const int64_t* off;   // [n + 1] point offsets
+  const int* sboff;     // [n + 1] block offsets
+  int n;
+  int64_t chunk;
+};
+
+// member of block b: the largest m with sboff[m] <= b
+__device__ __forceinline__ int seg_member(const SegMap& g, int b) {
+  int lo = 0, hi = g.n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (g.sboff[mid] <= b) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Fused elementwise + reduction per member: per-block partial sums, summed in block order by the
+// member's last block (deterministic).  Members whose active flag is 0 are skipped entirely.
 template <class Op>
-__global__ void __launch_bounds__(RED_THREADS) seg_fused_kernel(Op op, const int64_t* __restrict__ off,
-                                                                const int* __restrict__ active,
+__global__ void __launch_bounds__(RED_THREADS) seg_fused_kernel(Op op, SegMap g, const int* __restrict__ active,
                                                                 double* __restrict__ partial,
                                                                 unsigned* __restrict__ counter) {
   constexpr int K = Op::K;
-  const int m = blockIdx.y;
+  const int m = seg_member(g, blockIdx.x);
   if (active && !active[m]) return;  // uniform over the member's blocks
+  const int b0 = g.sboff[m], nb = g.sboff[m + 1] - b0, local = blockIdx.x - b0;
   double acc[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) acc[k] = 0.0;
-  const int64_t lo = off[m], hi = off[m + 1];
-  const int64_t stride = (int64_t)gridDim.x * RED_THREADS;
-  for (int64_t i = lo + (int64_t)blockIdx.x * RED_THREADS + threadIdx.x; i < hi; i += stride)
-    op.point(i, m, acc);
+  const int64_t beg = g.off[m] + (int64_t)local * g.chunk;
+  const int64_t end = min(beg + g.chunk, g.off[m + 1]);
+  for (int64_t i = beg + threadIdx.x; i < end; i += RED_THREADS) op.point(i, m, acc);
   __shared__ double sh[K][RED_THREADS / 32];
   __shared__ bool last;
   block_sum<K>(acc, sh);
-  double* part = partial + (int64_t)m * gridDim.x * K;
+  double* part = partial + (int64_t)b0 * K;
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) part[(int64_t)blockIdx.x * K + k] = acc[k];
+    for (int k = 0; k < K; ++k) part[(int64_t)local * K + k] = acc[k];
     __threadfence();
     const unsigned t = atomicAdd(counter + m, 1u);
-    last = (t == gridDim.x - 1);
+    last = (t == (unsigned)nb - 1u);
   }
   __syncthreads();
   if (!last) return;
@@ -70,7 +89,7 @@ __global__ void __launch_bounds__(RED_THREADS) seg_fused_kernel(Op op, const int
   double w[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) w[k] = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += RED_THREADS)
+  for (int b = threadIdx.x; b < nb; b += RED_THREADS)
 #pragma unroll
     for (int k = 0; k < K; ++k) w[k] += __ldcg(part + (int64_t)b * K + k);
   block_sum<K>(w, sh);
@@ -167,34 +186,34 @@ struct SegBetaOp {  // zr = (z, r); zro = (z, r_old); beta = (zr - zro) / rz; rz
   }
 };
 
-__global__ void seg_pupdate_kernel(double* __restrict__ p, const double* __restrict__ z,
-                                   const double* __restrict__ scal, const int64_t* __restrict__ off,
-                                   const int* __restrict__ active) {
-  const int m = blockIdx.y;
+__global__ void __launch_bounds__(RED_THREADS) seg_pupdate_kernel(double* __restrict__ p,
+                                                                  const double* __restrict__ z,
+                                                                  const double* __restrict__ scal, SegMap g,
+                                                                  const int* __restrict__ active) {
+  const int m = seg_member(g, blockIdx.x);
   if (!active[m]) return;
   const double beta = scal[m * SG_SLOTS + SG_BETA];
-  const int64_t hi = off[m + 1];
-  for (int64_t i = off[m] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hi;
-       i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = fma(beta, p[i], z[i]);
+  const int64_t beg = g.off[m] + (int64_t)(blockIdx.x - g.sboff[m]) * g.chunk;
+  const int64_t end = min(beg + g.chunk, g.off[m + 1]);
+  for (int64_t i = beg + threadIdx.x; i < end; i += RED_THREADS) p[i] = fma(beta, p[i], z[i]);
 }
 
 // Members' vectors to and from the union vector: piece m of u is member m's vector.
-__global__ void seg_gather_kernel(double* __restrict__ u, const double* const* __restrict__ src,
-                                  const int64_t* __restrict__ off) {
-  const int m = blockIdx.y;
-  const double* a = src[m];
-  const int64_t lo = off[m], n = off[m + 1] - lo;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    u[lo + i] = a[i];
+__global__ void __launch_bounds__(RED_THREADS) seg_gather_kernel(double* __restrict__ u,
+                                                                 const double* const* __restrict__ src, SegMap g) {
+  const int m = seg_member(g, blockIdx.x);
+  const double* a = src[m] - g.off[m];
+  const int64_t beg = g.off[m] + (int64_t)(blockIdx.x - g.sboff[m]) * g.chunk;
+  const int64_t end = min(beg + g.chunk, g.off[m + 1]);
+  for (int64_t i = beg + threadIdx.x; i < end; i += RED_THREADS) u[i] = a[i];
 }
-__global__ void seg_scatter_kernel(const double* __restrict__ u, double* const* __restrict__ dst,
-                                   const int64_t* __restrict__ off) {
-  const int m = blockIdx.y;
-  double* a = dst[m];
-  const int64_t lo = off[m], n = off[m + 1] - lo;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    a[i] = u[lo + i];
+__global__ void __launch_bounds__(RED_THREADS) seg_scatter_kernel(const double* __restrict__ u,
+                                                                  double* const* __restrict__ dst, SegMap g) {
+  const int m = seg_member(g, blockIdx.x);
+  double* a = dst[m] - g.off[m];
+  const int64_t beg = g.off[m] + (int64_t)(blockIdx.x - g.sboff[m]) * g.chunk;
+  const int64_t end = min(beg + g.chunk, g.off[m + 1]);
+  for (int64_t i = beg + threadIdx.x; i < end; i += RED_THREADS) a[i] = u[i];
 }
 
 struct SegStats {
@@ -206,7 +225,8 @@ struct SegStats {
 // After the first residual: every member's relative residual, active flag, and the loop's
 // condition (some member above tolerance).
 __global__ void seg_init_check_kernel(const double* __restrict__ scal, SegStats* st, int* active,
-                                      int n, double tol, int maxit, cudaGraphConditionalHandle hw) {
+                                      int n, double tol, int maxit, bool graph,
+                                      cudaGraphConditionalHandle hw, int* any_out) {
   int any = 0;
   for (int m = threadIdx.x; m < n; m += blockDim.x) {
     const double ref = scal[m * SG_SLOTS + SG_R0];
@@ -219,14 +239,17 @@ __global__ void seg_init_check_kernel(const double* __restrict__ scal, SegStats*
     any |= on;
   }
   any = __syncthreads_or(any);
-  if (threadIdx.x == 0) cudaGraphSetConditional(hw, any ? 1u : 0u);
+  if (threadIdx.x == 0) {
+    *any_out = any;
+    if (graph) cudaGraphSetConditional(hw, any ? 1u : 0u);
+  }
 }
 
 // After each update: the active members count the iteration and test their residual; the loop
 // (and the preconditioner of this iteration) continues while any member stays active.
 __global__ void seg_check_kernel(const double* __restrict__ scal, SegStats* st, int* active, int n,
-                                 double tol, int maxit, cudaGraphConditionalHandle hw,
-                                 cudaGraphConditionalHandle hif) {
+                                 double tol, int maxit, bool graph, cudaGraphConditionalHandle hw,
+                                 cudaGraphConditionalHandle hif, int* any_out) {
   int any = 0;
   for (int m = threadIdx.x; m < n; m += blockDim.x) {
     if (!active[m]) continue;
@@ -241,8 +264,11 @@ __global__ void seg_check_kernel(const double* __restrict__ scal, SegStats* st, 
   }
   any = __syncthreads_or(any);
   if (threadIdx.x == 0) {
-    cudaGraphSetConditional(hw, any ? 1u : 0u);
-    cudaGraphSetConditional(hif, any ? 1u : 0u);
+    *any_out = any;
+    if (graph) {
+      cudaGraphSetConditional(hw, any ? 1u : 0u);
+      cudaGraphSetConditional(hif, any ? 1u : 0u);
+    }
   }
 }
 
@@ -272,23 +298,23 @@ struct BatchGroup {
   double* scal = nullptr;         // [n][SG_SLOTS]
   int* active = nullptr;          // [n]
   SegStats* stats = nullptr;      // [n]
-  double* partial = nullptr;      // [n][SEG_BLOCKS][2]
+  int* any = nullptr;             // [1]: some member still active (host-driven loop)
+  int* hany = nullptr;            // pinned host mirror
+  int* sboff = nullptr;           // [n + 1] block offsets of the per-member kernels
+  int sblocks = 0;                // their grid
+  int64_t chunk = 0;              // points per block
+  double* partial = nullptr;      // [sblocks][2]
   unsigned* counter = nullptr;    // [n]
   CoarseGroup cg;
 };
 
-static int seg_blocks_x(const BatchGroup& G, int threads) {
-  int64_t mx = 1;
-  for (int m = 0; m < G.n; ++m) mx = std::max<int64_t>(mx, G.hoff[m + 1] - G.hoff[m]);
-  return (int)std::min<int64_t>(SEG_BLOCKS, (mx + threads - 1) / threads);
-}
+static SegMap seg_map(const BatchGroup& G) { return SegMap{G.off, G.sboff, G.n, G.chunk}; }
 
 template <class Op>
 static int run_seg(const BatchGroup& G, const Op& op, bool skip_inactive, cudaStream_t s, double bytes) {
   ProfScope prof(SE_K_KRYLOV, s, (double)G.fine.L, bytes, 2.0 * G.fine.L);
-  const dim3 grid(seg_blocks_x(G, RED_THREADS), G.n);
-  seg_fused_kernel<Op><<<grid, RED_THREADS, 0, s>>>(op, G.off, skip_inactive ? G.active : nullptr,
-                                                    G.partial, G.counter);
+  seg_fused_kernel<Op><<<G.sblocks, RED_THREADS, 0, s>>>(op, seg_map(G), skip_inactive ? G.active : nullptr,
+                                                         G.partial, G.counter);
   SE_LAUNCH_CHECK();
   return SE_OK;
 }
@@ -415,6 +441,7 @@ static int build_union_level(se_pmg_s* U, int l, const std::vector<se_pmg_s*>& P
 
 static void destroy_group(BatchGroup* G) {
   if (!G) return;
+  if (G->hany) cudaFreeHost(G->hany);
   if (G->U) {
     cudaStreamSynchronize(G->U->stream);
     G->U->allocs.release();
@@ -427,7 +454,7 @@ static void destroy_group(BatchGroup* G) {
   delete G;
 }
 
-static int build_group(BatchGroup* G, const std::vector<se_problem>& probs) {
+static int build_group(BatchGroup* G, const std::vector<se_problem>& probs, int op_df) {
   const int n = G->n = (int)G->idx.size();
   std::vector<se_pmg_s*> Pm(n);
   for (int m = 0; m < n; ++m) Pm[m] = probs[G->idx[m]].pmg;
@@ -469,8 +496,11 @@ static int build_group(BatchGroup* G, const std::vector<se_problem>& probs) {
   SE_TRY(coarse_group_setup(&G->cg, clv.data(), cwk.data(), n, fp32, rin, xout, coff.data(),
                             d.coarse_tol, d.coarse_maxit, U->allocs, s));
   U->cgroup = &G->cg;
-  // outer solver state
+  // outer solver state: level 0 in FP64, or in double-float arithmetic (operator_df64; the df64
+  // geometry is made for the outer operator only, the V-cycle keeps its own arithmetic)
+  if (op_df) SE_TRY(make_df_geometry(U->owned[0], U->allocs, s));
   G->fine = U->owned[0];
+  G->fine.df = op_df != 0;
   const int64_t L = G->fine.L;
   Allocs& A = U->allocs;
   for (double** v : {&G->b, &G->x, &G->r, &G->r_old, &G->z, &G->p, &G->w}) SE_TRY(dmalloc(A, v, (size_t)L));
@@ -488,8 +518,24 @@ static int build_group(BatchGroup* G, const std::vector<se_problem>& probs) {
   SE_TRY(dmalloc(A, &G->scal, (size_t)n * SG_SLOTS));
   SE_TRY(dmalloc(A, &G->active, (size_t)n));
   SE_TRY(dmalloc_bytes(A, reinterpret_cast<void**>(&G->stats), (size_t)n * sizeof(SegStats)));
-  SE_TRY(dmalloc(A, &G->partial, (size_t)n * SEG_BLOCKS * 2));
+  {  // block map: about 8 blocks per SM over the whole union, chunks of whole warps
+    int dev = 0, sms = 0;
+    SE_CUDA(cudaGetDevice(&dev));
+    SE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t target = 8 * (int64_t)sms;
+    int64_t chunk = (L + target - 1) / target;
+    chunk = std::max<int64_t>(4 * RED_THREADS, (chunk + RED_THREADS - 1) / RED_THREADS * RED_THREADS);
+    std::vector<int> sb(n + 1, 0);
+    for (int m = 0; m < n; ++m) sb[m + 1] = sb[m] + (int)((G->hoff[m + 1] - G->hoff[m] + chunk - 1) / chunk);
+    G->chunk = chunk;
+    G->sblocks = sb[n];
+    SE_TRY(dmalloc(A, &G->sboff, (size_t)n + 1));
+    SE_CUDA(cudaMemcpyAsync(G->sboff, sb.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  }
+  SE_TRY(dmalloc(A, &G->partial, (size_t)G->sblocks * 2));
   SE_TRY(dmalloc(A, &G->counter, (size_t)n));
+  SE_TRY(dmalloc(A, &G->any, 1));
+  SE_CUDA(cudaMallocHost(&G->hany, sizeof(int)));
   SE_CUDA(cudaMemcpyAsync(G->off, G->hoff.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   SE_CUDA(cudaMemcpyAsync(G->bsrc, bs.data(), n * sizeof(double*), cudaMemcpyHostToDevice, s));
   SE_CUDA(cudaMemcpyAsync(G->xdst, xs.data(), n * sizeof(double*), cudaMemcpyHostToDevice, s));
@@ -505,15 +551,15 @@ static int append_group_solve(cudaGraph_t Gr, cudaStream_t cs, BatchGroup* G, do
                               int tol_norm) {
   const Level& lv = G->fine;
   const int64_t L = lv.L;
-  const dim3 vgrid(seg_blocks_x(*G, 256), G->n);
   cudaGraphConditionalHandle hw, hif;
   SE_CUDA(cudaGraphConditionalHandleCreate(&hw, Gr, 0, 0));
   SE_CUDA(cudaStreamBeginCaptureToGraph(cs, Gr, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   int rc = SE_OK;
   cudaGraph_t wbody = nullptr, ifbody = nullptr;
   do {
-    seg_gather_kernel<<<vgrid, 256, 0, cs>>>(G->b, G->bsrc, G->off);
-    seg_gather_kernel<<<vgrid, 256, 0, cs>>>(G->x, const_cast<const double* const*>(G->xdst), G->off);
+    seg_gather_kernel<<<G->sblocks, RED_THREADS, 0, cs>>>(G->b, G->bsrc, seg_map(*G));
+    seg_gather_kernel<<<G->sblocks, RED_THREADS, 0, cs>>>(G->x, const_cast<const double* const*>(G->xdst),
+                                                          seg_map(*G));
     if ((rc = ax_apply<double>(lv, G->x, G->w, cs)) != SE_OK) break;
     if ((rc = axpby<double>(1.0, G->b, -1.0, G->w, G->r, L, cs)) != SE_OK) break;  // r = b - A x
     if ((rc = pmg_apply(G->U, G->r, G->z, cs)) != SE_OK) break;                    // z = M r
@@ -526,9 +572,10 @@ static int append_group_solve(cudaGraph_t Gr, cudaStream_t cs, BatchGroup* G, do
       rc = SE_ECUDA;
       break;
     }
-    seg_init_check_kernel<<<1, 256, 0, cs>>>(G->scal, G->stats, G->active, G->n, tol, maxit, hw);
+    seg_init_check_kernel<<<1, 256, 0, cs>>>(G->scal, G->stats, G->active, G->n, tol, maxit, true, hw,
+                                             G->any);
     if ((rc = add_conditional(cs, hw, cudaGraphCondTypeWhile, &wbody)) != SE_OK) break;
-    seg_scatter_kernel<<<vgrid, 256, 0, cs>>>(G->x, G->xdst, G->off);  // after the loop
+    seg_scatter_kernel<<<G->sblocks, RED_THREADS, 0, cs>>>(G->x, G->xdst, seg_map(*G));  // after the loop
   } while (0);
   cudaGraph_t out = nullptr;
   cudaError_t ec = cudaStreamEndCapture(cs, &out);
@@ -543,7 +590,8 @@ static int append_group_solve(cudaGraph_t Gr, cudaStream_t cs, BatchGroup* G, do
     if ((rc = run_seg(*G, SegUpdateOp{G->x, G->p, G->r, G->w, G->r_old, lv.pflag, G->scal}, true, cs,
                       57.0 * L)) != SE_OK)
       break;
-    seg_check_kernel<<<1, 256, 0, cs>>>(G->scal, G->stats, G->active, G->n, tol, maxit, hw, hif);
+    seg_check_kernel<<<1, 256, 0, cs>>>(G->scal, G->stats, G->active, G->n, tol, maxit, true, hw, hif,
+                                        G->any);
     rc = add_conditional(cs, hif, cudaGraphCondTypeIf, &ifbody);
   } while (0);
   ec = cudaStreamEndCapture(cs, &out);
@@ -557,7 +605,7 @@ static int append_group_solve(cudaGraph_t Gr, cudaStream_t cs, BatchGroup* G, do
       break;
     {
       ProfScope prof(SE_K_KRYLOV, cs, (double)L, 24.0 * L, 2.0 * L);
-      seg_pupdate_kernel<<<vgrid, 256, 0, cs>>>(G->p, G->z, G->scal, G->off, G->active);
+      seg_pupdate_kernel<<<G->sblocks, RED_THREADS, 0, cs>>>(G->p, G->z, G->scal, seg_map(*G), G->active);
       if (cudaGetLastError() != cudaSuccess) {
         set_error("se_batch: launch failed");
         rc = SE_ECUDA;
@@ -570,9 +618,61 @@ static int append_group_solve(cudaGraph_t Gr, cudaStream_t cs, BatchGroup* G, do
   return SE_OK;
 }
 
+// The same solve with the loop driven from the host (one read of the "any member active" flag per
+// iteration): the launches of the graph, each one visible to the library's event profiler.
+static int run_group_host(BatchGroup* G, double tol, int maxit, int tol_norm, cudaStream_t s) {
+  const Level& lv = G->fine;
+  const int64_t L = lv.L;
+  cudaGraphConditionalHandle none{};
+  auto any_left = [&](int* out) {
+    if (cudaMemcpyAsync(G->hany, G->any, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      set_error("se_batch: %s", cudaGetErrorString(cudaGetLastError()));
+      return SE_ECUDA;
+    }
+    *out = *G->hany;
+    return SE_OK;
+  };
+  seg_gather_kernel<<<G->sblocks, RED_THREADS, 0, s>>>(G->b, G->bsrc, seg_map(*G));
+  seg_gather_kernel<<<G->sblocks, RED_THREADS, 0, s>>>(G->x, const_cast<const double* const*>(G->xdst),
+                                                       seg_map(*G));
+  SE_LAUNCH_CHECK();
+  SE_TRY(ax_apply<double>(lv, G->x, G->w, s));
+  SE_TRY(axpby<double>(1.0, G->b, -1.0, G->w, G->r, L, s));
+  SE_TRY(pmg_apply(G->U, G->r, G->z, s));
+  SE_TRY(run_seg(*G, SegInitOp{G->r, G->z, lv.pflag, G->scal}, false, s, 17.0 * L));
+  if (tol_norm == SE_TOL_B) SE_TRY(run_seg(*G, SegNormOp{G->b, lv.pflag, G->scal}, false, s, 9.0 * L));
+  SE_CUDA(cudaMemcpyAsync(G->p, G->z, L * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  seg_init_check_kernel<<<1, 256, 0, s>>>(G->scal, G->stats, G->active, G->n, tol, maxit, false, none,
+                                          G->any);
+  SE_LAUNCH_CHECK();
+  int go = 0;
+  SE_TRY(any_left(&go));
+  while (go) {
+    SE_TRY(ax_apply<double>(lv, G->p, G->w, s));
+    SE_TRY(run_seg(*G, SegAlphaOp{G->p, G->w, lv.pflag, G->scal}, true, s, 17.0 * L));
+    SE_TRY(run_seg(*G, SegUpdateOp{G->x, G->p, G->r, G->w, G->r_old, lv.pflag, G->scal}, true, s, 57.0 * L));
+    seg_check_kernel<<<1, 256, 0, s>>>(G->scal, G->stats, G->active, G->n, tol, maxit, false, none, none,
+                                       G->any);
+    SE_LAUNCH_CHECK();
+    SE_TRY(any_left(&go));
+    if (!go) break;
+    SE_TRY(pmg_apply(G->U, G->r, G->z, s));
+    SE_TRY(run_seg(*G, SegBetaOp{G->z, G->r, G->r_old, lv.pflag, G->scal}, true, s, 25.0 * L));
+    {
+      ProfScope prof(SE_K_KRYLOV, s, (double)L, 24.0 * L, 2.0 * L);
+      seg_pupdate_kernel<<<G->sblocks, RED_THREADS, 0, s>>>(G->p, G->z, G->scal, seg_map(*G), G->active);
+      SE_LAUNCH_CHECK();
+    }
+  }
+  seg_scatter_kernel<<<G->sblocks, RED_THREADS, 0, s>>>(G->x, G->xdst, seg_map(*G));
+  SE_LAUNCH_CHECK();
+  return SE_OK;
+}
+
 // Problems that share a group: same preconditioner configuration, one of the supported kinds.
-static bool groupable(const se_problem& q, const se_solve_opts& o) {
-  if (!q.pmg || o.operator_df64) return false;
+static bool groupable(const se_problem& q, const se_solve_opts&) {
+  if (!q.pmg) return false;
   const se_pmg_desc& d = q.pmg->desc;
   return (d.precision == SE_FP64 || d.precision == SE_FP32) && d.cycle == SE_CYCLE_MULTIPLICATIVE &&
          (d.smoother == SE_SMOOTH_RAS || d.smoother == SE_SMOOTH_JACOBI);
@@ -600,6 +700,8 @@ struct se_batch_s {
   std::vector<BatchGroup*> groups;
   std::vector<int> alone;          // problems with their own graph branch
   std::vector<int> group_of, slot;  // per problem: group index (-1: alone) and member slot
+  bool host = false;                // graph_capture == 0: loops driven from the host
+  std::vector<se_solve_stats> alone_stats;
 };
 
 static void batch_free(se_batch_s* B) {
@@ -655,13 +757,23 @@ int se_batch_create(int n, const se_problem* probs, const se_solve_opts* opts, s
     auto* G = new BatchGroup();
     G->idx = members[g];
     B->groups.push_back(G);
-    rc = build_group(G, B->probs);
+    rc = build_group(G, B->probs, opts->operator_df64);
   }
   for (int i : B->alone) {
     if (rc != SE_OK) break;
     rc = prepare_graph_solve(probs[i].mesh);
     if (rc == SE_OK && opts->operator_df64)
       rc = make_df_geometry(probs[i].mesh->fine, probs[i].mesh->allocs, probs[i].mesh->stream);
+  }
+  B->host = opts->graph_capture == 0;
+  B->alone_stats.assign(n, se_solve_stats{});
+  if (B->host) {
+    if (rc != SE_OK) {
+      batch_free(B);
+      return rc;
+    }
+    *out = B;
+    return SE_OK;
   }
   cudaGraph_t Gr = nullptr;
   if (rc == SE_OK && cudaGraphCreate(&Gr, 0) != cudaSuccess) {
@@ -699,7 +811,21 @@ int se_batch_create(int n, const se_problem* probs, const se_solve_opts* opts, s
 
 int se_batch_run(se_batch_t B, void* stream) {
   SE_CHECK(B, SE_EINVAL, "se_batch_run: null batch");
-  SE_CUDA(cudaGraphLaunch(B->exec, reinterpret_cast<cudaStream_t>(stream)));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!B->host) {
+    SE_CUDA(cudaGraphLaunch(B->exec, s));
+    return SE_OK;
+  }
+  for (BatchGroup* G : B->groups)
+    SE_TRY(run_group_host(G, B->opts.tol, B->opts.maxit, B->opts.tol_norm, s));
+  for (int i : B->alone) {  // their own host-driven solve loops
+    se_solve_opts o = B->opts;
+    o.graph_capture = 0;
+    o.stream = s;
+    const int rc = se_solve(B->probs[i].mesh, B->probs[i].pmg, B->probs[i].b, B->probs[i].x, &o,
+                            &B->alone_stats[i]);
+    if (rc != SE_OK && rc != SE_ENOTCONV) return rc;
+  }
   return SE_OK;
 }
 
@@ -730,6 +856,9 @@ int se_batch_stats(se_batch_t B, void* stream, se_solve_stats* out) {
                   B->opts.maxit, q.rel);
         rc = SE_ENOTCONV;
       }
+    } else if (B->host) {
+      st = B->alone_stats[i];
+      rc = st.status;
     } else {
       rc = read_graph_stats(B->probs[i].mesh, s, &st, tol, B->opts.maxit);
     }

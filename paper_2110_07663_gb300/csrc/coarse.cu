@@ -512,15 +512,27 @@ static int coarse_group_setup_t(CoarseGroup* g, const Level* const* lv, CoarseWo
   SE_CHECK(per_sm >= 1, SE_ECUDA, "grouped coarse solver kernel cannot be resident");
   const int cap = sms * per_sm;
   SE_CHECK(n <= cap, SE_EINVAL, "grouped coarse solve: %d problems above the %d resident blocks", n, cap);
-  // blocks per problem: about 16 nodes per thread, at most the problem's own work-space size;
-  // the total must be co-resident (cooperative launch)
+  // blocks per problem: one node per thread where the co-resident capacity allows (the FP64
+  // work of an iteration needs every SM), at most the problem's own work-space size; otherwise
+  // proportional to the problem's nodes, at least one each (cooperative launch: the total must
+  // be co-resident)
   std::vector<int> nb(n);
-  int total = 0;
+  int64_t want_total = 0;
   for (int m = 0; m < n; ++m) {
-    const int64_t want = (lv[m]->n_global + 16 * CG_THREADS - 1) / (16 * CG_THREADS);
+    const int64_t want = (lv[m]->n_global + CG_THREADS - 1) / CG_THREADS;
     nb[m] = (int)std::max<int64_t>(1, std::min<int64_t>(want, w[m]->nblocks));
-    total += nb[m];
+    want_total += nb[m];
   }
+  if (want_total > cap) {
+    int64_t nodes_total = 0;
+    for (int m = 0; m < n; ++m) nodes_total += lv[m]->n_global;
+    for (int m = 0; m < n; ++m) {
+      const int64_t share = (int64_t)((double)(cap - n) * (double)lv[m]->n_global / (double)nodes_total);
+      nb[m] = (int)std::max<int64_t>(1, std::min<int64_t>(nb[m], 1 + share));
+    }
+  }
+  int total = 0;
+  for (int m = 0; m < n; ++m) total += nb[m];
   while (total > cap) {
     int big = 0;
     for (int m = 1; m < n; ++m)

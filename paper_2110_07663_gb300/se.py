@@ -479,11 +479,12 @@ def _opts(tol, maxit, stream, method=SE_FPCG, restart=20, graph_capture=1, tol_n
     return o
 
 
-def se_batch_create(problems, tol=1e-8, maxit=1000, stream=None, operator_df64=0, tol_norm=0):
+def se_batch_create(problems, tol=1e-8, maxit=1000, stream=None, operator_df64=0, tol_norm=0,
+                    graph_capture=1):
     """problems: list of (mesh, pmg or None, b, x).  Returns the batch handle."""
     arr = _problems(problems)
     h = _vp()
-    o = _opts(tol, maxit, stream, tol_norm=tol_norm)
+    o = _opts(tol, maxit, stream, tol_norm=tol_norm, graph_capture=graph_capture)
     o.operator_df64 = operator_df64
     _check(lib.se_batch_create(len(problems), arr, C.byref(o), C.byref(h)))
     return h.value

@@ -117,26 +117,34 @@ def test_df64_solve_parity(smoother, method):
         c.close()
 
 
-def test_df64_operator_in_a_batch_equals_each_solve_alone():
-    """Batched graph solves with the df64 outer operator: each problem bit for bit as its own graph
-    solve with the same options, and within the tolerance of the FP64-operator solve."""
+def test_df64_operator_in_a_batch_matches_each_solve_alone():
+    """Batched solves with the df64 outer operator (problems grouped by preconditioner
+    configuration, the group's outer operator in df64): each problem meets the tolerance and
+    agrees with its own df64-operator graph solve and with the FP64-operator solve to within
+    rounding (iterations within one)."""
     from tests.gpu_common import gpu
     torch, se = gpu()
     probs = []
     try:
-        for nel, p, sched, seed in [((3, 3, 2), 5, (5, 3, 1), 1), ((2, 3, 3), 7, (7, 3, 1), 2)]:
+        for nel, p, sched, seed in [((3, 3, 2), 5, (5, 3, 1), 1), ((2, 3, 3), 7, (7, 3, 1), 2),
+                                    ((3, 2, 3), 7, (7, 3, 1), 3)]:
             c = Case(nel, p, seed=seed)
             P = se.se_pmg_setup(c.m, se.pmg_desc(sched, se.SE_SMOOTH_RAS, 2, precision=se.SE_FP32))
             probs.append((c, P, gpu_rhs(c), c.empty().zero_()))
         B = se.se_batch_create([(c.m, P, b, x) for c, P, b, x in probs], tol=1e-8, maxit=200,
                                operator_df64=1)
-        se.se_batch_run(B)
-        torch.cuda.synchronize()
-        se.se_batch_destroy(B)
-        for c, P, b, x in probs:
+        try:
+            assert se.se_batch_info(B) == (2, 3)
+            se.se_batch_run(B)
+            stats = se.se_batch_stats(B, len(probs))
+        finally:
+            se.se_batch_destroy(B)
+        for (c, P, b, x), sb in zip(probs, stats):
+            assert sb.rel_residual <= 1e-8
             xa = c.empty().zero_()
             st = se.se_solve(c.m, P, b, xa, tol=1e-8, graph_capture=1, operator_df64=1)
-            assert torch.equal(xa, x)
+            assert abs(sb.iterations - st.iterations) <= 1
+            assert rel_err(c.to_np(x), c.to_np(xa)) <= 1e-6
             x64 = c.empty().zero_()
             st64 = se.se_solve(c.m, P, b, x64, tol=1e-8)
             assert abs(st.iterations - st64.iterations) <= 1
