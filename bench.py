@@ -725,6 +725,65 @@ def run_serve(args):
     print(json.dumps(out))
 
 
+def run_setup_profile(args):
+    """Set-up cost of a new served mesh (the part of serving that does not overlap with solves):
+    mesh creation, the FP32-V-cycle Cheby-RAS(2) preconditioner set-up with FP64 and with df64
+    Arnoldi rounds (per-kernel-class times of the set-up from the library's event profiler), the
+    first graph solve (capture included) and a steady graph solve, for meshes of the served size
+    range."""
+    import torch
+    from paper_2110_07663_gb300 import se
+    import workloads as wl
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    cases = [((8, 8, 8), 5), ((24, 24, 24), 7), ((40, 40, 40), 9)]
+    out = []
+    for nel, p in cases:
+        rec = {"nel": list(nel), "p": p}
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m = se.se_mesh_create(nel, p, perturb_frac=0.05, seed=1, deform_amp=wl.DEFORM_AMP)
+        torch.cuda.synchronize()
+        rec["mesh_ms"] = round((time.perf_counter() - t0) * 1e3, 2)
+        info = se.se_mesh_get_info(m)
+        rec["n_dof"] = info.n_dof
+        b = torch.empty(info.L, dtype=torch.float64, device="cuda")
+        for arn in (0, 1):
+            desc = se.pmg_desc(SERVE_SCHEDULES[p], se.SE_SMOOTH_RAS, 2, precision=se.SE_FP32, arnoldi_df64=arn)
+            se.se_prof_reset()
+            se.se_prof_enable(True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            P = se.se_pmg_setup(m, desc)
+            torch.cuda.synchronize()
+            wall = (time.perf_counter() - t0) * 1e3
+            se.se_prof_enable(False)
+            prof = {se.KERNEL_NAMES[k]: round(se.se_prof_query(k)["ms"], 2) for k in range(se.SE_K_COUNT)
+                    if se.se_prof_query(k)["launches"]}
+            key = "pmg_df64_arnoldi" if arn else "pmg_fp64_arnoldi"
+            rec[key] = {"wall_ms": round(wall, 2), "kernels_ms": prof}
+            if arn:
+                xyz = torch.empty(3 * info.L, dtype=torch.float64, device="cuda")
+                se.se_mesh_nodes(m, xyz)
+                X = xyz.view(3, -1)
+                f = 3 * math.pi ** 2 * torch.sin(math.pi * X[0]) * torch.sin(math.pi * X[1]) * torch.sin(math.pi * X[2])
+                se.se_mesh_rhs(m, f.contiguous(), b)
+                del xyz, X, f
+                x = torch.zeros_like(b)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st = se.se_solve(m, P, b, x, tol=1e-8, graph_capture=1, stream=stream)
+                rec["first_solve_ms"] = round((time.perf_counter() - t0) * 1e3, 2)
+                x.zero_()
+                st = se.se_solve(m, P, b, x, tol=1e-8, graph_capture=1, stream=stream)
+                rec["steady_solve_ms"] = round(st.ms_total, 2)
+                rec["iterations"] = st.iterations
+            se.se_pmg_destroy(P)
+        se.se_mesh_destroy(m)
+        out.append(rec)
+    print(json.dumps({"metric": "new-mesh set-up of served requests (ms)", "cases": out}))
+
+
 def run_precision_study(args):
     """FP32 V-cycle / FP64 Krylov against the all-FP64 method on the 4^3-element box at p = 7 and
     p = 9: iterations, solve time, and the error of each solution against the FP64 oracle
@@ -1061,6 +1120,8 @@ def main():
                     help="skip the Cheby-RAS(2) FP64 / FP32-V-cycle record of the headline line")
     ap.add_argument("--oracle-full", action="store_true",
                     help="with --impl reference: time the oracle once on the whole workload")
+    ap.add_argument("--setup-profile", action="store_true",
+                    help="time the set-up of new served meshes (mesh, preconditioner, first solve)")
     ap.add_argument("--peaks", action="store_true",
                     help="measure the FP64 / FP32 / packed-FP32 FMA roofs of this GPU and exit")
     ap.add_argument("--cpu-timeout", type=float, default=240.0)
@@ -1104,6 +1165,8 @@ def main():
         run_reference(args)
     elif args.peaks:
         run_peaks(args)
+    elif args.setup_profile:
+        run_setup_profile(args)
     elif args.batch:
         run_batch(args)
     elif args.serve:
