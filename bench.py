@@ -138,17 +138,27 @@ def alu_peak_tflops(kind, sm_max_mhz, sms=N_SMS_NOMINAL):
     return sms * (128 if kind == "f32" else FP64_FMA_PER_CLK_PER_SM) * 2 * sm_max_mhz * 1e6 / 1e12
 
 
-def dram_traffic(kernel, variant):
-    """DRAM bytes per launch from the committed ncu capture summary, if one matches."""
+def _profile_entry(kernel, variant):
     try:
         with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
             tab = json.load(f)
     except OSError:
-        return None, None
-    e = tab.get(f"{kernel}:{variant}")
+        return None
+    return tab.get(f"{kernel}:{variant}")
+
+
+def dram_traffic(kernel, variant):
+    """DRAM bytes per launch from the committed ncu capture summary, if one matches."""
+    e = _profile_entry(kernel, variant)
     if not e:
         return None, None
     return e["bytes_per_launch_bench_workload"], e["source"]
+
+
+def pipe_busy(kernel, variant):
+    """Executed-instruction pipe utilisation of the kernel from its committed ncu capture."""
+    e = _profile_entry(kernel, variant)
+    return e.get("pipe_busy_ncu") if e else None
 
 
 def roofline(kernel, variant, d, pk, pk_kind):
@@ -171,6 +181,7 @@ def roofline(kernel, variant, d, pk, pk_kind):
                 "unit": "TFLOP/s", "frac": round(achieved / alu, 4), "traffic": traffic,
                 "algorithmic_bytes_per_launch": d["bytes"] / n, "flops_per_launch": d["flops"] / n,
                 "avg_launch_ms": round(avg_s * 1e3, 4), "traffic_source": src,
+                "pipe_busy_ncu": pipe_busy(kernel, variant),
                 "peak_source": (f"derived: {sms} SMs x 128 FP32 instr/clk x {sm_max:.0f} MHz / "
                                 f"{DF64_INSTR_PER_FLOP} FP32 instr per df64 flop") if kind == "df64" else
                                (f"derived: {sms} SMs x {128 if fp32 else 2} {'FP32' if fp32 else 'FP64'} "
@@ -297,7 +308,7 @@ def run_peaks(args):
     with ClockSampler(0) as clk:
         meas, sms = {}, None
         for _ in range(3):
-            for kind, name in ((0, "f64"), (1, "f32"), (2, "f32x2")):
+            for kind, name in ((0, "f64"), (1, "f32"), (2, "f32x2"), (3, "tf32_mma_sync")):
                 t, sms = se.se_prof_fma_peak(kind, stream)
                 meas[name] = max(meas.get(name, 0.0), round(t, 3))
     pk, _ = peaks()
@@ -306,6 +317,7 @@ def run_peaks(args):
     print(json.dumps({"measured_fma_tflops": meas, "sms": sms, "derived_tflops": derived,
                       "derived_from": f"{sms} SMs x FMA lanes/clk (FP64 2, FP32 128) x 2 flop x "
                                       f"{sm_max:.0f} MHz",
+                      "tf32_mma_sync_over_f32x2": round(meas["tf32_mma_sync"] / meas["f32x2"], 3),
                       "frac_of_derived": {"f64": round(meas["f64"] / derived["f64"], 4),
                                           "f32": round(meas["f32"] / derived["f32"], 4),
                                           "f32x2": round(meas["f32x2"] / derived["f32"], 4)},
@@ -399,7 +411,9 @@ def run_gpu(args):
     # bracketed by CUDA events on its stream; gives the per-kernel times and the roofline
     step(graph=0)
     torch.cuda.synchronize()
+    se.se_pmg_coarse_stats(P, reset=True)
     host_loop_ms, prof, variants = profiled_variants(se, lambda: step(graph=0), args.steps, stream)
+    coarse_solves, coarse_iters = se.se_pmg_coarse_stats(P)
     # our kernels per timed step: those of the profiled pass plus the graph's own control
     # kernels (one at the start, one convergence test per iteration)
     launches = sum(v["launches"] for v in prof.values()) + args.steps * (1 + iters)
@@ -440,6 +454,24 @@ def run_gpu(args):
     (dom, dvar), d = max(variants.items(), key=lambda kv: kv[1]["ms"])
     roof = roofline(dom, dvar, d, pk, pk_kind)
     kernels = kernel_table(variants, args.steps, pk, pk_kind)
+    coarse = None
+    if coarse_solves and "coarse_pcg" in prof and prof["coarse_pcg"]["launches"]:
+        # the coarse Jacobi-PCG: latency-bound (one grid synchronisation per iteration); its FP64
+        # work per iteration and node: 27-point product 54 flops, preconditioner 1, six vector
+        # updates 12, three inner products 6, direction updates 4 -> 77 flops
+        n_c = se.se_pmg_level_info(P, len(wk["schedule"]) - 1).n_global
+        ms_c = prof["coarse_pcg"]["ms"]
+        us_it = ms_c * 1e3 / max(coarse_iters, 1)
+        tf = 77.0 * n_c * coarse_iters / (ms_c * 1e-3) / 1e12
+        fp64_peak = alu_peak_tflops("f64", pk.get("sm_max_mhz", 2070.0), pk["sms"])
+        coarse = {"solves_per_step": coarse_solves / args.steps,
+                  "iterations_per_solve": round(coarse_iters / coarse_solves, 2),
+                  "us_per_iteration": round(us_it, 2), "nodes": n_c,
+                  "fp64_tflops": round(tf, 4), "fp64_peak_tflops": round(fp64_peak, 4),
+                  "roof_frac": round(tf / fp64_peak, 4),
+                  "bound": "latency (one grid synchronisation per iteration)"}
+        kernels["coarse_pcg p=0 f64"]["roof_frac"] = coarse["roof_frac"]
+        kernels["coarse_pcg p=0 f64"]["bound"] = "alu"
     schwarz = None
     if not args.no_schwarz:
         schwarz = schwarz_record(se, m, b, x, stream, wk, pk, pk_kind, op_df, args.steps)
@@ -473,6 +505,7 @@ def run_gpu(args):
         "roofline": roof,
         "kernels": kernels,
         "clocks": clk.summary(),
+        "coarse": coarse,
         "schwarz": schwarz,
     }
     if rank == 0 and not args.no_cpu_baseline and world == 1:

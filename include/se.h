@@ -226,6 +226,11 @@ int se_pmg_prolong(se_pmg_t pmg, int lvl, const double* ec, double* ef, void* st
  * launch, pipelined form of the iteration: one grid synchronisation per iteration).  *iters
  * receives the iteration count (synchronises). */
 int se_pmg_coarse_solve(se_pmg_t pmg, const double* r, double* x, int* iters, void* stream);
+/* Coarse solves of this preconditioner since the last reset (every launch of its coarsest level,
+ * inside V-cycles or by se_pmg_coarse_solve) and their total Jacobi-PCG iterations; reset != 0
+ * starts a new count.  Synchronises the preconditioner's stream (the caller synchronises other
+ * streams its solves ran on). */
+int se_pmg_coarse_stats(se_pmg_t pmg, int reset, int64_t* solves, int64_t* iterations);
 /* Same coarse solve as se_pmg_coarse_solve, for callers that must not allocate device memory
  * during the call: code running after its memory pool is fixed (an application or framework
  * that reserved the device memory up front and owns every later allocation), or a steady-state
@@ -465,7 +470,8 @@ int se_prof_query_variant(int kind, int variant, double* ms_total, int64_t* laun
 
 /* ALU roof of this GPU for the roofline of arithmetic-bound kernels (measurement only; the paper
  * has no counterpart): fused multiply-add throughput with independent chains on every SM,
- * kind 0 = FP64, 1 = FP32, 2 = FP32 in packed pairs (fma.rn.f32x2).  *tflops receives the best
+ * kind 0 = FP64, 1 = FP32, 2 = FP32 in packed pairs (fma.rn.f32x2), 3 = TF32 tensor-core
+ * multiply-adds with FP32 accumulation (warp-level mma.sync m16n8k8).  *tflops receives the best
  * of three timed launches (2 flops per FMA), *sms (may be NULL) the device's SM count.  The
  * launches go to `stream` (NULL: the legacy default stream); the call synchronises. */
 int se_prof_fma_peak(int kind, double* tflops, int* sms, void* stream);

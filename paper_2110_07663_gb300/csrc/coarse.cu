@@ -252,6 +252,7 @@ struct CoarseArgs {
   double *x, *r, *u, *p, *q, *s, *z, *w0, *w1, *part;
   unsigned* count;
   int* status;
+  unsigned long long* totals;  // iterations and solves, accumulated (null: not counted)
   double tol;
   int maxit;
   long long timeout_ns;
@@ -367,7 +368,13 @@ __device__ __forceinline__ void coarse_pcg_run(const CoarseArgs<T>& c, unsigned 
   if (ok) {
     for (int l = t0; l < c.L; l += stride) c.xout[l] = (T)c.x[c.l2g[l]];
   }
-  if (blk == 0 && threadIdx.x == 0) c.status[1] = it;
+  if (blk == 0 && threadIdx.x == 0) {
+    c.status[1] = it;
+    if (c.totals) {
+      atomicAdd(c.totals, (unsigned long long)it);
+      atomicAdd(c.totals + 1, 1ULL);
+    }
+  }
 }
 
 template <class T>
@@ -427,6 +434,8 @@ int coarse_alloc(const Level& lv, Allocs& allocs, CoarseWork* w) {
   SE_TRY(dmalloc(allocs, &w->status, 2));
   SE_CUDA(cudaMemset(w->bar, 0, 2 * sizeof(unsigned)));
   SE_CUDA(cudaMemset(w->status, 0, 2 * sizeof(int)));
+  SE_TRY(dmalloc(allocs, &w->totals, 2));
+  SE_CUDA(cudaMemset(w->totals, 0, 2 * sizeof(unsigned long long)));
   return SE_OK;
 }
 
@@ -456,6 +465,7 @@ int coarse_solve(const Level& lv, CoarseWork& w, const T* r_l, T* x_l, double to
   a.part = w.partial;
   a.count = w.bar;
   a.status = w.status;
+  a.totals = w.totals;
   a.tol = tol;
   a.maxit = maxit;
   a.timeout_ns = BARRIER_TIMEOUT_NS;
@@ -495,6 +505,7 @@ static CoarseArgs<T> coarse_args(const Level& lv, const CoarseWork& w, const T* 
   a.part = w.partial;
   a.count = w.bar;
   a.status = w.status;
+  a.totals = w.totals;
   a.tol = tol;
   a.maxit = maxit;
   a.timeout_ns = BARRIER_TIMEOUT_NS;

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "pmg_internal.h"
 
@@ -295,12 +296,18 @@ static void box_lengths(se_mesh_s* m) {
   const double amp = m->desc.deform_amp;
   const int64_t E = (int64_t)nx * ny * nz;
   m->box_len.assign(3 * E, 0.0);
-  auto corner = [&](int a, int b, int c, double* x) {
-    const int64_t v = a + (int64_t)(nx + 1) * (b + (int64_t)(ny + 1) * c);
+  // every lattice vertex mapped once (a vertex is a corner of up to 8 elements)
+  const int64_t nv = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+  std::vector<double> mapped(3 * nv);
+  for (int64_t v = 0; v < nv; ++v) {
     const double* V = &m->verts[3 * v];
     const double sm = std::sin(2.0 * M_PI * V[0]) * std::sin(2.0 * M_PI * V[1]) *
                       std::sin(2.0 * M_PI * V[2]);
-    for (int q = 0; q < 3; ++q) x[q] = V[q] + amp * sm;
+    for (int q = 0; q < 3; ++q) mapped[3 * v + q] = V[q] + amp * sm;
+  }
+  auto corner = [&](int a, int b, int c, double* x) {
+    const int64_t v = a + (int64_t)(nx + 1) * (b + (int64_t)(ny + 1) * c);
+    for (int q = 0; q < 3; ++q) x[q] = mapped[3 * v + q];
   };
   for (int64_t e = 0; e < E; ++e) {
     const int ex = (int)(e % nx), ey = (int)((e / nx) % ny), ez = (int)(e / ((int64_t)nx * ny));

@@ -511,6 +511,17 @@ int se_pmg_destroy(se_pmg_t P) {
   return SE_OK;
 }
 
+int se_pmg_coarse_stats(se_pmg_t P, int reset, int64_t* solves, int64_t* iterations) {
+  SE_CHECK(P && P->cw.totals, SE_EINVAL, "se_pmg_coarse_stats: null argument");
+  unsigned long long h[2] = {0, 0};
+  SE_CUDA(cudaStreamSynchronize(P->stream));
+  SE_CUDA(cudaMemcpy(h, P->cw.totals, sizeof(h), cudaMemcpyDeviceToHost));
+  if (solves) *solves = (int64_t)h[1];
+  if (iterations) *iterations = (int64_t)h[0];
+  if (reset) SE_CUDA(cudaMemset(P->cw.totals, 0, sizeof(h)));
+  return SE_OK;
+}
+
 int se_pmg_apply(se_pmg_t P, const double* r, double* z, void* stream) {
   SE_CHECK(P && r && z, SE_EINVAL, "se_pmg_apply: null argument");
   return pmg_apply(P, r, z, as_stream(stream, P->stream));

@@ -296,6 +296,7 @@ struct CoarseWork {
   unsigned* bar;    // [2]: arrival count (monotonic within a launch), unused
   int* status;      // [2]: error flag, iterations
   int nblocks;
+  unsigned long long* totals = nullptr;  // [2]: iterations and solves since the last reset (may be null)
 };
 size_t coarse_partial_doubles(int nblocks);
 int coarse_alloc(const Level& lv, Allocs& allocs, CoarseWork* w);

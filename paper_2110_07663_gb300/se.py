@@ -127,6 +127,7 @@ _SIGS = {
     "se_ax": ([_vp, _vp, _vp, _ip, _vp], C.c_int),
     "se_residual": ([_vp, _vp, _vp, _vp, _ip, _vp], C.c_int),
     "se_prof_fma_peak": ([_ip, C.POINTER(C.c_double), C.POINTER(_ip), _vp], C.c_int),
+    "se_pmg_coarse_stats": ([_vp, _ip, C.POINTER(C.c_int64), C.POINTER(C.c_int64)], C.c_int),
     "se_gs": ([_vp, _vp, _ip, _vp], C.c_int),
     "se_gsmap_create": ([C.c_int64, _vp, _vp, C.POINTER(_vp)], C.c_int),
     "se_gsmap_apply": ([_vp, _vp, _ip, _vp], C.c_int),
@@ -395,6 +396,13 @@ def se_pmg_coarse_solve(P, r, x, stream=None) -> int:
     it = C.c_int()
     _check(lib.se_pmg_coarse_solve(P, _ptr(r), _ptr(x), C.byref(it), _stream(stream)))
     return it.value
+
+
+def se_pmg_coarse_stats(P, reset=False):
+    """(coarse solves, total coarse Jacobi-PCG iterations) since the last reset."""
+    n, it = C.c_int64(), C.c_int64()
+    _check(lib.se_pmg_coarse_stats(P, 1 if reset else 0, C.byref(n), C.byref(it)))
+    return n.value, it.value
 
 
 def se_pmg_coarse_solve_noalloc(P, r, x, stream=None) -> int:

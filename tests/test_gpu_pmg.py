@@ -254,3 +254,26 @@ def test_two_preconditioners_on_one_mesh():
         se.se_pmg_destroy(P1)
     finally:
         c.close()
+
+
+def test_coarse_stats_count_solves_and_iterations():
+    """se_pmg_coarse_stats counts every coarse solve and its Jacobi-PCG iterations, on the device,
+    including those inside V-cycles (one per V-cycle), and resets on request."""
+    c = Case((3, 3, 2), 5, seed=3)
+    se, torch = c.se, c.torch
+    P = se.se_pmg_setup(c.m, se.pmg_desc((5, 3, 1), se.SE_SMOOTH_RAS, 2))
+    try:
+        se.se_pmg_coarse_stats(P, reset=True)
+        lc = o.make_level(c.V, c.nel, 1, c.bc, c.amp)
+        info = se.se_pmg_level_info(P, 2)
+        it1 = se.se_pmg_coarse_solve(P, c.to_gpu(c.random_continuous(5, lc)), c.empty(info.L))
+        it2 = se.se_pmg_coarse_solve(P, c.to_gpu(c.random_continuous(6, lc)), c.empty(info.L))
+        assert se.se_pmg_coarse_stats(P) == (2, it1 + it2)
+        z = c.empty()
+        se.se_pmg_apply(P, c.to_gpu(c.random_continuous(7)), z)
+        n, its = se.se_pmg_coarse_stats(P, reset=True)
+        assert n == 3 and its > it1 + it2
+        assert se.se_pmg_coarse_stats(P) == (0, 0)
+    finally:
+        se.se_pmg_destroy(P)
+        c.close()
