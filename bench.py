@@ -512,6 +512,34 @@ def run_gpu(args):
         out["cpu_baseline"] = cpu_baseline_subprocess(args.cpu_timeout, sm_names[smoother], cheb_order)
     se.se_pmg_destroy(P)
     se.se_mesh_destroy(m)
+    del x, b
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    if world == 1 and not args.no_extras:
+        # the batched and served modes, measured in the same run after the headline's mesh is
+        # freed (outside its timed region)
+        bm = batch_measure(64, 3, 3)
+        out["batch"] = {"workload": bm["config"]["workload"], "ms_per_batch": bm["ms_per_step"],
+                        "value": bm["value"], "unit": bm["unit"], "groups": bm["config"]["groups"],
+                        "grouped_problems": bm["config"]["grouped_problems"],
+                        "iterations_min_max": bm["config"]["iterations_min_max"],
+                        "worst_rel_residual": bm["config"]["worst_rel_residual"],
+                        "serial_fp64_ms": bm["serial_fp64"]["ms"],
+                        "speedup_over_serial_fp64": bm["serial_fp64"]["speedup_of_batch"],
+                        "profiled_pass_ms": bm["profiled_pass_ms"], "roofline": bm["roofline"],
+                        "top_kernels": dict(list(bm["kernels"].items())[:6])}
+        torch.cuda.empty_cache()
+        import workloads as wl_
+        free, _ = torch.cuda.mem_get_info()
+        reqs = wl_.serve_requests(n=300, rate=200.0, seed=0)
+        served = serve_stream(se, reqs, int(0.8 * free), 8, se.SE_FP32)
+        serial = serve_stream(se, reqs[:30], int(0.8 * free), 1, se.SE_FP64)
+        out["serve"] = {"workload": "first 300 requests of the Poisson-arrival stream at 200/s (E log-uniform "
+                                    "in [512, 65536], p in {5,7,9}, 30% resident-mesh reuse), tol 1e-8, "
+                                    "8 slots, FP32 V-cycle / FP64 Krylov",
+                        "served": served,
+                        "one_slot_fp64_first_30": {k: serial[k] for k in ("solves_per_s", "p50_ms", "p99_ms",
+                                                                          "completed")}}
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
@@ -558,7 +586,7 @@ def cpu_baseline_subprocess(timeout_s, smoother="ras", order=2):
                       f"iterations in {t:.1f} s, single thread"}
 
 
-def run_batch(args):
+def batch_measure(nprob, steps, warmup, op_df=0):
     """64 independent problems (E from {8^3..24^3}, p from {3,5,7,9}, seeded maps and right-hand
     sides), FP32 V-cycle / FP64 Krylov, all solved by ONE graph launch per step, tiles tuned per
     p first; compared with the same 64 problems solved one after another with the plain FP64
@@ -568,7 +596,7 @@ def run_batch(args):
     from paper_2110_07663_gb300 import se
     import workloads as wl
     torch.cuda.set_device(0)
-    specs = wl.batch_problems(args.batch)
+    specs = wl.batch_problems(nprob)
     t0 = time.perf_counter()
     tuned = {p: se.se_tune(p, se.SE_FP32) for p in sorted({sp["p"] for sp in specs})}
     tune_s = time.perf_counter() - t0
@@ -592,7 +620,6 @@ def run_batch(args):
         total_dof += info.n_dof
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
-    op_df = 1 if args.operator_df64 else 0
     B = se.se_batch_create([(m, P32, b, x) for (m, P32, P64, b, x, info) in probs], tol=1e-8, maxit=500,
                            operator_df64=op_df)
     groups, grouped = se.se_batch_info(B)
@@ -603,17 +630,17 @@ def run_batch(args):
             pr[4].zero_()
         se.se_batch_run(B, stream)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         batch_step()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(0) as clk:
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             batch_step()
         e1.record(stream)
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = e0.elapsed_time(e1) / steps
     stats = se.se_batch_stats(B, len(probs), stream)
     its = [s_.iterations for s_ in stats]
     worst = max(s_.rel_residual for s_ in stats)
@@ -652,7 +679,7 @@ def run_batch(args):
         se.se_mesh_destroy(m)
     out = {
         "metric": "batched Poisson solves: total time & aggregate GDOF/s", "value": round(total_dof / (ms * 1e-3) / 1e9, 4),
-        "unit": "GDOF/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "unit": "GDOF/s", "n_gpus": 1, "steps": steps, "warmup": warmup,
         "ms_per_step": round(ms, 2), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 V-cycle / f64 Krylov" + (" (df64 operator)" if op_df else ""), "data": "synthetic",
         "config": {"workload": f"{len(probs)} problems, E in {{8^3..24^3}}, p in {{3,5,7,9}}, "
@@ -672,7 +699,12 @@ def run_batch(args):
         "roofline": roof,
         "kernels": ktable,
     }
-    print(json.dumps(out))
+    return out
+
+
+def run_batch(args):
+    print(json.dumps(batch_measure(args.batch, args.steps, args.warmup,
+                                   1 if args.operator_df64 else 0)))
 
 
 SERVE_SCHEDULES = {5: (5, 3, 1), 7: (7, 3, 1), 9: (9, 5, 1)}
@@ -1149,6 +1181,8 @@ def main():
     ap.add_argument("--operator-df64", action="store_true",
                     help="df64 outer operator (solve, batch, serve); serve: also df64 Arnoldi set-up")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batch and serve records of the headline line")
     ap.add_argument("--no-schwarz", action="store_true",
                     help="skip the Cheby-RAS(2) FP64 / FP32-V-cycle record of the headline line")
     ap.add_argument("--oracle-full", action="store_true",
