@@ -355,6 +355,17 @@ def run_gpu(args):
     op_df = 1 if (args.df64 or args.operator_df64) else 0
     sm_names = {se.SE_SMOOTH_RAS: "RAS", se.SE_SMOOTH_JACOBI: "Jac", se.SE_SMOOTH_ASM: "ASM"}
     t_setup0 = time.perf_counter()
+    tiles = None
+    if args.tune_tiles:
+        # the project's launch-tile autotuner for every order of the schedule (set-up, untimed)
+        prec_t = se.SE_FP32 if args.precond_fp32 else se.SE_FP64
+        tiles = {}
+        for pp in sorted(q for q in set(wk["schedule"]) if q >= 2):
+            t64 = se.se_tune(pp, se.SE_FP64)
+            tiles[f"p={pp} f64"] = [t64.ax_elems_per_block, t64.fdm_elems_per_block]
+            if prec_t == se.SE_FP32:
+                t32 = se.se_tune(pp, se.SE_FP32)
+                tiles[f"p={pp} f32"] = [t32.ax_elems_per_block, t32.fdm_elems_per_block]
     search = None
     if args.smoother == "auto":
         # the method's run-time preconditioner selection (Sec. 5) over the workload's smoother set,
@@ -485,7 +496,7 @@ def run_gpu(args):
                                + (f"{sm_names[smoother]}, additive V-cycle (no Chebyshev), " if args.cycle == "additive"
                                   else f"Cheby-{sm_names[smoother]}({cheb_order}), ")
                                + f"FPCG tol 1e-8, {prec_name} preconditioner, {op_name} outer operator",
-                   "iterations": iters, "setup_s": round(setup_s, 2),
+                   "iterations": iters, "setup_s": round(setup_s, 2), "tuned_tiles": tiles,
                    "time_to_solution_cold_s": round(setup_s + ms_max * 1e-3, 3),
                    "e2e_scope": ("per step: b host->device, the graph solve, x device->host; mesh and "
                                  "preconditioner set-up (setup_s, incl. the search) are outside it"),
@@ -1181,6 +1192,8 @@ def main():
     ap.add_argument("--operator-df64", action="store_true",
                     help="df64 outer operator (solve, batch, serve); serve: also df64 Arnoldi set-up")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tune-tiles", action="store_true",
+                    help="run the launch-tile autotuner for the schedule's orders during set-up")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batch and serve records of the headline line")
     ap.add_argument("--no-schwarz", action="store_true",
