@@ -322,7 +322,10 @@ typedef struct se_problem {
   double* x;
 } se_problem;
 typedef struct se_batch_s* se_batch_t;
-/* Builds and instantiates the batch graph (the inputs are captured by pointer). */
+/* Builds and instantiates the batch graph (the inputs are captured by pointer).  The batch uses
+ * the problems' handles while it exists (a group's coarse solves run in its members'
+ * preconditioner work space): destroy it before any of them, and do not solve a member on its
+ * own while the batch runs. */
 int se_batch_create(int n, const se_problem* probs, const se_solve_opts* opts, se_batch_t* out);
 /* One graph launch on `stream` (NULL: legacy default stream); returns without waiting. */
 int se_batch_run(se_batch_t batch, void* stream);

@@ -10,7 +10,8 @@ exhausted.  Multigrid: the transfers are adjoint and reproduce coarse polynomial
 steps (pre-smoothing, coarse correction with the re-evaluated residual, post-smoothing) built
 from dense matrices, and contracts the error.  Solvers: the converged solution equals a dense
 direct solve; the discrete solution converges spectrally; flexible CG reduces to textbook PCG
-for a fixed preconditioner and keeps consecutive directions conjugate for a varying one.
+for a fixed preconditioner and keeps consecutive directions conjugate for a varying one;
+FGMRES reaches the minimal residual over its Krylov space (and per restart cycle).
 """
 import math
 
@@ -532,3 +533,48 @@ def test_fpcg_keeps_consecutive_directions_conjugate_under_a_varying_preconditio
 
     assert run("flexible").max() <= 1e-12
     assert run("textbook").max() >= 1e-3
+
+
+def test_fgmres_residual_is_the_krylov_minimum():
+    """Right-preconditioned GMRES (Sec. 2.2) with a fixed preconditioner and no restart within k
+    steps: its residual after k steps is the smallest of ||r_0 - A M q|| over q in the Krylov space
+    span{r_0, (A M) r_0, ..., (A M)^{k-1} r_0} (unique-node 2-norm), computed here from the
+    brute-force assembled matrix by a dense least-squares solve.  Errors in the Givens rotations,
+    the back substitution or the x update change the residual and fail the comparison."""
+    nel = (2, 2, 2)
+    V = wl.vertex_lattice(nel, 0.1, seed=4)
+    lv, b = o.problem(V, nel, 3)
+    d = o.jacobi_diag(lv)
+    cols = free_nodes(lv)
+    xg, wg = o.gll(3)
+    Af = assembled_stiffness(lv, xg, wg)[np.ix_(cols, cols)]
+    Mf = np.diag(1.0 / np.diag(Af))
+    r0 = o.to_global(lv, b)[cols]
+    A = lambda u: o.ax(lv, u)
+    M = lambda r: lv.mask * r / d
+    dotf = lambda a, c: o.dot(lv, a, c)
+    AM = Af @ Mf
+    for k in (1, 2, 4, 7):
+        x, it, _ = o.fgmres(A, M, b, np.zeros_like(b), dotf, m=20, tol=0.0, maxit=k)
+        assert it == k
+        res = np.linalg.norm(r0 - Af @ o.to_global(lv, x)[cols])
+        K = np.empty((len(cols), k))
+        v = r0.copy()
+        for j in range(k):
+            K[:, j] = v / np.linalg.norm(v)
+            v = AM @ K[:, j]
+        Q, _ = np.linalg.qr(K)
+        y, *_ = np.linalg.lstsq(AM @ Q, r0, rcond=None)
+        best = np.linalg.norm(r0 - AM @ Q @ y)
+        assert abs(res - best) <= 1e-9 * np.linalg.norm(r0), (k, res, best)
+    # restarted: two cycles of two steps end where two minimisations from the first iterate end
+    x2, it2, _ = o.fgmres(A, M, b, np.zeros_like(b), dotf, m=2, tol=0.0, maxit=4)
+    r = r0.copy()
+    xs = np.zeros(len(cols))
+    for _ in range(2):
+        K = np.stack([r / np.linalg.norm(r), AM @ r / np.linalg.norm(AM @ r)], axis=1)
+        Q, _ = np.linalg.qr(K)
+        y, *_ = np.linalg.lstsq(AM @ Q, r, rcond=None)
+        xs = xs + Mf @ (Q @ y)
+        r = r0 - Af @ xs
+    assert np.allclose(o.to_global(lv, x2)[cols], xs, rtol=0, atol=1e-9 * np.abs(xs).max())
