@@ -745,14 +745,24 @@ def serve_stream(se, reqs, budget, slots, precision, t_scale=1.0, proj=0, op_df=
             tickets.append(se.se_serve_submit(S, q))
         except se.SeError:
             refused += 1
-    results = [se.se_serve_wait(S, t, 3.6e6, allow=(se.SE_ENOTCONV,)) for t in tickets]
+    results = [se.se_serve_wait(S, t, 3.6e6, allow=(se.SE_ENOTCONV, se.SE_ETIMEOUT)) for t in tickets]
     wall = time.perf_counter() - t0
     st = se.se_serve_stats(S)
     se.se_serve_destroy(S)
-    its = [r.iterations for r in results]
-    worst = max(r.rel_residual for r in results) if results else None
+    ok = [r for r in results if r.status == se.SE_OK]
+    its = [r.iterations for r in ok]
+    worst = max(r.rel_residual for r in ok) if ok else None
     setups = [r.setup_ms for r in results if r.new_mesh]
-    solves = [r.solve_ms for r in results]
+    solves = [r.solve_ms for r in ok]
+    failures = []  # every failed request, with what identifies its mesh
+    for i, r in enumerate(results):
+        if r.status != se.SE_OK:
+            m = reqs[i]["mesh"]
+            failures.append({"index": i, "status": r.status, "iterations": r.iterations,
+                             "rel_residual": r.rel_residual, "new_mesh": r.new_mesh,
+                             "nel": list(m["nel"]), "p": m["p"], "seed": m["seed"],
+                             "perturb_frac": m["perturb_frac"], "rhs_seed": reqs[i]["rhs_seed"],
+                             "setup_ms": round(r.setup_ms, 1), "solve_ms": round(r.solve_ms, 1)})
     return {"requests": len(reqs), "completed": st.completed, "refused": st.refused + refused,
             "failed": st.failed, "solves_per_s": round(st.solves_per_s, 2),
             "p50_ms": round(st.p50_ms, 1), "p99_ms": round(st.p99_ms, 1), "mean_ms": round(st.mean_ms, 1),
@@ -762,7 +772,8 @@ def serve_stream(se, reqs, budget, slots, precision, t_scale=1.0, proj=0, op_df=
             "mean_setup_ms_new_mesh": round(statistics.mean(setups), 1) if setups else None,
             "mean_solve_ms": round(statistics.mean(solves), 1) if solves else None,
             "proj_vectors": proj, "projected": st.projected,
-            "mean_iterations": round(statistics.mean(its), 2) if its else None}
+            "mean_iterations": round(statistics.mean(its), 2) if its else None,
+            "failures": failures[:20]}
 
 
 def run_serve(args):

@@ -871,6 +871,11 @@ int se_batch_stats(se_batch_t B, void* stream, se_solve_stats* out) {
     set_error("se_batch: a pipelined kernel's bounded wait expired (results invalid)");
     worst = SE_ETIMEOUT;
   }
+  for (size_t i = 0; i < B->probs.size(); ++i)  // grouped or alone: the coarse solves' waits
+    if (B->probs[i].pmg && coarse_fault_take(B->probs[i].pmg->cw, s) != SE_OK) {
+      out[i].status = SE_ETIMEOUT;
+      worst = SE_ETIMEOUT;
+    }
   return worst;
 }
 

@@ -373,6 +373,7 @@ __device__ __forceinline__ void coarse_pcg_run(const CoarseArgs<T>& c, unsigned 
     if (c.totals) {
       atomicAdd(c.totals, (unsigned long long)it);
       atomicAdd(c.totals + 1, 1ULL);
+      if (!ok) atomicAdd(c.totals + 2, 1ULL);  // results of this solve are invalid
     }
   }
 }
@@ -434,8 +435,8 @@ int coarse_alloc(const Level& lv, Allocs& allocs, CoarseWork* w) {
   SE_TRY(dmalloc(allocs, &w->status, 2));
   SE_CUDA(cudaMemset(w->bar, 0, 2 * sizeof(unsigned)));
   SE_CUDA(cudaMemset(w->status, 0, 2 * sizeof(int)));
-  SE_TRY(dmalloc(allocs, &w->totals, 2));
-  SE_CUDA(cudaMemset(w->totals, 0, 2 * sizeof(unsigned long long)));
+  SE_TRY(dmalloc(allocs, &w->totals, 3));
+  SE_CUDA(cudaMemset(w->totals, 0, 3 * sizeof(unsigned long long)));
   return SE_OK;
 }
 
@@ -600,6 +601,17 @@ int coarse_group_solve(const CoarseGroup& g, cudaStream_t s) {
 }
 template int coarse_group_solve<double>(const CoarseGroup&, cudaStream_t);
 template int coarse_group_solve<float>(const CoarseGroup&, cudaStream_t);
+
+int coarse_fault_take(CoarseWork& w, cudaStream_t s) {
+  if (!w.totals) return SE_OK;
+  unsigned long long f = 0;
+  SE_CUDA(cudaStreamSynchronize(s));
+  SE_CUDA(cudaMemcpy(&f, w.totals + 2, sizeof(f), cudaMemcpyDeviceToHost));
+  if (f == 0) return SE_OK;
+  SE_CUDA(cudaMemset(w.totals + 2, 0, sizeof(f)));
+  set_error("coarse solve: %llu solve(s) gave up a bounded grid-synchronisation wait (results invalid)", f);
+  return SE_ETIMEOUT;
+}
 
 template int coarse_solve<double>(const Level&, CoarseWork&, const double*, double*, double, int, cudaStream_t);
 template int coarse_solve<float>(const Level&, CoarseWork&, const float*, float*, double, int, cudaStream_t);

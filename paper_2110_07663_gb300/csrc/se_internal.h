@@ -296,8 +296,13 @@ struct CoarseWork {
   unsigned* bar;    // [2]: arrival count (monotonic within a launch), unused
   int* status;      // [2]: error flag, iterations
   int nblocks;
-  unsigned long long* totals = nullptr;  // [2]: iterations and solves since the last reset (may be null)
+  // [3]: iterations and solves since the last reset, and solves whose bounded waits expired
+  // (kept until read); may be null
+  unsigned long long* totals = nullptr;
 };
+// SE_ETIMEOUT (and a cleared count) if a coarse solve of this work space gave up a bounded wait
+// since the last call; synchronises `s` first.
+int coarse_fault_take(CoarseWork& w, cudaStream_t s);
 size_t coarse_partial_doubles(int nblocks);
 int coarse_alloc(const Level& lv, Allocs& allocs, CoarseWork* w);
 template <class T>

@@ -207,6 +207,7 @@ extern "C" int se_solve(se_mesh_t m, se_pmg_t P, const double* b, double* x,
     set_error("se_solve: a pipelined kernel's bounded wait expired (results invalid)");
     rc = SE_ETIMEOUT;
   }
+  if (P && coarse_fault_take(P->cw, s) != SE_OK) rc = SE_ETIMEOUT;
   st.ms_total = ms;
   st.status = rc;
   if (stats) *stats = st;
