@@ -5,8 +5,8 @@
 // shared-memory stage with cp.async.bulk, completion counted by an mbarrier transaction count;
 // two stages alternate, so the loads of the next group run while the current one is contracted.
 // The contractions are those of ax_local_kernel (sum factorisation, 12N+15 flops per point).
-// Every mbarrier wait is bounded (wall clock, ~1 s): on expiry the kernel records a status in
-// g_pipeline_status, waits (bounded) for the copies it issued, and returns.
+// Every mbarrier wait is bounded (wall clock, ~1 s): on expiry the kernel records SE_ETIMEOUT in
+// the level's status word, waits (bounded) for the copies it issued, and returns.
 // Only for even N: then every element block (N^3 floats) is a multiple of 16 bytes, as the bulk
 // copy requires for sizes and addresses.
 #include <cstdint>
@@ -14,8 +14,6 @@
 #include "se_internal.h"
 
 namespace se {
-
-__device__ int g_pipeline_status = 0;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -50,12 +48,13 @@ __device__ __forceinline__ long long gtimer() {
   return t;
 }
 // Bounded wait for phase `parity` of `bar`; false on expiry (status recorded).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, long long limit_ns) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, long long limit_ns,
+                                                  int* pstatus) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = gtimer();
   while (!mbar_try_wait(bar, parity)) {
     if (gtimer() - t0 > limit_ns) {
-      atomicExch(&g_pipeline_status, SE_ETIMEOUT);
+      atomicExch(pstatus, SE_ETIMEOUT);
       return false;
     }
   }
@@ -76,7 +75,8 @@ __global__ void __launch_bounds__(512) ax_tma_kernel(int64_t E, int NE, int64_t 
                                                      float* __restrict__ y,
                                                      const float* __restrict__ sub, int nx,
                                                      int ny, int nz,
-                                                     const uint8_t* __restrict__ pflag) {
+                                                     const uint8_t* __restrict__ pflag,
+                                                     int* __restrict__ pstatus) {
   constexpr int N2 = N * N, N3 = N * N * N, A = RES ? 8 : 7;  // blocks per stage
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int S = NE * N3;                       // floats per element-group block
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(512) ax_tma_kernel(int64_t E, int NE, int64_t 
   int st = 0;
   bool ok = true;
   for (; g < ngroups; g += gridDim.x) {
-    const bool expired = !mbar_wait_bounded(&bars[st], (phases >> st) & 1u, PIPE_LIMIT_NS);
+    const bool expired = !mbar_wait_bounded(&bars[st], (phases >> st) & 1u, PIPE_LIMIT_NS, pstatus);
     if (__syncthreads_or(expired)) {  // the whole block leaves together
       ok = false;
       break;
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(512) ax_tma_kernel(int64_t E, int NE, int64_t 
   }
   if (!ok && tid == 0) {
     // wait (bounded) for copies still in flight before the block's shared memory goes away
-    for (int s2 = 0; s2 < 2; ++s2) mbar_wait_bounded(&bars[s2], (phases >> s2) & 1u, PIPE_LIMIT_NS);
+    for (int s2 = 0; s2 < 2; ++s2) mbar_wait_bounded(&bars[s2], (phases >> s2) & 1u, PIPE_LIMIT_NS, pstatus);
   }
 }
 
@@ -211,6 +211,7 @@ template <int N, bool RES>
 static int launch_ax_tma_t(const Level& lv, const float* u, float* y, int NE, const float* sub,
                            cudaStream_t s) {
   constexpr int N3 = N * N * N, A = RES ? 8 : 7;
+  SE_CHECK(lv.pstatus, SE_EINVAL, "ax_tma: level without a status word");
   const int threads = NE * N * N;
   const size_t smem = (size_t)((2 * A + 2) * NE * N3 + ((N * N + 3) / 4) * 4 + 4) * sizeof(float) +
                       2 * sizeof(uint64_t);
@@ -228,7 +229,8 @@ static int launch_ax_tma_t(const Level& lv, const float* u, float* y, int NE, co
   if (grid > groups) grid = groups;
   ax_tma_kernel<N, RES><<<(unsigned)grid, threads, smem, s>>>(lv.E, NE, groups, u, lv.G32, lv.L,
                                                                lv.D32, y, sub, lv.nel[0],
-                                                               lv.nel[1], lv.nel[2], lv.pflag);
+                                                               lv.nel[1], lv.nel[2], lv.pflag,
+                                                               lv.pstatus);
   SE_LAUNCH_CHECK();
   return SE_OK;
 }
@@ -266,12 +268,15 @@ int ax_local_tma(const Level& lv, const float* u, float* y, cudaStream_t s, cons
   }
 }
 
-int pipeline_status_take(int* status) {
-  int h = 0, zero = 0;
-  SE_CUDA(cudaMemcpyFromSymbol(&h, g_pipeline_status, sizeof(int)));
-  if (h) SE_CUDA(cudaMemcpyToSymbol(g_pipeline_status, &zero, sizeof(int)));
-  *status = h;
-  return SE_OK;
+int level_pipeline_take(const Level& lv, cudaStream_t s) {
+  if (!lv.pstatus) return SE_OK;
+  int h = 0;
+  SE_CUDA(cudaStreamSynchronize(s));
+  SE_CUDA(cudaMemcpy(&h, lv.pstatus, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h == 0) return SE_OK;
+  SE_TRY(dzero(lv.pstatus, sizeof(int), s));
+  set_error("p = %d level: a pipelined kernel's bounded wait expired (results invalid)", lv.p);
+  return SE_ETIMEOUT;
 }
 
 }  // namespace se

@@ -347,6 +347,8 @@ static int build_union_level(se_pmg_s* U, int l, const std::vector<se_pmg_s*>& P
   const bool want64 = l == 0 || (!fp32 && !coarsest);
   const bool want32 = fp32 && !coarsest;
   SE_TRY(dmalloc(A, &u.pflag, (size_t)u.L));
+  SE_TRY(dmalloc(A, &u.pstatus, 1));
+  SE_TRY(dzero(u.pstatus, sizeof(int), s));
   if (want64) SE_TRY(dmalloc(A, &u.G64, 6 * (size_t)u.L));
   if (want32) SE_TRY(dmalloc(A, &u.G32, 6 * (size_t)u.L));
   const bool ras = smoother == SE_SMOOTH_RAS && !coarsest;
@@ -866,16 +868,19 @@ int se_batch_stats(se_batch_t B, void* stream, se_solve_stats* out) {
     out[i] = st;
     if (rc != SE_OK) worst = rc;
   }
-  int pipe = 0;
-  if (pipeline_status_take(&pipe) == SE_OK && pipe != 0) {
-    set_error("se_batch: a pipelined kernel's bounded wait expired (results invalid)");
-    worst = SE_ETIMEOUT;
-  }
-  for (size_t i = 0; i < B->probs.size(); ++i)  // grouped or alone: the coarse solves' waits
-    if (B->probs[i].pmg && coarse_fault_take(B->probs[i].pmg->cw, s) != SE_OK) {
+  // bounded device waits: a group's union levels count against all its members
+  std::vector<bool> group_fault(B->groups.size(), false);
+  for (size_t g = 0; g < B->groups.size(); ++g)
+    group_fault[g] = pmg_faults_take(B->groups[g]->U, s) != SE_OK;
+  for (size_t i = 0; i < B->probs.size(); ++i) {
+    bool f = B->group_of[i] >= 0 && group_fault[B->group_of[i]];
+    if (level_pipeline_take(B->probs[i].mesh->fine, s) != SE_OK) f = true;
+    if (B->probs[i].pmg && pmg_faults_take(B->probs[i].pmg, s) != SE_OK) f = true;
+    if (f) {
       out[i].status = SE_ETIMEOUT;
       worst = SE_ETIMEOUT;
     }
+  }
   return worst;
 }
 

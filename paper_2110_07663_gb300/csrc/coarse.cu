@@ -433,10 +433,10 @@ int coarse_alloc(const Level& lv, Allocs& allocs, CoarseWork* w) {
   SE_TRY(dmalloc(allocs, &w->partial, coarse_partial_doubles(w->nblocks)));
   SE_TRY(dmalloc(allocs, &w->bar, 2));
   SE_TRY(dmalloc(allocs, &w->status, 2));
-  SE_CUDA(cudaMemset(w->bar, 0, 2 * sizeof(unsigned)));
-  SE_CUDA(cudaMemset(w->status, 0, 2 * sizeof(int)));
+  SE_TRY(dzero(w->bar, 2 * sizeof(unsigned), allocs.stream));
+  SE_TRY(dzero(w->status, 2 * sizeof(int), allocs.stream));
   SE_TRY(dmalloc(allocs, &w->totals, 3));
-  SE_CUDA(cudaMemset(w->totals, 0, 3 * sizeof(unsigned long long)));
+  SE_TRY(dzero(w->totals, 3 * sizeof(unsigned long long), allocs.stream));
   return SE_OK;
 }
 
@@ -608,7 +608,7 @@ int coarse_fault_take(CoarseWork& w, cudaStream_t s) {
   SE_CUDA(cudaStreamSynchronize(s));
   SE_CUDA(cudaMemcpy(&f, w.totals + 2, sizeof(f), cudaMemcpyDeviceToHost));
   if (f == 0) return SE_OK;
-  SE_CUDA(cudaMemset(w.totals + 2, 0, sizeof(f)));
+  SE_TRY(dzero(w.totals + 2, sizeof(f), s));
   set_error("coarse solve: %llu solve(s) gave up a bounded grid-synchronisation wait (results invalid)", f);
   return SE_ETIMEOUT;
 }
@@ -638,9 +638,10 @@ extern "C" int se_selftest_wait_timeout(double timeout_ms) {
   SE_CUDA(cudaMalloc(&bar, 2 * sizeof(unsigned)));
   SE_CUDA(cudaMalloc(&status, 2 * sizeof(int)));
   SE_CUDA(cudaMalloc(&part, coarse_partial_doubles(NB + 1) * sizeof(double)));
-  SE_CUDA(cudaMemset(bar, 0, 2 * sizeof(unsigned)));
-  SE_CUDA(cudaMemset(status, 0, 2 * sizeof(int)));
-  barrier_timeout_kernel<<<NB, 32>>>(bar, status, part, (long long)(timeout_ms * 1e6));
+  // everything of this self-test on the legacy default stream (0), in order
+  SE_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), 0));
+  SE_CUDA(cudaMemsetAsync(status, 0, 2 * sizeof(int), 0));
+  barrier_timeout_kernel<<<NB, 32, 0, 0>>>(bar, status, part, (long long)(timeout_ms * 1e6));
   cudaError_t e = cudaDeviceSynchronize();
   int h[2] = {0, 0};
   cudaMemcpy(h, status, sizeof(h), cudaMemcpyDeviceToHost);

@@ -73,6 +73,18 @@ void dfree(Allocs& a, void* p, size_t bytes) {
   cudaFreeAsync(p, a.stream);
 }
 
+int h2d(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  SE_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
+  SE_CUDA(cudaStreamSynchronize(s));
+  return SE_OK;
+}
+
+int dzero(void* p, size_t bytes, cudaStream_t s) {
+  SE_CUDA(cudaMemsetAsync(p, 0, bytes, s));
+  SE_CUDA(cudaStreamSynchronize(s));
+  return SE_OK;
+}
+
 static std::mutex g_pin_mu;
 static std::vector<double*> g_pin_free;
 
@@ -177,8 +189,8 @@ int scratch_alloc(Allocs& a, Scratch* s) {
   SE_TRY(dmalloc(a, &s->partial, (size_t)RED_MAX_BLOCKS * 4));
   SE_TRY(dmalloc(a, &s->counter, 1));
   SE_TRY(dmalloc(a, &s->scal, SCAL_SLOTS));
-  SE_CUDA(cudaMemset(s->counter, 0, sizeof(unsigned)));
-  SE_CUDA(cudaMemset(s->scal, 0, SCAL_SLOTS * sizeof(double)));
+  SE_TRY(dzero(s->counter, sizeof(unsigned), a.stream));
+  SE_TRY(dzero(s->scal, SCAL_SLOTS * sizeof(double), a.stream));
   SE_TRY(pinned_scalars(&s->hscal));
   return SE_OK;
 }

@@ -148,9 +148,9 @@ int fdm_setup(const se_mesh_s* m, Level& lv, Allocs& allocs, bool want32, cudaSt
   SE_TRY(dmalloc(allocs, &dKe, N * N));
   SE_TRY(dmalloc(allocs, &dw, N));
   SE_TRY(dmalloc(allocs, &dlen, 3 * E));
-  SE_CUDA(cudaMemcpy(dKe, Ke, N * N * sizeof(double), cudaMemcpyHostToDevice));
-  SE_CUDA(cudaMemcpy(dw, lv.basis.w, N * sizeof(double), cudaMemcpyHostToDevice));
-  SE_CUDA(cudaMemcpy(dlen, m->box_len.data(), 3 * E * sizeof(double), cudaMemcpyHostToDevice));
+  SE_TRY(h2d(dKe, Ke, N * N * sizeof(double), s));
+  SE_TRY(h2d(dw, lv.basis.w, N * sizeof(double), s));
+  SE_TRY(h2d(dlen, m->box_len.data(), 3 * E * sizeof(double), s));
   SE_TRY(dmalloc(allocs, &lv.S64, 3 * E * PB * PB));
   SE_TRY(dmalloc(allocs, &lv.lam64, 3 * E * PB));
   int bits = 0;

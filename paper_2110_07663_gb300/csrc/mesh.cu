@@ -202,6 +202,8 @@ int build_level(se_mesh_s* m, int p, Level* lvp, Allocs& allocs, cudaStream_t s)
   lv.L = lv.E * N3;
   lv.NX = lv.nel[0] * p + 1;
   lv.NY = lv.nel[1] * p + 1;
+  SE_TRY(dmalloc(allocs, &lv.pstatus, 1));
+  SE_TRY(dzero(lv.pstatus, sizeof(int), s));
   lv.NZ = lv.nel[2] * p + 1;
   lv.n_global = (int64_t)lv.NX * lv.NY * lv.NZ;
   SE_CHECK(lv.L < (int64_t)1 << 31, SE_EINVAL, "mesh too large: %lld local points (limit 2^31)",
@@ -216,23 +218,23 @@ int build_level(se_mesh_s* m, int p, Level* lvp, Allocs& allocs, cudaStream_t s)
   SE_TRY(dmalloc(allocs, &dw, N));
   float D32h[(SE_MAX_ORDER + 1) * (SE_MAX_ORDER + 1)];
   for (int t = 0; t < N * N; ++t) D32h[t] = (float)lv.basis.D[t];
-  SE_CUDA(cudaMemcpy(lv.D64, lv.basis.D, N * N * sizeof(double), cudaMemcpyHostToDevice));
-  SE_CUDA(cudaMemcpy(lv.D32, D32h, N * N * sizeof(float), cudaMemcpyHostToDevice));
-  SE_CUDA(cudaMemcpy(dxi, lv.basis.xi, N * sizeof(double), cudaMemcpyHostToDevice));
-  SE_CUDA(cudaMemcpy(dw, lv.basis.w, N * sizeof(double), cudaMemcpyHostToDevice));
+  SE_TRY(h2d(lv.D64, lv.basis.D, N * N * sizeof(double), s));
+  SE_TRY(h2d(lv.D32, D32h, N * N * sizeof(float), s));
+  SE_TRY(h2d(dxi, lv.basis.xi, N * sizeof(double), s));
+  SE_TRY(h2d(dw, lv.basis.w, N * sizeof(double), s));
   if (ax_eo_supported(p)) {
     const int H = N / 2;
     double tab[4 * (SE_MAX_ORDER + 1) * (SE_MAX_ORDER + 1) / 4 + 4];
     ax_eo_tables(lv.basis, tab);
     SE_TRY(dmalloc(allocs, &lv.eo64, 4 * H * H));
-    SE_CUDA(cudaMemcpy(lv.eo64, tab, 4 * H * H * sizeof(double), cudaMemcpyHostToDevice));
+    SE_TRY(h2d(lv.eo64, tab, 4 * H * H * sizeof(double), s));
   }
 
   // geometry
   double* dverts = nullptr;
   const size_t nv = m->verts.size();
   SE_TRY(dmalloc(allocs, &dverts, nv));
-  SE_CUDA(cudaMemcpy(dverts, m->verts.data(), nv * sizeof(double), cudaMemcpyHostToDevice));
+  SE_TRY(h2d(dverts, m->verts.data(), nv * sizeof(double), s));
   SE_TRY(dmalloc(allocs, &lv.X, 3 * (size_t)lv.L));
   SE_TRY(dmalloc(allocs, &lv.G64, 6 * (size_t)lv.L));
   SE_TRY(dmalloc(allocs, &lv.B, (size_t)lv.L));
@@ -402,10 +404,7 @@ int se_mesh_create(const se_mesh_desc* desc, se_mesh_t* out) {
           }
     }
     if ((st = dmalloc(m->allocs, &m->nbr, nb.size())) != SE_OK) return fail(st);
-    if (cudaMemcpy(m->nbr, nb.data(), nb.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) {
-      set_error("se_mesh_create: neighbour upload failed");
-      return fail(SE_ECUDA);
-    }
+    if ((st = h2d(m->nbr, nb.data(), nb.size() * sizeof(int), m->stream)) != SE_OK) return fail(st);
   }
   box_lengths(m);
   if ((st = build_level(m, desc->p, &m->fine, m->allocs, m->stream)) != SE_OK) return fail(st);

@@ -395,8 +395,8 @@ static int pmg_build(se_pmg_s* P) {
     for (int q = 0; q < Nf * Nc; ++q) J32[q] = (float)J[q];
     SE_TRY(dmalloc(P->allocs, &P->J64[l], Nf * Nc));
     SE_TRY(dmalloc(P->allocs, &P->J32[l], Nf * Nc));
-    SE_CUDA(cudaMemcpy(P->J64[l], J.data(), Nf * Nc * sizeof(double), cudaMemcpyHostToDevice));
-    SE_CUDA(cudaMemcpy(P->J32[l], J32.data(), Nf * Nc * sizeof(float), cudaMemcpyHostToDevice));
+    SE_TRY(h2d(P->J64[l], J.data(), Nf * Nc * sizeof(double), P->stream));
+    SE_TRY(h2d(P->J32[l], J32.data(), Nf * Nc * sizeof(float), P->stream));
   }
   SE_TRY(coarse_alloc(*P->lv[P->nlev - 1], P->allocs, &P->cw));
   for (int l = 0; l < P->nlev; ++l) {
@@ -440,6 +440,14 @@ static int precision_io(se_pmg_s* P, int lvl, const double* in, double* out, cud
     return convert<float, double>(V.x, out, L, s);
   }
   return f64(in, out);
+}
+
+int pmg_faults_take(se_pmg_s* P, cudaStream_t s) {
+  int rc = SE_OK;
+  for (int l = 0; l < P->nlev; ++l)
+    if (P->lv[l] && level_pipeline_take(*P->lv[l], s) != SE_OK) rc = SE_ETIMEOUT;
+  if (coarse_fault_take(P->cw, s) != SE_OK) rc = SE_ETIMEOUT;
+  return rc;
 }
 
 }  // namespace se
@@ -518,7 +526,7 @@ int se_pmg_coarse_stats(se_pmg_t P, int reset, int64_t* solves, int64_t* iterati
   SE_CUDA(cudaMemcpy(h, P->cw.totals, sizeof(h), cudaMemcpyDeviceToHost));
   if (solves) *solves = (int64_t)h[1];
   if (iterations) *iterations = (int64_t)h[0];
-  if (reset) SE_CUDA(cudaMemset(P->cw.totals, 0, sizeof(h)));
+  if (reset) SE_TRY(dzero(P->cw.totals, sizeof(h), P->stream));
   return SE_OK;
 }
 

@@ -25,6 +25,9 @@ int append_fpcg_solve(cudaGraph_t G, cudaStream_t cs, se_mesh_s* m, se_pmg_s* P,
 int add_conditional(cudaStream_t cs, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
                     cudaGraph_t* body);
 int pmg_alloc_vecs(se_pmg_s* P, int l, bool fp32);
+// SE_ETIMEOUT if a bounded device wait in P's kernels (a pipelined operator of one of its levels,
+// its coarse solve) expired since the last call; clears those records.  Synchronises s.
+int pmg_faults_take(se_pmg_s* P, cudaStream_t s);
 // b = M QQ^T B_L f for f = pi^2 (k1^2+k2^2+k3^2) a sin(k1 pi x) sin(k2 pi y) sin(k3 pi z), the
 // right-hand side of the manufactured solution u* = a sin(k1 pi x) sin(k2 pi y) sin(k3 pi z).
 int rhs_modes(se_mesh_s* m, const int k[3], double a, double* b, cudaStream_t s);

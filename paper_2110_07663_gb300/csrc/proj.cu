@@ -47,11 +47,7 @@ int se_proj_create(se_mesh_t m, int max_vectors, se_proj_t* out) {
   if (rc == SE_OK) {
     std::vector<double*> ptrs(max_vectors);
     for (int i = 0; i < max_vectors; ++i) ptrs[i] = p->X + (size_t)i * L;
-    if (cudaMemcpy(p->xptr, ptrs.data(), max_vectors * sizeof(double*), cudaMemcpyHostToDevice) !=
-        cudaSuccess) {
-      set_error("se_proj_create: copy failed");
-      rc = SE_ECUDA;
-    }
+    rc = h2d(p->xptr, ptrs.data(), max_vectors * sizeof(double*), m->stream);
   }
   if (rc != SE_OK) {
     cudaStreamSynchronize(m->stream);

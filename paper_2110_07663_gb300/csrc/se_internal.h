@@ -58,6 +58,12 @@ int dmalloc_bytes(Allocs& a, void** p, size_t bytes);
 void dfree(Allocs& a, void* p, size_t bytes);
 // Stream-ordered device buffer outside any handle (usable on every stream once this returns).
 int dmalloc_transient(void** p, size_t bytes, cudaStream_t s);
+// Upload and zero fill ordered on the owner's stream s, complete when they return.  Set-up code
+// uses these, never the synchronous cudaMemcpy / cudaMemset: those run on the legacy default
+// stream, which a non-blocking stream does not wait for, so a kernel on such a stream could read
+// a table before its upload had landed.
+int h2d(void* dst, const void* src, size_t bytes, cudaStream_t s);
+int dzero(void* p, size_t bytes, cudaStream_t s);
 // Pinned host scalars, recycled through a process-wide free list (cudaFreeHost may wait for the
 // whole device).
 int pinned_scalars(double** out);
@@ -139,6 +145,9 @@ struct Level {
   int64_t gsm_n[5] = {0, 0, 0, 0, 0};    // groups of 2, 4, 8, other copies; masked single copies
   int64_t gsm_seg[5] = {0, 0, 0, 0, 0};
   int64_t gsm_entries = 0;   // local ids in groups of two or more
+  // [1]: set to SE_ETIMEOUT by a pipelined kernel of this level whose bounded wait expired
+  // (its output is then invalid); read and cleared by level_pipeline_take
+  int* pstatus = nullptr;
 };
 
 // ------------------------------------------------------------------ reduction scratch
@@ -374,7 +383,9 @@ int make_df_geometry(Level& lv, Allocs& allocs, cudaStream_t s);
 inline bool ax_df_route(const Level& lv) {
   return lv.df && lv.Gdf && (ax_eo_supported(lv.p) ? lv.eodf != nullptr : lv.Ddf != nullptr);
 }
-int pipeline_status_take(int* status);
+// SE_ETIMEOUT (and the record cleared) if a pipelined kernel of lv gave up a bounded wait since
+// the last call; synchronises s first.
+int level_pipeline_take(const Level& lv, cudaStream_t s);
 int fdm_elems_per_block(int p, bool fp32);
 size_t fdm_smem_bytes(int p, bool fp32, int ne);
 int fdm_block_threads(int p, bool fp32, int ne);

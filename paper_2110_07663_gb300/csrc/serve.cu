@@ -214,7 +214,8 @@ static void finish_ticket(se_server_s* S, Ticket* t) {
   Resident* r = t->res;
   se_solve_stats st{};
   int rc = graph_solve_result(r->m, r->m->stream, t->req.tol, t->req.maxit, &st);
-  if (coarse_fault_take(r->P->cw, r->m->stream) != SE_OK) rc = SE_ETIMEOUT;
+  if (level_pipeline_take(r->m->fine, r->m->stream) != SE_OK) rc = SE_ETIMEOUT;
+  if (pmg_faults_take(r->P, r->m->stream) != SE_OK) rc = SE_ETIMEOUT;
   if (t->req.x_host && rc != SE_ECUDA)
     if (cudaMemcpy(t->req.x_host, r->x, r->L * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
       rc = SE_ECUDA;

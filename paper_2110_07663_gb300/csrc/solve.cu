@@ -24,7 +24,7 @@ static int ensure_solve_work(se_mesh_s* m, int restart, bool gmres) {
     SE_TRY(dmalloc(m->allocs, &m->gm_y, restart));
     std::vector<double*> zs(restart);
     for (int j = 0; j < restart; ++j) zs[j] = m->gmZ + (size_t)j * L;
-    SE_CUDA(cudaMemcpy(m->gm_zs, zs.data(), restart * sizeof(double*), cudaMemcpyHostToDevice));
+    SE_TRY(h2d(m->gm_zs, zs.data(), restart * sizeof(double*), m->stream));
     m->gm_m = restart;
   }
   return SE_OK;
@@ -202,12 +202,8 @@ extern "C" int se_solve(se_mesh_t m, se_pmg_t P, const double* b, double* x,
   cudaEventSynchronize(m->ev1);
   float ms = 0.f;
   cudaEventElapsedTime(&ms, m->ev0, m->ev1);
-  int pipe = 0;
-  if (pipeline_status_take(&pipe) == SE_OK && pipe != 0) {
-    set_error("se_solve: a pipelined kernel's bounded wait expired (results invalid)");
-    rc = SE_ETIMEOUT;
-  }
-  if (P && coarse_fault_take(P->cw, s) != SE_OK) rc = SE_ETIMEOUT;
+  if (level_pipeline_take(m->fine, s) != SE_OK) rc = SE_ETIMEOUT;
+  if (P && pmg_faults_take(P, s) != SE_OK) rc = SE_ETIMEOUT;
   st.ms_total = ms;
   st.status = rc;
   if (stats) *stats = st;
