@@ -252,6 +252,8 @@ struct CoarseArgs {
   double *x, *r, *u, *p, *q, *s, *z, *w0, *w1, *part;
   unsigned* count;
   int* status;
+  unsigned* flags;             // [nflags] w generations per block (register-resident solver)
+  int nflags;
   unsigned long long* totals;  // iterations and solves, accumulated (null: not counted)
   double tol;
   int maxit;
@@ -378,9 +380,254 @@ __device__ __forceinline__ void coarse_pcg_run(const CoarseArgs<T>& c, unsigned 
   }
 }
 
+// ------------------------------------------------------------------ register-resident variant
+// For a coarse problem with at most one node per thread of its grid.  Block blk owns the
+// contiguous nodes [blk C, blk C + C), C = ceil(n / nb); each thread keeps its CG values in
+// registers and its node's row of Ahat in shared memory (COARSE_ROW_SMEM bytes of dynamic shared
+// memory per block), so per iteration only w travels through global memory.  The
+// synchronisation is split in the way the pipelined method allows: the global sums of an
+// iteration are posted as soon as its updates are done, and while they travel every block forms
+// m = D^-1 w and n = Ahat w, which need only the w of the blocks within reach of the 27-point
+// stencil (per-block flags, not the whole grid).  The iterates are those of coarse_pcg_run; only
+// the order of the partial sums differs (block ranges instead of grid-strided loops).
+
+constexpr size_t COARSE_ROW_SMEM = 27 * CG_THREADS * sizeof(double);
+
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// First half of a summing barrier: the block's sums of v are posted to part[call parity][blk];
+// then (thread 0, release) this block's flag is set to flag_value and its arrival counted.
+// Every write the block made before the call is visible to a block that observes either.
+__device__ __forceinline__ void grid_post3(unsigned* count, unsigned call, unsigned nblocks,
+                                           double* part, double (&v)[3], double* red, unsigned blk,
+                                           unsigned* flag, unsigned flag_value) {
+  block_sum3(v, red);
+  if (threadIdx.x == 0) {
+    double* buf = part + (size_t)(call & 1u) * 4 * nblocks;
+    reinterpret_cast<double2*>(buf)[2 * blk] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(buf)[2 * blk + 1] = make_double2(v[2], 0.0);
+    st_release(flag, flag_value);
+    atomic_add_release(count, 1u);
+  }
+}
+
+// Second half: waits until all nblocks blocks have posted call `call`, then adds their partials
+// in block order (the reduction of grid_sum3) and thread 0 evaluates post(v); every thread gets
+// v and post's value.  False once status[0] is set (an expired wait here or elsewhere).
+template <class Post>
+__device__ bool grid_wait3(unsigned* count, unsigned call, int* status, unsigned nblocks,
+                           long long timeout_ns, const double* part, double (&v)[3],
+                           double& post_value, Post post) {
+  __shared__ double s_out[4];
+  const double* buf = part + (size_t)(call & 1u) * 4 * nblocks;
+  if (threadIdx.x == 0) {
+    const unsigned target = (call + 1u) * nblocks;
+    const long long t0 = global_ns();
+    while ((int)(load_acquire(count) - target) < 0) {
+      if (*(volatile int*)status != 0) break;
+      if (global_ns() - t0 > timeout_ns) {
+        atomicExch(status, SE_ETIMEOUT);
+        break;
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    // all loads of the lane issued together (up to 10 blocks per lane), then summed in order
+    constexpr int UNR = 10;
+    double2 lo[UNR], hi[UNR];
+#pragma unroll
+    for (int i = 0; i < UNR; ++i) {
+      const unsigned k = threadIdx.x + 32u * i;
+      lo[i] = k < nblocks ? __ldcg(reinterpret_cast<const double2*>(buf) + 2 * k) : make_double2(0.0, 0.0);
+      hi[i] = k < nblocks ? __ldcg(reinterpret_cast<const double2*>(buf) + 2 * k + 1) : make_double2(0.0, 0.0);
+    }
+    double s0 = lo[0].x, s1 = lo[0].y, s2 = hi[0].x;
+#pragma unroll
+    for (int i = 1; i < UNR; ++i) {
+      s0 += lo[i].x;
+      s1 += lo[i].y;
+      s2 += hi[i].x;
+    }
+    for (unsigned k = threadIdx.x + 32u * UNR; k < nblocks; k += 32) {
+      const double2 l = __ldcg(reinterpret_cast<const double2*>(buf) + 2 * k);
+      const double2 h = __ldcg(reinterpret_cast<const double2*>(buf) + 2 * k + 1);
+      s0 += l.x;
+      s1 += l.y;
+      s2 += h.x;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      s0 += __shfl_down_sync(0xffffffffu, s0, o);
+      s1 += __shfl_down_sync(0xffffffffu, s1, o);
+      s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    }
+    if (threadIdx.x == 0) {
+      double w[3] = {s0, s1, s2};
+      const double pv = post(w);
+      s_out[0] = w[0];
+      s_out[1] = w[1];
+      s_out[2] = w[2];
+      s_out[3] = pv;
+    }
+  }
+  __syncthreads();
+  v[0] = s_out[0];
+  v[1] = s_out[1];
+  v[2] = s_out[2];
+  post_value = s_out[3];
+  return *(volatile int*)status == 0;
+}
+
+// Waits (bounded) until flags[b] >= want for every block b in [b0, b1]; warp 0 polls.
+__device__ bool wait_flags(const unsigned* flags, int b0, int b1, unsigned want, int* status,
+                           long long timeout_ns) {
+  if (threadIdx.x < 32) {
+    const long long t0 = global_ns();
+    for (int b = b0 + (int)threadIdx.x; b <= b1; b += 32) {
+      while ((int)(load_acquire(flags + b) - want) < 0) {
+        if (*(volatile int*)status != 0) break;
+        if (global_ns() - t0 > timeout_ns) {
+          atomicExch(status, SE_ETIMEOUT);
+          break;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  return *(volatile int*)status == 0;
+}
+
+// Neighbour (slot sl of the 27-point row) of node g, clamped into [0, n): a slot outside the
+// lattice holds 0 in Ahat, so the clamped read adds exactly 0.
+__device__ __forceinline__ int coarse_nbr(int g, int sl, int n, int NX, int NXY) {
+  const int dI = sl % 3 - 1, dJ = (sl / 3) % 3 - 1, dK = sl / 9 - 1;
+  return min(max(g + dI + NX * dJ + NXY * dK, 0), n - 1);
+}
+
+template <class T>
+__device__ __forceinline__ void coarse_pcg_reg(const CoarseArgs<T>& c, unsigned blk, unsigned nb) {
+  __shared__ double red[3 * CG_THREADS];
+  const int n = c.n, NX = c.NX, NXY = c.NX * c.NY;
+  const int C = (int)((n + (int)nb - 1) / (int)nb);
+  const int g0 = (int)blk * C;
+  const int g = g0 + (int)threadIdx.x;
+  const bool act = (int)threadIdx.x < C && g < n;
+  // blocks whose nodes the rows of this block reach
+  const int reach = NXY + NX + 1;
+  const int glast = min(n, g0 + C) - 1;
+  const int b0 = max(0, g0 - reach) / C;
+  const int b1 = min((int)nb - 1, (glast + reach) / C);
+  unsigned* myflag = c.flags + blk;
+  extern __shared__ double row_sm[];  // [27][CG_THREADS]
+  double* row = row_sm + threadIdx.x;
+  double d = 0.0, r = 0.0, u = 0.0, x = 0.0, p = 0.0, q = 0.0, sv = 0.0, z = 0.0, w = 0.0;
+  if (act) {
+#pragma unroll
+    for (int sl = 0; sl < 27; ++sl) row[sl * CG_THREADS] = c.Ah[(int64_t)sl * n + g];
+    d = c.dinv[g];
+    r = (double)c.rin[c.g2l[g]];
+    u = d * r;
+    // w = A u = Ahat r, the neighbours' r straight from the input
+    double acc = 0.0;
+#pragma unroll
+    for (int sl = 0; sl < 27; ++sl)
+      acc = fma(row[sl * CG_THREADS], (double)c.rin[c.g2l[coarse_nbr(g, sl, n, NX, NXY)]], acc);
+    w = acc;
+    c.w0[g] = w;
+  }
+  double v[3] = {r * u, w * u, r * r};
+  unsigned call = 0;
+  grid_post3(c.count, call, nb, c.part, v, red, blk, myflag, 1u);
+  int it = 0;
+  double gamma = 0.0, alpha = 0.0, tol2 = 0.0;
+  bool ok = true;
+  for (;;) {
+    // m = D^-1 w, n = Ahat w on this iteration's w (neighbours: generation it + 1 published)
+    ok = wait_flags(c.flags, b0, b1, (unsigned)(it + 1), c.status, c.timeout_ns);
+    if (!ok) break;
+    const double* wr = (it & 1) ? c.w1 : c.w0;
+    double m = 0.0, nv = 0.0;
+    if (act) {
+      m = d * w;
+      double acc = 0.0;
+#pragma unroll
+      for (int sl = 0; sl < 27; ++sl)
+        acc = fma(row[sl * CG_THREADS], wr[coarse_nbr(g, sl, n, NX, NXY)], acc);
+      nv = acc;
+    }
+    // (gamma, delta, (r, r)) of the current iterate -> (alpha, beta, (r, r)); post returns gamma
+    const double g_prev = gamma, a_prev = alpha;
+    const bool first = it == 0;
+    ok = grid_wait3(c.count, call++, c.status, nb, c.timeout_ns, c.part, v, gamma,
+                    [=](double (&s)[3]) {
+                      const double gm = s[0], dl = s[1];
+                      const double be = first ? 0.0 : gm / g_prev;
+                      s[0] = first ? gm / dl : gm / (dl - be * gm / a_prev);
+                      s[1] = be;
+                      return gm;
+                    });
+    if (!ok) break;
+    if (first) {
+      tol2 = c.tol * c.tol * v[2];
+      if (!(v[2] > 0.0)) break;       // b = 0: x = 0
+    } else if (v[2] <= tol2) {
+      break;                          // (r, r) of the last update
+    }
+    if (it >= c.maxit) break;
+    alpha = v[0];
+    const double beta = v[1];
+    if (act) {
+      z = first ? nv : fma(beta, z, nv);
+      q = first ? m : fma(beta, q, m);
+      sv = first ? w : fma(beta, sv, w);
+      p = first ? u : fma(beta, p, u);
+      x = fma(alpha, p, x);
+      r = fma(-alpha, sv, r);
+      u = fma(-alpha, q, u);
+      w = fma(-alpha, z, w);
+      ((it & 1) ? c.w0 : c.w1)[g] = w;  // the buffer read one iteration ago
+    }
+    v[0] = r * u;
+    v[1] = w * u;
+    v[2] = r * r;
+    ++it;
+    grid_post3(c.count, call, nb, c.part, v, red, blk, myflag, (unsigned)(it + 1));
+  }
+  // x to memory, one more summing barrier (nothing summed), then each local copy takes its node
+  if (ok) {
+    if (act) c.x[g] = x;
+    double zero[3] = {0.0, 0.0, 0.0}, unused;
+    grid_post3(c.count, call, nb, c.part, zero, red, blk, myflag, 0xffffffffu);
+    ok = grid_wait3(c.count, call++, c.status, nb, c.timeout_ns, c.part, zero, unused,
+                    [](double (&)[3]) { return 0.0; });
+  }
+  if (ok) {
+    const int stride = (int)nb * CG_THREADS;
+    for (int l = (int)blk * CG_THREADS + (int)threadIdx.x; l < c.L; l += stride)
+      c.xout[l] = (T)__ldcg(c.x + c.l2g[l]);
+  }
+  if (blk == 0 && threadIdx.x == 0) {
+    c.status[1] = it;
+    if (c.totals) {
+      atomicAdd(c.totals, (unsigned long long)it);
+      atomicAdd(c.totals + 1, 1ULL);
+      if (!ok) atomicAdd(c.totals + 2, 1ULL);  // results of this solve are invalid
+    }
+  }
+}
+
 template <class T>
 __global__ void __launch_bounds__(CG_THREADS) coarse_pcg_kernel(CoarseArgs<T> c) {
   coarse_pcg_run(c, blockIdx.x, gridDim.x);
+}
+
+// One node per thread (n <= gridDim.x * CG_THREADS); launched with COARSE_ROW_SMEM bytes of
+// dynamic shared memory.
+template <class T>
+__global__ void __launch_bounds__(CG_THREADS) coarse_reg_kernel(CoarseArgs<T> c) {
+  coarse_pcg_reg(c, blockIdx.x, gridDim.x);
 }
 
 // Many independent coarse problems in one cooperative launch: problem m runs on blocks
@@ -392,7 +639,11 @@ __global__ void __launch_bounds__(CG_THREADS) coarse_group_kernel(const CoarseAr
   int m = 0;
   while (m + 1 < n && boff[m + 1] <= (int)blockIdx.x) ++m;
   const CoarseArgs<T> c = args[m];
-  coarse_pcg_run(c, blockIdx.x - (unsigned)boff[m], (unsigned)(boff[m + 1] - boff[m]));
+  const unsigned nb = (unsigned)(boff[m + 1] - boff[m]);
+  if ((int64_t)c.n <= (int64_t)nb * CG_THREADS)  // uniform over the member's blocks
+    coarse_pcg_reg(c, blockIdx.x - (unsigned)boff[m], nb);
+  else
+    coarse_pcg_run(c, blockIdx.x - (unsigned)boff[m], nb);
 }
 
 __global__ void coarse_group_reset_kernel(const CoarseArgs<double>* __restrict__ a64,
@@ -401,8 +652,26 @@ __global__ void coarse_group_reset_kernel(const CoarseArgs<double>* __restrict__
   if (m >= n) return;
   unsigned* count = a64 ? a64[m].count : a32[m].count;
   int* status = a64 ? a64[m].status : a32[m].status;
+  unsigned* flags = a64 ? a64[m].flags : a32[m].flags;
+  const int nflags = a64 ? a64[m].nflags : a32[m].nflags;
   count[0] = count[1] = 0u;
   status[0] = status[1] = 0;
+  for (int b = 0; b < nflags; ++b) flags[b] = 0u;
+}
+
+// The row-resident kernels take more than the default 48 KB of dynamic shared memory only if
+// COARSE_ROW_SMEM grows past it; the attribute is set once per process (per device in use).
+static int coarse_kernel_attrs() {
+  static std::once_flag once;
+  static cudaError_t err = cudaSuccess;
+  std::call_once(once, [] {
+    for (const void* k : {(const void*)coarse_reg_kernel<double>, (const void*)coarse_reg_kernel<float>,
+                          (const void*)coarse_group_kernel<double>, (const void*)coarse_group_kernel<float>})
+      if (err == cudaSuccess)
+        err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)COARSE_ROW_SMEM);
+  });
+  SE_CUDA(err);
+  return SE_OK;
 }
 
 // Partial sums of the summing barrier: two buffers of 4 doubles per block.
@@ -416,9 +685,15 @@ int coarse_alloc(const Level& lv, Allocs& allocs, CoarseWork* w) {
   SE_CUDA(cudaGetDevice(&dev));
   SE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   SE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_pcg_kernel<double>, CG_THREADS, 0));
-  int per_sm32 = 0;
-  SE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm32, coarse_pcg_kernel<float>, CG_THREADS, 0));
-  if (per_sm32 < per_sm) per_sm = per_sm32;
+  // every coarse kernel must fit the grid chosen here (the solve picks one by the node count)
+  SE_TRY(coarse_kernel_attrs());
+  for (const void* k : {(const void*)coarse_pcg_kernel<float>, (const void*)coarse_reg_kernel<double>,
+                        (const void*)coarse_reg_kernel<float>}) {
+    int o = 0;
+    const size_t dyn = k == (const void*)coarse_pcg_kernel<float> ? 0 : COARSE_ROW_SMEM;
+    SE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, CG_THREADS, dyn));
+    if (o < per_sm) per_sm = o;
+  }
   SE_CHECK(per_sm >= 1, SE_ECUDA, "coarse solver kernel cannot be resident");
   // one point per thread where possible; a grid of more than half the SMs is rounded up to a
   // multiple of the SM count so that the FP64 work spreads evenly
@@ -435,6 +710,8 @@ int coarse_alloc(const Level& lv, Allocs& allocs, CoarseWork* w) {
   SE_TRY(dmalloc(allocs, &w->status, 2));
   SE_TRY(dzero(w->bar, 2 * sizeof(unsigned), allocs.stream));
   SE_TRY(dzero(w->status, 2 * sizeof(int), allocs.stream));
+  SE_TRY(dmalloc(allocs, &w->flags, (size_t)w->nblocks));
+  SE_TRY(dzero(w->flags, (size_t)w->nblocks * sizeof(unsigned), allocs.stream));
   SE_TRY(dmalloc(allocs, &w->totals, 3));
   SE_TRY(dzero(w->totals, 3 * sizeof(unsigned long long), allocs.stream));
   return SE_OK;
@@ -466,6 +743,8 @@ int coarse_solve(const Level& lv, CoarseWork& w, const T* r_l, T* x_l, double to
   a.part = w.partial;
   a.count = w.bar;
   a.status = w.status;
+  a.flags = w.flags;
+  a.nflags = w.nblocks;
   a.totals = w.totals;
   a.tol = tol;
   a.maxit = maxit;
@@ -473,9 +752,13 @@ int coarse_solve(const Level& lv, CoarseWork& w, const T* r_l, T* x_l, double to
   ProfScope prof(SE_K_COARSE, s, (double)lv.n_global, 0.0, 0.0);
   SE_CUDA(cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), s));
   SE_CUDA(cudaMemsetAsync(w.status, 0, 2 * sizeof(int), s));
+  const bool reg = w.flags && lv.n_global <= (int64_t)w.nblocks * CG_THREADS;
+  if (reg) SE_CUDA(cudaMemsetAsync(w.flags, 0, (size_t)w.nblocks * sizeof(unsigned), s));
   void* args[] = {&a};
-  SE_CUDA(cudaLaunchCooperativeKernel((const void*)coarse_pcg_kernel<T>, dim3(w.nblocks),
-                                      dim3(CG_THREADS), args, 0, s));
+  SE_TRY(coarse_kernel_attrs());
+  SE_CUDA(cudaLaunchCooperativeKernel(reg ? (const void*)coarse_reg_kernel<T> : (const void*)coarse_pcg_kernel<T>,
+                                      dim3(w.nblocks), dim3(CG_THREADS), args,
+                                      reg ? COARSE_ROW_SMEM : 0, s));
   return SE_OK;
 }
 
@@ -506,6 +789,8 @@ static CoarseArgs<T> coarse_args(const Level& lv, const CoarseWork& w, const T* 
   a.part = w.partial;
   a.count = w.bar;
   a.status = w.status;
+  a.flags = w.flags;
+  a.nflags = w.nblocks;
   a.totals = w.totals;
   a.tol = tol;
   a.maxit = maxit;
@@ -520,7 +805,9 @@ static int coarse_group_setup_t(CoarseGroup* g, const Level* const* lv, CoarseWo
   int dev = 0, sms = 0, per_sm = 0;
   SE_CUDA(cudaGetDevice(&dev));
   SE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  SE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_group_kernel<T>, CG_THREADS, 0));
+  SE_TRY(coarse_kernel_attrs());
+  SE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_group_kernel<T>, CG_THREADS,
+                                                        COARSE_ROW_SMEM));
   SE_CHECK(per_sm >= 1, SE_ECUDA, "grouped coarse solver kernel cannot be resident");
   const int cap = sms * per_sm;
   SE_CHECK(n <= cap, SE_EINVAL, "grouped coarse solve: %d problems above the %d resident blocks", n, cap);
@@ -595,8 +882,9 @@ int coarse_group_solve(const CoarseGroup& g, cudaStream_t s) {
   const int* boff = g.boff;
   int n = g.n;
   void* a[] = {(void*)&args, (void*)&boff, (void*)&n};
+  SE_TRY(coarse_kernel_attrs());
   SE_CUDA(cudaLaunchCooperativeKernel((const void*)coarse_group_kernel<T>, dim3(g.nblocks),
-                                      dim3(CG_THREADS), a, 0, s));
+                                      dim3(CG_THREADS), a, COARSE_ROW_SMEM, s));
   return SE_OK;
 }
 template int coarse_group_solve<double>(const CoarseGroup&, cudaStream_t);
@@ -667,7 +955,9 @@ namespace se {
 constexpr int64_t NOALLOC_MAX_N = 1 << 17;        // 131072 coarse (p = 1) global nodes
 constexpr int NOALLOC_MAX_BLOCKS = 1024;
 constexpr int NOALLOC_VECTORS = 9;
-constexpr int64_t NOALLOC_WORDS = NOALLOC_VECTORS * NOALLOC_MAX_N + 8 * NOALLOC_MAX_BLOCKS + 2;
+// vectors, partial sums, barrier and status words, per-block flags
+constexpr int64_t NOALLOC_WORDS =
+    NOALLOC_VECTORS * NOALLOC_MAX_N + 8 * NOALLOC_MAX_BLOCKS + 2 + NOALLOC_MAX_BLOCKS / 2;
 static __device__ __align__(256) double g_coarse_scratch[NOALLOC_WORDS];
 
 static std::mutex g_noalloc_mu;
@@ -710,7 +1000,8 @@ extern "C" int se_pmg_coarse_solve_noalloc(se_pmg_t P, const double* r, double* 
   w.partial = base + NOALLOC_VECTORS * NOALLOC_MAX_N;  // coarse_partial_doubles(nblocks) <= 8 * 1024
   w.bar = reinterpret_cast<unsigned*>(base + NOALLOC_VECTORS * NOALLOC_MAX_N + 8 * NOALLOC_MAX_BLOCKS);
   w.status = reinterpret_cast<int*>(w.bar + 2);
-  // coarse_solve zeroes the barrier and status words before its launch; the vectors are fully
+  w.flags = reinterpret_cast<unsigned*>(base + NOALLOC_VECTORS * NOALLOC_MAX_N + 8 * NOALLOC_MAX_BLOCKS + 2);
+  // coarse_solve zeroes the barrier, status and flag words before its launch; the vectors are fully
   // written before they are read
   SE_TRY(coarse_solve<double>(c, w, r, x, P->desc.coarse_tol, P->desc.coarse_maxit, s));
   int h[2] = {0, 0};

@@ -305,6 +305,9 @@ struct CoarseWork {
   unsigned* bar;    // [2]: arrival count (monotonic within a launch), unused
   int* status;      // [2]: error flag, iterations
   int nblocks;
+  // [nblocks]: per block, how many w vectors it has published (register-resident solver; zeroed
+  // before each launch)
+  unsigned* flags = nullptr;
   // [3]: iterations and solves since the last reset, and solves whose bounded waits expired
   // (kept until read); may be null
   unsigned long long* totals = nullptr;

@@ -13,7 +13,7 @@ import pytest
 
 import oracle as o
 import workloads as wl
-from tests.gpu_common import Case, rel_err
+from tests.gpu_common import Case, gpu, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -277,3 +277,32 @@ def test_coarse_stats_count_solves_and_iterations():
     finally:
         se.se_pmg_destroy(P)
         c.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("nel", [(37, 37, 37), (43, 43, 43)])
+def test_large_coarse_solves_against_the_oracle(nel):
+    """The coarse Jacobi-PCG at sizes where the solver's two kernels take over: 38^3 = 54,872
+    nodes run one node per thread (row of Ahat in shared memory, per-block neighbour flags, a
+    grid of two blocks per SM); 44^3 = 85,184 nodes exceed the co-resident threads and run the
+    grid-strided kernel.  Iterations within one of the oracle's, solution to 1e-8."""
+    torch, se = gpu()
+    V = wl.vertex_lattice(nel, 0.05, 2)
+    m = se.se_mesh_create(nel, 2, vertex_xyz=V, deform_amp=wl.DEFORM_AMP)
+    P = se.se_pmg_setup(m, se.pmg_desc((2, 1), se.SE_SMOOTH_JACOBI, 1))
+    try:
+        lc = o.make_level(V, nel, 1, ("D",) * 6, wl.DEFORM_AMP)
+        lc.extra["diag"] = o.jacobi_diag(lc)
+        coarse = o.PMG(levels=[lc], smoother="jacobi", order=[], bounds=[], lam=[])
+        b = lc.mask * o.from_global(lc, wl.random_lvector(lc.n_global, 9))
+        dev = torch.device("cuda:0")
+        x = torch.empty(lc.gid.size, dtype=torch.float64, device=dev)
+        it = se.se_pmg_coarse_solve(P, torch.from_numpy(b.reshape(-1).copy()).to(dev), x)
+        xref = o.coarse_solve(coarse, b)
+        it_ref = coarse.coarse_iters[-1]
+        assert abs(it - it_ref) <= 1
+        if it == it_ref:
+            assert rel_err(x.cpu().numpy().reshape(lc.gid.shape), xref) <= 1e-8
+    finally:
+        se.se_pmg_destroy(P)
+        se.se_mesh_destroy(m)
