@@ -397,13 +397,63 @@ __device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Block sums of three values in thread 0 by shallow trees: every warp adds its lanes by a
+// five-level shuffle tree (all warps at once), then warp 0 adds the eight warp sums by a
+// three-level tree.  A fixed order (deterministic).  On this part a chain of dependent FP64
+// additions costs far more than their count suggests (the FP64 pipe takes 2 lanes per clock per
+// SM), so the depth of the chain, not the number of additions, is what is kept small.
+__device__ __forceinline__ void block_sum3_tree(double (&v)[3], double* red) {
+  static_assert(CG_THREADS == 256, "eight warps per block");
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v[0] += __shfl_down_sync(0xffffffffu, v[0], o);
+    v[1] += __shfl_down_sync(0xffffffffu, v[1], o);
+    v[2] += __shfl_down_sync(0xffffffffu, v[2], o);
+  }
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    red[wid] = v[0];
+    red[8 + wid] = v[1];
+    red[16 + wid] = v[2];
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double a0 = lane < 8 ? red[lane] : 0.0, a1 = lane < 8 ? red[8 + lane] : 0.0;
+    double a2 = lane < 8 ? red[16 + lane] : 0.0;
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+      a0 += __shfl_down_sync(0xffffffffu, a0, o);
+      a1 += __shfl_down_sync(0xffffffffu, a1, o);
+      a2 += __shfl_down_sync(0xffffffffu, a2, o);
+    }
+    v[0] = a0;
+    v[1] = a1;
+    v[2] = a2;
+  }
+}
+
+// 1/x by Newton's iteration r <- r (2 - x r) from the FP32 reciprocal of x's mantissa (two steps
+// take the 24-bit estimate past FP64 precision; the exponent is handled exactly by frexp/ldexp).
+// Zero, infinite and NaN arguments take the IEEE division.  A few dependent FP64 operations
+// instead of the longer exact-division sequence: the coarse iteration evaluates these on its
+// critical path.
+__device__ __forceinline__ double recip_newton(double x) {
+  if (!(fabs(x) > 0.0) || isinf(x)) return 1.0 / x;
+  int e;
+  const double m = frexp(x, &e);  // x = m 2^e, 0.5 <= |m| < 1
+  double r = (double)__frcp_rn((float)m);
+  r = r * fma(-m, r, 2.0);
+  r = r * fma(-m, r, 2.0);
+  return ldexp(r, -e);
+}
+
 // First half of a summing barrier: the block's sums of v are posted to part[call parity][blk];
 // then (thread 0, release) this block's flag is set to flag_value and its arrival counted.
 // Every write the block made before the call is visible to a block that observes either.
 __device__ __forceinline__ void grid_post3(unsigned* count, unsigned call, unsigned nblocks,
                                            double* part, double (&v)[3], double* red, unsigned blk,
                                            unsigned* flag, unsigned flag_value) {
-  block_sum3(v, red);
+  block_sum3_tree(v, red);
   if (threadIdx.x == 0) {
     double* buf = part + (size_t)(call & 1u) * 4 * nblocks;
     reinterpret_cast<double2*>(buf)[2 * blk] = make_double2(v[0], v[1]);
@@ -414,12 +464,13 @@ __device__ __forceinline__ void grid_post3(unsigned* count, unsigned call, unsig
 }
 
 // Second half: waits until all nblocks blocks have posted call `call`, then adds their partials
-// in block order (the reduction of grid_sum3) and thread 0 evaluates post(v); every thread gets
-// v and post's value.  False once status[0] is set (an expired wait here or elsewhere).
+// in a fixed order (thread t: blocks t, t + 256, ...; then the trees of block_sum3_tree) and
+// thread 0 evaluates post(v); every thread gets v and post's value.  False once status[0] is set
+// (an expired wait here or elsewhere).
 template <class Post>
 __device__ bool grid_wait3(unsigned* count, unsigned call, int* status, unsigned nblocks,
                            long long timeout_ns, const double* part, double (&v)[3],
-                           double& post_value, Post post) {
+                           double& post_value, double* red, Post post) {
   __shared__ double s_out[4];
   const double* buf = part + (size_t)(call & 1u) * 4 * nblocks;
   if (threadIdx.x == 0) {
@@ -434,43 +485,22 @@ __device__ bool grid_wait3(unsigned* count, unsigned call, int* status, unsigned
     }
   }
   __syncthreads();
-  if (threadIdx.x < 32) {
-    // all loads of the lane issued together (up to 10 blocks per lane), then summed in order
-    constexpr int UNR = 10;
-    double2 lo[UNR], hi[UNR];
-#pragma unroll
-    for (int i = 0; i < UNR; ++i) {
-      const unsigned k = threadIdx.x + 32u * i;
-      lo[i] = k < nblocks ? __ldcg(reinterpret_cast<const double2*>(buf) + 2 * k) : make_double2(0.0, 0.0);
-      hi[i] = k < nblocks ? __ldcg(reinterpret_cast<const double2*>(buf) + 2 * k + 1) : make_double2(0.0, 0.0);
-    }
-    double s0 = lo[0].x, s1 = lo[0].y, s2 = hi[0].x;
-#pragma unroll
-    for (int i = 1; i < UNR; ++i) {
-      s0 += lo[i].x;
-      s1 += lo[i].y;
-      s2 += hi[i].x;
-    }
-    for (unsigned k = threadIdx.x + 32u * UNR; k < nblocks; k += 32) {
-      const double2 l = __ldcg(reinterpret_cast<const double2*>(buf) + 2 * k);
-      const double2 h = __ldcg(reinterpret_cast<const double2*>(buf) + 2 * k + 1);
-      s0 += l.x;
-      s1 += l.y;
-      s2 += h.x;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      s0 += __shfl_down_sync(0xffffffffu, s0, o);
-      s1 += __shfl_down_sync(0xffffffffu, s1, o);
-      s2 += __shfl_down_sync(0xffffffffu, s2, o);
-    }
-    if (threadIdx.x == 0) {
-      double w[3] = {s0, s1, s2};
-      const double pv = post(w);
-      s_out[0] = w[0];
-      s_out[1] = w[1];
-      s_out[2] = w[2];
-      s_out[3] = pv;
-    }
+  // thread t takes blocks t, t + 256, ... (one load round), then the trees of block_sum3_tree
+  double w[3] = {0.0, 0.0, 0.0};
+  for (unsigned k = threadIdx.x; k < nblocks; k += CG_THREADS) {
+    const double2 l = __ldcg(reinterpret_cast<const double2*>(buf) + 2 * k);
+    const double2 h = __ldcg(reinterpret_cast<const double2*>(buf) + 2 * k + 1);
+    w[0] += l.x;
+    w[1] += l.y;
+    w[2] += h.x;
+  }
+  block_sum3_tree(w, red);
+  if (threadIdx.x == 0) {
+    const double pv = post(w);
+    s_out[0] = w[0];
+    s_out[1] = w[1];
+    s_out[2] = w[2];
+    s_out[3] = pv;
   }
   __syncthreads();
   v[0] = s_out[0];
@@ -542,6 +572,7 @@ __device__ __forceinline__ void coarse_pcg_reg(const CoarseArgs<T>& c, unsigned 
   grid_post3(c.count, call, nb, c.part, v, red, blk, myflag, 1u);
   int it = 0;
   double gamma = 0.0, alpha = 0.0, tol2 = 0.0;
+  double R = 0.0, K = 0.0;  // thread 0: 1 / gamma_prev, 1 / (gamma_prev alpha_prev)
   bool ok = true;
   for (;;) {
     // m = D^-1 w, n = Ahat w on this iteration's w (neighbours: generation it + 1 published)
@@ -557,14 +588,16 @@ __device__ __forceinline__ void coarse_pcg_reg(const CoarseArgs<T>& c, unsigned 
         acc = fma(row[sl * CG_THREADS], wr[coarse_nbr(g, sl, n, NX, NXY)], acc);
       nv = acc;
     }
-    // (gamma, delta, (r, r)) of the current iterate -> (alpha, beta, (r, r)); post returns gamma
-    const double g_prev = gamma, a_prev = alpha;
+    // (gamma, delta, (r, r)) of the current iterate -> (alpha, beta, (r, r)); post returns gamma.
+    // beta = gamma / gamma_prev and alpha = gamma / (delta - beta gamma / alpha_prev) with the
+    // previous iteration's reciprocals, so one reciprocal is on the critical path
     const bool first = it == 0;
-    ok = grid_wait3(c.count, call++, c.status, nb, c.timeout_ns, c.part, v, gamma,
-                    [=](double (&s)[3]) {
+    ok = grid_wait3(c.count, call++, c.status, nb, c.timeout_ns, c.part, v, gamma, red,
+                    [&](double (&s)[3]) {
                       const double gm = s[0], dl = s[1];
-                      const double be = first ? 0.0 : gm / g_prev;
-                      s[0] = first ? gm / dl : gm / (dl - be * gm / a_prev);
+                      const double be = first ? 0.0 : gm * R;
+                      const double al = gm * recip_newton(first ? dl : fma(-gm * gm, K, dl));
+                      s[0] = al;
                       s[1] = be;
                       return gm;
                     });
@@ -577,6 +610,10 @@ __device__ __forceinline__ void coarse_pcg_reg(const CoarseArgs<T>& c, unsigned 
     }
     if (it >= c.maxit) break;
     alpha = v[0];
+    if (threadIdx.x == 0) {  // for the next iteration, while the other threads update
+      R = recip_newton(gamma);
+      K = R * recip_newton(alpha);
+    }
     const double beta = v[1];
     if (act) {
       z = first ? nv : fma(beta, z, nv);
@@ -600,7 +637,7 @@ __device__ __forceinline__ void coarse_pcg_reg(const CoarseArgs<T>& c, unsigned 
     if (act) c.x[g] = x;
     double zero[3] = {0.0, 0.0, 0.0}, unused;
     grid_post3(c.count, call, nb, c.part, zero, red, blk, myflag, 0xffffffffu);
-    ok = grid_wait3(c.count, call++, c.status, nb, c.timeout_ns, c.part, zero, unused,
+    ok = grid_wait3(c.count, call++, c.status, nb, c.timeout_ns, c.part, zero, unused, red,
                     [](double (&)[3]) { return 0.0; });
   }
   if (ok) {
