@@ -432,21 +432,6 @@ __device__ __forceinline__ void block_sum3_tree(double (&v)[3], double* red) {
   }
 }
 
-// 1/x by Newton's iteration r <- r (2 - x r) from the FP32 reciprocal of x's mantissa (two steps
-// take the 24-bit estimate past FP64 precision; the exponent is handled exactly by frexp/ldexp).
-// Zero, infinite and NaN arguments take the IEEE division.  A few dependent FP64 operations
-// instead of the longer exact-division sequence: the coarse iteration evaluates these on its
-// critical path.
-__device__ __forceinline__ double recip_newton(double x) {
-  if (!(fabs(x) > 0.0) || isinf(x)) return 1.0 / x;
-  int e;
-  const double m = frexp(x, &e);  // x = m 2^e, 0.5 <= |m| < 1
-  double r = (double)__frcp_rn((float)m);
-  r = r * fma(-m, r, 2.0);
-  r = r * fma(-m, r, 2.0);
-  return ldexp(r, -e);
-}
-
 // First half of a summing barrier: the block's sums of v are posted to part[call parity][blk];
 // then (thread 0, release) this block's flag is set to flag_value and its arrival counted.
 // Every write the block made before the call is visible to a block that observes either.
@@ -590,13 +575,14 @@ __device__ __forceinline__ void coarse_pcg_reg(const CoarseArgs<T>& c, unsigned 
     }
     // (gamma, delta, (r, r)) of the current iterate -> (alpha, beta, (r, r)); post returns gamma.
     // beta = gamma / gamma_prev and alpha = gamma / (delta - beta gamma / alpha_prev) with the
-    // previous iteration's reciprocals, so one reciprocal is on the critical path
+    // previous iteration's reciprocals, so one division is on the critical path (an FP64
+    // division is a long chain of dependent FP64 operations on this part)
     const bool first = it == 0;
     ok = grid_wait3(c.count, call++, c.status, nb, c.timeout_ns, c.part, v, gamma, red,
                     [&](double (&s)[3]) {
                       const double gm = s[0], dl = s[1];
                       const double be = first ? 0.0 : gm * R;
-                      const double al = gm * recip_newton(first ? dl : fma(-gm * gm, K, dl));
+                      const double al = gm / (first ? dl : fma(-gm * gm, K, dl));
                       s[0] = al;
                       s[1] = be;
                       return gm;
@@ -611,8 +597,8 @@ __device__ __forceinline__ void coarse_pcg_reg(const CoarseArgs<T>& c, unsigned 
     if (it >= c.maxit) break;
     alpha = v[0];
     if (threadIdx.x == 0) {  // for the next iteration, while the other threads update
-      R = recip_newton(gamma);
-      K = R * recip_newton(alpha);
+      R = 1.0 / gamma;
+      K = R / alpha;
     }
     const double beta = v[1];
     if (act) {
