@@ -477,6 +477,62 @@ int gs_apply(const Level& lv, T* u, bool mask, cudaStream_t s) {
   }
 }
 
+// ------------------------------------------------------------------ folded FP64 operator
+// The even-odd kernel sums the x-interfaces inside its blocks and masks (ax_local_eo_fold); the y
+// and z sweeps follow, then the x-interfaces between blocks.  The order of the three direction
+// sums does not change the set each copy adds up (see above), and each pair still writes one sum
+// to both sides, so all copies of a node keep the same bits.  This removes the x sweep, which
+// reads and writes every sector of the vector (an x-interface copy is the first or last value of
+// a row of N), from the operator applications of the solve.
+bool ax_fold_ok(const Level& lv) {
+  return !ax_df_route(lv) && lv.eo64 && ax_eo_supported(lv.p) && !lv.gsm_ids && lv.nel[0] >= 1 &&
+         lv.nel[1] >= 1 && lv.nel[2] >= 1 && lv.pflag;
+}
+
+template <int N>
+static int gs_after_fold(const Level& lv, double* y, int NE, cudaStream_t s) {
+  const int nx = lv.nel[0], ny = lv.nel[1], nz = lv.nel[2];
+  constexpr int N2 = N * N;
+  const int var = prof_variant<double>(lv.p);
+  if (ny > 1) {
+    const int64_t n = (int64_t)N2 * nx * (ny - 1) * nz;  // interface pairs
+    ProfScope prof(SE_K_GS, s, (double)n, 4.0 * n * sizeof(double), (double)n, var);
+    gs_sweep_y<double, N><<<grid_for((n + GS_YZ_PAIRS - 1) / GS_YZ_PAIRS, 256), 256, 0, s>>>(nx, ny, nz, y);
+    SE_LAUNCH_CHECK();
+  }
+  if (nz > 1) {
+    const int64_t n = (int64_t)N2 * nx * ny * (nz - 1);
+    ProfScope prof(SE_K_GS, s, (double)n, 4.0 * n * sizeof(double), (double)n, var);
+    gs_sweep_z<double, N><<<grid_for((n + GS_YZ_PAIRS - 1) / GS_YZ_PAIRS, 256), 256, 0, s>>>(nx, ny, nz, y);
+    SE_LAUNCH_CHECK();
+  }
+  const int64_t nbnd = (lv.E + NE - 1) / NE - 1;
+  if (nx > 1 && nbnd > 0) {
+    const double n = (double)nbnd * N2;  // at most this many pairs
+    ProfScope prof(SE_K_GS, s, n, 4.0 * n * sizeof(double), n, var);
+    SE_TRY(gs_fold_fixup(lv, y, NE, s));
+  }
+  return SE_OK;
+}
+
+int ax_apply_folded(const Level& lv, const double* u, double* y, const double* b, cudaStream_t s) {
+  const int NE = ax_elems_per_block(lv.p, false);
+  {
+    const double pts = (double)lv.L;
+    ProfScope prof(SE_K_AX, s, pts, pts * ((b ? 9.0 : 8.0) * sizeof(double) + 1.0),
+                   pts * (12.0 * lv.N + 15.0), prof_variant<double>(lv.p));
+    SE_TRY(ax_local_eo_fold(lv, u, y, b, NE, s));
+  }
+  switch (lv.N) {
+    case 2: return gs_after_fold<2>(lv, y, NE, s);
+    case 4: return gs_after_fold<4>(lv, y, NE, s);
+    case 6: return gs_after_fold<6>(lv, y, NE, s);
+    case 8: return gs_after_fold<8>(lv, y, NE, s);
+    case 10: return gs_after_fold<10>(lv, y, NE, s);
+    default: set_error("ax_apply_folded: unsupported N=%d", lv.N); return SE_EINVAL;
+  }
+}
+
 template <typename T>
 __global__ void mask_kernel(int64_t L, const uint8_t* __restrict__ pflag, T* __restrict__ u) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

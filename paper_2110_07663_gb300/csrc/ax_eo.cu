@@ -87,13 +87,18 @@ __device__ __forceinline__ void eo_apply(const T* __restrict__ Ep, const T* __re
 }
 
 // tables: [0] Ep(D), [1] Om(D), [2] Ep(D^T), [3] Om(D^T), each H*H
-template <int N, typename T>
+// FOLD (T = double): the block's elements are consecutive in the element numbering, so
+// neighbours along x (same row of the lattice, nx elements per row) are usually in the same
+// block.  The kernel then also does the x part of QQ^T for them: both copies of each such
+// x-interface node get left + right (the same bits on both sides), and it applies the Dirichlet
+// mask (point flags); the x-interfaces between consecutive blocks are left to gs_fold_fixup_x.
+template <int N, typename T, bool FOLD = false>
 __global__ void __launch_bounds__(512) ax_eo_kernel(int64_t E, int NE, const double* __restrict__ u,
                                                     const T* __restrict__ G, int64_t L,
                                                     const T* __restrict__ tables,
                                                     double* __restrict__ y,
                                                     const uint8_t* __restrict__ pflag,
-                                                    const double* __restrict__ sub) {
+                                                    const double* __restrict__ sub, int nx = 0) {
   constexpr int N2 = N * N, N3 = N * N * N, H = N / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tab = reinterpret_cast<T*>(smem_raw);                    // 4 H^2
@@ -146,11 +151,74 @@ __global__ void __launch_bounds__(512) ax_eo_kernel(int64_t E, int NE, const dou
   __syncthreads();
   if (valid) eo_apply<N, true>(EpT, OmT, st, sy, a + N * b, N2);
   __syncthreads();
-  if (valid) {
+  if constexpr (FOLD) {
+    static_assert(sizeof(T) == sizeof(double), "the folded output is FP64");
+    double* so = reinterpret_cast<double*>(sy);
+    if (valid) {  // this copy's output, in place
 #pragma unroll
-    for (int q = 0; q < N; ++q)
-      y[eb + t + N2 * q] = ax_output(io_cast<double>(sy[t + N2 * q]), sub, pflag, eb + t + N2 * q);
+      for (int q = 0; q < N; ++q) so[t + N2 * q] = ax_output(so[t + N2 * q], sub, pflag, eb + t + N2 * q);
+    }
+    __syncthreads();
+    if (valid) {
+      // thread (le, t = i + N j) holds the points (i, j, k) of its element for k = 0..N-1
+      const int i = t % N;
+      const int ex = (int)(e % nx);
+      const bool lo = i == 0 && ex > 0 && le > 0;                            // partner: le - 1
+      const bool hi = i == N - 1 && ex < nx - 1 && le + 1 < NE && e + 1 < E;  // partner: le + 1
+      const double* sp = lo ? so - 4 * N3 + (N - 1) : (hi ? so + 4 * N3 - (N - 1) : so);
+#pragma unroll
+      for (int q = 0; q < N; ++q) {
+        const int pt = t + N2 * q;
+        const int64_t gi = eb + pt;
+        double v = so[pt];
+        if (lo) v = sp[pt] + v;  // left copy + right copy on both sides
+        if (hi) v = v + sp[pt];
+        y[gi] = (pflag[gi] & PF_FREE) ? v : 0.0;
+      }
+    }
+  } else {
+    if (valid) {
+#pragma unroll
+      for (int q = 0; q < N; ++q)
+        y[eb + t + N2 * q] = ax_output(io_cast<double>(sy[t + N2 * q]), sub, pflag, eb + t + N2 * q);
+    }
   }
+}
+
+// The x-interfaces that ax_eo_kernel<FOLD> leaves: element e = (b + 1) NE - 1, the last of block b,
+// and e + 1, the first of block b + 1, when both lie in one row.  Thread: (boundary, point (j, k)
+// of the face).  Masked copies are zero on both sides (a node's copies are all masked or none).
+template <int N>
+__global__ void gs_fold_fixup_x(int64_t E, int NE, int nx, double* __restrict__ y) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nbnd = (E + NE - 1) / NE - 1;
+  if (t >= nbnd * N2) return;
+  const int64_t b = t / N2;
+  const int jk = (int)(t - b * N2);
+  const int64_t e = (b + 1) * NE - 1;
+  if (e + 1 >= E || (int)(e % nx) == nx - 1) return;
+  const int64_t ia = e * N3 + (N - 1) + (int64_t)N * jk;  // (N - 1, j, k) of e
+  const int64_t ib = (e + 1) * N3 + (int64_t)N * jk;      // (0, j, k) of e + 1
+  const double v = y[ia] + y[ib];
+  y[ia] = v;
+  y[ib] = v;
+}
+
+template <int N>
+static int launch_ax_eo_fold(const Level& lv, const double* u, double* y, const double* sub, int NE,
+                             cudaStream_t s) {
+  constexpr int H = N / 2;
+  const int threads = NE * N * N;
+  const size_t smem = (4 * H * H + (size_t)NE * 4 * N * N * N) * sizeof(double);
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      ax_eo_kernel<N, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  SE_CUDA(attr);
+  const unsigned blocks = (unsigned)((lv.E + NE - 1) / NE);
+  ax_eo_kernel<N, double, true><<<blocks, threads, smem, s>>>(lv.E, NE, u, lv.G64, lv.L, lv.eo64, y,
+                                                              lv.pflag, sub, lv.nel[0]);
+  SE_LAUNCH_CHECK();
+  return SE_OK;
 }
 
 template <int N, typename T>
@@ -199,6 +267,36 @@ static int ax_eo_dispatch(const Level& lv, const double* u, double* y, const T* 
 int ax_local_eo(const Level& lv, const double* u, double* y, cudaStream_t s, const double* sub) {
   SE_CHECK(lv.eo64 != nullptr, SE_EINVAL, "ax_eo: folded tables missing");
   return ax_eo_dispatch<double>(lv, u, y, lv.G64, lv.eo64, s, sub);
+}
+
+int ax_local_eo_fold(const Level& lv, const double* u, double* y, const double* sub, int NE,
+                     cudaStream_t s) {
+  SE_CHECK(lv.eo64 != nullptr && lv.nel[0] >= 1, SE_EINVAL, "ax_eo_fold: folded tables or lattice missing");
+  switch (lv.N) {
+    case 2: return launch_ax_eo_fold<2>(lv, u, y, sub, NE, s);
+    case 4: return launch_ax_eo_fold<4>(lv, u, y, sub, NE, s);
+    case 6: return launch_ax_eo_fold<6>(lv, u, y, sub, NE, s);
+    case 8: return launch_ax_eo_fold<8>(lv, u, y, sub, NE, s);
+    case 10: return launch_ax_eo_fold<10>(lv, u, y, sub, NE, s);
+    default: set_error("ax_eo_fold: unsupported N=%d", lv.N); return SE_EINVAL;
+  }
+}
+
+int gs_fold_fixup(const Level& lv, double* y, int NE, cudaStream_t s) {
+  const int64_t nbnd = (lv.E + NE - 1) / NE - 1;
+  if (nbnd <= 0 || lv.nel[0] <= 1) return SE_OK;
+  const int64_t n = nbnd * lv.N * lv.N;
+  switch (lv.N) {
+#define SE_FIX_CASE(NN)                                                                      \
+  case NN:                                                                                   \
+    gs_fold_fixup_x<NN><<<grid_for(n, 256), 256, 0, s>>>(lv.E, NE, lv.nel[0], y);            \
+    break;
+    SE_FIX_CASE(2) SE_FIX_CASE(4) SE_FIX_CASE(6) SE_FIX_CASE(8) SE_FIX_CASE(10)
+#undef SE_FIX_CASE
+    default: set_error("gs_fold_fixup: unsupported N=%d", lv.N); return SE_EINVAL;
+  }
+  SE_LAUNCH_CHECK();
+  return SE_OK;
 }
 
 int ax_local_eo_df(const Level& lv, const double* u, double* y, cudaStream_t s, const double* sub) {
