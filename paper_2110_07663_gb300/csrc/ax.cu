@@ -478,10 +478,10 @@ int gs_apply(const Level& lv, T* u, bool mask, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ folded FP64 operator
-// The even-odd kernel sums the x-interfaces inside its blocks and masks (ax_local_eo_fold); the y
-// and z sweeps follow, then the x-interfaces between blocks.  The order of the three direction
-// sums does not change the set each copy adds up (see above), and each pair still writes one sum
-// to both sides, so all copies of a node keep the same bits.  This removes the x sweep, which
+// The even-odd kernel sums the x-interfaces inside its blocks and masks (ax_local_eo_fold); the
+// x-interfaces between blocks follow (gs_fold_fixup), then the y and z sweeps, so each direction is
+// complete before the next starts, as in the sweeps above, and each pair still writes one sum to
+// both sides (all copies of a node keep the same bits).  This removes the x sweep, which
 // reads and writes every sector of the vector (an x-interface copy is the first or last value of
 // a row of N), from the operator applications of the solve.
 bool ax_fold_ok(const Level& lv) {
@@ -494,6 +494,15 @@ static int gs_after_fold(const Level& lv, double* y, int NE, cudaStream_t s) {
   const int nx = lv.nel[0], ny = lv.nel[1], nz = lv.nel[2];
   constexpr int N2 = N * N;
   const int var = prof_variant<double>(lv.p);
+  // the x direction must be complete before the y sweep adds across y-interfaces: a copy summed
+  // across a block-boundary x-interface after the y sweep would count its y-partner's x-neighbour
+  // twice
+  const int64_t nbnd = (lv.E + NE - 1) / NE - 1;
+  if (nx > 1 && nbnd > 0) {
+    const double n = (double)nbnd * N2;  // at most this many pairs
+    ProfScope prof(SE_K_GS, s, n, 4.0 * n * sizeof(double), n, var);
+    SE_TRY(gs_fold_fixup(lv, y, NE, s));
+  }
   if (ny > 1) {
     const int64_t n = (int64_t)N2 * nx * (ny - 1) * nz;  // interface pairs
     ProfScope prof(SE_K_GS, s, (double)n, 4.0 * n * sizeof(double), (double)n, var);
@@ -505,12 +514,6 @@ static int gs_after_fold(const Level& lv, double* y, int NE, cudaStream_t s) {
     ProfScope prof(SE_K_GS, s, (double)n, 4.0 * n * sizeof(double), (double)n, var);
     gs_sweep_z<double, N><<<grid_for((n + GS_YZ_PAIRS - 1) / GS_YZ_PAIRS, 256), 256, 0, s>>>(nx, ny, nz, y);
     SE_LAUNCH_CHECK();
-  }
-  const int64_t nbnd = (lv.E + NE - 1) / NE - 1;
-  if (nx > 1 && nbnd > 0) {
-    const double n = (double)nbnd * N2;  // at most this many pairs
-    ProfScope prof(SE_K_GS, s, n, 4.0 * n * sizeof(double), n, var);
-    SE_TRY(gs_fold_fixup(lv, y, NE, s));
   }
   return SE_OK;
 }

@@ -229,8 +229,8 @@ int gsmap_apply(const Level& lv, T* u, bool mask, cudaStream_t s);
 // Builds lv's index map from its lattice numbering (SE_MESH_GS_MAP).
 int build_level_gsmap(Level& lv, Allocs& allocs, cudaStream_t s);
 // FP64 operator with the x part of QQ^T and the mask inside the even-odd kernel (even N, box
-// lattice, sweeps): y = A u, or b - A u when b is given; the y and z sweeps and the x-interfaces
-// between the kernel's blocks follow (ax.cu).
+// lattice, sweeps): y = A u, or b - A u when b is given; the x-interfaces between the kernel's
+// blocks, then the y and z sweeps follow (ax.cu).
 bool ax_fold_ok(const Level& lv);
 int ax_apply_folded(const Level& lv, const double* u, double* y, const double* b, cudaStream_t s);
 template <class T>
