@@ -91,14 +91,16 @@ __device__ __forceinline__ void eo_apply(const T* __restrict__ Ep, const T* __re
 // neighbours along x (same row of the lattice, nx elements per row) are usually in the same
 // block.  The kernel then also does the x part of QQ^T for them: both copies of each such
 // x-interface node get left + right (the same bits on both sides), and it applies the Dirichlet
-// mask (point flags); the x-interfaces between consecutive blocks are left to gs_fold_fixup_x.
+// mask (bit f of `bits`: face f = x0, x1, y0, y1, z0, z1 is Dirichlet); the x-interfaces between
+// consecutive blocks are left to gs_fold_fixup_x.
 template <int N, typename T, bool FOLD = false>
 __global__ void __launch_bounds__(512) ax_eo_kernel(int64_t E, int NE, const double* __restrict__ u,
                                                     const T* __restrict__ G, int64_t L,
                                                     const T* __restrict__ tables,
                                                     double* __restrict__ y,
                                                     const uint8_t* __restrict__ pflag,
-                                                    const double* __restrict__ sub, int nx = 0) {
+                                                    const double* __restrict__ sub, int nx = 0,
+                                                    int ny = 0, int nz = 0, int bits = 0) {
   constexpr int N2 = N * N, N3 = N * N * N, H = N / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tab = reinterpret_cast<T*>(smem_raw);                    // 4 H^2
@@ -153,27 +155,38 @@ __global__ void __launch_bounds__(512) ax_eo_kernel(int64_t E, int NE, const dou
   __syncthreads();
   if constexpr (FOLD) {
     static_assert(sizeof(T) == sizeof(double), "the folded output is FP64");
-    double* so = reinterpret_cast<double*>(sy);
-    if (valid) {  // this copy's output, in place
-#pragma unroll
-      for (int q = 0; q < N; ++q) so[t + N2 * q] = ax_output(so[t + N2 * q], sub, pflag, eb + t + N2 * q);
-    }
-    __syncthreads();
+    const double* so = reinterpret_cast<const double*>(sy);
     if (valid) {
-      // thread (le, t = i + N j) holds the points (i, j, k) of its element for k = 0..N-1
-      const int i = t % N;
-      const int ex = (int)(e % nx);
+      // thread (le, t = i + N j) writes the points (i, j, k) of its element, k = 0..N-1.  The
+      // multiplicity (residual form) and the Dirichlet mask follow from the place in the lattice:
+      // a copy on an interior interface normal to a direction has 2 copies along it, and a copy on
+      // a Dirichlet face of the box is masked.  Both copies of an interface node have the same
+      // multiplicity, so the partner's residual is formed here from its accumulator.
+      const int i = t % N, j = t / N;
+      const int ei = (int)e;  // E < 2^31
+      const int ex = ei % nx, ey = (ei / nx) % ny, ez = ei / (nx * ny);
       const bool lo = i == 0 && ex > 0 && le > 0;                            // partner: le - 1
       const bool hi = i == N - 1 && ex < nx - 1 && le + 1 < NE && e + 1 < E;  // partner: le + 1
-      const double* sp = lo ? so - 4 * N3 + (N - 1) : (hi ? so + 4 * N3 - (N - 1) : so);
+      const int poff = lo ? -4 * N3 + (N - 1) : (hi ? 4 * N3 - (N - 1) : 0);  // in shared memory
+      const int goff = lo ? -N3 + (N - 1) : (hi ? N3 - (N - 1) : 0);          // in the vector
+      const bool xin = (i == 0 && ex > 0) || (i == N - 1 && ex < nx - 1);
+      const bool yin = (j == 0 && ey > 0) || (j == N - 1 && ey < ny - 1);
+      const bool dxy = ((bits & 1) && i == 0 && ex == 0) || ((bits & 2) && i == N - 1 && ex == nx - 1) ||
+                       ((bits & 4) && j == 0 && ey == 0) || ((bits & 8) && j == N - 1 && ey == ny - 1);
+      const double wxy = (xin ? 0.5 : 1.0) * (yin ? 0.5 : 1.0);
 #pragma unroll
       for (int q = 0; q < N; ++q) {
         const int pt = t + N2 * q;
         const int64_t gi = eb + pt;
-        double v = so[pt];
-        if (lo) v = sp[pt] + v;  // left copy + right copy on both sides
-        if (hi) v = v + sp[pt];
-        y[gi] = (pflag[gi] & PF_FREE) ? v : 0.0;
+        const bool zin = (q == 0 && ez > 0) || (q == N - 1 && ez < nz - 1);
+        const bool dz = ((bits & 16) && q == 0 && ez == 0) || ((bits & 32) && q == N - 1 && ez == nz - 1);
+        const double w = zin ? 0.5 * wxy : wxy;
+        double v = sub ? sub[gi] * w - so[pt] : so[pt];
+        if (lo || hi) {
+          const double pv = sub ? sub[gi + goff] * w - so[pt + poff] : so[pt + poff];
+          v = lo ? pv + v : v + pv;  // left copy + right copy on both sides
+        }
+        y[gi] = (dxy || dz) ? 0.0 : v;
       }
     }
   } else {
@@ -215,8 +228,12 @@ static int launch_ax_eo_fold(const Level& lv, const double* u, double* y, const 
       ax_eo_kernel<N, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   SE_CUDA(attr);
   const unsigned blocks = (unsigned)((lv.E + NE - 1) / NE);
+  int bits = 0;
+  for (int f = 0; f < 6; ++f)
+    if (lv.bc[f] == SE_BC_DIRICHLET) bits |= 1 << f;
   ax_eo_kernel<N, double, true><<<blocks, threads, smem, s>>>(lv.E, NE, u, lv.G64, lv.L, lv.eo64, y,
-                                                              lv.pflag, sub, lv.nel[0]);
+                                                              lv.pflag, sub, lv.nel[0], lv.nel[1],
+                                                              lv.nel[2], bits);
   SE_LAUNCH_CHECK();
   return SE_OK;
 }
