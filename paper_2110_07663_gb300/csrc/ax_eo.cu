@@ -173,20 +173,33 @@ __global__ void __launch_bounds__(512) ax_eo_kernel(int64_t E, int NE, const dou
       const bool yin = (j == 0 && ey > 0) || (j == N - 1 && ey < ny - 1);
       const bool dxy = ((bits & 1) && i == 0 && ex == 0) || ((bits & 2) && i == N - 1 && ex == nx - 1) ||
                        ((bits & 4) && j == 0 && ey == 0) || ((bits & 8) && j == N - 1 && ey == ny - 1);
-      const double wxy = (xin ? 0.5 : 1.0) * (yin ? 0.5 : 1.0);
+      // this kernel is bound by the FP64 pipe: the weights 2^-(interfaces) are built from their
+      // bits, and the plain form adds no FP64 operation but the interface sums
+      if (sub) {
 #pragma unroll
-      for (int q = 0; q < N; ++q) {
-        const int pt = t + N2 * q;
-        const int64_t gi = eb + pt;
-        const bool zin = (q == 0 && ez > 0) || (q == N - 1 && ez < nz - 1);
-        const bool dz = ((bits & 16) && q == 0 && ez == 0) || ((bits & 32) && q == N - 1 && ez == nz - 1);
-        const double w = zin ? 0.5 * wxy : wxy;
-        double v = sub ? sub[gi] * w - so[pt] : so[pt];
-        if (lo || hi) {
-          const double pv = sub ? sub[gi + goff] * w - so[pt + poff] : so[pt + poff];
-          v = lo ? pv + v : v + pv;  // left copy + right copy on both sides
+        for (int q = 0; q < N; ++q) {
+          const int pt = t + N2 * q;
+          const int64_t gi = eb + pt;
+          const bool zin = (q == 0 && ez > 0) || (q == N - 1 && ez < nz - 1);
+          const bool dz = ((bits & 16) && q == 0 && ez == 0) || ((bits & 32) && q == N - 1 && ez == nz - 1);
+          const double w = __longlong_as_double((long long)(1023 - (int)xin - (int)yin - (int)zin) << 52);
+          double v = sub[gi] * w - so[pt];
+          if (lo || hi) {
+            const double pv = sub[gi + goff] * w - so[pt + poff];
+            v = lo ? pv + v : v + pv;  // left copy + right copy on both sides
+          }
+          y[gi] = (dxy || dz) ? 0.0 : v;
         }
-        y[gi] = (dxy || dz) ? 0.0 : v;
+      } else {
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+          const int pt = t + N2 * q;
+          const bool dz = ((bits & 16) && q == 0 && ez == 0) || ((bits & 32) && q == N - 1 && ez == nz - 1);
+          double v = so[pt];
+          if (lo) v = so[pt + poff] + v;
+          if (hi) v = v + so[pt + poff];
+          y[eb + pt] = (dxy || dz) ? 0.0 : v;
+        }
       }
     }
   } else {
@@ -292,7 +305,6 @@ int ax_local_eo_fold(const Level& lv, const double* u, double* y, const double* 
   switch (lv.N) {
     case 2: return launch_ax_eo_fold<2>(lv, u, y, sub, NE, s);
     case 4: return launch_ax_eo_fold<4>(lv, u, y, sub, NE, s);
-    case 6: return launch_ax_eo_fold<6>(lv, u, y, sub, NE, s);
     case 8: return launch_ax_eo_fold<8>(lv, u, y, sub, NE, s);
     case 10: return launch_ax_eo_fold<10>(lv, u, y, sub, NE, s);
     default: set_error("ax_eo_fold: unsupported N=%d", lv.N); return SE_EINVAL;
