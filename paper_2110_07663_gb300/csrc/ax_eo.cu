@@ -155,51 +155,53 @@ __global__ void __launch_bounds__(512) ax_eo_kernel(int64_t E, int NE, const dou
   __syncthreads();
   if constexpr (FOLD) {
     static_assert(sizeof(T) == sizeof(double), "the folded output is FP64");
-    const double* so = reinterpret_cast<const double*>(sy);
+    // the kernel is bound by the FP64 pipe, where a warp instruction costs the same with 2 or 32
+    // lanes active: each interface pair is added once, by one lane of densely packed warps, and
+    // the weights 2^-(interfaces) of the residual form are built from their exponent bits
+    double* so0 = reinterpret_cast<double*>(tab + 4 * H * H);  // element 0 of the block
+    double* so = reinterpret_cast<double*>(sy);
+    // thread (le, t = i + N j) holds the points (i, j, k) of its element, k = 0..N-1; its place
+    // in the lattice gives the multiplicity (a copy on an interior interface normal to a
+    // direction has 2 copies along it) and the Dirichlet mask
+    const int i = t % N, j = t / N;
+    const int ei = (int)e;  // E < 2^31
+    const int ex = ei % nx, ey = (ei / nx) % ny, ez = ei / (nx * ny);
+    if (sub) {  // residual form: each copy's b / multiplicity - (A_L u), in place
+      if (valid) {
+        const int xy = (int)((i == 0 && ex > 0) || (i == N - 1 && ex < nx - 1)) +
+                       (int)((j == 0 && ey > 0) || (j == N - 1 && ey < ny - 1));
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+          const int pt = t + N2 * q;
+          const int zin = (int)((q == 0 && ez > 0) || (q == N - 1 && ez < nz - 1));
+          const double w = __longlong_as_double((long long)(1023 - xy - zin) << 52);
+          so[pt] = sub[eb + pt] * w - so[pt];
+        }
+      }
+      __syncthreads();
+    }
+    // x-interfaces inside the block: (N - 1, j, k) of element lp and (0, j, k) of lp + 1 when
+    // both lie in one row; both copies get left + right
+    const int64_t e0 = (int64_t)blockIdx.x * NE;
+    for (int idx = threadIdx.x; idx < (NE - 1) * N2; idx += blockDim.x) {
+      const int lp = idx / N2, jk = idx - lp * N2;
+      const int el = (int)(e0 + lp);
+      if (el + 1 < E && el % nx < nx - 1) {
+        double* a = so0 + lp * 4 * N3 + (N - 1) + N * jk;
+        double* b = a + 4 * N3 - (N - 1);
+        const double v = *a + *b;
+        *a = v;
+        *b = v;
+      }
+    }
+    __syncthreads();
     if (valid) {
-      // thread (le, t = i + N j) writes the points (i, j, k) of its element, k = 0..N-1.  The
-      // multiplicity (residual form) and the Dirichlet mask follow from the place in the lattice:
-      // a copy on an interior interface normal to a direction has 2 copies along it, and a copy on
-      // a Dirichlet face of the box is masked.  Both copies of an interface node have the same
-      // multiplicity, so the partner's residual is formed here from its accumulator.
-      const int i = t % N, j = t / N;
-      const int ei = (int)e;  // E < 2^31
-      const int ex = ei % nx, ey = (ei / nx) % ny, ez = ei / (nx * ny);
-      const bool lo = i == 0 && ex > 0 && le > 0;                            // partner: le - 1
-      const bool hi = i == N - 1 && ex < nx - 1 && le + 1 < NE && e + 1 < E;  // partner: le + 1
-      const int poff = lo ? -4 * N3 + (N - 1) : (hi ? 4 * N3 - (N - 1) : 0);  // in shared memory
-      const int goff = lo ? -N3 + (N - 1) : (hi ? N3 - (N - 1) : 0);          // in the vector
-      const bool xin = (i == 0 && ex > 0) || (i == N - 1 && ex < nx - 1);
-      const bool yin = (j == 0 && ey > 0) || (j == N - 1 && ey < ny - 1);
       const bool dxy = ((bits & 1) && i == 0 && ex == 0) || ((bits & 2) && i == N - 1 && ex == nx - 1) ||
                        ((bits & 4) && j == 0 && ey == 0) || ((bits & 8) && j == N - 1 && ey == ny - 1);
-      // this kernel is bound by the FP64 pipe: the weights 2^-(interfaces) are built from their
-      // bits, and the plain form adds no FP64 operation but the interface sums
-      if (sub) {
 #pragma unroll
-        for (int q = 0; q < N; ++q) {
-          const int pt = t + N2 * q;
-          const int64_t gi = eb + pt;
-          const bool zin = (q == 0 && ez > 0) || (q == N - 1 && ez < nz - 1);
-          const bool dz = ((bits & 16) && q == 0 && ez == 0) || ((bits & 32) && q == N - 1 && ez == nz - 1);
-          const double w = __longlong_as_double((long long)(1023 - (int)xin - (int)yin - (int)zin) << 52);
-          double v = sub[gi] * w - so[pt];
-          if (lo || hi) {
-            const double pv = sub[gi + goff] * w - so[pt + poff];
-            v = lo ? pv + v : v + pv;  // left copy + right copy on both sides
-          }
-          y[gi] = (dxy || dz) ? 0.0 : v;
-        }
-      } else {
-#pragma unroll
-        for (int q = 0; q < N; ++q) {
-          const int pt = t + N2 * q;
-          const bool dz = ((bits & 16) && q == 0 && ez == 0) || ((bits & 32) && q == N - 1 && ez == nz - 1);
-          double v = so[pt];
-          if (lo) v = so[pt + poff] + v;
-          if (hi) v = v + so[pt + poff];
-          y[eb + pt] = (dxy || dz) ? 0.0 : v;
-        }
+      for (int q = 0; q < N; ++q) {
+        const bool dz = ((bits & 16) && q == 0 && ez == 0) || ((bits & 32) && q == N - 1 && ez == nz - 1);
+        y[eb + t + N2 * q] = (dxy || dz) ? 0.0 : so[t + N2 * q];
       }
     }
   } else {
