@@ -484,11 +484,9 @@ int gs_apply(const Level& lv, T* u, bool mask, cudaStream_t s) {
 // both sides (all copies of a node keep the same bits).  This removes the x sweep, which
 // reads and writes every sector of the vector (an x-interface copy is the first or last value of
 // a row of N), from the operator applications of the solve.
-// Not at N = 6: there the folded kernel needs more registers than the plain one (78 against 64),
-// which costs a resident block per SM and more than the x sweep it saves (measured at 32^3).
 bool ax_fold_ok(const Level& lv) {
-  return !ax_df_route(lv) && lv.eo64 && ax_eo_supported(lv.p) && lv.N != 6 && !lv.gsm_ids &&
-         lv.nel[0] >= 1 && lv.nel[1] >= 1 && lv.nel[2] >= 1;
+  return !ax_df_route(lv) && lv.eo64 && ax_eo_supported(lv.p) && !lv.gsm_ids && lv.nel[0] >= 1 &&
+         lv.nel[1] >= 1 && lv.nel[2] >= 1;
 }
 
 template <int N>
@@ -531,6 +529,7 @@ int ax_apply_folded(const Level& lv, const double* u, double* y, const double* b
   switch (lv.N) {
     case 2: return gs_after_fold<2>(lv, y, NE, s);
     case 4: return gs_after_fold<4>(lv, y, NE, s);
+    case 6: return gs_after_fold<6>(lv, y, NE, s);
     case 8: return gs_after_fold<8>(lv, y, NE, s);
     case 10: return gs_after_fold<10>(lv, y, NE, s);
     default: set_error("ax_apply_folded: unsupported N=%d", lv.N); return SE_EINVAL;

@@ -307,6 +307,7 @@ int ax_local_eo_fold(const Level& lv, const double* u, double* y, const double* 
   switch (lv.N) {
     case 2: return launch_ax_eo_fold<2>(lv, u, y, sub, NE, s);
     case 4: return launch_ax_eo_fold<4>(lv, u, y, sub, NE, s);
+    case 6: return launch_ax_eo_fold<6>(lv, u, y, sub, NE, s);
     case 8: return launch_ax_eo_fold<8>(lv, u, y, sub, NE, s);
     case 10: return launch_ax_eo_fold<10>(lv, u, y, sub, NE, s);
     default: set_error("ax_eo_fold: unsupported N=%d", lv.N); return SE_EINVAL;
