@@ -196,14 +196,16 @@ def roofline(kernel, variant, d, pk, pk_kind):
             else "fallback 6.8 TB/s"}
 
 
-def profiled_variants(se, solve, steps, stream):
+def profiled_variants(se, solve, steps, stream, label="profiled_pass"):
     """Runs `solve` (host-driven) `steps` times with every library launch bracketed by CUDA events
-    on its stream; returns (ms per solve of the pass, per-class totals, per-variant totals)."""
+    on its stream; returns (ms per solve of the pass, per-class totals, per-variant totals).  The
+    pass is an NVTX range named `label` (the headline's: "profiled_pass"), so that a profiler can
+    select exactly these launches."""
     import torch
     se.se_prof_reset()
     se.se_prof_enable(True)
     p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.nvtx.range_push("profiled_pass")  # lets a profiler select exactly these launches
+    torch.cuda.nvtx.range_push(label)
     p0.record(stream)
     for _ in range(steps):
         solve()
@@ -273,7 +275,8 @@ def schwarz_record(se, m, b, x, stream, wk, pk, pk_kind, op_df, steps):
             ms = e0.elapsed_time(e1) / k
             solve(graph=0)
             torch.cuda.synchronize()
-            _, _, variants = profiled_variants(se, lambda: solve(graph=0), 1, stream)
+            _, _, variants = profiled_variants(se, lambda: solve(graph=0), 1, stream,
+                                               label="profiled_pass_schwarz")
             table = kernel_table(variants, 1, pk, pk_kind)
             fdm = {}
             for (kk, v), q in variants.items():
@@ -666,7 +669,7 @@ def batch_measure(nprob, steps, warmup, op_df=0):
 
     host_batch()
     torch.cuda.synchronize()
-    prof_ms, _, variants = profiled_variants(se, host_batch, 1, stream)
+    prof_ms, _, variants = profiled_variants(se, host_batch, 1, stream, label="profiled_pass_batch")
     se.se_batch_destroy(Bh)
     pk, pk_kind = peaks()
     pk["sms"] = torch.cuda.get_device_properties(0).multi_processor_count
