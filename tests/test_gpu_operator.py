@@ -202,11 +202,13 @@ def test_fp32_pipelined_operator_steady_state_and_residual_forms():
     ((21, 2, 2), 1, ("D", "D", "N", "N", "D", "D")),   # p = 1: blocks of 64 elements
     ((7, 6, 5), 9, ("D",) * 6),                        # blocks of 3
 ])
-def test_folded_fp64_operator_against_the_oracle(nel, p, bc):
-    """The FP64 operator at even N does the x part of QQ^T and the Dirichlet mask inside its
-    blocks, then the y and z sweeps and the x-interfaces between blocks: r = b - A u through
-    se_residual and the mixed-boundary meshes, element by element against the oracle at 1e-12;
-    all copies of every node bitwise equal."""
+@pytest.mark.parametrize("fp32", [False, True])
+def test_folded_operator_against_the_oracle(nel, p, bc, fp32):
+    """The FP64 operator at even N and the FP32 pipelined operator do the x part of QQ^T and the
+    Dirichlet mask inside their blocks (element groups), then the x-interfaces between blocks and
+    the y and z sweeps: r = b - A u through se_residual on ragged and mixed-boundary meshes,
+    element by element against the oracle (1e-12 in FP64, 2e-5 in FP32); all copies of every
+    node bitwise equal."""
     c = Case(nel, p, seed=17, bc=bc)
     try:
         um = c.random_continuous(21)
@@ -214,9 +216,9 @@ def test_folded_fp64_operator_against_the_oracle(nel, p, bc):
         ref = b - o.ax(c.lv, um)
         r = c.empty()
         r.fill_(float("nan"))
-        c.se.se_residual(c.m, c.to_gpu(b), c.to_gpu(um), r, 0)
+        c.se.se_residual(c.m, c.to_gpu(b), c.to_gpu(um), r, c.se.SE_AX_FP32 if fp32 else 0)
         got = c.to_np(r)
-        assert rel_err(got, ref) <= 1e-12
+        assert rel_err(got, ref) <= (2e-5 if fp32 else 1e-12)
         # copies of one node hold the same bits: scatter to global ids and back
         gid = c.lv.gid.reshape(-1)
         first = np.full(c.lv.n_global, -1, dtype=np.int64)
