@@ -494,8 +494,11 @@ bool ax_fold_ok32(const Level& lv) {
          lv.nel[2] >= 1;
 }
 
+// mask: the folded kernel left the Dirichlet copies unmasked (FP32 form); they are zeroed after
+// the x direction and before the y and z sums, which then add zeros for them (a node's copies
+// are all on a Dirichlet face or none)
 template <class T, int N>
-static int gs_after_fold(const Level& lv, T* y, int NE, cudaStream_t s) {
+static int gs_after_fold(const Level& lv, T* y, int NE, cudaStream_t s, bool mask = false) {
   const int nx = lv.nel[0], ny = lv.nel[1], nz = lv.nel[2];
   constexpr int N2 = N * N;
   const int var = prof_variant<T>(lv.p);
@@ -507,6 +510,16 @@ static int gs_after_fold(const Level& lv, T* y, int NE, cudaStream_t s) {
     const double n = (double)nbnd * N2;  // at most this many pairs
     ProfScope prof(SE_K_GS, s, n, 4.0 * n * sizeof(T), n, var);
     SE_TRY(gs_fold_fixup<T>(lv, y, NE, s));
+  }
+  int bits = 0;
+  if (mask)
+    for (int f = 0; f < 6; ++f)
+      if (lv.bc[f] == SE_BC_DIRICHLET) bits |= 1 << f;
+  if (bits) {
+    const int64_t n = 2 * N2 * ((int64_t)ny * nz + (int64_t)nx * nz + (int64_t)nx * ny);
+    ProfScope prof(SE_K_GS, s, (double)n, 0.0, 0.0, var);
+    gs_mask_faces<T, N><<<grid_for(n, 256), 256, 0, s>>>(nx, ny, nz, bits, y);
+    SE_LAUNCH_CHECK();
   }
   if (ny > 1) {
     const int64_t n = (int64_t)N2 * nx * (ny - 1) * nz;  // interface pairs
@@ -550,11 +563,11 @@ int ax_apply_folded32(const Level& lv, const float* u, float* y, const float* b,
     SE_TRY(ax_local_tma(lv, u, y, s, b, true));
   }
   switch (lv.N) {
-    case 2: return gs_after_fold<float, 2>(lv, y, NE, s);
-    case 4: return gs_after_fold<float, 4>(lv, y, NE, s);
-    case 6: return gs_after_fold<float, 6>(lv, y, NE, s);
-    case 8: return gs_after_fold<float, 8>(lv, y, NE, s);
-    case 10: return gs_after_fold<float, 10>(lv, y, NE, s);
+    case 2: return gs_after_fold<float, 2>(lv, y, NE, s, true);
+    case 4: return gs_after_fold<float, 4>(lv, y, NE, s, true);
+    case 6: return gs_after_fold<float, 6>(lv, y, NE, s, true);
+    case 8: return gs_after_fold<float, 8>(lv, y, NE, s, true);
+    case 10: return gs_after_fold<float, 10>(lv, y, NE, s, true);
     default: set_error("ax_apply_folded32: unsupported N=%d", lv.N); return SE_EINVAL;
   }
 }

@@ -67,11 +67,10 @@ constexpr long long PIPE_LIMIT_NS = 1000000000LL;
 // output is b / multiplicity - A_L u; the multiplicity follows from the element's place in the
 // lattice (copies = product over directions of 2 on an interior element interface, else 1), or,
 // for a level that is a union of several lattices (nx = 0), from the point flags.
-// FOLD (box lattice, nx > 0): the x part of QQ^T for the x-neighbours inside a group and the
-// Dirichlet mask (bit f of `bits`: face f = x0, x1, y0, y1, z0, z1 is Dirichlet), as in the
-// folded FP64 operator: the copies on x-faces go through a small shared-memory buffer, and after
-// the group's last barrier each face copy stores left + right; the x-interfaces between groups
-// are left to gs_fold_fixup_x.
+// FOLD (box lattice, nx > 0): the x part of QQ^T for the x-neighbours inside a group, after the
+// group's outputs are written (the main loop is that of the plain form: this kernel's speed is
+// set by its load pipeline and issue rate); the x-interfaces between groups and the Dirichlet
+// mask are left to gs_fold_fixup_x and gs_mask_faces.
 template <int N, bool RES, bool FOLD = false>
 __global__ void __launch_bounds__(512) ax_tma_kernel(int64_t E, int NE, int64_t ngroups,
                                                      const float* __restrict__ u,
@@ -81,7 +80,7 @@ __global__ void __launch_bounds__(512) ax_tma_kernel(int64_t E, int NE, int64_t 
                                                      const float* __restrict__ sub, int nx,
                                                      int ny, int nz,
                                                      const uint8_t* __restrict__ pflag,
-                                                     int* __restrict__ pstatus, int bits = 0) {
+                                                     int* __restrict__ pstatus) {
   constexpr int N2 = N * N, N3 = N * N * N, A = RES ? 8 : 7;  // blocks per stage
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int S = NE * N3;                       // floats per element-group block
@@ -90,7 +89,6 @@ __global__ void __launch_bounds__(512) ax_tma_kernel(int64_t E, int NE, int64_t 
   float* sws = swr + S;
   float* sD = sws + S;
   uint64_t* bars = reinterpret_cast<uint64_t*>(sD + ((N2 + 3) / 4) * 4 + 4);
-  float* sface = reinterpret_cast<float*>(bars + 2);  // FOLD: [NE][2 faces][N^2]
   const int tid = threadIdx.x;
   const int le = tid / N2, ij = tid - le * N2;
   const int i = ij % N, j = ij / N;
@@ -189,20 +187,10 @@ __global__ void __launch_bounds__(512) ax_tma_kernel(int64_t E, int NE, int64_t 
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue(st, g + 2 * (int64_t)gridDim.x);
     }
-    int ex = 0, ey = 0, ez = 0;
-    if constexpr (FOLD) {
-      const int ei = (int)(e0 + le);  // E < 2^31
-      ex = ei % nx;
-      ey = (ei / nx) % ny;
-      ez = ei / (nx * ny);
-    }
-    const bool xface = FOLD && (i == 0 || i == N - 1);
     if (valid) {
       const float* cwr = swr + le * N3;
       const float* cws = sws + le * N3;
       float* yo = y + (e0 + le) * N3;
-      const bool dxy = FOLD && (((bits & 1) && i == 0 && ex == 0) || ((bits & 2) && i == N - 1 && ex == nx - 1) ||
-                                ((bits & 4) && j == 0 && ey == 0) || ((bits & 8) && j == N - 1 && ey == ny - 1));
 #pragma unroll
       for (int k = 0; k < N; ++k) {
         float acc = ry[k];
@@ -211,31 +199,30 @@ __global__ void __launch_bounds__(512) ax_tma_kernel(int64_t E, int NE, int64_t 
           acc += Dci[l] * cwr[l + N * j + N2 * k];
           acc += Dcj[l] * cws[i + N * l + N2 * k];
         }
-        float v = RES ? bw[k] - acc : acc;
-        if constexpr (FOLD) {
-          const bool dz = ((bits & 16) && k == 0 && ez == 0) || ((bits & 32) && k == N - 1 && ez == nz - 1);
-          if (dxy || dz) v = 0.f;
-          if (xface) sface[(le * 2 + (i == 0 ? 0 : 1)) * N2 + j + N * k] = v;
-          else yo[ij + N2 * k] = v;
-        } else {
-          yo[ij + N2 * k] = v;
-        }
+        yo[ij + N2 * k] = RES ? bw[k] - acc : acc;
       }
     }
-    __syncthreads();  // swr/sws free for the next group; FOLD: the group's face copies complete
-    if (FOLD && valid && xface) {
-      // left + right on both sides of each x-interface inside the group
-      const bool lo = i == 0 && ex > 0 && le > 0;
-      const bool hi = i == N - 1 && ex < nx - 1 && le + 1 < NE && e0 + le + 1 < E;
-      const float* own = sface + (le * 2 + (i == 0 ? 0 : 1)) * N2 + j;
-      const float* par = lo ? sface + ((le - 1) * 2 + 1) * N2 + j : sface + ((le + 1) * 2) * N2 + j;
-      float* yo = y + (e0 + le) * N3;
+    __syncthreads();  // swr/sws free for the next group; FOLD: the group's outputs are written
+    if constexpr (FOLD) {
+      // left + right on both sides of each x-interface inside the group: the lanes of the
+      // right-hand copies (i = 0) read both copies back (the block's own writes, ordered by the
+      // barrier) and write the sum to both
+      const int64_t e = e0 + le;
+      if (valid && i == 0 && le > 0 && (int)(e % nx) > 0) {
+        float* yr = y + e * N3 + N * j;            // (0, j, k) of e
+        float* yl = y + (e - 1) * N3 + (N - 1) + N * j;  // (N - 1, j, k) of e - 1
+        float a[N], b[N];
 #pragma unroll
-      for (int k = 0; k < N; ++k) {
-        float v = own[N * k];
-        if (lo) v = par[N * k] + v;
-        if (hi) v = v + par[N * k];
-        yo[ij + N2 * k] = v;
+        for (int k = 0; k < N; ++k) {
+          a[k] = __ldcg(yl + N2 * k);
+          b[k] = __ldcg(yr + N2 * k);
+        }
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          const float v = a[k] + b[k];
+          yl[N2 * k] = v;
+          yr[N2 * k] = v;
+        }
       }
     }
     st ^= 1;
@@ -253,14 +240,10 @@ static int launch_ax_tma_t(const Level& lv, const float* u, float* y, int NE, co
   SE_CHECK(lv.pstatus, SE_EINVAL, "ax_tma: level without a status word");
   const int threads = NE * N * N;
   const size_t smem = (size_t)((2 * A + 2) * NE * N3 + ((N * N + 3) / 4) * 4 + 4) * sizeof(float) +
-                      2 * sizeof(uint64_t) + (FOLD ? (size_t)NE * 2 * N * N * sizeof(float) : 0);
+                      2 * sizeof(uint64_t);
   static const cudaError_t attr = cudaFuncSetAttribute(
       ax_tma_kernel<N, RES, FOLD>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   SE_CUDA(attr);
-  int bits = 0;
-  if (FOLD)
-    for (int f = 0; f < 6; ++f)
-      if (lv.bc[f] == SE_BC_DIRICHLET) bits |= 1 << f;
   int per_sm = 0;
   SE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ax_tma_kernel<N, RES, FOLD>, threads, smem));
   SE_CHECK(per_sm >= 1, SE_ECUDA, "ax_tma: no resident block fits (NE=%d)", NE);
@@ -273,7 +256,7 @@ static int launch_ax_tma_t(const Level& lv, const float* u, float* y, int NE, co
   ax_tma_kernel<N, RES, FOLD><<<(unsigned)grid, threads, smem, s>>>(lv.E, NE, groups, u, lv.G32, lv.L,
                                                                      lv.D32, y, sub, lv.nel[0],
                                                                      lv.nel[1], lv.nel[2], lv.pflag,
-                                                                     lv.pstatus, bits);
+                                                                     lv.pstatus);
   SE_LAUNCH_CHECK();
   return SE_OK;
 }
