@@ -489,48 +489,30 @@ bool ax_fold_ok(const Level& lv) {
          lv.nel[1] >= 1 && lv.nel[2] >= 1;
 }
 
-bool ax_fold_ok32(const Level& lv) {
-  return lv.G32 && ax_tma_supported(lv.p) && !lv.gsm_ids && lv.nel[0] >= 1 && lv.nel[1] >= 1 &&
-         lv.nel[2] >= 1;
-}
-
-// mask: the folded kernel left the Dirichlet copies unmasked (FP32 form); they are zeroed after
-// the x direction and before the y and z sums, which then add zeros for them (a node's copies
-// are all on a Dirichlet face or none)
-template <class T, int N>
-static int gs_after_fold(const Level& lv, T* y, int NE, cudaStream_t s, bool mask = false) {
+template <int N>
+static int gs_after_fold(const Level& lv, double* y, int NE, cudaStream_t s) {
   const int nx = lv.nel[0], ny = lv.nel[1], nz = lv.nel[2];
   constexpr int N2 = N * N;
-  const int var = prof_variant<T>(lv.p);
+  const int var = prof_variant<double>(lv.p);
   // the x direction must be complete before the y sweep adds across y-interfaces: a copy summed
   // across a block-boundary x-interface after the y sweep would count its y-partner's x-neighbour
   // twice
   const int64_t nbnd = (lv.E + NE - 1) / NE - 1;
   if (nx > 1 && nbnd > 0) {
     const double n = (double)nbnd * N2;  // at most this many pairs
-    ProfScope prof(SE_K_GS, s, n, 4.0 * n * sizeof(T), n, var);
-    SE_TRY(gs_fold_fixup<T>(lv, y, NE, s));
-  }
-  int bits = 0;
-  if (mask)
-    for (int f = 0; f < 6; ++f)
-      if (lv.bc[f] == SE_BC_DIRICHLET) bits |= 1 << f;
-  if (bits) {
-    const int64_t n = 2 * N2 * ((int64_t)ny * nz + (int64_t)nx * nz + (int64_t)nx * ny);
-    ProfScope prof(SE_K_GS, s, (double)n, 0.0, 0.0, var);
-    gs_mask_faces<T, N><<<grid_for(n, 256), 256, 0, s>>>(nx, ny, nz, bits, y);
-    SE_LAUNCH_CHECK();
+    ProfScope prof(SE_K_GS, s, n, 4.0 * n * sizeof(double), n, var);
+    SE_TRY(gs_fold_fixup(lv, y, NE, s));
   }
   if (ny > 1) {
     const int64_t n = (int64_t)N2 * nx * (ny - 1) * nz;  // interface pairs
-    ProfScope prof(SE_K_GS, s, (double)n, 4.0 * n * sizeof(T), (double)n, var);
-    gs_sweep_y<T, N><<<grid_for((n + GS_YZ_PAIRS - 1) / GS_YZ_PAIRS, 256), 256, 0, s>>>(nx, ny, nz, y);
+    ProfScope prof(SE_K_GS, s, (double)n, 4.0 * n * sizeof(double), (double)n, var);
+    gs_sweep_y<double, N><<<grid_for((n + GS_YZ_PAIRS - 1) / GS_YZ_PAIRS, 256), 256, 0, s>>>(nx, ny, nz, y);
     SE_LAUNCH_CHECK();
   }
   if (nz > 1) {
     const int64_t n = (int64_t)N2 * nx * ny * (nz - 1);
-    ProfScope prof(SE_K_GS, s, (double)n, 4.0 * n * sizeof(T), (double)n, var);
-    gs_sweep_z<T, N><<<grid_for((n + GS_YZ_PAIRS - 1) / GS_YZ_PAIRS, 256), 256, 0, s>>>(nx, ny, nz, y);
+    ProfScope prof(SE_K_GS, s, (double)n, 4.0 * n * sizeof(double), (double)n, var);
+    gs_sweep_z<double, N><<<grid_for((n + GS_YZ_PAIRS - 1) / GS_YZ_PAIRS, 256), 256, 0, s>>>(nx, ny, nz, y);
     SE_LAUNCH_CHECK();
   }
   return SE_OK;
@@ -545,30 +527,12 @@ int ax_apply_folded(const Level& lv, const double* u, double* y, const double* b
     SE_TRY(ax_local_eo_fold(lv, u, y, b, NE, s));
   }
   switch (lv.N) {
-    case 2: return gs_after_fold<double, 2>(lv, y, NE, s);
-    case 4: return gs_after_fold<double, 4>(lv, y, NE, s);
-    case 6: return gs_after_fold<double, 6>(lv, y, NE, s);
-    case 8: return gs_after_fold<double, 8>(lv, y, NE, s);
-    case 10: return gs_after_fold<double, 10>(lv, y, NE, s);
+    case 2: return gs_after_fold<2>(lv, y, NE, s);
+    case 4: return gs_after_fold<4>(lv, y, NE, s);
+    case 6: return gs_after_fold<6>(lv, y, NE, s);
+    case 8: return gs_after_fold<8>(lv, y, NE, s);
+    case 10: return gs_after_fold<10>(lv, y, NE, s);
     default: set_error("ax_apply_folded: unsupported N=%d", lv.N); return SE_EINVAL;
-  }
-}
-
-int ax_apply_folded32(const Level& lv, const float* u, float* y, const float* b, cudaStream_t s) {
-  const int NE = ax_tma_group(lv.p);
-  {
-    const double pts = (double)lv.L;
-    ProfScope prof(SE_K_AX, s, pts, pts * (b ? 9.0 : 8.0) * sizeof(float),
-                   pts * (12.0 * lv.N + 15.0), prof_variant<float>(lv.p));
-    SE_TRY(ax_local_tma(lv, u, y, s, b, true));
-  }
-  switch (lv.N) {
-    case 2: return gs_after_fold<float, 2>(lv, y, NE, s, true);
-    case 4: return gs_after_fold<float, 4>(lv, y, NE, s, true);
-    case 6: return gs_after_fold<float, 6>(lv, y, NE, s, true);
-    case 8: return gs_after_fold<float, 8>(lv, y, NE, s, true);
-    case 10: return gs_after_fold<float, 10>(lv, y, NE, s, true);
-    default: set_error("ax_apply_folded32: unsupported N=%d", lv.N); return SE_EINVAL;
   }
 }
 

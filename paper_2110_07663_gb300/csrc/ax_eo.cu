@@ -216,8 +216,8 @@ __global__ void __launch_bounds__(512) ax_eo_kernel(int64_t E, int NE, const dou
 // The x-interfaces that ax_eo_kernel<FOLD> leaves: element e = (b + 1) NE - 1, the last of block b,
 // and e + 1, the first of block b + 1, when both lie in one row.  Thread: (boundary, point (j, k)
 // of the face).  Masked copies are zero on both sides (a node's copies are all masked or none).
-template <typename T, int N>
-__global__ void gs_fold_fixup_x(int64_t E, int NE, int nx, T* __restrict__ y) {
+template <int N>
+__global__ void gs_fold_fixup_x(int64_t E, int NE, int nx, double* __restrict__ y) {
   constexpr int N2 = N * N, N3 = N2 * N;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nbnd = (E + NE - 1) / NE - 1;
@@ -228,7 +228,7 @@ __global__ void gs_fold_fixup_x(int64_t E, int NE, int nx, T* __restrict__ y) {
   if (e + 1 >= E || (int)(e % nx) == nx - 1) return;
   const int64_t ia = e * N3 + (N - 1) + (int64_t)N * jk;  // (N - 1, j, k) of e
   const int64_t ib = (e + 1) * N3 + (int64_t)N * jk;      // (0, j, k) of e + 1
-  const T v = y[ia] + y[ib];
+  const double v = y[ia] + y[ib];
   y[ia] = v;
   y[ib] = v;
 }
@@ -314,15 +314,14 @@ int ax_local_eo_fold(const Level& lv, const double* u, double* y, const double* 
   }
 }
 
-template <class T>
-int gs_fold_fixup(const Level& lv, T* y, int NE, cudaStream_t s) {
+int gs_fold_fixup(const Level& lv, double* y, int NE, cudaStream_t s) {
   const int64_t nbnd = (lv.E + NE - 1) / NE - 1;
   if (nbnd <= 0 || lv.nel[0] <= 1) return SE_OK;
   const int64_t n = nbnd * lv.N * lv.N;
   switch (lv.N) {
 #define SE_FIX_CASE(NN)                                                                      \
   case NN:                                                                                   \
-    gs_fold_fixup_x<T, NN><<<grid_for(n, 256), 256, 0, s>>>(lv.E, NE, lv.nel[0], y);         \
+    gs_fold_fixup_x<NN><<<grid_for(n, 256), 256, 0, s>>>(lv.E, NE, lv.nel[0], y);            \
     break;
     SE_FIX_CASE(2) SE_FIX_CASE(4) SE_FIX_CASE(6) SE_FIX_CASE(8) SE_FIX_CASE(10)
 #undef SE_FIX_CASE
@@ -331,8 +330,6 @@ int gs_fold_fixup(const Level& lv, T* y, int NE, cudaStream_t s) {
   SE_LAUNCH_CHECK();
   return SE_OK;
 }
-template int gs_fold_fixup<double>(const Level&, double*, int, cudaStream_t);
-template int gs_fold_fixup<float>(const Level&, float*, int, cudaStream_t);
 
 int ax_local_eo_df(const Level& lv, const double* u, double* y, cudaStream_t s, const double* sub) {
   SE_CHECK(lv.Gdf != nullptr && lv.eodf != nullptr, SE_EINVAL, "ax_eo_df: df64 geometry missing");

@@ -67,11 +67,7 @@ constexpr long long PIPE_LIMIT_NS = 1000000000LL;
 // output is b / multiplicity - A_L u; the multiplicity follows from the element's place in the
 // lattice (copies = product over directions of 2 on an interior element interface, else 1), or,
 // for a level that is a union of several lattices (nx = 0), from the point flags.
-// FOLD (box lattice, nx > 0): the x part of QQ^T for the x-neighbours inside a group, after the
-// group's outputs are written (the main loop is that of the plain form: this kernel's speed is
-// set by its load pipeline and issue rate); the x-interfaces between groups and the Dirichlet
-// mask are left to gs_fold_fixup_x and gs_mask_faces.
-template <int N, bool RES, bool FOLD = false>
+template <int N, bool RES>
 __global__ void __launch_bounds__(512) ax_tma_kernel(int64_t E, int NE, int64_t ngroups,
                                                      const float* __restrict__ u,
                                                      const float* __restrict__ G, int64_t L,
@@ -202,29 +198,7 @@ __global__ void __launch_bounds__(512) ax_tma_kernel(int64_t E, int NE, int64_t 
         yo[ij + N2 * k] = RES ? bw[k] - acc : acc;
       }
     }
-    __syncthreads();  // swr/sws free for the next group; FOLD: the group's outputs are written
-    if constexpr (FOLD) {
-      // left + right on both sides of each x-interface inside the group: the lanes of the
-      // right-hand copies (i = 0) read both copies back (the block's own writes, ordered by the
-      // barrier) and write the sum to both
-      const int64_t e = e0 + le;
-      if (valid && i == 0 && le > 0 && (int)(e % nx) > 0) {
-        float* yr = y + e * N3 + N * j;            // (0, j, k) of e
-        float* yl = y + (e - 1) * N3 + (N - 1) + N * j;  // (N - 1, j, k) of e - 1
-        float a[N], b[N];
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-          a[k] = __ldcg(yl + N2 * k);
-          b[k] = __ldcg(yr + N2 * k);
-        }
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-          const float v = a[k] + b[k];
-          yl[N2 * k] = v;
-          yr[N2 * k] = v;
-        }
-      }
-    }
+    __syncthreads();  // swr/sws free for the next group
     st ^= 1;
   }
   if (!ok && tid == 0) {
@@ -233,7 +207,7 @@ __global__ void __launch_bounds__(512) ax_tma_kernel(int64_t E, int NE, int64_t 
   }
 }
 
-template <int N, bool RES, bool FOLD = false>
+template <int N, bool RES>
 static int launch_ax_tma_t(const Level& lv, const float* u, float* y, int NE, const float* sub,
                            cudaStream_t s) {
   constexpr int N3 = N * N * N, A = RES ? 8 : 7;
@@ -242,10 +216,10 @@ static int launch_ax_tma_t(const Level& lv, const float* u, float* y, int NE, co
   const size_t smem = (size_t)((2 * A + 2) * NE * N3 + ((N * N + 3) / 4) * 4 + 4) * sizeof(float) +
                       2 * sizeof(uint64_t);
   static const cudaError_t attr = cudaFuncSetAttribute(
-      ax_tma_kernel<N, RES, FOLD>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+      ax_tma_kernel<N, RES>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   SE_CUDA(attr);
   int per_sm = 0;
-  SE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ax_tma_kernel<N, RES, FOLD>, threads, smem));
+  SE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ax_tma_kernel<N, RES>, threads, smem));
   SE_CHECK(per_sm >= 1, SE_ECUDA, "ax_tma: no resident block fits (NE=%d)", NE);
   int dev = 0, sms = 0;
   SE_CUDA(cudaGetDevice(&dev));
@@ -253,20 +227,17 @@ static int launch_ax_tma_t(const Level& lv, const float* u, float* y, int NE, co
   const int64_t groups = (lv.E + NE - 1) / NE;
   int64_t grid = (int64_t)sms * per_sm;
   if (grid > groups) grid = groups;
-  ax_tma_kernel<N, RES, FOLD><<<(unsigned)grid, threads, smem, s>>>(lv.E, NE, groups, u, lv.G32, lv.L,
-                                                                     lv.D32, y, sub, lv.nel[0],
-                                                                     lv.nel[1], lv.nel[2], lv.pflag,
-                                                                     lv.pstatus);
+  ax_tma_kernel<N, RES><<<(unsigned)grid, threads, smem, s>>>(lv.E, NE, groups, u, lv.G32, lv.L,
+                                                               lv.D32, y, sub, lv.nel[0],
+                                                               lv.nel[1], lv.nel[2], lv.pflag,
+                                                               lv.pstatus);
   SE_LAUNCH_CHECK();
   return SE_OK;
 }
 
 template <int N>
 static int launch_ax_tma(const Level& lv, const float* u, float* y, int NE, const float* sub,
-                         cudaStream_t s, bool fold = false) {
-  if (fold)
-    return sub ? launch_ax_tma_t<N, true, true>(lv, u, y, NE, sub, s)
-               : launch_ax_tma_t<N, false, true>(lv, u, y, NE, sub, s);
+                         cudaStream_t s) {
   return sub ? launch_ax_tma_t<N, true>(lv, u, y, NE, sub, s)
              : launch_ax_tma_t<N, false>(lv, u, y, NE, sub, s);
 }
@@ -285,16 +256,14 @@ int ax_tma_group(int p) {
 
 bool ax_tma_supported(int p) { return (p + 1) % 2 == 0 && p + 1 >= 2 && p + 1 <= 10; }
 
-int ax_local_tma(const Level& lv, const float* u, float* y, cudaStream_t s, const float* sub,
-                 bool fold) {
+int ax_local_tma(const Level& lv, const float* u, float* y, cudaStream_t s, const float* sub) {
   const int NE = ax_tma_group(lv.p);
-  SE_CHECK(!fold || lv.nel[0] >= 1, SE_EINVAL, "ax_tma: the folded form needs the box lattice");
   switch (lv.N) {
-    case 2: return launch_ax_tma<2>(lv, u, y, NE, sub, s, fold);
-    case 4: return launch_ax_tma<4>(lv, u, y, NE, sub, s, fold);
-    case 6: return launch_ax_tma<6>(lv, u, y, NE, sub, s, fold);
-    case 8: return launch_ax_tma<8>(lv, u, y, NE, sub, s, fold);
-    case 10: return launch_ax_tma<10>(lv, u, y, NE, sub, s, fold);
+    case 2: return launch_ax_tma<2>(lv, u, y, NE, sub, s);
+    case 4: return launch_ax_tma<4>(lv, u, y, NE, sub, s);
+    case 6: return launch_ax_tma<6>(lv, u, y, NE, sub, s);
+    case 8: return launch_ax_tma<8>(lv, u, y, NE, sub, s);
+    case 10: return launch_ax_tma<10>(lv, u, y, NE, sub, s);
     default: set_error("ax_tma: unsupported N=%d", lv.N); return SE_EINVAL;
   }
 }

@@ -231,29 +231,20 @@ int build_level_gsmap(Level& lv, Allocs& allocs, cudaStream_t s);
 // FP64 operator with the x part of QQ^T and the mask inside the even-odd kernel (even N, box
 // lattice, sweeps): y = A u, or b - A u when b is given; the x-interfaces between the kernel's
 // blocks, then the y and z sweeps follow (ax.cu).
-// The same for the FP32 pipelined operator (ax_tma_kernel<FOLD>).
 bool ax_fold_ok(const Level& lv);
-bool ax_fold_ok32(const Level& lv);
 int ax_apply_folded(const Level& lv, const double* u, double* y, const double* b, cudaStream_t s);
-int ax_apply_folded32(const Level& lv, const float* u, float* y, const float* b, cudaStream_t s);
 template <class T>
 inline int ax_apply(const Level& lv, const T* u, T* y, cudaStream_t s) {
-  if constexpr (sizeof(T) == 8) {
+  if constexpr (sizeof(T) == 8)
     if (ax_fold_ok(lv)) return ax_apply_folded(lv, u, y, nullptr, s);
-  } else {
-    if (ax_fold_ok32(lv)) return ax_apply_folded32(lv, u, y, nullptr, s);
-  }
   SE_TRY(ax_local<T>(lv, u, y, false, s));
   return gs_apply<T>(lv, y, true, s);
 }
 // r = b - A u (masked), one operator pass: no separate subtraction over the vector.
 template <class T>
 inline int residual_apply(const Level& lv, const T* b, const T* u, T* r, cudaStream_t s) {
-  if constexpr (sizeof(T) == 8) {
+  if constexpr (sizeof(T) == 8)
     if (ax_fold_ok(lv)) return ax_apply_folded(lv, u, r, b, s);
-  } else {
-    if (ax_fold_ok32(lv)) return ax_apply_folded32(lv, u, r, b, s);
-  }
   SE_TRY(ax_local<T>(lv, u, r, false, s, b));
   return gs_apply<T>(lv, r, true, s);
 }
@@ -390,8 +381,7 @@ int ax_elems_per_block(int p, bool fp32);
 // FP32 Ax pipelined with TMA bulk copies (even N only); device status of its bounded waits.
 bool ax_tma_supported(int p);
 int ax_tma_group(int p);
-int ax_local_tma(const Level& lv, const float* u, float* y, cudaStream_t s, const float* sub,
-                 bool fold = false);
+int ax_local_tma(const Level& lv, const float* u, float* y, cudaStream_t s, const float* sub);
 // FP64 Ax with even-odd folded contractions (even N).
 bool ax_eo_supported(int p);
 void ax_eo_tables(const Basis1D& b, double* out);
@@ -399,9 +389,8 @@ int ax_local_eo(const Level& lv, const double* u, double* y, cudaStream_t s, con
 // The same with the x-interface sums of the block's elements and the mask (NE elements per block).
 int ax_local_eo_fold(const Level& lv, const double* u, double* y, const double* sub, int NE,
                      cudaStream_t s);
-// The x-interfaces between consecutive blocks (groups) of NE elements of a folded operator.
-template <class T>
-int gs_fold_fixup(const Level& lv, T* y, int NE, cudaStream_t s);
+// The x-interfaces between consecutive blocks of ax_local_eo_fold (NE elements per block).
+int gs_fold_fixup(const Level& lv, double* y, int NE, cudaStream_t s);
 // The same contractions in df64 arithmetic (FP64 in and out); needs lv.Gdf and lv.eodf.
 int ax_local_eo_df(const Level& lv, const double* u, double* y, cudaStream_t s, const double* sub);
 // b[i] = nearest df64 of a[i] (device arrays, stream-ordered).
