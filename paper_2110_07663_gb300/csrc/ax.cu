@@ -239,19 +239,13 @@ __host__ __device__ constexpr int gs_x_seg() { return sizeof(T) == 4 ? 16 : 8; }
 // With Dirichlet bits (mask), the x sweep also applies the mask: a copy whose node lies on a
 // Dirichlet face is zeroed before the sums and stored as zero (every copy of every element passes
 // through some run, and a node's copies are all masked or none, so overlapping runs agree).
-// Warps of the x sweep of an nx x ny x nz lattice.
 template <typename T, int N>
-__host__ __device__ inline int gs_x_warps(int nx, int ny, int nz) {
-  constexpr int R = 32 / N, NG = (N * N + R - 1) / R, SEG = gs_x_seg<T>();
-  return ny * nz * NG * ((nx - 1 + SEG - 1) / SEG);
-}
-
-template <typename T, int N>
-__device__ __forceinline__ void gs_sweep_x_body(int nx, int ny, int nz, int bits, T* __restrict__ u,
-                                                int warp, int lane) {
+__global__ void __launch_bounds__(256) gs_sweep_x(int nx, int ny, int nz, int bits, T* __restrict__ u) {
   constexpr int N3 = N * N * N, R = 32 / N, NG = (N * N + R - 1) / R, SEG = gs_x_seg<T>();
   // index decomposition in 32-bit integers (every count here is below L < 2^31; a 64-bit
   // division by a run-time value costs an order of magnitude more instructions)
+  const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
   const int nseg = (nx - 1 + SEG - 1) / SEG;
   const int items = ny * nz * NG * nseg;               // (row group, run, element row along x)
   if (warp >= items) return;                           // whole warps
@@ -303,23 +297,18 @@ __device__ __forceinline__ void gs_sweep_x_body(int nx, int ny, int nz, int bits
   }
 }
 
-template <typename T, int N>
-__global__ void __launch_bounds__(256) gs_sweep_x(int nx, int ny, int nz, int bits, T* __restrict__ u) {
-  gs_sweep_x_body<T, N>(nx, ny, nz, bits, u, (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5),
-                        (int)(threadIdx.x & 31));
-}
-
 // y and z sweeps: each thread adds GS_YZ_PAIRS interface pairs, strided so that a warp's
 // accesses stay contiguous, all loads issued before any store (these kernels are bound by memory
 // latency, not bandwidth).
 constexpr int GS_YZ_PAIRS = 4;
 
 template <typename T, int N>
-__device__ __forceinline__ void gs_sweep_y_body(int nx, int ny, int nz, T* __restrict__ u, int t0) {
+__global__ void gs_sweep_y(int nx, int ny, int nz, T* __restrict__ u) {
   constexpr int N3 = N * N * N, K = GS_YZ_PAIRS;
   const int nif = ny - 1;
   const int total = N * N * nx * nif * nz;  // < L < 2^31: 32-bit index arithmetic
   const int nthr = (total + K - 1) / K;
+  const int t0 = (int)(blockIdx.x * blockDim.x + threadIdx.x);
   if (t0 >= nthr) return;
   int64_t ia[K], ib[K];
   T a[K], b[K];
@@ -353,11 +342,12 @@ __device__ __forceinline__ void gs_sweep_y_body(int nx, int ny, int nz, T* __res
 }
 
 template <typename T, int N>
-__device__ __forceinline__ void gs_sweep_z_body(int nx, int ny, int nz, T* __restrict__ u, int t0) {
+__global__ void gs_sweep_z(int nx, int ny, int nz, T* __restrict__ u) {
   constexpr int N2 = N * N, N3 = N2 * N, K = GS_YZ_PAIRS;
   const int nif = nz - 1;
   const int total = N2 * nx * ny * nif;  // < L < 2^31: 32-bit index arithmetic
   const int nthr = (total + K - 1) / K;
+  const int t0 = (int)(blockIdx.x * blockDim.x + threadIdx.x);
   if (t0 >= nthr) return;
   int64_t ia[K], ib[K];
   T a[K], b[K];
@@ -381,52 +371,6 @@ __device__ __forceinline__ void gs_sweep_z_body(int nx, int ny, int nz, T* __res
     u[ia[kk]] = sum;
     u[ib[kk]] = sum;
   }
-}
-
-template <typename T, int N>
-__global__ void gs_sweep_y(int nx, int ny, int nz, T* __restrict__ u) {
-  gs_sweep_y_body<T, N>(nx, ny, nz, u, (int)(blockIdx.x * blockDim.x + threadIdx.x));
-}
-
-template <typename T, int N>
-__global__ void gs_sweep_z(int nx, int ny, int nz, T* __restrict__ u) {
-  gs_sweep_z_body<T, N>(nx, ny, nz, u, (int)(blockIdx.x * blockDim.x + threadIdx.x));
-}
-
-// Sweeps over a union of box lattices (the levels of a batch group: the members' elements end to
-// end).  Work item t of a kernel belongs to the member m with pre[m] <= t < pre[m + 1] (a binary
-// search over the few members); within it the single-lattice sweep runs on the member's
-// dimensions and elements.
-__device__ __forceinline__ int lat_member(const int* __restrict__ pre, int n, int t) {
-  int lo = 0, hi = n;
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (__ldg(pre + mid) <= t) lo = mid;
-    else hi = mid;
-  }
-  return lo;
-}
-
-template <typename T, int N>
-__global__ void __launch_bounds__(256) gs_msweep_x(LatTable lt, const int* __restrict__ pre, T* __restrict__ u) {
-  const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  if (warp >= __ldg(pre + lt.n)) return;  // whole warps
-  const int m = lat_member(pre, lt.n, warp);
-  constexpr int N3 = N * N * N;
-  gs_sweep_x_body<T, N>(__ldg(lt.dims + 3 * m), __ldg(lt.dims + 3 * m + 1), __ldg(lt.dims + 3 * m + 2), 0,
-                        u + __ldg(lt.e0 + m) * N3, warp - __ldg(pre + m), (int)(threadIdx.x & 31));
-}
-
-template <typename T, int N>
-__global__ void gs_msweep_yz(LatTable lt, const int* __restrict__ pre, T* __restrict__ u, int dir) {
-  const int t = (int)(blockIdx.x * blockDim.x + threadIdx.x);
-  if (t >= __ldg(pre + lt.n)) return;
-  const int m = lat_member(pre, lt.n, t);
-  constexpr int N3 = N * N * N;
-  const int nx = __ldg(lt.dims + 3 * m), ny = __ldg(lt.dims + 3 * m + 1), nz = __ldg(lt.dims + 3 * m + 2);
-  T* um = u + __ldg(lt.e0 + m) * N3;
-  if (dir == 1) gs_sweep_y_body<T, N>(nx, ny, nz, um, t - __ldg(pre + m));
-  else gs_sweep_z_body<T, N>(nx, ny, nz, um, t - __ldg(pre + m));
 }
 
 // Zero the copies on the Dirichlet faces (bit f of `bits`: face f = x0, x1, y0, y1, z0, z1).
@@ -519,11 +463,7 @@ static double interface_copies(const Level& lv) {
 }
 
 template <class T>
-static int gs_multi(const Level& lv, T* u, bool mask, cudaStream_t s);
-
-template <class T>
 int gs_apply(const Level& lv, T* u, bool mask, cudaStream_t s) {
-  if (lv.lat.n > 0) return gs_multi<T>(lv, u, mask, s);
   if (lv.gsm_ids) return gsmap_apply<T>(lv, u, mask, s);
   const double shared = interface_copies(lv);
   const double bytes = shared * 2.0 * sizeof(T), flops = shared;
@@ -600,107 +540,6 @@ template <typename T>
 __global__ void mask_kernel(int64_t L, const uint8_t* __restrict__ pflag, T* __restrict__ u) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx < L && !(pflag[idx] & PF_FREE)) u[idx] = T(0);
-}
-
-// QQ^T of a union of box lattices: the mask by the point flags (a masked node has all its copies
-// on a Dirichlet face), then the x, y and z sweeps of every member, one launch each.
-template <class T, int N>
-static int gs_multi_t(const Level& lv, T* u, bool mask, cudaStream_t s) {
-  const int n = lv.lat.n;
-  const int* pre = lv.lat_pre;
-  SE_CHECK(lv.lat_pre != nullptr, SE_EINVAL, "gs: union level without member tables");
-  const int* tot = lv.lat_tot;
-  const int var = prof_variant<T>(lv.p);
-  if (mask) {
-    ProfScope prof(SE_K_GS, s, (double)lv.L, (double)lv.L, 0.0, var);
-    mask_kernel<T><<<grid_for(lv.L, 256), 256, 0, s>>>(lv.L, lv.pflag, u);
-    SE_LAUNCH_CHECK();
-  }
-  const int xs = sizeof(T) == 4 ? 0 : 1;
-  if (tot[xs] > 0) {
-    ProfScope prof(SE_K_GS, s, (double)lv.L, lv.lat_copies * 2.0 * sizeof(T), lv.lat_copies, var);
-    gs_msweep_x<T, N><<<grid_for(32 * (int64_t)tot[xs], 256), 256, 0, s>>>(lv.lat, pre + xs * (n + 1), u);
-    SE_LAUNCH_CHECK();
-  }
-  for (int d = 1; d <= 2; ++d) {
-    if (tot[1 + d] == 0) continue;
-    ProfScope prof(SE_K_GS, s, (double)tot[1 + d], 0.0, 0.0, var);
-    gs_msweep_yz<T, N><<<grid_for(tot[1 + d], 256), 256, 0, s>>>(lv.lat, pre + (1 + d) * (n + 1), u, d);
-    SE_LAUNCH_CHECK();
-  }
-  return SE_OK;
-}
-
-template <class T>
-static int gs_multi(const Level& lv, T* u, bool mask, cudaStream_t s) {
-  switch (lv.N) {
-#define SE_GSM_CASE(NN) \
-  case NN: return gs_multi_t<T, NN>(lv, u, mask, s);
-    SE_GSM_CASE(2) SE_GSM_CASE(3) SE_GSM_CASE(4) SE_GSM_CASE(5) SE_GSM_CASE(6)
-    SE_GSM_CASE(7) SE_GSM_CASE(8) SE_GSM_CASE(9) SE_GSM_CASE(10) SE_GSM_CASE(11)
-#undef SE_GSM_CASE
-    default: set_error("gs: unsupported N=%d", lv.N); return SE_EINVAL;
-  }
-}
-
-template <int N>
-static void lattice_counts(const Level& a, int c[4]) {
-  const int nx = a.nel[0], ny = a.nel[1], nz = a.nel[2], K = GS_YZ_PAIRS;
-  c[0] = nx > 1 ? gs_x_warps<float, N>(nx, ny, nz) : 0;
-  c[1] = nx > 1 ? gs_x_warps<double, N>(nx, ny, nz) : 0;
-  c[2] = (N * N * nx * (ny - 1) * nz + K - 1) / K;
-  c[3] = (N * N * nx * ny * (nz - 1) + K - 1) / K;
-}
-
-int lattice_table(Level& u, const std::vector<const Level*>& members, Allocs& allocs, cudaStream_t s) {
-  const int n = (int)members.size();
-  SE_CHECK(n >= 1, SE_EINVAL, "lattice_table: no member");
-  std::vector<int> dims(3 * (size_t)n);
-  std::vector<int64_t> e0(n);
-  std::vector<int> pre(4 * (size_t)(n + 1), 0);  // [4][n + 1] prefix counts
-  int64_t eo = 0;
-  double copies = 0.0;
-  for (int m = 0; m < n; ++m) {
-    const Level& a = *members[m];
-    SE_CHECK(a.N == u.N && a.nel[0] >= 1 && a.nel[1] >= 1 && a.nel[2] >= 1, SE_EINVAL,
-             "lattice_table: member %d is not a box lattice of order %d", m, u.p);
-    for (int d = 0; d < 3; ++d) dims[3 * m + d] = a.nel[d];
-    e0[m] = eo;
-    eo += a.E;
-    copies += interface_copies(a);
-    int c[4] = {0, 0, 0, 0};
-    switch (u.N) {
-#define SE_LC_CASE(NN) \
-  case NN: lattice_counts<NN>(a, c); break;
-      SE_LC_CASE(2) SE_LC_CASE(3) SE_LC_CASE(4) SE_LC_CASE(5) SE_LC_CASE(6)
-      SE_LC_CASE(7) SE_LC_CASE(8) SE_LC_CASE(9) SE_LC_CASE(10) SE_LC_CASE(11)
-#undef SE_LC_CASE
-      default: set_error("lattice_table: unsupported N=%d", u.N); return SE_EINVAL;
-    }
-    for (int k = 0; k < 4; ++k) {
-      const int64_t next = (int64_t)pre[k * (n + 1) + m] + c[k];
-      SE_CHECK(next < ((int64_t)1 << 31), SE_EINVAL, "lattice_table: too much work for 32-bit counts");
-      pre[k * (n + 1) + m + 1] = (int)next;
-    }
-  }
-  SE_CHECK(eo == u.E, SE_EINVAL, "lattice_table: members hold %lld elements, the level %lld",
-           (long long)eo, (long long)u.E);
-  for (int k = 0; k < 4; ++k) u.lat_tot[k] = pre[k * (n + 1) + n];
-  int* ddims = nullptr;
-  int64_t* de0 = nullptr;
-  int* dpre = nullptr;
-  SE_TRY(dmalloc(allocs, &ddims, dims.size()));
-  SE_TRY(dmalloc(allocs, &de0, e0.size()));
-  SE_TRY(dmalloc(allocs, &dpre, pre.size()));
-  SE_TRY(h2d(ddims, dims.data(), dims.size() * sizeof(int), s));
-  SE_TRY(h2d(de0, e0.data(), e0.size() * sizeof(int64_t), s));
-  SE_TRY(h2d(dpre, pre.data(), pre.size() * sizeof(int), s));
-  u.lat.n = n;
-  u.lat.dims = ddims;
-  u.lat.e0 = de0;
-  u.lat_pre = dpre;
-  u.lat_copies = copies;
-  return SE_OK;
 }
 
 template int ax_local<double>(const Level&, const double*, double*, bool, cudaStream_t, const double*);

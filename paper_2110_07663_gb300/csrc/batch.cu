@@ -368,8 +368,15 @@ static int build_union_level(se_pmg_s* U, int l, const std::vector<se_pmg_s*>& P
       SE_TRY(dmalloc(A, &u.fdm_dinv64, (size_t)u.E * PB * PB * PB));
     }
   }
-  int64_t eo = 0, lo = 0;
-  std::vector<const Level*> members(n);
+  std::vector<int64_t> gid((size_t)u.L);
+  std::vector<uint8_t> dir((size_t)u.L);
+  int64_t eo = 0, lo = 0, go = 0;
+  int* l2g = nullptr;
+  int64_t maxL = 0;
+  for (const se_pmg_s* P : Pm) maxL = std::max(maxL, P->lv[l]->L);
+  SE_TRY(dmalloc_transient(reinterpret_cast<void**>(&l2g), (size_t)maxL * sizeof(int), s));
+  std::vector<int> g32((size_t)maxL);
+  std::vector<uint8_t> pf((size_t)maxL);
   int rc = SE_OK;
   for (int m = 0; m < n && rc == SE_OK; ++m) {
     const Level& a = *Pm[m]->lv[l];
@@ -409,14 +416,27 @@ static int build_union_level(se_pmg_s* U, int l, const std::vector<se_pmg_s*>& P
       set_error("se_batch: union level kernel launch failed");
       rc = SE_ECUDA;
     }
-    members[m] = &a;
+    // global ids of the member's lattice, shifted past the previous members'
+    if (rc == SE_OK) rc = local_to_global(a, l2g, s);
+    if (rc == SE_OK &&
+        (cudaMemcpyAsync(g32.data(), l2g, (size_t)a.L * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+         cudaMemcpyAsync(pf.data(), a.pflag, (size_t)a.L, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+         cudaStreamSynchronize(s) != cudaSuccess)) {
+      set_error("se_batch: %s", cudaGetErrorString(cudaGetLastError()));
+      rc = SE_ECUDA;
+    }
+    for (int64_t q = 0; q < a.L && rc == SE_OK; ++q) {
+      gid[(size_t)(lo + q)] = go + g32[(size_t)q];
+      dir[(size_t)(lo + q)] = (pf[(size_t)q] & PF_FREE) ? 0 : 1;
+    }
     eo += a.E;
     lo += a.L;
+    go += a.n_global;
     (void)N3;
   }
+  cudaFreeAsync(l2g, s);
   SE_TRY(rc);
-  // QQ^T of the union: every member is a box lattice, so its direction sweeps, all members at once
-  SE_TRY(lattice_table(u, members, A, s));
+  SE_TRY(build_gsmap_from_gid(u, gid.data(), dir.data(), A, s));
   U->lv[l] = &U->owned[l];
   return SE_OK;
 }

@@ -154,6 +154,14 @@ int build_level_gsmap(Level& lv, Allocs& allocs, cudaStream_t s) {
   return gsmap_upload(h, lv, allocs, s);
 }
 
+int build_gsmap_from_gid(Level& lv, const int64_t* gid, const uint8_t* dirichlet, Allocs& allocs,
+                         cudaStream_t s) {
+  SE_TRY(gsmap_validate(lv.L, gid));
+  GsMapHost h;
+  SE_TRY(gsmap_build_host(lv.L, gid, dirichlet, h));
+  return gsmap_upload(h, lv, allocs, s);
+}
+
 // ------------------------------------------------------------------ device
 template <typename T, int M>
 __device__ __forceinline__ void gsm_group(const int* __restrict__ ids, T* __restrict__ u, bool mask) {

@@ -99,13 +99,6 @@ double uniform01(uint64_t seed, uint64_t c);
 // Dirichlet face).
 constexpr uint8_t PF_FREE = 0x80;
 
-// Members of a union of box lattices (device arrays): dimensions and first element of each.
-struct LatTable {
-  int n = 0;
-  const int* dims = nullptr;    // [n][3]: nx, ny, nz
-  const int64_t* e0 = nullptr;  // [n]
-};
-
 // ------------------------------------------------------------------ one discretisation level
 struct Level {
   int p = 0, N = 0;
@@ -152,13 +145,6 @@ struct Level {
   int64_t gsm_n[5] = {0, 0, 0, 0, 0};    // groups of 2, 4, 8, other copies; masked single copies
   int64_t gsm_seg[5] = {0, 0, 0, 0, 0};
   int64_t gsm_entries = 0;   // local ids in groups of two or more
-  // union of box lattices (the levels of a batch group: members' elements end to end): QQ^T by
-  // the direction sweeps of every member at once (lattice_table, gs_apply)
-  LatTable lat;
-  const int* lat_pre = nullptr;  // [4][lat.n + 1]: prefix counts of x-sweep warps (FP32, FP64),
-                                 // y- and z-sweep threads
-  int lat_tot[4] = {0, 0, 0, 0};  // the four totals (host copy)
-  double lat_copies = 0.0;       // interface copies over all members
   // [1]: set to SE_ETIMEOUT by a pipelined kernel of this level whose bounded wait expired
   // (its output is then invalid); read and cleared by level_pipeline_take
   int* pstatus = nullptr;
@@ -237,9 +223,6 @@ int ax_local(const Level& lv, const T* u, T* y, bool mask_in, cudaStream_t s,
              const T* sub = nullptr);
 template <class T>
 int gs_apply(const Level& lv, T* u, bool mask, cudaStream_t s);
-// Member tables of a union level u (members' levels in order, all of u's order): QQ^T of u then
-// runs the members' direction sweeps in three launches.
-int lattice_table(Level& u, const std::vector<const Level*>& members, Allocs& allocs, cudaStream_t s);
 // QQ^T by the index map of lv (gsm_ids set); gs_apply dispatches to it.
 template <class T>
 int gsmap_apply(const Level& lv, T* u, bool mask, cudaStream_t s);
@@ -362,6 +345,9 @@ int coarse_group_setup(CoarseGroup* g, const Level* const* lv, CoarseWork* const
                        Allocs& allocs, cudaStream_t s);
 template <class T>
 int coarse_group_solve(const CoarseGroup& g, cudaStream_t s);
+// QQ^T index map of a level from host global ids (any labels, int64) and Dirichlet bytes.
+int build_gsmap_from_gid(Level& lv, const int64_t* gid, const uint8_t* dirichlet, Allocs& allocs,
+                         cudaStream_t s);
 
 // ------------------------------------------------------------------ profiling (common.cu)
 // Profiling variant of a launch: polynomial order p (0..31) plus 32 for FP32 arithmetic, plus 64
