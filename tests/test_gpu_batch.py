@@ -75,6 +75,7 @@ def test_batch_groups_match_alone_and_converge():
              ((4, 4, 4), 7, (7, 5, 3, 1), se.SE_FP64, 1), ((3, 4, 3), 7, (7, 5, 3, 1), se.SE_FP64, 1),
              ((4, 3, 4), 5, (5, 3, 1), se.SE_FP64, 0), ((3, 3, 3), 5, (5, 3, 1), se.SE_FP64, 0),
              ((3, 3, 3), 7, (7, 3, 1), se.SE_FP32, 2)]
+    specs.insert(2, ((1, 3, 4), 3, (3, 1), se.SE_FP32, 1))
     probs = [problem(se, torch, nel, p, 40 + i, sch, prec, sm)
              for i, (nel, p, sch, prec, sm) in enumerate(specs)]
     # one problem without a preconditioner (Jacobi PCG): runs alone
@@ -90,9 +91,10 @@ def test_batch_groups_match_alone_and_converge():
         B = se.se_batch_create([(m, P, b, x) for (m, P, b), x in zip(entries, xs)], tol=1e-8)
         try:
             groups, grouped = se.se_batch_info(B)
-            # FP32 RAS p=3 (2), p=7 7-3-1 (2), FP64 RAS 7-5-3-1 (2), FP64 Jacobi p=5 (2), and the
-            # single-member groups of p=5 and p=9; ASM and no preconditioner run alone
-            assert groups == 6 and grouped == 10, (groups, grouped)
+            # FP32 RAS p=3 (3, one member a single element row), p=7 7-3-1 (2), FP64 RAS 7-5-3-1
+            # (2), FP64 Jacobi p=5 (2), and the single-member groups of p=5 and p=9; ASM and no
+            # preconditioner run alone
+            assert groups == 6 and grouped == 11, (groups, grouped)
             first = None
             for rep in range(2):
                 for x in xs:
@@ -103,7 +105,7 @@ def test_batch_groups_match_alone_and_converge():
                 for k, ((it, xa), st, x, (m, P, b)) in enumerate(zip(alone, stats, xs, entries)):
                     assert st.rel_residual <= 1e-8, (k, st.rel_residual)
                     assert true_rel_residual(se, torch, m, b, x) <= 1.5e-8, k
-                    if k >= 10:   # alone in the graph: the se_solve graph itself
+                    if k >= 11:   # alone in the graph: the se_solve graph itself
                         assert st.iterations == it and torch.equal(x, xa), k
                     else:
                         assert abs(st.iterations - it) <= 1, (k, st.iterations, it)
