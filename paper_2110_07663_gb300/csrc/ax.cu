@@ -518,13 +518,14 @@ static int gs_after_fold(const Level& lv, double* y, int NE, cudaStream_t s) {
   return SE_OK;
 }
 
-int ax_apply_folded(const Level& lv, const double* u, double* y, const double* b, cudaStream_t s) {
+int ax_apply_folded(const Level& lv, const double* u, double* y, const double* b, cudaStream_t s,
+                    const double* dinv) {
   const int NE = ax_elems_per_block(lv.p, false);
   {
     const double pts = (double)lv.L;
     ProfScope prof(SE_K_AX, s, pts, pts * ((b ? 9.0 : 8.0) * sizeof(double) + 1.0),
                    pts * (12.0 * lv.N + 15.0), prof_variant<double>(lv.p));
-    SE_TRY(ax_local_eo_fold(lv, u, y, b, NE, s));
+    SE_TRY(ax_local_eo_fold(lv, u, y, b, NE, s, dinv));
   }
   switch (lv.N) {
     case 2: return gs_after_fold<2>(lv, y, NE, s);

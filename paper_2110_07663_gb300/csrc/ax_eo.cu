@@ -93,14 +93,17 @@ __device__ __forceinline__ void eo_apply(const T* __restrict__ Ep, const T* __re
 // x-interface node get left + right (the same bits on both sides), and it applies the Dirichlet
 // mask (bit f of `bits`: face f = x0, x1, y0, y1, z0, z1 is Dirichlet); the x-interfaces between
 // consecutive blocks are left to gs_fold_fixup_x.
-template <int N, typename T, bool FOLD = false>
+// SCALE (with FOLD): the input is dinv .* u, formed as it is loaded (the first step of a
+// Jacobi-Chebyshev smoother applies A to D^-1 r without storing D^-1 r).
+template <int N, typename T, bool FOLD = false, bool SCALE = false>
 __global__ void __launch_bounds__(512) ax_eo_kernel(int64_t E, int NE, const double* __restrict__ u,
                                                     const T* __restrict__ G, int64_t L,
                                                     const T* __restrict__ tables,
                                                     double* __restrict__ y,
                                                     const uint8_t* __restrict__ pflag,
                                                     const double* __restrict__ sub, int nx = 0,
-                                                    int ny = 0, int nz = 0, int bits = 0) {
+                                                    int ny = 0, int nz = 0, int bits = 0,
+                                                    const double* __restrict__ dinv = nullptr) {
   constexpr int N2 = N * N, N3 = N * N * N, H = N / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tab = reinterpret_cast<T*>(smem_raw);                    // 4 H^2
@@ -117,7 +120,10 @@ __global__ void __launch_bounds__(512) ax_eo_kernel(int64_t E, int NE, const dou
   const int64_t eb = e * N3;
   if (valid) {
 #pragma unroll
-    for (int q = 0; q < N; ++q) su[t + N2 * q] = from_io<T>(u[eb + t + N2 * q]);
+    for (int q = 0; q < N; ++q) {
+      if constexpr (SCALE) su[t + N2 * q] = u[eb + t + N2 * q] * dinv[eb + t + N2 * q];
+      else su[t + N2 * q] = from_io<T>(u[eb + t + N2 * q]);
+    }
   }
   __syncthreads();
   const T* EpD = tab;
@@ -233,24 +239,30 @@ __global__ void gs_fold_fixup_x(int64_t E, int NE, int nx, double* __restrict__ 
   y[ib] = v;
 }
 
-template <int N>
-static int launch_ax_eo_fold(const Level& lv, const double* u, double* y, const double* sub, int NE,
-                             cudaStream_t s) {
+template <int N, bool SCALE>
+static int launch_ax_eo_fold_t(const Level& lv, const double* u, double* y, const double* sub, int NE,
+                               const double* dinv, cudaStream_t s) {
   constexpr int H = N / 2;
   const int threads = NE * N * N;
   const size_t smem = (4 * H * H + (size_t)NE * 4 * N * N * N) * sizeof(double);
   static const cudaError_t attr = cudaFuncSetAttribute(
-      ax_eo_kernel<N, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      ax_eo_kernel<N, double, true, SCALE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   SE_CUDA(attr);
   const unsigned blocks = (unsigned)((lv.E + NE - 1) / NE);
   int bits = 0;
   for (int f = 0; f < 6; ++f)
     if (lv.bc[f] == SE_BC_DIRICHLET) bits |= 1 << f;
-  ax_eo_kernel<N, double, true><<<blocks, threads, smem, s>>>(lv.E, NE, u, lv.G64, lv.L, lv.eo64, y,
-                                                              lv.pflag, sub, lv.nel[0], lv.nel[1],
-                                                              lv.nel[2], bits);
+  ax_eo_kernel<N, double, true, SCALE><<<blocks, threads, smem, s>>>(
+      lv.E, NE, u, lv.G64, lv.L, lv.eo64, y, lv.pflag, sub, lv.nel[0], lv.nel[1], lv.nel[2], bits, dinv);
   SE_LAUNCH_CHECK();
   return SE_OK;
+}
+
+template <int N>
+static int launch_ax_eo_fold(const Level& lv, const double* u, double* y, const double* sub, int NE,
+                             cudaStream_t s, const double* dinv) {
+  return dinv ? launch_ax_eo_fold_t<N, true>(lv, u, y, sub, NE, dinv, s)
+              : launch_ax_eo_fold_t<N, false>(lv, u, y, sub, NE, nullptr, s);
 }
 
 template <int N, typename T>
@@ -302,14 +314,14 @@ int ax_local_eo(const Level& lv, const double* u, double* y, cudaStream_t s, con
 }
 
 int ax_local_eo_fold(const Level& lv, const double* u, double* y, const double* sub, int NE,
-                     cudaStream_t s) {
+                     cudaStream_t s, const double* dinv) {
   SE_CHECK(lv.eo64 != nullptr && lv.nel[0] >= 1, SE_EINVAL, "ax_eo_fold: folded tables or lattice missing");
   switch (lv.N) {
-    case 2: return launch_ax_eo_fold<2>(lv, u, y, sub, NE, s);
-    case 4: return launch_ax_eo_fold<4>(lv, u, y, sub, NE, s);
-    case 6: return launch_ax_eo_fold<6>(lv, u, y, sub, NE, s);
-    case 8: return launch_ax_eo_fold<8>(lv, u, y, sub, NE, s);
-    case 10: return launch_ax_eo_fold<10>(lv, u, y, sub, NE, s);
+    case 2: return launch_ax_eo_fold<2>(lv, u, y, sub, NE, s, dinv);
+    case 4: return launch_ax_eo_fold<4>(lv, u, y, sub, NE, s, dinv);
+    case 6: return launch_ax_eo_fold<6>(lv, u, y, sub, NE, s, dinv);
+    case 8: return launch_ax_eo_fold<8>(lv, u, y, sub, NE, s, dinv);
+    case 10: return launch_ax_eo_fold<10>(lv, u, y, sub, NE, s, dinv);
     default: set_error("ax_eo_fold: unsupported N=%d", lv.N); return SE_EINVAL;
   }
 }

@@ -152,16 +152,18 @@ template int scale_mul<float>(const float*, const float*, float*, int64_t, cudaS
 // the rounding of an FMA chain.  The constants are formed on the host in FP64:
 //   k_d = 1 + c1, k_r = scale (1 + c1) + c2, c1s = c1 scale, k_s = -scale,
 //   k_sl = -c2 scale (from_r) or -c2, the weight of the surrogate output in the last update.
-template <class T, bool FIRST, bool FROM_R, bool LAST>
+// RS (FROM_R only): the smoothed residual of the first step is dinv .* rin, formed here.
+template <class T, bool FIRST, bool FROM_R, bool LAST, bool RS = false>
 __global__ void cheb_update_kernel(T* __restrict__ x, T* __restrict__ d, T* __restrict__ r,
                                    const T* __restrict__ sv, const T* __restrict__ dinv, int64_t n,
-                                   T c1, T c2, T scale, T k_d, T k_r, T c1s, T k_s, T k_sl) {
+                                   T c1, T c2, T scale, T k_d, T k_r, T c1s, T k_s, T k_sl,
+                                   const T* __restrict__ rin) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   // every load of this instantiation is unconditional, so all are in flight together
-  const T r0 = r[i];
   const T s0 = sv[i];
   const T di = dinv ? dinv[i] : T(1);
+  const T r0 = RS ? di * rin[i] : r[i];
   const T d0 = FROM_R ? T(0) : d[i];
   const T x0 = FIRST ? T(0) : x[i];
   if constexpr (LAST) {
@@ -186,34 +188,37 @@ __global__ void cheb_update_kernel(T* __restrict__ x, T* __restrict__ d, T* __re
 }
 template <class T>
 int cheb_update(T* x, T* d, T* r, const T* sv, const T* dinv, int64_t n, T c1, T c2, bool first,
-                cudaStream_t s, T scale, bool from_r, bool last) {
+                cudaStream_t s, T scale, bool from_r, bool last, const T* rin) {
+  SE_CHECK(!rin || (from_r && dinv), SE_EINVAL, "cheb_update: a scaled residual needs the first step and dinv");
   const double words = 2.0 + (dinv ? 1.0 : 0.0) + (from_r ? 0.0 : 1.0) + (first ? 0.0 : 1.0) +
                        (last ? 1.0 : 3.0);
   ProfScope prof(SE_K_CHEBY_UPD, s, (double)n, words * n * sizeof(T), 6.0 * n, prof_variant<T>(0));
   const unsigned g = grid_for(n, 256);
-  const int key = (first ? 4 : 0) + (from_r ? 2 : 0) + (last ? 1 : 0);
+  const int key = (rin ? 8 : 0) + (first ? 4 : 0) + (from_r ? 2 : 0) + (last ? 1 : 0);
   const double C1 = (double)c1, C2 = (double)c2, SC = (double)scale;
   const T k_d = T(1.0 + C1), k_r = T(SC * (1.0 + C1) + C2), c1s = T(C1 * SC), k_s = T(-SC);
   const T k_sl = T(from_r ? -C2 * SC : -C2);
   switch (key) {
-#define SE_CHEB_CASE(K, F, R, L)                                                                 \
+#define SE_CHEB_CASE(K, F, R, L, RS)                                                             \
   case K:                                                                                        \
-    cheb_update_kernel<T, F, R, L><<<g, 256, 0, s>>>(x, d, r, sv, dinv, n, c1, c2, scale, k_d, k_r, \
-                                                     c1s, k_s, k_sl);                            \
+    cheb_update_kernel<T, F, R, L, RS><<<g, 256, 0, s>>>(x, d, r, sv, dinv, n, c1, c2, scale, k_d, \
+                                                         k_r, c1s, k_s, k_sl, rin);              \
     break;
-    SE_CHEB_CASE(0, false, false, false) SE_CHEB_CASE(1, false, false, true)
-    SE_CHEB_CASE(2, false, true, false) SE_CHEB_CASE(3, false, true, true)
-    SE_CHEB_CASE(4, true, false, false) SE_CHEB_CASE(5, true, false, true)
-    SE_CHEB_CASE(6, true, true, false) SE_CHEB_CASE(7, true, true, true)
+    SE_CHEB_CASE(0, false, false, false, false) SE_CHEB_CASE(1, false, false, true, false)
+    SE_CHEB_CASE(2, false, true, false, false) SE_CHEB_CASE(3, false, true, true, false)
+    SE_CHEB_CASE(4, true, false, false, false) SE_CHEB_CASE(5, true, false, true, false)
+    SE_CHEB_CASE(6, true, true, false, false) SE_CHEB_CASE(7, true, true, true, false)
+    SE_CHEB_CASE(10, false, true, false, true) SE_CHEB_CASE(11, false, true, true, true)
+    SE_CHEB_CASE(14, true, true, false, true) SE_CHEB_CASE(15, true, true, true, true)
 #undef SE_CHEB_CASE
   }
   SE_LAUNCH_CHECK();
   return SE_OK;
 }
 template int cheb_update<double>(double*, double*, double*, const double*, const double*, int64_t,
-                                 double, double, bool, cudaStream_t, double, bool, bool);
+                                 double, double, bool, cudaStream_t, double, bool, bool, const double*);
 template int cheb_update<float>(float*, float*, float*, const float*, const float*, int64_t, float,
-                                float, bool, cudaStream_t, float, bool, bool);
+                                float, bool, cudaStream_t, float, bool, bool, const float*);
 
 // ------------------------------------------------------------------ FPCG kernels (FP64)
 struct AlphaOp {  // pw = (p, w); alpha = rz / pw

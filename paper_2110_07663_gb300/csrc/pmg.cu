@@ -113,17 +113,26 @@ int cheby(se_pmg_s* P, int l, const T* res, T* x, bool first, cudaStream_t s) {
   const double sigma = theta / delta;
   double rho = 1.0 / sigma;
   const int order = P->desc.cheb_order[l];
-  SE_TRY(smooth<T>(P, l, res, V.cr, s));                         // r = S res
+  const bool jac = P->desc.smoother == SE_SMOOTH_JACOBI;
+  // FP64 Jacobi on a folded-operator level: S res = D^-1 res is not stored; the first step's
+  // operator scales its input as it loads it and the update forms D^-1 res itself
+  bool fused = false;
+  if constexpr (std::is_same<T, double>::value) fused = jac && order >= 1 && ax_fold_ok(lv);
+  if (!fused) SE_TRY(smooth<T>(P, l, res, V.cr, s));             // r = S res
   const T inv_theta = T(1.0 / theta);
   if (order == 0) {                                              // x (+)= r / theta
     if (first) return axpby<T>(inv_theta, V.cr, T(0), V.cr, x, lv.L, s);
     return axpby<T>(inv_theta, V.cr, T(1), x, x, lv.L, s);
   }
-  const bool jac = P->desc.smoother == SE_SMOOTH_JACOBI;
   // d = r / theta is not stored: the first step applies A (and S) to r and scales by 1/theta
   for (int k = 0; k < order; ++k) {
     const bool from_r = k == 0, last = k == order - 1;
-    SE_TRY(ax_apply<T>(lv, from_r ? V.cr : V.cd, V.w, s));       // A d  (A r for the first step)
+    if constexpr (std::is_same<T, double>::value) {
+      if (fused && from_r) SE_TRY(ax_apply_folded(lv, res, V.w, nullptr, s, lv.dinv64));  // A D^-1 res
+      else SE_TRY(ax_apply<T>(lv, from_r ? V.cr : V.cd, V.w, s));
+    } else {
+      SE_TRY(ax_apply<T>(lv, from_r ? V.cr : V.cd, V.w, s));     // A d  (A r for the first step)
+    }
     const double rho_new = 1.0 / (2.0 * sigma - rho);
     const T c1 = T(rho_new * rho), c2 = T(2.0 * rho_new / delta);
     const T* sa = V.w;                                           // Jacobi: dinv .* A d in the update
@@ -132,7 +141,8 @@ int cheby(se_pmg_s* P, int l, const T* res, T* x, bool first, cudaStream_t s) {
       sa = V.sv;
     }
     SE_TRY(cheb_update<T>(x, V.cd, V.cr, sa, jac ? dinv_of<T>(lv) : (const T*)nullptr, lv.L, c1, c2,
-                          first && k == 0, s, inv_theta, from_r, last));  // last: also x += d
+                          first && k == 0, s, inv_theta, from_r, last,
+                          fused && from_r ? res : (const T*)nullptr));  // last: also x += d
     rho = rho_new;
   }
   return SE_OK;

@@ -232,7 +232,9 @@ int build_level_gsmap(Level& lv, Allocs& allocs, cudaStream_t s);
 // lattice, sweeps): y = A u, or b - A u when b is given; the x-interfaces between the kernel's
 // blocks, then the y and z sweeps follow (ax.cu).
 bool ax_fold_ok(const Level& lv);
-int ax_apply_folded(const Level& lv, const double* u, double* y, const double* b, cudaStream_t s);
+// dinv: y = A (dinv .* u) (the input scaled as it is loaded)
+int ax_apply_folded(const Level& lv, const double* u, double* y, const double* b, cudaStream_t s,
+                    const double* dinv = nullptr);
 template <class T>
 inline int ax_apply(const Level& lv, const T* u, T* y, cudaStream_t s) {
   if constexpr (sizeof(T) == 8)
@@ -268,8 +270,11 @@ int fill_zero(T* x, int64_t n, cudaStream_t s);
 template <class T>
 int axpby(T a, const T* x, T b, const T* y, T* out, int64_t n, cudaStream_t s);  // out=a x+b y
 template <class T>
+// rin (first step of a Jacobi smoother, from_r): the smoothed residual is dinv .* rin, formed
+// here instead of read from r (r is then only written, when the step is not the last)
 int cheb_update(T* x, T* d, T* r, const T* sv, const T* dinv, int64_t n, T c1, T c2,
-                bool first, cudaStream_t s, T scale = T(1), bool from_r = false, bool last = false);
+                bool first, cudaStream_t s, T scale = T(1), bool from_r = false, bool last = false,
+                const T* rin = nullptr);
 template <class T>
 int scale_mul(const T* a, const T* b, T* out, int64_t n, cudaStream_t s);  // out = a*b
 // FP64 Krylov kernels with device scalars (slots of Scratch::scal)
@@ -388,7 +393,7 @@ void ax_eo_tables(const Basis1D& b, double* out);
 int ax_local_eo(const Level& lv, const double* u, double* y, cudaStream_t s, const double* sub);
 // The same with the x-interface sums of the block's elements and the mask (NE elements per block).
 int ax_local_eo_fold(const Level& lv, const double* u, double* y, const double* sub, int NE,
-                     cudaStream_t s);
+                     cudaStream_t s, const double* dinv = nullptr);
 // The x-interfaces between consecutive blocks of ax_local_eo_fold (NE elements per block).
 int gs_fold_fixup(const Level& lv, double* y, int NE, cudaStream_t s);
 // The same contractions in df64 arithmetic (FP64 in and out); needs lv.Gdf and lv.eodf.
