@@ -238,10 +238,11 @@ int se_pmg_coarse_stats(se_pmg_t pmg, int reset, int64_t* solves, int64_t* itera
  * library convenience.  It calls no cudaMalloc/cudaFree: the CG vectors, partial sums and
  * barrier words live in one static device array of the library (about 9.5 MB, held by every
  * GPU that loads the library until the process exits), so the coarsest level may have at most
- * 131072 global nodes; larger problems get SE_EINVAL.  The first call on each device looks up
- * the array's device address with that device current; make that first call before any stream
- * capture.  The address is kept for the life of the process, so the entry point must not be
- * called again after cudaDeviceReset on that device.  The caller passes r and x (coarse L-vectors) as for se_pmg_coarse_solve.  All calls
+ * 131072 global nodes; larger problems get SE_EINVAL.  The call synchronises its stream, so it
+ * cannot be captured into a CUDA graph.  The first call on each device looks up the array's
+ * device address with that device current and keeps it for the life of the process, so the entry
+ * point must not be called again after cudaDeviceReset on that device.  The caller passes r and
+ * x (coarse L-vectors) as for se_pmg_coarse_solve.  All calls
  * share the one array, which keeps the last call's contents (the call resets what must start at
  * zero): calls whose work overlaps on the GPU (other streams, other threads, other handles)
  * race and must be serialised by the caller.  Synchronises the stream. */
