@@ -174,7 +174,7 @@ typedef struct se_pmg_desc {
                                     0 <= eig_lo < eig_hi */
   int arnoldi_steps;             /* Arnoldi rounds for lambda-tilde; paper: 10 */
   uint64_t seed;                 /* start-vector stream: level l uses 1000 + l + 7919*seed */
-  double coarse_tol;             /* coarsest-level Jacobi-PCG relative tolerance (1e-4) */
+  double coarse_tol;             /* coarsest-level Jacobi-PCG relative tolerance (1e-2) */
   int coarse_maxit;              /* and iteration cap (500) */
   int precision;                 /* SE_FP64; SE_FP32 for the whole V-cycle except the coarse
                                     solve (Arnoldi and coarse solve stay FP64); SE_DF64: FP64

@@ -23,7 +23,7 @@ static void fill_desc_vec(se_pmg_desc* d, const std::vector<int>& sched, int smo
   d->eig_hi = 1.1;
   d->arnoldi_steps = 10;
   d->seed = 0;
-  d->coarse_tol = 1e-4;
+  d->coarse_tol = 1e-2;  // an inexact coarse solve, the size of one AMG cycle (Sec. 2.2.2)
   d->coarse_maxit = 500;
   d->precision = precision;
 }

@@ -333,7 +333,7 @@ def se_jacobi_diag(m, d, stream=None):
 
 # ----------------------------------------------------------------------------- p-multigrid
 def pmg_desc(schedule, smoother=SE_SMOOTH_RAS, cheb_order=2, eig_lo=0.1, eig_hi=1.1,
-             arnoldi_steps=10, seed=0, coarse_tol=1e-4, coarse_maxit=500, precision=SE_FP64,
+             arnoldi_steps=10, seed=0, coarse_tol=1e-2, coarse_maxit=500, precision=SE_FP64,
              arnoldi_df64=0, cycle=SE_CYCLE_MULTIPLICATIVE):
     d = se_pmg_desc()
     d.nlev = len(schedule)
