@@ -281,6 +281,14 @@ typedef struct se_solve_stats {
  * Returns SE_ENOTCONV (stats filled) if maxit is reached.  Synchronises. */
 int se_solve(se_mesh_t m, se_pmg_t pmg, const double* b, double* x, const se_solve_opts* opts,
              se_solve_stats* stats);
+/* se_solve with HOST buffers (L doubles each): b_host is copied to the device, the solve starts
+ * from x0_host (copied too) or from zero (x0_host == NULL), and the solution is copied to x_host
+ * (which may be x0_host).  The copies run on the solve's stream into device vectors the mesh
+ * keeps from the first call (so a repeated graph solve reuses its graph); page-locked host
+ * buffers give the copy engines' full rate, pageable ones are staged by the driver.  Returns as
+ * se_solve; x_host holds the last iterate also when the status is SE_ENOTCONV.  Synchronises. */
+int se_solve_host(se_mesh_t m, se_pmg_t pmg, const double* b_host, const double* x0_host,
+                  double* x_host, const se_solve_opts* opts, se_solve_stats* stats);
 
 /* ---------------------------------------------------------------- projection (Secs. 3.2 and 4.2) */
 /* A space of up to max_vectors (1..16) prior solutions of A x = b on mesh m, for successive

@@ -189,6 +189,7 @@ struct se_mesh_s {
   float* tmpc32 = nullptr;       // [L], allocated by the first FP32 se_residual
   // outer-solver work vectors, allocated on the first se_solve
   double *sr = nullptr, *sr2 = nullptr, *sz = nullptr, *sp = nullptr, *sw = nullptr;
+  double *hb = nullptr, *hx = nullptr;  // device b and x of se_solve_host (first call)
   int gm_m = 0;                  // FGMRES restart length the V/Z blocks were sized for
   double* gmV = nullptr;         // [(m+1) L]
   double* gmZ = nullptr;         // [m L]

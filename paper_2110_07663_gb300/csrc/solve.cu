@@ -210,6 +210,23 @@ extern "C" int se_solve(se_mesh_t m, se_pmg_t P, const double* b, double* x,
   return rc;
 }
 
+extern "C" int se_solve_host(se_mesh_t m, se_pmg_t P, const double* b_host, const double* x0_host,
+                             double* x_host, const se_solve_opts* opts, se_solve_stats* stats) {
+  SE_CHECK(m && b_host && x_host && opts, SE_EINVAL, "se_solve_host: null argument");
+  const int64_t L = m->fine.L;
+  if (!m->hb) SE_TRY(dmalloc(m->allocs, &m->hb, (size_t)L));
+  if (!m->hx) SE_TRY(dmalloc(m->allocs, &m->hx, (size_t)L));
+  cudaStream_t s = as_stream(opts->stream, m->stream);
+  SE_CUDA(cudaMemcpyAsync(m->hb, b_host, (size_t)L * sizeof(double), cudaMemcpyHostToDevice, s));
+  if (x0_host) SE_CUDA(cudaMemcpyAsync(m->hx, x0_host, (size_t)L * sizeof(double), cudaMemcpyHostToDevice, s));
+  else SE_CUDA(cudaMemsetAsync(m->hx, 0, (size_t)L * sizeof(double), s));
+  const int rc = se_solve(m, P, m->hb, m->hx, opts, stats);
+  if (rc != SE_OK && rc != SE_ENOTCONV) return rc;
+  SE_CUDA(cudaMemcpyAsync(x_host, m->hx, (size_t)L * sizeof(double), cudaMemcpyDeviceToHost, s));
+  SE_CUDA(cudaStreamSynchronize(s));
+  return rc;
+}
+
 // =============================================================================================
 // Device-driven flexible PCG as one CUDA graph: the iteration is a WHILE node whose condition a
 // one-thread kernel sets from the device-resident residual norm; after convergence an IF node

@@ -152,6 +152,8 @@ _SIGS = {
     "se_pmg_coarse_solve": ([_vp, _vp, _vp, C.POINTER(C.c_int), _vp], C.c_int),
     "se_pmg_coarse_solve_noalloc": ([_vp, _vp, _vp, C.POINTER(C.c_int), _vp], C.c_int),
     "se_solve": ([_vp, _vp, _vp, _vp, C.POINTER(se_solve_opts), C.POINTER(se_solve_stats)], C.c_int),
+    "se_solve_host": ([_vp, _vp, _vp, _vp, _vp, C.POINTER(se_solve_opts), C.POINTER(se_solve_stats)],
+                      C.c_int),
     "se_batch_create": ([_ip, C.POINTER(se_problem), C.POINTER(se_solve_opts), C.POINTER(_vp)], C.c_int),
     "se_batch_run": ([_vp, _vp], C.c_int),
     "se_batch_stats": ([_vp, _vp, C.POINTER(se_solve_stats)], C.c_int),
@@ -422,6 +424,36 @@ def se_solve(m, P, b, x, method=SE_FPCG, tol=1e-8, maxit=1000, restart=20, graph
     o.stream = _stream(stream)
     st = se_solve_stats()
     _check(lib.se_solve(m, P, _ptr(b), _ptr(x), C.byref(o), C.byref(st)),
+           allow=(SE_ENOTCONV,) if allow_notconv else ())
+    return st
+
+
+def _host_ptr(a):
+    """Address of a contiguous float64 host array (CPU tensor or numpy array); None -> NULL."""
+    if a is None:
+        return None
+    if hasattr(a, "is_cuda"):
+        if a.is_cuda or a.dtype.itemsize != 8 or not a.is_contiguous():
+            raise ValueError("expected a contiguous float64 CPU tensor")
+        return a.data_ptr()
+    if a.dtype.itemsize != 8 or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("expected a contiguous float64 array")
+    return a.ctypes.data
+
+
+def se_solve_host(m, P, b_host, x_host, x0_host=None, method=SE_FPCG, tol=1e-8, maxit=1000,
+                  restart=20, graph_capture=0, stream=None, allow_notconv=False, tol_norm=0,
+                  operator_df64=0) -> se_solve_stats:
+    """se_solve with host buffers (the copies inside the library call); x starts from zero unless
+    x0_host is given."""
+    o = se_solve_opts()
+    o.method, o.restart, o.tol, o.maxit, o.graph_capture = method, restart, tol, maxit, graph_capture
+    o.tol_norm = tol_norm
+    o.operator_df64 = operator_df64
+    o.stream = _stream(stream)
+    st = se_solve_stats()
+    _check(lib.se_solve_host(m, P, _host_ptr(b_host), _host_ptr(x0_host), _host_ptr(x_host), C.byref(o),
+                             C.byref(st)),
            allow=(SE_ENOTCONV,) if allow_notconv else ())
     return st
 

@@ -275,3 +275,41 @@ def test_headline_configuration_against_the_oracle(graph):
         if P:
             se.se_pmg_destroy(P)
         se.se_mesh_destroy(m)
+
+
+@pytest.mark.parametrize("graph", [0, 1])
+def test_solve_with_host_buffers_equals_the_device_solve(graph):
+    """se_solve_host (b copied in, x from zero or from a host guess, x copied out inside the call)
+    gives bitwise the device solve's result and statistics, with pinned and with pageable host
+    buffers; a repeated call reuses the mesh's device vectors (and, graph-driven, its graph)."""
+    c = Case((4, 3, 3), 5, seed=8)
+    se, torch = c.se, c.torch
+    P = se.se_pmg_setup(c.m, se.pmg_desc((5, 3, 1), se.SE_SMOOTH_JACOBI, 1))
+    try:
+        b = c.to_gpu(c.random_continuous(31))
+        x = torch.zeros_like(b)
+        ref = se.se_solve(c.m, P, b, x, tol=1e-8, graph_capture=graph)
+        xref = x.cpu().numpy()
+        for pinned in (False, True):
+            bh = b.cpu()
+            xh = torch.full((c.info.L,), float("nan"), dtype=torch.float64)
+            if pinned:
+                bh, xh = bh.pin_memory(), xh.pin_memory()
+            for _ in range(2):
+                st = se.se_solve_host(c.m, P, bh, xh, tol=1e-8, graph_capture=graph)
+                assert st.iterations == ref.iterations and st.rel_residual == ref.rel_residual
+                assert np.array_equal(xh.numpy(), xref)
+        # from a host initial guess: the solve with that guess on the device
+        x0 = c.random_continuous(32)
+        x.copy_(c.to_gpu(x0))
+        ref0 = se.se_solve(c.m, P, b, x, tol=1e-8, graph_capture=graph)
+        xh = np.empty(c.info.L)
+        st0 = se.se_solve_host(c.m, P, b.cpu().numpy(), xh, x0_host=np.ascontiguousarray(x0.reshape(-1)),
+                               tol=1e-8, graph_capture=graph)
+        assert st0.iterations == ref0.iterations
+        assert np.array_equal(xh, x.cpu().numpy())
+        with pytest.raises(ValueError):
+            se.se_solve_host(c.m, P, b, xh)   # a device tensor is not a host buffer
+    finally:
+        se.se_pmg_destroy(P)
+        c.close()
