@@ -312,7 +312,8 @@ int se_proj_update(se_proj_t proj, const double* x, int* size, void* stream);
 /* Many independent problems solved together by flexible PCG in one device-driven CUDA graph.
  * Problems whose preconditioners share a configuration (schedule, smoother RAS or Jacobi,
  * Chebyshev orders, bounds multipliers, coarse tolerance, FP64 or FP32 V-cycle, multiplicative
- * cycle) form a group that is solved as one union problem: each phase of an iteration (outer
+ * cycle) and a size class (element counts below 4096, then one class per factor 8) form a group
+ * that is solved as one union problem (groups are independent branches of the graph): each phase of an iteration (outer
  * operator, QQ^T, smoother, Chebyshev update, transfers, coarse solves) is one launch over all
  * members' elements, inner products and convergence stay per problem (a converged problem keeps
  * its iterate while the others continue), and each member's Chebyshev bounds (Sec. 2.2.3) are

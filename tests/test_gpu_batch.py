@@ -185,3 +185,33 @@ def test_batch_rejects_shared_mesh():
     finally:
         se.se_pmg_destroy(P)
         se.se_mesh_destroy(m)
+
+
+def test_batch_size_classes_form_separate_groups():
+    """Problems of one preconditioner configuration whose element counts fall in different size
+    classes (below 4096 elements, then one class per factor 8) are solved as different groups,
+    each converging as its stand-alone solve does."""
+    torch, se = gpu()
+    specs = [((4, 4, 4), 3, 61), ((5, 4, 4), 3, 62), ((16, 16, 16), 3, 63)]
+    probs = [problem(se, torch, nel, p, seed, (3, 1), se.SE_FP32) for nel, p, seed in specs]
+    try:
+        entries = [(m, P, b) for (m, P, b, _) in probs]
+        alone = []
+        for m, P, b in entries:
+            x = torch.zeros_like(b)
+            alone.append(se.se_solve(m, P, b, x, tol=1e-8, graph_capture=1).iterations)
+        xs = [torch.zeros_like(b) for (_, _, b) in entries]
+        B = se.se_batch_create([(m, P, b, x) for (m, P, b), x in zip(entries, xs)], tol=1e-8)
+        try:
+            assert se.se_batch_info(B) == (2, 3)
+            se.se_batch_run(B)
+            stats = se.se_batch_stats(B, len(entries))
+            for k, (st, x, (m, P, b)) in enumerate(zip(stats, xs, entries)):
+                assert abs(st.iterations - alone[k]) <= 1, k
+                assert true_rel_residual(se, torch, m, b, x) <= 1.5e-8, k
+        finally:
+            se.se_batch_destroy(B)
+    finally:
+        for m, P, b, _ in probs:
+            se.se_pmg_destroy(P)
+            se.se_mesh_destroy(m)
