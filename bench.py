@@ -437,7 +437,7 @@ def run_gpu(args):
     x_host = torch.empty(L, dtype=torch.float64).pin_memory()
     torch.cuda.synchronize()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = max(1, min(args.steps, 5))
     se.se_solve_host(m, P, b_host, x_host, tol=1e-8, maxit=500, stream=stream, graph_capture=1,
                      operator_df64=op_df)  # captures
     torch.cuda.synchronize()
