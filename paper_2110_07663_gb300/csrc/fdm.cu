@@ -33,9 +33,23 @@ __device__ void jacobi_eigen(int n, double* A, double* V) {
       for (int q = p + 1; q < n; ++q) {
         const double apq = A[p * n + q];
         if (fabs(apq) < 1e-300) continue;
-        const double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
-        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        // The angle needs no FP64 accuracy (a rotation that leaves a small a_pq is followed by
+        // the next sweep's), only the rotation's orthogonality does: t from FP32 operations
+        // (where the quotient of two doubles' difference underflows or overflows in FP32, the
+        // FP64 form), then c = 1/sqrt(1 + t^2) and s = t c in FP64.  On this part FP64 division
+        // and square root are long instruction sequences on the narrow FP64 pipe.
+        const double dq = A[q * n + q] - A[p * n + p], e2 = 2.0 * apq;
+        double t;
+        float thf = 0.0f;
+        const bool f32 = fabs(e2) >= 1e-30 && fabs(e2) <= 1e30 && fabs(dq) <= 1e30 &&
+                         isfinite(thf = (float)dq / (float)e2);
+        if (f32) {
+          t = (double)(copysignf(1.0f, thf) / (fabsf(thf) + sqrtf(fmaf(thf, thf, 1.0f))));
+        } else {
+          const double theta = dq / e2;
+          t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        }
+        const double c = rsqrt(fma(t, t, 1.0)), s = t * c;
         for (int k = 0; k < n; ++k) {
           const double akp = A[k * n + p], akq = A[k * n + q];
           A[k * n + p] = c * akp - s * akq;
