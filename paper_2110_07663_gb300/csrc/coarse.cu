@@ -397,39 +397,25 @@ __device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Block sums of three values in thread 0 by shallow trees: every warp adds its lanes by a
-// five-level shuffle tree (all warps at once), then warp 0 adds the eight warp sums by a
-// three-level tree.  A fixed order (deterministic).  On this part a chain of dependent FP64
-// additions costs far more than their count suggests (the FP64 pipe takes 2 lanes per clock per
-// SM), so the depth of the chain, not the number of additions, is what is kept small.
-__device__ __forceinline__ void block_sum3_tree(double (&v)[3], double* red) {
-  static_assert(CG_THREADS == 256, "eight warps per block");
+// Block sums of three values in thread 0, one warp per value: the values go through shared
+// memory, warp k adds value k (lane l: threads l, l + 32, ... in order, then a five-level
+// shuffle tree).  Each warp-wide FP64 addition occupies the SM's 2-lane FP64 pipe for 16 cycles
+// however many lanes are active, so three warps adding 12 times cost a third of the pipe time of
+// eight warps' trees, at a similar depth of dependent additions.  A fixed order (deterministic).
+__device__ __forceinline__ void block_sum3_split(double (&v)[3], double* red, double* out3) {
+  static_assert(CG_THREADS % 32 == 0 && CG_THREADS >= 96, "three warps");
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    v[0] += __shfl_down_sync(0xffffffffu, v[0], o);
-    v[1] += __shfl_down_sync(0xffffffffu, v[1], o);
-    v[2] += __shfl_down_sync(0xffffffffu, v[2], o);
-  }
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) {
-    red[wid] = v[0];
-    red[8 + wid] = v[1];
-    red[16 + wid] = v[2];
+  for (int k = 0; k < 3; ++k) red[k * CG_THREADS + threadIdx.x] = v[k];
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (w < 3) {
+    double acc = red[w * CG_THREADS + lane];
+#pragma unroll
+    for (int i = lane + 32; i < CG_THREADS; i += 32) acc += red[w * CG_THREADS + i];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) out3[w] = acc;
   }
   __syncthreads();
-  if (threadIdx.x < 32) {
-    double a0 = lane < 8 ? red[lane] : 0.0, a1 = lane < 8 ? red[8 + lane] : 0.0;
-    double a2 = lane < 8 ? red[16 + lane] : 0.0;
-#pragma unroll
-    for (int o = 4; o > 0; o >>= 1) {
-      a0 += __shfl_down_sync(0xffffffffu, a0, o);
-      a1 += __shfl_down_sync(0xffffffffu, a1, o);
-      a2 += __shfl_down_sync(0xffffffffu, a2, o);
-    }
-    v[0] = a0;
-    v[1] = a1;
-    v[2] = a2;
-  }
 }
 
 // First half of a summing barrier: the block's sums of v are posted to part[call parity][blk];
@@ -438,18 +424,19 @@ __device__ __forceinline__ void block_sum3_tree(double (&v)[3], double* red) {
 __device__ __forceinline__ void grid_post3(unsigned* count, unsigned call, unsigned nblocks,
                                            double* part, double (&v)[3], double* red, unsigned blk,
                                            unsigned* flag, unsigned flag_value) {
-  block_sum3_tree(v, red);
+  __shared__ double s3[3];
+  block_sum3_split(v, red, s3);
   if (threadIdx.x == 0) {
     double* buf = part + (size_t)(call & 1u) * 4 * nblocks;
-    reinterpret_cast<double2*>(buf)[2 * blk] = make_double2(v[0], v[1]);
-    reinterpret_cast<double2*>(buf)[2 * blk + 1] = make_double2(v[2], 0.0);
+    reinterpret_cast<double2*>(buf)[2 * blk] = make_double2(s3[0], s3[1]);
+    reinterpret_cast<double2*>(buf)[2 * blk + 1] = make_double2(s3[2], 0.0);
     st_release(flag, flag_value);
     atomic_add_release(count, 1u);
   }
 }
 
 // Second half: waits until all nblocks blocks have posted call `call`, then adds their partials
-// in a fixed order (thread t: blocks t, t + 256, ...; then the trees of block_sum3_tree) and
+// in a fixed order (warp k adds value k of the blocks in order, lane-sequentially, then a tree) and
 // thread 0 evaluates post(v); every thread gets v and post's value.  False once status[0] is set
 // (an expired wait here or elsewhere).
 template <class Post>
@@ -470,17 +457,32 @@ __device__ bool grid_wait3(unsigned* count, unsigned call, int* status, unsigned
     }
   }
   __syncthreads();
-  // thread t takes blocks t, t + 256, ... (one load round), then the trees of block_sum3_tree
+  // warp k adds value k of every block (lane l: blocks l, l + 32, ..., all loads issued first),
+  // then a shuffle tree; thread 0 gathers the three sums
   double w[3] = {0.0, 0.0, 0.0};
-  for (unsigned k = threadIdx.x; k < nblocks; k += CG_THREADS) {
-    const double2 l = __ldcg(reinterpret_cast<const double2*>(buf) + 2 * k);
-    const double2 h = __ldcg(reinterpret_cast<const double2*>(buf) + 2 * k + 1);
-    w[0] += l.x;
-    w[1] += l.y;
-    w[2] += h.x;
+  {
+    const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (wp < 3) {
+      constexpr int UNR = 10;
+      double t[UNR];
+#pragma unroll
+      for (int i = 0; i < UNR; ++i) {
+        const unsigned k = lane + 32u * i;
+        t[i] = k < nblocks ? __ldcg(buf + 4 * k + wp) : 0.0;
+      }
+      double acc = t[0];
+#pragma unroll
+      for (int i = 1; i < UNR; ++i) acc += t[i];
+      for (unsigned k = lane + 32u * UNR; k < nblocks; k += 32) acc += __ldcg(buf + 4 * k + wp);
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+      if (lane == 0) red[wp] = acc;
+    }
   }
-  block_sum3_tree(w, red);
+  __syncthreads();
   if (threadIdx.x == 0) {
+    w[0] = red[0];
+    w[1] = red[1];
+    w[2] = red[2];
     const double pv = post(w);
     s_out[0] = w[0];
     s_out[1] = w[1];
