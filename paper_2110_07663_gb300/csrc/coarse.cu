@@ -31,13 +31,30 @@ __device__ __forceinline__ long long global_ns() {
 constexpr int CG_THREADS = 256;
 
 // Sums of three values over the block, left in thread 0.  Every thread posts its values to shared
-// memory and one warp adds them, lane l taking entries l, l + 32, ... in order, then a shuffle
-// tree: a fixed order (deterministic) and a short chain of dependent FP64 additions.
+// memory; with three warps or more, warp k adds value k (lane l: entries l, l + 32, ... in order,
+// then a shuffle tree), otherwise warp 0 adds all three: a fixed order (deterministic), few
+// warp-wide FP64 additions (each occupies the SM's 2-lane FP64 pipe for 16 cycles) and a short
+// chain of dependent ones.
 __device__ __forceinline__ void block_sum3(double (&v)[3], double* red) {
+  __shared__ double s3[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) red[k * blockDim.x + threadIdx.x] = v[k];
   __syncthreads();
-  if (threadIdx.x < 32) {
+  const unsigned w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (blockDim.x >= 96) {
+    if (w < 3) {
+      double acc = red[w * blockDim.x + lane];
+      for (unsigned i = lane + 32; i < blockDim.x; i += 32) acc += red[w * blockDim.x + i];
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+      if (lane == 0) s3[w] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      v[0] = s3[0];
+      v[1] = s3[1];
+      v[2] = s3[2];
+    }
+  } else if (threadIdx.x < 32) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       double acc = red[k * blockDim.x + threadIdx.x];
@@ -45,6 +62,23 @@ __device__ __forceinline__ void block_sum3(double (&v)[3], double* red) {
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
       v[k] = acc;
     }
+  }
+}
+
+// Pairwise sum of K register values in a fixed order: depth ceil(log2 K) instead of K - 1 (a
+// dependent FP64 addition costs far more here than an independent one).
+template <int K>
+__device__ __forceinline__ double pairwise_sum(const double (&a)[K]) {
+  if constexpr (K == 1) {
+    return a[0];
+  } else {
+    constexpr int H = K / 2;
+    double lo[H], hi[K - H];
+#pragma unroll
+    for (int i = 0; i < H; ++i) lo[i] = a[i];
+#pragma unroll
+    for (int i = 0; i < K - H; ++i) hi[i] = a[H + i];
+    return pairwise_sum<H>(lo) + pairwise_sum<K - H>(hi);
   }
 }
 
@@ -398,7 +432,7 @@ __device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
 }
 
 // Block sums of three values in thread 0, one warp per value: the values go through shared
-// memory, warp k adds value k (lane l: threads l, l + 32, ... in order, then a five-level
+// memory, warp k adds value k (lane l: threads l, l + 32, ... pairwise, then a five-level
 // shuffle tree).  Each warp-wide FP64 addition occupies the SM's 2-lane FP64 pipe for 16 cycles
 // however many lanes are active, so three warps adding 12 times cost a third of the pipe time of
 // eight warps' trees, at a similar depth of dependent additions.  A fixed order (deterministic).
@@ -409,9 +443,10 @@ __device__ __forceinline__ void block_sum3_split(double (&v)[3], double* red, do
   __syncthreads();
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (w < 3) {
-    double acc = red[w * CG_THREADS + lane];
+    double a[CG_THREADS / 32];
 #pragma unroll
-    for (int i = lane + 32; i < CG_THREADS; i += 32) acc += red[w * CG_THREADS + i];
+    for (int i = 0; i < CG_THREADS / 32; ++i) a[i] = red[w * CG_THREADS + lane + 32 * i];
+    double acc = pairwise_sum(a);
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if (lane == 0) out3[w] = acc;
   }
@@ -470,9 +505,7 @@ __device__ bool grid_wait3(unsigned* count, unsigned call, int* status, unsigned
         const unsigned k = lane + 32u * i;
         t[i] = k < nblocks ? __ldcg(buf + 4 * k + wp) : 0.0;
       }
-      double acc = t[0];
-#pragma unroll
-      for (int i = 1; i < UNR; ++i) acc += t[i];
+      double acc = pairwise_sum(t);
       for (unsigned k = lane + 32u * UNR; k < nblocks; k += 32) acc += __ldcg(buf + 4 * k + wp);
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
       if (lane == 0) red[wp] = acc;
