@@ -140,15 +140,15 @@ __device__ bool grid_sum3(unsigned* count, unsigned call, int* status, unsigned 
       lo[i] = k < nblocks ? __ldcg(reinterpret_cast<const double2*>(buf) + 2 * k) : make_double2(0.0, 0.0);
       hi[i] = k < nblocks ? __ldcg(reinterpret_cast<const double2*>(buf) + 2 * k + 1) : make_double2(0.0, 0.0);
     }
-    double s0 = lo[0].x, s1 = lo[0].y, s2 = hi[0].x;  // nblocks >= 1: lane 0 has a block
+    // pairwise within the lane (absent blocks contribute exact zeros): short dependent chains
+    double a0[UNR], a1[UNR], a2[UNR];
 #pragma unroll
-    for (int i = 1; i < UNR; ++i) {
-      if (threadIdx.x + 32u * i < nblocks) {
-        s0 += lo[i].x;
-        s1 += lo[i].y;
-        s2 += hi[i].x;
-      }
+    for (int i = 0; i < UNR; ++i) {
+      a0[i] = lo[i].x;
+      a1[i] = lo[i].y;
+      a2[i] = hi[i].x;
     }
+    double s0 = pairwise_sum(a0), s1 = pairwise_sum(a1), s2 = pairwise_sum(a2);
     for (unsigned k = threadIdx.x + 32u * UNR; k < nblocks; k += 32) {
       const double2 l = __ldcg(reinterpret_cast<const double2*>(buf) + 2 * k);
       const double2 h = __ldcg(reinterpret_cast<const double2*>(buf) + 2 * k + 1);
