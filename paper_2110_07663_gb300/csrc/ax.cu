@@ -297,37 +297,65 @@ __global__ void __launch_bounds__(256) gs_sweep_x(int nx, int ny, int nz, int bi
   }
 }
 
-// y and z sweeps: each thread adds GS_YZ_PAIRS interface pairs, strided so that a warp's
-// accesses stay contiguous, all loads issued before any store (these kernels are bound by memory
-// latency, not bandwidth).
+// The y/z launch: each thread takes GS_YZ_PAIRS items, strided so that a warp's accesses stay
+// contiguous, all loads issued before any store (these launches are bound by memory latency, not
+// bandwidth).
 constexpr int GS_YZ_PAIRS = 4;
 
+// y and z directions in one launch (the x direction complete before it).  Items: y-pairs
+// (element e, e + nx; copies (i, p, k), (i, 0, k)) and z-pairs (e, e + nx ny; (i, j, p), (i, j, 0)).
+// A node on a y- and a z-interface has four copies; the y-item at k = p (ez < nz - 1) takes all
+// four and sums them as the two sweeps would, (y-pair at k = p) + (y-pair of e + nx ny at k = 0),
+// so every copy keeps the bits of the sweep order; the y-item at k = 0 of e + nx ny and the
+// z-items at j = p (ey < ny - 1) and j = 0 (ey > 0) belong to such groups and do nothing.  Every
+// interface copy is then read and written once, by one thread.
 template <typename T, int N>
-__global__ void gs_sweep_y(int nx, int ny, int nz, T* __restrict__ u) {
-  constexpr int N3 = N * N * N, K = GS_YZ_PAIRS;
-  const int nif = ny - 1;
-  const int total = N * N * nx * nif * nz;  // < L < 2^31: 32-bit index arithmetic
+__global__ void gs_sweep_yz(int nx, int ny, int nz, T* __restrict__ u) {
+  constexpr int N2 = N * N, N3 = N2 * N, K = GS_YZ_PAIRS;
+  const int ny1 = ny - 1, nz1 = nz - 1;
+  const int ty = N2 * nx * ny1 * nz;   // y-items, ordered (i, k, ex, ey, ez)
+  const int total = ty + N2 * nx * ny * nz1;  // then z-items (ij, e), e over ez < nz - 1
   const int nthr = (total + K - 1) / K;
   const int t0 = (int)(blockIdx.x * blockDim.x + threadIdx.x);
   if (t0 >= nthr) return;
-  int64_t ia[K], ib[K];
-  T a[K], b[K];
+  const int64_t exy = (int64_t)nx * ny;
+  int64_t ia[K], ib[K], ic[K], id[K];
+  T a[K], b[K], c[K], d[K];
 #pragma unroll
   for (int kk = 0; kk < K; ++kk) {
     const int t = t0 + kk * nthr;
     ia[kk] = -1;
-    if (t < total) {
+    ic[kk] = -1;
+    if (t < ty) {
       const int i = t % N;
       int q = t / N;
       const int k = q % N;
       q /= N;
       const int ex = q % nx;
       q /= nx;
-      const int ey = q % nif;
-      const int ez = q / nif;
+      const int ey = q % ny1;
+      const int ez = q / ny1;
+      if (k == 0 && ez > 0) continue;                 // in the group of e - nx ny
       const int64_t e = ex + (int64_t)nx * (ey + (int64_t)ny * ez);
-      ia[kk] = e * N3 + i + N * ((N - 1) + N * k);      // element e, j = p
-      ib[kk] = (e + nx) * N3 + i + (int64_t)N * N * k;  // element e + nx, j = 0
+      ia[kk] = e * N3 + i + N * ((N - 1) + N * k);     // element e, j = p
+      ib[kk] = (e + nx) * N3 + i + (int64_t)N2 * k;    // element e + nx, j = 0
+      a[kk] = u[ia[kk]];
+      b[kk] = u[ib[kk]];
+      if (k == N - 1 && ez < nz1) {                    // four copies: also k = 0 of e + nx ny
+        ic[kk] = (e + exy) * N3 + i + N * (N - 1);
+        id[kk] = (e + exy + nx) * N3 + i;
+        c[kk] = u[ic[kk]];
+        d[kk] = u[id[kk]];
+      }
+    } else if (t < total) {
+      const int tz = t - ty;
+      const int ij = tz % N2;
+      const int64_t e = tz / N2;                       // elements with ez < nz - 1, in order
+      const int j = ij / N;
+      const int ey = (int)((e / nx) % ny);
+      if ((j == N - 1 && ey < ny1) || (j == 0 && ey > 0)) continue;  // in a y-item's group
+      ia[kk] = e * N3 + ij + N2 * (N - 1);             // element e, k = p
+      ib[kk] = (e + exy) * N3 + ij;                    // element e + nx ny, k = 0
       a[kk] = u[ia[kk]];
       b[kk] = u[ib[kk]];
     }
@@ -335,42 +363,34 @@ __global__ void gs_sweep_y(int nx, int ny, int nz, T* __restrict__ u) {
 #pragma unroll
   for (int kk = 0; kk < K; ++kk) {
     if (ia[kk] < 0) continue;
-    const T sum = a[kk] + b[kk];
+    T sum = a[kk] + b[kk];
+    if (ic[kk] >= 0) {
+      sum = sum + (c[kk] + d[kk]);
+      u[ic[kk]] = sum;
+      u[id[kk]] = sum;
+    }
     u[ia[kk]] = sum;
     u[ib[kk]] = sum;
   }
 }
 
+// Interface copies the fused y/z launch reads and writes once each.
+template <int N>
+static double yz_copies(int nx, int ny, int nz) {
+  return 2.0 * N * N * ((double)nx * (ny - 1) * nz + (double)nx * ny * (nz - 1)) -
+         4.0 * N * (double)nx * (ny - 1) * (nz - 1);
+}
+
+// The fused y/z launch with one profiling scope; `bytes` < 0: the interface copies' bytes.
 template <typename T, int N>
-__global__ void gs_sweep_z(int nx, int ny, int nz, T* __restrict__ u) {
-  constexpr int N2 = N * N, N3 = N2 * N, K = GS_YZ_PAIRS;
-  const int nif = nz - 1;
-  const int total = N2 * nx * ny * nif;  // < L < 2^31: 32-bit index arithmetic
-  const int nthr = (total + K - 1) / K;
-  const int t0 = (int)(blockIdx.x * blockDim.x + threadIdx.x);
-  if (t0 >= nthr) return;
-  int64_t ia[K], ib[K];
-  T a[K], b[K];
-#pragma unroll
-  for (int kk = 0; kk < K; ++kk) {
-    const int t = t0 + kk * nthr;
-    ia[kk] = -1;
-    if (t < total) {
-      const int ij = t % N2;
-      const int64_t e = t / N2;  // elements with ez < nz - 1, in order
-      ia[kk] = e * N3 + ij + N2 * (N - 1);            // element e, k = p
-      ib[kk] = (e + (int64_t)nx * ny) * N3 + ij;      // element e + nx ny, k = 0
-      a[kk] = u[ia[kk]];
-      b[kk] = u[ib[kk]];
-    }
-  }
-#pragma unroll
-  for (int kk = 0; kk < K; ++kk) {
-    if (ia[kk] < 0) continue;
-    const T sum = a[kk] + b[kk];
-    u[ia[kk]] = sum;
-    u[ib[kk]] = sum;
-  }
+static int gs_yz(int nx, int ny, int nz, T* u, int var, double bytes, cudaStream_t s) {
+  if (ny <= 1 && nz <= 1) return SE_OK;
+  const int64_t items = (int64_t)N * N * nx * ((int64_t)(ny - 1) * nz + (int64_t)ny * (nz - 1));
+  const double copies = yz_copies<N>(nx, ny, nz);
+  ProfScope prof(SE_K_GS, s, copies, bytes < 0 ? 2.0 * copies * sizeof(T) : bytes, (double)items, var);
+  gs_sweep_yz<T, N><<<grid_for((items + GS_YZ_PAIRS - 1) / GS_YZ_PAIRS, 256), 256, 0, s>>>(nx, ny, nz, u);
+  SE_LAUNCH_CHECK();
+  return SE_OK;
 }
 
 // Zero the copies on the Dirichlet faces (bit f of `bits`: face f = x0, x1, y0, y1, z0, z1).
@@ -440,19 +460,7 @@ static int gs_sweeps(const Level& lv, T* u, bool mask, double bytes, double flop
     gs_sweep_x<T, N><<<grid_for(32 * warps, 256), 256, 0, s>>>(nx, ny, nz, bits, u);
     SE_LAUNCH_CHECK();
   }
-  if (ny > 1) {
-    const int64_t n = (int64_t)N2 * nx * (ny - 1) * nz;
-    ProfScope prof(SE_K_GS, s, (double)n, 0.0, 0.0, var);
-    gs_sweep_y<T, N><<<grid_for((n + GS_YZ_PAIRS - 1) / GS_YZ_PAIRS, 256), 256, 0, s>>>(nx, ny, nz, u);
-    SE_LAUNCH_CHECK();
-  }
-  if (nz > 1) {
-    const int64_t n = (int64_t)N2 * nx * ny * (nz - 1);
-    ProfScope prof(SE_K_GS, s, (double)n, 0.0, 0.0, var);
-    gs_sweep_z<T, N><<<grid_for((n + GS_YZ_PAIRS - 1) / GS_YZ_PAIRS, 256), 256, 0, s>>>(nx, ny, nz, u);
-    SE_LAUNCH_CHECK();
-  }
-  return SE_OK;
+  return gs_yz<T, N>(nx, ny, nz, u, var, 0.0, s);
 }
 
 // Copies on element interfaces (each is read and written once by the algorithm).
@@ -479,9 +487,9 @@ int gs_apply(const Level& lv, T* u, bool mask, cudaStream_t s) {
 
 // ------------------------------------------------------------------ folded FP64 operator
 // The even-odd kernel sums the x-interfaces inside its blocks and masks (ax_local_eo_fold); the
-// x-interfaces between blocks follow (gs_fold_fixup), then the y and z sweeps, so each direction is
-// complete before the next starts, as in the sweeps above, and each pair still writes one sum to
-// both sides (all copies of a node keep the same bits).  This removes the x sweep, which
+// x-interfaces between blocks follow (gs_fold_fixup), then the fused y/z launch, so the x direction
+// is complete before y and z start, as in the sweeps above, and every copy of a node gets the
+// same bits.  This removes the x sweep, which
 // reads and writes every sector of the vector (an x-interface copy is the first or last value of
 // a row of N), from the operator applications of the solve.
 bool ax_fold_ok(const Level& lv) {
@@ -503,19 +511,7 @@ static int gs_after_fold(const Level& lv, double* y, int NE, cudaStream_t s) {
     ProfScope prof(SE_K_GS, s, n, 4.0 * n * sizeof(double), n, var);
     SE_TRY(gs_fold_fixup(lv, y, NE, s));
   }
-  if (ny > 1) {
-    const int64_t n = (int64_t)N2 * nx * (ny - 1) * nz;  // interface pairs
-    ProfScope prof(SE_K_GS, s, (double)n, 4.0 * n * sizeof(double), (double)n, var);
-    gs_sweep_y<double, N><<<grid_for((n + GS_YZ_PAIRS - 1) / GS_YZ_PAIRS, 256), 256, 0, s>>>(nx, ny, nz, y);
-    SE_LAUNCH_CHECK();
-  }
-  if (nz > 1) {
-    const int64_t n = (int64_t)N2 * nx * ny * (nz - 1);
-    ProfScope prof(SE_K_GS, s, (double)n, 4.0 * n * sizeof(double), (double)n, var);
-    gs_sweep_z<double, N><<<grid_for((n + GS_YZ_PAIRS - 1) / GS_YZ_PAIRS, 256), 256, 0, s>>>(nx, ny, nz, y);
-    SE_LAUNCH_CHECK();
-  }
-  return SE_OK;
+  return gs_yz<double, N>(nx, ny, nz, y, var, -1.0, s);
 }
 
 int ax_apply_folded(const Level& lv, const double* u, double* y, const double* b, cudaStream_t s,

@@ -18,6 +18,13 @@ __device__ __forceinline__ double scale_pow2(double a, int k) {
   return __longlong_as_double(e == 0x7FF ? b : (e > k ? r : 0LL));
 }
 
+// The FP32 form: |a| < 2^-123 (zero and subnormals included) gives 0; NaN/Inf pass through.
+__device__ __forceinline__ float scale_pow2(float a, int k) {
+  const int b = __float_as_int(a);
+  const int e = (b >> 23) & 0xFF;
+  return __int_as_float(e == 0xFF ? b : (e > k ? b - (k << 23) : 0));
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);

@@ -11,8 +11,14 @@
 // M[o][n-1-l])/2 for the line operator M (J or J^T), output o and its mirror are E_o + O_o and
 // E_o - O_o: n/2 fewer FMAs per output pair at the cost of n + m adds per line (about 20% fewer
 // FP64 instructions; GB300 runs this kernel on its FP64 pipe).  Several elements share a block.
-// Odd N (even orders) use the plain kernel, one element per block.
+// At N = 4 <-> 2 the fold costs more than it saves (10 instead of 8 FP64 instructions per line):
+// transfer_small_kernel contracts densely, one thread per output value of each direction, several
+// elements per block.  Odd N (even orders) use the plain kernel, one element per block.
+// The restriction's 1/mult_f (1, 1/2, 1/4, 1/8) is applied by lowering the binary exponent with
+// integer instructions (scale_pow2), not by an FP64 multiply: exact for every value above 2^-1019
+// (2^-123 in FP32), and the FP64 pipe keeps only the contractions.
 #include "se_internal.h"
+#include "reduce.h"
 
 namespace se {
 
@@ -34,10 +40,7 @@ __global__ void __launch_bounds__(128) transfer_kernel(int Nf, int Nc, const T* 
   const int Ni3 = Ni * Ni * Ni, No3 = No * No * No;
   for (int q = tid; q < Ni3; q += nt) {
     T v = in[e * Ni3 + q];
-    if (RESTRICT) {
-      const int mlog = __ffs(pflag_in[e * Ni3 + q] & 0x0F) - 1;
-      v *= mlog == 0 ? T(1) : (mlog == 1 ? T(0.5) : (mlog == 2 ? T(0.25) : T(0.125)));
-    }
+    if (RESTRICT) v = scale_pow2(v, mult_log2(pflag_in[e * Ni3 + q]));
     t0[q] = v;
   }
   __syncthreads();
@@ -124,10 +127,7 @@ __global__ void __launch_bounds__(256) transfer_eo_kernel(int64_t E, int NE, con
   for (int q = tid; q < ne * NI3; q += nt) {
     const int le = q / NI3, pt = q - le * NI3;
     T v = in[e0 * NI3 + q];
-    if (RESTRICT) {
-      const int mlog = __ffs(pflag_in[e0 * NI3 + q] & 0x0F) - 1;
-      v *= mlog == 0 ? T(1) : (mlog == 1 ? T(0.5) : (mlog == 2 ? T(0.25) : T(0.125)));
-    }
+    if (RESTRICT) v = scale_pow2(v, mult_log2(pflag_in[e0 * NI3 + q]));
     bufA[le * A + pt] = v;
   }
   __syncthreads();
@@ -158,6 +158,86 @@ __global__ void __launch_bounds__(256) transfer_eo_kernel(int64_t E, int NE, con
   }
 }
 
+// Small orders: each direction's outputs are computed one per thread (NI FMAs from shared
+// memory), so every warp of a phase is full when NE x (outputs per element) is a multiple of 32.
+// Buffers: A = input, then direction-s output; B = direction-r output, then direction-t output.
+template <int NF, int NC, bool RESTRICT>
+struct TransferSmallDims {
+  static constexpr int NI = RESTRICT ? NF : NC, NO = RESTRICT ? NC : NF;
+  static constexpr int R1 = NO * NI * NI, R2 = NO * NO * NI, NO3 = NO * NO * NO, NI3 = NI * NI * NI;
+  static constexpr int MX = R1 > R2 ? (R1 > NO3 ? R1 : NO3) : (R2 > NO3 ? R2 : NO3);
+  static constexpr int THREADS = 256, NE = THREADS / MX;
+  static constexpr int A = NI3 > R2 ? NI3 : R2, B = R1 > NO3 ? R1 : NO3;
+  static_assert(NE >= 1 && (NE * NO3) % 32 == 0 && (NE * R1) % 32 == 0 && (NE * R2) % 32 == 0,
+                "every phase of a small transfer fills whole warps");
+};
+
+template <typename T, int NF, int NC, bool RESTRICT>
+__global__ void __launch_bounds__(256) transfer_small_kernel(int64_t E, const T* __restrict__ Jg,
+                                                             const T* __restrict__ in,
+                                                             const uint8_t* __restrict__ pflag_in,
+                                                             T* __restrict__ out, bool accumulate) {
+  using D = TransferSmallDims<NF, NC, RESTRICT>;
+  constexpr int NI = D::NI, NO = D::NO, NE = D::NE, NI3 = D::NI3, NO3 = D::NO3;
+  __shared__ T sM[NO * NI];  // line operator M[o][i]: prolong J[o][i], restrict J^T: J[i][o]
+  __shared__ T bufA[NE * D::A];
+  __shared__ T bufB[NE * D::B];
+  const int tid = threadIdx.x;
+  for (int q = tid; q < NO * NI; q += D::THREADS) {
+    const int o = q / NI, i = q - o * NI;
+    sM[q] = RESTRICT ? Jg[i * NC + o] : Jg[o * NC + i];
+  }
+  const int64_t e0 = (int64_t)blockIdx.x * NE;
+  const int ne = (int)((E - e0) < NE ? (E - e0) : NE);
+  for (int q = tid; q < ne * NI3; q += D::THREADS) {
+    const int le = q / NI3, pt = q - le * NI3;
+    T v = in[e0 * NI3 + q];
+    if (RESTRICT) v = scale_pow2(v, mult_log2(pflag_in[e0 * NI3 + q]));
+    bufA[le * D::A + pt] = v;
+  }
+  __syncthreads();
+  // direction r: B[k][j][a] = sum_i M(a, i) A[k][j][i]
+  for (int q = tid; q < ne * D::R1; q += D::THREADS) {
+    const int le = q / D::R1, r = q - le * D::R1, a = r % NO, jk = r / NO;
+    const T* src = bufA + le * D::A + NI * jk;
+    T acc = T(0);
+#pragma unroll
+    for (int i = 0; i < NI; ++i) acc = fma(sM[a * NI + i], src[i], acc);
+    bufB[le * D::B + r] = acc;
+  }
+  __syncthreads();
+  // direction s: A[k][b][a] = sum_j M(b, j) B[k][j][a]
+  for (int q = tid; q < ne * D::R2; q += D::THREADS) {
+    const int le = q / D::R2, r = q - le * D::R2, a = r % NO, b = (r / NO) % NO, k = r / (NO * NO);
+    const T* src = bufB + le * D::B + a + NO * NI * k;
+    T acc = T(0);
+#pragma unroll
+    for (int j = 0; j < NI; ++j) acc = fma(sM[b * NI + j], src[NO * j], acc);
+    bufA[le * D::A + r] = acc;
+  }
+  __syncthreads();
+  // direction t: out[c][b][a] = sum_k M(c, k) A[k][b][a]
+  for (int q = tid; q < ne * NO3; q += D::THREADS) {
+    const int le = q / NO3, r = q - le * NO3, ab = r % (NO * NO), c = r / (NO * NO);
+    const T* src = bufA + le * D::A + ab;
+    T acc = T(0);
+#pragma unroll
+    for (int k = 0; k < NI; ++k) acc = fma(sM[c * NI + k], src[NO * NO * k], acc);
+    const int64_t o = e0 * NO3 + q;
+    out[o] = accumulate ? out[o] + acc : acc;
+  }
+}
+
+template <typename T, int NF, int NC, bool RESTRICT>
+static int launch_transfer_small(const Level& f, const T* J, const T* in, const uint8_t* pflag, T* out,
+                                 bool accumulate, cudaStream_t s) {
+  using D = TransferSmallDims<NF, NC, RESTRICT>;
+  const unsigned blocks = (unsigned)((f.E + D::NE - 1) / D::NE);
+  transfer_small_kernel<T, NF, NC, RESTRICT><<<blocks, D::THREADS, 0, s>>>(f.E, J, in, pflag, out, accumulate);
+  SE_LAUNCH_CHECK();
+  return SE_OK;
+}
+
 template <typename T, int NF, int NC, bool RESTRICT>
 static int launch_transfer_eo(const Level& f, const T* J, const T* in, const uint8_t* pflag, T* out,
                               bool accumulate, cudaStream_t s) {
@@ -181,16 +261,21 @@ static int launch_transfer_eo(const Level& f, const T* J, const T* in, const uin
   return SE_OK;
 }
 
-// Even-even pairs (Nf, Nc) with Nc < Nf <= SE_MAX_ORDER + 1: the folded kernel; false otherwise.
+// Even-even pairs (Nf, Nc) with Nc < Nf <= SE_MAX_ORDER + 1: the folded kernel (the dense
+// small-order kernel at 4 <-> 2); false otherwise.
 template <typename T, bool RESTRICT>
 static bool transfer_eo(const Level& f, const Level& c, const T* J, const T* in, const uint8_t* pflag,
                         T* out, bool accumulate, cudaStream_t s, int* st) {
+  if (f.N == 4 && c.N == 2) {
+    *st = launch_transfer_small<T, 4, 2, RESTRICT>(f, J, in, pflag, out, accumulate, s);
+    return true;
+  }
 #define SE_TR(NF_, NC_)                                                                      \
   if (f.N == NF_ && c.N == NC_) {                                                            \
     *st = launch_transfer_eo<T, NF_, NC_, RESTRICT>(f, J, in, pflag, out, accumulate, s);    \
     return true;                                                                             \
   }
-  SE_TR(4, 2) SE_TR(6, 2) SE_TR(6, 4) SE_TR(8, 2) SE_TR(8, 4) SE_TR(8, 6)
+  SE_TR(6, 2) SE_TR(6, 4) SE_TR(8, 2) SE_TR(8, 4) SE_TR(8, 6)
   SE_TR(10, 2) SE_TR(10, 4) SE_TR(10, 6) SE_TR(10, 8)
 #undef SE_TR
   return false;

@@ -43,3 +43,31 @@ def test_restrict_and_prolong_all_coarse_orders(pf, precision):
                 se.se_pmg_destroy(P)
     finally:
         c.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_small_order_transfers_with_ragged_blocks(precision):
+    """p = 3 <-> 1 runs the dense small-order kernel (8 elements per block restricting, 4
+    prolonging): 5 x 3 x 3 = 45 elements leave a partial last block in both directions."""
+    nel = (5, 3, 3)
+    c = Case(nel, 3, seed=31, bc=("D", "N", "N", "D", "D", "N"))
+    se = c.se
+    prec = se.SE_FP64 if precision == "fp64" else se.SE_FP32
+    tol = 1e-13 if precision == "fp64" else 1e-5
+    try:
+        P = se.se_pmg_setup(c.m, se.pmg_desc((3, 1), se.SE_SMOOTH_JACOBI, 1, precision=prec))
+        try:
+            lc = o.make_level(c.V, nel, 1, c.bc, c.amp)
+            r = c.random_continuous(7, c.lv)
+            rc = c.empty(lc.gid.size)
+            se.se_pmg_restrict(P, 0, c.to_gpu(r), rc)
+            err_r = rel_err(c.to_np(rc, lc.gid.shape), o.restrict(c.lv, lc, r))
+            ec = c.random_continuous(8, lc)
+            ef = c.empty(c.lv.gid.size)
+            se.se_pmg_prolong(P, 0, c.to_gpu(ec), ef)
+            err_p = rel_err(c.to_np(ef, c.lv.gid.shape), o.prolong(c.lv, lc, ec))
+            assert err_r <= tol and err_p <= tol, (err_r, err_p)
+        finally:
+            se.se_pmg_destroy(P)
+    finally:
+        c.close()
