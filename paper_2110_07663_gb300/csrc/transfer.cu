@@ -97,6 +97,36 @@ __device__ __forceinline__ void eo_transfer_line(const T* __restrict__ Ep, const
   }
 }
 
+// The last direction's line, stored straight to memory: dst[so * o] = (M v)_o, or += with
+// `accumulate`.
+template <typename T, int NI, int NO>
+__device__ __forceinline__ void eo_transfer_line_out(const T* __restrict__ Ep, const T* __restrict__ Om,
+                                                     const T* src, int si, T* __restrict__ dst, int so,
+                                                     bool accumulate) {
+  constexpr int HI = NI / 2, HO = NO / 2;
+  T e[HI], o[HI];
+#pragma unroll
+  for (int l = 0; l < HI; ++l) {
+    const T a = src[si * l], b = src[si * (NI - 1 - l)];
+    e[l] = a + b;
+    o[l] = a - b;
+  }
+#pragma unroll
+  for (int k = 0; k < HO; ++k) {
+    T E = T(0), O = T(0);
+#pragma unroll
+    for (int l = 0; l < HI; ++l) {
+      E = fma(Ep[k * HI + l], e[l], E);
+      O = fma(Om[k * HI + l], o[l], O);
+    }
+    const T lo = E + O, hi = E - O;
+    T* d0 = dst + so * k;
+    T* d1 = dst + so * (NO - 1 - k);
+    *d0 = accumulate ? *d0 + lo : lo;
+    *d1 = accumulate ? *d1 + hi : hi;
+  }
+}
+
 // NE elements per block; prolong: NI = NC -> NO = NF, restrict: NI = NF -> NO = NC.
 template <typename T, int NF, int NC, bool RESTRICT>
 __global__ void __launch_bounds__(256) transfer_eo_kernel(int64_t E, int NE, const T* __restrict__ Jg,
@@ -107,7 +137,7 @@ __global__ void __launch_bounds__(256) transfer_eo_kernel(int64_t E, int NE, con
   constexpr int HI = NI / 2, HO = NO / 2;
   constexpr int NI3 = NI * NI * NI, NO3 = NO * NO * NO;
   constexpr int A = (NI3 > NO * NO * NI ? NI3 : NO * NO * NI);  // input, then direction-s output
-  constexpr int B = (NO * NI * NI > NO3 ? NO * NI * NI : NO3);    // direction-r, then -t output
+  constexpr int B = NO * NI * NI;                                 // direction-r output
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Ep = reinterpret_cast<T*>(smem_raw);
   T* Om = Ep + HO * HI;
@@ -144,17 +174,13 @@ __global__ void __launch_bounds__(256) transfer_eo_kernel(int64_t E, int NE, con
                                 bufA + le * A + a + NO * NO * k, NO);
   }
   __syncthreads();
-  // direction t: B[c][b][a] = sum_k M(c, k) A[k][b][a]      lines (a, b), NO^2 per element
+  // direction t: out[c][b][a] = sum_k M(c, k) A[k][b][a]    lines (a, b), NO^2 per element,
+  // stored to memory from the line (a warp's lanes hold consecutive (a, b): each plane c of an
+  // element is a contiguous store)
   for (int q = tid; q < ne * NO * NO; q += nt) {
     const int le = q / (NO * NO), ab = q - le * (NO * NO);
-    eo_transfer_line<T, NI, NO>(Ep, Om, bufA + le * A + ab, NO * NO, bufB + le * B + ab, NO * NO);
-  }
-  __syncthreads();
-  for (int q = tid; q < ne * NO3; q += nt) {
-    const int le = q / NO3, pt = q - le * NO3;
-    const T v = bufB[le * B + pt];
-    const int64_t o = e0 * NO3 + q;
-    out[o] = accumulate ? out[o] + v : v;
+    eo_transfer_line_out<T, NI, NO>(Ep, Om, bufA + le * A + ab, NO * NO,
+                                    out + (e0 + le) * NO3 + ab, NO * NO, accumulate);
   }
 }
 
@@ -243,7 +269,7 @@ static int launch_transfer_eo(const Level& f, const T* J, const T* in, const uin
                               bool accumulate, cudaStream_t s) {
   constexpr int NI = RESTRICT ? NF : NC, NO = RESTRICT ? NC : NF;
   constexpr int A = (NI * NI * NI > NO * NO * NI ? NI * NI * NI : NO * NO * NI);
-  constexpr int B = (NO * NI * NI > NO * NO * NO ? NO * NI * NI : NO * NO * NO);
+  constexpr int B = NO * NI * NI;
   // about 256 lines of the first direction per block, and at most 96 KB of shared memory (the
   // prolongation from N = 2 to 8 or 10 would need more than the 200 KB a block may have)
   constexpr int NE_LINES = (256 / (NI * NI)) < 1 ? 1 : (256 / (NI * NI));
