@@ -5,6 +5,8 @@
 // about one FP64 FMA per 11 bytes moved.  Inner products therefore apply the 1/multiplicity
 // weight (1, 1/2, 1/4 or 1/8, exact powers of two) to one operand by lowering its binary
 // exponent with integer instructions, leaving one FP64 FMA per point and product.
+#include <algorithm>
+
 #include "se_internal.h"
 #include "reduce.h"
 
@@ -12,19 +14,39 @@ namespace se {
 
 // Generic fused elementwise + reduction kernel.  Op provides:
 //   static constexpr int K (number of reduced values, >= 1),
-//   __device__ void point(int64_t i, double (&acc)[K])
-//   __device__ void finalize(const double* sums)   (K sums, called once by the last block)
+//   struct V (the values one point loads),
+//   __device__ void setup()   (loop-invariant scalars, read once per thread into the op's copy),
+//   __device__ V load(int64_t i) const,
+//   __device__ void apply(int64_t i, const V& v, double (&acc)[K]) const   (stores, sums),
+//   __device__ void finalize(const double* sums)   (K sums, called once by the last block).
+// A thread walks its points (grid stride) U at a time: all loads of the U points are issued
+// before the first store, since a store could alias a later point's load and would otherwise
+// hold it back.  U = 4 for ops that load two vectors, 2 for more.  The grid is the blocks that
+// are resident at once (fused_blocks), so no block waits for a second wave.  The points and the
+// order of each thread's sums are those of the plain grid-stride loop over that grid.
+constexpr int FUSED_U = 4;
+
 template <class Op>
-__global__ void __launch_bounds__(RED_THREADS) fused_kernel(Op op, int64_t n,
+__global__ void __launch_bounds__(RED_THREADS) fused_kernel(Op op_in, int64_t n,
                                                             double* __restrict__ partial,
                                                             unsigned* __restrict__ counter) {
   constexpr int K = Op::K;
+  constexpr int U = sizeof(typename Op::V) <= 24 ? FUSED_U : 2;
+  Op op = op_in;
+  op.setup();
   double acc[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) acc[k] = 0.0;
   const int64_t stride = (int64_t)gridDim.x * RED_THREADS;
-  for (int64_t i = (int64_t)blockIdx.x * RED_THREADS + threadIdx.x; i < n; i += stride)
-    op.point(i, acc);
+  int64_t i = (int64_t)blockIdx.x * RED_THREADS + threadIdx.x;
+  for (; i + (U - 1) * stride < n; i += U * stride) {
+    typename Op::V v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = op.load(i + u * stride);
+#pragma unroll
+    for (int u = 0; u < U; ++u) op.apply(i + u * stride, v[u], acc);
+  }
+  for (; i < n; i += stride) op.apply(i, op.load(i), acc);
   {
     __shared__ double sh[K][RED_THREADS / 32];
     __shared__ bool last;
@@ -54,11 +76,27 @@ __global__ void __launch_bounds__(RED_THREADS) fused_kernel(Op op, int64_t n,
   }
 }
 
+// Blocks of fused_kernel<Op> resident on the device at once (at most RED_MAX_BLOCKS), once per
+// op type; the device's SM count, not a fixed one.
+template <class Op>
+static int64_t fused_blocks() {
+  static const int64_t cap = [] {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_kernel<Op>, RED_THREADS, 0) != cudaSuccess ||
+        sms < 1 || per_sm < 1)
+      return (int64_t)RED_MAX_BLOCKS;
+    return std::min<int64_t>(RED_MAX_BLOCKS, (int64_t)sms * per_sm);
+  }();
+  return cap;
+}
+
 template <class Op>
 static int run_fused(const Op& op, int64_t n, Scratch& sc, cudaStream_t s, int kind, double bytes,
                      double flops) {
   ProfScope prof(kind, s, (double)n, bytes, flops);
-  const unsigned blocks = grid_for(n, RED_THREADS, RED_MAX_BLOCKS);
+  const unsigned blocks = grid_for(n, RED_THREADS, fused_blocks<Op>());
   fused_kernel<Op><<<blocks, RED_THREADS, 0, s>>>(op, n, sc.partial, sc.counter);
   SE_LAUNCH_CHECK();
   return SE_OK;
@@ -71,8 +109,11 @@ struct DotOp {  // dst = (a, b)
   const double* b;
   const uint8_t* pf;
   double* dst;
-  __device__ void point(int64_t i, double (&acc)[1]) const {
-    acc[0] = fma(scale_pow2(a[i], mult_log2(pf[i])), b[i], acc[0]);
+  struct V { double a, b; uint8_t f; };
+  __device__ void setup() {}
+  __device__ V load(int64_t i) const { return {a[i], b[i], pf[i]}; }
+  __device__ void apply(int64_t, const V& v, double (&acc)[1]) const {
+    acc[0] = fma(scale_pow2(v.a, mult_log2(v.f)), v.b, acc[0]);
   }
   __device__ void finalize(const double* s) const { *dst = s[0]; }
 };
@@ -153,47 +194,71 @@ template int scale_mul<float>(const float*, const float*, float*, int64_t, cudaS
 //   k_d = 1 + c1, k_r = scale (1 + c1) + c2, c1s = c1 scale, k_s = -scale,
 //   k_sl = -c2 scale (from_r) or -c2, the weight of the surrogate output in the last update.
 // RS (FROM_R only): the smoothed residual of the first step is dinv .* rin, formed here.
+// In FP64 the last step with RS is bound by the FP64 pipe (about 4 instructions per point against
+// 4-5 words): it factors dinv out of its two terms.
+constexpr int CHEB_U = 2;
+
 template <class T, bool FIRST, bool FROM_R, bool LAST, bool RS = false>
 __global__ void cheb_update_kernel(T* __restrict__ x, T* __restrict__ d, T* __restrict__ r,
                                    const T* __restrict__ sv, const T* __restrict__ dinv, int64_t n,
                                    T c1, T c2, T scale, T k_d, T k_r, T c1s, T k_s, T k_sl,
                                    const T* __restrict__ rin) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  // every load of this instantiation is unconditional, so all are in flight together
-  const T s0 = sv[i];
-  const T di = dinv ? dinv[i] : T(1);
-  const T r0 = RS ? di * rin[i] : r[i];
-  const T d0 = FROM_R ? T(0) : d[i];
-  const T x0 = FIRST ? T(0) : x[i];
-  if constexpr (LAST) {
-    // x + d + c1 d + c2 (r - s)
-    const T w = dinv ? k_sl * di : k_sl;
-    const T t = FIRST ? w * s0 : fma(w, s0, x0);
-    x[i] = FROM_R ? fma(k_r, r0, t) : fma(k_d, d0, fma(c2, r0, t));
-  } else if constexpr (FROM_R) {
-    // d = scale r: x + d, r - scale s, c1 d + c2 r'
-    const T w = dinv ? k_s * di : k_s;
-    const T rv = fma(w, s0, r0);
-    x[i] = FIRST ? scale * r0 : fma(scale, r0, x0);
-    r[i] = rv;
-    d[i] = fma(c1s, r0, c2 * rv);
-  } else {
-    const T sval = dinv ? di * s0 : s0;
-    const T rv = r0 - sval;
-    x[i] = FIRST ? d0 : x0 + d0;
-    r[i] = rv;
-    d[i] = fma(c1, d0, c2 * rv);
+  // CHEB_U points per thread, blockDim apart (coalesced): every load of the CHEB_U points is
+  // issued before the first store
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x * CHEB_U + threadIdx.x;
+  T s0[CHEB_U], di[CHEB_U], r0[CHEB_U], d0[CHEB_U], x0[CHEB_U];
+#pragma unroll
+  for (int u = 0; u < CHEB_U; ++u) {
+    const int64_t i = i0 + (int64_t)u * blockDim.x;
+    if (i < n) {
+      s0[u] = sv[i];
+      di[u] = dinv ? dinv[i] : T(1);
+      r0[u] = RS ? rin[i] : r[i];
+      d0[u] = FROM_R ? T(0) : d[i];
+      x0[u] = FIRST ? T(0) : x[i];
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < CHEB_U; ++u) {
+    const int64_t i = i0 + (int64_t)u * blockDim.x;
+    if (i >= n) break;
+    if constexpr (RS && LAST) {
+      // x + dinv (k_r rin + k_sl s): three FP64 instructions per point (the form below takes
+      // four with the scaled residual formed first; this kernel is bound by the FP64 pipe)
+      const T u2 = fma(k_r, r0[u], k_sl * s0[u]);
+      x[i] = FIRST ? di[u] * u2 : fma(di[u], u2, x0[u]);
+      continue;
+    }
+    if (RS) r0[u] = di[u] * r0[u];
+    if constexpr (LAST) {
+      // x + d + c1 d + c2 (r - s)
+      const T w = dinv ? k_sl * di[u] : k_sl;
+      const T t = FIRST ? w * s0[u] : fma(w, s0[u], x0[u]);
+      x[i] = FROM_R ? fma(k_r, r0[u], t) : fma(k_d, d0[u], fma(c2, r0[u], t));
+    } else if constexpr (FROM_R) {
+      // d = scale r: x + d, r - scale s, c1 d + c2 r'
+      const T w = dinv ? k_s * di[u] : k_s;
+      const T rv = fma(w, s0[u], r0[u]);
+      x[i] = FIRST ? scale * r0[u] : fma(scale, r0[u], x0[u]);
+      r[i] = rv;
+      d[i] = fma(c1s, r0[u], c2 * rv);
+    } else {
+      const T sval = dinv ? di[u] * s0[u] : s0[u];
+      const T rv = r0[u] - sval;
+      x[i] = FIRST ? d0[u] : x0[u] + d0[u];
+      r[i] = rv;
+      d[i] = fma(c1, d0[u], c2 * rv);
+    }
   }
 }
 template <class T>
 int cheb_update(T* x, T* d, T* r, const T* sv, const T* dinv, int64_t n, T c1, T c2, bool first,
-                cudaStream_t s, T scale, bool from_r, bool last, const T* rin) {
+                cudaStream_t s, T scale, bool from_r, bool last, const T* rin, int prof_p) {
   SE_CHECK(!rin || (from_r && dinv), SE_EINVAL, "cheb_update: a scaled residual needs the first step and dinv");
   const double words = 2.0 + (dinv ? 1.0 : 0.0) + (from_r ? 0.0 : 1.0) + (first ? 0.0 : 1.0) +
                        (last ? 1.0 : 3.0);
-  ProfScope prof(SE_K_CHEBY_UPD, s, (double)n, words * n * sizeof(T), 6.0 * n, prof_variant<T>(0));
-  const unsigned g = grid_for(n, 256);
+  ProfScope prof(SE_K_CHEBY_UPD, s, (double)n, words * n * sizeof(T), 6.0 * n, prof_variant<T>(prof_p));
+  const unsigned g = grid_for((n + CHEB_U - 1) / CHEB_U, 256);
   const int key = (rin ? 8 : 0) + (first ? 4 : 0) + (from_r ? 2 : 0) + (last ? 1 : 0);
   const double C1 = (double)c1, C2 = (double)c2, SC = (double)scale;
   const T k_d = T(1.0 + C1), k_r = T(SC * (1.0 + C1) + C2), c1s = T(C1 * SC), k_s = T(-SC);
@@ -216,9 +281,10 @@ int cheb_update(T* x, T* d, T* r, const T* sv, const T* dinv, int64_t n, T c1, T
   return SE_OK;
 }
 template int cheb_update<double>(double*, double*, double*, const double*, const double*, int64_t,
-                                 double, double, bool, cudaStream_t, double, bool, bool, const double*);
+                                 double, double, bool, cudaStream_t, double, bool, bool, const double*,
+                                 int);
 template int cheb_update<float>(float*, float*, float*, const float*, const float*, int64_t, float,
-                                float, bool, cudaStream_t, float, bool, bool, const float*);
+                                float, bool, cudaStream_t, float, bool, bool, const float*, int);
 
 // ------------------------------------------------------------------ FPCG kernels (FP64)
 struct AlphaOp {  // pw = (p, w); alpha = rz / pw
@@ -227,8 +293,11 @@ struct AlphaOp {  // pw = (p, w); alpha = rz / pw
   const double* w;
   const uint8_t* pf;
   double* scal;
-  __device__ void point(int64_t i, double (&acc)[1]) const {
-    acc[0] = fma(scale_pow2(p[i], mult_log2(pf[i])), w[i], acc[0]);
+  struct V { double p, w; uint8_t f; };
+  __device__ void setup() {}
+  __device__ V load(int64_t i) const { return {p[i], w[i], pf[i]}; }
+  __device__ void apply(int64_t, const V& v, double (&acc)[1]) const {
+    acc[0] = fma(scale_pow2(v.p, mult_log2(v.f)), v.w, acc[0]);
   }
   __device__ void finalize(const double* s) const {
     scal[SC_PW] = s[0];
@@ -245,12 +314,15 @@ struct UpdateXROp {  // x += alpha p; r2 = r - alpha w; rr = (r2, r2)
   double* r2;
   const uint8_t* pf;
   double* scal;
-  __device__ void point(int64_t i, double (&acc)[1]) const {
-    const double alpha = scal[SC_ALPHA];
-    x[i] = fma(alpha, p[i], x[i]);
-    const double rv = fma(-alpha, w[i], r[i]);
+  double alpha;
+  struct V { double x, p, r, w; uint8_t f; };
+  __device__ void setup() { alpha = scal[SC_ALPHA]; }
+  __device__ V load(int64_t i) const { return {x[i], p[i], r[i], w[i], pf[i]}; }
+  __device__ void apply(int64_t i, const V& v, double (&acc)[1]) const {
+    x[i] = fma(alpha, v.p, v.x);
+    const double rv = fma(-alpha, v.w, v.r);
     r2[i] = rv;
-    acc[0] = fma(scale_pow2(rv, mult_log2(pf[i])), rv, acc[0]);
+    acc[0] = fma(scale_pow2(rv, mult_log2(v.f)), rv, acc[0]);
   }
   __device__ void finalize(const double* s) const { scal[SC_RR] = s[0]; }
 };
@@ -262,10 +334,13 @@ struct BetaOp {  // zr = (z, r2); zro = (z, r); beta = (zr - zro)/rz; rz = zr
   const double* r;
   const uint8_t* pf;
   double* scal;
-  __device__ void point(int64_t i, double (&acc)[2]) const {
-    const double zw = scale_pow2(z[i], mult_log2(pf[i]));
-    acc[0] = fma(zw, r2[i], acc[0]);
-    acc[1] = fma(zw, r[i], acc[1]);
+  struct V { double z, r2, r; uint8_t f; };
+  __device__ void setup() {}
+  __device__ V load(int64_t i) const { return {z[i], r2[i], r[i], pf[i]}; }
+  __device__ void apply(int64_t, const V& v, double (&acc)[2]) const {
+    const double zw = scale_pow2(v.z, mult_log2(v.f));
+    acc[0] = fma(zw, v.r2, acc[0]);
+    acc[1] = fma(zw, v.r, acc[1]);
   }
   __device__ void finalize(const double* s) const {
     scal[SC_BETA] = (s[0] - s[1]) / scal[SC_RZ];
@@ -279,11 +354,13 @@ struct RZInitOp {  // rz = (r, z); rr = (r, r); r0 = rr
   const double* z;
   const uint8_t* pf;
   double* scal;
-  __device__ void point(int64_t i, double (&acc)[2]) const {
-    const double rv = r[i];
-    const double rw = scale_pow2(rv, mult_log2(pf[i]));
-    acc[0] = fma(rw, z[i], acc[0]);
-    acc[1] = fma(rw, rv, acc[1]);
+  struct V { double r, z; uint8_t f; };
+  __device__ void setup() {}
+  __device__ V load(int64_t i) const { return {r[i], z[i], pf[i]}; }
+  __device__ void apply(int64_t, const V& v, double (&acc)[2]) const {
+    const double rw = scale_pow2(v.r, mult_log2(v.f));
+    acc[0] = fma(rw, v.z, acc[0]);
+    acc[1] = fma(rw, v.r, acc[1]);
   }
   __device__ void finalize(const double* s) const {
     scal[SC_RZ] = s[0];
@@ -294,8 +371,22 @@ struct RZInitOp {  // rz = (r, z); rr = (r, r); r0 = rr
 
 __global__ void pupdate_kernel(double* __restrict__ p, const double* __restrict__ z,
                                const double* __restrict__ scal, int64_t n) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) p[i] = fma(scal[SC_BETA], p[i], z[i]);
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x * FUSED_U + threadIdx.x;
+  const double beta = scal[SC_BETA];
+  double pv[FUSED_U], zv[FUSED_U];
+#pragma unroll
+  for (int u = 0; u < FUSED_U; ++u) {
+    const int64_t i = i0 + (int64_t)u * blockDim.x;
+    if (i < n) {
+      pv[u] = p[i];
+      zv[u] = z[i];
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < FUSED_U; ++u) {
+    const int64_t i = i0 + (int64_t)u * blockDim.x;
+    if (i < n) p[i] = fma(beta, pv[u], zv[u]);
+  }
 }
 
 int fpcg_init(const Level& lv, const double* r, const double* z, Scratch& sc, cudaStream_t s) {
@@ -318,7 +409,7 @@ int fpcg_beta(const Level& lv, const double* z, const double* r2, const double* 
 }
 int fpcg_pupdate(const Level& lv, double* p, const double* z, Scratch& sc, cudaStream_t s) {
   ProfScope prof(SE_K_KRYLOV, s, (double)lv.L, lv.L * 24.0, lv.L * 2.0);
-  pupdate_kernel<<<grid_for(lv.L, 256), 256, 0, s>>>(p, z, sc.scal, lv.L);
+  pupdate_kernel<<<grid_for((lv.L + FUSED_U - 1) / FUSED_U, 256), 256, 0, s>>>(p, z, sc.scal, lv.L);
   SE_LAUNCH_CHECK();
   return SE_OK;
 }
@@ -331,8 +422,11 @@ struct DotToSlotOp {  // scal[slot] = (a, b)
   const uint8_t* pf;
   double* scal;
   int slot;
-  __device__ void point(int64_t i, double (&acc)[1]) const {
-    acc[0] = fma(scale_pow2(a[i], mult_log2(pf[i])), b[i], acc[0]);
+  struct V { double a, b; uint8_t f; };
+  __device__ void setup() {}
+  __device__ V load(int64_t i) const { return {a[i], b[i], pf[i]}; }
+  __device__ void apply(int64_t, const V& v, double (&acc)[1]) const {
+    acc[0] = fma(scale_pow2(v.a, mult_log2(v.f)), v.b, acc[0]);
   }
   __device__ void finalize(const double* s) const { scal[slot] = s[0]; }
 };
@@ -345,10 +439,14 @@ struct AxpyDotOp {  // w -= scal[hslot] v; scal[nslot] = (w, vnext) (vnext may b
   const uint8_t* pf;
   double* scal;
   int hslot, nslot;
-  __device__ void point(int64_t i, double (&acc)[1]) const {
-    const double wv = fma(-scal[hslot], v[i], w[i]);
+  double h;
+  struct V { double v, w, vn; uint8_t f; };
+  __device__ void setup() { h = scal[hslot]; }
+  __device__ V load(int64_t i) const { return {v[i], w[i], vnext ? vnext[i] : 0.0, pf[i]}; }
+  __device__ void apply(int64_t i, const V& q, double (&acc)[1]) const {
+    const double wv = fma(-h, q.v, q.w);
     w[i] = wv;
-    acc[0] = fma(scale_pow2(wv, mult_log2(pf[i])), vnext ? vnext[i] : wv, acc[0]);
+    acc[0] = fma(scale_pow2(wv, mult_log2(q.f)), vnext && vnext != w ? q.vn : wv, acc[0]);
   }
   __device__ void finalize(const double* s) const { scal[nslot] = s[0]; }
 };
@@ -419,14 +517,16 @@ struct UpdateXR2Op {
   double* r_old;
   const uint8_t* pf;
   double* scal;
-  __device__ void point(int64_t i, double (&acc)[1]) const {
-    const double alpha = scal[SC_ALPHA];
-    x[i] = fma(alpha, p[i], x[i]);
-    const double ro = r[i];
-    r_old[i] = ro;
-    const double rv = fma(-alpha, w[i], ro);
+  double alpha;
+  struct V { double x, p, r, w; uint8_t f; };
+  __device__ void setup() { alpha = scal[SC_ALPHA]; }
+  __device__ V load(int64_t i) const { return {x[i], p[i], r[i], w[i], pf[i]}; }
+  __device__ void apply(int64_t i, const V& v, double (&acc)[1]) const {
+    x[i] = fma(alpha, v.p, v.x);
+    r_old[i] = v.r;
+    const double rv = fma(-alpha, v.w, v.r);
     r[i] = rv;
-    acc[0] = fma(scale_pow2(rv, mult_log2(pf[i])), rv, acc[0]);
+    acc[0] = fma(scale_pow2(rv, mult_log2(v.f)), rv, acc[0]);
   }
   __device__ void finalize(const double* s) const { scal[SC_RR] = s[0]; }
 };

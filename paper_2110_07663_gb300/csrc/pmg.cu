@@ -142,7 +142,7 @@ int cheby(se_pmg_s* P, int l, const T* res, T* x, bool first, cudaStream_t s) {
     }
     SE_TRY(cheb_update<T>(x, V.cd, V.cr, sa, jac ? dinv_of<T>(lv) : (const T*)nullptr, lv.L, c1, c2,
                           first && k == 0, s, inv_theta, from_r, last,
-                          fused && from_r ? res : (const T*)nullptr));  // last: also x += d
+                          fused && from_r ? res : (const T*)nullptr, lv.p));  // last: also x += d
     rho = rho_new;
   }
   return SE_OK;

@@ -275,7 +275,7 @@ template <class T>
 // here instead of read from r (r is then only written, when the step is not the last)
 int cheb_update(T* x, T* d, T* r, const T* sv, const T* dinv, int64_t n, T c1, T c2,
                 bool first, cudaStream_t s, T scale = T(1), bool from_r = false, bool last = false,
-                const T* rin = nullptr);
+                const T* rin = nullptr, int prof_p = 0);  // prof_p: the level's order, for profiles
 template <class T>
 int scale_mul(const T* a, const T* b, T* out, int64_t n, cudaStream_t s);  // out = a*b
 // FP64 Krylov kernels with device scalars (slots of Scratch::scal)
