@@ -218,6 +218,8 @@ int ax_local(const Level& lv, const T* u, T* y, bool mask_in, cudaStream_t s, co
 //      interface copies by shuffles (below);
 //   y: lanes run along i: rows of N contiguous copies;
 //   z: lanes run along (i, j): planes of N^2 contiguous copies.
+// The y and z sweeps run as one launch (gs_sweep_yz): a node with copies across a y- and a
+// z-interface is summed by one thread in the order of the two sweeps.
 // Masking (Dirichlet) zeroes the copies on Dirichlet faces within the x sweep, before any sum (a
 // node on such a face has all its copies there), so the sweeps then add zeros for masked nodes;
 // a lattice one element wide in x has a separate mask kernel.

@@ -231,7 +231,7 @@ int gsmap_apply(const Level& lv, T* u, bool mask, cudaStream_t s);
 int build_level_gsmap(Level& lv, Allocs& allocs, cudaStream_t s);
 // FP64 operator with the x part of QQ^T and the mask inside the even-odd kernel (even N, box
 // lattice, sweeps): y = A u, or b - A u when b is given; the x-interfaces between the kernel's
-// blocks, then the y and z sweeps follow (ax.cu).
+// blocks, then the y/z launch follow (ax.cu).
 bool ax_fold_ok(const Level& lv);
 // dinv: y = A (dinv .* u) (the input scaled as it is loaded)
 int ax_apply_folded(const Level& lv, const double* u, double* y, const double* b, cudaStream_t s,
