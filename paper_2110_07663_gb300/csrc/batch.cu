@@ -58,20 +58,34 @@ __device__ __forceinline__ int seg_member(const SegMap& g, int b) {
 
 // Fused elementwise + reduction per member: per-block partial sums, summed in block order by the
 // member's last block (deterministic).  Members whose active flag is 0 are skipped entirely.
+// Op: K, struct V (one point's loads), setup(m) (the member's scalars), load(i), apply(i, v, acc),
+// finalize(m, sums).  A thread takes its points U at a time with all their loads issued before
+// the first store (a store could alias a later load); the order of its sums is unchanged.
 template <class Op>
-__global__ void __launch_bounds__(RED_THREADS) seg_fused_kernel(Op op, SegMap g, const int* __restrict__ active,
+__global__ void __launch_bounds__(RED_THREADS) seg_fused_kernel(Op op_in, SegMap g, const int* __restrict__ active,
                                                                 double* __restrict__ partial,
                                                                 unsigned* __restrict__ counter) {
   constexpr int K = Op::K;
+  constexpr int U = sizeof(typename Op::V) <= 24 ? 4 : 2;
   const int m = seg_member(g, blockIdx.x);
   if (active && !active[m]) return;  // uniform over the member's blocks
   const int b0 = g.sboff[m], nb = g.sboff[m + 1] - b0, local = blockIdx.x - b0;
+  Op op = op_in;
+  op.setup(m);
   double acc[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) acc[k] = 0.0;
   const int64_t beg = g.off[m] + (int64_t)local * g.chunk;
   const int64_t end = min(beg + g.chunk, g.off[m + 1]);
-  for (int64_t i = beg + threadIdx.x; i < end; i += RED_THREADS) op.point(i, m, acc);
+  int64_t i = beg + threadIdx.x;
+  for (; i + (U - 1) * RED_THREADS < end; i += U * RED_THREADS) {
+    typename Op::V v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = op.load(i + u * RED_THREADS);
+#pragma unroll
+    for (int u = 0; u < U; ++u) op.apply(i + u * RED_THREADS, v[u], acc);
+  }
+  for (; i < end; i += RED_THREADS) op.apply(i, op.load(i), acc);
   __shared__ double sh[K][RED_THREADS / 32];
   __shared__ bool last;
   block_sum<K>(acc, sh);
@@ -105,11 +119,13 @@ struct SegInitOp {  // rz = (r, z), rr = (r, r), r0 = rr
   const double* z;
   const uint8_t* pf;
   double* scal;
-  __device__ void point(int64_t i, int, double (&acc)[2]) const {
-    const double rv = r[i];
-    const double rw = scale_pow2(rv, mult_log2(pf[i]));
-    acc[0] = fma(rw, z[i], acc[0]);
-    acc[1] = fma(rw, rv, acc[1]);
+  struct V { double r, z; uint8_t f; };
+  __device__ void setup(int) {}
+  __device__ V load(int64_t i) const { return {r[i], z[i], pf[i]}; }
+  __device__ void apply(int64_t, const V& v, double (&acc)[2]) const {
+    const double rw = scale_pow2(v.r, mult_log2(v.f));
+    acc[0] = fma(rw, v.z, acc[0]);
+    acc[1] = fma(rw, v.r, acc[1]);
   }
   __device__ void finalize(int m, const double* s) const {
     double* q = scal + m * SG_SLOTS;
@@ -124,8 +140,11 @@ struct SegNormOp {  // r0 = (b, b): the reference of the ||b||-relative stopping
   const double* b;
   const uint8_t* pf;
   double* scal;
-  __device__ void point(int64_t i, int, double (&acc)[1]) const {
-    acc[0] = fma(scale_pow2(b[i], mult_log2(pf[i])), b[i], acc[0]);
+  struct V { double b; uint8_t f; };
+  __device__ void setup(int) {}
+  __device__ V load(int64_t i) const { return {b[i], pf[i]}; }
+  __device__ void apply(int64_t, const V& v, double (&acc)[1]) const {
+    acc[0] = fma(scale_pow2(v.b, mult_log2(v.f)), v.b, acc[0]);
   }
   __device__ void finalize(int m, const double* s) const { scal[m * SG_SLOTS + SG_R0] = s[0]; }
 };
@@ -136,8 +155,11 @@ struct SegAlphaOp {  // pw = (p, w); alpha = rz / pw
   const double* w;
   const uint8_t* pf;
   double* scal;
-  __device__ void point(int64_t i, int, double (&acc)[1]) const {
-    acc[0] = fma(scale_pow2(p[i], mult_log2(pf[i])), w[i], acc[0]);
+  struct V { double p, w; uint8_t f; };
+  __device__ void setup(int) {}
+  __device__ V load(int64_t i) const { return {p[i], w[i], pf[i]}; }
+  __device__ void apply(int64_t, const V& v, double (&acc)[1]) const {
+    acc[0] = fma(scale_pow2(v.p, mult_log2(v.f)), v.w, acc[0]);
   }
   __device__ void finalize(int m, const double* s) const {
     double* q = scal + m * SG_SLOTS;
@@ -155,14 +177,16 @@ struct SegUpdateOp {  // x += alpha p; r_old = r; r -= alpha w; rr = (r, r)
   double* r_old;
   const uint8_t* pf;
   double* scal;
-  __device__ void point(int64_t i, int m, double (&acc)[1]) const {
-    const double alpha = scal[m * SG_SLOTS + SG_ALPHA];
-    x[i] = fma(alpha, p[i], x[i]);
-    const double ro = r[i];
-    r_old[i] = ro;
-    const double rv = fma(-alpha, w[i], ro);
+  double alpha;
+  struct V { double x, p, r, w; uint8_t f; };
+  __device__ void setup(int m) { alpha = scal[m * SG_SLOTS + SG_ALPHA]; }
+  __device__ V load(int64_t i) const { return {x[i], p[i], r[i], w[i], pf[i]}; }
+  __device__ void apply(int64_t i, const V& v, double (&acc)[1]) const {
+    x[i] = fma(alpha, v.p, v.x);
+    r_old[i] = v.r;
+    const double rv = fma(-alpha, v.w, v.r);
     r[i] = rv;
-    acc[0] = fma(scale_pow2(rv, mult_log2(pf[i])), rv, acc[0]);
+    acc[0] = fma(scale_pow2(rv, mult_log2(v.f)), rv, acc[0]);
   }
   __device__ void finalize(int m, const double* s) const { scal[m * SG_SLOTS + SG_RR] = s[0]; }
 };
@@ -174,10 +198,13 @@ struct SegBetaOp {  // zr = (z, r); zro = (z, r_old); beta = (zr - zro) / rz; rz
   const double* r_old;
   const uint8_t* pf;
   double* scal;
-  __device__ void point(int64_t i, int, double (&acc)[2]) const {
-    const double zw = scale_pow2(z[i], mult_log2(pf[i]));
-    acc[0] = fma(zw, r[i], acc[0]);
-    acc[1] = fma(zw, r_old[i], acc[1]);
+  struct V { double z, r, ro; uint8_t f; };
+  __device__ void setup(int) {}
+  __device__ V load(int64_t i) const { return {z[i], r[i], r_old[i], pf[i]}; }
+  __device__ void apply(int64_t, const V& v, double (&acc)[2]) const {
+    const double zw = scale_pow2(v.z, mult_log2(v.f));
+    acc[0] = fma(zw, v.r, acc[0]);
+    acc[1] = fma(zw, v.ro, acc[1]);
   }
   __device__ void finalize(int m, const double* s) const {
     double* q = scal + m * SG_SLOTS;
@@ -195,7 +222,18 @@ __global__ void __launch_bounds__(RED_THREADS) seg_pupdate_kernel(double* __rest
   const double beta = scal[m * SG_SLOTS + SG_BETA];
   const int64_t beg = g.off[m] + (int64_t)(blockIdx.x - g.sboff[m]) * g.chunk;
   const int64_t end = min(beg + g.chunk, g.off[m + 1]);
-  for (int64_t i = beg + threadIdx.x; i < end; i += RED_THREADS) p[i] = fma(beta, p[i], z[i]);
+  int64_t i = beg + threadIdx.x;
+  for (; i + 3 * RED_THREADS < end; i += 4 * RED_THREADS) {
+    double pv[4], zv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      pv[u] = p[i + u * RED_THREADS];
+      zv[u] = z[i + u * RED_THREADS];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) p[i + u * RED_THREADS] = fma(beta, pv[u], zv[u]);
+  }
+  for (; i < end; i += RED_THREADS) p[i] = fma(beta, p[i], z[i]);
 }
 
 // Members' vectors to and from the union vector: piece m of u is member m's vector.
