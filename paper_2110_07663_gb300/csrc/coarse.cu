@@ -1018,22 +1018,13 @@ constexpr int64_t NOALLOC_WORDS =
     NOALLOC_VECTORS * NOALLOC_MAX_N + 8 * NOALLOC_MAX_BLOCKS + 2 + NOALLOC_MAX_BLOCKS / 2;
 static __device__ __align__(256) double g_coarse_scratch[NOALLOC_WORDS];
 
-static std::mutex g_noalloc_mu;
-static double* g_noalloc_ptr[64] = {};  // device address of g_coarse_scratch, per device
-
 // Host code must not use g_coarse_scratch itself (that name is a host-side stand-in): the
-// device address is looked up once per device, with that device current.
+// device address is looked up on every call, with the caller's device current (cheap, and never
+// stale after a device reset).
 static int noalloc_scratch(double** out) {
-  int dev = 0;
-  SE_CUDA(cudaGetDevice(&dev));
-  SE_CHECK(dev >= 0 && dev < 64, SE_EINVAL, "device ordinal %d out of range", dev);
-  std::lock_guard<std::mutex> g(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    SE_CUDA(cudaGetSymbolAddress(&p, g_coarse_scratch));
-    g_noalloc_ptr[dev] = static_cast<double*>(p);
-  }
-  *out = g_noalloc_ptr[dev];
+  void* p = nullptr;
+  SE_CUDA(cudaGetSymbolAddress(&p, g_coarse_scratch));
+  *out = static_cast<double*>(p);
   return SE_OK;
 }
 }  // namespace se
