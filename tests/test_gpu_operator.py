@@ -201,12 +201,14 @@ def test_fp32_pipelined_operator_steady_state_and_residual_forms():
     ((1, 4, 6), 7, ("D",) * 6),                        # no x-interface
     ((21, 2, 2), 1, ("D", "D", "N", "N", "D", "D")),   # p = 1: blocks of 64 elements
     ((7, 6, 5), 9, ("D",) * 6),                        # blocks of 3
+    ((16, 3, 2), 7, ("D", "N", "D", "D", "N", "D")),   # 4 blocks of 4 per row
+    ((32, 2, 2), 5, ("N", "D", "D", "D", "D", "N")),   # 4 blocks of 8 per row
 ])
 @pytest.mark.parametrize("fp32", [False, True])
 def test_folded_operator_against_the_oracle(nel, p, bc, fp32):
     """The FP64 operator at even N and the FP32 pipelined operator do the x part of QQ^T and the
     Dirichlet mask inside their blocks (element groups), then the x-interfaces between blocks and
-    the y and z sweeps: r = b - A u through se_residual on ragged and mixed-boundary meshes,
+    the y and z directions: r = b - A u through se_residual on ragged and mixed-boundary meshes,
     element by element against the oracle (1e-12 in FP64, 2e-5 in FP32); all copies of every
     node bitwise equal."""
     c = Case(nel, p, seed=17, bc=bc)
