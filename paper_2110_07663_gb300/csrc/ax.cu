@@ -320,8 +320,8 @@ __global__ void gs_sweep_yz(int nx, int ny, int nz, T* __restrict__ u) {
   const int nthr = (total + K - 1) / K;
   const int t0 = (int)(blockIdx.x * blockDim.x + threadIdx.x);
   if (t0 >= nthr) return;
-  const int64_t exy = (int64_t)nx * ny;
-  int64_t ia[K], ib[K], ic[K], id[K];
+  const int exy = nx * ny;
+  int ia[K], ib[K], ic[K], id[K];  // point indices < L < 2^31
   T a[K], b[K], c[K], d[K];
 #pragma unroll
   for (int kk = 0; kk < K; ++kk) {
@@ -338,9 +338,9 @@ __global__ void gs_sweep_yz(int nx, int ny, int nz, T* __restrict__ u) {
       const int ey = q % ny1;
       const int ez = q / ny1;
       if (k == 0 && ez > 0) continue;                 // in the group of e - nx ny
-      const int64_t e = ex + (int64_t)nx * (ey + (int64_t)ny * ez);
+      const int e = ex + nx * (ey + ny * ez);
       ia[kk] = e * N3 + i + N * ((N - 1) + N * k);     // element e, j = p
-      ib[kk] = (e + nx) * N3 + i + (int64_t)N2 * k;    // element e + nx, j = 0
+      ib[kk] = (e + nx) * N3 + i + N2 * k;             // element e + nx, j = 0
       a[kk] = u[ia[kk]];
       b[kk] = u[ib[kk]];
       if (k == N - 1 && ez < nz1) {                    // four copies: also k = 0 of e + nx ny
@@ -352,9 +352,9 @@ __global__ void gs_sweep_yz(int nx, int ny, int nz, T* __restrict__ u) {
     } else if (t < total) {
       const int tz = t - ty;
       const int ij = tz % N2;
-      const int64_t e = tz / N2;                       // elements with ez < nz - 1, in order
+      const int e = tz / N2;                           // elements with ez < nz - 1, in order
       const int j = ij / N;
-      const int ey = (int)((e / nx) % ny);
+      const int ey = (e / nx) % ny;
       if ((j == N - 1 && ey < ny1) || (j == 0 && ey > 0)) continue;  // in a y-item's group
       ia[kk] = e * N3 + ij + N2 * (N - 1);             // element e, k = p
       ib[kk] = (e + exy) * N3 + ij;                    // element e + nx ny, k = 0
