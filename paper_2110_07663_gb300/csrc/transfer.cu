@@ -2,7 +2,8 @@
 //   prolongation  e_f = (J x J x J) e_c            element by element
 //   restriction   r_c = M_c QQ^T_c (J^T x J^T x J^T)(r_f / mult_f)
 // with J_ij = h^c_j(xi^f_i).  For a continuous r_f the restriction is the transpose of the
-// global prolongation.  The three directions are contracted in turn in shared memory.
+// global prolongation.  The three directions are contracted in turn through shared memory (the
+// folded kernel stores the last one straight from its lines).
 //
 // Both GLL node sets are symmetric about 0 and h^c_{Nc-1-j}(-x) = h^c_j(x), so J is
 // centro-symmetric: J[Nf-1-i][Nc-1-j] = J[i][j] (and so is J^T).  For even Nf and Nc each line
@@ -16,7 +17,8 @@
 // elements per block.  Odd N (even orders) use the plain kernel, one element per block.
 // The restriction's 1/mult_f (1, 1/2, 1/4, 1/8) is applied by lowering the binary exponent with
 // integer instructions (scale_pow2), not by an FP64 multiply: exact for every value above 2^-1019
-// (2^-123 in FP32), and the FP64 pipe keeps only the contractions.
+// (2^-123 in FP32; smaller magnitudes, far below any residual a solve forms, become 0), and the
+// FP64 pipe keeps only the contractions.
 #include "se_internal.h"
 #include "reduce.h"
 
