@@ -521,7 +521,10 @@ int ax_apply_folded(const Level& lv, const double* u, double* y, const double* b
   const int NE = ax_elems_per_block(lv.p, false);
   {
     const double pts = (double)lv.L;
-    ProfScope prof(SE_K_AX, s, pts, pts * ((b ? 9.0 : 8.0) * sizeof(double) + 1.0),
+    // u, y, 6 geometric factors, b (residual form) and D^-1 (scaled input) per point; the
+    // folded kernel reads no point flags (mask and weights from the lattice position)
+    ProfScope prof(SE_K_AX, s, pts,
+                   pts * (8.0 + (b ? 1.0 : 0.0) + (dinv ? 1.0 : 0.0)) * sizeof(double),
                    pts * (12.0 * lv.N + 15.0), prof_variant<double>(lv.p));
     SE_TRY(ax_local_eo_fold(lv, u, y, b, NE, s, dinv));
   }
